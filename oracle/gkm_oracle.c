@@ -1,0 +1,569 @@
+/*
+ * GK-means oracle: a plain, slow, FP64 CPU restatement of the graph-guided
+ * k-means of Deng & Zhao, "Fast k-means based on KNN Graph" (arXiv 1705.01813).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent checker for the CUDA
+ * library.  It shares no code, header, table or helper with the CUDA path, and
+ * only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+ * load it.  The product path never calls it.
+ *
+ * Every function follows the paper in its own order and notation:
+ *   - k-means objective and the two Lloyd steps: Eq. 1 and the paragraph after it (Sec. 1)
+ *   - composite vectors D_r and the objective I: Eq. 2 (Sec. 3.1)
+ *   - candidate clusters from the kappa neighbours: Alg. 2 (Sec. 4.2), in its
+ *     "closest centroid among the collected clusters" form (end of Sec. 4.2)
+ *   - KNN-graph construction by repeated fast k-means: Alg. 3 (Sec. 4.3)
+ *   - cluster count k0 = floor(n / xi): Alg. 3 and Sec. 4.3
+ *   - one k-means iteration per graph round: Sec. 4.5
+ *   - average distortion: Eq. 4 (Sec. 5.1)
+ *
+ * Readings where the paper is silent (all stated again where they are used):
+ *   R1 the sample's own cluster is a candidate as well as its neighbours';
+ *   R2 the assignment is synchronous (every sample against the previous centroids);
+ *   R3 ties go to the smaller (distance, label) / (distance, index) key;
+ *   R4 an empty cluster keeps its previous centroid and has no members;
+ *   R5 labels and centroids carry over from one graph round to the next;
+ *   R6 a cluster larger than max_cluster is cut into ceil(m / max_cluster)
+ *      runs of consecutive members (ascending sample id) whose sizes differ by
+ *      at most one;
+ *   R7 graph distances are squared Euclidean; graph rows hold no self and no
+ *      repeated neighbour and are sorted by (distance, index);
+ *   R8 random numbers come from the SplitMix64 generator (Steele, Lea & Flood,
+ *      OOPSLA 2014) used as a counter-based function, see or_draw().
+ *
+ * Inputs X are read as stored (FP32) and widened to FP64 element by element.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------- */
+/* R8: SplitMix64.  The published generator keeps a 64-bit state s, adds the   */
+/* constant gamma = 0x9E3779B97F4A7C15 and returns a mixed copy of the state.  */
+/* The j-th output (j >= 1) of the generator seeded with `key` is therefore    */
+/* mix(key + j * gamma); or_draw(key, c) returns output c + 1.                 */
+/* ------------------------------------------------------------------------- */
+static const uint64_t OR_GAMMA = 0x9E3779B97F4A7C15ULL;
+static const uint64_t OR_TAG_LABELS = 0x4C41424C00000000ULL; /* "LABL" */
+static const uint64_t OR_TAG_GRAPH = 0x4752415000000000ULL;  /* "GRAP" */
+
+static uint64_t or_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* The generator as published: advance the state, return the mixed state. */
+uint64_t or_splitmix64_next(uint64_t *state)
+{
+    *state += OR_GAMMA;
+    return or_mix(*state);
+}
+
+uint64_t or_draw(uint64_t key, uint64_t counter)
+{
+    return or_mix(key + (counter + 1) * OR_GAMMA);
+}
+
+/* squared Euclidean distance in FP64, inputs widened exactly */
+static double or_d2_ff(const float *a, const float *b, int64_t d)
+{
+    double s = 0.0;
+    for (int64_t t = 0; t < d; t++) {
+        double diff = (double)a[t] - (double)b[t];
+        s += diff * diff;
+    }
+    return s;
+}
+
+static double or_d2_fd(const float *a, const double *c, int64_t d)
+{
+    double s = 0.0;
+    for (int64_t t = 0; t < d; t++) {
+        double diff = (double)a[t] - c[t];
+        s += diff * diff;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Seeded initial state                                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Seeded random initial labelling: label of sample i = draw(seed^LABL, i) mod k. */
+void or_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels)
+{
+    uint64_t key = seed ^ OR_TAG_LABELS;
+    for (int64_t i = 0; i < n; i++)
+        labels[i] = (int32_t)(or_draw(key, (uint64_t)i) % (uint64_t)k);
+}
+
+/* Key order of R3/R7: smaller distance first, then smaller index. */
+static int or_key_less(double da, int32_t ia, double db, int32_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+/* insertion sort of one graph row by (distance, index) */
+static void or_sort_row(int32_t *idx, double *dist, int32_t len)
+{
+    for (int32_t a = 1; a < len; a++) {
+        int32_t ii = idx[a];
+        double dd = dist[a];
+        int32_t b = a - 1;
+        while (b >= 0 && or_key_less(dd, ii, dist[b], idx[b])) {
+            idx[b + 1] = idx[b];
+            dist[b + 1] = dist[b];
+            b--;
+        }
+        idx[b + 1] = ii;
+        dist[b + 1] = dd;
+    }
+}
+
+/*
+ * Random initial KNN graph (Alg. 3, "Initialize G^t with random lists").
+ * Row i draws j = draw(seed^GRAP, i * 2^32 + a) mod n for a = 0, 1, ...,
+ * rejects j == i and indices it already holds, and stops at kappa accepted.
+ * The row is then sorted by (distance, index) (R7).
+ */
+void or_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                   int32_t *g_idx, double *g_dist)
+{
+    uint64_t key = seed ^ OR_TAG_GRAPH;
+    for (int64_t i = 0; i < n; i++) {
+        int32_t *row = g_idx + i * kappa;
+        double *rd = g_dist + i * kappa;
+        int32_t got = 0;
+        for (uint64_t a = 0; got < kappa; a++) {
+            int64_t j = (int64_t)(or_draw(key, ((uint64_t)i << 32) | a) % (uint64_t)n);
+            if (j == i)
+                continue;
+            int dup = 0;
+            for (int32_t q = 0; q < got; q++)
+                if (row[q] == j) {
+                    dup = 1;
+                    break;
+                }
+            if (dup)
+                continue;
+            row[got] = (int32_t)j;
+            rd[got] = or_d2_ff(X + i * ld, X + j * ld, d);
+            got++;
+        }
+        or_sort_row(row, rd, kappa);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Assignment: Alg. 2 with the closest-centroid rule (GK-means^-)            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * For each listed sample i (all samples when rows == NULL):
+ *   Q = { L[i] } (R1)  union  { L[G[i][j]] : j < kappa }   (Alg. 2, candidate loop)
+ *   L'[i] = the r in Q with the smallest (||x_i - C_r||^2, r)  (R2, R3)
+ * best[i] receives that distance and uniq[i] (optional) the size of Q.
+ * When kappa == 0 and all_clusters != 0 every cluster is a candidate
+ * (exhaustive Lloyd assignment, the textbook rule after Eq. 1).
+ */
+static void or_assign_impl(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *G, int32_t kappa,
+                           const double *C, int32_t k, const int32_t *L_in, int32_t *L_out, double *best,
+                           int32_t *uniq, const int64_t *rows, int64_t nrows, int all_clusters)
+{
+    int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kappa + 1));
+    int64_t cnt = rows ? nrows : n;
+    for (int64_t r = 0; r < cnt; r++) {
+        int64_t i = rows ? rows[r] : r;
+        const float *x = X + i * ld;
+        int32_t bestr = -1;
+        double bestd = 0.0;
+        int32_t u = 0;
+        if (all_clusters) {
+            for (int32_t c = 0; c < k; c++) {
+                double dd = or_d2_fd(x, C + (int64_t)c * d, d);
+                if (bestr < 0 || or_key_less(dd, c, bestd, bestr)) {
+                    bestd = dd;
+                    bestr = c;
+                }
+            }
+            u = k;
+        } else {
+            Q[u++] = L_in[i];
+            for (int32_t j = 0; j < kappa; j++) {
+                int32_t lab = L_in[G[i * kappa + j]];
+                int seen = 0;
+                for (int32_t q = 0; q < u; q++)
+                    if (Q[q] == lab) {
+                        seen = 1;
+                        break;
+                    }
+                if (!seen)
+                    Q[u++] = lab;
+            }
+            for (int32_t q = 0; q < u; q++) {
+                double dd = or_d2_fd(x, C + (int64_t)Q[q] * d, d);
+                if (bestr < 0 || or_key_less(dd, Q[q], bestd, bestr)) {
+                    bestd = dd;
+                    bestr = Q[q];
+                }
+            }
+        }
+        if (L_out)
+            L_out[rows ? r : i] = bestr;
+        if (best)
+            best[rows ? r : i] = bestd;
+        if (uniq)
+            uniq[rows ? r : i] = u;
+    }
+    free(Q);
+}
+
+void or_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *G, int32_t kappa,
+               const double *C, int32_t k, const int32_t *L_in, int32_t *L_out, double *best, int32_t *uniq,
+               const int64_t *rows, int64_t nrows)
+{
+    or_assign_impl(X, n, d, ld, G, kappa, C, k, L_in, L_out, best, uniq, rows, nrows, 0);
+}
+
+/* Exhaustive Lloyd assignment: every one of the k centroids is a candidate. */
+void or_assign_exhaustive(const float *X, int64_t n, int64_t d, int64_t ld, const double *C, int32_t k,
+                          int32_t *L_out, double *best)
+{
+    or_assign_impl(X, n, d, ld, NULL, 0, C, k, NULL, L_out, best, NULL, NULL, 0, 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Update: centroid = mean of members (Sec. 1), D_r of Eq. 2, E of Eq. 4     */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * counts[r] = n_r, D_r = sum of the members of S_r (ascending sample order),
+ * C_r = D_r / n_r, and an empty cluster keeps its previous C_r (R4).
+ * On return *E = (1/n) sum_i ||x_i - C_{L[i]}||^2 (Eq. 4, computed directly)
+ * and, if I_out is given, *I_out = sum_r D_r'D_r / n_r (Eq. 2).
+ */
+void or_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *L, int32_t k, double *C,
+               int64_t *counts, double *E, double *I_out)
+{
+    double *D = (double *)calloc((size_t)k * (size_t)d, sizeof(double));
+    for (int32_t r = 0; r < k; r++)
+        counts[r] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int32_t r = L[i];
+        counts[r]++;
+        for (int64_t t = 0; t < d; t++)
+            D[(int64_t)r * d + t] += (double)X[i * ld + t];
+    }
+    double I = 0.0;
+    for (int32_t r = 0; r < k; r++) {
+        if (counts[r] == 0)
+            continue;
+        double dd = 0.0;
+        for (int64_t t = 0; t < d; t++) {
+            C[(int64_t)r * d + t] = D[(int64_t)r * d + t] / (double)counts[r];
+            dd += D[(int64_t)r * d + t] * D[(int64_t)r * d + t];
+        }
+        I += dd / (double)counts[r];
+    }
+    if (E) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            s += or_d2_fd(X + i * ld, C + (int64_t)L[i] * d, d);
+        *E = s / (double)n;
+    }
+    if (I_out)
+        *I_out = I;
+    free(D);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fit: C^0 = update(L^0); then T times { assign; update }                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * E_log (2*iters + 1 entries): E after the initial update, then for each
+ * iteration E after the assignment (mean best distance against the previous
+ * centroids) and E after the update.  C starts at zero so that a cluster
+ * empty from the start has a defined (unused) centroid.
+ */
+void or_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *G, int32_t kappa,
+            int32_t iters, const int32_t *L0, int32_t *L, double *C, int64_t *counts, double *E_log)
+{
+    int32_t *L2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *best = (double *)malloc(sizeof(double) * (size_t)n);
+    memcpy(L, L0, sizeof(int32_t) * (size_t)n);
+    memset(C, 0, sizeof(double) * (size_t)k * (size_t)d);
+    or_update(X, n, d, ld, L, k, C, counts, &E_log[0], NULL);
+    for (int32_t t = 0; t < iters; t++) {
+        or_assign(X, n, d, ld, G, kappa, C, k, L, L2, best, NULL, NULL, 0);
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            s += best[i];
+        E_log[1 + 2 * t] = s / (double)n;
+        memcpy(L, L2, sizeof(int32_t) * (size_t)n);
+        or_update(X, n, d, ld, L, k, C, counts, &E_log[2 + 2 * t], NULL);
+    }
+    free(L2);
+    free(best);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Graph refinement: Alg. 3, exhaustive pairs inside each cluster            */
+/* ------------------------------------------------------------------------- */
+
+/* Cluster set S as lists of members in ascending sample id (counting sort). */
+static void or_group(const int32_t *L, int64_t n, int32_t k, int64_t *offsets, int32_t *members)
+{
+    int64_t *fill = (int64_t *)calloc((size_t)k + 1, sizeof(int64_t));
+    for (int32_t r = 0; r <= k; r++)
+        offsets[r] = 0;
+    for (int64_t i = 0; i < n; i++)
+        offsets[L[i] + 1]++;
+    for (int32_t r = 0; r < k; r++)
+        offsets[r + 1] += offsets[r];
+    for (int64_t i = 0; i < n; i++) {
+        int32_t r = L[i];
+        members[offsets[r] + fill[r]] = (int32_t)i;
+        fill[r]++;
+    }
+    free(fill);
+}
+
+/*
+ * Merge the pair (dist, j) into row i (Alg. 3, "Update G[i] ... with d(x_i, x_j)"):
+ * the row keeps its kappa smallest keys (R3/R7), never holds j twice and never
+ * holds i.  The row is sorted, so the new key is placed by insertion.
+ */
+static void or_merge(int32_t *row, double *rd, int32_t kappa, int32_t i, double dist, int32_t j)
+{
+    if (j == i)
+        return;
+    for (int32_t q = 0; q < kappa; q++)
+        if (row[q] == j)
+            return;
+    if (!or_key_less(dist, j, rd[kappa - 1], row[kappa - 1]))
+        return;
+    int32_t b = kappa - 1;
+    while (b > 0 && or_key_less(dist, j, rd[b - 1], row[b - 1])) {
+        row[b] = row[b - 1];
+        rd[b] = rd[b - 1];
+        b--;
+    }
+    row[b] = j;
+    rd[b] = dist;
+}
+
+/* R6: sizes and starts of the runs a cluster of m members is cut into. */
+static int64_t or_nchunks(int64_t m, int32_t cap)
+{
+    return (m + cap - 1) / cap;
+}
+
+static void or_chunk(int64_t m, int64_t nc, int64_t c, int64_t *start, int64_t *size)
+{
+    int64_t base = m / nc, rem = m % nc;
+    *start = c * base + (c < rem ? c : rem);
+    *size = base + (c < rem ? 1 : 0);
+}
+
+/* bit set of visited pairs (Alg. 3, "if <i,j> is NOT visited"); n*n bits */
+typedef struct {
+    uint8_t *bits;
+    int64_t n;
+} or_visited;
+
+static int or_test_and_set(or_visited *v, int64_t i, int64_t j)
+{
+    int64_t a = i < j ? i : j, b = i < j ? j : i;
+    int64_t bit = a * v->n + b;
+    int was = (v->bits[bit >> 3] >> (bit & 7)) & 1;
+    v->bits[bit >> 3] |= (uint8_t)(1u << (bit & 7));
+    return was;
+}
+
+/*
+ * One refinement of G given labels L in [0, k): for every run of every
+ * cluster (R6) and every pair i < j in it, merge d(x_i, x_j) into rows i and j.
+ * With `visited`, a pair seen in an earlier call is skipped.
+ */
+static void or_refine_impl(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *L, int32_t k,
+                           int32_t kappa, int32_t cap, int32_t *g_idx, double *g_dist, or_visited *visited)
+{
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)k + 1));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_group(L, n, k, off, mem);
+    for (int32_t r = 0; r < k; r++) {
+        int64_t m = off[r + 1] - off[r];
+        if (m < 2)
+            continue;
+        int64_t nc = or_nchunks(m, cap);
+        for (int64_t c = 0; c < nc; c++) {
+            int64_t s0, sz;
+            or_chunk(m, nc, c, &s0, &sz);
+            const int32_t *S = mem + off[r] + s0;
+            for (int64_t a = 0; a < sz; a++) {
+                for (int64_t b = a + 1; b < sz; b++) {
+                    int32_t i = S[a], j = S[b];
+                    if (visited && or_test_and_set(visited, i, j))
+                        continue;
+                    double dist = or_d2_ff(X + (int64_t)i * ld, X + (int64_t)j * ld, d);
+                    or_merge(g_idx + (int64_t)i * kappa, g_dist + (int64_t)i * kappa, kappa, i, dist, j);
+                    or_merge(g_idx + (int64_t)j * kappa, g_dist + (int64_t)j * kappa, kappa, j, dist, i);
+                }
+            }
+        }
+    }
+    free(off);
+    free(mem);
+}
+
+void or_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *L, int32_t k,
+                     int32_t kappa, int32_t max_cluster, int32_t *g_idx, double *g_dist)
+{
+    or_refine_impl(X, n, d, ld, L, k, kappa, max_cluster, g_idx, g_dist, NULL);
+}
+
+/*
+ * The same refinement for a few listed rows only (for spot checks at sizes
+ * where the full refinement is too slow): rows_idx/rows_dist hold the listed
+ * rows' lists on entry (nrows x kappa) and their refined lists on return.
+ * Row i meets exactly the members of its own run, so this equals the full
+ * refinement restricted to those rows.
+ */
+void or_graph_refine_rows(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *L, int32_t k,
+                          int32_t kappa, int32_t max_cluster, const int64_t *rows, int64_t nrows,
+                          int32_t *rows_idx, double *rows_dist)
+{
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)k + 1));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_group(L, n, k, off, mem);
+    for (int64_t q = 0; q < nrows; q++) {
+        int64_t i = rows[q];
+        int32_t r = L[i];
+        int64_t m = off[r + 1] - off[r];
+        int64_t pos = -1;
+        for (int64_t a = 0; a < m; a++)
+            if (mem[off[r] + a] == i) {
+                pos = a;
+                break;
+            }
+        int64_t nc = or_nchunks(m, max_cluster);
+        for (int64_t c = 0; c < nc; c++) {
+            int64_t s0, sz;
+            or_chunk(m, nc, c, &s0, &sz);
+            if (pos < s0 || pos >= s0 + sz)
+                continue;
+            for (int64_t b = 0; b < sz; b++) {
+                int32_t j = mem[off[r] + s0 + b];
+                if (j == i)
+                    continue;
+                double dist = or_d2_ff(X + i * ld, X + (int64_t)j * ld, d);
+                or_merge(rows_idx + q * kappa, rows_dist + q * kappa, kappa, (int32_t)i, dist, j);
+            }
+        }
+    }
+    free(off);
+    free(mem);
+}
+
+/* CSR of the cluster set, exposed for checks of the grouping step. */
+void or_group_csr(const int32_t *L, int64_t n, int32_t k, int64_t *offsets, int32_t *members)
+{
+    or_group(L, n, k, offsets, members);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 3: KNN graph by repeated fast k-means                                */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * G^0 random (or_init_graph), k0 = floor(n / xi) (at least 1), L^0 seeded
+ * random labels in [0, k0), C = update(L^0); then tau rounds of
+ *   one GK-means iteration at k0 on G^t (Sec. 4.5: t = 1): L = assign(L, C, G^t), C = update(L)
+ *   exhaustive pairs inside each cluster merged into G (R6, R7).
+ * use_visited != 0 keeps the visited-pair set of Alg. 3 (needs n*n bits).
+ * L_out (optional) receives the final labels, E_log (optional, 2*tau+1
+ * entries) the distortion after the initial update and after each assign and
+ * update.
+ */
+int or_build_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, int32_t xi, int32_t tau,
+                   int32_t max_cluster, uint64_t seed, int use_visited, int32_t *g_idx, double *g_dist,
+                   int32_t *L_out, double *E_log)
+{
+    int32_t k0 = (int32_t)(n / xi);
+    if (k0 < 1)
+        k0 = 1;
+    int32_t *L = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *L2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *best = (double *)malloc(sizeof(double) * (size_t)n);
+    double *C = (double *)calloc((size_t)k0 * (size_t)d, sizeof(double));
+    int64_t *counts = (int64_t *)malloc(sizeof(int64_t) * (size_t)k0);
+    or_visited vis = {NULL, n};
+    if (use_visited) {
+        vis.bits = (uint8_t *)calloc((size_t)((n * n + 7) / 8), 1);
+        if (!vis.bits)
+            return 1;
+    }
+    or_init_graph(X, n, d, ld, kappa, seed, g_idx, g_dist);
+    or_init_labels(n, k0, seed, L);
+    double e0;
+    or_update(X, n, d, ld, L, k0, C, counts, &e0, NULL);
+    if (E_log)
+        E_log[0] = e0;
+    for (int32_t t = 0; t < tau; t++) {
+        or_assign(X, n, d, ld, g_idx, kappa, C, k0, L, L2, best, NULL, NULL, 0);
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            s += best[i];
+        memcpy(L, L2, sizeof(int32_t) * (size_t)n);
+        double e;
+        or_update(X, n, d, ld, L, k0, C, counts, &e, NULL);
+        if (E_log) {
+            E_log[1 + 2 * t] = s / (double)n;
+            E_log[2 + 2 * t] = e;
+        }
+        or_refine_impl(X, n, d, ld, L, k0, kappa, max_cluster, g_idx, g_dist, use_visited ? &vis : NULL);
+    }
+    if (L_out)
+        memcpy(L_out, L, sizeof(int32_t) * (size_t)n);
+    free(L);
+    free(L2);
+    free(best);
+    free(C);
+    free(counts);
+    free(vis.bits);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Brute force (textbook) checkers                                           */
+/* ------------------------------------------------------------------------- */
+
+/* Exact KNN graph: all pairs, rows sorted by (distance, index), no self. */
+void or_brute_knn(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, int32_t *g_idx, double *g_dist)
+{
+    for (int64_t i = 0; i < n; i++) {
+        int32_t *row = g_idx + i * kappa;
+        double *rd = g_dist + i * kappa;
+        int32_t got = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i)
+                continue;
+            double dist = or_d2_ff(X + i * ld, X + j * ld, d);
+            if (got < kappa) {
+                row[got] = (int32_t)j;
+                rd[got] = dist;
+                got++;
+                if (got == kappa)
+                    or_sort_row(row, rd, kappa);
+            } else {
+                or_merge(row, rd, kappa, (int32_t)i, dist, (int32_t)j);
+            }
+        }
+        if (got < kappa)
+            or_sort_row(row, rd, got);
+    }
+}

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each check compares the oracle with a value fixed by the paper or by
+mathematics: hand-worked examples (tests/golden/worked_1d.json), the published
+SplitMix64 outputs (tests/golden/splitmix64.json), special cases that reduce to
+textbook routines (a complete graph makes the graph-guided assignment
+exhaustive Lloyd; k0 = 1 makes Alg. 3 an exact KNN search), closed forms (the
+Eq. 2 identity n E = sum ||x||^2 - I), and invariants (non-increasing
+distortion, sorted duplicate-free graph rows, result-neutral visited set).
+
+The second half plants plausible mistakes in a copy of the oracle's C source
+and shows that at least one pin fails for each.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TAG_LABELS = 0x4C41424C00000000
+TAG_GRAPH = 0x4752415000000000
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _col(x):
+    return np.asarray(x, np.float32).reshape(-1, 1)
+
+
+def _blobs(n, d, centers, seed, spread=0.6):
+    g = np.random.default_rng(seed)
+    c = g.uniform(-5, 5, size=(centers, d))
+    z = g.integers(0, centers, n)
+    return (c[z] + spread * g.standard_normal((n, d))).astype(np.float32)
+
+
+def _np_means(X, L, k, C_old):
+    X64 = X.astype(np.float64)
+    S = np.zeros((k, X.shape[1]))
+    np.add.at(S, L, X64)
+    cnt = np.bincount(L, minlength=k)
+    C = C_old.copy()
+    nz = cnt > 0
+    C[nz] = S[nz] / cnt[nz, None]
+    return C, cnt
+
+
+def _np_d2(X, C):
+    X64 = X.astype(np.float64)
+    return ((X64[:, None, :] - np.asarray(C, np.float64)[None, :, :]) ** 2).sum(-1)
+
+
+# ---------------------------------------------------------------- checks ----
+
+def check_splitmix(orc):
+    g = _golden("splitmix64.json")
+    assert orc.splitmix64_stream(1234567, 5) == [int(v) for v in g["seed_1234567_first5"]]
+    assert orc.splitmix64_stream(0, 1)[0] == int(g["seed_0_first"])
+    # the counter form used for the seeded start is output c+1 of the published generator
+    for key in (0, 1234567, 0xDEADBEEF ^ TAG_LABELS):
+        seq = orc.splitmix64_stream(key, 40)
+        assert [orc.draw(key, c) for c in range(40)] == seq
+
+
+def check_init_labels(orc):
+    n, k, seed = 5000, 37, 99
+    L = orc.init_labels(n, k, seed)
+    seq = orc.splitmix64_stream(seed ^ TAG_LABELS, n)
+    assert np.array_equal(L, np.array([v % k for v in seq], np.int32))
+    cnt = np.bincount(L, minlength=k)
+    chi2 = ((cnt - n / k) ** 2 / (n / k)).sum()
+    assert chi2 < 3 * k  # roughly uniform
+
+
+def check_init_graph(orc):
+    X = _blobs(300, 5, 4, 3)
+    n, kappa, seed = X.shape[0], 7, 11
+    gi, gd = orc.init_graph(X, kappa, seed)
+    full = _np_d2(X, X)
+    key = seed ^ TAG_GRAPH
+    for i in range(n):
+        row = gi[i]
+        assert i not in row and len(set(row.tolist())) == kappa
+        assert np.array_equal(gd[i], full[i, row])
+        keys = list(zip(gd[i].tolist(), row.tolist()))
+        assert keys == sorted(keys)
+        # the set follows the rejection rule over the published generator's outputs
+        want, a = [], 0
+        while len(want) < kappa:
+            j = orc.draw(key, (i << 32) | a) % n
+            a += 1
+            if j != i and j not in want:
+                want.append(j)
+        assert sorted(want) == sorted(row.tolist())
+
+
+def check_worked_assign(orc):
+    g = _golden("worked_1d.json")
+    a = g["assign"]
+    X = _col(a["x"])
+    C, cnt, E, _ = orc.update(X, a["labels"], a["k"])
+    assert np.allclose(C, a["centroids_before"], rtol=0, atol=1e-15)
+    assert E == pytest.approx(a["distortion_before"], rel=1e-15)
+    Lo, best, uniq = orc.assign(X, a["graph"], C, a["labels"])
+    assert Lo.tolist() == a["labels_after_assign"]
+    assert np.allclose(best, a["best_d2"], rtol=0, atol=1e-15)
+    assert uniq.tolist() == a["uniq"]
+    assert best.mean() == pytest.approx(a["distortion_after_assign"], rel=1e-15)
+    C2, _, E2, _ = orc.update(X, Lo, a["k"], C)
+    assert np.allclose(C2, a["centroids_after_update"], rtol=0, atol=1e-15)
+    assert E2 == pytest.approx(a["distortion_after_update"], rel=1e-15)
+    for case in ("own_label", "tie"):
+        c = g[case]
+        Lo, _, _ = orc.assign(_col(c["x"]), c["graph"], c["centroids"], c["labels"])
+        assert Lo.tolist() == c["labels_after_assign"], case
+
+
+def check_assign_complete_graph(orc):
+    X = _blobs(60, 3, 5, 5)
+    n, k = X.shape[0], 7
+    g = np.random.default_rng(1)
+    L = g.permutation(np.arange(n) % k).astype(np.int32)
+    C, _, _, _ = orc.update(X, L, k)
+    G = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    Lg, bg, uq = orc.assign(X, G, C, L)
+    Le, be = orc.assign_exhaustive(X, C)
+    D = _np_d2(X, C)
+    assert np.array_equal(Lg, Le)
+    assert np.array_equal(Le, D.argmin(1).astype(np.int32))  # argmin: first (smaller) label on ties
+    assert np.allclose(be, D.min(1), rtol=1e-14, atol=0)
+    assert np.array_equal(bg, be)
+    assert (uq == k).all()
+
+
+def check_assign_restricted(orc):
+    """With a sparse graph only the own and the neighbours' clusters are candidates."""
+    X = _blobs(200, 4, 6, 7)
+    n, k, kappa = X.shape[0], 12, 3
+    g = np.random.default_rng(2)
+    L = g.integers(0, k, n).astype(np.int32)
+    C, _, E0, _ = orc.update(X, L, k)
+    G = np.stack([g.choice(np.delete(np.arange(n), i), kappa, replace=False) for i in range(n)]).astype(np.int32)
+    Lo, best, uq = orc.assign(X, G, C, L)
+    D = _np_d2(X, C)
+    for i in range(n):
+        Q = sorted(set([L[i]] + [L[j] for j in G[i]]))
+        assert uq[i] == len(Q)
+        sub = D[i, Q]
+        assert Lo[i] == Q[int(np.argmin(sub))]
+        assert best[i] == pytest.approx(sub.min(), rel=1e-14)
+    # own label among the candidates: the assignment never raises the distortion
+    assert best.mean() <= E0 * (1 + 1e-15)
+
+
+def check_update(orc):
+    X = _blobs(500, 6, 5, 9)
+    n, k = X.shape[0], 9
+    g = np.random.default_rng(3)
+    L = g.integers(0, k - 2, n).astype(np.int32)  # clusters k-2, k-1 empty
+    C_old = g.standard_normal((k, X.shape[1]))
+    C, cnt, E, I = orc.update(X, L, k, C_old)
+    Cn, cn = _np_means(X, L, k, C_old)
+    assert np.array_equal(cnt, cn)
+    assert np.allclose(C, Cn, rtol=1e-13, atol=1e-13)
+    assert np.array_equal(C[k - 2:], C_old[k - 2:])  # empty clusters keep their centroid
+    direct = ((X.astype(np.float64) - C[L]) ** 2).sum(1).mean()
+    assert E == pytest.approx(direct, rel=1e-12)
+    # Eq. 2: with exact means n E = sum ||x||^2 - sum_r D_r'D_r / n_r
+    sx = (X.astype(np.float64) ** 2).sum()
+    assert n * E == pytest.approx(sx - I, rel=1e-9)
+
+
+def _np_lloyd(X, L, k, iters):
+    C = np.zeros((k, X.shape[1]))
+    C, _ = _np_means(X, L, k, C)
+    for _ in range(iters):
+        L = _np_d2(X, C).argmin(1)
+        C, _ = _np_means(X, L, k, C)
+    return L.astype(np.int32), C
+
+
+def check_fit(orc):
+    X = _blobs(80, 2, 4, 13)
+    n, k, T = X.shape[0], 6, 5
+    L0 = orc.init_labels(n, k, 4)
+    G = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    L, C, cnt, E = orc.fit(X, k, G, T, L0)
+    Ln, Cn = _np_lloyd(X, L0, k, T)
+    assert np.array_equal(L, Ln)
+    assert np.allclose(C[cnt > 0], Cn[cnt > 0], rtol=1e-12, atol=1e-12)
+    assert (np.diff(E) <= 1e-12 * E[:-1]).all()
+    # a sparse graph: still non-increasing at every half step
+    Xb = _blobs(1500, 8, 30, 14)
+    Gb, _ = orc.brute_knn(Xb, 6)
+    L0b = orc.init_labels(Xb.shape[0], 40, 5)
+    _, _, _, Eb = orc.fit(Xb, 40, Gb, 6, L0b)
+    assert (np.diff(Eb) <= 1e-12 * Eb[:-1]).all()
+
+
+def check_worked_refine(orc):
+    r = _golden("worked_1d.json")["refine"]
+    X = _col(r["x"])
+    for cap, key in ((128, "cap128"), (2, "cap2")):
+        gi, gd = orc.graph_refine(X, r["labels"], r["k"], r["graph_idx"], r["graph_dist"], cap)
+        assert gi.tolist() == r[key + "_idx"], cap
+        assert gd.tolist() == [[float(v) for v in row] for row in r[key + "_dist"]], cap
+
+
+def _np_knn(X, kappa):
+    D = _np_d2(X, X)
+    n = X.shape[0]
+    idx = np.empty((n, kappa), np.int32)
+    for i in range(n):
+        js = np.array([j for j in range(n) if j != i])
+        order = np.lexsort((js, D[i, js]))[:kappa]
+        idx[i] = js[order]
+    return idx, np.take_along_axis(D, idx.astype(np.int64), 1)
+
+
+def check_exact_knn_special_case(orc):
+    X = _blobs(90, 4, 3, 21)
+    X[10] = X[3]  # an exact tie in distance
+    kappa = 8
+    bi, bd = orc.brute_knn(X, kappa)
+    ni, nd = _np_knn(X, kappa)
+    assert np.array_equal(bi, ni) and np.allclose(bd, nd, rtol=1e-14, atol=0)
+    # n < 2 xi gives k0 = 1: one cluster, one round of exhaustive pairs = exact KNN
+    gi, gd, L, _ = orc.build_graph(X, kappa, xi=50, tau=1, max_cluster=128, seed=3)
+    assert (L == 0).all()
+    assert np.array_equal(gi, bi) and np.array_equal(gd, bd)
+
+
+def _row_invariants(X, gi, gd):
+    n, kappa = gi.shape
+    full = _np_d2(X, X)
+    for i in range(n):
+        row = gi[i].tolist()
+        assert i not in row and len(set(row)) == kappa
+        keys = list(zip(gd[i].tolist(), row))
+        assert keys == sorted(keys)
+        assert np.allclose(gd[i], full[i, gi[i]], rtol=1e-14, atol=0)
+
+
+def check_graph_invariants_and_monotone(orc):
+    X = _blobs(700, 8, 12, 31)
+    kappa, xi = 10, 50
+    prev = None
+    bi, _ = orc.brute_knn(X, 1)
+    rec = []
+    for tau in range(0, 5):
+        gi, gd, _, E = orc.build_graph(X, kappa, xi=xi, tau=tau, max_cluster=128, seed=8)
+        _row_invariants(X, gi, gd)
+        if prev is not None:
+            # the kappa-th and top-1 keys only ever improve from round to round
+            assert (gd[:, -1] <= prev[1][:, -1]).all()
+            assert (gd[:, 0] <= prev[1][:, 0]).all()
+        rec.append(float((gi[:, 0] == bi[:, 0]).mean()))
+        prev = (gi, gd)
+    assert all(b >= a for a, b in zip(rec, rec[1:]))
+    assert rec[-1] > rec[0]
+
+
+def check_visited_neutral(orc):
+    X = _blobs(400, 6, 8, 41)
+    a = orc.build_graph(X, 9, xi=40, tau=4, max_cluster=32, seed=5, use_visited=False)
+    b = orc.build_graph(X, 9, xi=40, tau=4, max_cluster=32, seed=5, use_visited=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def check_refine_rows_and_chunks(orc):
+    X = _blobs(900, 5, 10, 51)
+    n, k, kappa, cap = X.shape[0], 6, 6, 40  # clusters of ~150 cut into runs of <= 40
+    g = np.random.default_rng(6)
+    L = g.integers(0, k, n).astype(np.int32)
+    gi0, gd0 = orc.init_graph(X, kappa, 77)
+    gi, gd = orc.graph_refine(X, L, k, gi0, gd0, cap)
+    rows = g.choice(n, 50, replace=False)
+    ri, rd = orc.graph_refine_rows(X, L, k, rows, gi0[rows], gd0[rows], cap)
+    assert np.array_equal(ri, gi[rows]) and np.array_equal(rd, gd[rows])
+    # every new neighbour comes from the row's own run of its cluster
+    off, mem = orc.group_csr(L, k)
+    run_of = np.empty(n, np.int64)
+    for r in range(k):
+        m = off[r + 1] - off[r]
+        nc = -(-m // cap)
+        base, rem = m // nc, m % nc
+        for c in range(nc):
+            s0 = c * base + min(c, rem)
+            sz = base + (1 if c < rem else 0)
+            assert sz <= cap and sz >= base
+            run_of[mem[off[r] + s0: off[r] + s0 + sz]] = r * 100000 + c
+    for i in range(n):
+        for j in set(gi[i].tolist()) - set(gi0[i].tolist()):
+            assert run_of[j] == run_of[i]
+
+
+def check_group_csr(orc):
+    g = np.random.default_rng(8)
+    L = g.integers(0, 50, 3000).astype(np.int32)
+    off, mem = orc.group_csr(L, 53)
+    assert np.array_equal(mem, np.argsort(L, kind="stable").astype(np.int32))
+    assert np.array_equal(off, np.concatenate([[0], np.cumsum(np.bincount(L, minlength=53))]))
+
+
+CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_assign_complete_graph,
+          check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
+          check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
+          check_group_csr]
+
+
+@pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
+def test_oracle_pin(check):
+    check(O.default())
+
+
+def test_paper_trends():
+    """Qualitative claims on synthetic data: recall rises with tau (Sec. 4.3, Fig. 3 text) and a
+    sample visits fewer clusters than it has neighbours (Sec. 4.2)."""
+    from paper_1705_01813_gb300 import datagen
+    X = datagen.gauss_mixture(3000, 16, 40, seed=1)
+    orc = O.default()
+    bi, _ = orc.brute_knn(X, 1)
+    r1 = (orc.build_graph(X, 10, xi=50, tau=1, seed=2)[0][:, 0] == bi[:, 0]).mean()
+    gi, gd, L, E = orc.build_graph(X, 10, xi=50, tau=6, seed=2)
+    r6 = (gi[:, 0] == bi[:, 0]).mean()
+    assert r6 > r1 and r6 > 0.5
+    k = 30
+    L0 = orc.init_labels(X.shape[0], k, 3)
+    Lf, C, cnt, Ef = orc.fit(X, k, gi, 5, L0)
+    _, _, uq = orc.assign(X, gi, C, Lf)
+    assert uq.mean() < 10
+    # close to exhaustive Lloyd from the same start (Sec. 5.3: quality drops very little)
+    Ln, Cn = _np_lloyd(X, L0, k, 5)
+    En = ((X.astype(np.float64) - Cn[Ln]) ** 2).sum(1).mean()
+    assert Ef[-1] <= En * 1.05
+
+
+# ------------------------------------------------------- planted mistakes ----
+
+MUTANTS = [
+    ("own_label_dropped", "Q[u++] = L_in[i];", "(void)0;", check_worked_assign),
+    ("tie_to_larger", "(da == db && ia < ib)", "(da == db && ia > ib)", check_worked_assign),
+    ("distance_sign", "double diff = (double)a[t] - c[t];", "double diff = (double)a[t] + c[t];",
+     check_worked_assign),
+    ("empty_cluster_zeroed", "        if (counts[r] == 0)\n            continue;\n        double dd = 0.0;",
+     "        if (counts[r] == 0) {\n            for (int64_t t = 0; t < d; t++) C[(int64_t)r * d + t] = 0.0;\n"
+     "            continue;\n        }\n        double dd = 0.0;", check_update),
+    ("I_without_division", "I += dd / (double)counts[r];", "I += dd;", check_update),
+    ("merge_without_dedupe", "        if (row[q] == j)\n            return;", "        if (0)\n            return;",
+     check_worked_refine),
+    ("run_start_wrong", "*start = c * base + (c < rem ? c : rem);", "*start = c * base;",
+     check_refine_rows_and_chunks),
+    ("knn_self_allowed", "            if (j == i)\n                continue;\n            double dist = or_d2_ff(X + i * ld",
+     "            double dist = or_d2_ff(X + i * ld", check_exact_knn_special_case),
+    ("init_graph_self_allowed", "            if (j == i)\n                continue;\n            int dup = 0;",
+     "            int dup = 0;", check_init_graph),
+    ("graph_seed_reused", "uint64_t key = seed ^ OR_TAG_GRAPH;", "uint64_t key = seed ^ OR_TAG_LABELS;",
+     check_init_graph),
+]
+
+
+@pytest.mark.parametrize("name,find,repl,check", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, name, find, repl, check):
+    src = open(os.path.join(os.path.dirname(O.__file__), "gkm_oracle.c")).read()
+    assert src.count(find) >= 1, name
+    mut = tmp_path / f"{name}.c"
+    mut.write_text(src.replace(find, repl))
+    lib = O.compile_source(str(mut), str(tmp_path / f"lib{name}.so"))
+    with pytest.raises(AssertionError):
+        check(O.Oracle(lib))
