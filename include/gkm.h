@@ -1,0 +1,198 @@
+/*
+ * gkm.h - C ABI of libgkm, a CUDA (sm_103a) implementation of graph-guided
+ * k-means ("GK-means", Deng & Zhao, "Fast k-means based on KNN Graph",
+ * arXiv 1705.01813).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is DEVICE memory owned by the caller unless it is
+ *    marked "host".  The library never allocates, frees or keeps a pointer
+ *    after the call returns (scratch comes from the caller's workspace `ws`).
+ *  - The sample matrix X is row-major: sample i, coordinate t at
+ *    X[i * ld + t], n rows (n < 2^31), d coordinates (1 <= d <= 4096),
+ *    ld >= d.  Element type: FP32.
+ *    X must be 4-byte aligned; with X 16-byte aligned and d, ld multiples
+ *    of 4 the kernels use 16-byte vector loads.
+ *  - Labels are int32 in [0, k).  A KNN graph is two n x kappa row-major
+ *    arrays: g_idx (int32 neighbour ids) and g_dist (FP32 squared Euclidean
+ *    distances); each row is sorted by (distance, id), holds no self and no
+ *    repeated id.
+ *  - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and is asynchronous unless the entry point says it synchronises.
+ *  - Arguments are checked on the host before anything is enqueued; a bad
+ *    argument returns GK_ERR_INVALID and gk_last_error() says why.  Errors the
+ *    kernels find (a label or neighbour id out of range) are recorded in a
+ *    status word inside `ws` and read back by gk_read_status().
+ *  - ws/ws_bytes: caller-provided device scratch of at least
+ *    gk_workspace_size(op, ...) bytes, 256-byte aligned.  A call that needs
+ *    more returns GK_ERR_INVALID with the required size in the message.
+ *    Concurrent calls must use distinct workspaces.
+ *  - The library is reentrant across streams; its only global state is the
+ *    thread-local message returned by gk_last_error().
+ */
+#ifndef GKM_H
+#define GKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GK_API __attribute__((visibility("default")))
+#else
+#define GK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GK_OK = 0,
+    GK_ERR_INVALID = 1, /* bad argument, or a kernel found an out-of-range label / id */
+    GK_ERR_CUDA = 2,    /* a CUDA runtime call failed */
+    GK_ERR_NOMEM = 3,   /* workspace too small for a data-dependent size */
+    GK_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up */
+    GK_ERR_NUMERIC = 5  /* non-finite value met */
+} gk_status;
+
+/* Operation ids for gk_workspace_size(). */
+enum {
+    GK_OP_ASSIGN = 0,
+    GK_OP_UPDATE = 1,
+    GK_OP_REFINE = 2,
+    GK_OP_FIT = 3,
+    GK_OP_BUILD = 4
+};
+
+/* Parameters of the graph construction (Alg. 3 and Sec. 4.4 of the paper). */
+typedef struct {
+    int32_t kappa;       /* neighbours per sample, 1 <= kappa <= 128 and kappa < n      */
+    int32_t xi;          /* target cluster size; k0 = max(1, floor(n / xi))  (Alg. 3)   */
+    int32_t tau;         /* refinement rounds (Alg. 3), >= 0                            */
+    int32_t max_cluster; /* a cluster larger than this is cut into runs of consecutive
+                            members (ascending id) whose sizes differ by at most one    */
+    uint64_t seed;       /* seed of the random initial graph and labels (SplitMix64)    */
+    int32_t precision;   /* 0: exact FP32 pair distances                                */
+    int32_t reserved;    /* must be 0                                                   */
+} gk_graph_params;
+
+/* Library version string (static storage). */
+GK_API const char *gk_version(void);
+
+/* Message of the last failed call on this host thread (static storage, never NULL). */
+GK_API const char *gk_last_error(void);
+
+/*
+ * Bytes of workspace the operation `op` (GK_OP_ASSIGN, _UPDATE, _REFINE, _FIT)
+ * needs for these sizes; 0 for an unknown op.  k is the number of clusters.
+ * The graph construction has its own query, gk_workspace_size_build().
+ */
+GK_API size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa);
+
+/* Workspace bytes of gk_build_knn_graph() for these sizes and parameters. */
+GK_API size_t gk_workspace_size_build(int64_t n, int64_t d, const gk_graph_params *p);
+
+/*
+ * Seeded random initial labelling (the paper starts from a partition; the
+ * random start replaces its two-means tree).  labels[i] = SplitMix64 output
+ * (i + 1) of the generator seeded with seed ^ 0x4C41424C00000000, modulo k.
+ * labels: device int32[n], written.
+ */
+GK_API int gk_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, void *stream);
+
+/*
+ * Random initial KNN graph ("Initialize G with random lists", Alg. 3).
+ * Row i takes draws j = output(i * 2^32 + a + 1) mod n, a = 0, 1, ..., of the
+ * SplitMix64 generator seeded with seed ^ 0x4752415000000000, rejecting j == i
+ * and ids it already holds, until kappa are accepted; their squared distances
+ * are computed in FP32 and the row sorted by (distance, id).
+ * g_idx: device int32[n * kappa], g_dist: device float[n * kappa], written.
+ */
+GK_API int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed, int32_t *g_idx,
+                  float *g_dist, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Graph-guided assignment step (Alg. 2, candidate loop, with the
+ * closest-centroid rule given at the end of Sec. 4.2).  For each sample i the
+ * candidate clusters are its own label and the labels of its kappa graph
+ * neighbours; labels_out[i] is the candidate r with the smallest
+ * (||x_i - C_r||^2, r).  All samples use the same input centroids.
+ *   g_idx     device int32[n * kappa], neighbour ids in [0, n)
+ *   C         device float[k * d], centroids, row-major with stride d
+ *   labels_in device int32[n];  labels_out device int32[n] (may not alias labels_in)
+ *   best_d2   device float[n] or NULL: the winning squared distance
+ *   sum_d2    device double[1] or NULL: sum of best_d2 (n times the distortion
+ *             after the assignment, Eq. 4), computed in FP64
+ *   n_changed device int64[1] or NULL: samples whose label changed
+ */
+GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                   const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                   double *sum_d2, int64_t *n_changed, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Centroid update (Sec. 1: each centroid becomes the mean of its members).
+ * Members are grouped by label (CSR, members in ascending id); per cluster the
+ * composite vector D_r (Eq. 2) is summed with compensated FP32 arithmetic and
+ * widened to FP64, and C_r = D_r / n_r.  An empty cluster keeps its centroid.
+ *   C        device float[k * d], in: previous centroids, out: new centroids
+ *   counts   device int32[k] or NULL: cluster sizes n_r
+ *   sum_d2   device double[1] or NULL: n times the distortion after the update
+ *            (Eq. 4), from the Eq. 2 identity sum ||x||^2 - sum_r D_r'D_r / n_r
+ *   offsets, members  device int32[k + 1] / int32[n] or NULL: the CSR grouping
+ *            (cluster r owns members[offsets[r] .. offsets[r+1]) )
+ */
+GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
+                   int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/*
+ * One graph refinement (Alg. 3, the exhaustive pairs inside each cluster):
+ * samples are grouped by label; a cluster of m > max_cluster members is cut
+ * into ceil(m / max_cluster) runs of consecutive members whose sizes differ by
+ * at most one; every pair (i, j) inside a run is merged into rows i and j, a
+ * row keeping its kappa smallest (distance, id) keys with no self and no
+ * repeated id.  Pair distances are squared Euclidean in FP32.
+ *   g_idx / g_dist  device, n x kappa, in: current graph, out: refined graph
+ */
+GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                    int32_t kappa, int32_t max_cluster, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/*
+ * KNN-graph construction by repeated fast k-means (Alg. 3): random graph and
+ * labels at k0 = max(1, floor(n / xi)), centroids from those labels, then tau
+ * rounds of { one graph-guided assignment, one update, one refinement }
+ * (one k-means iteration per round, Sec. 4.5; labels and centroids carry over
+ * from round to round).
+ *   labels_out device int32[n] or NULL: the final labels at k0
+ *   e_log      HOST double[2 * tau + 1] or NULL: distortion after the first
+ *              update, then after each assignment and update.  A non-NULL
+ *              e_log makes the call synchronise the stream.
+ */
+GK_API int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p, int32_t *g_idx,
+                       float *g_dist, int32_t *labels_out, double *e_log, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Graph-guided k-means (Alg. 2 with the closest-centroid rule): centroids
+ * from the initial labels, then `iters` x { assignment, update }.
+ *   init_labels device int32[n] or NULL (NULL: gk_init_labels(seed))
+ *   labels_out  device int32[n]; C_out device float[k * d]; counts_out device int32[k] or NULL
+ *   e_log       HOST double[2 * iters + 1] or NULL, as in gk_build_knn_graph
+ *               (non-NULL synchronises the stream)
+ */
+GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
+                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
+                  int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Synchronise `stream`, return the status word the kernels of calls that used
+ * `ws` recorded (GK_OK if none), and clear it.  Also returns GK_ERR_CUDA if the
+ * stream itself reports an error.
+ */
+GK_API int gk_read_status(void *ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKM_H */

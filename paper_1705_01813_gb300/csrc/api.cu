@@ -1,0 +1,357 @@
+// C entry points of libgkm (declared in include/gkm.h): argument checks,
+// workspace layout and the step sequences of the fit (Alg. 2 with the
+// closest-centroid rule) and of the graph construction (Alg. 3).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+using namespace gkm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define GK_CUDA(call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(GK_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                    \
+    } while (0)
+
+constexpr int64_t MAX_ROWS = (int64_t)1 << 31;
+constexpr int MAX_LOG = 4096;  // e_log entries kept on the device
+constexpr int MAX_D = 4096;    // the assignment stages one sample per warp in shared memory
+
+int check_x(const float *X, int64_t n, int64_t d, int64_t ld, int64_t min_n)
+{
+    if (!X)
+        return fail(GK_ERR_INVALID, "X is NULL");
+    if (n < min_n || n >= MAX_ROWS)
+        return fail(GK_ERR_INVALID, "n = %lld out of range [%lld, 2^31)", (long long)n, (long long)min_n);
+    if (d < 1 || d > MAX_D)
+        return fail(GK_ERR_INVALID, "d = %lld out of range [1, %d]", (long long)d, MAX_D);
+    if (ld < d)
+        return fail(GK_ERR_INVALID, "ld = %lld < d = %lld", (long long)ld, (long long)d);
+    if ((reinterpret_cast<uintptr_t>(X) & 3) != 0)
+        return fail(GK_ERR_INVALID, "X is not 4-byte aligned");
+    return GK_OK;
+}
+
+int check_kappa(int32_t kappa, int64_t n)
+{
+    if (kappa < 1 || kappa > MAX_KAPPA || (int64_t)kappa >= n)
+        return fail(GK_ERR_INVALID, "kappa = %d out of range [1, min(%d, n - 1)]", kappa, MAX_KAPPA);
+    return GK_OK;
+}
+
+int check_ws(void *ws, size_t ws_bytes, size_t need)
+{
+    if (!ws)
+        return fail(GK_ERR_INVALID, "workspace is NULL (needs %zu bytes)", need);
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0)
+        return fail(GK_ERR_INVALID, "workspace is not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(GK_ERR_INVALID, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+    return GK_OK;
+}
+
+// Workspace layouts.  Every layout starts with the device status word.
+struct GroupBufs {
+    int32_t *offsets, *members, *counts;
+    void *scratch;
+};
+
+struct Layout {
+    DevStatus *st;
+    // grouping
+    GroupBufs grp;
+    void *upd_scratch;
+    void *asg_scratch;
+    int32_t *labels_a;
+    int32_t *labels_b;
+    float *cent;
+    double *elog;
+    size_t bytes;
+};
+
+Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
+{
+    Carver cv{static_cast<char *>(ws), 0, 0};
+    Layout L{};
+    L.st = cv.take<DevStatus>(1);
+    bool need_group = op == GK_OP_UPDATE || op == GK_OP_REFINE || op == GK_OP_FIT || op == GK_OP_BUILD;
+    bool need_update = op == GK_OP_UPDATE || op == GK_OP_FIT || op == GK_OP_BUILD;
+    bool need_assign = op == GK_OP_ASSIGN || op == GK_OP_FIT || op == GK_OP_BUILD;
+    if (need_group) {
+        L.grp.offsets = cv.take<int32_t>((size_t)k + 1);
+        L.grp.members = cv.take<int32_t>((size_t)n);
+        L.grp.counts = cv.take<int32_t>((size_t)k);
+        L.grp.scratch = cv.take<char>(group_scratch_bytes(n, k));
+    }
+    if (need_update)
+        L.upd_scratch = cv.take<char>(update_scratch_bytes(n, k));
+    if (need_assign)
+        L.asg_scratch = cv.take<char>(assign_scratch_bytes(n));
+    if (op == GK_OP_FIT || op == GK_OP_BUILD) {
+        L.labels_b = cv.take<int32_t>((size_t)n);
+        L.elog = cv.take<double>(MAX_LOG);
+    }
+    if (op == GK_OP_BUILD) {
+        L.labels_a = cv.take<int32_t>((size_t)n);
+        L.cent = cv.take<float>((size_t)k * (size_t)d);
+    }
+    L.bytes = cv.off;
+    return L;
+}
+
+int32_t build_k0(int64_t n, int32_t xi) { return (int32_t)(n / xi > 0 ? n / xi : 1); }
+
+}  // namespace
+
+extern "C" {
+
+const char *gk_version(void) { return "libgkm 0.1 (sm_103a)"; }
+
+const char *gk_last_error(void) { return g_err; }
+
+size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa)
+{
+    (void)kappa;
+    if (op < GK_OP_ASSIGN || op > GK_OP_FIT || n < 0 || d < 0 || k < 0)
+        return 0;
+    return carve(nullptr, op, n, d, k).bytes;
+}
+
+size_t gk_workspace_size_build(int64_t n, int64_t d, const gk_graph_params *p)
+{
+    if (!p || p->xi < 1 || n < 0 || d < 0)
+        return 0;
+    return carve(nullptr, GK_OP_BUILD, n, d, build_k0(n, p->xi)).bytes;
+}
+
+int gk_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, void *stream)
+{
+    if (n < 1 || n >= MAX_ROWS)
+        return fail(GK_ERR_INVALID, "n = %lld out of range", (long long)n);
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (!labels)
+        return fail(GK_ERR_INVALID, "labels is NULL");
+    GK_CUDA(launch_init_labels(n, k, seed, labels, (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed, int32_t *g_idx,
+                  float *g_dist, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (!g_idx || !g_dist)
+        return fail(GK_ERR_INVALID, "graph arrays are NULL");
+    if ((rc = check_ws(ws, ws_bytes, sizeof(DevStatus))))
+        return rc;
+    GK_CUDA(launch_init_graph(X, n, d, ld, kappa, seed, g_idx, g_dist, static_cast<DevStatus *>(ws),
+                              (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                   const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                   double *sum_d2, int64_t *n_changed, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (!g_idx || !C || !labels_in || !labels_out)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    if (labels_in == labels_out)
+        return fail(GK_ERR_INVALID, "labels_out must not alias labels_in");
+    Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_ASSIGN, n, d, k);
+    GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
+                          L.asg_scratch, L.st, (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
+                   int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws, size_t ws_bytes,
+                   void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 1)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (!labels || !C)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_UPDATE, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_UPDATE, n, d, k);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *off = offsets ? offsets : L.grp.offsets;
+    int32_t *mem = members ? members : L.grp.members;
+    int32_t *cnt = counts ? counts : L.grp.counts;
+    GK_CUDA(launch_group(labels, n, k, off, mem, cnt, L.grp.scratch, L.st, s));
+    GK_CUDA(launch_update(X, n, d, ld, off, mem, k, C, cnt, sum_d2, L.upd_scratch, s));
+    return GK_OK;
+}
+
+int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                    int32_t kappa, int32_t max_cluster, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
+                    void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (max_cluster < 2)
+        return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
+    if (!labels || !g_idx || !g_dist)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_REFINE, n, d, k);
+    cudaStream_t s = (cudaStream_t)stream;
+    GK_CUDA(launch_group(labels, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+    GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist, L.st, s));
+    return GK_OK;
+}
+
+int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
+                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
+                  int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (iters < 0 || 2 * iters + 1 > MAX_LOG)
+        return fail(GK_ERR_INVALID, "iters = %d out of range [0, %d]", iters, (MAX_LOG - 1) / 2);
+    if (!g_idx || !labels_out || !C_out)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_FIT, n, d, k);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *cnt = counts_out ? counts_out : L.grp.counts;
+
+    // ping-pong the labels so that the final ones land in labels_out
+    int32_t *cur = (iters % 2 == 0) ? labels_out : L.labels_b;
+    int32_t *nxt = (iters % 2 == 0) ? L.labels_b : labels_out;
+    if (init_labels)
+        GK_CUDA(cudaMemcpyAsync(cur, init_labels, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    else
+        GK_CUDA(launch_init_labels(n, k, seed, cur, s));
+    GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)k * (size_t)d, s));
+    GK_CUDA(launch_group(cur, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
+    GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
+    for (int t = 0; t < iters; t++) {
+        GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
+                              L.asg_scratch, L.st, s));
+        GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
+                              L.upd_scratch, s));
+        int32_t *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    if (e_log) {
+        GK_CUDA(cudaMemcpyAsync(e_log, L.elog, sizeof(double) * (size_t)(2 * iters + 1), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < 2 * iters + 1; q++)
+            e_log[q] /= (double)n;
+    }
+    return GK_OK;
+}
+
+int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p, int32_t *g_idx,
+                       float *g_dist, int32_t *labels_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if (!p)
+        return fail(GK_ERR_INVALID, "params is NULL");
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
+        return rc;
+    if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 || p->precision != 0 ||
+        p->reserved != 0)
+        return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
+                    p->max_cluster, p->precision);
+    if (!g_idx || !g_dist)
+        return fail(GK_ERR_INVALID, "graph arrays are NULL");
+    const int32_t k0 = build_k0(n, p->xi);
+    Layout L = carve(nullptr, GK_OP_BUILD, n, d, k0);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_BUILD, n, d, k0);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tau = p->tau;
+    int32_t *cur = L.labels_a, *nxt = L.labels_b;
+    GK_CUDA(launch_init_graph(X, n, d, ld, p->kappa, p->seed, g_idx, g_dist, L.st, s));
+    GK_CUDA(launch_init_labels(n, k0, p->seed, cur, s));
+    GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)k0 * (size_t)d, s));
+    GK_CUDA(launch_group(cur, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+    GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
+                          L.upd_scratch, s));
+    for (int t = 0; t < tau; t++) {
+        // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
+        GK_CUDA(launch_assign(X, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
+                              nullptr, L.asg_scratch, L.st, s));
+        GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
+                              L.elog + 2 + 2 * t, L.upd_scratch, s));
+        // exhaustive pairs inside the clusters of the new partition
+        GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
+                              g_dist, L.st, s));
+        int32_t *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    if (labels_out)
+        GK_CUDA(cudaMemcpyAsync(labels_out, cur, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (e_log) {
+        GK_CUDA(cudaMemcpyAsync(e_log, L.elog, sizeof(double) * (size_t)(2 * tau + 1), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < 2 * tau + 1; q++)
+            e_log[q] /= (double)n;
+    }
+    return GK_OK;
+}
+
+int gk_read_status(void *ws, void *stream)
+{
+    if (!ws)
+        return fail(GK_ERR_INVALID, "workspace is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    GK_CUDA(cudaStreamSynchronize(s));
+    unsigned h[2] = {0, 0};
+    GK_CUDA(cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0] != 0) {
+        GK_CUDA(cudaMemset(ws, 0, sizeof(h)));
+        return fail((int)h[0], "device status %u (detail %u)", h[0], h[1]);
+    }
+    return GK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// Graph-guided assignment (Alg. 2 candidate loop with the closest-centroid
+// rule of Sec. 4.2, "GK-means^-"):
+//   Q_i = { L[i] } u { L[G[i][j]] : j < kappa }          (candidate clusters)
+//   L'[i] = argmin over r in Q_i of (||x_i - C_r||^2, r)  (ties -> smaller label)
+//
+// One warp per sample.  The warp stages x_i in shared memory, gathers the
+// kappa + 1 candidate labels 32 at a time and removes repeats with
+// __match_any_sync plus a scan of the labels already kept, then each lane
+// takes candidates lane, lane + 32, ... and computes their distances with
+// 16-byte centroid loads; a shuffle reduction picks the (distance, label)
+// minimum.  Per-block FP64 partial sums of the winning distances and the
+// count of changed labels are reduced in a fixed order afterwards, so every
+// run gives the same bits.
+#include "common.cuh"
+
+namespace gkm {
+
+constexpr int AS_WARPS = 8;
+constexpr int AS_BLOCKS = 152 * 8;  // fixed grid: the FP64 partial sums have a fixed order
+constexpr int AS_QCAP = MAX_KAPPA + 1;
+
+template <int VEC>
+__device__ __forceinline__ float cand_d2(const float *__restrict__ xs, const float *__restrict__ c, int d);
+
+template <>
+__device__ __forceinline__ float cand_d2<4>(const float *__restrict__ xs, const float *__restrict__ c, int d)
+{
+    const float4 *x4 = reinterpret_cast<const float4 *>(xs);
+    const float4 *c4 = reinterpret_cast<const float4 *>(c);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const int nv = d >> 2;
+#pragma unroll 4
+    for (int t = 0; t < nv; t++) {
+        float4 xv = x4[t];
+        float4 cv = __ldg(c4 + t);
+        float e0 = xv.x - cv.x, e1 = xv.y - cv.y, e2 = xv.z - cv.z, e3 = xv.w - cv.w;
+        a0 = fmaf(e0, e0, a0);
+        a1 = fmaf(e1, e1, a1);
+        a2 = fmaf(e2, e2, a2);
+        a3 = fmaf(e3, e3, a3);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+template <>
+__device__ __forceinline__ float cand_d2<1>(const float *__restrict__ xs, const float *__restrict__ c, int d)
+{
+    float a0 = 0.f, a1 = 0.f;
+    int t = 0;
+    for (; t + 1 < d; t += 2) {
+        float e0 = xs[t] - __ldg(c + t), e1 = xs[t + 1] - __ldg(c + t + 1);
+        a0 = fmaf(e0, e0, a0);
+        a1 = fmaf(e1, e1, a1);
+    }
+    if (t < d) {
+        float e0 = xs[t] - __ldg(c + t);
+        a0 = fmaf(e0, e0, a0);
+    }
+    return a0 + a1;
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+                                                          const int32_t *__restrict__ G, int kappa,
+                                                          const float *__restrict__ C, int k,
+                                                          const int32_t *__restrict__ Lin,
+                                                          int32_t *__restrict__ Lout, float *__restrict__ best_out,
+                                                          double *__restrict__ blk_sum,
+                                                          unsigned long long *__restrict__ blk_changed,
+                                                          DevStatus *st)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int dpad = (d + 3) & ~3;
+    float *xs = smem + w * dpad;
+    int *qlist = reinterpret_cast<int *>(smem + AS_WARPS * dpad) + w * AS_QCAP;
+    __shared__ double s_sum[AS_WARPS];
+    __shared__ unsigned long long s_chg[AS_WARPS];
+
+    double wsum = 0.0;
+    unsigned long long wchg = 0;
+    const int ncand = kappa + 1;
+    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+        // stage x_i
+        const float *xi = X + i * ld;
+        if (VEC == 4) {
+            const float4 *x4 = reinterpret_cast<const float4 *>(xi);
+            for (int t = lane; t < (d >> 2); t += 32)
+                reinterpret_cast<float4 *>(xs)[t] = x4[t];
+        } else {
+            for (int t = lane; t < d; t += 32)
+                xs[t] = xi[t];
+        }
+        // candidate labels: slot 0 is the own label, slot 1 + j the label of neighbour j
+        const int own = Lin[i];
+        int u = 0;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            int c = c0 + lane;
+            int lab = -1;
+            if (c == 0) {
+                lab = own;
+            } else if (c < ncand) {
+                int nb = G[i * kappa + (c - 1)];
+                if ((unsigned)nb < (unsigned)n)
+                    lab = Lin[nb];
+                else
+                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
+            }
+            if (c < ncand && (unsigned)lab >= (unsigned)k) {
+                flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                lab = -1;
+            }
+            unsigned peers = __match_any_sync(FULL_MASK, lab);
+            bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
+            if (keep)
+                for (int q = 0; q < u; q++)
+                    if (qlist[q] == lab) {
+                        keep = false;
+                        break;
+                    }
+            unsigned keeps = __ballot_sync(FULL_MASK, keep);
+            __syncwarp();
+            if (keep)
+                qlist[u + __popc(keeps & lanemask_lt())] = lab;
+            u += __popc(keeps);
+            __syncwarp();
+        }
+        // distances to the kept centroids, lane-parallel over candidates
+        float bd = __int_as_float(0x7f800000);
+        int br = 0x7fffffff;
+        for (int q = lane; q < u; q += 32) {
+            int r = qlist[q];
+            float dv = cand_d2<VEC>(xs, C + (int64_t)r * d, d);
+            if (key_less(dv, r, bd, br)) {
+                bd = dv;
+                br = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float od = __shfl_xor_sync(FULL_MASK, bd, o);
+            int orr = __shfl_xor_sync(FULL_MASK, br, o);
+            if (key_less(od, orr, bd, br)) {
+                bd = od;
+                br = orr;
+            }
+        }
+        if (lane == 0) {
+            if (br == 0x7fffffff)  // no valid candidate (own label out of range): keep the input label
+                br = own, bd = 0.f;
+            Lout[i] = br;
+            if (best_out)
+                best_out[i] = bd;
+            wsum += (double)bd;
+            wchg += (br != own) ? 1ull : 0ull;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s_sum[w] = wsum;
+        s_chg[w] = wchg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int q = 0; q < AS_WARPS; q++) {
+            t += s_sum[q];
+            c += s_chg[q];
+        }
+        blk_sum[blockIdx.x] = t;
+        blk_changed[blockIdx.x] = c;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_assign_finish(const double *__restrict__ blk_sum,
+                                                        const unsigned long long *__restrict__ blk_changed, int nb,
+                                                        double *__restrict__ sum_d2, int64_t *__restrict__ n_changed)
+{
+    __shared__ double s[1024];
+    __shared__ unsigned long long c[1024];
+    double a = 0.0;
+    unsigned long long b = 0;
+    for (int i = threadIdx.x; i < nb; i += 1024) {
+        a += blk_sum[i];
+        b += blk_changed[i];
+    }
+    s[threadIdx.x] = a;
+    c[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s[threadIdx.x] += s[threadIdx.x + w];
+            c[threadIdx.x] += c[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (sum_d2)
+            *sum_d2 = s[0];
+        if (n_changed)
+            *n_changed = (int64_t)c[0];
+    }
+}
+
+size_t assign_scratch_bytes(int64_t)
+{
+    return ((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255);
+}
+
+cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                          const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s)
+{
+    double *blk_sum = static_cast<double *>(scratch);
+    unsigned long long *blk_chg = reinterpret_cast<unsigned long long *>(blk_sum + AS_BLOCKS);
+    int dpad = (int)((d + 3) & ~3);
+    size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
+    bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+    cudaError_t e;
+    if (vec4) {
+        if (shm > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_assign<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                cudaSuccess)
+            return e;
+        k_assign<4><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+                                                            labels_out, best_d2, blk_sum, blk_chg, st);
+    } else {
+        if (shm > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(k_assign<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                cudaSuccess)
+            return e;
+        k_assign<1><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+                                                            labels_out, best_d2, blk_sum, blk_chg, st);
+    }
+    if (sum_d2 || n_changed)
+        k_assign_finish<<<1, 1024, 0, s>>>(blk_sum, blk_chg, AS_BLOCKS, sum_d2, n_changed);
+    return cudaGetLastError();
+}
+
+}  // namespace gkm

@@ -1,0 +1,125 @@
+// Shared device helpers of libgkm (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gkm.h"
+
+namespace gkm {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int MAX_KAPPA = 128;
+
+// Device status word kept at the start of every workspace: the first error a
+// kernel meets (code, detail).  Kernels record and skip; they never trap.
+struct DevStatus {
+    unsigned code;
+    unsigned detail;
+    unsigned pad[62];  // keeps what follows 256-byte aligned
+};
+
+__device__ __forceinline__ void flag_error(DevStatus *st, unsigned code, unsigned detail)
+{
+    if (st && atomicCAS(&st->code, 0u, code) == 0u)
+        st->detail = detail;
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the generator advances its
+// state by gamma and returns mix(state).  Used as a counter-based function:
+// draw(key, c) is output number c + 1 of the generator whose state starts at key.
+constexpr uint64_t SM64_GAMMA = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t TAG_LABELS = 0x4C41424C00000000ull;  // "LABL"
+constexpr uint64_t TAG_GRAPH = 0x4752415000000000ull;   // "GRAP"
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint64_t counter)
+{
+    return sm64_mix(key + (counter + 1ull) * SM64_GAMMA);
+}
+
+// Squared Euclidean distance between two samples in FP32, one accumulator,
+// coordinates in ascending order: acc = fma(x_t - y_t, x_t - y_t, acc).
+// Every exact pair distance of the graph (initial graph, refinement, rerank)
+// uses this order, so that the distance of a pair is the same bits wherever it
+// is computed and d(i, j) == d(j, i).
+__device__ __forceinline__ float pair_d2_seq(const float *__restrict__ a, const float *__restrict__ b, int d)
+{
+    float acc = 0.f;
+    for (int t = 0; t < d; t++) {
+        float diff = a[t] - b[t];
+        acc = fmaf(diff, diff, acc);
+    }
+    return acc;
+}
+
+// (distance, index) key order of graph rows: smaller distance first, then smaller id.
+__device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+}  // namespace gkm
+
+// ---- host-side launch helpers (internal) ---------------------------------
+namespace gkm {
+
+// Workspace carving: bump allocator over the caller's buffer.
+struct Carver {
+    char *base;
+    size_t off;
+    size_t cap;
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+// Internal launchers (each returns cudaError_t of the launch).
+cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s);
+cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                              int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s);
+
+// Grouping of samples by label (CSR).  Scratch sizes via group_scratch_bytes().
+size_t group_scratch_bytes(int64_t n, int32_t k);
+cudaError_t launch_group(const int32_t *labels, int64_t n, int32_t k, int32_t *offsets, int32_t *members,
+                         int32_t *counts_out, void *scratch, DevStatus *st, cudaStream_t s);
+
+// Exclusive scan of int32 counts (count elements) into out (count + 1 elements, out[count] = total).
+size_t scan_scratch_bytes(int64_t count);
+cudaError_t launch_scan(const int32_t *in, int32_t *out, int64_t count, void *scratch, cudaStream_t s);
+
+size_t update_scratch_bytes(int64_t n, int32_t k);
+cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                          void *scratch, cudaStream_t s);
+
+size_t assign_scratch_bytes(int64_t n);
+cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                          const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s);
+
+cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
+                          float *g_dist, DevStatus *st, cudaStream_t s);
+
+}  // namespace gkm

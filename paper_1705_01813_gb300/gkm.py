@@ -1,0 +1,254 @@
+"""Python binding of libgkm (the C ABI in include/gkm.h).
+
+Argument marshalling only: every step runs in the CUDA library.  PyTorch
+supplies device memory (tensors, the workspace) and the current CUDA stream.
+There is no CPU fallback: if ``libgkm.so`` is missing or fails to load, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build_native
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+_lock = threading.Lock()
+
+GK_OK, GK_ERR_INVALID, GK_ERR_CUDA, GK_ERR_NOMEM, GK_ERR_TIMEOUT, GK_ERR_NUMERIC = range(6)
+GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD = range(5)
+
+#: every entry point the header declares (checked by the tests)
+EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
+           "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
+           "gk_kmeans_fit", "gk_read_status"]
+
+
+class GraphParams(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_int32), ("xi", ctypes.c_int32), ("tau", ctypes.c_int32),
+                ("max_cluster", ctypes.c_int32), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class GkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libgkm error {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return build_native.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgkm.so (compiling it first if it is missing and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(build_native.LIB):
+                if not build_if_missing:
+                    raise RuntimeError(f"libgkm.so not built ({build_native.LIB})")
+                build_native.build()
+            L = ctypes.CDLL(build_native.LIB)
+            P, I64, I32, U64, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_size_t
+            L.gk_version.restype = ctypes.c_char_p
+            L.gk_version.argtypes = []
+            L.gk_last_error.restype = ctypes.c_char_p
+            L.gk_last_error.argtypes = []
+            L.gk_workspace_size.restype = SZ
+            L.gk_workspace_size.argtypes = [I32, I64, I64, I32, I32]
+            L.gk_workspace_size_build.restype = SZ
+            L.gk_workspace_size_build.argtypes = [I64, I64, ctypes.POINTER(GraphParams)]
+            L.gk_init_labels.argtypes = [I64, I32, U64, P, P]
+            L.gk_init_graph.argtypes = [P, I64, I64, I64, I32, U64, P, P, P, SZ, P]
+            L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, P, SZ, P]
+            L.gk_update_step.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P, P, P, SZ, P]
+            L.gk_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, P, P, P, SZ, P]
+            L.gk_build_knn_graph.argtypes = [P, I64, I64, I64, ctypes.POINTER(GraphParams), P, P, P, P, P, SZ, P]
+            L.gk_kmeans_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, U64, P, P, P, P, P, SZ, P]
+            L.gk_read_status.argtypes = [P, P]
+            for name in EXPORTS:
+                if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != GK_OK:
+        raise GkError(rc, load().gk_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _x(X: torch.Tensor):
+    if X.device.type != "cuda" or X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a CUDA float32 matrix with unit column stride")
+    return X.shape[0], X.shape[1], X.stride(0)
+
+
+def _dev(t: torch.Tensor, dtype, name: str):
+    if t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+class Workspace:
+    """Device scratch for the library, allocated by torch's caching allocator."""
+
+    def __init__(self, nbytes: int, device=None):
+        self.nbytes = max(256, int(nbytes))
+        self.buf = torch.zeros(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        self.off = (-base) % 256
+        self.ptr = ctypes.c_void_p(base + self.off)
+
+    def status(self, stream=None) -> int:
+        return load().gk_read_status(self.ptr, _stream(stream))
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device=None) -> Workspace:
+    dev = torch.device(device) if device is not None else torch.device("cuda")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    key = (str(dev), threading.get_ident())
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < nbytes:
+        ws = Workspace(max(nbytes, int(ws.nbytes * 1.25) if ws else nbytes), dev)
+        _ws_cache[key] = ws
+    return ws
+
+
+def workspace_size(op: int, n: int, d: int, k: int, kappa: int = 0) -> int:
+    return int(load().gk_workspace_size(op, n, d, k, kappa))
+
+
+def workspace_size_build(n: int, d: int, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int = 128,
+                         seed: int = 0) -> int:
+    p = GraphParams(kappa, xi, tau, max_cluster, seed, 0, 0)
+    return int(load().gk_workspace_size_build(n, d, ctypes.byref(p)))
+
+
+def version() -> str:
+    return load().gk_version().decode()
+
+
+def init_labels(n: int, k: int, seed: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty(n, dtype=torch.int32, device="cuda") if out is None else _dev(out, torch.int32, "out")
+    _check(load().gk_init_labels(n, k, seed, _ptr(out), _stream(stream)))
+    return out
+
+
+def init_graph(X: torch.Tensor, kappa: int, seed: int, ws: Workspace | None = None, stream=None):
+    n, d, ld = _x(X)
+    gi = torch.empty((n, kappa), dtype=torch.int32, device=X.device)
+    gd = torch.empty((n, kappa), dtype=torch.float32, device=X.device)
+    ws = ws or workspace(256, X.device)
+    _check(load().gk_init_graph(_ptr(X), n, d, ld, kappa, seed, _ptr(gi), _ptr(gd), ws.ptr, ws.nbytes,
+                                _stream(stream)))
+    return gi, gd
+
+
+def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=None, sum_d2=None, n_changed=None,
+                ws: Workspace | None = None, stream=None):
+    """Graph-guided assignment; returns (labels_out, best_d2, sum_d2, n_changed) tensors."""
+    n, d, ld = _x(X)
+    _dev(g_idx, torch.int32, "g_idx")
+    _dev(C, torch.float32, "C")
+    _dev(labels_in, torch.int32, "labels_in")
+    k, kappa = C.shape[0], g_idx.shape[1]
+    dev = X.device
+    labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
+    best_d2 = torch.empty(n, dtype=torch.float32, device=dev) if best_d2 is None else best_d2
+    sum_d2 = torch.empty(1, dtype=torch.float64, device=dev) if sum_d2 is None else sum_d2
+    n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is None else n_changed
+    ws = ws or workspace(workspace_size(GK_OP_ASSIGN, n, d, k, kappa), dev)
+    _check(load().gk_assign_step(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
+                                 _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), ws.ptr, ws.nbytes,
+                                 _stream(stream)))
+    return labels_out, best_d2, sum_d2, n_changed
+
+
+def update_step(X, labels, k: int, C, counts=None, sum_d2=None, offsets=None, members=None,
+                ws: Workspace | None = None, stream=None):
+    """Centroid update in place on C; returns (C, counts, sum_d2, offsets, members)."""
+    n, d, ld = _x(X)
+    _dev(labels, torch.int32, "labels")
+    _dev(C, torch.float32, "C")
+    dev = X.device
+    counts = torch.empty(k, dtype=torch.int32, device=dev) if counts is None else counts
+    sum_d2 = torch.empty(1, dtype=torch.float64, device=dev) if sum_d2 is None else sum_d2
+    offsets = torch.empty(k + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    members = torch.empty(n, dtype=torch.int32, device=dev) if members is None else members
+    ws = ws or workspace(workspace_size(GK_OP_UPDATE, n, d, k), dev)
+    _check(load().gk_update_step(_ptr(X), n, d, ld, _ptr(labels), k, _ptr(C), _ptr(counts), _ptr(sum_d2),
+                                 _ptr(offsets), _ptr(members), ws.ptr, ws.nbytes, _stream(stream)))
+    return C, counts, sum_d2, offsets, members
+
+
+def graph_refine(X, labels, k: int, g_idx, g_dist, max_cluster: int = 128, ws: Workspace | None = None,
+                 stream=None):
+    """One refinement of the graph in place (pairs inside each cluster)."""
+    n, d, ld = _x(X)
+    _dev(labels, torch.int32, "labels")
+    _dev(g_idx, torch.int32, "g_idx")
+    _dev(g_dist, torch.float32, "g_dist")
+    kappa = g_idx.shape[1]
+    ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, kappa), X.device)
+    _check(load().gk_graph_refine(_ptr(X), n, d, ld, _ptr(labels), k, kappa, max_cluster, _ptr(g_idx),
+                                  _ptr(g_dist), ws.ptr, ws.nbytes, _stream(stream)))
+    return g_idx, g_dist
+
+
+def build_knn_graph(X, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int = 128, seed: int = 0,
+                    labels_out=None, g_idx=None, g_dist=None, want_log: bool = True, ws: Workspace | None = None,
+                    stream=None):
+    """Alg. 3; returns (g_idx, g_dist, labels at k0, distortion log or None)."""
+    n, d, ld = _x(X)
+    dev = X.device
+    p = GraphParams(kappa, xi, tau, max_cluster, seed, 0, 0)
+    g_idx = torch.empty((n, kappa), dtype=torch.int32, device=dev) if g_idx is None else g_idx
+    g_dist = torch.empty((n, kappa), dtype=torch.float32, device=dev) if g_dist is None else g_dist
+    labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
+    log = (ctypes.c_double * (2 * tau + 1))() if want_log else None
+    ws = ws or workspace(int(load().gk_workspace_size_build(n, d, ctypes.byref(p))), dev)
+    _check(load().gk_build_knn_graph(_ptr(X), n, d, ld, ctypes.byref(p), _ptr(g_idx), _ptr(g_dist),
+                                     _ptr(labels_out), log, ws.ptr, ws.nbytes, _stream(stream)))
+    return g_idx, g_dist, labels_out, (list(log) if want_log else None)
+
+
+def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, labels_out=None, C_out=None,
+               counts_out=None, want_log: bool = True, ws: Workspace | None = None, stream=None):
+    """Graph-guided k-means; returns (labels, centroids, counts, distortion log or None)."""
+    n, d, ld = _x(X)
+    dev = X.device
+    _dev(g_idx, torch.int32, "g_idx")
+    kappa = g_idx.shape[1]
+    labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
+    C_out = torch.empty((k, d), dtype=torch.float32, device=dev) if C_out is None else C_out
+    counts_out = torch.empty(k, dtype=torch.int32, device=dev) if counts_out is None else counts_out
+    log = (ctypes.c_double * (2 * iters + 1))() if want_log else None
+    ws = ws or workspace(workspace_size(GK_OP_FIT, n, d, k, kappa), dev)
+    _check(load().gk_kmeans_fit(_ptr(X), n, d, ld, k, _ptr(g_idx), kappa, iters, _ptr(init_labels), seed,
+                                _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
+                                _stream(stream)))
+    return labels_out, C_out, counts_out, (list(log) if want_log else None)
+
+
+def read_status(ws: Workspace, stream=None) -> int:
+    """Synchronise and return (and clear) the device status word of a workspace."""
+    return int(load().gk_read_status(ws.ptr, _stream(stream)))

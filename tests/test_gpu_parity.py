@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every step is checked in lockstep: both sides get the same inputs (seeded
+synthetic data, the oracle's own labels, graphs and FP32-rounded centroids),
+and the GPU's outputs are compared element by element under the rules of
+tests/parity.py.  Sizes span several tiles with ragged tails; the full-size
+SIFT-shaped workload is checked on sampled outputs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_1705_01813_gb300 import datagen  # noqa: E402
+from tests import parity as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_01813_gb300 import gkm
+    gkm.load()
+    return gkm
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _blobs(n, d, centers, seed, spread=1.0, box=10.0):
+    g = np.random.default_rng(seed)
+    c = g.uniform(-box, box, size=(centers, d))
+    z = g.integers(0, centers, n)
+    return (c[z] + spread * g.standard_normal((n, d))).astype(np.float32)
+
+
+# --------------------------------------------------------------- seeded start
+
+@pytest.mark.parametrize("n,k,seed", [(1, 1, 0), (20000, 200, 170501813), (100003, 9999, 5), (777, 1000, 2**63 + 7)])
+def test_init_labels_bit_exact(G, n, k, seed):
+    g = _np(G.init_labels(n, k, seed))
+    o = O.init_labels(n, k, seed)
+    assert np.array_equal(g, o)
+
+
+@pytest.mark.parametrize("n,d,kappa,seed", [(3000, 32, 20, 1), (1037, 33, 50, 7), (130, 8, 128, 3), (2, 5, 1, 9)])
+def test_init_graph(G, n, d, kappa, seed):
+    X = _blobs(n, d, 10, seed)
+    gi, gd = G.init_graph(_cuda(X), kappa, seed)
+    gi, gd = _np(gi), _np(gd)
+    oi, od = O.init_graph(X, kappa, seed)
+    # the neighbour sets come from the generator alone: bit-exact
+    assert np.array_equal(np.sort(gi, 1), np.sort(oi, 1))
+    P.row_invariants(X, gi, gd)
+    P.check_graph(X, gi, gd, oi, od)
+
+
+def test_init_graph_integer_data_exact(G):
+    X = datagen.sift_like(4000, 128, 50, seed=3)
+    gi, gd = G.init_graph(_cuda(X), 50, 11)
+    oi, od = O.init_graph(X, 50, 11)
+    P.check_graph(X, _np(gi), _np(gd), oi, od, exact=True)
+
+
+# ------------------------------------------------------------------ assign
+
+def _assign_case(G, X, kappa, k, seed, graph="knn"):
+    n = X.shape[0]
+    if graph == "knn":
+        gi, _ = O.brute_knn(X, kappa) if n * n * X.shape[1] <= 2e9 else O.init_graph(X, kappa, seed)
+    else:
+        gi, _ = O.init_graph(X, kappa, seed)
+    L = O.init_labels(n, k, seed)
+    C64, cnt, _, _ = O.update(X, L, k)
+    C32 = C64.astype(np.float32)
+    Lo, best, uq = O.assign(X, gi, C32.astype(np.float64), L)
+    lo, bd, s, ch = G.assign_step(_cuda(X), _cuda(gi), _cuda(C32), _cuda(L))
+    torch.cuda.synchronize()
+    ex = P.check_labels(X, C32, _np(lo), Lo, best)
+    # winning distances, their FP64 sum and the changed count
+    agree = _np(lo) == Lo
+    err = np.abs(_np(bd)[agree] - best[agree]) / np.maximum(best[agree], 1e-30)
+    assert err.max() <= P.REL
+    P.check_rel(_np(s)[0], best.sum(), what="sum of best d2")
+    assert abs(int(_np(ch)[0]) - int((Lo != L).sum())) <= ex
+    return ex
+
+
+@pytest.mark.parametrize("n,d,k,kappa", [
+    (20000, 32, 200, 20),     # plain-method Gaussian mixture
+    (5003, 36, 97, 33),       # ragged n, kappa > 32 (two candidate rounds)
+    (4099, 33, 61, 7),        # odd d: scalar load path
+    (3001, 960, 40, 50),      # GIST-like width
+    (1500, 1, 5, 3),          # d = 1
+    (700, 16, 3, 128),        # kappa at its maximum, many repeated labels
+])
+def test_assign_lockstep(G, n, d, k, kappa):
+    X = _blobs(n, d, max(2, k // 2), n + d)
+    ex = _assign_case(G, X, kappa, k, seed=n)
+    assert ex <= max(2, n // 1000)
+
+
+def test_assign_complete_graph_is_lloyd(G):
+    """kappa = n - 1: every cluster is a candidate, so the step is exhaustive Lloyd."""
+    X = _blobs(100, 6, 4, 1)
+    n, k = 100, 9
+    gi = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    L = O.init_labels(n, k, 3)
+    C64, _, _, _ = O.update(X, L, k)
+    C32 = C64.astype(np.float32)
+    Le, be = O.assign_exhaustive(X, C32.astype(np.float64))
+    lo, bd, _, _ = G.assign_step(_cuda(X), _cuda(gi[:, :99]), _cuda(C32), _cuda(L))
+    P.check_labels(X, C32, _np(lo), Le, be)
+
+
+# ------------------------------------------------------------------ update
+
+@pytest.mark.parametrize("n,d,k", [(20000, 32, 200), (5003, 36, 97), (4099, 33, 6000), (3001, 960, 40),
+                                   (1000, 1, 1), (257, 1030, 3), (70000, 8, 70000)])
+def test_update_lockstep(G, n, d, k):
+    X = _blobs(n, d, 7, d)
+    g = np.random.default_rng(n)
+    L = g.integers(0, k, n).astype(np.int32)
+    if k > 3:
+        L[L == 1] = 0  # cluster 1 empty
+    C_old = g.standard_normal((k, d)).astype(np.float32)
+    C64, cnt, E, I = O.update(X, L, k, C_old.astype(np.float64))
+    Ct = _cuda(C_old)
+    _, counts, s, off, mem = G.update_step(_cuda(X), _cuda(L), k, Ct)
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(counts), cnt.astype(np.int32))
+    o_off, o_mem = O.group_csr(L, k)
+    assert np.array_equal(_np(off), o_off.astype(np.int32))
+    assert np.array_equal(_np(mem), o_mem)
+    Cg = _np(Ct)
+    P.check_centroids(Cg, C64, cnt)
+    assert np.array_equal(Cg[cnt == 0], C_old[cnt == 0])  # empty clusters keep their centroid
+    P.check_rel(_np(s)[0] / n, E, what="distortion after update")
+
+
+def test_update_integer_data(G):
+    X = datagen.sift_like(30011, 128, 300, seed=4)
+    k = 1000
+    L = O.init_labels(X.shape[0], k, 8)
+    C64, cnt, E, _ = O.update(X, L, k)
+    Ct = torch.zeros((k, 128), device="cuda")
+    _, counts, s, _, _ = G.update_step(_cuda(X), _cuda(L), k, Ct)
+    P.check_centroids(_np(Ct), C64, cnt)
+    P.check_rel(_np(s)[0] / X.shape[0], E, what="distortion after update")
+
+
+# ------------------------------------------------------------------ refine
+
+def _refine_case(G, X, k, kappa, cap, seed, exact=False):
+    n = X.shape[0]
+    L = O.init_labels(n, k, seed)
+    gi32, gd32 = G.init_graph(_cuda(X), kappa, seed)
+    oi, od = O.init_graph(X, kappa, seed)
+    ri, rd = O.graph_refine(X, L, k, oi, od, cap)
+    G.graph_refine(_cuda(X), _cuda(L), k, gi32, gd32, cap)
+    torch.cuda.synchronize()
+    gi, gd = _np(gi32), _np(gd32)
+    P.row_invariants(X, gi, gd)
+    return P.check_graph(X, gi, gd, ri, rd, exact=exact)
+
+
+@pytest.mark.parametrize("n,d,k,kappa,cap", [
+    (20000, 32, 400, 20, 128),   # k0 = n / 50 at the plain-method size
+    (5003, 36, 60, 33, 128),     # clusters of ~83
+    (6007, 17, 20, 10, 128),     # clusters of ~300 cut into runs
+    (3001, 960, 50, 50, 128),    # GIST-like width
+    (2000, 8, 3, 16, 500),       # runs longer than one 128-wide tile
+    (900, 5, 6, 6, 40),          # small cap, uneven runs
+])
+def test_refine_lockstep(G, n, d, k, kappa, cap):
+    X = _blobs(n, d, 20, n)
+    ex = _refine_case(G, X, k, kappa, cap, seed=d)
+    assert ex <= max(3, n // 500)
+
+
+def test_refine_integer_data_bit_exact(G):
+    X = datagen.sift_like(20000, 128, 400, seed=5)
+    _refine_case(G, X, 400, 50, 128, seed=9, exact=True)
+
+
+def test_exact_knn_special_case(G):
+    """n < 2 xi gives k0 = 1: one round of Alg. 3 is an exact KNN search."""
+    X = _blobs(90, 4, 3, 21)
+    gi, gd, L, log = G.build_knn_graph(_cuda(X), 8, xi=50, tau=1, max_cluster=128, seed=3)
+    bi, bd = O.brute_knn(X, 8)
+    assert (_np(L) == 0).all()
+    P.row_invariants(X, _np(gi), _np(gd))
+    P.check_graph(X, _np(gi), _np(gd), bi, bd)
+    Xs = datagen.sift_like(97, 128, 5, seed=2)
+    gi, gd, _, _ = G.build_knn_graph(_cuda(Xs), 12, xi=50, tau=1, max_cluster=128, seed=4)
+    bi, bd = O.brute_knn(Xs, 12)
+    P.check_graph(Xs, _np(gi), _np(gd), bi, bd, exact=True)
+
+
+# --------------------------------------------------------------- fit / build
+
+def test_fit_lockstep_and_free_running(G):
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = w.data()
+    gi, _, _, _ = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
+    L0 = O.init_labels(w.n, w.k, w.seed)
+    Lo, Co, cnto, Eo = O.fit(X, w.k, gi, w.iters, L0)
+    lg, Cg, cntg, Eg = G.kmeans_fit(_cuda(X), w.k, _cuda(gi), w.iters, init_labels=_cuda(L0))
+    Eg = np.array(Eg)
+    assert (np.diff(Eg) <= 1e-6 * Eg[:-1]).all()  # non-increasing
+    # free running: the final distortion agrees with the oracle's
+    P.check_rel(Eg[-1], Eo[-1], rel=1e-4, what="final distortion")
+    frac = (_np(lg) != Lo).mean()
+    assert frac < 1e-3
+
+
+def test_build_graph_free_running(G):
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = w.data()
+    oi, od, oL, oE = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
+    gi, gd, gL, gE = G.build_knn_graph(_cuda(X), w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster,
+                                       seed=w.seed)
+    gi, gd = _np(gi), _np(gd)
+    P.row_invariants(X, gi[:2000], gd[:2000], rows=np.arange(2000))
+    bi, _ = O.brute_knn(X[:3000], 1)
+    # same quality as the oracle's graph: top-1 agreement and kappa-th distance
+    agree = (gi[:, 0] == oi[:, 0]).mean()
+    assert agree > 0.97
+    assert abs(np.mean(gd[:, -1]) / np.mean(od[:, -1]) - 1) < 1e-3
+    assert abs(gE[-1] / oE[-1] - 1) < 1e-3
+
+
+# --------------------------------------------------------------- edge cases
+
+def test_edge_k1_and_k_above_n(G):
+    X = _blobs(300, 7, 3, 1)
+    # k = 1: everything in one cluster
+    L = np.zeros(300, np.int32)
+    Ct = torch.zeros((1, 7), device="cuda")
+    _, counts, s, off, mem = G.update_step(_cuda(X), _cuda(L), 1, Ct)
+    C64, cnt, E, _ = O.update(X, L, 1)
+    P.check_centroids(_np(Ct), C64)
+    assert np.array_equal(_np(mem), np.arange(300))
+    # k > n: most clusters empty, assignment still consistent
+    k = 1000
+    _assign_case(G, X, 5, k, seed=2)
+
+
+def test_edge_two_samples(G):
+    X = np.array([[0.0, 1.0], [3.0, 5.0]], np.float32)
+    gi, gd = G.init_graph(_cuda(X), 1, 0)
+    assert _np(gi).tolist() == [[1], [0]] and _np(gd).tolist() == [[25.0], [25.0]]
+    lo, bd, s, ch = G.assign_step(_cuda(X), gi, _cuda(np.array([[0.0, 1.0], [3.0, 5.0]], np.float32)),
+                                  _cuda(np.array([1, 0], np.int32)))
+    assert _np(lo).tolist() == [0, 1]
+
+
+def test_out_of_range_labels_are_reported(G):
+    X = _blobs(500, 4, 3, 2)
+    L = np.zeros(500, np.int32)
+    L[17] = 9  # k = 5
+    ws = G.Workspace(G.workspace_size(G.GK_OP_UPDATE, 500, 4, 5))
+    G.update_step(_cuda(X), _cuda(L), 5, torch.zeros((5, 4), device="cuda"), ws=ws)
+    assert G.read_status(ws) == G.GK_ERR_INVALID
+    assert G.read_status(ws) == G.GK_OK  # cleared
+    gi = np.tile(np.arange(1, 4, dtype=np.int32), (500, 1))
+    gi[3, 1] = 10**6  # neighbour id out of range
+    ws2 = G.Workspace(G.workspace_size(G.GK_OP_ASSIGN, 500, 4, 5, 3))
+    G.assign_step(_cuda(X), _cuda(gi), torch.zeros((5, 4), device="cuda"), _cuda(np.zeros(500, np.int32)), ws=ws2)
+    assert G.read_status(ws2) == G.GK_ERR_INVALID
+
+
+def test_deterministic_and_resumable(G):
+    """Same inputs give the same bits; a fit split at iteration t and resumed equals the unsplit fit."""
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = _cuda(w.data())
+    gi, gd, _, _ = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=3, seed=1)
+    gi2, gd2, _, _ = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=3, seed=1)
+    assert torch.equal(gi, gi2) and torch.equal(gd, gd2)
+    L0 = G.init_labels(w.n, w.k, 4)
+    la, Ca, _, Ea = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0)
+    lb, Cb, _, Eb = G.kmeans_fit(X, w.k, gi, 3, init_labels=L0)
+    # resume: three more iterations from the saved labels (centroids follow from the labels)
+    lc, Cc, _, Ec = G.kmeans_fit(X, w.k, gi, 3, init_labels=lb.clone())
+    assert torch.equal(la, lc) and torch.equal(Ca, Cc)
+    assert Ea[-1] == Ec[-1]
