@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the graph-guided k-means hot path on GB300.
+
+One step is one pass of the whole path over the workload (default: the
+SIFT-shaped n = 1,000,000, d = 128, k = 10,000, kappa = 50 workload):
+  graph construction (Alg. 3): random graph and labels at k0 = n / xi, then
+      tau = 10 rounds of {graph-guided assignment, grouping, update, pair refinement}
+  graph-guided k-means (Alg. 2, closest-centroid rule): seeded labels at k,
+      then 10 iterations of {assignment, grouping, update}
+The step is driven through the library's step entry points with CUDA events
+between the calls (the same kernels the one-call API runs), which gives the
+per-kernel durations used for the roofline.  `e2e` times the one-call API
+(gk_build_knn_graph + gk_kmeans_fit) with the samples copied from pinned host
+memory and the labels and centroids copied back inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gkm|reference]
+Under torchrun (N > 1) every rank runs an independent replica on its GPU
+(the path needs no exchange between GPUs); value = samples of all ranks / the
+slowest rank's time.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1705_01813_gb300 import datagen  # noqa: E402
+
+METRIC = "assign-step samples/s and fit time vs plain FP32; serve jobs/s, p50/p99"
+DEFAULT_WORKLOAD = "sift_n1000000_d128_k10000"
+CPU_SAMPLE = 100_000        # cpu_baseline: oracle on the first 100k samples (about 10-30 s)
+REF_SAMPLE = 40_000         # --impl reference: oracle per step on the first 40k samples
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gkm", "reference"], default="gkm")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        load = [v for v in sm if mx and v > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU path --
+
+class Path:
+    """Device buffers and the step sequence of one replica."""
+
+    def __init__(self, gkm, torch, w, X):
+        self.gkm, self.torch, self.w = gkm, torch, w
+        dev = X.device
+        n, d = X.shape
+        self.X, self.n, self.d = X, n, d
+        self.k0 = w.k0
+        i32, f32, f64 = torch.int32, torch.float32, torch.float64
+        self.gi = torch.empty((n, w.kappa), dtype=i32, device=dev)
+        self.gd = torch.empty((n, w.kappa), dtype=f32, device=dev)
+        self.la = torch.empty(n, dtype=i32, device=dev)
+        self.lb = torch.empty(n, dtype=i32, device=dev)
+        kmax = max(self.k0, w.k)
+        self.off = torch.empty(kmax + 1, dtype=i32, device=dev)
+        self.mem = torch.empty(n, dtype=i32, device=dev)
+        self.cnt = torch.empty(kmax, dtype=i32, device=dev)
+        self.C0 = torch.empty((self.k0, d), dtype=f32, device=dev)
+        self.C = torch.empty((w.k, d), dtype=f32, device=dev)
+        self.s = torch.empty(4, dtype=f64, device=dev)
+        self.ws = gkm.Workspace(max(gkm.workspace_size(gkm.GK_OP_FIT, n, d, kmax, w.kappa),
+                                    gkm.workspace_size_build(n, d, w.kappa, w.xi, w.tau, w.max_cluster)), dev)
+
+    def _ev(self):
+        return self.torch.cuda.Event(enable_timing=True)
+
+    def step(self, rec=None):
+        """Whole path once; rec (list) receives (tag, start_event, end_event) per call."""
+        g, w, torch = self.gkm, self.w, self.torch
+
+        def call(tag, fn, *a, **kw):
+            if rec is None:
+                return fn(*a, **kw)
+            e0, e1 = self._ev(), self._ev()
+            e0.record()
+            out = fn(*a, **kw)
+            e1.record()
+            rec.append((tag, e0, e1))
+            return out
+
+        n, ws = self.n, self.ws
+        # --- Alg. 3: KNN graph by repeated fast k-means at k0
+        call("init_graph", g.init_graph, self.X, w.kappa, w.seed, self.gi, self.gd, ws=ws)
+        g.init_labels(n, self.k0, w.seed, out=self.la)
+        self.C0.zero_()
+        call("group", g.group_by_label, self.la, self.k0, self.off, self.mem, self.cnt, ws=ws)
+        call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt, self.s[0:1], ws=ws)
+        cur, nxt = self.la, self.lb
+        for _ in range(w.tau):
+            call("assign", g.assign_step, self.X, self.gi, self.C0, cur, nxt, None, self.s[1:2], None, ws=ws)
+            call("group", g.group_by_label, nxt, self.k0, self.off, self.mem, self.cnt, ws=ws)
+            call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt,
+                 self.s[0:1], ws=ws)
+            call("refine", g.graph_refine_groups, self.X, self.off, self.mem, self.k0, self.gi, self.gd,
+                 w.max_cluster, ws=ws)
+            cur, nxt = nxt, cur
+        # --- Alg. 2 (closest-centroid rule) at k on the constructed graph
+        g.init_labels(n, w.k, w.seed + 1, out=self.la)
+        self.C.zero_()
+        cur, nxt = self.la, self.lb
+        call("group", g.group_by_label, cur, w.k, self.off, self.mem, self.cnt, ws=ws)
+        call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3], ws=ws)
+        for _ in range(w.iters):
+            call("assign", g.assign_step, self.X, self.gi, self.C, cur, nxt, None, self.s[3:4], None, ws=ws)
+            call("group", g.group_by_label, nxt, w.k, self.off, self.mem, self.cnt, ws=ws)
+            call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3],
+                 ws=ws)
+            cur, nxt = nxt, cur
+
+
+def _radix_passes(k):
+    bits = max(0, int(k - 1).bit_length())
+    return (bits + 7) // 8
+
+
+def launches_per_step(w):
+    """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
+    grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
+    upd, asg, ref = 2, 2, 1
+    graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
+    fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
+    return graph + fit
+
+
+def algorithmic_bytes(tag, w, k):
+    """HBM bytes one launch of a step's kernel must move (per-unit figures x units; L2-resident
+    label gathers not counted)."""
+    n, d, kappa = w.n, w.d, w.kappa
+    s = 4
+    if tag == "assign":
+        return n * (s * d + 4 * kappa + 4 + 4) + k * d * 4
+    if tag == "update":
+        return n * (s * d + 4) + k * (d * 4 + 8)
+    if tag == "group":
+        return n * 12 + 4 * (k + 1)
+    if tag == "refine":
+        return n * (s * d + 16 * kappa + 4) + 4 * (k + 1)
+    return 0
+
+
+def kernel_of(tag):
+    return {"assign": "k_assign", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine"}[tag]
+
+
+def source_sha(tag):
+    f = {"assign": "assign.cu", "update": "update.cu", "group": "group.cu", "refine": "refine.cu"}[tag]
+    with open(os.path.join(ROOT, "paper_1705_01813_gb300", "csrc", f), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(tag, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it is for the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    e = j.get(f"{kernel_of(tag)}:{workload}")
+    if not e or e.get("source_sha") != source_sha(tag):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1705_01813_gb300 import gkm
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = datagen.WORKLOADS[args.workload]
+    Xh = w.data()
+    X = torch.from_numpy(Xh).cuda()
+    gkm.load()
+
+    path = Path(gkm, torch, w, X)
+    for _ in range(args.warmup):
+        path.step()
+    torch.cuda.synchronize()
+    if gkm.read_status(path.ws) != gkm.GK_OK:
+        raise RuntimeError("device status error during warm-up")
+
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    rec = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for _ in range(args.steps):
+        path.step(rec)
+    t_end.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    per_tag = {}
+    for tag, e0, e1 in rec:
+        per_tag.setdefault(tag, []).append(e0.elapsed_time(e1) / 1e3)
+    status = gkm.read_status(path.ws)
+
+    # e2e through the one-call API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xpin = torch.from_numpy(Xh).pin_memory()
+        Xdev = torch.empty_like(X)
+        lab_h = torch.empty(w.n, dtype=torch.int32).pin_memory()
+        C_h = torch.empty((w.k, w.d), dtype=torch.float32).pin_memory()
+        gi = torch.empty((w.n, w.kappa), dtype=torch.int32, device="cuda")
+        gd = torch.empty((w.n, w.kappa), dtype=torch.float32, device="cuda")
+        lab0 = torch.empty(w.n, dtype=torch.int32, device="cuda")
+        lab = torch.empty(w.n, dtype=torch.int32, device="cuda")
+        C = torch.empty((w.k, w.d), dtype=torch.float32, device="cuda")
+        cnt = torch.empty(w.k, dtype=torch.int32, device="cuda")
+
+        def e2e_step():
+            Xdev.copy_(Xpin, non_blocking=True)
+            gkm.build_knn_graph(Xdev, w.kappa, w.xi, w.tau, w.max_cluster, w.seed, labels_out=lab0, g_idx=gi,
+                                g_dist=gd, want_log=False, ws=path.ws)
+            gkm.kmeans_fit(Xdev, w.k, gi, w.iters, seed=w.seed + 1, labels_out=lab, C_out=C, counts_out=cnt,
+                           want_log=False, ws=path.ws)
+            lab_h.copy_(lab, non_blocking=True)
+            C_h.copy_(C, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record()
+        for _ in range(args.steps):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        t_e2e = max(a.elapsed_time(b) / 1e3, wall)
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * w.n * args.steps / t_e2e, "unit": "samples/s",
+               "h2d_bytes_per_step": int(Xh.nbytes),
+               "d2h_bytes_per_step": int(lab_h.numel() * 4 + C_h.numel() * 4),
+               "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, bf16, peak_src = load_peaks()
+    # dominant kernel: the call with the largest share of the step
+    totals = {t: sum(v) for t, v in per_tag.items()}
+    dom = max(totals, key=totals.get)
+    n_graph = w.tau + 1
+    # per-launch algorithmic bytes: graph rounds run at k0, fit iterations at k
+    if dom in ("assign", "update", "group"):
+        ks = [w.k0] * (w.tau + (0 if dom == "assign" else 1)) + [w.k] * (w.iters + (0 if dom == "assign" else 1))
+        alg = sum(algorithmic_bytes(dom, w, k) for k in ks) / len(ks)
+    else:
+        alg = algorithmic_bytes(dom, w, w.k0)
+    avg = statistics.mean(per_tag[dom])
+    achieved = alg / avg / 1e9
+    assign_times = per_tag.get("assign", [])
+    fit_assign = assign_times[w.tau::w.tau + w.iters] if assign_times else []
+    step_s = elapsed / args.steps
+    res = {
+        "metric": METRIC,
+        "value": world * w.n * args.steps / elapsed,
+        "unit": "samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * step_s,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "kappa": w.kappa, "k0": w.k0, "xi": w.xi,
+                   "tau": w.tau, "iters": w.iters, "max_cluster": w.max_cluster,
+                   "step": "graph construction (tau rounds at k0) + fit (iters at k), whole path",
+                   "l2": "inputs larger than L2 (X is %d MB)" % (Xh.nbytes >> 20),
+                   "parallelism": f"replicas x{world}"},
+        "fit_s": step_s,
+        "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
+        "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},
+        "per_step_share": {t: round(v / sum(totals.values()), 4) for t, v in totals.items()},
+        "roofline": {"kernel": kernel_of(dom), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": int(alg),
+                     "traffic": ncu_traffic(dom, w.name)},
+        "gpu_launches": launches_per_step(w) * args.steps,
+        "clocks": ck,
+        "device_status": status,
+        "e2e": e2e,
+    }
+    # roofline of every call type, for context
+    res["roofline_all"] = {}
+    for t, v in per_tag.items():
+        if t == "init_graph":
+            continue
+        a = algorithmic_bytes(t, w, w.k0 if t == "refine" else w.k)
+        res["roofline_all"][t] = round(a / statistics.mean(v) / 1e9 / hbm, 4)
+    if world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(w, Xh)
+    print(json.dumps(res), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_step(O, w, X, k_scale):
+    ns = X.shape[0]
+    k = max(1, int(round(w.k * ns / w.n)))
+    gi, _, _, _ = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
+    L0 = O.init_labels(ns, k, w.seed + 1)
+    O.fit(X, k, gi, w.iters, L0)
+    return k
+
+
+def cpu_baseline(w, Xh):
+    from oracle import oracle as O
+    ns = min(CPU_SAMPLE, w.n)
+    X = np.ascontiguousarray(Xh[:ns])
+    t0 = time.perf_counter()
+    k = _oracle_step(O, w, X, True)
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {ns} samples of {w.name}, k = {k}, k0 = {ns // w.xi}, kappa = {w.kappa}, "
+                      f"tau = {w.tau}, iters = {w.iters}: graph construction + fit, single-threaded FP64 C",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = datagen.WORKLOADS[args.workload]
+    Xh = w.data()
+    ns = min(REF_SAMPLE, w.n)
+    X = np.ascontiguousarray(Xh[:ns])
+    for _ in range(args.warmup):
+        _oracle_step(O, w, X, True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        k = _oracle_step(O, w, X, True)
+    dt = time.perf_counter() - t0
+    v = ns * args.steps / dt
+    sample = (f"first {ns} samples of {w.name} per step, k = {k}, k0 = {ns // w.xi}: graph construction + fit, "
+              f"single-threaded FP64 C oracle")
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "kappa": w.kappa, "sample_n": ns},
+           "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,26 @@ GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, con
                     void *stream);
 
 /*
+ * The three steps the update and the refinement are made of, for callers that
+ * sequence the path themselves (they run the same kernels as the calls above).
+ *
+ * gk_group_by_label: the cluster set S (Alg. 1 and 3 map labels to it) as a
+ *   CSR: offsets int32[k + 1], members int32[n] (ascending id within a
+ *   cluster), counts int32[k] or NULL.  Workspace: gk_workspace_size(GK_OP_UPDATE, ...).
+ * gk_update_from_groups: the centroid update of gk_update_step given that CSR.
+ * gk_graph_refine_groups: the refinement of gk_graph_refine given that CSR.
+ * Labels out of range are reported through the status word, as above.
+ */
+GK_API int gk_group_by_label(const int32_t *labels, int64_t n, int32_t k, int32_t *offsets, int32_t *members,
+                             int32_t *counts, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                 const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                                 void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                  const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster,
+                                  int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * KNN-graph construction by repeated fast k-means (Alg. 3): random graph and
  * labels at k0 = max(1, floor(n / xi)), centroids from those labels, then tau
  * rounds of { one graph-guided assignment, one update, one refinement }

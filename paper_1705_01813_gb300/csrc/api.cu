@@ -237,6 +237,64 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
     return GK_OK;
 }
 
+int gk_group_by_label(const int32_t *labels, int64_t n, int32_t k, int32_t *offsets, int32_t *members,
+                      int32_t *counts, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if (n < 1 || n >= MAX_ROWS)
+        return fail(GK_ERR_INVALID, "n = %lld out of range", (long long)n);
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (!labels || !offsets || !members)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_UPDATE, n, 1, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_UPDATE, n, 1, k);
+    GK_CUDA(launch_group(labels, n, k, offsets, members, counts ? counts : L.grp.counts, L.grp.scratch, L.st,
+                         (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2, void *ws,
+                          size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 1)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (!offsets || !members || !C)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_UPDATE, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_UPDATE, n, d, k);
+    GK_CUDA(launch_update(X, n, d, ld, offsets, members, k, C, counts, sum_d2, L.upd_scratch, (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
+                           float *g_dist, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (k < 1)
+        return fail(GK_ERR_INVALID, "k = %d < 1", k);
+    if (max_cluster < 2)
+        return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
+    if (!offsets || !members || !g_idx || !g_dist)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    if ((rc = check_ws(ws, ws_bytes, sizeof(DevStatus))))
+        return rc;
+    GK_CUDA(launch_refine(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist,
+                          static_cast<DevStatus *>(ws), (cudaStream_t)stream));
+    return GK_OK;
+}
+
 int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
                   int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
                   int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)

@@ -25,7 +25,8 @@ GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD = range(5)
 #: every entry point the header declares (checked by the tests)
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
-           "gk_kmeans_fit", "gk_read_status"]
+           "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
+           "gk_graph_refine_groups"]
 
 
 class GraphParams(ctypes.Structure):
@@ -71,6 +72,9 @@ def load(build_if_missing: bool = True):
             L.gk_build_knn_graph.argtypes = [P, I64, I64, I64, ctypes.POINTER(GraphParams), P, P, P, P, P, SZ, P]
             L.gk_kmeans_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, U64, P, P, P, P, P, SZ, P]
             L.gk_read_status.argtypes = [P, P]
+            L.gk_group_by_label.argtypes = [P, I64, I32, P, P, P, P, SZ, P]
+            L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
+            L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, P, P, P, SZ, P]
             for name in EXPORTS:
                 if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
                     getattr(L, name).restype = ctypes.c_int
@@ -153,19 +157,26 @@ def init_labels(n: int, k: int, seed: int, out: torch.Tensor | None = None, stre
     return out
 
 
-def init_graph(X: torch.Tensor, kappa: int, seed: int, ws: Workspace | None = None, stream=None):
+def init_graph(X: torch.Tensor, kappa: int, seed: int, g_idx=None, g_dist=None, ws: Workspace | None = None,
+               stream=None):
     n, d, ld = _x(X)
-    gi = torch.empty((n, kappa), dtype=torch.int32, device=X.device)
-    gd = torch.empty((n, kappa), dtype=torch.float32, device=X.device)
+    gi = torch.empty((n, kappa), dtype=torch.int32, device=X.device) if g_idx is None else g_idx
+    gd = torch.empty((n, kappa), dtype=torch.float32, device=X.device) if g_dist is None else g_dist
     ws = ws or workspace(256, X.device)
     _check(load().gk_init_graph(_ptr(X), n, d, ld, kappa, seed, _ptr(gi), _ptr(gd), ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return gi, gd
 
 
-def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=None, sum_d2=None, n_changed=None,
+ALLOC = "alloc"
+
+
+def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=ALLOC, n_changed=ALLOC,
                 ws: Workspace | None = None, stream=None):
-    """Graph-guided assignment; returns (labels_out, best_d2, sum_d2, n_changed) tensors."""
+    """Graph-guided assignment; returns (labels_out, best_d2, sum_d2, n_changed).
+
+    The optional outputs are allocated by default; pass a tensor to reuse it or
+    None to have the library skip that output."""
     n, d, ld = _x(X)
     _dev(g_idx, torch.int32, "g_idx")
     _dev(C, torch.float32, "C")
@@ -173,9 +184,9 @@ def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=None, sum_d2=No
     k, kappa = C.shape[0], g_idx.shape[1]
     dev = X.device
     labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
-    best_d2 = torch.empty(n, dtype=torch.float32, device=dev) if best_d2 is None else best_d2
-    sum_d2 = torch.empty(1, dtype=torch.float64, device=dev) if sum_d2 is None else sum_d2
-    n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is None else n_changed
+    best_d2 = torch.empty(n, dtype=torch.float32, device=dev) if best_d2 is ALLOC else best_d2
+    sum_d2 = torch.empty(1, dtype=torch.float64, device=dev) if sum_d2 is ALLOC else sum_d2
+    n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is ALLOC else n_changed
     ws = ws or workspace(workspace_size(GK_OP_ASSIGN, n, d, k, kappa), dev)
     _check(load().gk_assign_step(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
                                  _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), ws.ptr, ws.nbytes,
@@ -247,6 +258,42 @@ def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, la
                                 _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return labels_out, C_out, counts_out, (list(log) if want_log else None)
+
+
+def group_by_label(labels, k: int, offsets=None, members=None, counts=None, ws: Workspace | None = None,
+                   stream=None):
+    """CSR of the clusters: (offsets [k+1], members [n], counts [k])."""
+    _dev(labels, torch.int32, "labels")
+    n = labels.shape[0]
+    dev = labels.device
+    offsets = torch.empty(k + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    members = torch.empty(n, dtype=torch.int32, device=dev) if members is None else members
+    counts = torch.empty(k, dtype=torch.int32, device=dev) if counts is None else counts
+    ws = ws or workspace(workspace_size(GK_OP_UPDATE, n, 1, k), dev)
+    _check(load().gk_group_by_label(_ptr(labels), n, k, _ptr(offsets), _ptr(members), _ptr(counts), ws.ptr,
+                                    ws.nbytes, _stream(stream)))
+    return offsets, members, counts
+
+
+def update_from_groups(X, offsets, members, k: int, C, counts=None, sum_d2=None, ws: Workspace | None = None,
+                       stream=None):
+    """Segmented mean over a CSR grouping, in place on C."""
+    n, d, ld = _x(X)
+    ws = ws or workspace(workspace_size(GK_OP_UPDATE, n, d, k), X.device)
+    _check(load().gk_update_from_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, _ptr(C),
+                                        _ptr(counts), _ptr(sum_d2), ws.ptr, ws.nbytes, _stream(stream)))
+    return C
+
+
+def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster: int = 128,
+                        ws: Workspace | None = None, stream=None):
+    """Graph refinement over a CSR grouping, in place on (g_idx, g_dist)."""
+    n, d, ld = _x(X)
+    ws = ws or workspace(256, X.device)
+    _check(load().gk_graph_refine_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, g_idx.shape[1],
+                                         max_cluster, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
+                                         _stream(stream)))
+    return g_idx, g_dist
 
 
 def read_status(ws: Workspace, stream=None) -> int:
