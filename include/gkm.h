@@ -101,7 +101,7 @@ GK_API size_t gk_workspace_size_build(int64_t n, int64_t d, const gk_graph_param
 GK_API int gk_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, void *stream);
 
 /*
- * Random initial KNN graph ("Initialize G with random lists", Alg. 3).
+ * Random initial KNN graph (Alg. 3 begins from random neighbour lists).
  * Row i takes draws j = output(i * 2^32 + a + 1) mod n, a = 0, 1, ..., of the
  * SplitMix64 generator seeded with seed ^ 0x4752415000000000, rejecting j == i
  * and ids it already holds, until kappa are accepted; their squared distances
@@ -203,6 +203,32 @@ GK_API int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
 GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
                   int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
                   int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * gk_update_step without a workspace, for callers that cannot allocate device
+ * memory: for instance an application whose framework owns all device memory
+ * through its own pool and forbids raw cudaMalloc, or a latency-bound serving
+ * loop where cudaMalloc / cudaFree may synchronise the device.  (The paper has
+ * no counterpart: this is an interface choice of the library.)
+ *
+ * Same arguments and results as gk_update_step (no offsets / members
+ * outputs).  Scratch comes from one fixed array compiled into the library's
+ * device image: 24 MiB on every GPU that loads the library, held until the
+ * process exits.  Limits: n <= 1,048,576 and k <= 32,768; larger sizes return
+ * GK_ERR_INVALID with a message.  Nothing is allocated by the call.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps on
+ *    the GPU (different streams, or different host threads) race and corrupt
+ *    each other's results.  Serialise them, e.g. on one stream.
+ *  - The array keeps the previous call's contents; the call clears what must
+ *    start at zero.  Labels out of range are not reported through a status
+ *    word here (there is no workspace to read it from): they are left out of
+ *    `counts`, so sum(counts) < n reveals them.
+ */
+GK_API int gk_update_step_noalloc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                                  float *C, int32_t *counts, double *sum_d2, void *stream);
 
 /*
  * Synchronise `stream`, return the status word the kernels of calls that used

@@ -10,8 +10,9 @@
  * Every function follows the paper in its own order and notation:
  *   - k-means objective and the two Lloyd steps: Eq. 1 and the paragraph after it (Sec. 1)
  *   - composite vectors D_r and the objective I: Eq. 2 (Sec. 3.1)
- *   - candidate clusters from the kappa neighbours: Alg. 2 (Sec. 4.2), in its
- *     "closest centroid among the collected clusters" form (end of Sec. 4.2)
+ *   - candidate clusters from the kappa neighbours: Alg. 2 (Sec. 4.2), in the
+ *     form given at the end of Sec. 4.2, where a sample takes the nearest
+ *     centroid among the collected clusters
  *   - KNN-graph construction by repeated fast k-means: Alg. 3 (Sec. 4.3)
  *   - cluster count k0 = floor(n / xi): Alg. 3 and Sec. 4.3
  *   - one k-means iteration per graph round: Sec. 4.5
@@ -124,7 +125,7 @@ static void or_sort_row(int32_t *idx, double *dist, int32_t len)
 }
 
 /*
- * Random initial KNN graph (Alg. 3, "Initialize G^t with random lists").
+ * Random initial KNN graph (Alg. 3 begins from random neighbour lists).
  * Row i draws j = draw(seed^GRAP, i * 2^32 + a) mod n for a = 0, 1, ...,
  * rejects j == i and indices it already holds, and stops at kappa accepted.
  * The row is then sorted by (distance, index) (R7).
@@ -333,7 +334,7 @@ static void or_group(const int32_t *L, int64_t n, int32_t k, int64_t *offsets, i
 }
 
 /*
- * Merge the pair (dist, j) into row i (Alg. 3, "Update G[i] ... with d(x_i, x_j)"):
+ * Merge the pair (dist, j) into row i (Alg. 3: a compared pair updates both rows):
  * the row keeps its kappa smallest keys (R3/R7), never holds j twice and never
  * holds i.  The row is sorted, so the new key is placed by insertion.
  */
@@ -369,7 +370,7 @@ static void or_chunk(int64_t m, int64_t nc, int64_t c, int64_t *start, int64_t *
     *size = base + (c < rem ? 1 : 0);
 }
 
-/* bit set of visited pairs (Alg. 3, "if <i,j> is NOT visited"); n*n bits */
+/* bit set of the pairs compared so far (Alg. 3 skips a pair seen before); n*n bits */
 typedef struct {
     uint8_t *bits;
     int64_t n;

@@ -7,7 +7,7 @@ own code path never does.  It shares no code with the CUDA side: it compiles
 its own C file with gcc and marshals numpy arrays through ctypes.
 
 Every function restates the paper (Deng & Zhao, arXiv 1705.01813):
-  init_labels / init_graph   seeded start (Alg. 3 "random lists"; SplitMix64 by its published definition)
+  init_labels / init_graph   seeded start (Alg. 3 starts from random neighbour lists; SplitMix64 by its published definition)
   assign                     Alg. 2 with the closest-centroid rule of Sec. 4.2 (GK-means^-)
   assign_exhaustive          Lloyd's assignment after Eq. 1 (every centroid a candidate)
   update                     centroid = mean (Sec. 1), Eq. 2 objective I, Eq. 4 distortion

@@ -1,5 +1,5 @@
 // Seeded initial state: random labels and the random initial KNN graph
-// ("Initialize G with random lists", Alg. 3).  Random numbers come from the
+// (Alg. 3 starts from a graph of random neighbour lists).  Random numbers come from the
 // SplitMix64 generator used as a counter-based function (common.cuh).
 #include "common.cuh"
 

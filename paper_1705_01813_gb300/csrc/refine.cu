@@ -1,5 +1,6 @@
-// Graph refinement inside clusters (Alg. 3, "for each S_m, for each pair
-// <i, j> in S_m x S_m: update G[i] and G[j] with d(x_i, x_j)"), exact FP32.
+// Graph refinement inside clusters (Alg. 3: every pair of samples that share
+// a cluster is compared, and the pair's distance updates both samples' rows),
+// exact FP32.
 //
 // A cluster of m members (CSR, ascending id) larger than max_cluster is cut
 // into ceil(m / max_cluster) runs of consecutive members whose sizes differ by
