@@ -120,6 +120,14 @@ int32_t build_k0(int64_t n, int32_t xi) { return (int32_t)(n / xi > 0 ? n / xi :
 
 }  // namespace
 
+namespace gkm {
+// Lets other translation units of the library report through gk_last_error().
+void set_last_error(const char *msg)
+{
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+}  // namespace gkm
+
 extern "C" {
 
 const char *gk_version(void) { return "libgkm 0.1 (sm_103a)"; }

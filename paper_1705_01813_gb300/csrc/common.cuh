@@ -118,6 +118,8 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
                           const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
                           double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s);
 
+void set_last_error(const char *msg);
+
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                           float *g_dist, DevStatus *st, cudaStream_t s);

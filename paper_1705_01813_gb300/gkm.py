@@ -26,7 +26,7 @@ GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD = range(5)
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
-           "gk_graph_refine_groups"]
+           "gk_graph_refine_groups", "gk_update_step_noalloc"]
 
 
 class GraphParams(ctypes.Structure):
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
             L.gk_group_by_label.argtypes = [P, I64, I32, P, P, P, P, SZ, P]
             L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
             L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, P, P, P, SZ, P]
+            L.gk_update_step_noalloc.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
             for name in EXPORTS:
                 if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
                     getattr(L, name).restype = ctypes.c_int
