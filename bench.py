@@ -138,6 +138,7 @@ class Path:
         self.C = torch.empty((w.k, d), dtype=f32, device=dev)
         self.s = torch.empty(4, dtype=f64, device=dev)
         self.ws = gkm.Workspace(max(gkm.workspace_size(gkm.GK_OP_FIT, n, d, kmax, w.kappa),
+                                    gkm.workspace_size(gkm.GK_OP_REFINE, n, d, kmax, w.kappa),
                                     gkm.workspace_size_build(n, d, w.kappa, w.xi, w.tau, w.max_cluster)), dev)
 
     def _ev(self):
@@ -195,7 +196,7 @@ def _radix_passes(k):
 def launches_per_step(w):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
-    upd, asg, ref = 2, 2, 1
+    upd, asg, ref = 2, 2, 1 + 3 + 2  # refine: run count, scan, two tile widths
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit

@@ -167,6 +167,7 @@ GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, con
  *   cluster), counts int32[k] or NULL.  Workspace: gk_workspace_size(GK_OP_UPDATE, ...).
  * gk_update_from_groups: the centroid update of gk_update_step given that CSR.
  * gk_graph_refine_groups: the refinement of gk_graph_refine given that CSR.
+ *   Workspace: gk_workspace_size(GK_OP_REFINE, ...).
  * Labels out of range are reported through the status word, as above.
  */
 GK_API int gk_group_by_label(const int32_t *labels, int64_t n, int32_t k, int32_t *offsets, int32_t *members,

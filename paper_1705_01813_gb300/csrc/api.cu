@@ -79,6 +79,7 @@ struct Layout {
     GroupBufs grp;
     void *upd_scratch;
     void *asg_scratch;
+    void *ref_scratch;
     int32_t *labels_a;
     int32_t *labels_b;
     float *cent;
@@ -104,6 +105,8 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
         L.upd_scratch = cv.take<char>(update_scratch_bytes(n, k));
     if (need_assign)
         L.asg_scratch = cv.take<char>(assign_scratch_bytes(n));
+    if (op == GK_OP_REFINE || op == GK_OP_BUILD)
+        L.ref_scratch = cv.take<char>(refine_scratch_bytes(k));
     if (op == GK_OP_FIT || op == GK_OP_BUILD) {
         L.labels_b = cv.take<int32_t>((size_t)n);
         L.elog = cv.take<double>(MAX_LOG);
@@ -241,7 +244,8 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
     L = carve(ws, GK_OP_REFINE, n, d, k);
     cudaStream_t s = (cudaStream_t)stream;
     GK_CUDA(launch_group(labels, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist, L.st, s));
+    GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist,
+                          L.ref_scratch, L.st, s));
     return GK_OK;
 }
 
@@ -296,10 +300,12 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
     if (!offsets || !members || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
-    if ((rc = check_ws(ws, ws_bytes, sizeof(DevStatus))))
+    Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
-    GK_CUDA(launch_refine(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist,
-                          static_cast<DevStatus *>(ws), (cudaStream_t)stream));
+    L = carve(ws, GK_OP_REFINE, n, d, k);
+    GK_CUDA(launch_refine(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch, L.st,
+                          (cudaStream_t)stream));
     return GK_OK;
 }
 
@@ -389,7 +395,7 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
                               L.elog + 2 + 2 * t, L.upd_scratch, s));
         // exhaustive pairs inside the clusters of the new partition
         GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
-                              g_dist, L.st, s));
+                              g_dist, L.ref_scratch, L.st, s));
         int32_t *tmp = cur;
         cur = nxt;
         nxt = tmp;

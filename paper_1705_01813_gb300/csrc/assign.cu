@@ -173,6 +173,167 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restric
     }
 }
 
+// Sum of 32 per-lane partial values for 32 candidates at once: after the five
+// exchange steps lane l holds the total over the warp of v[l] (31 shuffles in
+// all, instead of 5 per candidate).
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32])
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; j++) {
+            float send = upper ? v[j] : v[j + o];
+            float keep = upper ? v[j + o] : v[j];
+            v[j] = keep + __shfl_xor_sync(FULL_MASK, send, o);
+        }
+    }
+    return v[0];
+}
+
+// Coalesced variant for 16-byte rows (d % 4 == 0, d <= 32 * 4 * NV): the warp
+// keeps x_i in registers (lane l owns vectors l, l + 32, ...), reads each
+// candidate centroid row with one coalesced 16-byte load per lane and vector,
+// and reduces 32 candidates' partial distances together.
+template <int NV>
+__global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
+                                                               int64_t ld, const int32_t *__restrict__ G, int kappa,
+                                                               const float *__restrict__ C, int k,
+                                                               const int32_t *__restrict__ Lin,
+                                                               int32_t *__restrict__ Lout,
+                                                               float *__restrict__ best_out,
+                                                               double *__restrict__ blk_sum,
+                                                               unsigned long long *__restrict__ blk_changed,
+                                                               DevStatus *st)
+{
+    __shared__ int s_q[AS_WARPS][AS_QCAP];
+    __shared__ double s_sum[AS_WARPS];
+    __shared__ unsigned long long s_chg[AS_WARPS];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    int *qlist = s_q[w];
+    const int d4 = d >> 2;
+    const float4 *C4 = reinterpret_cast<const float4 *>(C);
+
+    double wsum = 0.0;
+    unsigned long long wchg = 0;
+    const int ncand = kappa + 1;
+    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
+        float4 xv[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            int col = lane + 32 * v;
+            xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // candidate labels: slot 0 is the own label, slot 1 + j the label of neighbour j
+        const int own = Lin[i];
+        int u = 0;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            int c = c0 + lane;
+            int lab = -1;
+            if (c == 0) {
+                lab = own;
+            } else if (c < ncand) {
+                int nb = __ldcs(G + i * kappa + (c - 1));
+                if ((unsigned)nb < (unsigned)n)
+                    lab = Lin[nb];
+                else
+                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
+            }
+            if (c < ncand && (unsigned)lab >= (unsigned)k) {
+                flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                lab = -1;
+            }
+            unsigned peers = __match_any_sync(FULL_MASK, lab);
+            bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
+            if (keep)
+                for (int q = 0; q < u; q++)
+                    if (qlist[q] == lab) {
+                        keep = false;
+                        break;
+                    }
+            unsigned keeps = __ballot_sync(FULL_MASK, keep);
+            __syncwarp();
+            if (keep)
+                qlist[u + __popc(keeps & lanemask_lt())] = lab;
+            u += __popc(keeps);
+            __syncwarp();
+        }
+        float bd = __int_as_float(0x7f800000);
+        int br = 0x7fffffff;
+        for (int g0 = 0; g0 < u; g0 += 32) {
+            const int cnt = min(32, u - g0);
+            float part[32];
+#pragma unroll
+            for (int c = 0; c < 32; c++) {
+                float acc = 0.f;
+                if (c < cnt) {
+                    const float4 *row = C4 + (int64_t)qlist[g0 + c] * d4;
+                    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        int col = lane + 32 * v;
+                        if (col < d4) {
+                            float4 cv = __ldg(row + col);
+                            float e0 = xv[v].x - cv.x, e1 = xv[v].y - cv.y, e2 = xv[v].z - cv.z,
+                                  e3 = xv[v].w - cv.w;
+                            a0 = fmaf(e0, e0, a0);
+                            a1 = fmaf(e1, e1, a1);
+                            a0 = fmaf(e2, e2, a0);
+                            a1 = fmaf(e3, e3, a1);
+                        }
+                    }
+                    acc = a0 + a1;
+                }
+                part[c] = acc;
+            }
+            float tot = transpose_reduce32(part);
+            if (lane < cnt) {
+                int r = qlist[g0 + lane];
+                if (key_less(tot, r, bd, br)) {
+                    bd = tot;
+                    br = r;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float od = __shfl_xor_sync(FULL_MASK, bd, o);
+            int orr = __shfl_xor_sync(FULL_MASK, br, o);
+            if (key_less(od, orr, bd, br)) {
+                bd = od;
+                br = orr;
+            }
+        }
+        if (lane == 0) {
+            if (br == 0x7fffffff)  // no valid candidate (own label out of range): keep the input label
+                br = own, bd = 0.f;
+            Lout[i] = br;
+            if (best_out)
+                best_out[i] = bd;
+            wsum += (double)bd;
+            wchg += (br != own) ? 1ull : 0ull;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s_sum[w] = wsum;
+        s_chg[w] = wchg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int q = 0; q < AS_WARPS; q++) {
+            t += s_sum[q];
+            c += s_chg[q];
+        }
+        blk_sum[blockIdx.x] = t;
+        blk_changed[blockIdx.x] = c;
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_assign_finish(const double *__restrict__ blk_sum,
                                                         const unsigned long long *__restrict__ blk_changed, int nb,
                                                         double *__restrict__ sum_d2, int64_t *__restrict__ n_changed)
@@ -219,7 +380,21 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
     bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                 ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     cudaError_t e;
-    if (vec4) {
+    const int d4 = (int)(d / 4);
+    if (vec4 && d4 <= 32 * 8) {
+#define GK_ASG(NV)                                                                                               \
+    k_assign_rows<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,      \
+                                                          labels_out, best_d2, blk_sum, blk_chg, st)
+        if (d4 <= 32)
+            GK_ASG(1);
+        else if (d4 <= 64)
+            GK_ASG(2);
+        else if (d4 <= 128)
+            GK_ASG(4);
+        else
+            GK_ASG(8);
+#undef GK_ASG
+    } else if (vec4) {
         if (shm > 48 * 1024 &&
             (e = cudaFuncSetAttribute(k_assign<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
                 cudaSuccess)

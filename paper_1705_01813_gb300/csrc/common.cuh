@@ -59,6 +59,25 @@ __device__ __forceinline__ float pair_d2_seq(const float *__restrict__ a, const 
     return acc;
 }
 
+// The same sum with 16-byte loads (a, b 16-byte aligned, d a multiple of 4):
+// the accumulation order, and therefore the result, is that of pair_d2_seq.
+__device__ __forceinline__ float pair_d2_seq4(const float *__restrict__ a, const float *__restrict__ b, int d)
+{
+    const float4 *a4 = reinterpret_cast<const float4 *>(a);
+    const float4 *b4 = reinterpret_cast<const float4 *>(b);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int t = 0; t < (d >> 2); t++) {
+        float4 x = a4[t], y = __ldg(b4 + t);
+        float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+        acc = fmaf(e0, e0, acc);
+        acc = fmaf(e1, e1, acc);
+        acc = fmaf(e2, e2, acc);
+        acc = fmaf(e3, e3, acc);
+    }
+    return acc;
+}
+
 // (distance, index) key order of graph rows: smaller distance first, then smaller id.
 __device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
 {
@@ -120,8 +139,9 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
 
 void set_last_error(const char *msg);
 
+size_t refine_scratch_bytes(int32_t k);
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
-                          float *g_dist, DevStatus *st, cudaStream_t s);
+                          float *g_dist, void *scratch, DevStatus *st, cudaStream_t s);
 
 }  // namespace gkm

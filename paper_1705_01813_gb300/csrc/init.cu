@@ -33,7 +33,8 @@ constexpr int IG_WARPS = 4;
 __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__restrict__ X, int64_t n, int d,
                                                               int64_t ld, int kappa, uint64_t key,
                                                               int32_t *__restrict__ g_idx,
-                                                              float *__restrict__ g_dist, DevStatus *st)
+                                                              float *__restrict__ g_dist, DevStatus *st,
+                                                              bool vec4)
 {
     __shared__ int s_idx[IG_WARPS][MAX_KAPPA];
     __shared__ float s_dist[IG_WARPS][MAX_KAPPA];
@@ -71,8 +72,13 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
             __syncwarp();
         }
         const float *xi = X + i * ld;
-        for (int q = lane; q < kappa; q += 32)
-            rdist[q] = pair_d2_seq(xi, X + (int64_t)ridx[q] * ld, d);
+        if (vec4) {
+            for (int q = lane; q < kappa; q += 32)
+                rdist[q] = pair_d2_seq4(xi, X + (int64_t)ridx[q] * ld, d);
+        } else {
+            for (int q = lane; q < kappa; q += 32)
+                rdist[q] = pair_d2_seq(xi, X + (int64_t)ridx[q] * ld, d);
+        }
         __syncwarp();
         // rank sort: ids in a row are distinct, so keys are distinct
         int64_t out = i * (int64_t)kappa;
@@ -93,10 +99,11 @@ cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
                               int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
 {
     int64_t blocks = (n + IG_WARPS - 1) / IG_WARPS;
-    if (blocks > 152 * 32)
-        blocks = 152 * 32;
+    if (blocks > 152 * 64)
+        blocks = 152 * 64;
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, 0, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, g_idx,
-                                                           g_dist, st);
+                                                           g_dist, st, vec4);
     return cudaGetLastError();
 }
 

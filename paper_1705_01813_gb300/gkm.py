@@ -290,7 +290,7 @@ def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster:
                         ws: Workspace | None = None, stream=None):
     """Graph refinement over a CSR grouping, in place on (g_idx, g_dist)."""
     n, d, ld = _x(X)
-    ws = ws or workspace(256, X.device)
+    ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, g_idx.shape[1]), X.device)
     _check(load().gk_graph_refine_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, g_idx.shape[1],
                                          max_cluster, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
                                          _stream(stream)))
