@@ -29,6 +29,7 @@ cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *lab
 // rejection rule.  Each lane then computes the FP32 distance of one neighbour
 // (pair_d2_seq), and the row is sorted by (distance, id) by ranking.
 constexpr int IG_WARPS = 4;
+constexpr int IG_DC = 128;  // coordinates staged per step (vector path)
 
 __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__restrict__ X, int64_t n, int d,
                                                               int64_t ld, int kappa, uint64_t key,
@@ -38,6 +39,8 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
 {
     __shared__ int s_idx[IG_WARPS][MAX_KAPPA];
     __shared__ float s_dist[IG_WARPS][MAX_KAPPA];
+    // dynamic: per warp IG_DC floats of x_i, then 32 staged rows of IG_DC + 4 floats
+    extern __shared__ __align__(16) float s_dyn[];
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *ridx = s_idx[w];
     float *rdist = s_dist[w];
@@ -73,8 +76,44 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
         }
         const float *xi = X + i * ld;
         if (vec4) {
-            for (int q = lane; q < kappa; q += 32)
-                rdist[q] = pair_d2_seq4(xi, X + (int64_t)ridx[q] * ld, d);
+            // neighbour rows staged 32 at a time, IG_DC coordinates at a time, with
+            // one coalesced 16-byte load per lane and row; lane q then sums its
+            // row's squared differences in ascending coordinate order (the order
+            // of pair_d2_seq) from shared memory
+            float *xs = s_dyn + w * (IG_DC + 32 * (IG_DC + 4));
+            float *rows = xs + IG_DC;
+            for (int b0 = 0; b0 < kappa; b0 += 32) {
+                const int nb = min(32, kappa - b0);
+                float acc = 0.f;
+                for (int t0 = 0; t0 < d; t0 += IG_DC) {
+                    const int dc = min(IG_DC, d - t0);
+                    __syncwarp();
+                    for (int t = lane * 4; t < dc; t += 128)
+                        *reinterpret_cast<float4 *>(xs + t) = *reinterpret_cast<const float4 *>(xi + t0 + t);
+#pragma unroll 8
+                    for (int q = 0; q < nb; q++) {
+                        const float *src = X + (int64_t)ridx[b0 + q] * ld + t0;
+                        for (int t = lane * 4; t < dc; t += 128)
+                            *reinterpret_cast<float4 *>(rows + q * (IG_DC + 4) + t) =
+                                __ldg(reinterpret_cast<const float4 *>(src + t));
+                    }
+                    __syncwarp();
+                    if (lane < nb) {
+                        const float *myrow = rows + lane * (IG_DC + 4);
+                        for (int t = 0; t < dc; t += 4) {
+                            float4 a = *reinterpret_cast<const float4 *>(xs + t);
+                            float4 b = *reinterpret_cast<const float4 *>(myrow + t);
+                            float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+                            acc = fmaf(e0, e0, acc);
+                            acc = fmaf(e1, e1, acc);
+                            acc = fmaf(e2, e2, acc);
+                            acc = fmaf(e3, e3, acc);
+                        }
+                    }
+                }
+                if (lane < nb)
+                    rdist[b0 + lane] = acc;
+            }
         } else {
             for (int q = lane; q < kappa; q += 32)
                 rdist[q] = pair_d2_seq(xi, X + (int64_t)ridx[q] * ld, d);
@@ -102,7 +141,13 @@ cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
     if (blocks > 152 * 64)
         blocks = 152 * 64;
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, 0, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, g_idx,
+    const size_t shm = vec4 ? sizeof(float) * IG_WARPS * (IG_DC + 32 * (IG_DC + 4)) : 0;
+    if (shm) {
+        cudaError_t e = cudaFuncSetAttribute(k_init_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess)
+            return e;
+    }
+    k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, g_idx,
                                                            g_dist, st, vec4);
     return cudaGetLastError();
 }

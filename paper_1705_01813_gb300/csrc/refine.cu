@@ -40,7 +40,10 @@ struct RefineTile {
     static constexpr size_t fixed_bytes =
         sizeof(float) * (stage_floats > tile_floats ? stage_floats : tile_floats) + sizeof(int) * 2 * T;
     // per warp: row list (kappa ids + dists), candidates (T), new row (kappa)
-    __host__ __device__ static size_t warp_bytes(int kappa) { return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + T); }
+    __host__ __device__ static size_t warp_bytes(int kappa)
+    {
+        return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + T) + 4 * sizeof(unsigned);
+    }
     __host__ __device__ static size_t smem_bytes(int kappa) { return fixed_bytes + RF_WARPS * warp_bytes(kappa); }
 };
 
@@ -58,16 +61,33 @@ __device__ __forceinline__ int lower_rank(const float *v, const int *id, int len
     return lo;
 }
 
-// Merge the candidates (ids cid[0..ncol), distances drow[0..ncol)) into graph
-// row i (kappa sorted keys at gi / gd).  Warp-cooperative.
+// Merge the candidates (ids cid[0..ncol), ascending; distances drow[0..ncol))
+// into graph row i (kappa sorted keys at gi / gd).  Warp-cooperative.
+// Candidates already in the row are found by a binary search of each row id
+// among the (sorted) candidate ids and masked out; the others that beat the
+// row's kappa-th key are ranked among themselves and placed by rank.
 __device__ void merge_row(int i, const int *__restrict__ cid, const float *__restrict__ drow, int ncol, int kappa,
                           int32_t *__restrict__ gi, float *__restrict__ gd, int *li, float *lv, int *bi, float *bv,
-                          int *ni, float *nv)
+                          int *ni, float *nv, unsigned *dup)
 {
     const int lane = lane_id();
+    if (lane < 4)
+        dup[lane] = 0u;
+    __syncwarp();
     for (int q = lane; q < kappa; q += 32) {
-        li[q] = gi[q];
+        const int j = gi[q];
+        li[q] = j;
         lv[q] = gd[q];
+        int lo = 0, hi = ncol;  // first candidate id >= j
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (cid[mid] < j)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo < ncol && cid[lo] == j)
+            atomicOr(&dup[lo >> 5], 1u << (lo & 31));
     }
     __syncwarp();
     const float td = lv[kappa - 1];
@@ -75,20 +95,14 @@ __device__ void merge_row(int i, const int *__restrict__ cid, const float *__res
     // candidates that would enter the row and are not in it yet
     int ns = 0;
     for (int c0 = 0; c0 < ncol; c0 += 32) {
-        int c = c0 + lane;
+        const int c = c0 + lane;
         bool ok = c < ncol;
-        int j = ok ? cid[c] : -1;
-        float dv = ok ? drow[c] : 0.f;
-        ok = ok && j != i && key_less(dv, j, td, ti);
-        if (ok)
-            for (int q = 0; q < kappa; q++)
-                if (li[q] == j) {
-                    ok = false;
-                    break;
-                }
-        unsigned bal = __ballot_sync(FULL_MASK, ok);
+        const int j = ok ? cid[c] : -1;
+        const float dv = ok ? drow[c] : 0.f;
+        ok = ok && j != i && ((dup[c0 >> 5] >> lane) & 1u) == 0u && key_less(dv, j, td, ti);
+        const unsigned bal = __ballot_sync(FULL_MASK, ok);
         if (ok) {
-            int p = ns + __popc(bal & lanemask_lt());
+            const int p = ns + __popc(bal & lanemask_lt());
             bi[p] = j;
             bv[p] = dv;
         }
@@ -103,7 +117,7 @@ __device__ void merge_row(int i, const int *__restrict__ cid, const float *__res
     int kjs[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-        int b = lane + 32 * u;
+        const int b = lane + 32 * u;
         rk[u] = -1;
         if (b < ns) {
             kvs[u] = bv[b];
@@ -127,7 +141,7 @@ __device__ void merge_row(int i, const int *__restrict__ cid, const float *__res
 #pragma unroll
     for (int u = 0; u < 4; u++) {
         if (rk[u] >= 0) {
-            int pos = rk[u] + lower_rank(lv, li, kappa, kvs[u], kjs[u]);
+            const int pos = rk[u] + lower_rank(lv, li, kappa, kvs[u], kjs[u]);
             if (pos < kappa) {
                 ni[pos] = kjs[u];
                 nv[pos] = kvs[u];
@@ -135,9 +149,9 @@ __device__ void merge_row(int i, const int *__restrict__ cid, const float *__res
         }
     }
     for (int a = lane; a < kappa; a += 32) {
-        float kv = lv[a];
-        int kj = li[a];
-        int pos = a + lower_rank(bv, bi, ns, kv, kj);
+        const float kv = lv[a];
+        const int kj = li[a];
+        const int pos = a + lower_rank(bv, bi, ns, kv, kj);
         if (pos < kappa) {
             ni[pos] = kj;
             nv[pos] = kv;
@@ -185,6 +199,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_refine(const float *__restrict__
     float *nv = reinterpret_cast<float *>(ni + kappa);
     int *bi = reinterpret_cast<int *>(nv + kappa);
     float *bv = reinterpret_cast<float *>(bi + T);
+    unsigned *dup = reinterpret_cast<unsigned *>(bv + T);
     const int ty = tid >> 4, tx = tid & 15;
 
     // block `run` handles that run: find its cluster r, run_off[r] <= run < run_off[r + 1]
@@ -284,7 +299,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_refine(const float *__restrict__
                     if (i < 0)
                         continue;
                     merge_row(i, cid, dt + row * DS, ncl, kappa, g_idx + (int64_t)i * kappa,
-                              g_dist + (int64_t)i * kappa, li, lv, bi, bv, ni, nv);
+                              g_dist + (int64_t)i * kappa, li, lv, bi, bv, ni, nv, dup);
                 }
             }
         }

@@ -13,7 +13,7 @@
 
 namespace gkm {
 
-constexpr int UP_WARPS = 8;
+constexpr int UP_WARPS = 4;
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {
@@ -60,7 +60,12 @@ __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL]
     }
 }
 
-// CPL: row vectors per lane per column block (chosen from d by the launcher).
+// One block of UP_WARPS warps per cluster.  Each warp is split into G groups
+// of L lanes; the W * G groups of the block take members g, g + W G, ... of
+// the cluster (UNR of them in flight per group), and lane s of a group owns
+// row vectors s, s + L, ... (CPL of them per column block).  Group sums are
+// widened to FP64, combined across the groups of a warp by shuffles and across
+// the warps through shared memory in a fixed order (reproducible bits).
 template <int VEC, int CPL>
 __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restrict__ X, int d, int64_t ld,
                                                           const int32_t *__restrict__ off,
@@ -69,83 +74,105 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                                                           double *__restrict__ contrib)
 {
     using V = typename VecT<VEC>::T;
-    const int lane = lane_id();
+    constexpr int UNR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : 4);  // member rows in flight per group
+    __shared__ double s_part[UP_WARPS][32 * CPL * VEC];
+    __shared__ double s_sq[UP_WARPS];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
     const int nv = d / VEC;  // vectors per row
     int L = 1;
     while (L < 32 && L < nv)
         L <<= 1;
     const int G = 32 / L;
     const int g = lane / L, sub = lane % L;
+    const int gstride = UP_WARPS * G, gidx = w * G + g;
     const int64_t ldv = ld / VEC;
     const V *Xv = reinterpret_cast<const V *>(X);
 
-    for (int r = blockIdx.x * UP_WARPS + (threadIdx.x >> 5); r < k; r += gridDim.x * UP_WARPS) {
-        const int beg = off[r], m = off[r + 1] - beg;
-        if (counts && lane == 0)
-            counts[r] = m;
-        if (m == 0) {
-            if (lane == 0)
-                contrib[r] = 0.0;
-            continue;
-        }
-        double sq_lane = 0.0, dd_lane = 0.0;
-        for (int cb = 0; cb < nv; cb += L * CPL) {
-            float s[CPL][VEC], c[CPL][VEC];
-            float qs = 0.f, qc = 0.f;
+    const int r = blockIdx.x;
+    if (r >= k)
+        return;
+    const int beg = off[r], m = off[r + 1] - beg;
+    if (counts && threadIdx.x == 0)
+        counts[r] = m;
+    if (m == 0) {
+        if (threadIdx.x == 0)
+            contrib[r] = 0.0;
+        return;
+    }
+    double sq_lane = 0.0, dd_lane = 0.0;
+    for (int cb = 0; cb < nv; cb += L * CPL) {
+        float s[CPL][VEC], c[CPL][VEC];
+        float qs = 0.f, qc = 0.f;
 #pragma unroll
-            for (int u = 0; u < CPL; u++)
+        for (int u = 0; u < CPL; u++)
 #pragma unroll
-                for (int q = 0; q < VEC; q++)
-                    s[u][q] = c[u][q] = 0.f;
-            // members in batches of 32 ids (one coalesced load), handed to the
-            // lane groups by shuffles; two members per group in flight
-            for (int b0 = 0; b0 < m; b0 += 32) {
-                const int nb = min(32, m - b0);
-                const int my_id = lane < nb ? mem[beg + b0 + lane] : 0;
-                for (int j = 0; j < nb; j += 2 * G) {
-                    const int p0 = j + g, p1 = j + G + g;
-                    const int id0 = __shfl_sync(FULL_MASK, my_id, p0 & 31);
-                    const int id1 = __shfl_sync(FULL_MASK, my_id, p1 & 31);
-                    V v0[CPL], v1[CPL];
-                    const V *row0 = Xv + (int64_t)id0 * ldv;
-                    const V *row1 = Xv + (int64_t)id1 * ldv;
+            for (int q = 0; q < VEC; q++)
+                s[u][q] = c[u][q] = 0.f;
+        for (int p0 = gidx; p0 < m; p0 += UNR * gstride) {
+            V v[UNR][CPL];
+#pragma unroll
+            for (int z = 0; z < UNR; z++) {
+                const int p = p0 + z * gstride;
+                if (p < m) {
+                    const V *row = Xv + (int64_t)__ldg(mem + beg + p) * ldv;
 #pragma unroll
                     for (int u = 0; u < CPL; u++) {
-                        int col = cb + sub + u * L;
-                        if (col < nv && p0 < nb)
-                            v0[u] = __ldcs(row0 + col);
-                        if (col < nv && p1 < nb)
-                            v1[u] = __ldcs(row1 + col);
-                    }
-                    if (p0 < nb)
-                        accumulate<VEC, CPL>(v0, s, c, qs, qc, cb, sub, L, nv);
-                    if (p1 < nb)
-                        accumulate<VEC, CPL>(v1, s, c, qs, qc, cb, sub, L, nv);
-                }
-            }
-            sq_lane += (double)qs - (double)qc;
-            // widen, combine the G groups, write the means of this column block
-#pragma unroll
-            for (int u = 0; u < CPL; u++) {
-                int col = cb + sub + u * L;
-#pragma unroll
-                for (int q = 0; q < VEC; q++) {
-                    double S = (double)s[u][q] - (double)c[u][q];
-                    for (int o = L; o < 32; o <<= 1)
-                        S += __shfl_xor_sync(FULL_MASK, S, o);
-                    if (col < nv && g == 0) {
-                        C[(int64_t)r * d + (int64_t)col * VEC + q] = (float)(S / (double)m);
-                        dd_lane += S * S;
+                        const int col = cb + sub + u * L;
+                        if (col < nv)
+                            v[z][u] = __ldcs(row + col);
                     }
                 }
             }
+#pragma unroll
+            for (int z = 0; z < UNR; z++)
+                if (p0 + z * gstride < m)
+                    accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
         }
-        for (int o = 1; o < 32; o <<= 1) {
-            sq_lane += __shfl_xor_sync(FULL_MASK, sq_lane, o);
-            dd_lane += __shfl_xor_sync(FULL_MASK, dd_lane, o);
+        sq_lane += (double)qs - (double)qc;
+        // widen, combine the G groups of the warp, then the warps of the block
+#pragma unroll
+        for (int u = 0; u < CPL; u++) {
+#pragma unroll
+            for (int q = 0; q < VEC; q++) {
+                double S = (double)s[u][q] - (double)c[u][q];
+                for (int o = L; o < 32; o <<= 1)
+                    S += __shfl_xor_sync(FULL_MASK, S, o);
+                if (g == 0)
+                    s_part[w][(u * L + sub) * VEC + q] = S;
+            }
         }
-        if (lane == 0)
-            contrib[r] = sq_lane - dd_lane / (double)m;
+        __syncthreads();
+        for (int e = threadIdx.x; e < L * CPL * VEC; e += UP_WARPS * 32) {
+            // entry e = (u * L + sb) * VEC + q holds column vector cb + sb + u * L, component q
+            const int u = (e / VEC) / L, sb = (e / VEC) % L;
+            const int colv = cb + sb + u * L;
+            if (colv < nv) {
+                double S = 0.0;
+                for (int ww = 0; ww < UP_WARPS; ww++)
+                    S += s_part[ww][e];
+                C[(int64_t)r * d + (int64_t)colv * VEC + (e % VEC)] = (float)(S / (double)m);
+                dd_lane += S * S;
+            }
+        }
+        __syncthreads();
+    }
+    // sum of ||x||^2 over all lanes, sum of D_t^2 over the threads that wrote means
+    for (int o = 1; o < 32; o <<= 1) {
+        sq_lane += __shfl_xor_sync(FULL_MASK, sq_lane, o);
+        dd_lane += __shfl_xor_sync(FULL_MASK, dd_lane, o);
+    }
+    if (lane == 0) {
+        s_sq[w] = sq_lane;
+        s_part[w][0] = dd_lane;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sq = 0.0, dd = 0.0;
+        for (int ww = 0; ww < UP_WARPS; ww++) {
+            sq += s_sq[ww];
+            dd += s_part[ww][0];
+        }
+        contrib[r] = sq - dd / (double)m;
     }
 }
 
@@ -176,9 +203,7 @@ cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, cons
 {
     (void)n;
     double *contrib = static_cast<double *>(scratch);
-    int64_t blocks = ((int64_t)k + UP_WARPS - 1) / UP_WARPS;
-    if (blocks > 152 * 64)
-        blocks = 152 * 64;
+    const int64_t blocks = k;
     bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const int nv = vec4 ? (int)(d / 4) : (int)d;
     const int L = nv >= 32 ? 32 : (nv >= 16 ? 16 : nv >= 8 ? 8 : nv >= 4 ? 4 : nv >= 2 ? 2 : 1);
