@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=1,
+                    help="graph refinement: 0 FP32 SIMT pair distances, 1 tensor-core Gram + FP32 rerank "
+                         "(same graph)")
+    ap.add_argument("--no-fp32-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -119,8 +123,9 @@ class ClockSampler:
 class Path:
     """Device buffers and the step sequence of one replica."""
 
-    def __init__(self, gkm, torch, w, X):
+    def __init__(self, gkm, torch, w, X, precision=1):
         self.gkm, self.torch, self.w = gkm, torch, w
+        self.precision = precision
         dev = X.device
         n, d = X.shape
         self.X, self.n, self.d = X, n, d
@@ -172,7 +177,7 @@ class Path:
             call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt,
                  self.s[0:1], ws=ws)
             call("refine", g.graph_refine_groups, self.X, self.off, self.mem, self.k0, self.gi, self.gd,
-                 w.max_cluster, ws=ws)
+                 w.max_cluster, self.precision, ws=ws)
             cur, nxt = nxt, cur
         # --- Alg. 2 (closest-centroid rule) at k on the constructed graph
         g.init_labels(n, w.k, w.seed + 1, out=self.la)
@@ -193,10 +198,11 @@ def _radix_passes(k):
     return (bits + 7) // 8
 
 
-def launches_per_step(w):
+def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
-    upd, asg, ref = 2, 2, 1 + 3 + 2  # refine: run count, scan, two tile widths
+    upd, asg = 2, 2
+    ref = 1 + 3 + (1 if precision == 1 else 2)  # refine: run count, scan, kernels
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit
@@ -218,25 +224,31 @@ def algorithmic_bytes(tag, w, k):
     return 0
 
 
-def kernel_of(tag):
-    return {"assign": "k_assign", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine"}[tag]
+def kernel_of(tag, precision=1):
+    if tag == "refine" and precision == 1:
+        return "k_refine_tc"
+    return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
+            "init_graph": "k_init_graph"}[tag]
 
 
-def source_sha(tag):
-    f = {"assign": "assign.cu", "update": "update.cu", "group": "group.cu", "refine": "refine.cu"}[tag]
+def source_sha(tag, precision=1):
+    f = {"assign": "assign.cu", "update": "update.cu", "group": "group.cu", "refine": "refine.cu",
+         "init_graph": "init.cu"}[tag]
+    if tag == "refine" and precision == 1:
+        f = "refine_tc.cu"
     with open(os.path.join(ROOT, "paper_1705_01813_gb300", "csrc", f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def ncu_traffic(tag, workload):
+def ncu_traffic(tag, workload, precision=1):
     """DRAM bytes per launch from the committed ncu summary, if it is for the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
-    e = j.get(f"{kernel_of(tag)}:{workload}")
-    if not e or e.get("source_sha") != source_sha(tag):
+    e = j.get(f"{kernel_of(tag, precision)}:{workload}")
+    if not e or e.get("source_sha") != source_sha(tag, precision):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -256,7 +268,7 @@ def run_gpu(args):
     X = torch.from_numpy(Xh).cuda()
     gkm.load()
 
-    path = Path(gkm, torch, w, X)
+    path = Path(gkm, torch, w, X, args.precision)
     for _ in range(args.warmup):
         path.step()
     torch.cuda.synchronize()
@@ -291,6 +303,21 @@ def run_gpu(args):
         per_tag.setdefault(tag, []).append(e0.elapsed_time(e1) / 1e3)
     status = gkm.read_status(path.ws)
 
+    # the plain FP32 path (SIMT pair distances) on the same workload, for comparison
+    fp32_ms = None
+    if args.precision != 0 and not args.no_fp32_compare:
+        path.precision = 0
+        path.step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(max(1, args.steps)):
+            path.step()
+        b.record()
+        torch.cuda.synchronize()
+        fp32_ms = a.elapsed_time(b) / max(1, args.steps)
+        path.precision = args.precision
+
     # e2e through the one-call API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -308,7 +335,7 @@ def run_gpu(args):
         def e2e_step():
             Xdev.copy_(Xpin, non_blocking=True)
             gkm.build_knn_graph(Xdev, w.kappa, w.xi, w.tau, w.max_cluster, w.seed, labels_out=lab0, g_idx=gi,
-                                g_dist=gd, want_log=False, ws=path.ws)
+                                g_dist=gd, want_log=False, precision=args.precision, ws=path.ws)
             gkm.kmeans_fit(Xdev, w.k, gi, w.iters, seed=w.seed + 1, labels_out=lab, C_out=C, counts_out=cnt,
                            want_log=False, ws=path.ws)
             lab_h.copy_(lab, non_blocking=True)
@@ -377,14 +404,16 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (X is %d MB)" % (Xh.nbytes >> 20),
                    "parallelism": f"replicas x{world}"},
         "fit_s": step_s,
+        "precision": {0: "fp32 simt pair distances", 1: "bf16 tcgen05 gram + exact fp32 rerank"}[args.precision],
+        "plain_fp32_ms_per_step": fp32_ms,
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},
         "per_step_share": {t: round(v / sum(totals.values()), 4) for t, v in totals.items()},
-        "roofline": {"kernel": kernel_of(dom), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": kernel_of(dom, args.precision), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": int(alg),
-                     "traffic": ncu_traffic(dom, w.name)},
-        "gpu_launches": launches_per_step(w) * args.steps,
+                     "traffic": ncu_traffic(dom, w.name, args.precision)},
+        "gpu_launches": launches_per_step(w, args.precision) * args.steps,
         "clocks": ck,
         "device_status": status,
         "e2e": e2e,

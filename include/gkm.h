@@ -72,7 +72,9 @@ typedef struct {
     int32_t max_cluster; /* a cluster larger than this is cut into runs of consecutive
                             members (ascending id) whose sizes differ by at most one    */
     uint64_t seed;       /* seed of the random initial graph and labels (SplitMix64)    */
-    int32_t precision;   /* 0: exact FP32 pair distances                                */
+    int32_t precision;   /* pair distances of the refinement: 0 FP32 on the SIMT cores;
+                            1 BF16 Gram on the tensor cores with an exact FP32 rerank of
+                            every pair inside its error bound (same graph as 0)        */
     int32_t reserved;    /* must be 0                                                   */
 } gk_graph_params;
 
@@ -151,12 +153,19 @@ GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  * into ceil(m / max_cluster) runs of consecutive members whose sizes differ by
  * at most one; every pair (i, j) inside a run is merged into rows i and j, a
  * row keeping its kappa smallest (distance, id) keys with no self and no
- * repeated id.  Pair distances are squared Euclidean in FP32.
+ * repeated id.  Pair distances are squared Euclidean in FP32, summed over
+ * coordinates in ascending order, so a pair has the same bits in every round.
+ *   precision  0: distances on the SIMT cores; 1: a BF16 Gram matrix per run
+ *              on the tensor cores gives d2 = |x|^2 + |y|^2 - 2 x.y, exact when
+ *              the run's centred coordinates are integers of magnitude <= 255
+ *              (and 2 d 255^2 < 2^24), otherwise every pair within a rigorous
+ *              error bound of entering a row is recomputed in FP32 as with 0;
+ *              both settings give the same graph.
  *   g_idx / g_dist  device, n x kappa, in: current graph, out: refined graph
  */
 GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
-                    int32_t kappa, int32_t max_cluster, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
-                    void *stream);
+                           int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist,
+                           void *ws, size_t ws_bytes, void *stream);
 
 /*
  * The three steps the update and the refinement are made of, for callers that
@@ -177,7 +186,8 @@ GK_API int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t l
                                  void *ws, size_t ws_bytes, void *stream);
 GK_API int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                                   const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster,
-                                  int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream);
+                                  int32_t precision, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
+                                  void *stream);
 
 /*
  * KNN-graph construction by repeated fast k-means (Alg. 3): random graph and

@@ -226,8 +226,8 @@ int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
 }
 
 int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
-                    int32_t kappa, int32_t max_cluster, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
-                    void *stream)
+                    int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist, void *ws,
+                    size_t ws_bytes, void *stream)
 {
     int rc;
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
@@ -236,6 +236,8 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
+    if (precision != 0 && precision != 1)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1: tensor-core Gram + FP32 rerank)", precision);
     if (!labels || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -245,7 +247,7 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
     cudaStream_t s = (cudaStream_t)stream;
     GK_CUDA(launch_group(labels, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
     GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist,
-                          L.ref_scratch, L.st, s));
+                          L.ref_scratch, L.st, s, precision));
     return GK_OK;
 }
 
@@ -288,8 +290,8 @@ int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, cons
 }
 
 int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
-                           float *g_dist, void *ws, size_t ws_bytes, void *stream)
+                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t precision,
+                           int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
@@ -298,6 +300,8 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
+    if (precision != 0 && precision != 1)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1: tensor-core Gram + FP32 rerank)", precision);
     if (!offsets || !members || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -305,7 +309,7 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
         return rc;
     L = carve(ws, GK_OP_REFINE, n, d, k);
     GK_CUDA(launch_refine(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch, L.st,
-                          (cudaStream_t)stream));
+                          (cudaStream_t)stream, precision));
     return GK_OK;
 }
 
@@ -366,8 +370,8 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
         return fail(GK_ERR_INVALID, "params is NULL");
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
         return rc;
-    if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 || p->precision != 0 ||
-        p->reserved != 0)
+    if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 ||
+        (p->precision != 0 && p->precision != 1) || p->reserved != 0)
         return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
                     p->max_cluster, p->precision);
     if (!g_idx || !g_dist)
@@ -395,7 +399,7 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
                               L.elog + 2 + 2 * t, L.upd_scratch, s));
         // exhaustive pairs inside the clusters of the new partition
         GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
-                              g_dist, L.ref_scratch, L.st, s));
+                              g_dist, L.ref_scratch, L.st, s, p->precision));
         int32_t *tmp = cur;
         cur = nxt;
         nxt = tmp;

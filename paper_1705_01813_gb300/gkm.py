@@ -68,13 +68,13 @@ def load(build_if_missing: bool = True):
             L.gk_init_graph.argtypes = [P, I64, I64, I64, I32, U64, P, P, P, SZ, P]
             L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, P, SZ, P]
             L.gk_update_step.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P, P, P, SZ, P]
-            L.gk_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, P, P, P, SZ, P]
+            L.gk_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_build_knn_graph.argtypes = [P, I64, I64, I64, ctypes.POINTER(GraphParams), P, P, P, P, P, SZ, P]
             L.gk_kmeans_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, U64, P, P, P, P, P, SZ, P]
             L.gk_read_status.argtypes = [P, P]
             L.gk_group_by_label.argtypes = [P, I64, I32, P, P, P, P, SZ, P]
             L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
-            L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, P, P, P, SZ, P]
+            L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_update_step_noalloc.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
             for name in EXPORTS:
                 if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
@@ -212,8 +212,8 @@ def update_step(X, labels, k: int, C, counts=None, sum_d2=None, offsets=None, me
     return C, counts, sum_d2, offsets, members
 
 
-def graph_refine(X, labels, k: int, g_idx, g_dist, max_cluster: int = 128, ws: Workspace | None = None,
-                 stream=None):
+def graph_refine(X, labels, k: int, g_idx, g_dist, max_cluster: int = 128, precision: int = 0,
+                 ws: Workspace | None = None, stream=None):
     """One refinement of the graph in place (pairs inside each cluster)."""
     n, d, ld = _x(X)
     _dev(labels, torch.int32, "labels")
@@ -221,18 +221,18 @@ def graph_refine(X, labels, k: int, g_idx, g_dist, max_cluster: int = 128, ws: W
     _dev(g_dist, torch.float32, "g_dist")
     kappa = g_idx.shape[1]
     ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, kappa), X.device)
-    _check(load().gk_graph_refine(_ptr(X), n, d, ld, _ptr(labels), k, kappa, max_cluster, _ptr(g_idx),
+    _check(load().gk_graph_refine(_ptr(X), n, d, ld, _ptr(labels), k, kappa, max_cluster, precision, _ptr(g_idx),
                                   _ptr(g_dist), ws.ptr, ws.nbytes, _stream(stream)))
     return g_idx, g_dist
 
 
 def build_knn_graph(X, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int = 128, seed: int = 0,
-                    labels_out=None, g_idx=None, g_dist=None, want_log: bool = True, ws: Workspace | None = None,
-                    stream=None):
+                    labels_out=None, g_idx=None, g_dist=None, want_log: bool = True, precision: int = 0,
+                    ws: Workspace | None = None, stream=None):
     """Alg. 3; returns (g_idx, g_dist, labels at k0, distortion log or None)."""
     n, d, ld = _x(X)
     dev = X.device
-    p = GraphParams(kappa, xi, tau, max_cluster, seed, 0, 0)
+    p = GraphParams(kappa, xi, tau, max_cluster, seed, precision, 0)
     g_idx = torch.empty((n, kappa), dtype=torch.int32, device=dev) if g_idx is None else g_idx
     g_dist = torch.empty((n, kappa), dtype=torch.float32, device=dev) if g_dist is None else g_dist
     labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
@@ -286,13 +286,13 @@ def update_from_groups(X, offsets, members, k: int, C, counts=None, sum_d2=None,
     return C
 
 
-def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster: int = 128,
+def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster: int = 128, precision: int = 0,
                         ws: Workspace | None = None, stream=None):
     """Graph refinement over a CSR grouping, in place on (g_idx, g_dist)."""
     n, d, ld = _x(X)
     ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, g_idx.shape[1]), X.device)
     _check(load().gk_graph_refine_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, g_idx.shape[1],
-                                         max_cluster, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
+                                         max_cluster, precision, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
                                          _stream(stream)))
     return g_idx, g_dist
 

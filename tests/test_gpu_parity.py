@@ -159,52 +159,86 @@ def test_update_integer_data(G):
 
 # ------------------------------------------------------------------ refine
 
-def _refine_case(G, X, k, kappa, cap, seed, exact=False):
+def _refine_case(G, X, k, kappa, cap, seed, exact=False, precision=0):
     n = X.shape[0]
     L = O.init_labels(n, k, seed)
     gi32, gd32 = G.init_graph(_cuda(X), kappa, seed)
     oi, od = O.init_graph(X, kappa, seed)
     ri, rd = O.graph_refine(X, L, k, oi, od, cap)
-    G.graph_refine(_cuda(X), _cuda(L), k, gi32, gd32, cap)
+    G.graph_refine(_cuda(X), _cuda(L), k, gi32, gd32, cap, precision=precision)
     torch.cuda.synchronize()
     gi, gd = _np(gi32), _np(gd32)
     P.row_invariants(X, gi, gd)
-    return P.check_graph(X, gi, gd, ri, rd, exact=exact)
+    return P.check_graph(X, gi, gd, ri, rd, exact=exact), gi, gd
 
 
-@pytest.mark.parametrize("n,d,k,kappa,cap", [
+REFINE_CASES = [
     (20000, 32, 400, 20, 128),   # k0 = n / 50 at the plain-method size
     (5003, 36, 60, 33, 128),     # clusters of ~83
     (6007, 17, 20, 10, 128),     # clusters of ~300 cut into runs
-    (3001, 960, 50, 50, 128),    # GIST-like width
+    (3001, 960, 50, 50, 128),    # GIST-like width (several K chunks on the tensor cores)
     (2000, 8, 3, 16, 500),       # runs longer than one 128-wide tile
     (900, 5, 6, 6, 40),          # small cap, uneven runs
-])
-def test_refine_lockstep(G, n, d, k, kappa, cap):
+    (4001, 100, 90, 12, 128),    # d not a multiple of 16 (zero-padded K)
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n,d,k,kappa,cap", REFINE_CASES)
+def test_refine_lockstep(G, n, d, k, kappa, cap, precision):
     X = _blobs(n, d, 20, n)
-    ex = _refine_case(G, X, k, kappa, cap, seed=d)
+    ex, _, _ = _refine_case(G, X, k, kappa, cap, seed=d, precision=precision)
     # every exempted row was checked to be a near tie; in 960-d the pair distances
     # concentrate (relative spread ~ 1/sqrt(d)), so near ties are more frequent there
     assert ex <= max(3, n // (50 if d > 256 else 500))
 
 
-def test_refine_integer_data_bit_exact(G):
+@pytest.mark.parametrize("n,d,k,kappa,cap", REFINE_CASES)
+def test_refine_tensor_core_path_equals_fp32_path(G, n, d, k, kappa, cap):
+    """The tensor-core Gram with its FP32 rerank gives the FP32 path's graph bit for bit."""
+    X = _blobs(n, d, 20, n)
+    _, gi0, gd0 = _refine_case(G, X, k, kappa, cap, seed=d, precision=0)
+    _, gi1, gd1 = _refine_case(G, X, k, kappa, cap, seed=d, precision=1)
+    assert np.array_equal(gi0, gi1) and np.array_equal(gd0, gd1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_refine_integer_data_bit_exact(G, precision):
     X = datagen.sift_like(20000, 128, 400, seed=5)
-    _refine_case(G, X, 400, 50, 128, seed=9, exact=True)
+    _refine_case(G, X, 400, 50, 128, seed=9, exact=True, precision=precision)
 
 
-def test_exact_knn_special_case(G):
+def test_refine_far_from_origin_rerank(G):
+    """Data far from the origin (large norms, small distances): the Gram distances
+    cancel badly, so correctness rests on the error bound and the FP32 rerank."""
+    X = (_blobs(3000, 64, 30, 8) + 1000.0).astype(np.float32)
+    _, gi0, gd0 = _refine_case(G, X, 60, 16, 128, seed=3, precision=0)
+    ex, gi1, gd1 = _refine_case(G, X, 60, 16, 128, seed=3, precision=1)
+    assert np.array_equal(gi0, gi1) and np.array_equal(gd0, gd1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exact_knn_special_case(G, precision):
     """n < 2 xi gives k0 = 1: one round of Alg. 3 is an exact KNN search."""
     X = _blobs(90, 4, 3, 21)
-    gi, gd, L, log = G.build_knn_graph(_cuda(X), 8, xi=50, tau=1, max_cluster=128, seed=3)
+    gi, gd, L, log = G.build_knn_graph(_cuda(X), 8, xi=50, tau=1, max_cluster=128, seed=3, precision=precision)
     bi, bd = O.brute_knn(X, 8)
     assert (_np(L) == 0).all()
     P.row_invariants(X, _np(gi), _np(gd))
     P.check_graph(X, _np(gi), _np(gd), bi, bd)
     Xs = datagen.sift_like(97, 128, 5, seed=2)
-    gi, gd, _, _ = G.build_knn_graph(_cuda(Xs), 12, xi=50, tau=1, max_cluster=128, seed=4)
+    gi, gd, _, _ = G.build_knn_graph(_cuda(Xs), 12, xi=50, tau=1, max_cluster=128, seed=4, precision=precision)
     bi, bd = O.brute_knn(Xs, 12)
     P.check_graph(Xs, _np(gi), _np(gd), bi, bd, exact=True)
+
+
+def test_build_graph_precisions_identical(G):
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = _cuda(w.data())
+    a = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=0)
+    b = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=1)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    assert a[3] == b[3]
 
 
 # --------------------------------------------------------------- fit / build
