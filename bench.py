@@ -172,7 +172,8 @@ class Path:
         call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt, self.s[0:1], ws=ws)
         cur, nxt = self.la, self.lb
         for _ in range(w.tau):
-            call("assign", g.assign_step, self.X, self.gi, self.C0, cur, nxt, None, self.s[1:2], None, ws=ws)
+            call("assign", g.assign_step, self.X, self.gi, self.C0, cur, nxt, None, self.s[1:2], None,
+                 self.precision, ws=ws)
             call("group", g.group_by_label, nxt, self.k0, self.off, self.mem, self.cnt, ws=ws)
             call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt,
                  self.s[0:1], ws=ws)
@@ -186,7 +187,8 @@ class Path:
         call("group", g.group_by_label, cur, w.k, self.off, self.mem, self.cnt, ws=ws)
         call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3], ws=ws)
         for _ in range(w.iters):
-            call("assign", g.assign_step, self.X, self.gi, self.C, cur, nxt, None, self.s[3:4], None, ws=ws)
+            call("assign", g.assign_step, self.X, self.gi, self.C, cur, nxt, None, self.s[3:4], None,
+                 self.precision, ws=ws)
             call("group", g.group_by_label, nxt, w.k, self.off, self.mem, self.cnt, ws=ws)
             call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3],
                  ws=ws)
@@ -201,7 +203,7 @@ def _radix_passes(k):
 def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
-    upd, asg = 2, 2
+    upd, asg = 2, (3 if precision == 1 else 2)  # assign: (shadow copy,) kernel, finish
     ref = 1 + 3 + (1 if precision == 1 else 2)  # refine: run count, scan, kernels
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
@@ -227,6 +229,8 @@ def algorithmic_bytes(tag, w, k):
 def kernel_of(tag, precision=1):
     if tag == "refine" and precision == 1:
         return "k_refine_tc"
+    if tag == "assign" and precision == 1:
+        return "k_assign_rows_bf"
     return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
             "init_graph": "k_init_graph"}[tag]
 
@@ -337,7 +341,7 @@ def run_gpu(args):
             gkm.build_knn_graph(Xdev, w.kappa, w.xi, w.tau, w.max_cluster, w.seed, labels_out=lab0, g_idx=gi,
                                 g_dist=gd, want_log=False, precision=args.precision, ws=path.ws)
             gkm.kmeans_fit(Xdev, w.k, gi, w.iters, seed=w.seed + 1, labels_out=lab, C_out=C, counts_out=cnt,
-                           want_log=False, ws=path.ws)
+                           want_log=False, precision=args.precision, ws=path.ws)
             lab_h.copy_(lab, non_blocking=True)
             C_h.copy_(C, non_blocking=True)
 
@@ -404,7 +408,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (X is %d MB)" % (Xh.nbytes >> 20),
                    "parallelism": f"replicas x{world}"},
         "fit_s": step_s,
-        "precision": {0: "fp32 simt pair distances", 1: "bf16 tcgen05 gram + exact fp32 rerank"}[args.precision],
+        "precision": {0: "fp32 throughout", 1: "bf16 tcgen05 gram (refine) and bf16 centroid copy (assign), each "
+                                               "with exact fp32 recompute inside its error bound"}[args.precision],
         "plain_fp32_ms_per_step": fp32_ms,
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},

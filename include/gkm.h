@@ -72,9 +72,10 @@ typedef struct {
     int32_t max_cluster; /* a cluster larger than this is cut into runs of consecutive
                             members (ascending id) whose sizes differ by at most one    */
     uint64_t seed;       /* seed of the random initial graph and labels (SplitMix64)    */
-    int32_t precision;   /* pair distances of the refinement: 0 FP32 on the SIMT cores;
-                            1 BF16 Gram on the tensor cores with an exact FP32 rerank of
-                            every pair inside its error bound (same graph as 0)        */
+    int32_t precision;   /* 0: FP32 throughout; 1: refinement pair distances from a BF16
+                            Gram on the tensor cores and assignment candidates against a
+                            BF16 centroid copy, each with an exact FP32 recompute of
+                            everything inside its error bound (same graph as 0)        */
     int32_t reserved;    /* must be 0                                                   */
 } gk_graph_params;
 
@@ -126,10 +127,16 @@ GK_API int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32
  *   sum_d2    device double[1] or NULL: sum of best_d2 (n times the distortion
  *             after the assignment, Eq. 4), computed in FP64
  *   n_changed device int64[1] or NULL: samples whose label changed
+ *   precision 0: candidate distances read the FP32 centroid rows; 1: they are
+ *             first taken against a BF16 copy of the centroids (half the bytes)
+ *             and every candidate within a rigorous error bound of the minimum
+ *             is recomputed against the FP32 rows in the same order as with 0,
+ *             so labels_out, best_d2, sum_d2 and n_changed are identical.
  */
 GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
-                   const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                   double *sum_d2, int64_t *n_changed, void *ws, size_t ws_bytes, void *stream);
+                          const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                          double *sum_d2, int64_t *n_changed, int32_t precision, void *ws, size_t ws_bytes,
+                          void *stream);
 
 /*
  * Centroid update (Sec. 1: each centroid becomes the mean of its members).
@@ -207,13 +214,15 @@ GK_API int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
  * Graph-guided k-means (Alg. 2 with the closest-centroid rule): centroids
  * from the initial labels, then `iters` x { assignment, update }.
  *   init_labels device int32[n] or NULL (NULL: gk_init_labels(seed))
+ *   precision   of the assignment steps, as in gk_assign_step (same results)
  *   labels_out  device int32[n]; C_out device float[k * d]; counts_out device int32[k] or NULL
  *   e_log       HOST double[2 * iters + 1] or NULL, as in gk_build_knn_graph
  *               (non-NULL synchronises the stream)
  */
-GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
-                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
-                  int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx,
+                         int32_t kappa, int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t precision,
+                         int32_t *labels_out, float *C_out, int32_t *counts_out, double *e_log, void *ws,
+                         size_t ws_bytes, void *stream);
 
 /*
  * gk_update_step without a workspace, for callers that cannot allocate device

@@ -104,7 +104,7 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     if (need_update)
         L.upd_scratch = cv.take<char>(update_scratch_bytes(n, k));
     if (need_assign)
-        L.asg_scratch = cv.take<char>(assign_scratch_bytes(n));
+        L.asg_scratch = cv.take<char>(assign_scratch_bytes(n, k, d));
     if (op == GK_OP_REFINE || op == GK_OP_BUILD)
         L.ref_scratch = cv.take<char>(refine_scratch_bytes(k));
     if (op == GK_OP_FIT || op == GK_OP_BUILD) {
@@ -181,7 +181,7 @@ int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kapp
 
 int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                    const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                   double *sum_d2, int64_t *n_changed, void *ws, size_t ws_bytes, void *stream)
+                   double *sum_d2, int64_t *n_changed, int32_t precision, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
@@ -192,12 +192,14 @@ int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
         return fail(GK_ERR_INVALID, "a required array is NULL");
     if (labels_in == labels_out)
         return fail(GK_ERR_INVALID, "labels_out must not alias labels_in");
+    if (precision != 0 && precision != 1)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32 rows, 1: BF16 shadow + exact recompute)", precision);
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_ASSIGN, n, d, k);
     GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
-                          L.asg_scratch, L.st, (cudaStream_t)stream));
+                          L.asg_scratch, L.st, (cudaStream_t)stream, precision));
     return GK_OK;
 }
 
@@ -314,8 +316,8 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
 }
 
 int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
-                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t *labels_out, float *C_out,
-                  int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t precision, int32_t *labels_out,
+                  float *C_out, int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
@@ -324,6 +326,8 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (iters < 0 || 2 * iters + 1 > MAX_LOG)
         return fail(GK_ERR_INVALID, "iters = %d out of range [0, %d]", iters, (MAX_LOG - 1) / 2);
+    if (precision != 0 && precision != 1)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32 rows, 1: BF16 shadow + exact recompute)", precision);
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
@@ -345,7 +349,7 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
     GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
     for (int t = 0; t < iters; t++) {
         GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
-                              L.asg_scratch, L.st, s));
+                              L.asg_scratch, L.st, s, precision));
         GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
                               L.upd_scratch, s));
@@ -393,7 +397,7 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
     for (int t = 0; t < tau; t++) {
         // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
         GK_CUDA(launch_assign(X, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
-                              nullptr, L.asg_scratch, L.st, s));
+                              nullptr, L.asg_scratch, L.st, s, p->precision));
         GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
                               L.elog + 2 + 2 * t, L.upd_scratch, s));

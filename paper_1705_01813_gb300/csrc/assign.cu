@@ -13,6 +13,8 @@
 // run gives the same bits.
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 namespace gkm {
 
 constexpr int AS_WARPS = 8;
@@ -192,6 +194,36 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32])
     return v[0];
 }
 
+__device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
+{
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&v.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Partial (per lane) squared distance of x (registers) to a row of 16-byte
+// vectors, in the accumulation order of k_assign_rows.
+template <int NV, typename RowLoad>
+__device__ __forceinline__ float lane_partial(const float4 (&xv)[NV], int d4, RowLoad load)
+{
+    const int lane = lane_id();
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        const int col = lane + 32 * v;
+        if (col < d4) {
+            const float4 cv = load(col);
+            const float e0 = xv[v].x - cv.x, e1 = xv[v].y - cv.y, e2 = xv[v].z - cv.z, e3 = xv[v].w - cv.w;
+            a0 = fmaf(e0, e0, a0);
+            a1 = fmaf(e1, e1, a1);
+            a0 = fmaf(e2, e2, a0);
+            a1 = fmaf(e3, e3, a1);
+        }
+    }
+    return a0 + a1;
+}
+
 // Coalesced variant for 16-byte rows (d % 4 == 0, d <= 32 * 4 * NV): the warp
 // keeps x_i in registers (lane l owns vectors l, l + 32, ...), reads each
 // candidate centroid row with one coalesced 16-byte load per lane and vector,
@@ -270,21 +302,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__re
                 float acc = 0.f;
                 if (c < cnt) {
                     const float4 *row = C4 + (int64_t)qlist[g0 + c] * d4;
-                    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                    for (int v = 0; v < NV; v++) {
-                        int col = lane + 32 * v;
-                        if (col < d4) {
-                            float4 cv = __ldg(row + col);
-                            float e0 = xv[v].x - cv.x, e1 = xv[v].y - cv.y, e2 = xv[v].z - cv.z,
-                                  e3 = xv[v].w - cv.w;
-                            a0 = fmaf(e0, e0, a0);
-                            a1 = fmaf(e1, e1, a1);
-                            a0 = fmaf(e2, e2, a0);
-                            a1 = fmaf(e3, e3, a1);
-                        }
-                    }
-                    acc = a0 + a1;
+                    acc = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
                 }
                 part[c] = acc;
             }
@@ -294,6 +312,202 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__re
                 if (key_less(tot, r, bd, br)) {
                     bd = tot;
                     br = r;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float od = __shfl_xor_sync(FULL_MASK, bd, o);
+            int orr = __shfl_xor_sync(FULL_MASK, br, o);
+            if (key_less(od, orr, bd, br)) {
+                bd = od;
+                br = orr;
+            }
+        }
+        if (lane == 0) {
+            if (br == 0x7fffffff)  // no valid candidate (own label out of range): keep the input label
+                br = own, bd = 0.f;
+            Lout[i] = br;
+            if (best_out)
+                best_out[i] = bd;
+            wsum += (double)bd;
+            wchg += (br != own) ? 1ull : 0ull;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s_sum[w] = wsum;
+        s_chg[w] = wchg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int q = 0; q < AS_WARPS; q++) {
+            t += s_sum[q];
+            c += s_chg[q];
+        }
+        blk_sum[blockIdx.x] = t;
+        blk_changed[blockIdx.x] = c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BF16 shadow of the centroids: Cb = bf16(C) and delta_r >= ||C_r - Cb_r||.
+// ---------------------------------------------------------------------------
+__global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bfloat16 *__restrict__ Cb,
+                              float *__restrict__ delta)
+{
+    const int lane = lane_id();
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < k; r += gridDim.x * (blockDim.x >> 5)) {
+        double e = 0.0;
+        for (int t = lane; t < d; t += 32) {
+            const float c = C[(int64_t)r * d + t];
+            const __nv_bfloat16 b = __float2bfloat16_rn(c);
+            Cb[(int64_t)r * d + t] = b;
+            const double diff = (double)c - (double)__bfloat162float(b);
+            e += diff * diff;
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            e += __shfl_xor_sync(FULL_MASK, e, o);
+        if (lane == 0)
+            delta[r] = (float)(sqrt(e) * (1.0 + 1e-6)) + 1e-30f;  // rounded up
+    }
+}
+
+// k_assign_rows with the candidate distances first taken against the BF16
+// shadow Cb (half the bytes per candidate row).  With delta_r >= ||C_r - Cb_r||,
+// |D - D~| <= delta_r (2 sqrt(D~) + delta_r) for the exact distances D, D~ to
+// C_r and Cb_r; adding the FP32 rounding of both sums gives a bound E_r, and
+// every candidate whose lower value D~ - E_r does not exceed the smallest upper
+// value D~ + E_r is recomputed against C with the FP32 kernel's order (same
+// lane partials, same reduction tree), so the winner and its distance are the
+// FP32 kernel's bit for bit.
+template <int NV>
+__global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *__restrict__ X, int64_t n, int d,
+                                                                  int64_t ld, const int32_t *__restrict__ G,
+                                                                  int kappa, const float *__restrict__ C,
+                                                                  const __nv_bfloat16 *__restrict__ Cb,
+                                                                  const float *__restrict__ delta, int k,
+                                                                  const int32_t *__restrict__ Lin,
+                                                                  int32_t *__restrict__ Lout,
+                                                                  float *__restrict__ best_out,
+                                                                  double *__restrict__ blk_sum,
+                                                                  unsigned long long *__restrict__ blk_changed,
+                                                                  DevStatus *st)
+{
+    __shared__ int s_q[AS_WARPS][AS_QCAP];
+    __shared__ double s_sum[AS_WARPS];
+    __shared__ unsigned long long s_chg[AS_WARPS];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    int *qlist = s_q[w];
+    const int d4 = d >> 2;
+    const float4 *C4 = reinterpret_cast<const float4 *>(C);
+    const uint2 *Cb4 = reinterpret_cast<const uint2 *>(Cb);  // 4 BF16 per 8 bytes
+    const float gam = (float)(d + 8) * 5.9604645e-8f;         // FP32 rounding of a d-term sum, relative
+
+    double wsum = 0.0;
+    unsigned long long wchg = 0;
+    const int ncand = kappa + 1;
+    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
+        float4 xv[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            int col = lane + 32 * v;
+            xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int own = Lin[i];
+        int u = 0;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            int c = c0 + lane;
+            int lab = -1;
+            if (c == 0) {
+                lab = own;
+            } else if (c < ncand) {
+                int nb = __ldcs(G + i * kappa + (c - 1));
+                if ((unsigned)nb < (unsigned)n)
+                    lab = Lin[nb];
+                else
+                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
+            }
+            if (c < ncand && (unsigned)lab >= (unsigned)k) {
+                flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                lab = -1;
+            }
+            unsigned peers = __match_any_sync(FULL_MASK, lab);
+            bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
+            if (keep)
+                for (int q = 0; q < u; q++)
+                    if (qlist[q] == lab) {
+                        keep = false;
+                        break;
+                    }
+            unsigned keeps = __ballot_sync(FULL_MASK, keep);
+            __syncwarp();
+            if (keep)
+                qlist[u + __popc(keeps & lanemask_lt())] = lab;
+            u += __popc(keeps);
+            __syncwarp();
+        }
+        // pass 1: BF16 distances of every candidate (lane g0 + l holds candidate g0 + l)
+        float lo_v[(AS_QCAP + 31) / 32], up_v[(AS_QCAP + 31) / 32];
+        float best_up = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int gq = 0; gq < (AS_QCAP + 31) / 32; gq++) {
+            const int g0 = gq * 32;
+            lo_v[gq] = up_v[gq] = __int_as_float(0x7f800000);
+            if (g0 < u) {
+                const int cnt = min(32, u - g0);
+                float part[32];
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    float acc = 0.f;
+                    if (c < cnt) {
+                        const uint2 *row = Cb4 + (int64_t)qlist[g0 + c] * d4;
+                        acc = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
+                    }
+                    part[c] = acc;
+                }
+                const float dt = transpose_reduce32(part);
+                if (lane < cnt) {
+                    const float dl = delta[qlist[g0 + lane]];
+                    const float e = 1.01f * (dl * (2.f * sqrtf(dt) + dl) + gam * (2.f * dt + dl * (2.f * sqrtf(dt) + dl)));
+                    lo_v[gq] = dt - e;
+                    up_v[gq] = dt + e;
+                    best_up = fminf(best_up, up_v[gq]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            best_up = fminf(best_up, __shfl_xor_sync(FULL_MASK, best_up, o));
+        // pass 2: the FP32 distances of the candidates that may be the minimum
+        float bd = __int_as_float(0x7f800000);
+        int br = 0x7fffffff;
+#pragma unroll
+        for (int gq = 0; gq < (AS_QCAP + 31) / 32; gq++) {
+            const int g0 = gq * 32;
+            if (g0 < u) {
+                const int cnt = min(32, u - g0);
+                const unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lo_v[gq] <= best_up);
+                float part[32];
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    float acc = 0.f;
+                    if ((sel >> c) & 1u) {
+                        const float4 *row = C4 + (int64_t)qlist[g0 + c] * d4;
+                        acc = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
+                    }
+                    part[c] = acc;
+                }
+                const float tot = transpose_reduce32(part);
+                if ((sel >> lane) & 1u) {
+                    const int r = qlist[g0 + lane];
+                    if (key_less(tot, r, bd, br)) {
+                        bd = tot;
+                        br = r;
+                    }
                 }
             }
         }
@@ -364,24 +578,45 @@ __global__ void __launch_bounds__(1024) k_assign_finish(const double *__restrict
     }
 }
 
-size_t assign_scratch_bytes(int64_t)
+size_t assign_scratch_bytes(int64_t, int32_t k, int64_t d)
 {
-    return ((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255);
+    const size_t part = ((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255);
+    const size_t shadow = (((size_t)k * (size_t)d * 2 + 255) & ~size_t(255)) + (((size_t)k * 4 + 255) & ~size_t(255));
+    return part + shadow;
 }
 
 cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                           const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s)
+                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,
+                          int precision)
 {
     double *blk_sum = static_cast<double *>(scratch);
     unsigned long long *blk_chg = reinterpret_cast<unsigned long long *>(blk_sum + AS_BLOCKS);
+    char *shadow = static_cast<char *>(scratch) +
+                   (((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255));
+    __nv_bfloat16 *Cb = reinterpret_cast<__nv_bfloat16 *>(shadow);
+    float *delta = reinterpret_cast<float *>(shadow + (((size_t)k * (size_t)d * 2 + 255) & ~size_t(255)));
     int dpad = (int)((d + 3) & ~3);
     size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
     bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                 ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     cudaError_t e;
     const int d4 = (int)(d / 4);
-    if (vec4 && d4 <= 32 * 8) {
+    if (precision == 1 && vec4 && d4 <= 32 * 8) {
+        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta);
+#define GK_ASGB(NV)                                                                                              \
+    k_assign_rows_bf<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,      \
+                                                             labels_in, labels_out, best_d2, blk_sum, blk_chg, st)
+        if (d4 <= 32)
+            GK_ASGB(1);
+        else if (d4 <= 64)
+            GK_ASGB(2);
+        else if (d4 <= 128)
+            GK_ASGB(4);
+        else
+            GK_ASGB(8);
+#undef GK_ASGB
+    } else if (vec4 && d4 <= 32 * 8) {
 #define GK_ASG(NV)                                                                                               \
     k_assign_rows<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,      \
                                                           labels_out, best_d2, blk_sum, blk_chg, st)

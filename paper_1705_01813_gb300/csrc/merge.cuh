@@ -21,33 +21,61 @@ __device__ __forceinline__ int lower_rank(const float *v, const int *id, int len
     return lo;
 }
 
+// A graph row's kappa keys held in registers (lane l owns entries l, l + 32,
+// l + 64, l + 96), so that the next row's list can be loaded while the
+// current row is merged.
+struct RowRegs {
+    int id[4];
+    float dv[4];
+};
+
+__device__ __forceinline__ void load_row(RowRegs &r, const int32_t *__restrict__ gi, const float *__restrict__ gd,
+                                         int kappa)
+{
+    const int lane = lane_id();
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int q = lane + 32 * u;
+        if (q < kappa) {
+            r.id[u] = __ldcg(gi + q);
+            r.dv[u] = __ldcg(gd + q);
+        }
+    }
+}
+
 // Merge the candidates (ids cid[0..ncol), ascending; distances drow[0..ncol))
-// into graph row i (kappa sorted keys at gi / gd).  Warp-cooperative.
-// Candidates already in the row are found by a binary search of each row id
-// among the (sorted) candidate ids and masked out; the others that beat the
-// row's kappa-th key are ranked among themselves and placed by rank.
-__device__ __forceinline__ void merge_row(int i, const int *__restrict__ cid, const float *__restrict__ drow, int ncol, int kappa,
-                          int32_t *__restrict__ gi, float *__restrict__ gd, int *li, float *lv, int *bi, float *bv,
-                          int *ni, float *nv, unsigned *dup)
+// into graph row i, whose current kappa sorted keys are in `cur`; the merged
+// row is written to gi / gd when it changes.  Warp-cooperative.  Candidates
+// already in the row are found by a binary search of each row id among the
+// (sorted) candidate ids and masked out; the others that beat the row's
+// kappa-th key are ranked among themselves and placed by rank.
+__device__ __forceinline__ void merge_row(int i, const int *__restrict__ cid, const float *__restrict__ drow,
+                                          int ncol, int kappa, const RowRegs &cur, int32_t *__restrict__ gi,
+                                          float *__restrict__ gd, int *li, float *lv, int *bi, float *bv, int *ni,
+                                          float *nv, unsigned *dup)
 {
     const int lane = lane_id();
     if (lane < 4)
         dup[lane] = 0u;
     __syncwarp();
-    for (int q = lane; q < kappa; q += 32) {
-        const int j = gi[q];
-        li[q] = j;
-        lv[q] = gd[q];
-        int lo = 0, hi = ncol;  // first candidate id >= j
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (cid[mid] < j)
-                lo = mid + 1;
-            else
-                hi = mid;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int q = lane + 32 * u;
+        if (q < kappa) {
+            const int j = cur.id[u];
+            li[q] = j;
+            lv[q] = cur.dv[u];
+            int lo = 0, hi = ncol;  // first candidate id >= j
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (cid[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo < ncol && cid[lo] == j)
+                atomicOr(&dup[lo >> 5], 1u << (lo & 31));
         }
-        if (lo < ncol && cid[lo] == j)
-            atomicOr(&dup[lo >> 5], 1u << (lo & 31));
     }
     __syncwarp();
     const float td = lv[kappa - 1];

@@ -58,7 +58,7 @@ __global__ void k_count_runs(const int32_t *__restrict__ off, int k, int cap, in
 }
 
 template <int T>
-__global__ void __launch_bounds__(RF_THREADS) k_refine(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+__global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const float *__restrict__ X, int64_t n, int d, int64_t ld,
                                                        const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ mem,
                                                        const int32_t *__restrict__ run_off, int k, int kappa,
@@ -177,12 +177,18 @@ __global__ void __launch_bounds__(RF_THREADS) k_refine(const float *__restrict__
                     for (int b = 0; b < Q; b++)
                         dt[(ty + 16 * a) * DS + tx + 16 * b] = acc[a][b];
                 __syncthreads();
+                RowRegs cur, nxt;
+                if (w < nr && rid[w] >= 0)
+                    load_row(cur, g_idx + (int64_t)rid[w] * kappa, g_dist + (int64_t)rid[w] * kappa, kappa);
                 for (int row = w; row < nr; row += RF_WARPS) {
-                    int i = rid[row];
-                    if (i < 0)
-                        continue;
-                    merge_row(i, cid, dt + row * DS, ncl, kappa, g_idx + (int64_t)i * kappa,
-                              g_dist + (int64_t)i * kappa, li, lv, bi, bv, ni, nv, dup);
+                    const int i = rid[row];
+                    const int rn = row + RF_WARPS;
+                    if (rn < nr && rid[rn] >= 0)  // next row's list in flight during this merge
+                        load_row(nxt, g_idx + (int64_t)rid[rn] * kappa, g_dist + (int64_t)rid[rn] * kappa, kappa);
+                    if (i >= 0)
+                        merge_row(i, cid, dt + row * DS, ncl, kappa, cur, g_idx + (int64_t)i * kappa,
+                                  g_dist + (int64_t)i * kappa, li, lv, bi, bv, ni, nv, dup);
+                    cur = nxt;
                 }
             }
         }

@@ -2,12 +2,13 @@
 // taken from a Gram matrix computed on the tensor cores (tcgen05, BF16 inputs,
 // FP32 accumulation in tensor memory), and the same results as the FP32 path.
 //
-// One CTA (4 warps) per run of <= 128 members.  The run's rows, centred on the
+// One CTA (8 warps) per run of <= 128 members.  The run's rows, centred on the
 // run's first member, are converted to BF16 and staged in shared memory in the
 // 128-byte swizzle layout (two 64-column K-blocks at a time); one thread issues
 // the 128 x N x 16 MMAs of G = X' X'^T into tensor memory and commits them to
-// an mbarrier.  Each warp then reads its 32 TMEM lanes (one row of G per
-// thread) and forms d2(i, j) = n_i + n_j - 2 G_ij with n_i = ||x_i'||^2.
+// an mbarrier.  Warps w and w + 4 then read TMEM lanes 32 (w % 4) .. + 31 (one
+// row of G per thread, half of the columns each) and form
+// d2(i, j) = n_i + n_j - 2 G_ij with n_i = ||x_i'||^2.
 //
 // Exactness: when every centred coordinate of the run is an integer of
 // magnitude <= 255 and 2 d 255^2 < 2^24, every BF16 value, product and partial
@@ -27,7 +28,7 @@
 
 namespace gkm {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr int TC_M = 128;              // rows of the tile (TMEM lanes)
 constexpr int TC_KB = 64;              // BF16 elements per K-block (one 128-byte swizzle row)
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
     const int kchunk = TC_KCH * TC_KB;
     for (int k0 = 0; k0 < d; k0 += kchunk) {
-        // stage rows: warp w handles rows w, w + 4, ...; lane l covers 4 consecutive coordinates
+        // stage rows: warp w handles rows w, w + 8, ...; lane l covers 4 consecutive coordinates
+#pragma unroll 4
         for (int row = w; row < TC_M; row += TC_WARPS) {
             const int a = rid[row];
             float part = 0.f;
@@ -207,11 +209,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
 
     // ---- distances from the Gram matrix into the tile ----
     if (!timed_out) {
-        const int i = 32 * w + lane;
+        const int quad = w & 3, half = w >> 2;
+        const int i = 32 * quad + lane;
         const float ni_ = nrm[i];
-        for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c0 = 64 * half; c0 < min(N, 64 * half + 64); c0 += 32) {
             float g[32];
-            tc::tmem_ld32(taddr + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, g);
+            tc::tmem_ld32(taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, g);
             tc::tmem_ld_wait();
             if (i < sz) {
 #pragma unroll
@@ -231,13 +234,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
         const float u = 1.0f / 256.0f;
         const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
         const float c2 = 1.02f * (d + 8) * 1.1920929e-7f;
+        RowRegs cur, nxt;
+        if (w < sz && rid[w] >= 0)
+            load_row(cur, g_idx + (int64_t)rid[w] * kappa, g_dist + (int64_t)rid[w] * kappa, kappa);
         for (int row = w; row < sz; row += TC_WARPS) {
             const int i = rid[row];
-            if (i < 0)
+            const int rn = row + TC_WARPS;
+            if (rn < sz && rid[rn] >= 0)  // next row's list in flight during this merge
+                load_row(nxt, g_idx + (int64_t)rid[rn] * kappa, g_dist + (int64_t)rid[rn] * kappa, kappa);
+            if (i < 0) {
+                cur = nxt;
                 continue;
+            }
             float *drow = dt + row * TC_DS;
             if (!exact) {
-                const float th = __ldg(g_dist + (int64_t)i * kappa + kappa - 1);
+                const int uq = (kappa - 1) >> 5;
+                const float src = uq == 0 ? cur.dv[0] : uq == 1 ? cur.dv[1] : uq == 2 ? cur.dv[2] : cur.dv[3];
+                const float th = __shfl_sync(FULL_MASK, src, (kappa - 1) & 31);
                 const float nr_i = nrm[row];
                 const float *xi = X + (int64_t)i * ld;
                 for (int cc = lane; cc < sz; cc += 32) {
@@ -252,8 +265,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
                 }
                 __syncwarp();
             }
-            merge_row(i, rid, drow, sz, kappa, g_idx + (int64_t)i * kappa, g_dist + (int64_t)i * kappa, li, lv, bi,
-                      bv, ni, nv, dup);
+            merge_row(i, rid, drow, sz, kappa, cur, g_idx + (int64_t)i * kappa, g_dist + (int64_t)i * kappa, li,
+                      lv, bi, bv, ni, nv, dup);
+            cur = nxt;
         }
     }
     tc::fence_before_sync();

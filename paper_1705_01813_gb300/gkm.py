@@ -66,11 +66,11 @@ def load(build_if_missing: bool = True):
             L.gk_workspace_size_build.argtypes = [I64, I64, ctypes.POINTER(GraphParams)]
             L.gk_init_labels.argtypes = [I64, I32, U64, P, P]
             L.gk_init_graph.argtypes = [P, I64, I64, I64, I32, U64, P, P, P, SZ, P]
-            L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, P, SZ, P]
+            L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, I32, P, SZ, P]
             L.gk_update_step.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P, P, P, SZ, P]
             L.gk_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_build_knn_graph.argtypes = [P, I64, I64, I64, ctypes.POINTER(GraphParams), P, P, P, P, P, SZ, P]
-            L.gk_kmeans_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, U64, P, P, P, P, P, SZ, P]
+            L.gk_kmeans_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, U64, I32, P, P, P, P, P, SZ, P]
             L.gk_read_status.argtypes = [P, P]
             L.gk_group_by_label.argtypes = [P, I64, I32, P, P, P, P, SZ, P]
             L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
@@ -173,7 +173,7 @@ ALLOC = "alloc"
 
 
 def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=ALLOC, n_changed=ALLOC,
-                ws: Workspace | None = None, stream=None):
+                precision: int = 0, ws: Workspace | None = None, stream=None):
     """Graph-guided assignment; returns (labels_out, best_d2, sum_d2, n_changed).
 
     The optional outputs are allocated by default; pass a tensor to reuse it or
@@ -190,8 +190,8 @@ def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=A
     n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is ALLOC else n_changed
     ws = ws or workspace(workspace_size(GK_OP_ASSIGN, n, d, k, kappa), dev)
     _check(load().gk_assign_step(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
-                                 _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), ws.ptr, ws.nbytes,
-                                 _stream(stream)))
+                                 _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), precision, ws.ptr,
+                                 ws.nbytes, _stream(stream)))
     return labels_out, best_d2, sum_d2, n_changed
 
 
@@ -244,7 +244,8 @@ def build_knn_graph(X, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int
 
 
 def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, labels_out=None, C_out=None,
-               counts_out=None, want_log: bool = True, ws: Workspace | None = None, stream=None):
+               counts_out=None, want_log: bool = True, precision: int = 0, ws: Workspace | None = None,
+               stream=None):
     """Graph-guided k-means; returns (labels, centroids, counts, distortion log or None)."""
     n, d, ld = _x(X)
     dev = X.device
@@ -256,7 +257,7 @@ def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, la
     log = (ctypes.c_double * (2 * iters + 1))() if want_log else None
     ws = ws or workspace(workspace_size(GK_OP_FIT, n, d, k, kappa), dev)
     _check(load().gk_kmeans_fit(_ptr(X), n, d, ld, k, _ptr(g_idx), kappa, iters, _ptr(init_labels), seed,
-                                _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
+                                precision, _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return labels_out, C_out, counts_out, (list(log) if want_log else None)
 

@@ -72,7 +72,7 @@ def test_init_graph_integer_data_exact(G):
 
 # ------------------------------------------------------------------ assign
 
-def _assign_case(G, X, kappa, k, seed, graph="knn"):
+def _assign_case(G, X, kappa, k, seed, graph="knn", precision=0):
     n = X.shape[0]
     if graph == "knn":
         gi, _ = O.brute_knn(X, kappa) if n * n * X.shape[1] <= 2e9 else O.init_graph(X, kappa, seed)
@@ -82,7 +82,7 @@ def _assign_case(G, X, kappa, k, seed, graph="knn"):
     C64, cnt, _, _ = O.update(X, L, k)
     C32 = C64.astype(np.float32)
     Lo, best, uq = O.assign(X, gi, C32.astype(np.float64), L)
-    lo, bd, s, ch = G.assign_step(_cuda(X), _cuda(gi), _cuda(C32), _cuda(L))
+    lo, bd, s, ch = G.assign_step(_cuda(X), _cuda(gi), _cuda(C32), _cuda(L), precision=precision)
     torch.cuda.synchronize()
     ex = P.check_labels(X, C32, _np(lo), Lo, best)
     # winning distances, their FP64 sum and the changed count
@@ -102,10 +102,34 @@ def _assign_case(G, X, kappa, k, seed, graph="knn"):
     (1500, 1, 5, 3),          # d = 1
     (700, 16, 3, 128),        # kappa at its maximum, many repeated labels
 ])
-def test_assign_lockstep(G, n, d, k, kappa):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_assign_lockstep(G, n, d, k, kappa, precision):
     X = _blobs(n, d, max(2, k // 2), n + d)
-    ex = _assign_case(G, X, kappa, k, seed=n)
+    ex = _assign_case(G, X, kappa, k, seed=n, precision=precision)
     assert ex <= max(2, n // 1000)
+
+
+@pytest.mark.parametrize("data", ["blobs", "far", "sift", "gist"])
+def test_assign_bf16_shadow_equals_fp32(G, data):
+    """Candidates against the BF16 centroid copy, with the exact recompute inside the
+    error bound, give the FP32 kernel's labels, distances, sum and count bit for bit."""
+    if data == "blobs":
+        X = _blobs(20000, 64, 100, 1)
+    elif data == "far":
+        X = (_blobs(20000, 64, 100, 2) + 500.0).astype(np.float32)
+    elif data == "sift":
+        X = datagen.sift_like(20000, 128, 500, seed=3)
+    else:
+        X = datagen.gist_like(6000, 960, 100, seed=4)
+    n, k = X.shape[0], 200
+    gi, _ = O.init_graph(X, 30, 5)
+    L = O.init_labels(n, k, 6)
+    C64, _, _, _ = O.update(X, L, k)
+    Xd, gd, Cd, Ld = _cuda(X), _cuda(gi), _cuda(C64.astype(np.float32)), _cuda(L)
+    a = G.assign_step(Xd, gd, Cd, Ld, precision=0)
+    b = G.assign_step(Xd, gd, Cd, Ld, precision=1)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
 
 
 def test_assign_complete_graph_is_lloyd(G):
@@ -230,6 +254,16 @@ def test_exact_knn_special_case(G, precision):
     gi, gd, _, _ = G.build_knn_graph(_cuda(Xs), 12, xi=50, tau=1, max_cluster=128, seed=4, precision=precision)
     bi, bd = O.brute_knn(Xs, 12)
     P.check_graph(Xs, _np(gi), _np(gd), bi, bd, exact=True)
+
+
+def test_fit_precisions_identical(G):
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = _cuda(w.data())
+    gi, _, _, _ = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=4, seed=w.seed)
+    L0 = G.init_labels(w.n, w.k, 9)
+    a = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=0)
+    b = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=1)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]) and a[3] == b[3]
 
 
 def test_build_graph_precisions_identical(G):
