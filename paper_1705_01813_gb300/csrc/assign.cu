@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
                                                                   DevStatus *st)
 {
     __shared__ int s_q[AS_WARPS][AS_QCAP];
+    __shared__ float s_lo[AS_WARPS][AS_QCAP + 31];
     __shared__ double s_sum[AS_WARPS];
     __shared__ unsigned long long s_chg[AS_WARPS];
     const int w = threadIdx.x >> 5, lane = lane_id();
@@ -450,64 +451,56 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
             u += __popc(keeps);
             __syncwarp();
         }
-        // pass 1: BF16 distances of every candidate (lane g0 + l holds candidate g0 + l)
-        float lo_v[(AS_QCAP + 31) / 32], up_v[(AS_QCAP + 31) / 32];
+        // pass 1: BF16 distances of every candidate (lane l holds candidate g0 + l of each group)
+        float *lov = s_lo[w];
         float best_up = __int_as_float(0x7f800000);
+#pragma unroll 1
+        for (int g0 = 0; g0 < u; g0 += 32) {
+            const int cnt = min(32, u - g0);
+            float part[32];
 #pragma unroll
-        for (int gq = 0; gq < (AS_QCAP + 31) / 32; gq++) {
-            const int g0 = gq * 32;
-            lo_v[gq] = up_v[gq] = __int_as_float(0x7f800000);
-            if (g0 < u) {
-                const int cnt = min(32, u - g0);
-                float part[32];
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    float acc = 0.f;
-                    if (c < cnt) {
-                        const uint2 *row = Cb4 + (int64_t)qlist[g0 + c] * d4;
-                        acc = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
-                    }
-                    part[c] = acc;
+            for (int c = 0; c < 32; c++) {
+                float acc = 0.f;
+                if (c < cnt) {
+                    const uint2 *row = Cb4 + (int64_t)qlist[g0 + c] * d4;
+                    acc = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
                 }
-                const float dt = transpose_reduce32(part);
-                if (lane < cnt) {
-                    const float dl = delta[qlist[g0 + lane]];
-                    const float e = 1.01f * (dl * (2.f * sqrtf(dt) + dl) + gam * (2.f * dt + dl * (2.f * sqrtf(dt) + dl)));
-                    lo_v[gq] = dt - e;
-                    up_v[gq] = dt + e;
-                    best_up = fminf(best_up, up_v[gq]);
-                }
+                part[c] = acc;
+            }
+            const float dt = transpose_reduce32(part);
+            if (lane < cnt) {
+                const float dl = delta[qlist[g0 + lane]];
+                const float sq = sqrtf(fmaxf(dt, 0.f));
+                const float e = 1.01f * (dl * (2.f * sq + dl) + gam * (2.f * dt + dl * (2.f * sq + dl)));
+                lov[g0 + lane] = dt - e;
+                best_up = fminf(best_up, dt + e);
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             best_up = fminf(best_up, __shfl_xor_sync(FULL_MASK, best_up, o));
-        // pass 2: the FP32 distances of the candidates that may be the minimum
+        __syncwarp();
+        // pass 2: FP32 distances of the candidates that may be the minimum, one at a
+        // time; the xor butterfly groups the lane partials as transpose_reduce32 does,
+        // so each total has the bits of the FP32 kernel
         float bd = __int_as_float(0x7f800000);
         int br = 0x7fffffff;
+#pragma unroll 1
+        for (int g0 = 0; g0 < u; g0 += 32) {
+            const int cnt = min(32, u - g0);
+            unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lov[g0 + lane] <= best_up);
+            while (sel) {
+                const int c = __ffs(sel) - 1;
+                sel &= sel - 1;
+                const int r = qlist[g0 + c];
+                const float4 *row = C4 + (int64_t)r * d4;
+                float tot = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
 #pragma unroll
-        for (int gq = 0; gq < (AS_QCAP + 31) / 32; gq++) {
-            const int g0 = gq * 32;
-            if (g0 < u) {
-                const int cnt = min(32, u - g0);
-                const unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lo_v[gq] <= best_up);
-                float part[32];
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    float acc = 0.f;
-                    if ((sel >> c) & 1u) {
-                        const float4 *row = C4 + (int64_t)qlist[g0 + c] * d4;
-                        acc = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
-                    }
-                    part[c] = acc;
-                }
-                const float tot = transpose_reduce32(part);
-                if ((sel >> lane) & 1u) {
-                    const int r = qlist[g0 + lane];
-                    if (key_less(tot, r, bd, br)) {
-                        bd = tot;
-                        br = r;
-                    }
+                for (int o = 16; o > 0; o >>= 1)
+                    tot += __shfl_xor_sync(FULL_MASK, tot, o);
+                if (key_less(tot, r, bd, br)) {
+                    bd = tot;
+                    br = r;
                 }
             }
         }

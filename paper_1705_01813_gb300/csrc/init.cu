@@ -28,6 +28,19 @@ cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *lab
 // first kappa - got kept draws are used, which is exactly the sequential
 // rejection rule.  Each lane then computes the FP32 distance of one neighbour
 // (pair_d2_seq), and the row is sorted by (distance, id) by ranking.
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), and the wait for all of them.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 constexpr int IG_WARPS = 4;
 constexpr int IG_DC = 128;  // coordinates staged per step (vector path)
 
@@ -90,13 +103,13 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
                     __syncwarp();
                     for (int t = lane * 4; t < dc; t += 128)
                         *reinterpret_cast<float4 *>(xs + t) = *reinterpret_cast<const float4 *>(xi + t0 + t);
-#pragma unroll 8
+                    // every row of the batch in flight at once (asynchronous copies to shared memory)
                     for (int q = 0; q < nb; q++) {
                         const float *src = X + (int64_t)ridx[b0 + q] * ld + t0;
                         for (int t = lane * 4; t < dc; t += 128)
-                            *reinterpret_cast<float4 *>(rows + q * (IG_DC + 4) + t) =
-                                __ldg(reinterpret_cast<const float4 *>(src + t));
+                            cp_async16(rows + q * (IG_DC + 4) + t, src + t);
                     }
+                    cp_async_wait_all();
                     __syncwarp();
                     if (lane < nb) {
                         const float *myrow = rows + lane * (IG_DC + 4);

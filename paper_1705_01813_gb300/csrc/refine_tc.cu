@@ -28,57 +28,68 @@
 
 namespace gkm {
 
-constexpr int TC_THREADS = 256;
-constexpr int TC_WARPS = TC_THREADS / 32;
-constexpr int TC_M = 128;              // rows of the tile (TMEM lanes)
+constexpr int TC_M = 128;              // rows of the MMA tile (TMEM lanes)
 constexpr int TC_KB = 64;              // BF16 elements per K-block (one 128-byte swizzle row)
 constexpr int TC_KCH = 2;              // K-blocks staged per chunk
 constexpr int TC_KB_BYTES = TC_M * 128;  // 16 KB per K-block
-constexpr int TC_DS = TC_M + 1;        // stride of the distance tile (floats)
 constexpr uint32_t TC_WAIT_ITERS = 1u << 22;
 
-struct TcLayout {
+// TN: widest run handled (64 or 128).  The 64-wide instance uses 4 warps, a
+// 64-column TMEM accumulator and a 64 x 65 distance tile, so more CTAs fit on
+// an SM; the 128-wide one 8 warps and 128 columns.
+template <int TN>
+struct TcCfg {
+    static constexpr int THREADS = TN == 64 ? 128 : 256;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int DS = TN + 1;  // stride of the distance tile (floats)
     // the staging area (K-blocks) and the distance tile share one region
-    static constexpr size_t region = (size_t)TC_KCH * TC_KB_BYTES > sizeof(float) * TC_M * TC_DS
+    static constexpr size_t region = (size_t)TC_KCH * TC_KB_BYTES > sizeof(float) * TN * DS
                                          ? (size_t)TC_KCH * TC_KB_BYTES
-                                         : sizeof(float) * TC_M * TC_DS;
+                                         : sizeof(float) * TN * DS;
     static constexpr size_t fixed = region + sizeof(float) * TC_M /*norms*/ + sizeof(int) * TC_M /*ids*/ +
                                     64 /*barrier, tmem slot, flags*/;
     __host__ __device__ static size_t warp_bytes(int kappa)
     {
-        return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + TC_M) + 4 * sizeof(unsigned);
+        return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + TN) + 4 * sizeof(unsigned);
     }
-    __host__ __device__ static size_t bytes(int kappa) { return 1024 /*alignment slack*/ + fixed + TC_WARPS * warp_bytes(kappa); }
+    __host__ __device__ static size_t bytes(int kappa)
+    {
+        return 1024 /*alignment slack*/ + fixed + WARPS * warp_bytes(kappa);
+    }
 };
 
-__global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+template <int TN>
+__global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *__restrict__ X, int64_t n, int d,
+                                                                  int64_t ld,
                                                           const int32_t *__restrict__ off,
                                                           const int32_t *__restrict__ mem,
                                                           const int32_t *__restrict__ run_off, int k, int kappa,
                                                           int cap, bool vec4, int32_t *__restrict__ g_idx,
                                                           float *__restrict__ g_dist, DevStatus *st)
 {
+    using CF = TcCfg<TN>;
+    constexpr int TC_THREADS = CF::THREADS, TC_WARPS = CF::WARPS, TC_DS = CF::DS;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *stage = base;                                   // K-blocks, 1024-aligned
     float *dt = reinterpret_cast<float *>(base);                   // distance tile (after the MMAs)
-    float *nrm = reinterpret_cast<float *>(base + TcLayout::region);
+    float *nrm = reinterpret_cast<float *>(base + CF::region);
     int *rid = reinterpret_cast<int *>(nrm + TC_M);
     uint64_t *bar = reinterpret_cast<uint64_t *>(rid + TC_M);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *flags = reinterpret_cast<int *>(tslot + 1);              // [0] not exact, [1] timeout
-    unsigned char *wb = base + TcLayout::fixed;
+    unsigned char *wb = base + CF::fixed;
 
     const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
-    unsigned char *wbase = wb + w * TcLayout::warp_bytes(kappa);
+    unsigned char *wbase = wb + w * CF::warp_bytes(kappa);
     int *li = reinterpret_cast<int *>(wbase);
     float *lv = reinterpret_cast<float *>(li + kappa);
     int *ni = reinterpret_cast<int *>(lv + kappa);
     float *nv = reinterpret_cast<float *>(ni + kappa);
     int *bi = reinterpret_cast<int *>(nv + kappa);
-    float *bv = reinterpret_cast<float *>(bi + TC_M);
-    unsigned *dup = reinterpret_cast<unsigned *>(bv + TC_M);
+    float *bv = reinterpret_cast<float *>(bi + TN);
+    unsigned *dup = reinterpret_cast<unsigned *>(bv + TN);
 
     // this block's run (as in the FP32 kernel)
     const int run = blockIdx.x;
@@ -97,13 +108,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
     const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
     const int c = run - run_off[r];
     const int s0 = c * rbase + min(c, rem), sz = rbase + (c < rem ? 1 : 0);
-    if (sz < 2 || sz > TC_M)  // runs longer than one tile are handled by the FP32 kernel
+    // the 64-wide instance takes runs of <= 64 members, the 128-wide one runs of 65..128;
+    // longer runs (max_cluster > 128) are handled by the FP32 kernel
+    if (sz < 2 || sz > TN || (TN == 128 && sz <= 64))
         return;
     const int32_t *S = mem + beg + s0;
     const int N = (sz + 15) & ~15;
 
     if (w == 0) {
-        tc::tmem_alloc(tslot, TC_M);
+        tc::tmem_alloc(tslot, TN);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
     for (int k0 = 0; k0 < d; k0 += kchunk) {
         // stage rows: warp w handles rows w, w + 8, ...; lane l covers 4 consecutive coordinates
 #pragma unroll 4
-        for (int row = w; row < TC_M; row += TC_WARPS) {
+        for (int row = w; row < TN; row += TC_WARPS) {
             const int a = rid[row];
             float part = 0.f;
             for (int kk = lane * 4; kk < kchunk; kk += 128) {
@@ -208,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
     const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
 
     // ---- distances from the Gram matrix into the tile ----
-    if (!timed_out) {
+    if (!timed_out && 32 * (w & 3) < TN) {
         const int quad = w & 3, half = w >> 2;
         const int i = 32 * quad + lane;
         const float ni_ = nrm[i];
@@ -273,23 +286,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_tc(const float *__restric
     tc::fence_before_sync();
     __syncthreads();
     if (w == 0)
-        tc::tmem_dealloc(taddr, TC_M);
+        tc::tmem_dealloc(taddr, TN);
 }
-
-size_t refine_tc_smem_bytes(int32_t kappa) { return TcLayout::bytes(kappa); }
 
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, int32_t k, int32_t kappa,
                              int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, DevStatus *st,
                              cudaStream_t s)
 {
-    const size_t shm = TcLayout::bytes(kappa);
-    cudaError_t e = cudaFuncSetAttribute(k_refine_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm64 = TcCfg<64>::bytes(kappa), shm128 = TcCfg<128>::bytes(kappa);
+    cudaError_t e = cudaFuncSetAttribute(k_refine_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64);
     if (e != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute(k_refine_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm128)) !=
+        cudaSuccess)
+        return e;
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    k_refine_tc<<<(unsigned)grid, TC_THREADS, shm, s>>>(X, n, (int)d, ld, offsets, members, run_off, k, kappa,
-                                                        max_cluster, vec4, g_idx, g_dist, st);
+    k_refine_tc<64><<<(unsigned)grid, TcCfg<64>::THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, k,
+                                                                      kappa, max_cluster, vec4, g_idx, g_dist, st);
+    k_refine_tc<128><<<(unsigned)grid, TcCfg<128>::THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
+                                                                         k, kappa, max_cluster, vec4, g_idx, g_dist,
+                                                                         st);
     return cudaGetLastError();
 }
 
