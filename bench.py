@@ -204,7 +204,7 @@ def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
     upd, asg = 2, (3 if precision == 1 else 2)  # assign: (shadow copy,) kernel, finish
-    ref = 1 + 3 + (1 if precision == 1 else 2)  # refine: run count, scan, kernels
+    ref = 1 + 3 + 2  # refine: run count, scan, two kernels (gram + merge, or two tile widths)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit

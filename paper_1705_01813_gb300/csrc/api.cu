@@ -106,7 +106,7 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     if (need_assign)
         L.asg_scratch = cv.take<char>(assign_scratch_bytes(n, k, d));
     if (op == GK_OP_REFINE || op == GK_OP_BUILD)
-        L.ref_scratch = cv.take<char>(refine_scratch_bytes(k));
+        L.ref_scratch = cv.take<char>(refine_scratch_bytes(n, k));
     if (op == GK_OP_FIT || op == GK_OP_BUILD) {
         L.labels_b = cv.take<int32_t>((size_t)n);
         L.elog = cv.take<double>(MAX_LOG);

@@ -141,14 +141,15 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
 
 void set_last_error(const char *msg);
 
-size_t refine_scratch_bytes(int32_t k);
+size_t refine_scratch_bytes(int64_t n, int32_t k);
 // precision 0: FP32 pair distances on the SIMT cores; 1: tensor-core Gram with exact FP32 rerank
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                           float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision);
+size_t refine_tc_scratch_bytes(int64_t n);
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, int32_t k, int32_t kappa,
-                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, DevStatus *st,
-                             cudaStream_t s);
+                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, void *scratch,
+                             DevStatus *st, cudaStream_t s);
 
 }  // namespace gkm

@@ -195,9 +195,11 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
     }
 }
 
-size_t refine_scratch_bytes(int32_t k)
+static size_t run_bytes(int32_t k) { return ((size_t)(2 * (k + 1)) * sizeof(int32_t) + 255) / 256 * 256; }
+
+size_t refine_scratch_bytes(int64_t n, int32_t k)
 {
-    return ((size_t)(2 * (k + 1)) * sizeof(int32_t) + 255) / 256 * 256 + scan_scratch_bytes(k);
+    return run_bytes(k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n);
 }
 
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
@@ -206,7 +208,8 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
 {
     int32_t *nruns = static_cast<int32_t *>(scratch);
     int32_t *run_off = nruns + (k + 1);
-    void *sc = static_cast<char *>(scratch) + ((size_t)(2 * (k + 1)) * sizeof(int32_t) + 255) / 256 * 256;
+    void *sc = static_cast<char *>(scratch) + run_bytes(k);
+    void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
     cudaError_t e = cudaFuncSetAttribute(k_refine<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64);
     if (e != cudaSuccess)
@@ -222,7 +225,7 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     if (precision == 1) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
         if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, k, kappa, max_cluster, grid, g_idx, g_dist,
-                                  st, s)) != cudaSuccess)
+                                  tc_scratch, st, s)) != cudaSuccess)
             return e;
         if (max_cluster > 128)
             k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, k,

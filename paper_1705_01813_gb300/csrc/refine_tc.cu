@@ -1,25 +1,30 @@
 // Graph refinement inside clusters (Alg. 3) with the pair distances of a run
-// taken from a Gram matrix computed on the tensor cores (tcgen05, BF16 inputs,
-// FP32 accumulation in tensor memory), and the same results as the FP32 path.
+// taken from a Gram matrix on the tensor cores (tcgen05, BF16 inputs, FP32
+// accumulation in tensor memory), and the same graph as the FP32 path.
 //
-// One CTA (8 warps) per run of <= 128 members.  The run's rows, centred on the
-// run's first member, are converted to BF16 and staged in shared memory in the
-// 128-byte swizzle layout (two 64-column K-blocks at a time); one thread issues
-// the 128 x N x 16 MMAs of G = X' X'^T into tensor memory and commits them to
-// an mbarrier.  Warps w and w + 4 then read TMEM lanes 32 (w % 4) .. + 31 (one
-// row of G per thread, half of the columns each) and form
-// d2(i, j) = n_i + n_j - 2 G_ij with n_i = ||x_i'||^2.
+// Two kernels per refinement:
 //
+// k_refine_gram, one CTA (4 warps) per run of <= 128 members.  The run's rows,
+// centred on the run's first member, are converted to BF16 and staged in
+// shared memory in the 128-byte swizzle layout (two 64-column K-blocks at a
+// time); one thread issues the 128 x N x 16 MMAs of G = X' X'^T into tensor
+// memory and commits them to an mbarrier.  Thread t then owns TMEM lane t,
+// i.e. row t of G, forms d2(t, j) = n_t + n_j - 2 G_tj (n = squared norms of
+// the centred rows) and appends to its graph row's candidate list every j
+// that may enter the row: key (d2, id_j) below the row's kappa-th key.
 // Exactness: when every centred coordinate of the run is an integer of
 // magnitude <= 255 and 2 d 255^2 < 2^24, every BF16 value, product and partial
 // sum is an exact integer below 2^24, so d2 equals the FP32 sum of squared
-// differences bit for bit (no rerank).  Otherwise a candidate is kept only if
-// its Gram distance minus a rigorous error bound E_ij beats the row's kappa-th
-// key, and its distance is then recomputed exactly in FP32 in the order of
-// pair_d2_seq; the bound covers the BF16 rounding of both operands
-// ((4u + 2u^2) ||x_i'|| ||x_j'||, u = 2^-8), FP32 accumulation and the final
-// combination, so no pair that would enter the row is dropped.
-// The merge into the graph rows is the one of the FP32 path (merge.cuh).
+// differences bit for bit.  Otherwise a pair is kept when d2 - E_tj is not
+// above the kappa-th distance, E_tj being a rigorous bound on the error of the
+// Gram distance (BF16 rounding of both operands, (4u + 2u^2) |x_t'| |x_j'|
+// with u = 2^-8, plus FP32 accumulation and combination), and marked for an
+// exact recompute.
+//
+// k_refine_merge, one warp per graph row that received candidates: marked
+// candidates are recomputed exactly in FP32 in the order of pair_d2_seq, and
+// the candidates are merged into the row as in the FP32 path (merge.cuh).
+// Rows that received nothing are not touched.
 #include "common.cuh"
 #include "merge.cuh"
 #include "tc.cuh"
@@ -28,70 +33,40 @@
 
 namespace gkm {
 
-constexpr int TC_M = 128;              // rows of the MMA tile (TMEM lanes)
-constexpr int TC_KB = 64;              // BF16 elements per K-block (one 128-byte swizzle row)
-constexpr int TC_KCH = 2;              // K-blocks staged per chunk
+constexpr int TC_M = 128;                // rows of the MMA tile (TMEM lanes) and widest run
+constexpr int TC_KB = 64;                // BF16 elements per K-block (one 128-byte swizzle row)
+constexpr int TC_KCH = 2;                // K-blocks staged per chunk
 constexpr int TC_KB_BYTES = TC_M * 128;  // 16 KB per K-block
+constexpr int TC_THREADS = 128;          // one thread per TMEM lane
+constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_CAP = 128;              // candidate slots per graph row
 constexpr uint32_t TC_WAIT_ITERS = 1u << 22;
+constexpr unsigned TC_RERANK = 0x80000000u;  // candidate id flag: distance needs the exact recompute
 
-// TN: widest run handled (64 or 128).  The 64-wide instance uses 4 warps, a
-// 64-column TMEM accumulator and a 64 x 65 distance tile, so more CTAs fit on
-// an SM; the 128-wide one 8 warps and 128 columns.
-template <int TN>
-struct TcCfg {
-    static constexpr int THREADS = TN == 64 ? 128 : 256;
-    static constexpr int WARPS = THREADS / 32;
-    static constexpr int DS = TN + 1;  // stride of the distance tile (floats)
-    // the staging area (K-blocks) and the distance tile share one region
-    static constexpr size_t region = (size_t)TC_KCH * TC_KB_BYTES > sizeof(float) * TN * DS
-                                         ? (size_t)TC_KCH * TC_KB_BYTES
-                                         : sizeof(float) * TN * DS;
-    static constexpr size_t fixed = region + sizeof(float) * TC_M /*norms*/ + sizeof(int) * TC_M /*ids*/ +
-                                    64 /*barrier, tmem slot, flags*/;
-    __host__ __device__ static size_t warp_bytes(int kappa)
-    {
-        return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + TN) + 4 * sizeof(unsigned);
-    }
-    __host__ __device__ static size_t bytes(int kappa)
-    {
-        return 1024 /*alignment slack*/ + fixed + WARPS * warp_bytes(kappa);
-    }
-};
+constexpr size_t TC_STAGE = (size_t)TC_KCH * TC_KB_BYTES;
+constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) * TC_M + sizeof(int) * TC_M + 64;
 
-template <int TN>
-__global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *__restrict__ X, int64_t n, int d,
-                                                                  int64_t ld,
-                                                          const int32_t *__restrict__ off,
-                                                          const int32_t *__restrict__ mem,
-                                                          const int32_t *__restrict__ run_off, int k, int kappa,
-                                                          int cap, bool vec4, int32_t *__restrict__ g_idx,
-                                                          float *__restrict__ g_dist, DevStatus *st)
+__global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restrict__ X, int64_t n, int d,
+                                                            int64_t ld, const int32_t *__restrict__ off,
+                                                            const int32_t *__restrict__ mem,
+                                                            const int32_t *__restrict__ run_off, int k, int kappa,
+                                                            int cap, const int32_t *__restrict__ g_idx,
+                                                            const float *__restrict__ g_dist,
+                                                            int32_t *__restrict__ cand_id,
+                                                            float *__restrict__ cand_d, int32_t *__restrict__ cand_n,
+                                                            DevStatus *st)
 {
-    using CF = TcCfg<TN>;
-    constexpr int TC_THREADS = CF::THREADS, TC_WARPS = CF::WARPS, TC_DS = CF::DS;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(
+    unsigned char *stage = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    unsigned char *stage = base;                                   // K-blocks, 1024-aligned
-    float *dt = reinterpret_cast<float *>(base);                   // distance tile (after the MMAs)
-    float *nrm = reinterpret_cast<float *>(base + CF::region);
+    float *nrm = reinterpret_cast<float *>(stage + TC_STAGE);
     int *rid = reinterpret_cast<int *>(nrm + TC_M);
     uint64_t *bar = reinterpret_cast<uint64_t *>(rid + TC_M);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
-    int *flags = reinterpret_cast<int *>(tslot + 1);              // [0] not exact, [1] timeout
-    unsigned char *wb = base + CF::fixed;
-
+    int *flags = reinterpret_cast<int *>(tslot + 1);  // [0] not exact, [1] timeout
     const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
-    unsigned char *wbase = wb + w * CF::warp_bytes(kappa);
-    int *li = reinterpret_cast<int *>(wbase);
-    float *lv = reinterpret_cast<float *>(li + kappa);
-    int *ni = reinterpret_cast<int *>(lv + kappa);
-    float *nv = reinterpret_cast<float *>(ni + kappa);
-    int *bi = reinterpret_cast<int *>(nv + kappa);
-    float *bv = reinterpret_cast<float *>(bi + TN);
-    unsigned *dup = reinterpret_cast<unsigned *>(bv + TN);
 
-    // this block's run (as in the FP32 kernel)
+    // this block's run: cluster r with run_off[r] <= run < run_off[r + 1]
     const int run = blockIdx.x;
     if (run >= run_off[k])
         return;
@@ -108,15 +83,14 @@ __global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *_
     const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
     const int c = run - run_off[r];
     const int s0 = c * rbase + min(c, rem), sz = rbase + (c < rem ? 1 : 0);
-    // the 64-wide instance takes runs of <= 64 members, the 128-wide one runs of 65..128;
-    // longer runs (max_cluster > 128) are handled by the FP32 kernel
-    if (sz < 2 || sz > TN || (TN == 128 && sz <= 64))
+    if (sz < 2 || sz > TC_M)  // longer runs (max_cluster > 128) go to the FP32 kernel
         return;
     const int32_t *S = mem + beg + s0;
     const int N = (sz + 15) & ~15;
+    const uint32_t ncols = sz <= 32 ? 32u : sz <= 64 ? 64u : 128u;
 
     if (w == 0) {
-        tc::tmem_alloc(tslot, TN);
+        tc::tmem_alloc(tslot, ncols);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -125,13 +99,13 @@ __global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *_
         flags[0] = 0;
         flags[1] = 0;
     }
-    for (int q = tid; q < TC_M; q += TC_THREADS) {
-        int a = q < sz ? S[q] : -1;
+    {
+        int a = tid < sz ? S[tid] : -1;
         if (a >= n) {
             flag_error(st, GK_ERR_INVALID, (unsigned)r);
             a = -1;
         }
-        rid[q] = a;
+        rid[tid] = a;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -139,16 +113,18 @@ __global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *_
     const uint32_t taddr = *tslot;
     const int ref = rid[0] >= 0 ? rid[0] : 0;
     const float *xref = X + (int64_t)ref * ld;
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     // ---- Gram matrix of the centred run, K-chunk by K-chunk ----
     bool inexact = false;
     uint32_t phase = 0;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
     const int kchunk = TC_KCH * TC_KB;
+    const int srows = (sz + 7) & ~7;  // rows staged (the rest of the tile is never read back)
     for (int k0 = 0; k0 < d; k0 += kchunk) {
-        // stage rows: warp w handles rows w, w + 8, ...; lane l covers 4 consecutive coordinates
+        // warp w stages rows w, w + 4, ...; lane l covers 4 consecutive coordinates
 #pragma unroll 4
-        for (int row = w; row < TN; row += TC_WARPS) {
+        for (int row = w; row < srows; row += TC_WARPS) {
             const int a = rid[row];
             float part = 0.f;
             for (int kk = lane * 4; kk < kchunk; kk += 128) {
@@ -220,93 +196,148 @@ __global__ void __launch_bounds__(TcCfg<TN>::THREADS) k_refine_tc(const float *_
     // integer run with |x| <= 255: exact only while 2 d 255^2 < 2^24
     const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
 
-    // ---- distances from the Gram matrix into the tile ----
-    if (!timed_out && 32 * (w & 3) < TN) {
-        const int quad = w & 3, half = w >> 2;
-        const int i = 32 * quad + lane;
-        const float ni_ = nrm[i];
-        for (int c0 = 64 * half; c0 < min(N, 64 * half + 64); c0 += 32) {
-            float g[32];
-            tc::tmem_ld32(taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, g);
-            tc::tmem_ld_wait();
-            if (i < sz) {
-#pragma unroll
-                for (int q = 0; q < 32; q++) {
-                    const int j = c0 + q;
-                    if (j < sz)
-                        dt[i * TC_DS + j] = (ni_ + nrm[j]) - 2.f * g[q];
-                }
-            }
+    // ---- candidates of row tid (TMEM lane tid) ----
+    if (!timed_out && 32 * w < sz) {
+        const int row = tid;
+        const int gi_row = row < sz ? rid[row] : -1;
+        float thd = 0.f;
+        int thi = 0;
+        if (gi_row >= 0) {
+            thd = __ldcg(g_dist + (int64_t)gi_row * kappa + kappa - 1);
+            thi = __ldcg(g_idx + (int64_t)gi_row * kappa + kappa - 1);
         }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-
-    // ---- merge (with an exact FP32 rerank of the pairs inside the error bound) ----
-    if (!timed_out) {
+        const float n_i = nrm[row];
         const float u = 1.0f / 256.0f;
         const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
         const float c2 = 1.02f * (d + 8) * 1.1920929e-7f;
-        RowRegs cur, nxt;
-        if (w < sz && rid[w] >= 0)
-            load_row(cur, g_idx + (int64_t)rid[w] * kappa, g_dist + (int64_t)rid[w] * kappa, kappa);
-        for (int row = w; row < sz; row += TC_WARPS) {
-            const int i = rid[row];
-            const int rn = row + TC_WARPS;
-            if (rn < sz && rid[rn] >= 0)  // next row's list in flight during this merge
-                load_row(nxt, g_idx + (int64_t)rid[rn] * kappa, g_dist + (int64_t)rid[rn] * kappa, kappa);
-            if (i < 0) {
-                cur = nxt;
-                continue;
-            }
-            float *drow = dt + row * TC_DS;
-            if (!exact) {
-                const int uq = (kappa - 1) >> 5;
-                const float src = uq == 0 ? cur.dv[0] : uq == 1 ? cur.dv[1] : uq == 2 ? cur.dv[2] : cur.dv[3];
-                const float th = __shfl_sync(FULL_MASK, src, (kappa - 1) & 31);
-                const float nr_i = nrm[row];
-                const float *xi = X + (int64_t)i * ld;
-                for (int cc = lane; cc < sz; cc += 32) {
-                    const float approx = drow[cc];
-                    const float e = c1 * sqrtf(nr_i * nrm[cc]) + c2 * (nr_i + nrm[cc]);
-                    const int j = rid[cc];
-                    float exact_d = __int_as_float(0x7f800000);
-                    if (j >= 0 && j != i && approx - e <= th)
-                        exact_d = vec4 ? pair_d2_seq4(xi, X + (int64_t)j * ld, d)
-                                       : pair_d2_seq(xi, X + (int64_t)j * ld, d);
-                    drow[cc] = exact_d;
+        int32_t *oid = cand_id + (int64_t)(gi_row >= 0 ? gi_row : 0) * TC_CAP;
+        float *od = cand_d + (int64_t)(gi_row >= 0 ? gi_row : 0) * TC_CAP;
+        int cnt = 0;
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            float g[32];
+            tc::tmem_ld32(taddr + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, g);
+            tc::tmem_ld_wait();
+            if (gi_row >= 0) {
+#pragma unroll
+                for (int q = 0; q < 32; q++) {
+                    const int j = c0 + q;
+                    if (j < sz && j != row) {
+                        const int jid = rid[j];
+                        const float d2 = (n_i + nrm[j]) - 2.f * g[q];
+                        bool keep;
+                        unsigned tag = 0;
+                        if (exact) {
+                            keep = key_less(d2, jid, thd, thi);
+                        } else {
+                            const float e = c1 * sqrtf(n_i * nrm[j]) + c2 * (n_i + nrm[j]);
+                            keep = d2 - e <= thd;
+                            tag = TC_RERANK;
+                        }
+                        if (keep && jid >= 0) {
+                            oid[cnt] = (int32_t)((unsigned)jid | tag);
+                            od[cnt] = d2;
+                            cnt++;
+                        }
+                    }
                 }
-                __syncwarp();
             }
-            merge_row(i, rid, drow, sz, kappa, cur, g_idx + (int64_t)i * kappa, g_dist + (int64_t)i * kappa, li,
-                      lv, bi, bv, ni, nv, dup);
-            cur = nxt;
         }
+        if (gi_row >= 0)
+            cand_n[gi_row] = cnt;
     }
     tc::fence_before_sync();
     __syncthreads();
     if (w == 0)
-        tc::tmem_dealloc(taddr, TN);
+        tc::tmem_dealloc(taddr, ncols);
+}
+
+// One warp per graph row: exact recompute of the marked candidates, then the
+// merge of the FP32 path.  Candidate ids arrive in ascending order.
+constexpr int MG_WARPS = 8;
+
+__host__ __device__ inline size_t merge_warp_bytes(int kappa)
+{
+    return (sizeof(int) + sizeof(float)) * (size_t)(2 * TC_CAP + 2 * kappa) + 16;
+}
+
+__global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__restrict__ X, int64_t n, int d,
+                                                                int64_t ld, int kappa,
+                                                                const int32_t *__restrict__ cand_id,
+                                                                const float *__restrict__ cand_d,
+                                                                const int32_t *__restrict__ cand_n,
+                                                                int32_t *__restrict__ g_idx,
+                                                                float *__restrict__ g_dist)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    unsigned char *wb = smem_raw + (size_t)w * merge_warp_bytes(kappa);
+    int *cid = reinterpret_cast<int *>(wb);
+    float *cdv = reinterpret_cast<float *>(cid + TC_CAP);
+    int *bi = reinterpret_cast<int *>(cdv + TC_CAP);
+    float *bv = reinterpret_cast<float *>(bi + TC_CAP);
+    int *li = reinterpret_cast<int *>(bv + TC_CAP);
+    float *lv = reinterpret_cast<float *>(li + kappa);
+    int *ni = reinterpret_cast<int *>(lv + kappa);
+    float *nv = reinterpret_cast<float *>(ni + kappa);
+    unsigned *dup = reinterpret_cast<unsigned *>(nv + kappa);
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+
+    for (int64_t i = (int64_t)blockIdx.x * MG_WARPS + w; i < n; i += (int64_t)gridDim.x * MG_WARPS) {
+        const int cnt = cand_n[i];
+        if (cnt == 0)
+            continue;
+        RowRegs cur;
+        load_row(cur, g_idx + i * kappa, g_dist + i * kappa, kappa);
+        const float *xi = X + i * ld;
+        for (int q = lane; q < cnt; q += 32) {
+            const unsigned raw = (unsigned)__ldcg(cand_id + i * TC_CAP + q);
+            const int j = (int)(raw & ~TC_RERANK);
+            float dv = __ldcg(cand_d + i * TC_CAP + q);
+            if (raw & TC_RERANK)
+                dv = vec4 ? pair_d2_seq4(xi, X + (int64_t)j * ld, d) : pair_d2_seq(xi, X + (int64_t)j * ld, d);
+            cid[q] = j;
+            cdv[q] = dv;
+        }
+        __syncwarp();
+        merge_row((int)i, cid, cdv, cnt, kappa, cur, g_idx + i * kappa, g_dist + i * kappa, li, lv, bi, bv, ni, nv,
+                  dup);
+        __syncwarp();
+    }
+}
+
+size_t refine_tc_scratch_bytes(int64_t n)
+{
+    const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
+    const size_t c = ((size_t)n * sizeof(int32_t) + 255) & ~size_t(255);
+    return 2 * a + c;
 }
 
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, int32_t k, int32_t kappa,
-                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, DevStatus *st,
-                             cudaStream_t s)
+                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, void *scratch,
+                             DevStatus *st, cudaStream_t s)
 {
-    const size_t shm64 = TcCfg<64>::bytes(kappa), shm128 = TcCfg<128>::bytes(kappa);
-    cudaError_t e = cudaFuncSetAttribute(k_refine_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64);
+    const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
+    int32_t *cand_id = static_cast<int32_t *>(scratch);
+    float *cand_d = reinterpret_cast<float *>(static_cast<char *>(scratch) + a);
+    int32_t *cand_n = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a);
+    cudaError_t e = cudaFuncSetAttribute(k_refine_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     if (e != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_refine_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm128)) !=
+    const size_t shm_merge = MG_WARPS * merge_warp_bytes(kappa);
+    if ((e = cudaFuncSetAttribute(k_refine_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_merge)) !=
         cudaSuccess)
         return e;
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    k_refine_tc<64><<<(unsigned)grid, TcCfg<64>::THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, k,
-                                                                      kappa, max_cluster, vec4, g_idx, g_dist, st);
-    k_refine_tc<128><<<(unsigned)grid, TcCfg<128>::THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
-                                                                         k, kappa, max_cluster, vec4, g_idx, g_dist,
-                                                                         st);
+    if ((e = cudaMemsetAsync(cand_n, 0, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess)
+        return e;
+    k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, k, kappa,
+                                                              max_cluster, g_idx, g_dist, cand_id, cand_d, cand_n,
+                                                              st);
+    int64_t mblocks = (n + MG_WARPS - 1) / MG_WARPS;
+    if (mblocks > 152 * 64)
+        mblocks = 152 * 64;
+    k_refine_merge<<<(unsigned)mblocks, MG_WARPS * 32, shm_merge, s>>>(X, n, (int)d, ld, kappa, cand_id, cand_d,
+                                                                        cand_n, g_idx, g_dist);
     return cudaGetLastError();
 }
 
