@@ -173,7 +173,7 @@ class Path:
         cur, nxt = self.la, self.lb
         for _ in range(w.tau):
             call("assign", g.assign_step, self.X, self.gi, self.C0, cur, nxt, None, self.s[1:2], None,
-                 self.precision, ws=ws)
+                 self.precision, self.mem, ws=ws)
             call("group", g.group_by_label, nxt, self.k0, self.off, self.mem, self.cnt, ws=ws)
             call("update", g.update_from_groups, self.X, self.off, self.mem, self.k0, self.C0, self.cnt,
                  self.s[0:1], ws=ws)
@@ -188,7 +188,7 @@ class Path:
         call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3], ws=ws)
         for _ in range(w.iters):
             call("assign", g.assign_step, self.X, self.gi, self.C, cur, nxt, None, self.s[3:4], None,
-                 self.precision, ws=ws)
+                 self.precision, self.mem, ws=ws)
             call("group", g.group_by_label, nxt, w.k, self.off, self.mem, self.cnt, ws=ws)
             call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3],
                  ws=ws)
@@ -203,7 +203,9 @@ def _radix_passes(k):
 def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
-    upd, asg = 2, (3 if precision == 1 else 2)  # assign: (shadow copy,) kernel, finish
+    upd = 2
+    # assign: shadow copy, tensor-core tiles, SIMT leftovers, reduce, finish (precision 1); kernel, reduce, finish
+    asg = 5 if precision == 1 and w.d <= 128 else (4 if precision == 1 else 3)
     ref = 1 + 3 + 2  # refine: run count, scan, two kernels (gram + merge, or two tile widths)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
@@ -230,7 +232,7 @@ def kernel_of(tag, precision=1):
     if tag == "refine" and precision == 1:
         return "k_refine_tc"
     if tag == "assign" and precision == 1:
-        return "k_assign_rows_bf"
+        return "k_assign_tc"
     return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
             "init_graph": "k_init_graph"}[tag]
 

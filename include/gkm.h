@@ -128,15 +128,19 @@ GK_API int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32
  *             after the assignment, Eq. 4), computed in FP64
  *   n_changed device int64[1] or NULL: samples whose label changed
  *   precision 0: candidate distances read the FP32 centroid rows; 1: they are
- *             first taken against a BF16 copy of the centroids (half the bytes)
+ *             first screened against a BF16 copy of the centroids (for d <= 128
+ *             on the tensor cores, 128 samples of adjacent clusters at a time)
  *             and every candidate within a rigorous error bound of the minimum
  *             is recomputed against the FP32 rows in the same order as with 0,
  *             so labels_out, best_d2, sum_d2 and n_changed are identical.
+ *   members   device int32[n] or NULL: the samples grouped by labels_in, as
+ *             gk_group_by_label returns them; used by precision 1 to form the
+ *             tiles (NULL: the call groups them itself)
  */
 GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                           const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                          double *sum_d2, int64_t *n_changed, int32_t precision, void *ws, size_t ws_bytes,
-                          void *stream);
+                          double *sum_d2, int64_t *n_changed, int32_t precision, const int32_t *members, void *ws,
+                          size_t ws_bytes, void *stream);
 
 /*
  * Centroid update (Sec. 1: each centroid becomes the mean of its members).

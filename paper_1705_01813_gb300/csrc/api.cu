@@ -92,7 +92,8 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     Carver cv{static_cast<char *>(ws), 0, 0};
     Layout L{};
     L.st = cv.take<DevStatus>(1);
-    bool need_group = op == GK_OP_UPDATE || op == GK_OP_REFINE || op == GK_OP_FIT || op == GK_OP_BUILD;
+    bool need_group = op == GK_OP_ASSIGN || op == GK_OP_UPDATE || op == GK_OP_REFINE || op == GK_OP_FIT ||
+                      op == GK_OP_BUILD;
     bool need_update = op == GK_OP_UPDATE || op == GK_OP_FIT || op == GK_OP_BUILD;
     bool need_assign = op == GK_OP_ASSIGN || op == GK_OP_FIT || op == GK_OP_BUILD;
     if (need_group) {
@@ -181,7 +182,8 @@ int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kapp
 
 int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                    const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                   double *sum_d2, int64_t *n_changed, int32_t precision, void *ws, size_t ws_bytes, void *stream)
+                   double *sum_d2, int64_t *n_changed, int32_t precision, const int32_t *members, void *ws,
+                   size_t ws_bytes, void *stream)
 {
     int rc;
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
@@ -198,8 +200,13 @@ int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_ASSIGN, n, d, k);
+    if (precision == 1 && !members) {  // group the samples by their input label for the tile screening
+        GK_CUDA(launch_group(labels_in, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st,
+                             (cudaStream_t)stream));
+        members = L.grp.members;
+    }
     GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
-                          L.asg_scratch, L.st, (cudaStream_t)stream, precision));
+                          L.asg_scratch, L.st, (cudaStream_t)stream, precision, members));
     return GK_OK;
 }
 
@@ -349,7 +356,7 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
     GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
     for (int t = 0; t < iters; t++) {
         GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
-                              L.asg_scratch, L.st, s, precision));
+                              L.asg_scratch, L.st, s, precision, L.grp.members));
         GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
                               L.upd_scratch, s));
@@ -397,7 +404,7 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
     for (int t = 0; t < tau; t++) {
         // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
         GK_CUDA(launch_assign(X, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
-                              nullptr, L.asg_scratch, L.st, s, p->precision));
+                              nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
         GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
                               L.elog + 2 + 2 * t, L.upd_scratch, s));

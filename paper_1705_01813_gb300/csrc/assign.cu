@@ -11,15 +11,23 @@
 // minimum.  Per-block FP64 partial sums of the winning distances and the
 // count of changed labels are reduced in a fixed order afterwards, so every
 // run gives the same bits.
+#include "assign_common.cuh"
 #include "common.cuh"
 
 #include <cuda_bf16.h>
 
 namespace gkm {
 
+bool assign_tc_supported(int64_t d, int64_t ld, const float *X, const float *C, int32_t kappa);
+cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                             const float *C, const __nv_bfloat16 *Cb, const float *delta, const float *cnorm,
+                             int32_t k, const int32_t *labels_in, const int32_t *members, int32_t *labels_out,
+                             float *best, int32_t *tile_flag, DevStatus *st, cudaStream_t s);
+
 constexpr int AS_WARPS = 8;
 constexpr int AS_BLOCKS = 152 * 8;  // fixed grid: the FP64 partial sums have a fixed order
 constexpr int AS_QCAP = MAX_KAPPA + 1;
+constexpr int AS_TILE = 128;  // samples per tile of the tensor-core assignment
 
 template <int VEC>
 __device__ __forceinline__ float cand_d2(const float *__restrict__ xs, const float *__restrict__ c, int d);
@@ -175,60 +183,11 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restric
     }
 }
 
-// Sum of 32 per-lane partial values for 32 candidates at once: after the five
-// exchange steps lane l holds the total over the warp of v[l] (31 shuffles in
-// all, instead of 5 per candidate).
-__device__ __forceinline__ float transpose_reduce32(float (&v)[32])
-{
-    const int lane = lane_id();
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool upper = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; j++) {
-            float send = upper ? v[j] : v[j + o];
-            float keep = upper ? v[j + o] : v[j];
-            v[j] = keep + __shfl_xor_sync(FULL_MASK, send, o);
-        }
-    }
-    return v[0];
-}
-
-__device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
-{
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&v.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    return make_float4(fa.x, fa.y, fb.x, fb.y);
-}
-
-// Partial (per lane) squared distance of x (registers) to a row of 16-byte
-// vectors, in the accumulation order of k_assign_rows.
-template <int NV, typename RowLoad>
-__device__ __forceinline__ float lane_partial(const float4 (&xv)[NV], int d4, RowLoad load)
-{
-    const int lane = lane_id();
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        const int col = lane + 32 * v;
-        if (col < d4) {
-            const float4 cv = load(col);
-            const float e0 = xv[v].x - cv.x, e1 = xv[v].y - cv.y, e2 = xv[v].z - cv.z, e3 = xv[v].w - cv.w;
-            a0 = fmaf(e0, e0, a0);
-            a1 = fmaf(e1, e1, a1);
-            a0 = fmaf(e2, e2, a0);
-            a1 = fmaf(e3, e3, a1);
-        }
-    }
-    return a0 + a1;
-}
-
 // Coalesced variant for 16-byte rows (d % 4 == 0, d <= 32 * 4 * NV): the warp
 // keeps x_i in registers (lane l owns vectors l, l + 32, ...), reads each
 // candidate centroid row with one coalesced 16-byte load per lane and vector,
 // and reduces 32 candidates' partial distances together.
-template <int NV>
+template <int NV, bool TILES>
 __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
@@ -237,6 +196,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__re
                                                                float *__restrict__ best_out,
                                                                double *__restrict__ blk_sum,
                                                                unsigned long long *__restrict__ blk_changed,
+                                                               const int32_t *__restrict__ tmem_members, const int32_t *__restrict__ tile_flag,
                                                                DevStatus *st)
 {
     __shared__ int s_q[AS_WARPS][AS_QCAP];
@@ -250,7 +210,13 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__re
     double wsum = 0.0;
     unsigned long long wchg = 0;
     const int ncand = kappa + 1;
-    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+    for (int64_t p = (int64_t)blockIdx.x * AS_WARPS + w; p < n; p += (int64_t)gridDim.x * AS_WARPS) {
+        int64_t i = p;
+        if (TILES) {  // only the samples of the tiles the tensor-core kernel left over
+            if (!tile_flag[p / AS_TILE])
+                continue;
+            i = tmem_members[p];
+        }
         const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
         float4 xv[NV];
 #pragma unroll
@@ -356,22 +322,27 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__re
 // BF16 shadow of the centroids: Cb = bf16(C) and delta_r >= ||C_r - Cb_r||.
 // ---------------------------------------------------------------------------
 __global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bfloat16 *__restrict__ Cb,
-                              float *__restrict__ delta)
+                              float *__restrict__ delta, float *__restrict__ cnorm)
 {
     const int lane = lane_id();
     for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < k; r += gridDim.x * (blockDim.x >> 5)) {
-        double e = 0.0;
+        double e = 0.0, c2 = 0.0;
         for (int t = lane; t < d; t += 32) {
             const float c = C[(int64_t)r * d + t];
             const __nv_bfloat16 b = __float2bfloat16_rn(c);
             Cb[(int64_t)r * d + t] = b;
             const double diff = (double)c - (double)__bfloat162float(b);
             e += diff * diff;
+            c2 += (double)c * (double)c;
         }
-        for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_xor_sync(FULL_MASK, e, o);
-        if (lane == 0)
+            c2 += __shfl_xor_sync(FULL_MASK, c2, o);
+        }
+        if (lane == 0) {
             delta[r] = (float)(sqrt(e) * (1.0 + 1e-6)) + 1e-30f;  // rounded up
+            cnorm[r] = (float)c2;                                 // ||C_r||^2 (a bound input only)
+        }
     }
 }
 
@@ -383,7 +354,7 @@ __global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bf
 // value D~ + E_r is recomputed against C with the FP32 kernel's order (same
 // lane partials, same reduction tree), so the winner and its distance are the
 // FP32 kernel's bit for bit.
-template <int NV>
+template <int NV, bool TILES>
 __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *__restrict__ X, int64_t n, int d,
                                                                   int64_t ld, const int32_t *__restrict__ G,
                                                                   int kappa, const float *__restrict__ C,
@@ -394,7 +365,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
                                                                   float *__restrict__ best_out,
                                                                   double *__restrict__ blk_sum,
                                                                   unsigned long long *__restrict__ blk_changed,
-                                                                  DevStatus *st)
+                                                                  const int32_t *__restrict__ tmem_members, const int32_t *__restrict__ tile_flag,
+                                                               DevStatus *st)
 {
     __shared__ int s_q[AS_WARPS][AS_QCAP];
     __shared__ float s_lo[AS_WARPS][AS_QCAP + 31];
@@ -410,7 +382,13 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
     double wsum = 0.0;
     unsigned long long wchg = 0;
     const int ncand = kappa + 1;
-    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+    for (int64_t p = (int64_t)blockIdx.x * AS_WARPS + w; p < n; p += (int64_t)gridDim.x * AS_WARPS) {
+        int64_t i = p;
+        if (TILES) {  // only the samples of the tiles the tensor-core kernel left over
+            if (!tile_flag[p / AS_TILE])
+                continue;
+            i = tmem_members[p];
+        }
         const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
         float4 xv[NV];
 #pragma unroll
@@ -541,6 +519,41 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
     }
 }
 
+// Per-block FP64 sums of best[] and counts of changed labels over fixed index
+// ranges (the same for every kernel that produced best[]), so the total has
+// the same bits whichever assignment kernel ran.
+__global__ void __launch_bounds__(256) k_assign_reduce(const float *__restrict__ best,
+                                                       const int32_t *__restrict__ Lin,
+                                                       const int32_t *__restrict__ Lout, int64_t n,
+                                                       double *__restrict__ blk_sum,
+                                                       unsigned long long *__restrict__ blk_changed)
+{
+    __shared__ double s[256];
+    __shared__ unsigned long long c[256];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(n, b0 + per);
+    double a = 0.0;
+    unsigned long long ch = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) {
+        a += (double)best[i];
+        ch += Lin[i] != Lout[i] ? 1ull : 0ull;
+    }
+    s[threadIdx.x] = a;
+    c[threadIdx.x] = ch;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s[threadIdx.x] += s[threadIdx.x + o];
+            c[threadIdx.x] += c[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        blk_sum[blockIdx.x] = s[0];
+        blk_changed[blockIdx.x] = c[0];
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_assign_finish(const double *__restrict__ blk_sum,
                                                         const unsigned long long *__restrict__ blk_changed, int nb,
                                                         double *__restrict__ sum_d2, int64_t *__restrict__ n_changed)
@@ -571,48 +584,69 @@ __global__ void __launch_bounds__(1024) k_assign_finish(const double *__restrict
     }
 }
 
-size_t assign_scratch_bytes(int64_t, int32_t k, int64_t d)
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d)
 {
-    const size_t part = ((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255);
-    const size_t shadow = (((size_t)k * (size_t)d * 2 + 255) & ~size_t(255)) + (((size_t)k * 4 + 255) & ~size_t(255));
-    return part + shadow;
+    const size_t part = al256((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)));
+    const size_t shadow = al256((size_t)k * (size_t)d * 2) + 2 * al256((size_t)k * 4);
+    const size_t best = al256((size_t)n * 4);
+    const size_t tiles = al256((size_t)((n + AS_TILE - 1) / AS_TILE) * 4);
+    return part + shadow + best + tiles;
 }
 
 cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                           const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
                           double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,
-                          int precision)
+                          int precision, const int32_t *members)
 {
-    double *blk_sum = static_cast<double *>(scratch);
+    char *sp = static_cast<char *>(scratch);
+    double *blk_sum = reinterpret_cast<double *>(sp);
     unsigned long long *blk_chg = reinterpret_cast<unsigned long long *>(blk_sum + AS_BLOCKS);
-    char *shadow = static_cast<char *>(scratch) +
-                   (((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)) + 255) & ~size_t(255));
-    __nv_bfloat16 *Cb = reinterpret_cast<__nv_bfloat16 *>(shadow);
-    float *delta = reinterpret_cast<float *>(shadow + (((size_t)k * (size_t)d * 2 + 255) & ~size_t(255)));
-    int dpad = (int)((d + 3) & ~3);
-    size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
-    bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
-                ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-    cudaError_t e;
+    sp += al256((size_t)AS_BLOCKS * (sizeof(double) + sizeof(unsigned long long)));
+    __nv_bfloat16 *Cb = reinterpret_cast<__nv_bfloat16 *>(sp);
+    sp += al256((size_t)k * (size_t)d * 2);
+    float *delta = reinterpret_cast<float *>(sp);
+    sp += al256((size_t)k * 4);
+    float *cnorm = reinterpret_cast<float *>(sp);
+    sp += al256((size_t)k * 4);
+    float *best = best_d2 ? best_d2 : reinterpret_cast<float *>(sp);
+    sp += al256((size_t)n * 4);
+    int32_t *tile_flag = reinterpret_cast<int32_t *>(sp);
+
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int d4 = (int)(d / 4);
+    cudaError_t e;
     if (precision == 1 && vec4 && d4 <= 32 * 8) {
-        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta);
-#define GK_ASGB(NV)                                                                                              \
-    k_assign_rows_bf<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,      \
-                                                             labels_in, labels_out, best_d2, blk_sum, blk_chg, st)
-        if (d4 <= 32)
-            GK_ASGB(1);
-        else if (d4 <= 64)
-            GK_ASGB(2);
-        else if (d4 <= 128)
-            GK_ASGB(4);
-        else
-            GK_ASGB(8);
+        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
+        const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
+        if (tiles) {
+            if ((e = launch_assign_tc(X, n, d, ld, g_idx, kappa, C, Cb, delta, cnorm, k, labels_in, members,
+                                      labels_out, best, tile_flag, st, s)) != cudaSuccess)
+                return e;
+        }
+#define GK_ASGB(NV, T)                                                                                           \
+    k_assign_rows_bf<NV, T><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,   \
+                                                                labels_in, labels_out, best, blk_sum, blk_chg,      \
+                                                                members, tile_flag, st)
+        if (tiles) {
+            GK_ASGB(1, true);  // d <= 128 on the tensor-core path
+        } else if (d4 <= 32) {
+            GK_ASGB(1, false);
+        } else if (d4 <= 64) {
+            GK_ASGB(2, false);
+        } else if (d4 <= 128) {
+            GK_ASGB(4, false);
+        } else {
+            GK_ASGB(8, false);
+        }
 #undef GK_ASGB
     } else if (vec4 && d4 <= 32 * 8) {
 #define GK_ASG(NV)                                                                                               \
-    k_assign_rows<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,      \
-                                                          labels_out, best_d2, blk_sum, blk_chg, st)
+    k_assign_rows<NV, false><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,  \
+                                                                 labels_out, best, blk_sum, blk_chg, nullptr,       \
+                                                                 nullptr, st)
         if (d4 <= 32)
             GK_ASG(1);
         else if (d4 <= 64)
@@ -622,23 +656,29 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
         else
             GK_ASG(8);
 #undef GK_ASG
-    } else if (vec4) {
-        if (shm > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_assign<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
-                cudaSuccess)
-            return e;
-        k_assign<4><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
-                                                            labels_out, best_d2, blk_sum, blk_chg, st);
     } else {
-        if (shm > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_assign<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
-                cudaSuccess)
-            return e;
-        k_assign<1><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
-                                                            labels_out, best_d2, blk_sum, blk_chg, st);
+        int dpad = (int)((d + 3) & ~3);
+        size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
+        if (vec4) {
+            if (shm > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k_assign<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                    cudaSuccess)
+                return e;
+            k_assign<4><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+                                                                labels_out, best, blk_sum, blk_chg, st);
+        } else {
+            if (shm > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k_assign<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                    cudaSuccess)
+                return e;
+            k_assign<1><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+                                                                labels_out, best, blk_sum, blk_chg, st);
+        }
     }
-    if (sum_d2 || n_changed)
+    if (sum_d2 || n_changed) {
+        k_assign_reduce<<<AS_BLOCKS, 256, 0, s>>>(best, labels_in, labels_out, n, blk_sum, blk_chg);
         k_assign_finish<<<1, 1024, 0, s>>>(blk_sum, blk_chg, AS_BLOCKS, sum_d2, n_changed);
+    }
     return cudaGetLastError();
 }
 

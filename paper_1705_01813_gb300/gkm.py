@@ -66,7 +66,7 @@ def load(build_if_missing: bool = True):
             L.gk_workspace_size_build.argtypes = [I64, I64, ctypes.POINTER(GraphParams)]
             L.gk_init_labels.argtypes = [I64, I32, U64, P, P]
             L.gk_init_graph.argtypes = [P, I64, I64, I64, I32, U64, P, P, P, SZ, P]
-            L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, I32, P, SZ, P]
+            L.gk_assign_step.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, I32, P, P, SZ, P]
             L.gk_update_step.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P, P, P, SZ, P]
             L.gk_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_build_knn_graph.argtypes = [P, I64, I64, I64, ctypes.POINTER(GraphParams), P, P, P, P, P, SZ, P]
@@ -173,7 +173,7 @@ ALLOC = "alloc"
 
 
 def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=ALLOC, n_changed=ALLOC,
-                precision: int = 0, ws: Workspace | None = None, stream=None):
+                precision: int = 0, members=None, ws: Workspace | None = None, stream=None):
     """Graph-guided assignment; returns (labels_out, best_d2, sum_d2, n_changed).
 
     The optional outputs are allocated by default; pass a tensor to reuse it or
@@ -190,8 +190,8 @@ def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=A
     n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is ALLOC else n_changed
     ws = ws or workspace(workspace_size(GK_OP_ASSIGN, n, d, k, kappa), dev)
     _check(load().gk_assign_step(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
-                                 _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), precision, ws.ptr,
-                                 ws.nbytes, _stream(stream)))
+                                 _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), precision,
+                                 _ptr(members), ws.ptr, ws.nbytes, _stream(stream)))
     return labels_out, best_d2, sum_d2, n_changed
 
 

@@ -49,26 +49,26 @@ def test_argument_errors(lib):
     P = _fake()
     ws = _fake(0x20000000)
     # n too small, kappa >= n, kappa > 128, ld < d, misaligned workspace, NULL arrays
-    assert lib.gk_assign_step(P, 1, 4, 4, P, 1, P, 2, P, _fake(0x30000000), None, None, None, 0, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 1, 4, 4, P, 1, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 10, P, 2, P, _fake(0x30000000), None, None, None, 0, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 10, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"kappa" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 1000, 4, 4, P, 129, P, 2, P, _fake(0x30000000), None, None, None, 0, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 1000, 4, 4, P, 129, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
-    assert lib.gk_assign_step(P, 10, 4, 3, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 3, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"ld" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, P, None, None, None, 0, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, P, None, None, None, 0, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"alias" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, _fake(0x20000010),
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, None, _fake(0x20000010),
                               1 << 20, None) == gkm.GK_ERR_INVALID
     assert b"aligned" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, ws, 16,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 16,
                               None) == gkm.GK_ERR_INVALID
     assert b"too small" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 3, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 3, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"precision" in lib.gk_last_error()
     assert lib.gk_update_step(None, 10, 4, 4, P, 2, P, None, None, None, None, ws, 1 << 20,

@@ -256,6 +256,28 @@ def test_exact_knn_special_case(G, precision):
     P.check_graph(Xs, _np(gi), _np(gd), bi, bd, exact=True)
 
 
+@pytest.mark.parametrize("n,d,k,kappa,graph", [
+    (3000, 32, 40, 10, "knn"),        # small union per tile
+    (20011, 64, 9000, 60, "random"),  # random labels and graph: unions overflow, SIMT leftovers
+    (20000, 128, 300, 50, "knn"),     # SIFT-like width, mid-size unions
+    (517, 16, 3, 20, "knn"),          # partial last tile, three clusters
+])
+def test_assign_tensor_core_tiles_equal_fp32(G, n, d, k, kappa, graph):
+    """Tensor-core screening over 128-sample tiles (with the SIMT kernel for tiles whose
+    candidate union is too large) gives the FP32 kernel's outputs bit for bit."""
+    X = datagen.sift_like(n, d, max(4, k // 3), seed=n) if d == 128 else _blobs(n, d, max(3, k // 2), n)
+    gi = O.brute_knn(X, kappa)[0] if (graph == "knn" and n <= 3000) else O.init_graph(X, kappa, 7)[0]
+    L = O.init_labels(n, k, 8)
+    C64, _, _, _ = O.update(X, L, k)
+    Xd, gd, Cd, Ld = _cuda(X), _cuda(gi), _cuda(C64.astype(np.float32)), _cuda(L)
+    a = G.assign_step(Xd, gd, Cd, Ld, precision=0)
+    off, mem, _ = G.group_by_label(Ld, k)
+    b = G.assign_step(Xd, gd, Cd, Ld, precision=1, members=mem)
+    c = G.assign_step(Xd, gd, Cd, Ld, precision=1)
+    for x, y, z in zip(a, b, c):
+        assert torch.equal(x, y) and torch.equal(x, z)
+
+
 def test_fit_precisions_identical(G):
     w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
     X = _cuda(w.data())
