@@ -21,8 +21,8 @@ namespace gkm {
 bool assign_tc_supported(int64_t d, int64_t ld, const float *X, const float *C, int32_t kappa);
 cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                              const float *C, const __nv_bfloat16 *Cb, const float *delta, const float *cnorm,
-                             int32_t k, const int32_t *labels_in, const int32_t *members, int32_t *labels_out,
-                             float *best, int32_t *tile_flag, DevStatus *st, cudaStream_t s);
+                             int32_t k, const int32_t *labels_in, const int32_t *members, int32_t *sel_lab,
+                             int32_t *sel_n, int32_t *tile_flag, DevStatus *st, cudaStream_t s);
 
 constexpr int AS_WARPS = 8;
 constexpr int AS_BLOCKS = 152 * 8;  // fixed grid: the FP64 partial sums have a fixed order
@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
                                                                   double *__restrict__ blk_sum,
                                                                   unsigned long long *__restrict__ blk_changed,
                                                                   const int32_t *__restrict__ tmem_members, const int32_t *__restrict__ tile_flag,
-                                                               DevStatus *st)
+                                                               const int32_t *__restrict__ sel_lab,
+                                                               const int32_t *__restrict__ sel_n, DevStatus *st)
 {
     __shared__ int s_q[AS_WARPS][AS_QCAP];
     __shared__ float s_lo[AS_WARPS][AS_QCAP + 31];
@@ -384,10 +385,11 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
     const int ncand = kappa + 1;
     for (int64_t p = (int64_t)blockIdx.x * AS_WARPS + w; p < n; p += (int64_t)gridDim.x * AS_WARPS) {
         int64_t i = p;
-        if (TILES) {  // only the samples of the tiles the tensor-core kernel left over
-            if (!tile_flag[p / AS_TILE])
-                continue;
+        int nl = -1;  // >= 0: the tensor-core screening left nl candidates for the exact pass
+        if (TILES) {
             i = tmem_members[p];
+            if (!tile_flag[p / AS_TILE])
+                nl = sel_n[i];
         }
         const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
         float4 xv[NV];
@@ -397,88 +399,103 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
             xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const int own = Lin[i];
-        int u = 0;
-        for (int c0 = 0; c0 < ncand; c0 += 32) {
-            int c = c0 + lane;
-            int lab = -1;
-            if (c == 0) {
-                lab = own;
-            } else if (c < ncand) {
-                int nb = __ldcs(G + i * kappa + (c - 1));
-                if ((unsigned)nb < (unsigned)n)
-                    lab = Lin[nb];
-                else
-                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
-            }
-            if (c < ncand && (unsigned)lab >= (unsigned)k) {
-                flag_error(st, GK_ERR_INVALID, (unsigned)i);
-                lab = -1;
-            }
-            unsigned peers = __match_any_sync(FULL_MASK, lab);
-            bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
-            if (keep)
-                for (int q = 0; q < u; q++)
-                    if (qlist[q] == lab) {
-                        keep = false;
-                        break;
-                    }
-            unsigned keeps = __ballot_sync(FULL_MASK, keep);
-            __syncwarp();
-            if (keep)
-                qlist[u + __popc(keeps & lanemask_lt())] = lab;
-            u += __popc(keeps);
-            __syncwarp();
-        }
-        // pass 1: BF16 distances of every candidate (lane l holds candidate g0 + l of each group)
-        float *lov = s_lo[w];
-        float best_up = __int_as_float(0x7f800000);
-#pragma unroll 1
-        for (int g0 = 0; g0 < u; g0 += 32) {
-            const int cnt = min(32, u - g0);
-            float part[32];
-#pragma unroll
-            for (int c = 0; c < 32; c++) {
-                float acc = 0.f;
-                if (c < cnt) {
-                    const uint2 *row = Cb4 + (int64_t)qlist[g0 + c] * d4;
-                    acc = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
-                }
-                part[c] = acc;
-            }
-            const float dt = transpose_reduce32(part);
-            if (lane < cnt) {
-                const float dl = delta[qlist[g0 + lane]];
-                const float sq = sqrtf(fmaxf(dt, 0.f));
-                const float e = 1.01f * (dl * (2.f * sq + dl) + gam * (2.f * dt + dl * (2.f * sq + dl)));
-                lov[g0 + lane] = dt - e;
-                best_up = fminf(best_up, dt + e);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            best_up = fminf(best_up, __shfl_xor_sync(FULL_MASK, best_up, o));
-        __syncwarp();
-        // pass 2: FP32 distances of the candidates that may be the minimum, one at a
-        // time; the xor butterfly groups the lane partials as transpose_reduce32 does,
-        // so each total has the bits of the FP32 kernel
         float bd = __int_as_float(0x7f800000);
         int br = 0x7fffffff;
-#pragma unroll 1
-        for (int g0 = 0; g0 < u; g0 += 32) {
-            const int cnt = min(32, u - g0);
-            unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lov[g0 + lane] <= best_up);
-            while (sel) {
-                const int c = __ffs(sel) - 1;
-                sel &= sel - 1;
-                const int r = qlist[g0 + c];
+        if (nl >= 0) {
+            // exact FP32 distances of the screened labels (same lane partials and reduction grouping)
+            const int mine = lane < nl ? __ldg(sel_lab + i * 8 + lane) : 0;
+#pragma unroll 4
+            for (int z = 0; z < nl; z++) {
+                const int r = __shfl_sync(FULL_MASK, mine, z);
                 const float4 *row = C4 + (int64_t)r * d4;
-                float tot = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    tot += __shfl_xor_sync(FULL_MASK, tot, o);
+                const float tot = warp_total(lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); }));
                 if (key_less(tot, r, bd, br)) {
                     bd = tot;
                     br = r;
+                }
+            }
+        } else {
+            int u = 0;
+            for (int c0 = 0; c0 < ncand; c0 += 32) {
+                int c = c0 + lane;
+                int lab = -1;
+                if (c == 0) {
+                    lab = own;
+                } else if (c < ncand) {
+                    int nb = __ldcs(G + i * kappa + (c - 1));
+                    if ((unsigned)nb < (unsigned)n)
+                        lab = Lin[nb];
+                    else
+                        flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                }
+                if (c < ncand && (unsigned)lab >= (unsigned)k) {
+                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                    lab = -1;
+                }
+                unsigned peers = __match_any_sync(FULL_MASK, lab);
+                bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
+                if (keep)
+                    for (int q = 0; q < u; q++)
+                        if (qlist[q] == lab) {
+                            keep = false;
+                            break;
+                        }
+                unsigned keeps = __ballot_sync(FULL_MASK, keep);
+                __syncwarp();
+                if (keep)
+                    qlist[u + __popc(keeps & lanemask_lt())] = lab;
+                u += __popc(keeps);
+                __syncwarp();
+            }
+            // pass 1: BF16 distances of every candidate (lane l holds candidate g0 + l of each group)
+            float *lov = s_lo[w];
+            float best_up = __int_as_float(0x7f800000);
+    #pragma unroll 1
+            for (int g0 = 0; g0 < u; g0 += 32) {
+                const int cnt = min(32, u - g0);
+                float part[32];
+    #pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    float acc = 0.f;
+                    if (c < cnt) {
+                        const uint2 *row = Cb4 + (int64_t)qlist[g0 + c] * d4;
+                        acc = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
+                    }
+                    part[c] = acc;
+                }
+                const float dt = transpose_reduce32(part);
+                if (lane < cnt) {
+                    const float dl = delta[qlist[g0 + lane]];
+                    const float sq = sqrtf(fmaxf(dt, 0.f));
+                    const float e = 1.01f * (dl * (2.f * sq + dl) + gam * (2.f * dt + dl * (2.f * sq + dl)));
+                    lov[g0 + lane] = dt - e;
+                    best_up = fminf(best_up, dt + e);
+                }
+            }
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                best_up = fminf(best_up, __shfl_xor_sync(FULL_MASK, best_up, o));
+            __syncwarp();
+            // pass 2: FP32 distances of the candidates that may be the minimum, one at a
+            // time; the xor butterfly groups the lane partials as transpose_reduce32 does,
+            // so each total has the bits of the FP32 kernel
+    #pragma unroll 1
+            for (int g0 = 0; g0 < u; g0 += 32) {
+                const int cnt = min(32, u - g0);
+                unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lov[g0 + lane] <= best_up);
+                while (sel) {
+                    const int c = __ffs(sel) - 1;
+                    sel &= sel - 1;
+                    const int r = qlist[g0 + c];
+                    const float4 *row = C4 + (int64_t)r * d4;
+                    float tot = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
+    #pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+                        tot += __shfl_xor_sync(FULL_MASK, tot, o);
+                    if (key_less(tot, r, bd, br)) {
+                        bd = tot;
+                        br = r;
+                    }
                 }
             }
         }
@@ -592,7 +609,8 @@ size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d)
     const size_t shadow = al256((size_t)k * (size_t)d * 2) + 2 * al256((size_t)k * 4);
     const size_t best = al256((size_t)n * 4);
     const size_t tiles = al256((size_t)((n + AS_TILE - 1) / AS_TILE) * 4);
-    return part + shadow + best + tiles;
+    const size_t sel = al256((size_t)n * 8 * 4) + al256((size_t)n * 4);
+    return part + shadow + best + tiles + sel;
 }
 
 cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
@@ -613,6 +631,10 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
     float *best = best_d2 ? best_d2 : reinterpret_cast<float *>(sp);
     sp += al256((size_t)n * 4);
     int32_t *tile_flag = reinterpret_cast<int32_t *>(sp);
+    sp += al256((size_t)((n + AS_TILE - 1) / AS_TILE) * 4);
+    int32_t *sel_lab = reinterpret_cast<int32_t *>(sp);
+    sp += al256((size_t)n * 8 * 4);
+    int32_t *sel_n = reinterpret_cast<int32_t *>(sp);
 
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
                       ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
@@ -623,13 +645,13 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
         const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
         if (tiles) {
             if ((e = launch_assign_tc(X, n, d, ld, g_idx, kappa, C, Cb, delta, cnorm, k, labels_in, members,
-                                      labels_out, best, tile_flag, st, s)) != cudaSuccess)
+                                      sel_lab, sel_n, tile_flag, st, s)) != cudaSuccess)
                 return e;
         }
 #define GK_ASGB(NV, T)                                                                                           \
     k_assign_rows_bf<NV, T><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,   \
                                                                 labels_in, labels_out, best, blk_sum, blk_chg,      \
-                                                                members, tile_flag, st)
+                                                                members, tile_flag, sel_lab, sel_n, st)
         if (tiles) {
             GK_ASGB(1, true);  // d <= 128 on the tensor-core path
         } else if (d4 <= 32) {

@@ -14,11 +14,12 @@
 // lane t (its sample): approx = |x|^2 + |c|^2 - 2 x~.c~ for its own candidate
 // columns only, with a rigorous bound E on |approx - D|, D being the FP32
 // path's distance (BF16 rounding of both operands (4u + 2u^2)|x||c|, u = 2^-8,
-// FP32 accumulation and norms, and the FP32 path's own rounding).  Every
-// candidate whose approx - E is not above the smallest approx + E is then
-// recomputed exactly by the warp with the FP32 path's lane partials and
-// reduction tree, so the argmin over (distance, label) and its distance are
-// the FP32 path's.
+// FP32 accumulation and norms, and the FP32 path's own rounding).  The labels
+// of every candidate whose approx - E is not above the smallest approx + E
+// (at most AT_SEL of them, else the sample is marked) are written out; the
+// SIMT kernel then recomputes exactly those with the FP32 path's lane partials
+// and reduction tree, so the argmin over (distance, label) and its distance
+// are the FP32 path's.
 #include "assign_common.cuh"
 #include "common.cuh"
 #include "tc.cuh"
@@ -34,7 +35,7 @@ constexpr int AT_NCH = 128;                // union columns per MMA chunk
 constexpr int AT_KB = 64;                  // BF16 per K-block (128-byte swizzle row)
 constexpr int AT_NKB = 2;                  // K-blocks: d <= 128
 constexpr int AT_KB_BYTES = AT_TILE * 128; // 16 KB
-constexpr int AT_SEL = 8;                  // screened candidates kept per sample
+constexpr int AT_SEL = 8;                  // screened candidates kept per sample (AS_SEL in assign.cu)
 constexpr int AT_MW = AT_UMAX / 32;        // mask words per sample
 constexpr int AT_VS = 33;                  // stride of the per-thread value rows
 constexpr uint32_t AT_WAIT_ITERS = 1u << 22;
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_assign_tc(const float *__restric
                                                           const float *__restrict__ cnorm, int k,
                                                           const int32_t *__restrict__ Lin,
                                                           const int32_t *__restrict__ members,
-                                                          int32_t *__restrict__ Lout, float *__restrict__ best_out,
+                                                          int32_t *__restrict__ sel_lab, int32_t *__restrict__ sel_n,
                                                           int32_t *__restrict__ tile_fallback, DevStatus *st)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -359,65 +360,19 @@ __global__ void __launch_bounds__(AT_THREADS) k_assign_tc(const float *__restric
             flag_error(st, GK_ERR_TIMEOUT, blockIdx.x);
     }
 
-    // ---- 7. exact FP32 recompute of the screened candidates, warp by warp ----
-    if (!overflow && !timed_out) {
-        const float4 *C4 = reinterpret_cast<const float4 *>(C);
-        for (int q = 0; q < 32; q++) {
-            const int row = 32 * w + q;
-            const int i = sid[row];  // uniform over the warp
-            if (i < 0)
-                continue;
-            const float bu = __shfl_sync(FULL_MASK, best_up, q);
-            const int cntq = __shfl_sync(FULL_MASK, nsel, q);
-            const bool over = __shfl_sync(FULL_MASK, (int)sel_over, q) != 0;
-            float4 xv[1];
-            xv[0] = lane < d4 ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)i * ld) + lane)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
-            float bd = __int_as_float(0x7f800000);
-            int br = 0x7fffffff;
-            if (!over) {
+    // ---- 7. the screened candidates of each sample, for the exact pass ----
+    if (!overflow && !timed_out && tid < ns) {
+        const int i = sid[tid];
+        if (i >= 0) {
+            int cnt = 0;
+            int32_t *out = sel_lab + (int64_t)i * AT_SEL;
+            if (!sel_over) {
 #pragma unroll
-                for (int z = 0; z < AT_SEL; z++) {
-                    if (z < cntq) {
-                        const int colz = __shfl_sync(FULL_MASK, sel_col[z], q);
-                        const float loz = __shfl_sync(FULL_MASK, sel_lo[z], q);
-                        if (loz <= bu) {
-                            const int r = ulab[colz];
-                            const float4 *rowp = C4 + (int64_t)r * d4;
-                            const float tot =
-                                warp_total(lane_partial<1>(xv, d4, [&](int cc) { return __ldg(rowp + cc); }));
-                            if (key_less(tot, r, bd, br)) {
-                                bd = tot;
-                                br = r;
-                            }
-                        }
-                    }
-                }
-            } else {
-                // too many candidates in range: every candidate of the sample, exactly
-                const unsigned *mr = mask + row * AT_MW;
-                for (int wd = 0; wd < (nu + 31) / 32; wd++) {
-                    unsigned m = mr[wd];
-                    while (m) {
-                        const int b = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int r = ulab[wd * 32 + b];
-                        const float4 *rowp = C4 + (int64_t)r * d4;
-                        const float tot =
-                            warp_total(lane_partial<1>(xv, d4, [&](int cc) { return __ldg(rowp + cc); }));
-                        if (key_less(tot, r, bd, br)) {
-                            bd = tot;
-                            br = r;
-                        }
-                    }
-                }
+                for (int z = 0; z < AT_SEL; z++)
+                    if (z < nsel && sel_lo[z] <= best_up)
+                        out[cnt++] = ulab[sel_col[z]];
             }
-            if (lane == 0) {
-                if (br == 0x7fffffff)  // no valid candidate (own label out of range): keep the input label
-                    br = Lin[i], bd = 0.f;
-                Lout[i] = br;
-                best_out[i] = bd;
-            }
+            sel_n[i] = sel_over ? -1 : cnt;
         }
     }
     tc::fence_before_sync();
@@ -434,8 +389,8 @@ bool assign_tc_supported(int64_t d, int64_t ld, const float *X, const float *C, 
 
 cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                              const float *C, const __nv_bfloat16 *Cb, const float *delta, const float *cnorm,
-                             int32_t k, const int32_t *labels_in, const int32_t *members, int32_t *labels_out,
-                             float *best, int32_t *tile_fallback, DevStatus *st, cudaStream_t s)
+                             int32_t k, const int32_t *labels_in, const int32_t *members, int32_t *sel_lab,
+                             int32_t *sel_n, int32_t *tile_fallback, DevStatus *st, cudaStream_t s)
 {
     const int64_t tiles = (n + AT_TILE - 1) / AT_TILE;
     cudaError_t e = cudaMemsetAsync(tile_fallback, 0, sizeof(int32_t) * (size_t)tiles, s);
@@ -445,7 +400,7 @@ cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
         cudaSuccess)
         return e;
     k_assign_tc<<<(unsigned)tiles, AT_THREADS, AtSmem::bytes, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta,
-                                                                   cnorm, k, labels_in, members, labels_out, best,
+                                                                   cnorm, k, labels_in, members, sel_lab, sel_n,
                                                                    tile_fallback, st);
     return cudaGetLastError();
 }
