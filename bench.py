@@ -53,9 +53,9 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1], default=1,
-                    help="graph refinement: 0 FP32 SIMT pair distances, 1 tensor-core Gram + FP32 rerank "
-                         "(same graph)")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=1,
+                    help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
+                         "BF16/tensor-core screening in the assignment (all give the same results)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     return ap.parse_args()
 
@@ -205,7 +205,7 @@ def launches_per_step(w, precision):
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
     upd = 2
     # assign: shadow copy, tensor-core tiles, SIMT leftovers, reduce, finish (precision 1); kernel, reduce, finish
-    asg = 5 if precision == 1 and w.d <= 128 else (4 if precision == 1 else 3)
+    asg = 5 if precision == 2 and w.d <= 128 else (4 if precision == 2 else 3)
     ref = 1 + 3 + 2  # refine: run count, scan, two kernels (gram + merge, or two tile widths)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
@@ -229,9 +229,9 @@ def algorithmic_bytes(tag, w, k):
 
 
 def kernel_of(tag, precision=1):
-    if tag == "refine" and precision == 1:
-        return "k_refine_tc"
-    if tag == "assign" and precision == 1:
+    if tag == "refine" and precision >= 1:
+        return "k_refine_gram"
+    if tag == "assign" and precision == 2:
         return "k_assign_tc"
     return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
             "init_graph": "k_init_graph"}[tag]
@@ -240,8 +240,10 @@ def kernel_of(tag, precision=1):
 def source_sha(tag, precision=1):
     f = {"assign": "assign.cu", "update": "update.cu", "group": "group.cu", "refine": "refine.cu",
          "init_graph": "init.cu"}[tag]
-    if tag == "refine" and precision == 1:
+    if tag == "refine" and precision >= 1:
         f = "refine_tc.cu"
+    if tag == "assign" and precision == 2:
+        f = "assign_tc.cu"
     with open(os.path.join(ROOT, "paper_1705_01813_gb300", "csrc", f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
@@ -410,8 +412,10 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (X is %d MB)" % (Xh.nbytes >> 20),
                    "parallelism": f"replicas x{world}"},
         "fit_s": step_s,
-        "precision": {0: "fp32 throughout", 1: "bf16 tcgen05 gram (refine) and bf16 centroid copy (assign), each "
-                                               "with exact fp32 recompute inside its error bound"}[args.precision],
+        "precision": {0: "fp32 throughout",
+                      1: "bf16 tcgen05 gram in the refinement with exact fp32 recompute inside its error bound",
+                      2: "1 plus bf16 tcgen05 screening of assignment candidates with exact fp32 recompute"}
+                     [args.precision],
         "plain_fp32_ms_per_step": fp32_ms,
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},

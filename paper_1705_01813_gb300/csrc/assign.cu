@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restric
 // candidate centroid row with one coalesced 16-byte load per lane and vector,
 // and reduces 32 candidates' partial distances together.
 template <int NV, bool TILES>
-__global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
+__global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
                                                                const int32_t *__restrict__ Lin,
@@ -640,7 +640,7 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
                       ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int d4 = (int)(d / 4);
     cudaError_t e;
-    if (precision == 1 && vec4 && d4 <= 32 * 8) {
+    if (precision == 2 && vec4 && d4 <= 32 * 8) {
         k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
         const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
         if (tiles) {

@@ -133,9 +133,8 @@ cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, cons
                           void *scratch, cudaStream_t s);
 
 size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d);
-// precision 0: FP32 centroid rows; 1: BF16 shadow rows first, exact FP32 recompute near the minimum (same result)
-// members: the grouping of labels_in (CSR members) or NULL; with precision 1 and d <= 128 it lets the
-// candidate distances of 128-sample tiles be screened on the tensor cores (same results)
+// precision 0 and 1: FP32 candidate rows; 2: BF16 screening (tensor cores over 128-sample tiles when
+// members, the grouping of labels_in, is given and d <= 128) with the exact FP32 recompute (same results)
 cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
                           const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
                           double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,

@@ -222,7 +222,7 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
         return e;
     // an upper bound of the number of runs: sum over clusters of (m / cap + 1)
     const int64_t grid = (int64_t)k + n / max_cluster + 1;
-    if (precision == 1) {
+    if (precision >= 1) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
         if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, k, kappa, max_cluster, grid, g_idx, g_dist,
                                   tc_scratch, st, s)) != cudaSuccess)

@@ -77,7 +77,7 @@ def test_argument_errors(lib):
                               None) == gkm.GK_ERR_INVALID
     assert lib.gk_graph_refine(P, 10, 4, 4, P, 2, 3, 1, 0, P, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
     assert b"max_cluster" in lib.gk_last_error()
-    assert lib.gk_graph_refine(P, 10, 4, 4, P, 2, 3, 8, 2, P, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_graph_refine(P, 10, 4, 4, P, 2, 3, 8, 5, P, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
     assert b"precision" in lib.gk_last_error()
     assert lib.gk_kmeans_fit(P, 10, 4, 4, 2, P, 3, 5000, None, 0, 0, P, P, None, None, ws, 1 << 20,
                              None) == gkm.GK_ERR_INVALID
