@@ -64,6 +64,19 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Largest value over the ranks of the default process group (the slowest replica's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(samples_per_rank: int, steps: int, world: int, slowest_s: float) -> float:
+    """Samples of all replicas per second of the slowest replica (weak scaling: each rank runs the workload)."""
+    return world * samples_per_rank * steps / slowest_s
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -303,9 +316,7 @@ def run_gpu(args):
     ck = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = reduce_max(elapsed, dist, "cuda")
     per_tag = {}
     for tag, e0, e1 in rec:
         per_tag.setdefault(tag, []).append(e0.elapsed_time(e1) / 1e3)
@@ -364,10 +375,8 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
         t_e2e = max(a.elapsed_time(b) / 1e3, wall)
         if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * w.n * args.steps / t_e2e, "unit": "samples/s",
+            t_e2e = reduce_max(t_e2e, dist, "cuda")
+        e2e = {"value": whole_job_rate(w.n, args.steps, world, t_e2e), "unit": "samples/s",
                "h2d_bytes_per_step": int(Xh.nbytes),
                "d2h_bytes_per_step": int(lab_h.numel() * 4 + C_h.numel() * 4),
                "ms_per_step": 1e3 * t_e2e / args.steps}
@@ -395,7 +404,7 @@ def run_gpu(args):
     step_s = elapsed / args.steps
     res = {
         "metric": METRIC,
-        "value": world * w.n * args.steps / elapsed,
+        "value": whole_job_rate(w.n, args.steps, world, elapsed),
         "unit": "samples/s",
         "n_gpus": world,
         "steps": args.steps,
