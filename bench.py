@@ -219,7 +219,7 @@ def launches_per_step(w, precision):
     upd = 2
     # assign: shadow copy, tensor-core tiles, SIMT leftovers, reduce, finish (precision 1); kernel, reduce, finish
     asg = 5 if precision == 2 and w.d <= 128 else (4 if precision == 2 else 3)
-    ref = 1 + 3 + 2  # refine: run count, scan, two kernels (gram + merge, or two tile widths)
+    ref = 1 + 3 + 1 + 2  # refine: run count, scan, run clusters, two kernels (gram + merge, or two tile widths)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit

@@ -184,39 +184,39 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restric
 }
 
 // Coalesced variant for 16-byte rows (d % 4 == 0, d <= 32 * 4 * NV): the warp
-// keeps x_i in registers (lane l owns vectors l, l + 32, ...), reads each
-// candidate centroid row with one coalesced 16-byte load per lane and vector,
-// and reduces 32 candidates' partial distances together.
-template <int NV, bool TILES>
+// keeps x_i in registers (lane l owns vectors l, l + 32, ...).  Repeated
+// candidate labels are dropped with __match_any_sync inside each batch of 32
+// and, across batches, with a per-warp open-addressing set in shared memory
+// (one atomicCAS per new label).  Distances are taken AS_G candidates at a
+// time (AS_G / 2 for rows over 512 floats): each lane loads one 16-byte vector
+// of every centroid of the group, and transpose_reduce completes the group's
+// sums together.  The candidate list is padded to a multiple of the group with
+// its first entry, whose second evaluation
+// cannot change the (distance, label) minimum.
+constexpr int AS_G = 8;
+constexpr int AS_HASH = 256;                                  // slots of the per-warp label set
+constexpr int AS_QROW = (AS_QCAP + AS_G + 3) / 4 * 4;         // candidate list row, padding included
+static_assert(AS_HASH > AS_QCAP, "the label set must never fill up");
+
+template <int NV>
 __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
                                                                const int32_t *__restrict__ Lin,
                                                                int32_t *__restrict__ Lout,
-                                                               float *__restrict__ best_out,
-                                                               double *__restrict__ blk_sum,
-                                                               unsigned long long *__restrict__ blk_changed,
-                                                               const int32_t *__restrict__ tmem_members, const int32_t *__restrict__ tile_flag,
-                                                               DevStatus *st)
+                                                               float *__restrict__ best_out, DevStatus *st)
 {
-    __shared__ int s_q[AS_WARPS][AS_QCAP];
-    __shared__ double s_sum[AS_WARPS];
-    __shared__ unsigned long long s_chg[AS_WARPS];
+    __shared__ __align__(16) int s_q[AS_WARPS][AS_QROW];
+    __shared__ __align__(16) int s_h[AS_WARPS][AS_HASH];
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *qlist = s_q[w];
+    int *tab = s_h[w];
+    constexpr int GS = NV >= 8 ? AS_G / 2 : AS_G;  // wide rows: smaller groups keep the loads in registers
     const int d4 = d >> 2;
     const float4 *C4 = reinterpret_cast<const float4 *>(C);
-
-    double wsum = 0.0;
-    unsigned long long wchg = 0;
     const int ncand = kappa + 1;
-    for (int64_t p = (int64_t)blockIdx.x * AS_WARPS + w; p < n; p += (int64_t)gridDim.x * AS_WARPS) {
-        int64_t i = p;
-        if (TILES) {  // only the samples of the tiles the tensor-core kernel left over
-            if (!tile_flag[p / AS_TILE])
-                continue;
-            i = tmem_members[p];
-        }
+
+    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
         const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
         float4 xv[NV];
 #pragma unroll
@@ -224,6 +224,10 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *_
             int col = lane + 32 * v;
             xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int q = lane * 4; q < AS_HASH; q += 128)
+            *reinterpret_cast<int4 *>(tab + q) = make_int4(-1, -1, -1, -1);
+        __syncwarp();
         // candidate labels: slot 0 is the own label, slot 1 + j the label of neighbour j
         const int own = Lin[i];
         int u = 0;
@@ -243,46 +247,59 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *_
                 flag_error(st, GK_ERR_INVALID, (unsigned)i);
                 lab = -1;
             }
-            unsigned peers = __match_any_sync(FULL_MASK, lab);
-            bool keep = lab >= 0 && (peers & lanemask_lt()) == 0u;
-            if (keep)
-                for (int q = 0; q < u; q++)
-                    if (qlist[q] == lab) {
-                        keep = false;
+            const unsigned peers = __match_any_sync(FULL_MASK, lab);
+            bool fresh = false;
+            if (lab >= 0 && (peers & lanemask_lt()) == 0u) {
+                unsigned h = ((unsigned)lab * 0x9E3779B1u) >> 24;  // 8-bit multiplicative hash
+                for (int probe = 0; probe < AS_HASH; probe++) {    // the set is never full: ends early
+                    const int old = atomicCAS(tab + h, -1, lab);
+                    if (old == -1) {
+                        fresh = true;
                         break;
                     }
-            unsigned keeps = __ballot_sync(FULL_MASK, keep);
-            __syncwarp();
-            if (keep)
-                qlist[u + __popc(keeps & lanemask_lt())] = lab;
-            u += __popc(keeps);
-            __syncwarp();
+                    if (old == lab)
+                        break;
+                    h = (h + 1) & (AS_HASH - 1);
+                }
+            }
+            const unsigned fr = __ballot_sync(FULL_MASK, fresh);
+            if (fresh)
+                qlist[u + __popc(fr & lanemask_lt())] = lab;
+            u += __popc(fr);
         }
+        __syncwarp();
+        if (u > 0 && lane < GS)
+            qlist[u + lane] = qlist[0];
+        __syncwarp();
+
         float bd = __int_as_float(0x7f800000);
         int br = 0x7fffffff;
-        for (int g0 = 0; g0 < u; g0 += 32) {
-            const int cnt = min(32, u - g0);
-            float part[32];
+        for (int g0 = 0; g0 < u; g0 += GS) {
+            int lab[GS];
 #pragma unroll
-            for (int c = 0; c < 32; c++) {
-                float acc = 0.f;
-                if (c < cnt) {
-                    const float4 *row = C4 + (int64_t)qlist[g0 + c] * d4;
-                    acc = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
-                }
-                part[c] = acc;
+            for (int c = 0; c < GS; c += 4) {
+                const int4 q4 = *reinterpret_cast<const int4 *>(qlist + g0 + c);
+                lab[c] = q4.x;
+                lab[c + 1] = q4.y;
+                lab[c + 2] = q4.z;
+                lab[c + 3] = q4.w;
             }
-            float tot = transpose_reduce32(part);
-            if (lane < cnt) {
-                int r = qlist[g0 + lane];
-                if (key_less(tot, r, bd, br)) {
-                    bd = tot;
-                    br = r;
-                }
+            float part[GS];
+#pragma unroll
+            for (int c = 0; c < GS; c++) {
+                const float4 *row = C4 + (int64_t)lab[c] * d4;
+                part[c] = lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); });
+            }
+            const float tot = transpose_reduce<GS>(part);
+            const int r = qlist[g0 + lane / (32 / GS)];
+            if (key_less(tot, r, bd, br)) {
+                bd = tot;
+                br = r;
             }
         }
+        // lanes that share bits 4 .. log2(32 / GS) hold the same candidates
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 16; o >= 32 / GS; o >>= 1) {
             float od = __shfl_xor_sync(FULL_MASK, bd, o);
             int orr = __shfl_xor_sync(FULL_MASK, br, o);
             if (key_less(od, orr, bd, br)) {
@@ -296,25 +313,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *_
             Lout[i] = br;
             if (best_out)
                 best_out[i] = bd;
-            wsum += (double)bd;
-            wchg += (br != own) ? 1ull : 0ull;
         }
         __syncwarp();
-    }
-    if (lane == 0) {
-        s_sum[w] = wsum;
-        s_chg[w] = wchg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        unsigned long long c = 0;
-        for (int q = 0; q < AS_WARPS; q++) {
-            t += s_sum[q];
-            c += s_chg[q];
-        }
-        blk_sum[blockIdx.x] = t;
-        blk_changed[blockIdx.x] = c;
     }
 }
 
@@ -666,9 +666,8 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
 #undef GK_ASGB
     } else if (vec4 && d4 <= 32 * 8) {
 #define GK_ASG(NV)                                                                                               \
-    k_assign_rows<NV, false><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,  \
-                                                                 labels_out, best, blk_sum, blk_chg, nullptr,       \
-                                                                 nullptr, st)
+    k_assign_rows<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,         \
+                                                          labels_out, best, st)
         if (d4 <= 32)
             GK_ASG(1);
         else if (d4 <= 64)

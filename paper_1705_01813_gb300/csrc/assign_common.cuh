@@ -9,24 +9,35 @@
 
 namespace gkm {
 
-// Sum of 32 per-lane partial values for 32 candidates at once: after the five
-// exchange steps lane l holds the total over the warp of v[l] (31 shuffles in
-// all, instead of 5 per candidate).
-__device__ __forceinline__ float transpose_reduce32(float (&v)[32])
+// Warp sums of G per-lane partial values (G = 2, 4, ..., 32 candidates) at
+// once.  The first log2 G exchange steps pair lanes across bit 4, 3, ... and
+// halve the values each lane holds; the remaining lane bits are summed with a
+// plain xor butterfly.  Every candidate's total is thus formed with the tree
+// of warp_total (bit 4 first, then 3, 2, 1, 0), so all three give the same
+// bits.  Afterwards lane l holds the total of candidate l / (32 / G).
+template <int G>
+__device__ __forceinline__ float transpose_reduce(float (&v)[G])
 {
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "G must be a power of two in [2, 32]");
     const int lane = lane_id();
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
+    for (int h = G / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
         const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int j = 0; j < o; j++) {
-            float send = upper ? v[j] : v[j + o];
-            float keep = upper ? v[j + o] : v[j];
+        for (int j = 0; j < h; j++) {
+            float send = upper ? v[j] : v[j + h];
+            float keep = upper ? v[j + h] : v[j];
             v[j] = keep + __shfl_xor_sync(FULL_MASK, send, o);
         }
     }
-    return v[0];
+    float t = v[0];
+#pragma unroll
+    for (int o = 16 / G; o >= 1; o >>= 1)
+        t += __shfl_xor_sync(FULL_MASK, t, o);
+    return t;
 }
+
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32]) { return transpose_reduce<32>(v); }
 
 __device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
 {
@@ -37,25 +48,29 @@ __device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
 }
 
 // Partial (per lane) squared distance of x (registers) to a row of 16-byte
-// vectors, in the accumulation order of k_assign_rows.
+// vectors, in the accumulation order of the assignment kernels: two
+// accumulators, (a0, a1) += (e0^2, e1^2), then += (e2^2, e3^2) per vector,
+// each a round-to-nearest FMA, and a0 + a1 at the end.  The packed FP32x2 FMA
+// of sm_100+ performs each pair at once with the same roundings; e = x - c is
+// formed as fma(c, -1, x), which is x - c rounded once.
 template <int NV, typename RowLoad>
 __device__ __forceinline__ float lane_partial(const float4 (&xv)[NV], int d4, RowLoad load)
 {
     const int lane = lane_id();
-    float a0 = 0.f, a1 = 0.f;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 a = make_float2(0.f, 0.f);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         const int col = lane + 32 * v;
         if (col < d4) {
             const float4 cv = load(col);
-            const float e0 = xv[v].x - cv.x, e1 = xv[v].y - cv.y, e2 = xv[v].z - cv.z, e3 = xv[v].w - cv.w;
-            a0 = fmaf(e0, e0, a0);
-            a1 = fmaf(e1, e1, a1);
-            a0 = fmaf(e2, e2, a0);
-            a1 = fmaf(e3, e3, a1);
+            const float2 e01 = __ffma2_rn(make_float2(cv.x, cv.y), m1, make_float2(xv[v].x, xv[v].y));
+            const float2 e23 = __ffma2_rn(make_float2(cv.z, cv.w), m1, make_float2(xv[v].z, xv[v].w));
+            a = __ffma2_rn(e01, e01, a);
+            a = __ffma2_rn(e23, e23, a);
         }
     }
-    return a0 + a1;
+    return a.x + a.y;
 }
 
 // Complete one candidate's distance from the lane partials: the xor butterfly

@@ -97,7 +97,6 @@ __global__ void __launch_bounds__(AT_THREADS) k_assign_tc(const float *__restric
     const int64_t p0 = (int64_t)blockIdx.x * AT_TILE;
     const int ns = (int)((n - p0) < AT_TILE ? (n - p0) : AT_TILE);
     const int lsz = kappa + 1;
-    const int d4 = d >> 2;
 
     if (w == 0) {
         tc::tmem_alloc(tslot, AT_NCH);

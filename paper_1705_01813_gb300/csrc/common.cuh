@@ -149,8 +149,8 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
                           float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision);
 size_t refine_tc_scratch_bytes(int64_t n);
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                             const int32_t *members, const int32_t *run_off, int32_t k, int32_t kappa,
-                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, void *scratch,
-                             DevStatus *st, cudaStream_t s);
+                             const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
+                             int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
+                             void *scratch, DevStatus *st, cudaStream_t s);
 
 }  // namespace gkm

@@ -48,6 +48,14 @@ struct RefineTile {
     __host__ __device__ static size_t smem_bytes(int kappa) { return fixed_bytes + RF_WARPS * warp_bytes(kappa); }
 };
 
+// Cluster of every run: run_cl[run_off[r] + c] = r for c < nruns[r].
+__global__ void k_run_clusters(const int32_t *__restrict__ run_off, int k, int32_t *__restrict__ run_cl)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x)
+        for (int q = run_off[r]; q < run_off[r + 1]; q++)
+            run_cl[q] = r;
+}
+
 // Runs of each cluster: ceil(m / cap) for m >= 2, else none.
 __global__ void k_count_runs(const int32_t *__restrict__ off, int k, int cap, int32_t *__restrict__ nruns)
 {
@@ -61,7 +69,8 @@ template <int T>
 __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const float *__restrict__ X, int64_t n, int d, int64_t ld,
                                                        const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ mem,
-                                                       const int32_t *__restrict__ run_off, int k, int kappa,
+                                                       const int32_t *__restrict__ run_off,
+                                                       const int32_t *__restrict__ run_cl, int k, int kappa,
                                                        int cap, int lo_run, int32_t *__restrict__ g_idx,
                                                        float *__restrict__ g_dist, DevStatus *st)
 {
@@ -89,15 +98,7 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
     const int run = blockIdx.x;
     if (run >= run_off[k])
         return;
-    int lo = 0, hi = k;  // last r with run_off[r] <= run
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (run_off[mid] <= run)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    const int r = lo;
+    const int r = run_cl[run];
     const int beg = off[r], m = off[r + 1] - beg;
     const int nc = (m + cap - 1) / cap, base = m / nc, rem = m % nc;
     const int c = run - run_off[r];
@@ -196,10 +197,12 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
 }
 
 static size_t run_bytes(int32_t k) { return ((size_t)(2 * (k + 1)) * sizeof(int32_t) + 255) / 256 * 256; }
+// runs per refinement are at most k + n / max_cluster (max_cluster >= 2)
+static size_t run_cl_bytes(int64_t n, int32_t k) { return ((size_t)(k + n / 2 + 1) * sizeof(int32_t) + 255) / 256 * 256; }
 
 size_t refine_scratch_bytes(int64_t n, int32_t k)
 {
-    return run_bytes(k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n);
+    return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n);
 }
 
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
@@ -208,7 +211,8 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
 {
     int32_t *nruns = static_cast<int32_t *>(scratch);
     int32_t *run_off = nruns + (k + 1);
-    void *sc = static_cast<char *>(scratch) + run_bytes(k);
+    int32_t *run_cl = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + run_bytes(k));
+    void *sc = static_cast<char *>(scratch) + run_bytes(k) + run_cl_bytes(n, k);
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
     cudaError_t e = cudaFuncSetAttribute(k_refine<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64);
@@ -220,23 +224,25 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     k_count_runs<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(offsets, k, max_cluster, nruns);
     if ((e = launch_scan(nruns, run_off, k, sc, s)) != cudaSuccess)
         return e;
+    k_run_clusters<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(run_off, k, run_cl);
     // an upper bound of the number of runs: sum over clusters of (m / cap + 1)
     const int64_t grid = (int64_t)k + n / max_cluster + 1;
     if (precision >= 1) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
-        if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, k, kappa, max_cluster, grid, g_idx, g_dist,
-                                  tc_scratch, st, s)) != cudaSuccess)
+        if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, grid, g_idx,
+                                  g_dist, tc_scratch, st, s)) != cudaSuccess)
             return e;
         if (max_cluster > 128)
-            k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, k,
-                                                                     kappa, max_cluster, 128, g_idx, g_dist, st);
+            k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
+                                                                     run_cl, k, kappa, max_cluster, 128, g_idx,
+                                                                     g_dist, st);
         return cudaGetLastError();
     }
     // runs of <= 64 members, then the longer runs (up to 128 per tile, longer runs in tiles)
-    k_refine<64><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, k, kappa,
-                                                           max_cluster, 0, g_idx, g_dist, st);
-    k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, k, kappa,
-                                                             max_cluster, 64, g_idx, g_dist, st);
+    k_refine<64><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+                                                           kappa, max_cluster, 0, g_idx, g_dist, st);
+    k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+                                                             kappa, max_cluster, 64, g_idx, g_dist, st);
     return cudaGetLastError();
 }
 

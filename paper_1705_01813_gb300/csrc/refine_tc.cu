@@ -49,7 +49,8 @@ constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) *
 __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restrict__ X, int64_t n, int d,
                                                             int64_t ld, const int32_t *__restrict__ off,
                                                             const int32_t *__restrict__ mem,
-                                                            const int32_t *__restrict__ run_off, int k, int kappa,
+                                                            const int32_t *__restrict__ run_off,
+                                                            const int32_t *__restrict__ run_cl, int k, int kappa,
                                                             int cap, const int32_t *__restrict__ g_idx,
                                                             const float *__restrict__ g_dist,
                                                             int32_t *__restrict__ cand_id,
@@ -70,15 +71,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     const int run = blockIdx.x;
     if (run >= run_off[k])
         return;
-    int lo = 0, hi = k;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (run_off[mid] <= run)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    const int r = lo;
+    const int r = run_cl[run];
     const int beg = off[r], m = off[r + 1] - beg;
     const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
     const int c = run - run_off[r];
@@ -123,7 +116,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     const int srows = (sz + 7) & ~7;  // rows staged (the rest of the tile is never read back)
     for (int k0 = 0; k0 < d; k0 += kchunk) {
         // warp w stages rows w, w + 4, ...; lane l covers 4 consecutive coordinates
-#pragma unroll 4
+#pragma unroll 8
         for (int row = w; row < srows; row += TC_WARPS) {
             const int a = rid[row];
             float part = 0.f;
@@ -313,9 +306,9 @@ size_t refine_tc_scratch_bytes(int64_t n)
 }
 
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                             const int32_t *members, const int32_t *run_off, int32_t k, int32_t kappa,
-                             int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist, void *scratch,
-                             DevStatus *st, cudaStream_t s)
+                             const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
+                             int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
+                             void *scratch, DevStatus *st, cudaStream_t s)
 {
     const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
     int32_t *cand_id = static_cast<int32_t *>(scratch);
@@ -330,9 +323,9 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
         return e;
     if ((e = cudaMemsetAsync(cand_n, 0, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess)
         return e;
-    k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, k, kappa,
-                                                              max_cluster, g_idx, g_dist, cand_id, cand_d, cand_n,
-                                                              st);
+    k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+                                                              kappa, max_cluster, g_idx, g_dist, cand_id, cand_d,
+                                                              cand_n, st);
     int64_t mblocks = (n + MG_WARPS - 1) / MG_WARPS;
     if (mblocks > 152 * 64)
         mblocks = 152 * 64;
