@@ -7,13 +7,33 @@
 
 namespace gkm {
 
-// Number of keys of (v, id)[0..len) smaller than (kv, kj); the array is sorted.
-__device__ __forceinline__ int lower_rank(const float *v, const int *id, int len, float kv, int kj)
+// A (distance, id) key packed in 64 bits so that one unsigned comparison
+// orders keys as key_less does: the distance's bits mapped to an unsigned
+// integer of the same order (sign bit set for non-negative values, all bits
+// inverted for negative ones; -0 is first made +0, which compares equal to
+// it) in the high word, the id (non-negative) in the low word.
+__device__ __forceinline__ uint64_t pack_key(float dv, int id)
+{
+    const unsigned b = __float_as_uint(dv + 0.0f);
+    const unsigned o = b ^ ((unsigned)((int)b >> 31) | 0x80000000u);
+    return ((uint64_t)o << 32) | (uint32_t)id;
+}
+
+__device__ __forceinline__ float key_dist(uint64_t key)
+{
+    const unsigned o = (unsigned)(key >> 32);
+    return __uint_as_float((o & 0x80000000u) ? (o ^ 0x80000000u) : ~o);
+}
+
+__device__ __forceinline__ int key_id(uint64_t key) { return (int)(uint32_t)key; }
+
+// Number of keys of the sorted k[0..len) smaller than key.
+__device__ __forceinline__ int lower_rank(const uint64_t *k, int len, uint64_t key)
 {
     int lo = 0, hi = len;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if (key_less(v[mid], id[mid], kv, kj))
+        if (k[mid] < key)
             lo = mid + 1;
         else
             hi = mid;
@@ -45,14 +65,16 @@ __device__ __forceinline__ void load_row(RowRegs &r, const int32_t *__restrict__
 
 // Merge the candidates (ids cid[0..ncol), ascending; distances drow[0..ncol))
 // into graph row i, whose current kappa sorted keys are in `cur`; the merged
-// row is written to gi / gd when it changes.  Warp-cooperative.  Candidates
-// already in the row are found by a binary search of each row id among the
-// (sorted) candidate ids and masked out; the others that beat the row's
-// kappa-th key are ranked among themselves and placed by rank.
+// row is written to gi / gd when it changes.  Warp-cooperative, on packed
+// keys; per-warp shared buffers rk, nk (kappa keys each), bk (ncol keys) and
+// dup (ncol bits).  Candidates already in the row are found by a binary
+// search of each row id among the (sorted) candidate ids and masked out; the
+// others that beat the row's kappa-th key are ranked among themselves and
+// placed by rank plus their position in the row.
 __device__ __forceinline__ void merge_row(int i, const int *__restrict__ cid, const float *__restrict__ drow,
                                           int ncol, int kappa, const RowRegs &cur, int32_t *__restrict__ gi,
-                                          float *__restrict__ gd, int *li, float *lv, int *bi, float *bv, int *ni,
-                                          float *nv, unsigned *dup)
+                                          float *__restrict__ gd, uint64_t *rk, uint64_t *bk, uint64_t *nk,
+                                          unsigned *dup)
 {
     const int lane = lane_id();
     if (lane < 4)
@@ -63,8 +85,7 @@ __device__ __forceinline__ void merge_row(int i, const int *__restrict__ cid, co
         const int q = lane + 32 * u;
         if (q < kappa) {
             const int j = cur.id[u];
-            li[q] = j;
-            lv[q] = cur.dv[u];
+            rk[q] = pack_key(cur.dv[u], j);
             int lo = 0, hi = ncol;  // first candidate id >= j
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
@@ -78,77 +99,64 @@ __device__ __forceinline__ void merge_row(int i, const int *__restrict__ cid, co
         }
     }
     __syncwarp();
-    const float td = lv[kappa - 1];
-    const int ti = li[kappa - 1];
+    const uint64_t th = rk[kappa - 1];
     // candidates that would enter the row and are not in it yet
     int ns = 0;
     for (int c0 = 0; c0 < ncol; c0 += 32) {
         const int c = c0 + lane;
         bool ok = c < ncol;
         const int j = ok ? cid[c] : -1;
-        const float dv = ok ? drow[c] : 0.f;
-        ok = ok && j != i && ((dup[c0 >> 5] >> lane) & 1u) == 0u && key_less(dv, j, td, ti);
+        const uint64_t key = ok ? pack_key(drow[c], j) : ~0ull;
+        ok = ok && j != i && ((dup[c0 >> 5] >> lane) & 1u) == 0u && key < th;
         const unsigned bal = __ballot_sync(FULL_MASK, ok);
-        if (ok) {
-            const int p = ns + __popc(bal & lanemask_lt());
-            bi[p] = j;
-            bv[p] = dv;
-        }
+        if (ok)
+            bk[ns + __popc(bal & lanemask_lt())] = key;
         ns += __popc(bal);
     }
     __syncwarp();
     if (ns == 0)
         return;
     // rank the candidates among themselves (keys are distinct: ids differ)
-    int rk[4];
-    float kvs[4];
-    int kjs[4];
+    int rnk[4];
+    uint64_t kb[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
         const int b = lane + 32 * u;
-        rk[u] = -1;
+        rnk[u] = -1;
         if (b < ns) {
-            kvs[u] = bv[b];
-            kjs[u] = bi[b];
+            kb[u] = bk[b];
             int r = 0;
             for (int q = 0; q < ns; q++)
-                r += key_less(bv[q], bi[q], kvs[u], kjs[u]) ? 1 : 0;
-            rk[u] = r;
+                r += bk[q] < kb[u] ? 1 : 0;
+            rnk[u] = r;
         }
     }
     __syncwarp();
-    // place the sorted candidates in bi / bv, then merge with the row
+    // sorted candidates in bk, then each key's slot in the merged row
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-        if (rk[u] >= 0) {
-            bi[rk[u]] = kjs[u];
-            bv[rk[u]] = kvs[u];
-        }
-    }
+    for (int u = 0; u < 4; u++)
+        if (rnk[u] >= 0)
+            bk[rnk[u]] = kb[u];
     __syncwarp();
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-        if (rk[u] >= 0) {
-            const int pos = rk[u] + lower_rank(lv, li, kappa, kvs[u], kjs[u]);
-            if (pos < kappa) {
-                ni[pos] = kjs[u];
-                nv[pos] = kvs[u];
-            }
+        if (rnk[u] >= 0) {
+            const int pos = rnk[u] + lower_rank(rk, kappa, kb[u]);
+            if (pos < kappa)
+                nk[pos] = kb[u];
         }
     }
     for (int a = lane; a < kappa; a += 32) {
-        const float kv = lv[a];
-        const int kj = li[a];
-        const int pos = a + lower_rank(bv, bi, ns, kv, kj);
-        if (pos < kappa) {
-            ni[pos] = kj;
-            nv[pos] = kv;
-        }
+        const uint64_t key = rk[a];
+        const int pos = a + lower_rank(bk, ns, key);
+        if (pos < kappa)
+            nk[pos] = key;
     }
     __syncwarp();
     for (int q = lane; q < kappa; q += 32) {
-        gi[q] = ni[q];
-        gd[q] = nv[q];
+        const uint64_t key = nk[q];
+        gi[q] = key_id(key);
+        gd[q] = key_dist(key);
     }
     __syncwarp();
 }

@@ -18,7 +18,8 @@
 // warp then merges the tile's candidates into the graph rows of its rows:
 // candidates that beat the row's kappa-th key and are not already in the row
 // are compacted, ranked among themselves, located in the row by binary
-// search, and the kappa smallest keys of the union are written back.  Every
+// search (all on 64-bit packed keys), and the kappa smallest keys of the union
+// are written back.  Every
 // row belongs to exactly one run per refinement, so blocks never write the
 // same row.
 #include "common.cuh"
@@ -40,11 +41,12 @@ struct RefineTile {
     static constexpr size_t tile_floats = (size_t)T * DS;
     static constexpr size_t fixed_bytes =
         sizeof(float) * (stage_floats > tile_floats ? stage_floats : tile_floats) + sizeof(int) * 2 * T;
-    // per warp: row list (kappa ids + dists), candidates (T), new row (kappa)
+    // per warp: row keys (kappa), merged-row keys (kappa), candidate keys (T), dup bits
     __host__ __device__ static size_t warp_bytes(int kappa)
     {
-        return (sizeof(int) + sizeof(float)) * (size_t)(2 * kappa + T) + 4 * sizeof(unsigned);
+        return sizeof(uint64_t) * (size_t)(2 * kappa + T) + 4 * sizeof(unsigned);
     }
+    static_assert(fixed_bytes % 8 == 0, "the per-warp key buffers need 8-byte alignment");
     __host__ __device__ static size_t smem_bytes(int kappa) { return fixed_bytes + RF_WARPS * warp_bytes(kappa); }
 };
 
@@ -85,13 +87,10 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
     int *cid = rid + T;
     const int tid = threadIdx.x, w = tid >> 5;
     unsigned char *wbase = reinterpret_cast<unsigned char *>(cid + T) + w * TL::warp_bytes(kappa);
-    int *li = reinterpret_cast<int *>(wbase);
-    float *lv = reinterpret_cast<float *>(li + kappa);
-    int *ni = reinterpret_cast<int *>(lv + kappa);
-    float *nv = reinterpret_cast<float *>(ni + kappa);
-    int *bi = reinterpret_cast<int *>(nv + kappa);
-    float *bv = reinterpret_cast<float *>(bi + T);
-    unsigned *dup = reinterpret_cast<unsigned *>(bv + T);
+    uint64_t *rk = reinterpret_cast<uint64_t *>(wbase);
+    uint64_t *nk = rk + kappa;
+    uint64_t *bk = nk + kappa;
+    unsigned *dup = reinterpret_cast<unsigned *>(bk + T);
     const int ty = tid >> 4, tx = tid & 15;
 
     // block `run` handles that run: find its cluster r, run_off[r] <= run < run_off[r + 1]
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
                         load_row(nxt, g_idx + (int64_t)rid[rn] * kappa, g_dist + (int64_t)rid[rn] * kappa, kappa);
                     if (i >= 0)
                         merge_row(i, cid, dt + row * DS, ncl, kappa, cur, g_idx + (int64_t)i * kappa,
-                                  g_dist + (int64_t)i * kappa, li, lv, bi, bv, ni, nv, dup);
+                                  g_dist + (int64_t)i * kappa, rk, bk, nk, dup);
                     cur = nxt;
                 }
             }

@@ -25,6 +25,7 @@
 // candidates are recomputed exactly in FP32 in the order of pair_d2_seq, and
 // the candidates are merged into the row as in the FP32 path (merge.cuh).
 // Rows that received nothing are not touched.
+#include "assign_common.cuh"
 #include "common.cuh"
 #include "merge.cuh"
 #include "tc.cuh"
@@ -39,6 +40,7 @@ constexpr int TC_KCH = 2;                // K-blocks staged per chunk
 constexpr int TC_KB_BYTES = TC_M * 128;  // 16 KB per K-block
 constexpr int TC_THREADS = 128;          // one thread per TMEM lane
 constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_RB = 8;                 // rows a warp stages per batch
 constexpr int TC_CAP = 128;              // candidate slots per graph row
 constexpr uint32_t TC_WAIT_ITERS = 1u << 22;
 constexpr unsigned TC_RERANK = 0x80000000u;  // candidate id flag: distance needs the exact recompute
@@ -92,13 +94,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
         flags[0] = 0;
         flags[1] = 0;
     }
-    {
-        int a = tid < sz ? S[tid] : -1;
-        if (a >= n) {
-            flag_error(st, GK_ERR_INVALID, (unsigned)r);
-            a = -1;
-        }
-        rid[tid] = a;
+    // this thread's graph row and its kappa-th key (read now so the loads overlap the staging)
+    int gi_row = tid < sz ? S[tid] : -1;
+    if (gi_row >= n) {
+        flag_error(st, GK_ERR_INVALID, (unsigned)r);
+        gi_row = -1;
+    }
+    rid[tid] = gi_row;
+    float thd = 0.f;
+    int thi = 0;
+    if (gi_row >= 0) {
+        thd = __ldcg(g_dist + (int64_t)gi_row * kappa + kappa - 1);
+        thi = __ldcg(g_idx + (int64_t)gi_row * kappa + kappa - 1);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -112,49 +119,68 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     bool inexact = false;
     uint32_t phase = 0;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
-    const int kchunk = TC_KCH * TC_KB;
-    const int srows = (sz + 7) & ~7;  // rows staged (the rest of the tile is never read back)
+    const int kchunk = TC_KCH * TC_KB;  // 128 coordinates: 4 per lane
+    const int srows = (sz + 7) & ~7;    // rows staged (the rest of the tile is never read back)
     for (int k0 = 0; k0 < d; k0 += kchunk) {
-        // warp w stages rows w, w + 4, ...; lane l covers 4 consecutive coordinates
-#pragma unroll 8
-        for (int row = w; row < srows; row += TC_WARPS) {
-            const int a = rid[row];
-            float part = 0.f;
-            for (int kk = lane * 4; kk < kchunk; kk += 128) {
-                const int t = k0 + kk;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
+        const int kk = lane * 4, t = k0 + kk;
+        const int kb = kk / TC_KB, kin = kk % TC_KB;
+        float xr[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            xr[e] = t + e < d ? __ldg(xref + t + e) : 0.f;
+        // warp w stages rows w, w + 4, ..., TC_RB of them per batch with their loads in flight together
+        for (int row0 = w; row0 < srows; row0 += TC_WARPS * TC_RB) {
+            float v[TC_RB][4];
+#pragma unroll
+            for (int b = 0; b < TC_RB; b++) {
+                const int row = row0 + b * TC_WARPS;
+                const int a = row < srows ? rid[row] : -1;
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    v[b][e] = 0.f;
                 if (a >= 0) {
+                    const float *xa = X + (int64_t)a * ld + t;
                     if (vec4 && t + 3 < d) {
-                        const float4 xa = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)a * ld + t));
-                        const float4 xr = __ldg(reinterpret_cast<const float4 *>(xref + t));
-                        v[0] = xa.x - xr.x;
-                        v[1] = xa.y - xr.y;
-                        v[2] = xa.z - xr.z;
-                        v[3] = xa.w - xr.w;
+                        const float4 q = __ldg(reinterpret_cast<const float4 *>(xa));
+                        v[b][0] = q.x;
+                        v[b][1] = q.y;
+                        v[b][2] = q.z;
+                        v[b][3] = q.w;
                     } else {
 #pragma unroll
                         for (int e = 0; e < 4; e++)
                             if (t + e < d)
-                                v[e] = __ldg(X + (int64_t)a * ld + t + e) - __ldg(xref + t + e);
+                                v[b][e] = __ldg(xa + e);
                     }
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        part = fmaf(v[e], v[e], part);
-                        inexact |= !(v[e] == rintf(v[e]) && fabsf(v[e]) <= 255.f);
-                    }
+                    for (int e = 0; e < 4; e++)
+                        v[b][e] = t + e < d ? v[b][e] - xr[e] : 0.f;
                 }
-                const int kb = kk / TC_KB, kin = kk % TC_KB;
-                __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
-                __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t *>(&p0);
-                pk.y = *reinterpret_cast<uint32_t *>(&p1);
-                *reinterpret_cast<uint2 *>(stage + kb * TC_KB_BYTES + tc::swz128_offset(row, kin)) = pk;
             }
-            for (int o = 16; o > 0; o >>= 1)
-                part += __shfl_xor_sync(FULL_MASK, part, o);
-            if (lane == 0)
-                nrm[row] = (k0 == 0 ? 0.f : nrm[row]) + part;
+            float part[TC_RB];
+#pragma unroll
+            for (int b = 0; b < TC_RB; b++) {
+                const int row = row0 + b * TC_WARPS;
+                part[b] = 0.f;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    part[b] = fmaf(v[b][e], v[b][e], part[b]);
+                    inexact |= !(v[b][e] == rintf(v[b][e]) && fabsf(v[b][e]) <= 255.f);
+                }
+                if (row < srows) {
+                    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[b][0], v[b][1]);
+                    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[b][2], v[b][3]);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<uint32_t *>(&p0);
+                    pk.y = *reinterpret_cast<uint32_t *>(&p1);
+                    *reinterpret_cast<uint2 *>(stage + kb * TC_KB_BYTES + tc::swz128_offset(row, kin)) = pk;
+                }
+            }
+            // lane l ends with the total of row row0 + (l / (32 / TC_RB)) TC_WARPS
+            const float tot = transpose_reduce<TC_RB>(part);
+            const int row = row0 + (lane / (32 / TC_RB)) * TC_WARPS;
+            if (lane % (32 / TC_RB) == 0 && row < srows)
+                nrm[row] = (k0 == 0 ? 0.f : nrm[row]) + tot;
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
@@ -192,13 +218,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     // ---- candidates of row tid (TMEM lane tid) ----
     if (!timed_out && 32 * w < sz) {
         const int row = tid;
-        const int gi_row = row < sz ? rid[row] : -1;
-        float thd = 0.f;
-        int thi = 0;
-        if (gi_row >= 0) {
-            thd = __ldcg(g_dist + (int64_t)gi_row * kappa + kappa - 1);
-            thi = __ldcg(g_idx + (int64_t)gi_row * kappa + kappa - 1);
-        }
         const float n_i = nrm[row];
         const float u = 1.0f / 256.0f;
         const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
@@ -248,9 +267,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
 // merge of the FP32 path.  Candidate ids arrive in ascending order.
 constexpr int MG_WARPS = 8;
 
+// per warp: candidate keys (TC_CAP), row and merged-row keys (kappa each), candidate ids and distances, dup bits
 __host__ __device__ inline size_t merge_warp_bytes(int kappa)
 {
-    return (sizeof(int) + sizeof(float)) * (size_t)(2 * TC_CAP + 2 * kappa) + 16;
+    return sizeof(uint64_t) * (size_t)(TC_CAP + 2 * kappa) + (sizeof(int) + sizeof(float)) * TC_CAP + 16;
 }
 
 __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__restrict__ X, int64_t n, int d,
@@ -264,15 +284,12 @@ __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = lane_id();
     unsigned char *wb = smem_raw + (size_t)w * merge_warp_bytes(kappa);
-    int *cid = reinterpret_cast<int *>(wb);
+    uint64_t *bk = reinterpret_cast<uint64_t *>(wb);
+    uint64_t *rk = bk + TC_CAP;
+    uint64_t *nk = rk + kappa;
+    int *cid = reinterpret_cast<int *>(nk + kappa);
     float *cdv = reinterpret_cast<float *>(cid + TC_CAP);
-    int *bi = reinterpret_cast<int *>(cdv + TC_CAP);
-    float *bv = reinterpret_cast<float *>(bi + TC_CAP);
-    int *li = reinterpret_cast<int *>(bv + TC_CAP);
-    float *lv = reinterpret_cast<float *>(li + kappa);
-    int *ni = reinterpret_cast<int *>(lv + kappa);
-    float *nv = reinterpret_cast<float *>(ni + kappa);
-    unsigned *dup = reinterpret_cast<unsigned *>(nv + kappa);
+    unsigned *dup = reinterpret_cast<unsigned *>(cdv + TC_CAP);
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     for (int64_t i = (int64_t)blockIdx.x * MG_WARPS + w; i < n; i += (int64_t)gridDim.x * MG_WARPS) {
@@ -292,8 +309,7 @@ __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__r
             cdv[q] = dv;
         }
         __syncwarp();
-        merge_row((int)i, cid, cdv, cnt, kappa, cur, g_idx + i * kappa, g_dist + i * kappa, li, lv, bi, bv, ni, nv,
-                  dup);
+        merge_row((int)i, cid, cdv, cnt, kappa, cur, g_idx + i * kappa, g_dist + i * kappa, rk, bk, nk, dup);
         __syncwarp();
     }
 }
