@@ -46,7 +46,14 @@ constexpr uint32_t TC_WAIT_ITERS = 1u << 22;
 constexpr unsigned TC_RERANK = 0x80000000u;  // candidate id flag: distance needs the exact recompute
 
 constexpr size_t TC_STAGE = (size_t)TC_KCH * TC_KB_BYTES;
-constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) * TC_M + sizeof(int) * TC_M + 64;
+constexpr size_t TC_BUF = (size_t)2 * TC_M * 32 * sizeof(int);  // ids and distances of one 32-column chunk
+static_assert(TC_BUF <= TC_STAGE, "the epilogue's candidate buffers reuse the staging area");
+constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) * TC_M + sizeof(int) * TC_M * 3 + 64;
+
+// Slot of entry m (< 32) of row r in the candidate buffers: rows of 32 words
+// with the entry index xor-ed by r % 32, so the 32 rows of a warp writing
+// their m-th entries, and a warp reading one row, touch 32 distinct banks.
+__device__ __forceinline__ int buf_slot(int r, int m) { return r * 32 + (m ^ (r & 31)); }
 
 __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restrict__ X, int64_t n, int d,
                                                             int64_t ld, const int32_t *__restrict__ off,
@@ -64,7 +71,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     float *nrm = reinterpret_cast<float *>(stage + TC_STAGE);
     int *rid = reinterpret_cast<int *>(nrm + TC_M);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(rid + TC_M);
+    int *bcnt = rid + TC_M;   // candidates of each row in the current chunk
+    int *btot = bcnt + TC_M;  // candidates of each row written so far
+    uint64_t *bar = reinterpret_cast<uint64_t *>(btot + TC_M);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *flags = reinterpret_cast<int *>(tslot + 1);  // [0] not exact, [1] timeout
     const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
@@ -215,17 +224,22 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     // integer run with |x| <= 255: exact only while 2 d 255^2 < 2^24
     const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
 
-    // ---- candidates of row tid (TMEM lane tid) ----
-    if (!timed_out && 32 * w < sz) {
-        const int row = tid;
-        const float n_i = nrm[row];
-        const float u = 1.0f / 256.0f;
-        const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
-        const float c2 = 1.02f * (d + 8) * 1.1920929e-7f;
-        int32_t *oid = cand_id + (int64_t)(gi_row >= 0 ? gi_row : 0) * TC_CAP;
-        float *od = cand_d + (int64_t)(gi_row >= 0 ? gi_row : 0) * TC_CAP;
-        int cnt = 0;
-        for (int c0 = 0; c0 < N; c0 += 32) {
+    // ---- candidates of row tid (TMEM lane tid), 32 columns at a time ----
+    // Each thread collects its row's candidates of the chunk in shared memory
+    // (the staging area is free once the MMAs completed); then each warp writes
+    // whole row segments to the global lists, so that the stores coalesce.
+    int *bid = reinterpret_cast<int *>(stage);
+    float *bdv = reinterpret_cast<float *>(bid + TC_M * 32);
+    const bool rows_here = !timed_out && 32 * w < sz;  // warp-uniform
+    const int row = tid;
+    const float n_i = nrm[row];
+    const float u = 1.0f / 256.0f;
+    const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
+    const float c2 = 1.02f * (d + 8) * 1.1920929e-7f;
+    btot[tid] = 0;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        int m = 0;
+        if (rows_here) {
             float g[32];
             tc::tmem_ld32(taddr + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, g);
             tc::tmem_ld_wait();
@@ -246,17 +260,33 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
                             tag = TC_RERANK;
                         }
                         if (keep && jid >= 0) {
-                            oid[cnt] = (int32_t)((unsigned)jid | tag);
-                            od[cnt] = d2;
-                            cnt++;
+                            bid[buf_slot(row, m)] = (int)((unsigned)jid | tag);
+                            bdv[buf_slot(row, m)] = d2;
+                            m++;
                         }
                     }
                 }
             }
         }
-        if (gi_row >= 0)
-            cand_n[gi_row] = cnt;
+        bcnt[tid] = m;
+        __syncthreads();
+        for (int r2 = w; r2 < sz; r2 += TC_WARPS) {
+            const int mr = bcnt[r2], g2 = rid[r2];
+            if (mr == 0 || g2 < 0)
+                continue;
+            const int base = btot[r2];
+            if (lane < mr) {
+                cand_id[(int64_t)g2 * TC_CAP + base + lane] = bid[buf_slot(r2, lane)];
+                cand_d[(int64_t)g2 * TC_CAP + base + lane] = bdv[buf_slot(r2, lane)];
+            }
+            __syncwarp();
+            if (lane == 0)
+                btot[r2] = base + mr;
+        }
+        __syncthreads();
     }
+    if (rows_here && gi_row >= 0)
+        cand_n[gi_row] = btot[tid];
     tc::fence_before_sync();
     __syncthreads();
     if (w == 0)
