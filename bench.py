@@ -57,6 +57,10 @@ def parse():
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
                          "BF16/tensor-core screening in the assignment (all give the same results)")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--traffic-from", metavar="CSV",
+                    help="no GPU run: read an ncu --csv log with dram__bytes_read.sum, dram__bytes_write.sum and "
+                         "gpu__time_duration.sum of this workload's kernels and record the per-launch means in "
+                         "profiles/traffic.json, tagged with the current kernel sources")
     return ap.parse_args()
 
 
@@ -250,15 +254,61 @@ def kernel_of(tag, precision=1):
             "init_graph": "k_init_graph"}[tag]
 
 
-def source_sha(tag, precision=1):
-    f = {"assign": "assign.cu", "update": "update.cu", "group": "group.cu", "refine": "refine.cu",
-         "init_graph": "init.cu"}[tag]
-    if tag == "refine" and precision >= 1:
-        f = "refine_tc.cu"
-    if tag == "assign" and precision == 2:
-        f = "assign_tc.cu"
+# source file of each kernel whose DRAM traffic is recorded
+KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_tc": "assign_tc.cu", "k_update": "update.cu",
+                 "k_radix_scatter": "group.cu", "k_refine": "refine.cu", "k_refine_gram": "refine_tc.cu",
+                 "k_refine_merge": "refine_tc.cu", "k_init_graph": "init.cu"}
+
+
+def file_sha(f):
     with open(os.path.join(ROOT, "paper_1705_01813_gb300", "csrc", f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def source_sha(tag, precision=1):
+    return file_sha(KERNEL_SOURCE[kernel_of(tag, precision)])
+
+
+def write_traffic(csv_path, workload):
+    """Per-launch DRAM bytes and ncu durations of the listed kernels from an ncu --csv log."""
+    import csv
+    import io
+    import re
+    with open(csv_path, errors="replace") as f:
+        lines = [ln for ln in f.read().splitlines() if ln.startswith('"')]
+    rows = list(csv.reader(io.StringIO("\n".join(lines))))
+    h = rows[0]
+    ki, ii, mi, ui, vi = (h.index(c) for c in ("Kernel Name", "ID", "Metric Name", "Metric Unit", "Metric Value"))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-3, "us": 1, "usecond": 1,
+             "nsecond": 1e-3, "ms": 1e3, "msecond": 1e3}
+    per = {}
+    for r in rows[1:]:
+        m = re.match(r"(?:void )?(?:gkm::)?(\w+)", r[ki])
+        name = m.group(1) if m else r[ki]
+        if name not in KERNEL_SOURCE:
+            continue
+        v = float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+        per.setdefault(name, {}).setdefault(r[ii], {})[r[mi]] = v
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    j = {}
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+    for name, launches in per.items():
+        ls = [m for m in launches.values() if "dram__bytes_read.sum" in m and "dram__bytes_write.sum" in m]
+        if not ls:
+            continue
+        rd = sum(m["dram__bytes_read.sum"] for m in ls) / len(ls)
+        wr = sum(m["dram__bytes_write.sum"] for m in ls) / len(ls)
+        us = [m["gpu__time_duration.sum"] for m in ls if "gpu__time_duration.sum" in m]
+        j[f"{name}:{workload}"] = {"dram_bytes_per_launch": int(rd + wr), "read": int(rd), "write": int(wr),
+                                   "launches": len(ls),
+                                   "ncu_us_per_launch": round(sum(us) / len(us), 1) if us else None,
+                                   "source_sha": file_sha(KERNEL_SOURCE[name])}
+    with open(p, "w") as f:
+        json.dump(j, f, indent=1)
+        f.write("\n")
+    print(json.dumps({k: v["dram_bytes_per_launch"] for k, v in j.items() if not k.startswith("_")}, indent=1))
 
 
 def ncu_traffic(tag, workload, precision=1):
@@ -503,7 +553,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.traffic_from:
+        write_traffic(args.traffic_from, args.workload)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
