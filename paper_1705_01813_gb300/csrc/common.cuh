@@ -93,6 +93,27 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned, L2 only),
+// grouping of the copies issued so far, and waits on the groups.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    cp_async_commit();
+    cp_async_wait<0>();
+}
+
 }  // namespace gkm
 
 // ---- host-side launch helpers (internal) ---------------------------------

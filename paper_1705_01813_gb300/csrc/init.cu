@@ -28,19 +28,6 @@ cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *lab
 // first kappa - got kept draws are used, which is exactly the sequential
 // rejection rule.  Each lane then computes the FP32 distance of one neighbour
 // (pair_d2_seq), and the row is sorted by (distance, id) by ranking.
-// 16-byte asynchronous copy global -> shared (both 16-byte aligned), and the wait for all of them.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
-                 "l"(gmem_src)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 constexpr int IG_WARPS = 4;
 constexpr int IG_DC = 128;  // coordinates staged per step (vector path)
 

@@ -3,17 +3,20 @@
 // D_r of Eq. 2 and the distortion after the update from the Eq. 2 identity
 //     n E = sum_i ||x_i||^2 - sum_r D_r'D_r / n_r.
 //
-// One warp per cluster.  The warp is split into G groups of L lanes
-// (L = lanes needed to cover a row with VEC-wide loads, at most 32); group g
-// sums members g, g + G, ... and lane s of a group owns row columns
-// s, s + L, ... (in VEC-wide vectors).  Sums are compensated (Kahan) FP32,
-// widened to FP64 before groups are combined, so the composite vectors keep
-// about FP64 accuracy without FP64 arithmetic per element.
+// One block per cluster; each warp is split into G groups of L lanes
+// (L = lanes needed to cover a row with VEC-wide loads, at most 32); a group
+// sums every (warps x G)-th member and lane s of a group owns row columns
+// s, s + L, ... (in VEC-wide vectors).  Sums are compensated (Kahan) FP32 and
+// combined as exact double-float pairs, so the composite vectors keep the
+// accuracy of the compensated sums with FP32 arithmetic only; FP64 appears
+// once per cluster, in the distortion term.
 #include "common.cuh"
 
 namespace gkm {
 
 constexpr int UP_WARPS = 4;
+constexpr int UP_MCHUNK = 1024;  // member ids staged in shared memory at a time
+constexpr int UP_R = 8;          // rows per pipeline stage of a group (PIPE kernels)
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {
@@ -22,6 +25,53 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     c = (t - s) - y;
     s = t;
 }
+
+// Double-float values (hi + lo, two FP32 numbers) and the error-free
+// transformations that add them (Knuth's two-sum, Dekker's fast two-sum):
+// cross-group and cross-warp combination, squares and the mean are done in
+// FP32 arithmetic with about 44 bits of precision, which keeps the Kahan sums
+// exact and spares the GPU's slow FP64 units.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b)  // |a| >= |b| or a == 0
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return fast_two_sum(s, e + a.lo + b.lo);
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o)
+{
+    return {__shfl_xor_sync(FULL_MASK, a.hi, o), __shfl_xor_sync(FULL_MASK, a.lo, o)};
+}
+
+// a^2 (the lo^2 term is below the pair's precision)
+__device__ __forceinline__ DF df_sqr(DF a)
+{
+    const float p = a.hi * a.hi;
+    const float e = fmaf(a.hi, a.hi, -p);
+    return fast_two_sum(p, fmaf(2.f * a.hi, a.lo, e));
+}
+
+// a / m rounded to FP32: q = a.hi / m (IEEE), whose remainder a.hi - q m is
+// exact in one fma, corrected by (remainder + a.lo) / m.
+__device__ __forceinline__ float df_div(DF a, float mf, float inv_m)
+{
+    const float q = a.hi / mf;
+    const float r = fmaf(-q, mf, a.hi) + a.lo;
+    return q + r * inv_m;
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
 template <int VEC>
 struct VecT;
@@ -64,9 +114,13 @@ __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL]
 // of L lanes; the W * G groups of the block take members g, g + W G, ... of
 // the cluster (UNR of them in flight per group), and lane s of a group owns
 // row vectors s, s + L, ... (CPL of them per column block).  Group sums are
-// widened to FP64, combined across the groups of a warp by shuffles and across
+// combined (double-float) across the groups of a warp by shuffles and across
 // the warps through shared memory in a fixed order (reproducible bits).
-template <int VEC, int CPL>
+// PIPE (16-byte vectors, one per lane, i.e. rows of at most 128 floats): the
+// member rows are streamed into a two-stage shared-memory ring with cp.async,
+// UP_R rows per group and stage, so the next stage's loads are in flight while
+// the current one is summed; the summation order is the same.
+template <int VEC, int CPL, bool PIPE>
 __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restrict__ X, int d, int64_t ld,
                                                           const int32_t *__restrict__ off,
                                                           const int32_t *__restrict__ mem, int k,
@@ -74,9 +128,12 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                                                           double *__restrict__ contrib)
 {
     using V = typename VecT<VEC>::T;
-    constexpr int UNR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : 4);  // member rows in flight per group
-    __shared__ double s_part[UP_WARPS][32 * CPL * VEC];
-    __shared__ double s_sq[UP_WARPS];
+    constexpr int UNR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : (CPL >= 2 ? 4 : 4));  // member rows in flight per group
+    __shared__ float2 s_part[UP_WARPS][32 * CPL * VEC];
+    __shared__ float2 s_sq[UP_WARPS], s_dd[UP_WARPS];
+    __shared__ int s_mem[UP_MCHUNK];
+    __shared__ __align__(16) float4 s_rows[PIPE ? UP_WARPS * 2 * UP_R * 32 : 1];
+    static_assert(!PIPE || (VEC == 4 && CPL == 1), "the pipelined variant covers one 16-byte vector per lane");
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const int nv = d / VEC;  // vectors per row
     int L = 1;
@@ -99,7 +156,8 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
             contrib[r] = 0.0;
         return;
     }
-    double sq_lane = 0.0, dd_lane = 0.0;
+    const float mf = (float)m, inv_m = 1.0f / mf;
+    DF sq_lane = {0.f, 0.f}, dd_lane = {0.f, 0.f};
     for (int cb = 0; cb < nv; cb += L * CPL) {
         float s[CPL][VEC], c[CPL][VEC];
         float qs = 0.f, qc = 0.f;
@@ -108,37 +166,82 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
 #pragma unroll
             for (int q = 0; q < VEC; q++)
                 s[u][q] = c[u][q] = 0.f;
-        for (int p0 = gidx; p0 < m; p0 += UNR * gstride) {
-            V v[UNR][CPL];
+        // the member ids of a chunk are staged in shared memory first, so each row
+        // load waits for one memory round trip instead of two
+        for (int mb = 0; mb < m; mb += UP_MCHUNK) {
+            const int mc = min(UP_MCHUNK, m - mb);
+            __syncthreads();  // the previous chunk's ids are no longer read
+            for (int q = threadIdx.x; q < mc; q += UP_WARPS * 32)
+                s_mem[q] = __ldg(mem + beg + mb + q);
+            __syncthreads();
+            if constexpr (PIPE) {
+                float4 *ring = s_rows + w * (2 * UP_R * 32);  // [stage][row][lane]
+                const int wlead = w * G;                       // the warp's first group has the most rows
+                const int njw = mc > wlead ? (mc - wlead + gstride - 1) / gstride : 0;
+                const int nst = (njw + UP_R - 1) / UP_R;
+                auto issue = [&](int t) {
+                    float4 *buf = ring + (t & 1) * (UP_R * 32);
 #pragma unroll
-            for (int z = 0; z < UNR; z++) {
-                const int p = p0 + z * gstride;
-                if (p < m) {
-                    const V *row = Xv + (int64_t)__ldg(mem + beg + p) * ldv;
+                    for (int z = 0; z < UP_R; z++) {
+                        const int p = gidx + gstride * (t * UP_R + z);
+                        if (p < mc && sub < nv)
+                            cp_async16(buf + z * 32 + lane, Xv + (int64_t)s_mem[p] * ldv + sub);
+                    }
+                    cp_async_commit();
+                };
+                if (nst > 0)
+                    issue(0);
+                for (int t = 0; t < nst; t++) {
+                    if (t + 1 < nst)
+                        issue(t + 1);
+                    else
+                        cp_async_commit();  // empty group: the wait below always leaves one
+                    cp_async_wait<1>();
+                    __syncwarp();
+                    const float4 *buf = ring + (t & 1) * (UP_R * 32);
 #pragma unroll
-                    for (int u = 0; u < CPL; u++) {
-                        const int col = cb + sub + u * L;
-                        if (col < nv)
-                            v[z][u] = __ldcs(row + col);
+                    for (int z = 0; z < UP_R; z++) {
+                        if (gidx + gstride * (t * UP_R + z) < mc) {
+                            const V v1[1] = {buf[z * 32 + lane]};
+                            accumulate<VEC, CPL>(v1, s, c, qs, qc, cb, sub, L, nv);
+                        }
+                    }
+                    __syncwarp();  // stage t & 1 is refilled by issue(t + 2)
+                }
+                continue;
+            }
+            for (int p0 = gidx; p0 < mc; p0 += UNR * gstride) {
+                V v[UNR][CPL];
+#pragma unroll
+                for (int z = 0; z < UNR; z++) {
+                    const int p = p0 + z * gstride;
+                    if (p < mc) {
+                        const V *row = Xv + (int64_t)s_mem[p] * ldv;
+#pragma unroll
+                        for (int u = 0; u < CPL; u++) {
+                            const int col = cb + sub + u * L;
+                            if (col < nv)
+                                v[z][u] = __ldcs(row + col);
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int z = 0; z < UNR; z++)
-                if (p0 + z * gstride < m)
-                    accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
+                for (int z = 0; z < UNR; z++)
+                    if (p0 + z * gstride < mc)
+                        accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
+            }
         }
-        sq_lane += (double)qs - (double)qc;
-        // widen, combine the G groups of the warp, then the warps of the block
+        sq_lane = df_add(sq_lane, fast_two_sum(qs, -qc));
+        // combine the G groups of the warp, then the warps of the block, in a fixed order
 #pragma unroll
         for (int u = 0; u < CPL; u++) {
 #pragma unroll
             for (int q = 0; q < VEC; q++) {
-                double S = (double)s[u][q] - (double)c[u][q];
+                DF S = fast_two_sum(s[u][q], -c[u][q]);  // the Kahan sum s - c, exactly
                 for (int o = L; o < 32; o <<= 1)
-                    S += __shfl_xor_sync(FULL_MASK, S, o);
+                    S = df_add(S, df_shfl_xor(S, o));
                 if (g == 0)
-                    s_part[w][(u * L + sub) * VEC + q] = S;
+                    s_part[w][(u * L + sub) * VEC + q] = make_float2(S.hi, S.lo);
             }
         }
         __syncthreads();
@@ -147,32 +250,32 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
             const int u = (e / VEC) / L, sb = (e / VEC) % L;
             const int colv = cb + sb + u * L;
             if (colv < nv) {
-                double S = 0.0;
-                for (int ww = 0; ww < UP_WARPS; ww++)
-                    S += s_part[ww][e];
-                C[(int64_t)r * d + (int64_t)colv * VEC + (e % VEC)] = (float)(S / (double)m);
-                dd_lane += S * S;
+                DF S = {s_part[0][e].x, s_part[0][e].y};
+                for (int ww = 1; ww < UP_WARPS; ww++)
+                    S = df_add(S, DF{s_part[ww][e].x, s_part[ww][e].y});
+                C[(int64_t)r * d + (int64_t)colv * VEC + (e % VEC)] = df_div(S, mf, inv_m);
+                dd_lane = df_add(dd_lane, df_sqr(S));
             }
         }
         __syncthreads();
     }
     // sum of ||x||^2 over all lanes, sum of D_t^2 over the threads that wrote means
     for (int o = 1; o < 32; o <<= 1) {
-        sq_lane += __shfl_xor_sync(FULL_MASK, sq_lane, o);
-        dd_lane += __shfl_xor_sync(FULL_MASK, dd_lane, o);
+        sq_lane = df_add(sq_lane, df_shfl_xor(sq_lane, o));
+        dd_lane = df_add(dd_lane, df_shfl_xor(dd_lane, o));
     }
     if (lane == 0) {
-        s_sq[w] = sq_lane;
-        s_part[w][0] = dd_lane;
+        s_sq[w] = make_float2(sq_lane.hi, sq_lane.lo);
+        s_dd[w] = make_float2(dd_lane.hi, dd_lane.lo);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sq = 0.0, dd = 0.0;
-        for (int ww = 0; ww < UP_WARPS; ww++) {
-            sq += s_sq[ww];
-            dd += s_part[ww][0];
+        DF sq = {s_sq[0].x, s_sq[0].y}, dd = {s_dd[0].x, s_dd[0].y};
+        for (int ww = 1; ww < UP_WARPS; ww++) {
+            sq = df_add(sq, DF{s_sq[ww].x, s_sq[ww].y});
+            dd = df_add(dd, DF{s_dd[ww].x, s_dd[ww].y});
         }
-        contrib[r] = sq - dd / (double)m;
+        contrib[r] = df_to_double(sq) - df_to_double(dd) / (double)m;
     }
 }
 
@@ -211,10 +314,10 @@ cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, cons
     const unsigned grid = (unsigned)blocks;
     const int dd = (int)d;
 #define GK_UPD(VEC, CPL) \
-    k_update<VEC, CPL><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib)
+    k_update<VEC, CPL, false><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib)
     if (vec4) {
         if (need <= 1)
-            GK_UPD(4, 1);
+            k_update<4, 1, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
         else if (need <= 2)
             GK_UPD(4, 2);
         else if (need <= 4)
