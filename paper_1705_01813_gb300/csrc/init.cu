@@ -2,6 +2,8 @@
 // (Alg. 3 starts from a graph of random neighbour lists).  Random numbers come from the
 // SplitMix64 generator used as a counter-based function (common.cuh).
 #include "common.cuh"
+#include "merge.cuh"
+#include "tc.cuh"
 
 namespace gkm {
 
@@ -30,20 +32,63 @@ cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *lab
 // (pair_d2_seq), and the row is sorted by (distance, id) by ranking.
 constexpr int IG_WARPS = 4;
 constexpr int IG_DC = 128;  // coordinates staged per step (vector path)
+constexpr uint32_t IG_WAIT_ITERS = 1u << 22;
 
-__global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__restrict__ X, int64_t n, int d,
-                                                              int64_t ld, int kappa, uint64_t key,
+// Rows staged per batch: kappa cut into equal batches of at most 32.
+__host__ __device__ inline int ig_batch(int kappa)
+{
+    const int nb = (kappa + 31) / 32;
+    return (kappa + nb - 1) / nb;
+}
+
+// Dynamic shared memory per warp: on the vector path a batch of rows, each
+// padded by 16 bytes so that the 32 lanes reading one row each hit distinct
+// banks; on both paths at least the kappa 8-byte keys of the rank sort (they
+// reuse the area).  Kernel and launcher both size the warp areas with this.
+__host__ __device__ inline size_t ig_warp_bytes(int kappa, bool vec4)
+{
+    size_t b = vec4 ? sizeof(float) * (size_t)ig_batch(kappa) * (IG_DC + 4) : 0;
+    if (b < sizeof(uint64_t) * (size_t)kappa)
+        b = sizeof(uint64_t) * (size_t)kappa;
+    return (b + 15) & ~size_t(15);
+}
+
+// Exact a mod n for 0 < n < 2^32 with minv = floor((2^64 - 1) / n): the
+// quotient estimate q = floor(a minv / 2^64) lies in [floor(a/n) - 2, floor(a/n)],
+// so at most two subtractions finish the remainder (Barrett reduction).
+__device__ __forceinline__ uint64_t mod_n(uint64_t a, uint64_t n, uint64_t minv)
+{
+    const uint64_t q = __umul64hi(a, minv);
+    uint64_t r = a - q * n;
+    if (r >= n)
+        r -= n;
+    if (r >= n)
+        r -= n;
+    return r;
+}
+
+__global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__restrict__ X, int64_t n, int d,
+                                                              int64_t ld, int kappa, uint64_t key, uint64_t minv,
                                                               int32_t *__restrict__ g_idx,
                                                               float *__restrict__ g_dist, DevStatus *st,
                                                               bool vec4)
 {
     __shared__ int s_idx[IG_WARPS][MAX_KAPPA];
-    __shared__ float s_dist[IG_WARPS][MAX_KAPPA];
-    // dynamic: per warp IG_DC floats of x_i, then 32 staged rows of IG_DC + 4 floats
+    __shared__ uint64_t s_bar[IG_WARPS];
+    // dynamic: per warp one batch of staged rows; after the distances, the row's keys
     extern __shared__ __align__(16) float s_dyn[];
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *ridx = s_idx[w];
-    float *rdist = s_dist[w];
+    const int B = ig_batch(kappa);
+    float *rows = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s_dyn) + (size_t)w * ig_warp_bytes(kappa, vec4));
+    uint64_t *rkey = reinterpret_cast<uint64_t *>(rows);
+    uint64_t *bar = s_bar + w;
+    if (lane == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t phase = 0;
     for (int64_t i = blockIdx.x * (int64_t)IG_WARPS + w; i < n; i += (int64_t)gridDim.x * IG_WARPS) {
         int got = 0;
         for (uint64_t a0 = 0; got < kappa; a0 += 32) {
@@ -57,7 +102,7 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
                 break;
             }
             uint64_t a = a0 + (uint64_t)lane;
-            int64_t j = (int64_t)(sm64_draw(key, ((uint64_t)i << 32) | a) % (uint64_t)n);
+            int64_t j = (int64_t)mod_n(sm64_draw(key, ((uint64_t)i << 32) | a), (uint64_t)n, minv);
             unsigned peers = __match_any_sync(FULL_MASK, (unsigned long long)j);
             bool ok = (j != i) && ((peers & lanemask_lt()) == 0u);
             if (ok)
@@ -75,60 +120,79 @@ __global__ void __launch_bounds__(IG_WARPS * 32) k_init_graph(const float *__res
             __syncwarp();
         }
         const float *xi = X + i * ld;
+        float dist[(MAX_KAPPA + 31) / 32];  // distance of neighbour b0 + lane of batch b (lane < batch size)
         if (vec4) {
-            // neighbour rows staged 32 at a time, IG_DC coordinates at a time, with
-            // one coalesced 16-byte load per lane and row; lane q then sums its
-            // row's squared differences in ascending coordinate order (the order
-            // of pair_d2_seq) from shared memory
-            float *xs = s_dyn + w * (IG_DC + 32 * (IG_DC + 4));
-            float *rows = xs + IG_DC;
-            for (int b0 = 0; b0 < kappa; b0 += 32) {
-                const int nb = min(32, kappa - b0);
+            // A batch's neighbour rows are copied to shared memory by the TMA engine
+            // (one bulk copy per row, issued by the row's lane, counted on the warp's
+            // mbarrier); lane q then sums its row's squared differences in ascending
+            // coordinate order (the order of pair_d2_seq), x_i coming through L1.
+            const float2 m1 = make_float2(-1.f, -1.f);
+            for (int b0 = 0, bi = 0; b0 < kappa; b0 += B, bi++) {
+                const int nb = min(B, kappa - b0);
                 float acc = 0.f;
                 for (int t0 = 0; t0 < d; t0 += IG_DC) {
                     const int dc = min(IG_DC, d - t0);
+                    __syncwarp();                 // the previous rows are no longer read
+                    tc::fence_proxy_async_smem();  // ... before the async proxy rewrites them
+                    if (lane == 0)
+                        tc::mbar_arrive_expect_tx(bar, (uint32_t)(nb * dc * 4));
                     __syncwarp();
-                    for (int t = lane * 4; t < dc; t += 128)
-                        *reinterpret_cast<float4 *>(xs + t) = *reinterpret_cast<const float4 *>(xi + t0 + t);
-                    // every row of the batch in flight at once (asynchronous copies to shared memory)
-                    for (int q = 0; q < nb; q++) {
-                        const float *src = X + (int64_t)ridx[b0 + q] * ld + t0;
-                        for (int t = lane * 4; t < dc; t += 128)
-                            cp_async16(rows + q * (IG_DC + 4) + t, src + t);
+                    if (lane < nb)
+                        tc::bulk_g2s(rows + lane * (IG_DC + 4), X + (int64_t)ridx[b0 + lane] * ld + t0,
+                                     (uint32_t)(dc * 4), bar);
+                    const bool ok = __all_sync(FULL_MASK, tc::mbar_wait_bounded(bar, phase, IG_WAIT_ITERS));
+                    phase ^= 1u;
+                    if (!ok) {  // the copies did not complete: report, give them one more bounded wait, stop
+                        if (lane == 0)
+                            flag_error(st, GK_ERR_TIMEOUT, (unsigned)i);
+                        tc::mbar_wait_bounded(bar, phase ^ 1u, IG_WAIT_ITERS);
+                        return;
                     }
-                    cp_async_wait_all();
-                    __syncwarp();
                     if (lane < nb) {
-                        const float *myrow = rows + lane * (IG_DC + 4);
-                        for (int t = 0; t < dc; t += 4) {
-                            float4 a = *reinterpret_cast<const float4 *>(xs + t);
-                            float4 b = *reinterpret_cast<const float4 *>(myrow + t);
-                            float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
-                            acc = fmaf(e0, e0, acc);
-                            acc = fmaf(e1, e1, acc);
-                            acc = fmaf(e2, e2, acc);
-                            acc = fmaf(e3, e3, acc);
+                        const float4 *xa = reinterpret_cast<const float4 *>(xi + t0);
+                        const float4 *xb = reinterpret_cast<const float4 *>(rows + lane * (IG_DC + 4));
+                        for (int t = 0; t < dc / 4; t++) {
+                            const float4 va = __ldg(xa + t), vb = xb[t];
+                            const float2 e01 = __ffma2_rn(make_float2(vb.x, vb.y), m1, make_float2(va.x, va.y));
+                            const float2 e23 = __ffma2_rn(make_float2(vb.z, vb.w), m1, make_float2(va.z, va.w));
+                            acc = fmaf(e01.x, e01.x, acc);
+                            acc = fmaf(e01.y, e01.y, acc);
+                            acc = fmaf(e23.x, e23.x, acc);
+                            acc = fmaf(e23.y, e23.y, acc);
                         }
                     }
                 }
-                if (lane < nb)
-                    rdist[b0 + lane] = acc;
+#pragma unroll
+                for (int q = 0; q < (MAX_KAPPA + 31) / 32; q++)
+                    if (q == bi)
+                        dist[q] = acc;
             }
         } else {
-            for (int q = lane; q < kappa; q += 32)
-                rdist[q] = pair_d2_seq(xi, X + (int64_t)ridx[q] * ld, d);
+            for (int b0 = 0, bi = 0; b0 < kappa; b0 += B, bi++) {
+                const float acc = lane < min(B, kappa - b0) ? pair_d2_seq(xi, X + (int64_t)ridx[b0 + lane] * ld, d) : 0.f;
+#pragma unroll
+                for (int q = 0; q < (MAX_KAPPA + 31) / 32; q++)
+                    if (q == bi)
+                        dist[q] = acc;
+            }
         }
         __syncwarp();
-        // rank sort: ids in a row are distinct, so keys are distinct
-        int64_t out = i * (int64_t)kappa;
+        // rank sort on packed (distance, id) keys: ids in a row are distinct, so keys are
+#pragma unroll
+        for (int q = 0; q < (MAX_KAPPA + 31) / 32; q++) {
+            const int e = q * B + lane;
+            if (lane < B && e < kappa)
+                rkey[e] = pack_key(dist[q], ridx[e]);
+        }
+        __syncwarp();
+        const int64_t out = i * (int64_t)kappa;
         for (int q = lane; q < kappa; q += 32) {
-            float dq = rdist[q];
-            int iq = ridx[q];
+            const uint64_t kq = rkey[q];
             int r = 0;
             for (int p = 0; p < kappa; p++)
-                r += key_less(rdist[p], ridx[p], dq, iq) ? 1 : 0;
-            g_idx[out + r] = iq;
-            g_dist[out + r] = dq;
+                r += rkey[p] < kq ? 1 : 0;
+            g_idx[out + r] = key_id(kq);
+            g_dist[out + r] = key_dist(kq);
         }
         __syncwarp();
     }
@@ -141,13 +205,12 @@ cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
     if (blocks > 152 * 64)
         blocks = 152 * 64;
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    const size_t shm = vec4 ? sizeof(float) * IG_WARPS * (IG_DC + 32 * (IG_DC + 4)) : 0;
-    if (shm) {
-        cudaError_t e = cudaFuncSetAttribute(k_init_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (e != cudaSuccess)
-            return e;
-    }
-    k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, g_idx,
+    const size_t shm = IG_WARPS * ig_warp_bytes(kappa, vec4);
+    cudaError_t e = cudaFuncSetAttribute(k_init_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t minv = ~0ull / (uint64_t)n;
+    k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, minv, g_idx,
                                                            g_dist, st, vec4);
     return cudaGetLastError();
 }

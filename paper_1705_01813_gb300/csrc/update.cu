@@ -208,27 +208,27 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                     }
                     __syncwarp();  // stage t & 1 is refilled by issue(t + 2)
                 }
-                continue;
-            }
-            for (int p0 = gidx; p0 < mc; p0 += UNR * gstride) {
-                V v[UNR][CPL];
+            } else {
+                for (int p0 = gidx; p0 < mc; p0 += UNR * gstride) {
+                    V v[UNR][CPL];
 #pragma unroll
-                for (int z = 0; z < UNR; z++) {
-                    const int p = p0 + z * gstride;
-                    if (p < mc) {
-                        const V *row = Xv + (int64_t)s_mem[p] * ldv;
+                    for (int z = 0; z < UNR; z++) {
+                        const int p = p0 + z * gstride;
+                        if (p < mc) {
+                            const V *row = Xv + (int64_t)s_mem[p] * ldv;
 #pragma unroll
-                        for (int u = 0; u < CPL; u++) {
-                            const int col = cb + sub + u * L;
-                            if (col < nv)
-                                v[z][u] = __ldcs(row + col);
+                            for (int u = 0; u < CPL; u++) {
+                                const int col = cb + sub + u * L;
+                                if (col < nv)
+                                    v[z][u] = __ldcs(row + col);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int z = 0; z < UNR; z++)
-                    if (p0 + z * gstride < mc)
-                        accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
+                    for (int z = 0; z < UNR; z++)
+                        if (p0 + z * gstride < mc)
+                            accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
+                }
             }
         }
         sq_lane = df_add(sq_lane, fast_two_sum(qs, -qc));
