@@ -40,8 +40,13 @@ from paper_1705_01813_gb300 import datagen  # noqa: E402
 
 METRIC = "assign-step samples/s and fit time vs plain FP32; serve jobs/s, p50/p99"
 DEFAULT_WORKLOAD = "sift_n1000000_d128_k10000"
-CPU_SAMPLE = 100_000        # cpu_baseline: oracle on the first 100k samples (about 10-30 s)
-REF_SAMPLE = 40_000         # --impl reference: oracle per step on the first 40k samples
+CPU_SAMPLE = 100_000        # cpu_baseline: oracle on the first 100k samples at d = 128 (about 10-30 s)
+REF_SAMPLE = 40_000         # --impl reference: oracle per step on the first 40k samples at d = 128
+
+
+def oracle_sample(w, base):
+    """Samples the oracle runs on: `base` at d = 128, fewer for wider rows (its time grows with d)."""
+    return min(w.n, max(2000, base * 128 // max(w.d, 1)))
 
 
 def parse():
@@ -166,8 +171,9 @@ class Path:
     def _ev(self):
         return self.torch.cuda.Event(enable_timing=True)
 
-    def step(self, rec=None):
-        """Whole path once; rec (list) receives (tag, start_event, end_event) per call."""
+    def step(self, rec=None, probe=None):
+        """Whole path once; rec (list) receives (tag, start_event, end_event) per call; probe(phase,
+        labels) is called with the labels the last assignment of each phase produced."""
         g, w, torch = self.gkm, self.w, self.torch
 
         def call(tag, fn, *a, **kw):
@@ -197,6 +203,8 @@ class Path:
             call("refine", g.graph_refine_groups, self.X, self.off, self.mem, self.k0, self.gi, self.gd,
                  w.max_cluster, self.precision, ws=ws)
             cur, nxt = nxt, cur
+        if probe:
+            probe("build", cur)
         # --- Alg. 2 (closest-centroid rule) at k on the constructed graph
         g.init_labels(n, w.k, w.seed + 1, out=self.la)
         self.C.zero_()
@@ -210,6 +218,15 @@ class Path:
             call("update", g.update_from_groups, self.X, self.off, self.mem, w.k, self.C, self.cnt, self.s[2:3],
                  ws=ws)
             cur, nxt = nxt, cur
+        if probe:
+            probe("fit", cur)
+
+    def mean_candidates(self, labels):
+        """u: mean number of distinct candidate clusters per sample ({L[i]} and the neighbours' labels)."""
+        torch = self.torch
+        labs = torch.cat([labels[:, None], labels[self.gi.long()]], 1)
+        srt, _ = torch.sort(labs, 1)
+        return float((1 + (srt[:, 1:] != srt[:, :-1]).sum(1)).double().mean())
 
 
 def _radix_passes(k):
@@ -245,8 +262,8 @@ def algorithmic_bytes(tag, w, k):
     return 0
 
 
-def kernel_of(tag, precision=1):
-    if tag == "refine" and precision >= 1:
+def kernel_of(tag, precision=1, d=128):
+    if tag == "refine" and precision >= 1 and d <= 128:  # the library's dispatch: tensor-core Gram for d <= 128
         return "k_refine_gram"
     if tag == "assign" and precision == 2:
         return "k_assign_tc"
@@ -265,8 +282,8 @@ def file_sha(f):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def source_sha(tag, precision=1):
-    return file_sha(KERNEL_SOURCE[kernel_of(tag, precision)])
+def source_sha(tag, precision=1, d=128):
+    return file_sha(KERNEL_SOURCE[kernel_of(tag, precision, d)])
 
 
 def write_traffic(csv_path, workload):
@@ -311,15 +328,15 @@ def write_traffic(csv_path, workload):
     print(json.dumps({k: v["dram_bytes_per_launch"] for k, v in j.items() if not k.startswith("_")}, indent=1))
 
 
-def ncu_traffic(tag, workload, precision=1):
+def ncu_traffic(tag, workload, precision=1, d=128):
     """DRAM bytes per launch from the committed ncu summary, if it is for the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
-    e = j.get(f"{kernel_of(tag, precision)}:{workload}")
-    if not e or e.get("source_sha") != source_sha(tag, precision):
+    e = j.get(f"{kernel_of(tag, precision, d)}:{workload}")
+    if not e or e.get("source_sha") != source_sha(tag, precision, d):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -340,8 +357,10 @@ def run_gpu(args):
     gkm.load()
 
     path = Path(gkm, torch, w, X, args.precision)
-    for _ in range(args.warmup):
-        path.step()
+    u = {}
+    for q in range(args.warmup):  # the last warm-up step also measures u (outside the timed region)
+        path.step(probe=(lambda ph, lab: u.__setitem__(ph, round(path.mean_candidates(lab), 2)))
+                  if q == args.warmup - 1 else None)
     torch.cuda.synchronize()
     if gkm.read_status(path.ws) != gkm.GK_OK:
         raise RuntimeError("device status error during warm-up")
@@ -479,11 +498,12 @@ def run_gpu(args):
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},
         "per_step_share": {t: round(v / sum(totals.values()), 4) for t, v in totals.items()},
-        "roofline": {"kernel": kernel_of(dom, args.precision), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": kernel_of(dom, args.precision, w.d), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": int(alg),
-                     "traffic": ncu_traffic(dom, w.name, args.precision)},
+                     "traffic": ncu_traffic(dom, w.name, args.precision, w.d)},
         "gpu_launches": launches_per_step(w, args.precision) * args.steps,
+        "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
         "e2e": e2e,
@@ -513,7 +533,7 @@ def _oracle_step(O, w, X, k_scale):
 
 def cpu_baseline(w, Xh):
     from oracle import oracle as O
-    ns = min(CPU_SAMPLE, w.n)
+    ns = oracle_sample(w, CPU_SAMPLE)
     X = np.ascontiguousarray(Xh[:ns])
     t0 = time.perf_counter()
     k = _oracle_step(O, w, X, True)
@@ -531,7 +551,7 @@ def run_reference(args):
     from oracle import oracle as O
     w = datagen.WORKLOADS[args.workload]
     Xh = w.data()
-    ns = min(REF_SAMPLE, w.n)
+    ns = oracle_sample(w, REF_SAMPLE)
     X = np.ascontiguousarray(Xh[:ns])
     for _ in range(args.warmup):
         _oracle_step(O, w, X, True)

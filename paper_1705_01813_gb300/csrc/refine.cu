@@ -226,7 +226,10 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     k_run_clusters<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(run_off, k, run_cl);
     // an upper bound of the number of runs: sum over clusters of (m / cap + 1)
     const int64_t grid = (int64_t)k + n / max_cluster + 1;
-    if (precision >= 1) {
+    // The BF16 Gram is exact only for integer data with 2 d 255^2 < 2^24 (d <= 128); otherwise every pair it
+    // keeps is recomputed in FP32 from the two full rows, which for d > 128 reads more than the FP32 tile
+    // kernels below (1M x 960: 91 ms against 25 ms per call), so precision >= 1 uses them there.
+    if (precision >= 1 && d <= 128) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
         if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, grid, g_idx,
                                   g_dist, tc_scratch, st, s)) != cudaSuccess)

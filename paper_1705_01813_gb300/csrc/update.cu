@@ -16,7 +16,7 @@ namespace gkm {
 
 constexpr int UP_WARPS = 4;
 constexpr int UP_MCHUNK = 1024;  // member ids staged in shared memory at a time
-constexpr int UP_R = 8;          // rows per pipeline stage of a group (PIPE kernels)
+constexpr int UP_RV = 8;         // 16-byte vectors per lane and pipeline stage (PIPE kernels): 8 / CPL rows
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {
@@ -116,10 +116,11 @@ __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL]
 // row vectors s, s + L, ... (CPL of them per column block).  Group sums are
 // combined (double-float) across the groups of a warp by shuffles and across
 // the warps through shared memory in a fixed order (reproducible bits).
-// PIPE (16-byte vectors, one per lane, i.e. rows of at most 128 floats): the
-// member rows are streamed into a two-stage shared-memory ring with cp.async,
-// UP_R rows per group and stage, so the next stage's loads are in flight while
-// the current one is summed; the summation order is the same.
+// PIPE (16-byte vectors): the member rows are streamed into a two-stage
+// shared-memory ring with cp.async, UP_RV / CPL rows per group and stage, so the
+// next stage's loads are in flight while the current one is summed; the
+// summation order is the same.  The ring shares its memory with the partial
+// sums of the epilogue, which run after it.
 template <int VEC, int CPL, bool PIPE>
 __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restrict__ X, int d, int64_t ld,
                                                           const int32_t *__restrict__ off,
@@ -129,11 +130,14 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
 {
     using V = typename VecT<VEC>::T;
     constexpr int UNR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : (CPL >= 2 ? 4 : 4));  // member rows in flight per group
-    __shared__ float2 s_part[UP_WARPS][32 * CPL * VEC];
+    constexpr int R = PIPE ? UP_RV / CPL : 1;  // rows per group and stage
+    constexpr size_t PART_BYTES = sizeof(float2) * UP_WARPS * 32 * CPL * VEC;
+    constexpr size_t RING_BYTES = PIPE ? sizeof(float4) * UP_WARPS * 2 * R * 32 * CPL : 0;
+    __shared__ __align__(16) unsigned char s_buf[PART_BYTES > RING_BYTES ? PART_BYTES : RING_BYTES];
+    auto s_part = reinterpret_cast<float2 (*)[32 * CPL * VEC]>(s_buf);
     __shared__ float2 s_sq[UP_WARPS], s_dd[UP_WARPS];
     __shared__ int s_mem[UP_MCHUNK];
-    __shared__ __align__(16) float4 s_rows[PIPE ? UP_WARPS * 2 * UP_R * 32 : 1];
-    static_assert(!PIPE || (VEC == 4 && CPL == 1), "the pipelined variant covers one 16-byte vector per lane");
+    static_assert(!PIPE || (VEC == 4 && UP_RV % CPL == 0), "the pipelined variant moves 16-byte vectors");
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const int nv = d / VEC;  // vectors per row
     int L = 1;
@@ -175,17 +179,24 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                 s_mem[q] = __ldg(mem + beg + mb + q);
             __syncthreads();
             if constexpr (PIPE) {
-                float4 *ring = s_rows + w * (2 * UP_R * 32);  // [stage][row][lane]
+                float4 *ring = reinterpret_cast<float4 *>(s_buf) + w * (2 * R * 32 * CPL);  // [stage][row][u][lane]
                 const int wlead = w * G;                       // the warp's first group has the most rows
                 const int njw = mc > wlead ? (mc - wlead + gstride - 1) / gstride : 0;
-                const int nst = (njw + UP_R - 1) / UP_R;
+                const int nst = (njw + R - 1) / R;
                 auto issue = [&](int t) {
-                    float4 *buf = ring + (t & 1) * (UP_R * 32);
+                    float4 *buf = ring + (t & 1) * (R * 32 * CPL);
 #pragma unroll
-                    for (int z = 0; z < UP_R; z++) {
-                        const int p = gidx + gstride * (t * UP_R + z);
-                        if (p < mc && sub < nv)
-                            cp_async16(buf + z * 32 + lane, Xv + (int64_t)s_mem[p] * ldv + sub);
+                    for (int z = 0; z < R; z++) {
+                        const int p = gidx + gstride * (t * R + z);
+                        if (p < mc) {
+                            const V *row = Xv + (int64_t)s_mem[p] * ldv;
+#pragma unroll
+                            for (int u = 0; u < CPL; u++) {
+                                const int col = cb + sub + u * L;
+                                if (col < nv)
+                                    cp_async16(buf + (z * CPL + u) * 32 + lane, row + col);
+                            }
+                        }
                     }
                     cp_async_commit();
                 };
@@ -198,12 +209,15 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                         cp_async_commit();  // empty group: the wait below always leaves one
                     cp_async_wait<1>();
                     __syncwarp();
-                    const float4 *buf = ring + (t & 1) * (UP_R * 32);
+                    const float4 *buf = ring + (t & 1) * (R * 32 * CPL);
 #pragma unroll
-                    for (int z = 0; z < UP_R; z++) {
-                        if (gidx + gstride * (t * UP_R + z) < mc) {
-                            const V v1[1] = {buf[z * 32 + lane]};
-                            accumulate<VEC, CPL>(v1, s, c, qs, qc, cb, sub, L, nv);
+                    for (int z = 0; z < R; z++) {
+                        if (gidx + gstride * (t * R + z) < mc) {
+                            V vz[CPL];
+#pragma unroll
+                            for (int u = 0; u < CPL; u++)
+                                vz[u] = buf[(z * CPL + u) * 32 + lane];
+                            accumulate<VEC, CPL>(vz, s, c, qs, qc, cb, sub, L, nv);
                         }
                     }
                     __syncwarp();  // stage t & 1 is refilled by issue(t + 2)
@@ -231,6 +245,8 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                 }
             }
         }
+        if constexpr (PIPE)
+            __syncthreads();  // every warp is done with the ring before the partial sums overwrite it
         sq_lane = df_add(sq_lane, fast_two_sum(qs, -qc));
         // combine the G groups of the warp, then the warps of the block, in a fixed order
 #pragma unroll
@@ -319,11 +335,11 @@ cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, cons
         if (need <= 1)
             k_update<4, 1, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
         else if (need <= 2)
-            GK_UPD(4, 2);
+            k_update<4, 2, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
         else if (need <= 4)
-            GK_UPD(4, 4);
+            k_update<4, 4, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
         else
-            GK_UPD(4, 8);
+            k_update<4, 8, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
     } else {
         if (need <= 1)
             GK_UPD(1, 1);
