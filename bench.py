@@ -62,6 +62,8 @@ def parse():
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
                          "BF16/tensor-core screening in the assignment (all give the same results)")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=96,
+                    help="jobs of the serving stream to run after the step measurement (0: none)")
     ap.add_argument("--traffic-from", metavar="CSV",
                     help="no GPU run: read an ncu --csv log with dram__bytes_read.sum, dram__bytes_write.sum and "
                          "gpu__time_duration.sum of this workload's kernels and record the per-launch means in "
@@ -515,11 +517,41 @@ def run_gpu(args):
             continue
         a = algorithmic_bytes(t, w, w.k0 if t == "refine" else w.k)
         res["roofline_all"][t] = round(a / statistics.mean(v) / 1e9 / hbm, 4)
+    if world == 1 and args.serve_jobs > 0:
+        res["serving"] = serving(args)
     if world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(w, Xh)
     print(json.dumps(res), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving(args):
+    """The serving workload (Poisson stream of clustering jobs, n log-uniform in [1e4, 1e6], d in
+    {64, 128, 256}, k = n / 100, kappa = 20, HBM budget 120 GB), bounded to its first jobs: the stream
+    at its arrival times (latency), all jobs at once (throughput), and the same jobs one at a time on
+    the FP32 path (the per-job form), with the largest relative difference of final distortion."""
+    import torch
+
+    from paper_1705_01813_gb300 import serve
+    specs = serve.job_specs(datagen.serving_jobs()[:args.serve_jobs])
+    p = serve.ServeParams(budget_bytes=120 << 30, slots=8, precision=args.precision)
+    srv = serve.Server(p)
+    srv.run(specs[:2], realtime=False)  # warm-up: library load, allocator, first launches
+    torch.cuda.synchronize()
+    live = serve.summarize(srv.run(specs, realtime=True))
+    sat_res = srv.run(specs, realtime=False)
+    sat = serve.summarize(sat_res)
+    ser_res = serve.run_serial(specs, serve.ServeParams(budget_bytes=p.budget_bytes, slots=1, precision=0))
+    ser = serve.summarize(ser_res)
+    dE = max(abs(a.distortion - b.distortion) / max(abs(b.distortion), 1e-300) for a, b in zip(sat_res, ser_res))
+    return {"jobs": len(specs), "rate_per_s": 20.0, "slots": p.slots, "budget_gb": 120,
+            "stream": {k: round(v, 3) if isinstance(v, float) else v for k, v in live.items()},
+            "saturation": {k: round(v, 3) if isinstance(v, float) else v for k, v in sat.items()},
+            "per_job_fp32_serial": {k: round(v, 3) if isinstance(v, float) else v for k, v in ser.items()},
+            "max_rel_distortion_diff": dE,
+            "workload": "first jobs of the seeded Poisson stream (rate 20/s): n log-uniform in [1e4, 1e6], "
+                        "d in {64, 128, 256}, k = n/100, kappa = 20, Gaussian mixtures generated on the device"}
 
 
 def _oracle_step(O, w, X, k_scale):

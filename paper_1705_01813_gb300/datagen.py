@@ -181,6 +181,19 @@ WORKLOADS = {
 }
 
 
+def gauss_mixture_device(n: int, d: int, n_centers: int, seed: int, device, box: float = 10.0, sigma: float = 1.0):
+    """The mixture of gauss_mixture drawn on the GPU with a seeded torch generator (same recipe, different
+    stream of random numbers): serving jobs generate their samples where they are clustered."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    centers = (torch.rand((n_centers, d), generator=g, device=device, dtype=torch.float32) * 2.0 - 1.0) * box
+    z = torch.randint(0, n_centers, (n,), generator=g, device=device)
+    X = torch.randn((n, d), generator=g, device=device, dtype=torch.float32).mul_(sigma)
+    X += centers[z]
+    return X
+
+
 def serving_jobs(count: int = 512, rate: float = 20.0, seed: int = BASE_SEED + 4):
     """Poisson job stream: arrival times, n log-uniform in [1e4, 1e6], d in {64,128,256}, k = n/100."""
     g = _rng(seed)

@@ -1,0 +1,71 @@
+"""Serving loop: a job's result is the same alone and among others, admission keeps the HBM budget and
+the slot count, and the latency summary is what it says."""
+import numpy as np
+import pytest
+
+from paper_1705_01813_gb300 import serve
+
+
+def _specs(sizes, arrival_gap=0.0):
+    return [serve.JobSpec(i, i * arrival_gap, n, d, max(1, n // 100), 20, 1000 + i) for i, (n, d) in enumerate(sizes)]
+
+
+def _peak_in_flight(res):
+    events = sorted([(r.start, 1) for r in res] + [(r.end, -1) for r in res], key=lambda e: (e[0], e[1]))
+    live = peak = 0
+    for _, dv in events:
+        live += dv
+        peak = max(peak, live)
+    return peak
+
+
+def test_summary_percentiles_and_rate():
+    res = [serve.JobResult(i, arrival=0.1 * i, start=0.1 * i, end=0.1 * i + 0.01 * (i + 1), n=100, d=8, k=1,
+                           distortion=1.0) for i in range(100)]
+    s = serve.summarize(res)
+    assert s["jobs"] == 100 and s["samples"] == 10000
+    # latency of job i is 10 (i + 1) ms; the q-quantile is the entry at index round(q (count - 1))
+    assert abs(s["p50_ms"] - 10 * (round(0.5 * 99) + 1)) < 1e-6
+    assert abs(s["p99_ms"] - 10 * (round(0.99 * 99) + 1)) < 1e-6
+    assert abs(s["span_s"] - (9.9 + 1.0)) < 1e-9 and abs(s["jobs_per_s"] - 100 / 10.9) < 1e-9
+
+
+def test_job_bytes_grows_with_the_job():
+    p = serve.ServeParams()
+    a, b, c = _specs([(10000, 64), (20000, 64), (20000, 128)])
+    assert serve.job_bytes(a, p) < serve.job_bytes(b, p) < serve.job_bytes(c, p)
+    assert serve.job_bytes(b, p) >= 20000 * 64 * 4 + 20000 * 20 * 8  # samples and graph at least
+
+
+@pytest.mark.gpu
+def test_result_alone_equals_result_in_the_mix():
+    import torch
+    specs = _specs([(12000, 64), (30011, 128), (15000, 256), (20000, 64), (10007, 128), (25000, 256)])
+    keep = serve.ServeParams(slots=4, keep_results=True)
+    mix = serve.Server(keep).run(specs, realtime=False)
+    assert _peak_in_flight(mix) >= 2  # the jobs did overlap
+    for s, rm in zip(specs, mix):
+        ra = serve.Server(serve.ServeParams(slots=1, keep_results=True)).run([s], realtime=False)[0]
+        assert torch.equal(ra.labels, rm.labels) and torch.equal(ra.centroids, rm.centroids)
+        assert ra.distortion == rm.distortion
+        assert rm.labels.shape == (s.n,) and rm.centroids.shape == (s.k, s.d)
+        assert np.isfinite(rm.distortion) and rm.distortion > 0
+
+
+@pytest.mark.gpu
+def test_admission_keeps_budget_and_slots():
+    specs = _specs([(20000, 128)] * 6)
+    p = serve.ServeParams(slots=4)
+    p.budget_bytes = 2 * serve.job_bytes(specs[0], p) + 1  # room for two of them
+    res = serve.Server(p).run(specs, realtime=False)
+    assert _peak_in_flight(res) <= 2
+    with pytest.raises(ValueError):
+        serve.Server(serve.ServeParams(budget_bytes=1)).run(specs[:1], realtime=False)
+
+
+@pytest.mark.gpu
+def test_stream_latency_counts_from_arrival():
+    specs = _specs([(10000, 64)] * 4, arrival_gap=0.05)
+    res = serve.Server(serve.ServeParams(slots=2)).run(specs, realtime=True)
+    for s, r in zip(specs, res):
+        assert r.start >= s.arrival - 1e-3 and r.end > r.start and abs(r.latency - (r.end - s.arrival)) < 1e-12
