@@ -542,13 +542,20 @@ def serving(args):
     live = serve.summarize(srv.run(specs, realtime=True))
     sat_res = srv.run(specs, realtime=False)
     sat = serve.summarize(sat_res)
+    pb = serve.ServeParams(budget_bytes=p.budget_bytes, slots=p.slots, precision=args.precision, batching=True)
+    bsrv = serve.Server(pb)
+    blive = serve.summarize(bsrv.run(specs, realtime=True))
+    bsat_res = bsrv.run(specs, realtime=False)
+    bsat = serve.summarize(bsat_res)
     ser_res = serve.run_serial(specs, serve.ServeParams(budget_bytes=p.budget_bytes, slots=1, precision=0))
     ser = serve.summarize(ser_res)
-    dE = max(abs(a.distortion - b.distortion) / max(abs(b.distortion), 1e-300) for a, b in zip(sat_res, ser_res))
+    dE = max(abs(a.distortion - b.distortion) / max(abs(b.distortion), 1e-300)
+             for res in (sat_res, bsat_res) for a, b in zip(res, ser_res))
+    r3 = lambda d: {k: round(v, 3) if isinstance(v, float) else v for k, v in d.items()}  # noqa: E731
     return {"jobs": len(specs), "rate_per_s": 20.0, "slots": p.slots, "budget_gb": 120,
-            "stream": {k: round(v, 3) if isinstance(v, float) else v for k, v in live.items()},
-            "saturation": {k: round(v, 3) if isinstance(v, float) else v for k, v in sat.items()},
-            "per_job_fp32_serial": {k: round(v, 3) if isinstance(v, float) else v for k, v in ser.items()},
+            "stream": r3(live), "saturation": r3(sat),
+            "batched_stream": r3(blive), "batched_saturation": r3(bsat),
+            "per_job_fp32_serial": r3(ser),
             "max_rel_distortion_diff": dE,
             "workload": "first jobs of the seeded Poisson stream (rate 20/s): n log-uniform in [1e4, 1e6], "
                         "d in {64, 128, 256}, k = n/100, kappa = 20, Gaussian mixtures generated on the device"}

@@ -13,6 +13,11 @@ kernels) and reads back the distortion log at the end.  Results do not depend
 on what else runs: every kernel is deterministic and each job has its own
 workspace and stream.
 
+With batching, the jobs waiting at a dispatch that share the head job's row
+width and kappa run together as one concatenated problem (run_batch): each
+kernel launch then serves all of them, which amortises launches over small
+jobs; a batch's jobs complete together.
+
 The loop itself is host code over the C ABI: one host thread per slot, each
 blocked in a library call (the ctypes call releases the interpreter lock)
 while its stream runs.
@@ -67,6 +72,9 @@ class ServeParams:
     iters: int = 10
     max_cluster: int = 128
     keep_results: bool = False     # keep each job's labels and centroids (device) in its result
+    batching: bool = False         # run eligible jobs of one (d, kappa) together (run_batch)
+    max_batch_jobs: int = 64
+    max_batch_samples: int = 4_000_000
 
 
 def job_specs(jobs: list[dict]) -> list[JobSpec]:
@@ -110,6 +118,103 @@ def run_job(s: JobSpec, p: ServeParams, device, stream: torch.cuda.Stream):
     return log[-1], labels, C
 
 
+def build_k0(n: int, xi: int) -> int:
+    """Clusters of the graph construction (the library's rule): floor(n / xi), at least 1."""
+    return max(1, n // xi)
+
+
+def batch_bytes(specs: list[JobSpec], p: ServeParams) -> int:
+    """Device bytes of a batch: the concatenated problem plus one job's worth of transient data."""
+    n = sum(s.n for s in specs)
+    d, kappa = specs[0].d, specs[0].kappa
+    k0 = sum(build_k0(s.n, p.xi) for s in specs)
+    k = sum(s.k for s in specs)
+    ws = max(gkm.workspace_size(gkm.GK_OP_FIT, n, d, max(k0, k), kappa),
+             gkm.workspace_size(gkm.GK_OP_REFINE, n, d, max(k0, k), kappa),
+             gkm.workspace_size_build(n, d, kappa, p.xi, p.tau, p.max_cluster))
+    one = max(s.n * s.d * 4 for s in specs)
+    return n * d * 4 + n * kappa * 8 + 3 * n * 4 + (k0 + k) * (d * 4 + 8) + ws + one + (1 << 20)
+
+
+def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.Stream):
+    """Jobs of one row width d and one kappa as one problem.  Their samples are concatenated; each
+    job's random graph and labels are drawn on its own slice (as alone) and shifted by the job's
+    first sample and first cluster.  No cluster and no graph row then spans two jobs, and the
+    shifts keep every tie order ((distance, id) in rows, (distance, label) in assignments), so each
+    launch of the assignment, grouping, update and refinement serves all jobs at once and every
+    job gets the labels and centroids it gets alone.  Returns [(distortion, labels, centroids)]."""
+    d, kappa = specs[0].d, specs[0].kappa
+    if any(s.d != d or s.kappa != kappa for s in specs):
+        raise ValueError("a batch holds jobs of one row width and one kappa")
+    ns = [s.n for s in specs]
+    k0s = [build_k0(n, p.xi) for n in ns]
+    ks = [s.k for s in specs]
+    noff = [0]
+    for n in ns:
+        noff.append(noff[-1] + n)
+    k0off, koff = [0], [0]
+    for a, b in zip(k0s, ks):
+        k0off.append(k0off[-1] + a)
+        koff.append(koff[-1] + b)
+    N, K0, K = noff[-1], k0off[-1], koff[-1]
+    i32, f32 = torch.int32, torch.float32
+    with torch.cuda.stream(stream):
+        X = torch.empty((N, d), dtype=f32, device=device)
+        gi = torch.empty((N, kappa), dtype=i32, device=device)
+        gd = torch.empty((N, kappa), dtype=f32, device=device)
+        la = torch.empty(N, dtype=i32, device=device)
+        lb = torch.empty(N, dtype=i32, device=device)
+        ws = gkm.Workspace(max(gkm.workspace_size(gkm.GK_OP_FIT, N, d, max(K0, K), kappa),
+                               gkm.workspace_size(gkm.GK_OP_REFINE, N, d, max(K0, K), kappa)), device)
+        for j, s in enumerate(specs):  # per job: samples, random graph, initial labels at k0
+            sl = slice(noff[j], noff[j + 1])
+            X[sl] = job_data(s, device)
+            gkm.init_graph(X[sl], kappa, s.seed, gi[sl], gd[sl], ws=ws, stream=stream)
+            gi[sl] += noff[j]
+            gkm.init_labels(s.n, k0s[j], s.seed, out=la[sl], stream=stream)
+            la[sl] += k0off[j]
+        off = torch.empty(max(K0, K) + 1, dtype=i32, device=device)
+        mem = torch.empty(N, dtype=i32, device=device)
+        cnt = torch.empty(max(K0, K), dtype=i32, device=device)
+        sd = torch.empty(2, dtype=torch.float64, device=device)
+        # Alg. 3 on the whole batch
+        C0 = torch.zeros((K0, d), dtype=f32, device=device)
+        gkm.group_by_label(la, K0, off, mem, cnt, ws=ws, stream=stream)
+        gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
+        cur, nxt = la, lb
+        for _ in range(p.tau):
+            gkm.assign_step(X, gi, C0, cur, nxt, None, sd[1:2], None, p.precision, mem, ws=ws, stream=stream)
+            gkm.group_by_label(nxt, K0, off, mem, cnt, ws=ws, stream=stream)
+            gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
+            gkm.graph_refine_groups(X, off, mem, K0, gi, gd, p.max_cluster, p.precision, ws=ws, stream=stream)
+            cur, nxt = nxt, cur
+        del C0, gd
+        # the fit at each job's k, from each job's seeded labels
+        cur, nxt = la, lb
+        for j, s in enumerate(specs):
+            sl = slice(noff[j], noff[j + 1])
+            gkm.init_labels(s.n, s.k, s.seed + 1, out=cur[sl], stream=stream)
+            cur[sl] += koff[j]
+        C = torch.zeros((K, d), dtype=f32, device=device)
+        gkm.group_by_label(cur, K, off, mem, cnt, ws=ws, stream=stream)
+        gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
+        for _ in range(p.iters):
+            gkm.assign_step(X, gi, C, cur, nxt, None, sd[1:2], None, p.precision, mem, ws=ws, stream=stream)
+            gkm.group_by_label(nxt, K, off, mem, cnt, ws=ws, stream=stream)
+            gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
+            cur, nxt = nxt, cur
+        # per-job results and distortion (mean squared distance to the own centroid, FP64 sums)
+        out = []
+        for j, s in enumerate(specs):
+            sl = slice(noff[j], noff[j + 1])
+            lab = cur[sl] - koff[j]
+            Cj = C[koff[j]:koff[j + 1]].clone()
+            E = ((X[sl].double() - Cj.double()[lab.long()]) ** 2).sum() / s.n
+            out.append((E, lab, Cj))
+        stream.synchronize()
+        return [(float(E), lab, Cj) for E, lab, Cj in out]
+
+
 class Server:
     """Admits jobs by HBM budget and slots, runs each on its own stream, records latencies."""
 
@@ -123,8 +228,9 @@ class Server:
         otherwise all are eligible at once (a saturation run).  Returns one result per job."""
         p = self.p
         for s in specs:
-            if job_bytes(s, p) > p.budget_bytes:
-                raise ValueError(f"job {s.jid} needs {job_bytes(s, p)} bytes, more than the budget")
+            need = batch_bytes([s], p) if p.batching else job_bytes(s, p)
+            if need > p.budget_bytes:
+                raise ValueError(f"job {s.jid} needs {need} bytes, more than the budget")
         lock = threading.Condition()
         state = {"used": 0, "inflight": 0, "error": None}
         results: dict[int, JobResult] = {}
@@ -132,25 +238,46 @@ class Server:
         free_streams = list(range(p.slots))
         t0 = time.perf_counter()
 
-        def worker(s: JobSpec, si: int, start: float, nbytes: int):
+        def worker(batch: list[JobSpec], si: int, start: float, nbytes: int):
             try:
                 torch.cuda.set_device(self.device)
-                E, labels, C = run_job(s, p, self.device, streams[si])
+                if p.batching:
+                    outs = run_batch(batch, p, self.device, streams[si])
+                else:
+                    outs = [run_job(batch[0], p, self.device, streams[si])]
                 end = time.perf_counter() - t0
-                res = JobResult(s.jid, s.arrival if realtime else 0.0, start, end, s.n, s.d, s.k, E,
-                                labels if p.keep_results else None, C if p.keep_results else None)
-                del labels, C
+                res = [JobResult(s.jid, s.arrival if realtime else 0.0, start, end, s.n, s.d, s.k, E,
+                                 labels if p.keep_results else None, C if p.keep_results else None)
+                       for s, (E, labels, C) in zip(batch, outs)]
+                del outs
             except BaseException as e:  # reported by run(); the slot and budget are released
                 res = None
                 with lock:
                     state["error"] = state["error"] or e
             with lock:
-                if res is not None:
-                    results[s.jid] = res
+                for r in res or []:
+                    results[r.jid] = r
                 state["used"] -= nbytes
                 state["inflight"] -= 1
                 free_streams.append(si)
                 lock.notify_all()
+
+        def next_batch(now: float) -> list[JobSpec]:
+            """The head job, and with batching the eligible jobs of its (d, kappa) after it."""
+            head = queue[0]
+            if not p.batching:
+                return [head]
+            out, total = [], 0
+            for s in queue:
+                if realtime and s.arrival > now:
+                    break
+                if (s.d, s.kappa) != (head.d, head.kappa):
+                    continue
+                if out and (len(out) >= p.max_batch_jobs or total + s.n > p.max_batch_samples):
+                    break
+                out.append(s)
+                total += s.n
+            return out
 
         threads = []
         queue = list(specs)
@@ -163,15 +290,17 @@ class Server:
                 if realtime and s.arrival > now:
                     lock.wait(timeout=s.arrival - now)
                     continue
-                nbytes = job_bytes(s, p)
+                batch = next_batch(now)
+                nbytes = batch_bytes(batch, p) if p.batching else job_bytes(s, p)
                 if state["inflight"] >= p.slots or state["used"] + nbytes > p.budget_bytes:
                     lock.wait(timeout=0.05)
                     continue
-                queue.pop(0)
+                for b in batch:
+                    queue.remove(b)
                 state["used"] += nbytes
                 state["inflight"] += 1
                 si = free_streams.pop()
-                th = threading.Thread(target=worker, args=(s, si, now, nbytes), daemon=True)
+                th = threading.Thread(target=worker, args=(batch, si, now, nbytes), daemon=True)
                 th.start()
                 threads.append(th)
         for th in threads:

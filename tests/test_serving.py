@@ -69,3 +69,26 @@ def test_stream_latency_counts_from_arrival():
     res = serve.Server(serve.ServeParams(slots=2)).run(specs, realtime=True)
     for s, r in zip(specs, res):
         assert r.start >= s.arrival - 1e-3 and r.end > r.start and abs(r.latency - (r.end - s.arrival)) < 1e-12
+
+
+@pytest.mark.gpu
+def test_batched_jobs_equal_jobs_alone():
+    """Jobs of one row width concatenated into one problem (shifted graph ids and labels) give each job
+    the labels and centroids it gets alone through the one-call library API."""
+    import torch
+    specs = _specs([(12000, 64), (15013, 128), (20000, 64), (10007, 128), (9000, 64), (30011, 128)])
+    pb = serve.ServeParams(slots=2, keep_results=True, batching=True)
+    batched = serve.Server(pb).run(specs, realtime=False)
+    assert len({r.end for r in batched}) < len(specs)  # some jobs completed together, in one batch
+    for s, rb in zip(specs, batched):
+        ra = serve.Server(serve.ServeParams(slots=1, keep_results=True)).run([s], realtime=False)[0]
+        assert torch.equal(ra.labels, rb.labels) and torch.equal(ra.centroids, rb.centroids)
+        assert abs(rb.distortion - ra.distortion) <= 1e-9 * abs(ra.distortion)
+
+
+@pytest.mark.gpu
+def test_batch_rejects_mixed_widths():
+    import torch
+    with pytest.raises(ValueError):
+        serve.run_batch(_specs([(1000, 64), (1000, 128)]), serve.ServeParams(), torch.device("cuda", 0),
+                        torch.cuda.current_stream())
