@@ -242,7 +242,9 @@ def launches_per_step(w, precision):
     upd = 2
     # assign: shadow copy, tensor-core tiles, SIMT leftovers, reduce, finish (precision 1); kernel, reduce, finish
     asg = 5 if precision == 2 and w.d <= 128 else (4 if precision == 2 else 3)
-    ref = 1 + 3 + 1 + 2  # refine: run count, scan, run clusters, two kernels (gram + merge, or two tile widths)
+    # refine: run count, scan, run clusters, then Gram + exact recompute + merge (tensor cores, d <= 128) or the
+    # two FP32 tile widths
+    ref = 1 + 3 + 1 + (3 if precision >= 1 and 64 <= w.d <= 128 else 2)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit
@@ -265,7 +267,7 @@ def algorithmic_bytes(tag, w, k):
 
 
 def kernel_of(tag, precision=1, d=128):
-    if tag == "refine" and precision >= 1 and d <= 128:  # the library's dispatch: tensor-core Gram for d <= 128
+    if tag == "refine" and precision >= 1 and 64 <= d <= 128:  # the library's dispatch: tensor-core Gram
         return "k_refine_gram"
     if tag == "assign" and precision == 2:
         return "k_assign_tc"

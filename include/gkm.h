@@ -74,9 +74,9 @@ typedef struct {
     uint64_t seed;       /* seed of the random initial graph and labels (SplitMix64)    */
     int32_t precision;   /* 0: FP32 throughout; 1: refinement pair distances from a BF16
                             Gram on the tensor cores with an exact FP32 recompute of the
-                            pairs inside its error bound (d <= 128; wider rows use the
-                            FP32 kernels); 2: 1 and the assignment's BF16 screening as
-                            in gk_assign_step.  All give the same graph.                */
+                            pairs inside its error bound (64 <= d <= 128; other widths
+                            use the FP32 kernels); 2: 1 and the assignment's BF16
+                            screening as in gk_assign_step.  All give the same graph.   */
     int32_t reserved;    /* must be 0                                                   */
 } gk_graph_params;
 
@@ -172,8 +172,8 @@ GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  *              the run's centred coordinates are integers of magnitude <= 255
  *              (and 2 d 255^2 < 2^24), otherwise every pair within a rigorous
  *              error bound of entering a row is recomputed in FP32 as with 0;
- *              for d > 128 (where the Gram cannot be exact) 1 and 2 use the
- *              SIMT kernels of 0; all settings give the same graph.
+ *              the tensor-core path serves 64 <= d <= 128; other widths use
+ *              the SIMT kernels of 0; all settings give the same graph.
  *   g_idx / g_dist  device, n x kappa, in: current graph, out: refined graph
  */
 GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,

@@ -32,7 +32,6 @@ int fail(int code, const char *fmt, ...)
 
 constexpr int64_t MAX_ROWS = (int64_t)1 << 31;
 constexpr int MAX_LOG = 4096;  // e_log entries kept on the device
-constexpr int MAX_D = 4096;    // the assignment stages one sample per warp in shared memory
 
 int check_x(const float *X, int64_t n, int64_t d, int64_t ld, int64_t min_n)
 {

@@ -10,6 +10,13 @@ namespace gkm {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr int MAX_KAPPA = 128;
+constexpr int MAX_D = 4096;  // widest row (the generic assignment stages one sample per warp in shared memory)
+
+// Kernels whose dynamic shared memory depends on kappa or d get the attribute
+// cudaFuncAttributeMaxDynamicSharedMemorySize set to their size at the largest
+// allowed kappa and d, the same value on every call: the attribute is per
+// function, and launches from several host threads must not see each other's
+// settings.
 
 // Device status word kept at the start of every workspace: the first error a
 // kernel meets (code, detail).  Kernels record and skip; they never trap.
@@ -168,7 +175,7 @@ size_t refine_scratch_bytes(int64_t n, int32_t k);
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                           float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision);
-size_t refine_tc_scratch_bytes(int64_t n);
+size_t refine_tc_scratch_bytes(int64_t n, int32_t k);
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
                              int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,

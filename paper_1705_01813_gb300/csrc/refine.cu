@@ -201,7 +201,7 @@ static size_t run_cl_bytes(int64_t n, int32_t k) { return ((size_t)(k + n / 2 + 
 
 size_t refine_scratch_bytes(int64_t n, int32_t k)
 {
-    return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n);
+    return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n, k);
 }
 
 cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
@@ -214,11 +214,12 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     void *sc = static_cast<char *>(scratch) + run_bytes(k) + run_cl_bytes(n, k);
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
-    cudaError_t e = cudaFuncSetAttribute(k_refine<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm64);
+    cudaError_t e = cudaFuncSetAttribute(k_refine<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
     if (e != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_refine<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm128)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_refine<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)RefineTile<128>::smem_bytes(MAX_KAPPA))) != cudaSuccess)
         return e;
     k_count_runs<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(offsets, k, max_cluster, nruns);
     if ((e = launch_scan(nruns, run_off, k, sc, s)) != cudaSuccess)
@@ -226,10 +227,11 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     k_run_clusters<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(run_off, k, run_cl);
     // an upper bound of the number of runs: sum over clusters of (m / cap + 1)
     const int64_t grid = (int64_t)k + n / max_cluster + 1;
-    // The BF16 Gram is exact only for integer data with 2 d 255^2 < 2^24 (d <= 128); otherwise every pair it
-    // keeps is recomputed in FP32 from the two full rows, which for d > 128 reads more than the FP32 tile
-    // kernels below (1M x 960: 91 ms against 25 ms per call), so precision >= 1 uses them there.
-    if (precision >= 1 && d <= 128) {
+    // The tensor-core path for 64 <= d <= 128.  Its Gram is exact only for integer data with 2 d 255^2 < 2^24
+    // (d <= 128), and wider rows made the recompute of every kept pair dearer than the FP32 tile kernels
+    // (1M x 960: 91 ms against 25 ms per call); for d < 64 the tile kernels' cost, proportional to d, is below
+    // the fixed per-run cost of the Gram path (20k x 32: 0.18 ms against 0.12 ms per call).
+    if (precision >= 1 && d >= 64 && d <= 128) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
         if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, grid, g_idx,
                                   g_dist, tc_scratch, st, s)) != cudaSuccess)

@@ -2,7 +2,7 @@
 // taken from a Gram matrix on the tensor cores (tcgen05, BF16 inputs, FP32
 // accumulation in tensor memory), and the same graph as the FP32 path.
 //
-// Two kernels per refinement:
+// Three kernels per refinement:
 //
 // k_refine_gram, one CTA (4 warps) per run of <= 128 members.  The run's rows,
 // centred on the run's first member, are converted to BF16 and staged in
@@ -18,13 +18,16 @@
 // differences bit for bit.  Otherwise a pair is kept when d2 - E_tj is not
 // above the kappa-th distance, E_tj being a rigorous bound on the error of the
 // Gram distance (BF16 rounding of both operands, (4u + 2u^2) |x_t'| |x_j'|
-// with u = 2^-8, plus FP32 accumulation and combination), and marked for an
-// exact recompute.
+// with u = 2^-8, plus FP32 accumulation and combination), marked (recorded by
+// its column in the run instead of its id), and the run is flagged.
 //
-// k_refine_merge, one warp per graph row that received candidates: marked
-// candidates are recomputed exactly in FP32 in the order of pair_d2_seq, and
-// the candidates are merged into the row as in the FP32 path (merge.cuh).
-// Rows that received nothing are not touched.
+// k_refine_exact, one CTA per flagged run: the run's FP32 rows are staged in
+// shared memory once and every marked pair is recomputed exactly in the order
+// of pair_d2_seq, in place.
+//
+// k_refine_merge, one warp per graph row that received candidates: the
+// candidates are merged into the row as in the FP32 path (merge.cuh).  Rows
+// that received nothing are not touched.
 #include "assign_common.cuh"
 #include "common.cuh"
 #include "merge.cuh"
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
                                                             const float *__restrict__ g_dist,
                                                             int32_t *__restrict__ cand_id,
                                                             float *__restrict__ cand_d, int32_t *__restrict__ cand_n,
-                                                            DevStatus *st)
+                                                            int32_t *__restrict__ run_tag, DevStatus *st)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *stage = reinterpret_cast<unsigned char *>(
@@ -223,6 +226,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
         flag_error(st, GK_ERR_TIMEOUT, (unsigned)run);
     // integer run with |x| <= 255: exact only while 2 d 255^2 < 2^24
     const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
+    if (tid == 0 && !timed_out)
+        run_tag[run] = exact ? 0 : 1;  // k_refine_exact recomputes the marked pairs of this run
 
     // ---- candidates of row tid (TMEM lane tid), 32 columns at a time ----
     // Each thread collects its row's candidates of the chunk in shared memory
@@ -260,7 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
                             tag = TC_RERANK;
                         }
                         if (keep && jid >= 0) {
-                            bid[buf_slot(row, m)] = (int)((unsigned)jid | tag);
+                            // a marked pair records the run column of j (k_refine_exact writes the id back)
+                            bid[buf_slot(row, m)] = tag ? (int)(TC_RERANK | (unsigned)j) : jid;
                             bdv[buf_slot(row, m)] = d2;
                             m++;
                         }
@@ -293,7 +299,100 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
         tc::tmem_dealloc(taddr, ncols);
 }
 
-// One warp per graph row: exact recompute of the marked candidates, then the
+// Exact distances of the marked candidates of an inexact run: one CTA per run
+// stages the run's FP32 rows in shared memory (row stride d + 1 words) and the
+// threads share out all (row, candidate) pairs of the run; each marked pair
+// (t, column c) is recomputed by one thread in the order of pair_d2_seq and
+// written back in place with the id of column c.  Runs the Gram kernel found
+// exact return at once.
+constexpr int EX_THREADS = TC_M;
+
+__global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const float *__restrict__ X, int64_t n, int d,
+                                                             int64_t ld, const int32_t *__restrict__ off,
+                                                             const int32_t *__restrict__ mem,
+                                                             const int32_t *__restrict__ run_off,
+                                                             const int32_t *__restrict__ run_cl, int k, int cap,
+                                                             const int32_t *__restrict__ run_tag,
+                                                             int32_t *__restrict__ cand_id,
+                                                             float *__restrict__ cand_d,
+                                                             const int32_t *__restrict__ cand_n, DevStatus *st)
+{
+    extern __shared__ float xs[];  // [sz][d + 1]
+    __shared__ int rid[TC_M], pre[TC_M + 1], wsum[EX_THREADS / 32];
+    const int run = blockIdx.x;
+    if (run >= run_off[k] || run_tag[run] == 0)
+        return;
+    const int r = run_cl[run];
+    const int beg = off[r], m = off[r + 1] - beg;
+    const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
+    const int c = run - run_off[r];
+    const int s0 = c * rbase + min(c, rem), sz = rbase + (c < rem ? 1 : 0);
+    if (sz < 2 || sz > TC_M)
+        return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
+    const int ds = d + 1;
+    int cnt = 0;
+    if (tid < sz) {
+        const int a = mem[beg + s0 + tid];
+        rid[tid] = (a >= 0 && a < n) ? a : -1;
+        cnt = rid[tid] >= 0 ? cand_n[rid[tid]] : 0;
+    }
+    // exclusive prefix of the rows' candidate counts
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o)
+            incl += v;
+    }
+    if (lane == 31)
+        wsum[w] = incl;
+    __syncthreads();
+    int base = 0;
+    for (int q = 0; q < w; q++)
+        base += wsum[q];
+    pre[tid] = base + incl - cnt;
+    if (tid == EX_THREADS - 1)
+        pre[EX_THREADS] = base + incl;
+#pragma unroll 4
+    for (int row = w; row < sz; row += EX_THREADS / 32) {
+        const int a = rid[row];
+        for (int t = lane; t < d; t += 32)
+            xs[row * ds + t] = a >= 0 ? __ldg(X + (int64_t)a * ld + t) : 0.f;
+    }
+    __syncthreads();
+    const int total = pre[EX_THREADS];
+    for (int p = tid; p < total; p += EX_THREADS) {
+        int lo = 0, hi = sz;  // the row of pair p: last row with pre[row] <= p
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] <= p)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int row = lo, q = p - pre[row];
+        const int64_t slot = (int64_t)rid[row] * TC_CAP + q;
+        const unsigned raw = (unsigned)cand_id[slot];
+        if (!(raw & TC_RERANK))
+            continue;
+        const int col = (int)(raw & ~TC_RERANK);
+        if (col >= sz || rid[col] < 0) {
+            flag_error(st, GK_ERR_INVALID, (unsigned)r);
+            continue;
+        }
+        const float *xa = xs + row * ds, *xb = xs + col * ds;
+        float acc = 0.f;
+        for (int t = 0; t < d; t++) {
+            const float e = xa[t] - xb[t];
+            acc = fmaf(e, e, acc);
+        }
+        cand_d[slot] = acc;
+        cand_id[slot] = rid[col];
+    }
+}
+
+// One warp per graph row that received candidates (all exact by now): the
 // merge of the FP32 path.  Candidate ids arrive in ascending order.
 constexpr int MG_WARPS = 8;
 
@@ -303,8 +402,7 @@ __host__ __device__ inline size_t merge_warp_bytes(int kappa)
     return sizeof(uint64_t) * (size_t)(TC_CAP + 2 * kappa) + (sizeof(int) + sizeof(float)) * TC_CAP + 16;
 }
 
-__global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__restrict__ X, int64_t n, int d,
-                                                                int64_t ld, int kappa,
+__global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(int64_t n, int kappa,
                                                                 const int32_t *__restrict__ cand_id,
                                                                 const float *__restrict__ cand_d,
                                                                 const int32_t *__restrict__ cand_n,
@@ -320,23 +418,15 @@ __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__r
     int *cid = reinterpret_cast<int *>(nk + kappa);
     float *cdv = reinterpret_cast<float *>(cid + TC_CAP);
     unsigned *dup = reinterpret_cast<unsigned *>(cdv + TC_CAP);
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-
     for (int64_t i = (int64_t)blockIdx.x * MG_WARPS + w; i < n; i += (int64_t)gridDim.x * MG_WARPS) {
         const int cnt = cand_n[i];
         if (cnt == 0)
             continue;
         RowRegs cur;
         load_row(cur, g_idx + i * kappa, g_dist + i * kappa, kappa);
-        const float *xi = X + i * ld;
         for (int q = lane; q < cnt; q += 32) {
-            const unsigned raw = (unsigned)__ldcg(cand_id + i * TC_CAP + q);
-            const int j = (int)(raw & ~TC_RERANK);
-            float dv = __ldcg(cand_d + i * TC_CAP + q);
-            if (raw & TC_RERANK)
-                dv = vec4 ? pair_d2_seq4(xi, X + (int64_t)j * ld, d) : pair_d2_seq(xi, X + (int64_t)j * ld, d);
-            cid[q] = j;
-            cdv[q] = dv;
+            cid[q] = (int)((unsigned)__ldcg(cand_id + i * TC_CAP + q) & ~TC_RERANK);
+            cdv[q] = __ldcg(cand_d + i * TC_CAP + q);
         }
         __syncwarp();
         merge_row((int)i, cid, cdv, cnt, kappa, cur, g_idx + i * kappa, g_dist + i * kappa, rk, bk, nk, dup);
@@ -344,11 +434,13 @@ __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(const float *__r
     }
 }
 
-size_t refine_tc_scratch_bytes(int64_t n)
+// candidate ids and distances (n x TC_CAP each), counts (n), run flags (at most k + n / 2 + 1 runs)
+size_t refine_tc_scratch_bytes(int64_t n, int32_t k)
 {
     const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
     const size_t c = ((size_t)n * sizeof(int32_t) + 255) & ~size_t(255);
-    return 2 * a + c;
+    const size_t t = ((size_t)(k + n / 2 + 1) * sizeof(int32_t) + 255) & ~size_t(255);
+    return 2 * a + c + t;
 }
 
 cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
@@ -360,23 +452,34 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
     int32_t *cand_id = static_cast<int32_t *>(scratch);
     float *cand_d = reinterpret_cast<float *>(static_cast<char *>(scratch) + a);
     int32_t *cand_n = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a);
+    int32_t *run_tag = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a +
+                                                   (((size_t)n * sizeof(int32_t) + 255) & ~size_t(255)));
     cudaError_t e = cudaFuncSetAttribute(k_refine_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     if (e != cudaSuccess)
         return e;
+    const size_t shm_exact = sizeof(float) * (size_t)TC_M * (size_t)(d + 1);  // d <= 128 on this path
+    if ((e = cudaFuncSetAttribute(k_refine_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * TC_M * (128 + 1)))) != cudaSuccess)
+        return e;
     const size_t shm_merge = MG_WARPS * merge_warp_bytes(kappa);
-    if ((e = cudaFuncSetAttribute(k_refine_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_merge)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_refine_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(MG_WARPS * merge_warp_bytes(MAX_KAPPA)))) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(cand_n, 0, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess)
         return e;
+    if ((e = cudaMemsetAsync(run_tag, 0, sizeof(int32_t) * (size_t)grid, s)) != cudaSuccess)
+        return e;
     k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                               kappa, max_cluster, g_idx, g_dist, cand_id, cand_d,
-                                                              cand_n, st);
+                                                              cand_n, run_tag, st);
+    k_refine_exact<<<(unsigned)grid, EX_THREADS, shm_exact, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl,
+                                                                 k, max_cluster, run_tag, cand_id, cand_d, cand_n,
+                                                                 st);
     int64_t mblocks = (n + MG_WARPS - 1) / MG_WARPS;
     if (mblocks > 152 * 64)
         mblocks = 152 * 64;
-    k_refine_merge<<<(unsigned)mblocks, MG_WARPS * 32, shm_merge, s>>>(X, n, (int)d, ld, kappa, cand_id, cand_d,
-                                                                        cand_n, g_idx, g_dist);
+    k_refine_merge<<<(unsigned)mblocks, MG_WARPS * 32, shm_merge, s>>>(n, kappa, cand_id, cand_d, cand_n, g_idx,
+                                                                        g_dist);
     return cudaGetLastError();
 }
 

@@ -201,10 +201,16 @@ REFINE_CASES = [
     (20000, 32, 400, 20, 128),   # k0 = n / 50 at the plain-method size
     (5003, 36, 60, 33, 128),     # clusters of ~83
     (6007, 17, 20, 10, 128),     # clusters of ~300 cut into runs
-    (3001, 960, 50, 50, 128),    # GIST-like width (several K chunks on the tensor cores)
+    (3001, 960, 50, 50, 128),    # GIST-like width (FP32 tile kernels at every precision)
     (2000, 8, 3, 16, 500),       # runs longer than one 128-wide tile
     (900, 5, 6, 6, 40),          # small cap, uneven runs
     (4001, 100, 90, 12, 128),    # d not a multiple of 16 (zero-padded K)
+    # widths the tensor-core path serves at precision >= 1 (64 <= d <= 128)
+    (20000, 64, 400, 20, 128),   # k0 = n / 50, two K-blocks of one chunk
+    (5003, 68, 60, 33, 128),     # clusters of ~83
+    (6007, 80, 20, 10, 128),     # clusters of ~300 cut into runs
+    (2000, 72, 3, 16, 500),      # runs longer than one 128-row tile go to the FP32 kernel
+    (1501, 65, 9, 12, 128),      # odd width: scalar staging
 ]
 
 
