@@ -62,6 +62,9 @@ def parse():
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
                          "BF16/tensor-core screening in the assignment (all give the same results)")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time the step launched op by op only (default: also captured into a CUDA graph, whose "
+                         "replay time is the value)")
     ap.add_argument("--serve-jobs", type=int, default=96,
                     help="jobs of the serving stream to run after the step measurement (0: none)")
     ap.add_argument("--traffic-from", metavar="CSV",
@@ -386,10 +389,34 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    elapsed_stream = t_start.elapsed_time(t_end) / 1e3
+    # the same step captured once into a CUDA graph and replayed (no launch gaps between kernels)
+    elapsed_graph, graph_note = None, None
+    if not args.no_graph:
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                path.step()
+            graph.replay()  # one untimed replay
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record()
+            for _ in range(args.steps):
+                graph.replay()
+            g1.record()
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            elapsed_graph = g0.elapsed_time(g1) / 1e3
+        except Exception as e:  # reported in the line; the stream-launched time stands
+            graph_note = f"capture failed: {str(e)[:160]}"
     ck = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) / 1e3
+    elapsed = elapsed_graph if elapsed_graph is not None else elapsed_stream
     if world > 1:
         elapsed = reduce_max(elapsed, dist, "cuda")
+        elapsed_stream = reduce_max(elapsed_stream, dist, "cuda")
     per_tag = {}
     for tag, e0, e1 in rec:
         per_tag.setdefault(tag, []).append(e0.elapsed_time(e1) / 1e3)
@@ -510,6 +537,9 @@ def run_gpu(args):
         "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
+        "cuda_graph": {"used": elapsed_graph is not None, "ms_per_step_graph": None if elapsed_graph is None else
+                       1e3 * elapsed_graph / args.steps, "ms_per_step_launched": 1e3 * elapsed_stream / args.steps,
+                       "note": graph_note},
         "e2e": e2e,
     }
     # roofline of every call type, for context

@@ -4,6 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "common.cuh"
 
@@ -128,6 +131,22 @@ namespace gkm {
 void set_last_error(const char *msg)
 {
     snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
+cudaError_t set_max_smem(const void *kernel, int bytes)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, kernel}))
+        return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) == cudaSuccess)
+        done.insert({dev, kernel});
+    return e;
 }
 }  // namespace gkm
 

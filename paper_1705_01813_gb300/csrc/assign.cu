@@ -682,13 +682,13 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
         size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
         const int shm_max = (int)(sizeof(float) * (size_t)AS_WARPS * MAX_D + sizeof(int) * AS_WARPS * AS_QCAP);
         if (vec4) {
-            if ((e = cudaFuncSetAttribute(k_assign<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm_max)) !=
+            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<4>), shm_max)) !=
                 cudaSuccess)
                 return e;
             k_assign<4><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
                                                                 labels_out, best, blk_sum, blk_chg, st);
         } else {
-            if ((e = cudaFuncSetAttribute(k_assign<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, shm_max)) !=
+            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<1>), shm_max)) !=
                 cudaSuccess)
                 return e;
             k_assign<1><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,

@@ -395,7 +395,7 @@ cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
     cudaError_t e = cudaMemsetAsync(tile_fallback, 0, sizeof(int32_t) * (size_t)tiles, s);
     if (e != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AtSmem::bytes)) !=
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign_tc), (int)AtSmem::bytes)) !=
         cudaSuccess)
         return e;
     k_assign_tc<<<(unsigned)tiles, AT_THREADS, AtSmem::bytes, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta,

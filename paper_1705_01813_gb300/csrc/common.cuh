@@ -14,9 +14,10 @@ constexpr int MAX_D = 4096;  // widest row (the generic assignment stages one sa
 
 // Kernels whose dynamic shared memory depends on kappa or d get the attribute
 // cudaFuncAttributeMaxDynamicSharedMemorySize set to their size at the largest
-// allowed kappa and d, the same value on every call: the attribute is per
-// function, and launches from several host threads must not see each other's
-// settings.
+// allowed kappa and d: the attribute is per function, and launches from
+// several host threads must not see each other's settings.  It is set once per
+// device and kernel (set_max_smem), so that calls after the first issue no
+// such API call and can be captured into a CUDA graph.
 
 // Device status word kept at the start of every workspace: the first error a
 // kernel meets (code, detail).  Kernels record and skip; they never trap.
@@ -140,6 +141,10 @@ struct Carver {
         return p;
     }
 };
+
+// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) on the current
+// device, the first time only (thread-safe); `bytes` must be the same on every call.
+cudaError_t set_max_smem(const void *kernel, int bytes);
 
 // Internal launchers (each returns cudaError_t of the launch).
 cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s);

@@ -206,8 +206,8 @@ cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, 
         blocks = 152 * 64;
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const size_t shm = IG_WARPS * ig_warp_bytes(kappa, vec4);
-    cudaError_t e = cudaFuncSetAttribute(k_init_graph, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(IG_WARPS * ig_warp_bytes(MAX_KAPPA, true)));
+    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_init_graph),
+                                 (int)(IG_WARPS * ig_warp_bytes(MAX_KAPPA, true)));
     if (e != cudaSuccess)
         return e;
     const uint64_t minv = ~0ull / (uint64_t)n;

@@ -214,12 +214,12 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     void *sc = static_cast<char *>(scratch) + run_bytes(k) + run_cl_bytes(n, k);
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
-    cudaError_t e = cudaFuncSetAttribute(k_refine<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
+    cudaError_t e =
+        set_max_smem(reinterpret_cast<const void *>(k_refine<64>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
     if (e != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_refine<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)RefineTile<128>::smem_bytes(MAX_KAPPA))) != cudaSuccess)
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128>),
+                          (int)RefineTile<128>::smem_bytes(MAX_KAPPA))) != cudaSuccess)
         return e;
     k_count_runs<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(offsets, k, max_cluster, nruns);
     if ((e = launch_scan(nruns, run_off, k, sc, s)) != cudaSuccess)

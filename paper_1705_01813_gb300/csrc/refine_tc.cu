@@ -454,16 +454,16 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
     int32_t *cand_n = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a);
     int32_t *run_tag = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a +
                                                    (((size_t)n * sizeof(int32_t) + 255) & ~size_t(255)));
-    cudaError_t e = cudaFuncSetAttribute(k_refine_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_refine_gram), (int)TC_SMEM);
     if (e != cudaSuccess)
         return e;
     const size_t shm_exact = sizeof(float) * (size_t)TC_M * (size_t)(d + 1);  // d <= 128 on this path
-    if ((e = cudaFuncSetAttribute(k_refine_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(float) * TC_M * (128 + 1)))) != cudaSuccess)
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact), (int)(sizeof(float) * TC_M * (128 + 1)))) !=
+        cudaSuccess)
         return e;
     const size_t shm_merge = MG_WARPS * merge_warp_bytes(kappa);
-    if ((e = cudaFuncSetAttribute(k_refine_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(MG_WARPS * merge_warp_bytes(MAX_KAPPA)))) != cudaSuccess)
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_merge),
+                          (int)(MG_WARPS * merge_warp_bytes(MAX_KAPPA)))) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(cand_n, 0, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess)
         return e;
