@@ -281,7 +281,7 @@ def kernel_of(tag, precision=1, d=128):
 # source file of each kernel whose DRAM traffic is recorded
 KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_tc": "assign_tc.cu", "k_update": "update.cu",
                  "k_radix_scatter": "group.cu", "k_refine": "refine.cu", "k_refine_gram": "refine_tc.cu",
-                 "k_refine_merge": "refine_tc.cu", "k_init_graph": "init.cu"}
+                 "k_refine_merge": "refine_tc.cu", "k_refine_exact": "refine_tc.cu", "k_init_graph": "init.cu"}
 
 
 def file_sha(f):

@@ -181,16 +181,23 @@ WORKLOADS = {
 }
 
 
-def gauss_mixture_device(n: int, d: int, n_centers: int, seed: int, device, box: float = 10.0, sigma: float = 1.0):
+def gauss_mixture_device(n: int, d: int, n_centers: int, seed: int, device, box: float = 10.0, sigma: float = 1.0,
+                         out=None, z_out=None):
     """The mixture of gauss_mixture drawn on the GPU with a seeded torch generator (same recipe, different
-    stream of random numbers): serving jobs generate their samples where they are clustered."""
+    stream of random numbers): serving jobs generate their samples where they are clustered.  out (n x d
+    float32) and z_out (n int64) may be given so that nothing of size n is allocated."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     centers = (torch.rand((n_centers, d), generator=g, device=device, dtype=torch.float32) * 2.0 - 1.0) * box
-    z = torch.randint(0, n_centers, (n,), generator=g, device=device)
-    X = torch.randn((n, d), generator=g, device=device, dtype=torch.float32).mul_(sigma)
-    X += centers[z]
+    z = torch.empty(n, dtype=torch.int64, device=device) if z_out is None else z_out
+    torch.randint(0, n_centers, (n,), generator=g, device=device, out=z)
+    X = torch.empty((n, d), dtype=torch.float32, device=device) if out is None else out
+    torch.randn((n, d), generator=g, device=device, dtype=torch.float32, out=X)
+    X.mul_(sigma)
+    step = 1 << 16  # the centres are added in chunks (bounded temporaries)
+    for s in range(0, n, step):
+        X[s:s + step] += centers[z[s:s + step]]
     return X
 
 

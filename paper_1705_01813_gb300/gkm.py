@@ -119,6 +119,19 @@ class Workspace:
         self.off = (-base) % 256
         self.ptr = ctypes.c_void_p(base + self.off)
 
+    @classmethod
+    def from_buffer(cls, buf: torch.Tensor, stream=None) -> "Workspace":
+        """A workspace over an existing uint8 device tensor (256-byte aligned start); its status word is
+        cleared on `stream`."""
+        if buf.dtype != torch.uint8 or not buf.is_cuda or buf.data_ptr() % 256 or buf.numel() < 256:
+            raise ValueError("workspace buffer: uint8 device tensor, 256-byte aligned, at least 256 bytes")
+        ws = cls.__new__(cls)
+        ws.nbytes, ws.buf, ws.off = int(buf.numel()), buf, 0
+        ws.ptr = ctypes.c_void_p(buf.data_ptr())
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+            buf[:256].zero_()
+        return ws
+
     def status(self, stream=None) -> int:
         return load().gk_read_status(self.ptr, _stream(stream))
 

@@ -18,9 +18,11 @@ width and kappa run together as one concatenated problem (run_batch): each
 kernel launch then serves all of them, which amortises launches over small
 jobs; a batch's jobs complete together.
 
-The loop itself is host code over the C ABI: one host thread per slot, each
-blocked in a library call (the ctypes call releases the interpreter lock)
-while its stream runs.
+Each slot owns an arena (one device buffer, as large as the largest job or
+batch the slot has run) from which a job takes all its tensors, so serving
+makes no device allocation per job.  The loop itself is host code over the C
+ABI: one host thread per slot, each blocked in a library call (the ctypes call
+releases the interpreter lock) while its stream runs.
 """
 from __future__ import annotations
 
@@ -83,21 +85,56 @@ def job_specs(jobs: list[dict]) -> list[JobSpec]:
     return sorted(out, key=lambda s: (s.arrival, s.jid))
 
 
+def job_ws_bytes(s: JobSpec, p: ServeParams) -> int:
+    return max(gkm.workspace_size_build(s.n, s.d, s.kappa, p.xi, p.tau, p.max_cluster),
+               gkm.workspace_size(gkm.GK_OP_FIT, s.n, s.d, s.k, s.kappa))
+
+
 def job_bytes(s: JobSpec, p: ServeParams) -> int:
-    """Device bytes a job holds while it runs."""
+    """Device bytes a job holds while it runs (what run_job takes from its slot's arena)."""
     f32 = 4
-    data = s.n * s.d * f32
+    data = s.n * s.d * f32 + 8 * s.n  # samples, mixture components while they are drawn
     graph = s.n * s.kappa * 8
     labels = 2 * s.n * 4
     cent = s.k * s.d * f32 + s.k * 4
-    ws_build = gkm.workspace_size_build(s.n, s.d, s.kappa, p.xi, p.tau, p.max_cluster)
-    ws_fit = gkm.workspace_size(gkm.GK_OP_FIT, s.n, s.d, s.k, s.kappa)
-    return data + graph + labels + cent + max(ws_build, ws_fit) + (1 << 20)
+    return data + graph + labels + cent + job_ws_bytes(s, p) + 16 * 256
 
 
-def job_data(s: JobSpec, device) -> torch.Tensor:
+class Arena:
+    """A slot's device memory: one byte buffer, allocated when the slot first needs it (and grown when a
+    larger job comes), from which a job takes its tensors with a bump pointer reset for every job.  A
+    serving run thus makes no device allocation per job (allocations and frees of the caching allocator
+    can synchronise the whole device)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.buf = None
+        self.off = 0
+
+    def reset(self, nbytes: int):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        self.off = 0
+
+    def take(self, shape, dtype) -> torch.Tensor:
+        numel = 1
+        for v in shape:
+            numel *= int(v)
+        nb = numel * torch.empty((), dtype=dtype).element_size()
+        off = (self.off + 255) & ~255
+        if off + nb > self.buf.numel():
+            raise MemoryError(f"arena of {self.buf.numel()} bytes cannot hold {nb} more at {off}")
+        self.off = off + nb
+        return self.buf[off:off + nb].view(dtype).view(tuple(int(v) for v in shape))
+
+    def workspace(self, nbytes: int, stream) -> gkm.Workspace:
+        return gkm.Workspace.from_buffer(self.take((max(256, int(nbytes)),), torch.uint8), stream)
+
+
+def job_data(s: JobSpec, device, out=None, z_out=None) -> torch.Tensor:
     """The job's samples: a mixture of n/100 unit Gaussians in [-10, 10]^d (seeded, generated on the device)."""
-    return datagen.gauss_mixture_device(s.n, s.d, max(1, s.n // 100), s.seed, device)
+    return datagen.gauss_mixture_device(s.n, s.d, max(1, s.n // 100), s.seed, device, out=out, z_out=z_out)
 
 
 def _device(device) -> torch.device:
@@ -105,16 +142,33 @@ def _device(device) -> torch.device:
     return dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
 
 
-def run_job(s: JobSpec, p: ServeParams, device, stream: torch.cuda.Stream):
-    """One job on `stream`: samples, graph (Alg. 3), fit (Alg. 2); returns (final distortion, labels, centroids)."""
+def run_job(s: JobSpec, p: ServeParams, device, stream: torch.cuda.Stream, arena: Arena | None = None):
+    """One job on `stream`: samples, graph (Alg. 3), fit (Alg. 2); returns (final distortion, labels, centroids).
+    With an arena every tensor of the job comes from it (the results too: copy them before the arena's next
+    job); without one they come from torch's allocator."""
+    i32, f32 = torch.int32, torch.float32
     with torch.cuda.stream(stream):
-        X = job_data(s, device)
-        gi, _, _, _ = gkm.build_knn_graph(X, s.kappa, xi=p.xi, tau=p.tau, max_cluster=p.max_cluster, seed=s.seed,
-                                          want_log=False, precision=p.precision, stream=stream)
-        L0 = gkm.init_labels(s.n, s.k, s.seed + 1, stream=stream)
-        labels, C, _, log = gkm.kmeans_fit(X, s.k, gi, p.iters, init_labels=L0, precision=p.precision,
-                                           stream=stream)
-        del X, gi, L0
+        if arena is None:
+            X = job_data(s, device)
+            gi, _, _, _ = gkm.build_knn_graph(X, s.kappa, xi=p.xi, tau=p.tau, max_cluster=p.max_cluster,
+                                              seed=s.seed, want_log=False, precision=p.precision, stream=stream)
+            L0 = gkm.init_labels(s.n, s.k, s.seed + 1, stream=stream)
+            labels, C, _, log = gkm.kmeans_fit(X, s.k, gi, p.iters, init_labels=L0, precision=p.precision,
+                                               stream=stream)
+            return log[-1], labels, C
+        arena.reset(job_bytes(s, p))
+        X = arena.take((s.n, s.d), f32)
+        job_data(s, device, out=X, z_out=arena.take((s.n,), torch.int64))
+        gi, gd = arena.take((s.n, s.kappa), i32), arena.take((s.n, s.kappa), f32)
+        lab0, labels = arena.take((s.n,), i32), arena.take((s.n,), i32)
+        C, cnt = arena.take((s.k, s.d), f32), arena.take((s.k,), i32)
+        ws = arena.workspace(job_ws_bytes(s, p), stream)
+        gkm.build_knn_graph(X, s.kappa, xi=p.xi, tau=p.tau, max_cluster=p.max_cluster, seed=s.seed,
+                            labels_out=lab0, g_idx=gi, g_dist=gd, want_log=False, precision=p.precision, ws=ws,
+                            stream=stream)
+        gkm.init_labels(s.n, s.k, s.seed + 1, out=lab0, stream=stream)
+        _, _, _, log = gkm.kmeans_fit(X, s.k, gi, p.iters, init_labels=lab0, labels_out=labels, C_out=C,
+                                      counts_out=cnt, precision=p.precision, ws=ws, stream=stream)
     return log[-1], labels, C
 
 
@@ -123,62 +177,68 @@ def build_k0(n: int, xi: int) -> int:
     return max(1, n // xi)
 
 
+def _batch_dims(specs: list[JobSpec], p: ServeParams):
+    ns = [s.n for s in specs]
+    k0s = [build_k0(n, p.xi) for n in ns]
+    ks = [s.k for s in specs]
+    noff, k0off, koff = [0], [0], [0]
+    for n, a, b in zip(ns, k0s, ks):
+        noff.append(noff[-1] + n)
+        k0off.append(k0off[-1] + a)
+        koff.append(koff[-1] + b)
+    return k0s, noff, k0off, koff
+
+
+def _batch_ws_bytes(N: int, d: int, K: int, kappa: int) -> int:
+    return max(gkm.workspace_size(gkm.GK_OP_FIT, N, d, K, kappa), gkm.workspace_size(gkm.GK_OP_REFINE, N, d, K, kappa))
+
+
 def batch_bytes(specs: list[JobSpec], p: ServeParams) -> int:
-    """Device bytes of a batch: the concatenated problem plus one job's worth of transient data."""
-    n = sum(s.n for s in specs)
+    """Device bytes of a batch (what run_batch takes from its slot's arena)."""
+    _, noff, k0off, koff = _batch_dims(specs, p)
+    N, K0, K = noff[-1], k0off[-1], koff[-1]
     d, kappa = specs[0].d, specs[0].kappa
-    k0 = sum(build_k0(s.n, p.xi) for s in specs)
-    k = sum(s.k for s in specs)
-    ws = max(gkm.workspace_size(gkm.GK_OP_FIT, n, d, max(k0, k), kappa),
-             gkm.workspace_size(gkm.GK_OP_REFINE, n, d, max(k0, k), kappa),
-             gkm.workspace_size_build(n, d, kappa, p.xi, p.tau, p.max_cluster))
-    one = max(s.n * s.d * 4 for s in specs)
-    return n * d * 4 + n * kappa * 8 + 3 * n * 4 + (k0 + k) * (d * 4 + 8) + ws + one + (1 << 20)
+    Km = max(K0, K)
+    return (N * d * 4 + 8 * max(s.n for s in specs) + N * kappa * 8 + 3 * N * 4 + (Km + 1) * 4 + Km * 4 + 16
+            + (K0 + K) * d * 4 + _batch_ws_bytes(N, d, Km, kappa) + 16 * 256)
 
 
-def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.Stream):
+def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.Stream, arena: Arena | None = None):
     """Jobs of one row width d and one kappa as one problem.  Their samples are concatenated; each
     job's random graph and labels are drawn on its own slice (as alone) and shifted by the job's
     first sample and first cluster.  No cluster and no graph row then spans two jobs, and the
     shifts keep every tie order ((distance, id) in rows, (distance, label) in assignments), so each
     launch of the assignment, grouping, update and refinement serves all jobs at once and every
-    job gets the labels and centroids it gets alone.  Returns [(distortion, labels, centroids)]."""
+    job gets the labels and centroids it gets alone.  All tensors come from `arena` (a private one
+    when none is given).  Returns [(distortion, labels, centroids)], the last two views into the
+    arena."""
     d, kappa = specs[0].d, specs[0].kappa
     if any(s.d != d or s.kappa != kappa for s in specs):
         raise ValueError("a batch holds jobs of one row width and one kappa")
-    ns = [s.n for s in specs]
-    k0s = [build_k0(n, p.xi) for n in ns]
-    ks = [s.k for s in specs]
-    noff = [0]
-    for n in ns:
-        noff.append(noff[-1] + n)
-    k0off, koff = [0], [0]
-    for a, b in zip(k0s, ks):
-        k0off.append(k0off[-1] + a)
-        koff.append(koff[-1] + b)
+    k0s, noff, k0off, koff = _batch_dims(specs, p)
     N, K0, K = noff[-1], k0off[-1], koff[-1]
+    Km = max(K0, K)
     i32, f32 = torch.int32, torch.float32
+    arena = arena or Arena(device)
     with torch.cuda.stream(stream):
-        X = torch.empty((N, d), dtype=f32, device=device)
-        gi = torch.empty((N, kappa), dtype=i32, device=device)
-        gd = torch.empty((N, kappa), dtype=f32, device=device)
-        la = torch.empty(N, dtype=i32, device=device)
-        lb = torch.empty(N, dtype=i32, device=device)
-        ws = gkm.Workspace(max(gkm.workspace_size(gkm.GK_OP_FIT, N, d, max(K0, K), kappa),
-                               gkm.workspace_size(gkm.GK_OP_REFINE, N, d, max(K0, K), kappa)), device)
+        arena.reset(batch_bytes(specs, p))
+        X = arena.take((N, d), f32)
+        z = arena.take((max(s.n for s in specs),), torch.int64)
+        gi, gd = arena.take((N, kappa), i32), arena.take((N, kappa), f32)
+        la, lb, mem = arena.take((N,), i32), arena.take((N,), i32), arena.take((N,), i32)
+        off, cnt = arena.take((Km + 1,), i32), arena.take((Km,), i32)
+        sd = arena.take((2,), torch.float64)
+        C0, C = arena.take((K0, d), f32), arena.take((K, d), f32)
+        ws = arena.workspace(_batch_ws_bytes(N, d, Km, kappa), stream)
         for j, s in enumerate(specs):  # per job: samples, random graph, initial labels at k0
             sl = slice(noff[j], noff[j + 1])
-            X[sl] = job_data(s, device)
+            job_data(s, device, out=X[sl], z_out=z[:s.n])
             gkm.init_graph(X[sl], kappa, s.seed, gi[sl], gd[sl], ws=ws, stream=stream)
             gi[sl] += noff[j]
             gkm.init_labels(s.n, k0s[j], s.seed, out=la[sl], stream=stream)
             la[sl] += k0off[j]
-        off = torch.empty(max(K0, K) + 1, dtype=i32, device=device)
-        mem = torch.empty(N, dtype=i32, device=device)
-        cnt = torch.empty(max(K0, K), dtype=i32, device=device)
-        sd = torch.empty(2, dtype=torch.float64, device=device)
         # Alg. 3 on the whole batch
-        C0 = torch.zeros((K0, d), dtype=f32, device=device)
+        C0.zero_()
         gkm.group_by_label(la, K0, off, mem, cnt, ws=ws, stream=stream)
         gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
         cur, nxt = la, lb
@@ -188,14 +248,13 @@ def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.S
             gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
             gkm.graph_refine_groups(X, off, mem, K0, gi, gd, p.max_cluster, p.precision, ws=ws, stream=stream)
             cur, nxt = nxt, cur
-        del C0, gd
         # the fit at each job's k, from each job's seeded labels
         cur, nxt = la, lb
         for j, s in enumerate(specs):
             sl = slice(noff[j], noff[j + 1])
             gkm.init_labels(s.n, s.k, s.seed + 1, out=cur[sl], stream=stream)
             cur[sl] += koff[j]
-        C = torch.zeros((K, d), dtype=f32, device=device)
+        C.zero_()
         gkm.group_by_label(cur, K, off, mem, cnt, ws=ws, stream=stream)
         gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
         for _ in range(p.iters):
@@ -203,14 +262,19 @@ def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.S
             gkm.group_by_label(nxt, K, off, mem, cnt, ws=ws, stream=stream)
             gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
             cur, nxt = nxt, cur
-        # per-job results and distortion (mean squared distance to the own centroid, FP64 sums)
+        # per job: labels back to the job's numbering, distortion (mean squared distance to the own
+        # centroid, FP64 sums over chunks of rows)
         out = []
+        step = 1 << 16
         for j, s in enumerate(specs):
             sl = slice(noff[j], noff[j + 1])
-            lab = cur[sl] - koff[j]
-            Cj = C[koff[j]:koff[j + 1]].clone()
-            E = ((X[sl].double() - Cj.double()[lab.long()]) ** 2).sum() / s.n
-            out.append((E, lab, Cj))
+            cur[sl] -= koff[j]
+            Cj = C[koff[j]:koff[j + 1]]
+            E = torch.zeros((), dtype=torch.float64, device=device)
+            for c0 in range(noff[j], noff[j + 1], step):
+                c1 = min(noff[j + 1], c0 + step)
+                E += ((X[c0:c1].double() - Cj[cur[c0:c1].long()].double()) ** 2).sum()
+            out.append((E / s.n, cur[sl], Cj))
         stream.synchronize()
         return [(float(E), lab, Cj) for E, lab, Cj in out]
 
@@ -221,6 +285,7 @@ class Server:
     def __init__(self, params: ServeParams | None = None, device=None):
         self.p = params or ServeParams()
         self.device = _device(device)
+        self.arenas: list[Arena] = []  # one per slot, kept across runs
         gkm.load()
 
     def run(self, specs: list[JobSpec], realtime: bool = True) -> list[JobResult]:
@@ -235,6 +300,8 @@ class Server:
         state = {"used": 0, "inflight": 0, "error": None}
         results: dict[int, JobResult] = {}
         streams = [torch.cuda.Stream(device=self.device) for _ in range(p.slots)]
+        while len(self.arenas) < p.slots:
+            self.arenas.append(Arena(self.device))
         free_streams = list(range(p.slots))
         t0 = time.perf_counter()
 
@@ -242,9 +309,13 @@ class Server:
             try:
                 torch.cuda.set_device(self.device)
                 if p.batching:
-                    outs = run_batch(batch, p, self.device, streams[si])
+                    outs = run_batch(batch, p, self.device, streams[si], self.arenas[si])
                 else:
-                    outs = [run_job(batch[0], p, self.device, streams[si])]
+                    outs = [run_job(batch[0], p, self.device, streams[si], self.arenas[si])]
+                if p.keep_results:  # out of the slot's arena before its next job
+                    with torch.cuda.stream(streams[si]):
+                        outs = [(E, lab.clone(), C.clone()) for E, lab, C in outs]
+                    streams[si].synchronize()
                 end = time.perf_counter() - t0
                 res = [JobResult(s.jid, s.arrival if realtime else 0.0, start, end, s.n, s.d, s.k, E,
                                  labels if p.keep_results else None, C if p.keep_results else None)
@@ -327,11 +398,16 @@ def run_serial(specs: list[JobSpec], params: ServeParams, device=None) -> list[J
     """The per-job form: one job at a time on one stream, all eligible at t = 0."""
     device = _device(device)
     stream = torch.cuda.Stream(device=device)
+    arena = Arena(device)
     out = []
     t0 = time.perf_counter()
     for s in specs:
         start = time.perf_counter() - t0
-        E, labels, C = run_job(s, params, device, stream)
+        E, labels, C = run_job(s, params, device, stream, arena)
+        if params.keep_results:
+            with torch.cuda.stream(stream):
+                labels, C = labels.clone(), C.clone()
+            stream.synchronize()
         end = time.perf_counter() - t0
         out.append(JobResult(s.jid, 0.0, start, end, s.n, s.d, s.k, E,
                              labels if params.keep_results else None, C if params.keep_results else None))

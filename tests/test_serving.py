@@ -92,3 +92,21 @@ def test_batch_rejects_mixed_widths():
     with pytest.raises(ValueError):
         serve.run_batch(_specs([(1000, 64), (1000, 128)]), serve.ServeParams(), torch.device("cuda", 0),
                         torch.cuda.current_stream())
+
+
+@pytest.mark.gpu
+def test_arena_run_equals_allocating_run():
+    """A job whose tensors come from a slot arena (reused by an earlier, different job) gives the same
+    results as the job with tensors from torch's allocator."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    p = serve.ServeParams()
+    arena = serve.Arena(dev)
+    first, second = _specs([(30011, 128), (12007, 64)])
+    serve.run_job(first, p, dev, stream, arena)  # leaves its contents in the arena
+    Ea, la, Ca = serve.run_job(second, p, dev, stream, arena)
+    Eb, lb, Cb = serve.run_job(second, p, dev, stream)
+    stream.synchronize()
+    assert torch.equal(la, lb) and torch.equal(Ca, Cb) and Ea == Eb
+    assert arena.buf.numel() >= serve.job_bytes(first, p)
