@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=1,
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=1,
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
-                         "BF16/tensor-core screening in the assignment (all give the same results)")
+                         "BF16 screening in the assignment (SIMT); 3 the screening on the tensor cores (all give "
+                         "the same results)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step launched op by op only (default: also captured into a CUDA graph, whose "
@@ -243,8 +244,9 @@ def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
     upd = 2
-    # assign: shadow copy, tensor-core tiles, SIMT leftovers, reduce, finish (precision 1); kernel, reduce, finish
-    asg = 5 if precision == 2 and w.d <= 128 else (4 if precision == 2 else 3)
+    # assign (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core
+    # tiles, SIMT leftovers (3)
+    asg = 3 if precision < 2 else (4 if precision == 2 or w.d > 128 else 5)
     # refine: run count, scan, run clusters, then Gram + exact recompute + merge (tensor cores, d <= 128) or the
     # two FP32 tile widths
     ref = 1 + 3 + 1 + (3 if precision >= 1 and 64 <= w.d <= 128 else 2)
@@ -273,13 +275,15 @@ def kernel_of(tag, precision=1, d=128):
     if tag == "refine" and precision >= 1 and 64 <= d <= 128:  # the library's dispatch: tensor-core Gram
         return "k_refine_gram"
     if tag == "assign" and precision == 2:
+        return "k_assign_rows_bf8"
+    if tag == "assign" and precision == 3:
         return "k_assign_tc"
     return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
             "init_graph": "k_init_graph"}[tag]
 
 
 # source file of each kernel whose DRAM traffic is recorded
-KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_tc": "assign_tc.cu", "k_update": "update.cu",
+KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_rows_bf8": "assign.cu", "k_assign_tc": "assign_tc.cu", "k_update": "update.cu",
                  "k_radix_scatter": "group.cu", "k_refine": "refine.cu", "k_refine_gram": "refine_tc.cu",
                  "k_refine_merge": "refine_tc.cu", "k_refine_exact": "refine_tc.cu", "k_init_graph": "init.cu"}
 

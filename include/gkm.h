@@ -75,8 +75,9 @@ typedef struct {
     int32_t precision;   /* 0: FP32 throughout; 1: refinement pair distances from a BF16
                             Gram on the tensor cores with an exact FP32 recompute of the
                             pairs inside its error bound (64 <= d <= 128; other widths
-                            use the FP32 kernels); 2: 1 and the assignment's BF16
-                            screening as in gk_assign_step.  All give the same graph.   */
+                            use the FP32 kernels); 2 and 3: 1 and the assignment's
+                            BF16 screening as in gk_assign_step.  All give the same
+                            graph.                                                      */
     int32_t reserved;    /* must be 0                                                   */
 } gk_graph_params;
 
@@ -128,14 +129,15 @@ GK_API int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32
  *   sum_d2    device double[1] or NULL: sum of best_d2 (n times the distortion
  *             after the assignment, Eq. 4), computed in FP64
  *   n_changed device int64[1] or NULL: samples whose label changed
- *   precision 0 or 1: candidate distances read the FP32 centroid rows; 2: they
- *             are first screened against a BF16 copy of the centroids (for
- *             d <= 128 on the tensor cores, 128 samples of adjacent clusters at
- *             a time) and every candidate within a rigorous error bound of the
- *             minimum is recomputed against the FP32 rows in the same order as
- *             with 0, so labels_out, best_d2, sum_d2 and n_changed are identical.
+ *   precision 0 or 1: candidate distances read the FP32 centroid rows; 2 and 3:
+ *             they are first screened against a BF16 copy of the centroids (2:
+ *             on the SIMT cores, one sample per warp; 3: for d <= 128 on the
+ *             tensor cores, 128 samples of adjacent clusters at a time) and
+ *             every candidate within a rigorous error bound of the minimum is
+ *             recomputed against the FP32 rows in the same order as with 0, so
+ *             labels_out, best_d2, sum_d2 and n_changed are identical.
  *   members   device int32[n] or NULL: the samples grouped by labels_in, as
- *             gk_group_by_label returns them; used by precision 2 to form the
+ *             gk_group_by_label returns them; used by precision 3 to form the
  *             tiles (NULL: the call groups them itself)
  */
 GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
@@ -167,7 +169,7 @@ GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  * row keeping its kappa smallest (distance, id) keys with no self and no
  * repeated id.  Pair distances are squared Euclidean in FP32, summed over
  * coordinates in ascending order, so a pair has the same bits in every round.
- *   precision  0: distances on the SIMT cores; 1 or 2: a BF16 Gram matrix per run
+ *   precision  0: distances on the SIMT cores; 1 to 3: a BF16 Gram matrix per run
  *              on the tensor cores gives d2 = |x|^2 + |y|^2 - 2 x.y, exact when
  *              the run's centred coordinates are integers of magnitude <= 255
  *              (and 2 d 255^2 < 2^24), otherwise every pair within a rigorous

@@ -212,14 +212,15 @@ int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
         return fail(GK_ERR_INVALID, "a required array is NULL");
     if (labels_in == labels_out)
         return fail(GK_ERR_INVALID, "labels_out must not alias labels_in");
-    if (precision < 0 || precision > 2)
-        return fail(GK_ERR_INVALID, "precision = %d (0, 1: FP32 rows; 2: BF16 screening + exact recompute)",
+    if (precision < 0 || precision > 3)
+        return fail(GK_ERR_INVALID,
+                    "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_ASSIGN, n, d, k);
-    if (precision == 2 && !members) {  // group the samples by their input label for the tile screening
+    if (precision == 3 && !members) {  // group the samples by their input label for the tile screening
         GK_CUDA(launch_group(labels_in, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st,
                              (cudaStream_t)stream));
         members = L.grp.members;
@@ -264,8 +265,8 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
-    if (precision < 0 || precision > 2)
-        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 or 2: tensor-core Gram + FP32 rerank)", precision);
+    if (precision < 0 || precision > 3)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 to 3: tensor-core Gram + FP32 rerank)", precision);
     if (!labels || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -328,8 +329,8 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
-    if (precision < 0 || precision > 2)
-        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 or 2: tensor-core Gram + FP32 rerank)", precision);
+    if (precision < 0 || precision > 3)
+        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 to 3: tensor-core Gram + FP32 rerank)", precision);
     if (!offsets || !members || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -352,8 +353,9 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (iters < 0 || 2 * iters + 1 > MAX_LOG)
         return fail(GK_ERR_INVALID, "iters = %d out of range [0, %d]", iters, (MAX_LOG - 1) / 2);
-    if (precision < 0 || precision > 2)
-        return fail(GK_ERR_INVALID, "precision = %d (0, 1: FP32 rows; 2: BF16 screening + exact recompute)",
+    if (precision < 0 || precision > 3)
+        return fail(GK_ERR_INVALID,
+                    "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
@@ -402,7 +404,7 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
     if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
         return rc;
     if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 ||
-        p->precision < 0 || p->precision > 2 || p->reserved != 0)
+        p->precision < 0 || p->precision > 3 || p->reserved != 0)
         return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
                     p->max_cluster, p->precision);
     if (!g_idx || !g_dist)

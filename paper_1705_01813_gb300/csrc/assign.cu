@@ -318,6 +318,151 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *_
     }
 }
 
+// k_assign_rows with the candidate distances screened against the BF16 copy Cb
+// of the centroids (half the bytes per candidate row).  Pass 1 takes every
+// candidate's distance D~ to Cb_r as k_assign_rows does (same lane layout,
+// same 8-candidate groups, BF16 rows widened exactly); with delta_r >=
+// ||C_r - Cb_r||, |D - D~| <= delta_r (2 sqrt(D~) + delta_r) for the exact
+// distances D, D~, and adding the FP32 rounding of both sums gives a bound E_r.
+// Pass 2 recomputes, one at a time and against C, every candidate whose lower
+// value D~ - E_r does not exceed the smallest upper value D~ + E_r (usually the
+// winner alone), with the lane partials and summation tree of k_assign_rows,
+// so the winner and its distance are that kernel's bit for bit.
+template <int NV>
+__global__ void __launch_bounds__(AS_WARPS * 32, NV >= 4 ? 3 : 4) k_assign_rows_bf8(
+    const float *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
+    const float *__restrict__ C, const __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ delta, int k,
+    const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout, float *__restrict__ best_out, DevStatus *st)
+{
+    __shared__ __align__(16) int s_q[AS_WARPS][AS_QROW];
+    __shared__ __align__(16) int s_h[AS_WARPS][AS_HASH];
+    __shared__ float s_lo[AS_WARPS][AS_QROW];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    int *qlist = s_q[w];
+    int *tab = s_h[w];
+    float *lov = s_lo[w];
+    constexpr int GS = NV >= 8 ? AS_G / 2 : AS_G;
+    const int d4 = d >> 2;
+    const float4 *C4 = reinterpret_cast<const float4 *>(C);
+    const uint2 *Cb4 = reinterpret_cast<const uint2 *>(Cb);  // 4 BF16 per 8 bytes
+    const float gam = (float)(d + 8) * 5.9604645e-8f;         // FP32 rounding of a d-term sum, relative
+    const int ncand = kappa + 1;
+
+    for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
+        float4 xv[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            int col = lane + 32 * v;
+            xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = lane * 4; q < AS_HASH; q += 128)
+            *reinterpret_cast<int4 *>(tab + q) = make_int4(-1, -1, -1, -1);
+        __syncwarp();
+        const int own = Lin[i];
+        int u = 0;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            int c = c0 + lane;
+            int lab = -1;
+            if (c == 0) {
+                lab = own;
+            } else if (c < ncand) {
+                int nb = __ldcs(G + i * kappa + (c - 1));
+                if ((unsigned)nb < (unsigned)n)
+                    lab = Lin[nb];
+                else
+                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
+            }
+            if (c < ncand && (unsigned)lab >= (unsigned)k) {
+                flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                lab = -1;
+            }
+            const unsigned peers = __match_any_sync(FULL_MASK, lab);
+            bool fresh = false;
+            if (lab >= 0 && (peers & lanemask_lt()) == 0u) {
+                unsigned h = ((unsigned)lab * 0x9E3779B1u) >> 24;
+                for (int probe = 0; probe < AS_HASH; probe++) {
+                    const int old = atomicCAS(tab + h, -1, lab);
+                    if (old == -1) {
+                        fresh = true;
+                        break;
+                    }
+                    if (old == lab)
+                        break;
+                    h = (h + 1) & (AS_HASH - 1);
+                }
+            }
+            const unsigned fr = __ballot_sync(FULL_MASK, fresh);
+            if (fresh)
+                qlist[u + __popc(fr & lanemask_lt())] = lab;
+            u += __popc(fr);
+        }
+        __syncwarp();
+        if (u > 0 && lane < GS)
+            qlist[u + lane] = qlist[0];
+        __syncwarp();
+
+        // pass 1: BF16 distances with their bounds
+        float best_up = __int_as_float(0x7f800000);
+        for (int g0 = 0; g0 < u; g0 += GS) {
+            int lab[GS];
+#pragma unroll
+            for (int c = 0; c < GS; c += 4) {
+                const int4 q4 = *reinterpret_cast<const int4 *>(qlist + g0 + c);
+                lab[c] = q4.x;
+                lab[c + 1] = q4.y;
+                lab[c + 2] = q4.z;
+                lab[c + 3] = q4.w;
+            }
+            float part[GS];
+#pragma unroll
+            for (int c = 0; c < GS; c++) {
+                const uint2 *row = Cb4 + (int64_t)lab[c] * d4;
+                part[c] = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
+            }
+            const float dt = transpose_reduce<GS>(part);
+            const int cl = lane / (32 / GS);
+            const float dl = __ldg(delta + qlist[g0 + cl]);
+            const float sq = sqrtf(fmaxf(dt, 0.f));
+            const float e = 1.01f * (dl * (2.f * sq + dl) + gam * (2.f * dt + dl * (2.f * sq + dl)));
+            if (lane % (32 / GS) == 0)
+                lov[g0 + cl] = dt - e;
+            best_up = fminf(best_up, dt + e);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            best_up = fminf(best_up, __shfl_xor_sync(FULL_MASK, best_up, o));
+        __syncwarp();
+        // pass 2: exact FP32 distances of the candidates that may be the minimum
+        float bd = __int_as_float(0x7f800000);
+        int br = 0x7fffffff;
+        for (int g0 = 0; g0 < u; g0 += 32) {
+            const int cnt = min(32, u - g0);
+            unsigned sel = __ballot_sync(FULL_MASK, lane < cnt && lov[g0 + lane] <= best_up);
+            while (sel) {
+                const int c = __ffs(sel) - 1;
+                sel &= sel - 1;
+                const int r = qlist[g0 + c];
+                const float4 *row = C4 + (int64_t)r * d4;
+                const float tot = warp_total(lane_partial<NV>(xv, d4, [&](int col) { return __ldg(row + col); }));
+                if (key_less(tot, r, bd, br)) {
+                    bd = tot;
+                    br = r;
+                }
+            }
+        }
+        if (lane == 0) {
+            if (br == 0x7fffffff)  // no valid candidate (own label out of range): keep the input label
+                br = own, bd = 0.f;
+            Lout[i] = br;
+            if (best_out)
+                best_out[i] = bd;
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // BF16 shadow of the centroids: Cb = bf16(C) and delta_r >= ||C_r - Cb_r||.
 // ---------------------------------------------------------------------------
@@ -641,6 +786,20 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
     const int d4 = (int)(d / 4);
     cudaError_t e;
     if (precision == 2 && vec4 && d4 <= 32 * 8) {
+        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
+#define GK_ASB8(NV)                                                                                              \
+    k_assign_rows_bf8<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,      \
+                                                             labels_in, labels_out, best, st)
+        if (d4 <= 32)
+            GK_ASB8(1);
+        else if (d4 <= 64)
+            GK_ASB8(2);
+        else if (d4 <= 128)
+            GK_ASB8(4);
+        else
+            GK_ASB8(8);
+#undef GK_ASB8
+    } else if (precision == 3 && vec4 && d4 <= 32 * 8) {
         k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
         const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
         if (tiles) {

@@ -73,7 +73,7 @@ def test_argument_errors(lib):
     assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 16,
                               None) == gkm.GK_ERR_INVALID
     assert b"too small" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 3, None, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 4, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"precision" in lib.gk_last_error()
     assert lib.gk_update_step(None, 10, 4, 4, P, 2, P, None, None, None, None, ws, 1 << 20,

@@ -102,7 +102,7 @@ def _assign_case(G, X, kappa, k, seed, graph="knn", precision=0):
     (1500, 1, 5, 3),          # d = 1
     (700, 16, 3, 128),        # kappa at its maximum, many repeated labels
 ])
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 2, 3])
 def test_assign_lockstep(G, n, d, k, kappa, precision):
     X = _blobs(n, d, max(2, k // 2), n + d)
     ex = _assign_case(G, X, kappa, k, seed=n, precision=precision)
@@ -127,9 +127,10 @@ def test_assign_bf16_shadow_equals_fp32(G, data):
     C64, _, _, _ = O.update(X, L, k)
     Xd, gd, Cd, Ld = _cuda(X), _cuda(gi), _cuda(C64.astype(np.float32)), _cuda(L)
     a = G.assign_step(Xd, gd, Cd, Ld, precision=0)
-    b = G.assign_step(Xd, gd, Cd, Ld, precision=2)
-    for x, y in zip(a, b):
-        assert torch.equal(x, y)
+    for prec in (2, 3):
+        b = G.assign_step(Xd, gd, Cd, Ld, precision=prec)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
 
 
 def test_assign_complete_graph_is_lloyd(G):
@@ -279,8 +280,8 @@ def test_assign_tensor_core_tiles_equal_fp32(G, n, d, k, kappa, graph):
     Xd, gd, Cd, Ld = _cuda(X), _cuda(gi), _cuda(C64.astype(np.float32)), _cuda(L)
     a = G.assign_step(Xd, gd, Cd, Ld, precision=0)
     off, mem, _ = G.group_by_label(Ld, k)
-    b = G.assign_step(Xd, gd, Cd, Ld, precision=2, members=mem)
-    c = G.assign_step(Xd, gd, Cd, Ld, precision=2)
+    b = G.assign_step(Xd, gd, Cd, Ld, precision=3, members=mem)
+    c = G.assign_step(Xd, gd, Cd, Ld, precision=3)
     for x, y, z in zip(a, b, c):
         assert torch.equal(x, y) and torch.equal(x, z)
 
@@ -291,7 +292,7 @@ def test_fit_precisions_identical(G):
     gi, _, _, _ = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=4, seed=w.seed)
     L0 = G.init_labels(w.n, w.k, 9)
     a = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=0)
-    for prec in (1, 2):
+    for prec in (1, 2, 3):
         b = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=prec)
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]) and a[3] == b[3]
 
@@ -300,7 +301,7 @@ def test_build_graph_precisions_identical(G):
     w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
     X = _cuda(w.data())
     a = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=0)
-    for prec in (1, 2):
+    for prec in (1, 2, 3):
         b = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=prec)
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
         assert a[3] == b[3]
