@@ -259,6 +259,46 @@ GK_API int gk_update_step_noalloc(const float *X, int64_t n, int64_t d, int64_t 
                                   float *C, int32_t *counts, double *sum_d2, void *stream);
 
 /*
+ * BF16 samples.  Each call below is the call of the same name without _bf16,
+ * with X holding the samples as BF16 values (their 16-bit patterns, row-major,
+ * leading dimension ld in elements, 2-byte aligned) instead of FP32.  Every
+ * element is widened exactly to FP32 when read and all arithmetic is the FP32
+ * path's, so the results are those of the FP32 call on the widened samples,
+ * bit for bit; the samples take half the device memory and half the read
+ * traffic.  (The deep-feature workload of the paper's largest experiment,
+ * Sec. 5, stores its 10^7 x 512 vectors this way.)  The assignment's BF16
+ * screening (precision 2 and 3) reads FP32 samples only: with BF16 samples the
+ * assignment takes precision 0 or 1 (gk_assign_step_bf16, gk_kmeans_fit_bf16,
+ * and p->precision of gk_build_knn_graph_bf16), else GK_ERR_INVALID.
+ */
+GK_API int gk_init_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                              int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_assign_step_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                               int32_t kappa, const float *C, int32_t k, const int32_t *labels_in,
+                               int32_t *labels_out, float *best_d2, double *sum_d2, int64_t *n_changed,
+                               int32_t precision, const int32_t *members, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_update_step_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                               float *C, int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members,
+                               void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_graph_refine_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                                int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist,
+                                void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_update_from_groups_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                      const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                                      void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_graph_refine_groups_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                       const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster,
+                                       int32_t precision, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
+                                       void *stream);
+GK_API int gk_build_knn_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p,
+                                   int32_t *g_idx, float *g_dist, int32_t *labels_out, double *e_log, void *ws,
+                                   size_t ws_bytes, void *stream);
+GK_API int gk_kmeans_fit_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx,
+                              int32_t kappa, int32_t iters, const int32_t *init_labels, uint64_t seed,
+                              int32_t precision, int32_t *labels_out, float *C_out, int32_t *counts_out,
+                              double *e_log, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Synchronise `stream`, return the status word the kernels of calls that used
  * `ws` recorded (GK_OK if none), and clear it.  Also returns GK_ERR_CUDA if the
  * stream itself reports an error.

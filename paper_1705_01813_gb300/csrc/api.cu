@@ -36,7 +36,7 @@ int fail(int code, const char *fmt, ...)
 constexpr int64_t MAX_ROWS = (int64_t)1 << 31;
 constexpr int MAX_LOG = 4096;  // e_log entries kept on the device
 
-int check_x(const float *X, int64_t n, int64_t d, int64_t ld, int64_t min_n)
+int check_x(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int64_t min_n)
 {
     if (!X)
         return fail(GK_ERR_INVALID, "X is NULL");
@@ -46,8 +46,8 @@ int check_x(const float *X, int64_t n, int64_t d, int64_t ld, int64_t min_n)
         return fail(GK_ERR_INVALID, "d = %lld out of range [1, %d]", (long long)d, MAX_D);
     if (ld < d)
         return fail(GK_ERR_INVALID, "ld = %lld < d = %lld", (long long)ld, (long long)d);
-    if ((reinterpret_cast<uintptr_t>(X) & 3) != 0)
-        return fail(GK_ERR_INVALID, "X is not 4-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(X) & (bf16 ? 1 : 3)) != 0)
+        return fail(GK_ERR_INVALID, "X is not %d-byte aligned", bf16 ? 2 : 4);
     return GK_OK;
 }
 
@@ -183,28 +183,41 @@ int gk_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, void *s
     return GK_OK;
 }
 
-int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed, int32_t *g_idx,
-                  float *g_dist, void *ws, size_t ws_bytes, void *stream)
+static int init_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                           int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
         return rc;
     if (!g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "graph arrays are NULL");
     if ((rc = check_ws(ws, ws_bytes, sizeof(DevStatus))))
         return rc;
-    GK_CUDA(launch_init_graph(X, n, d, ld, kappa, seed, g_idx, g_dist, static_cast<DevStatus *>(ws),
+    GK_CUDA(launch_init_graph(X, bf16, n, d, ld, kappa, seed, g_idx, g_dist, static_cast<DevStatus *>(ws),
                               (cudaStream_t)stream));
     return GK_OK;
 }
 
-int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
-                   const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                   double *sum_d2, int64_t *n_changed, int32_t precision, const int32_t *members, void *ws,
-                   size_t ws_bytes, void *stream)
+int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed, int32_t *g_idx,
+                  float *g_dist, void *ws, size_t ws_bytes, void *stream)
+{
+    return init_graph_impl(X, false, n, d, ld, kappa, seed, g_idx, g_dist, ws, ws_bytes, stream);
+}
+
+int gk_init_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                       int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream)
+{
+    return init_graph_impl(X, true, n, d, ld, kappa, seed, g_idx, g_dist, ws, ws_bytes, stream);
+}
+
+
+static int assign_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                            int32_t kappa, const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out,
+                            float *best_d2, double *sum_d2, int64_t *n_changed, int32_t precision,
+                            const int32_t *members, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -216,6 +229,9 @@ int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
         return fail(GK_ERR_INVALID,
                     "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
+    if (bf16 && precision >= 2)
+        return fail(GK_ERR_INVALID,
+                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
@@ -225,17 +241,36 @@ int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
                              (cudaStream_t)stream));
         members = L.grp.members;
     }
-    GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
+    GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
                           L.asg_scratch, L.st, (cudaStream_t)stream, precision, members));
     return GK_OK;
 }
 
-int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
-                   int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws, size_t ws_bytes,
-                   void *stream)
+int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                   const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                   double *sum_d2, int64_t *n_changed, int32_t precision, const int32_t *members, void *ws,
+                   size_t ws_bytes, void *stream)
+{
+    return assign_step_impl(X, false, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2,
+                            n_changed, precision, members, ws, ws_bytes, stream);
+}
+
+int gk_assign_step_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                        const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                        double *sum_d2, int64_t *n_changed, int32_t precision, const int32_t *members, void *ws,
+                        size_t ws_bytes, void *stream)
+{
+    return assign_step_impl(X, true, n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2, sum_d2, n_changed,
+                            precision, members, ws, ws_bytes, stream);
+}
+
+
+static int update_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *labels,
+                            int32_t k, float *C, int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members,
+                            void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 1)))
+    if ((rc = check_x(X, bf16, n, d, ld, 1)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -250,16 +285,31 @@ int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32
     int32_t *mem = members ? members : L.grp.members;
     int32_t *cnt = counts ? counts : L.grp.counts;
     GK_CUDA(launch_group(labels, n, k, off, mem, cnt, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, n, d, ld, off, mem, k, C, cnt, sum_d2, L.upd_scratch, s));
+    GK_CUDA(launch_update(X, bf16, n, d, ld, off, mem, k, C, cnt, sum_d2, L.upd_scratch, s));
     return GK_OK;
 }
 
-int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
-                    int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist, void *ws,
-                    size_t ws_bytes, void *stream)
+int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
+                   int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws, size_t ws_bytes,
+                   void *stream)
+{
+    return update_step_impl(X, false, n, d, ld, labels, k, C, counts, sum_d2, offsets, members, ws, ws_bytes, stream);
+}
+
+int gk_update_step_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                        float *C, int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws,
+                        size_t ws_bytes, void *stream)
+{
+    return update_step_impl(X, true, n, d, ld, labels, k, C, counts, sum_d2, offsets, members, ws, ws_bytes, stream);
+}
+
+
+static int graph_refine_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *labels,
+                             int32_t k, int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx,
+                             float *g_dist, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -275,10 +325,27 @@ int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int3
     L = carve(ws, GK_OP_REFINE, n, d, k);
     cudaStream_t s = (cudaStream_t)stream;
     GK_CUDA(launch_group(labels, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist,
+    GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, kappa, max_cluster, g_idx, g_dist,
                           L.ref_scratch, L.st, s, precision));
     return GK_OK;
 }
+
+int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                    int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist, void *ws,
+                    size_t ws_bytes, void *stream)
+{
+    return graph_refine_impl(X, false, n, d, ld, labels, k, kappa, max_cluster, precision, g_idx, g_dist, ws,
+                             ws_bytes, stream);
+}
+
+int gk_graph_refine_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                         int32_t kappa, int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist,
+                         void *ws, size_t ws_bytes, void *stream)
+{
+    return graph_refine_impl(X, true, n, d, ld, labels, k, kappa, max_cluster, precision, g_idx, g_dist, ws,
+                             ws_bytes, stream);
+}
+
 
 int gk_group_by_label(const int32_t *labels, int64_t n, int32_t k, int32_t *offsets, int32_t *members,
                       int32_t *counts, void *ws, size_t ws_bytes, void *stream)
@@ -299,12 +366,12 @@ int gk_group_by_label(const int32_t *labels, int64_t n, int32_t k, int32_t *offs
     return GK_OK;
 }
 
-int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2, void *ws,
-                          size_t ws_bytes, void *stream)
+static int update_from_groups_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                   const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                                   void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 1)))
+    if ((rc = check_x(X, bf16, n, d, ld, 1)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -314,16 +381,33 @@ int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, cons
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_UPDATE, n, d, k);
-    GK_CUDA(launch_update(X, n, d, ld, offsets, members, k, C, counts, sum_d2, L.upd_scratch, (cudaStream_t)stream));
+    GK_CUDA(launch_update(X, bf16, n, d, ld, offsets, members, k, C, counts, sum_d2, L.upd_scratch,
+                          (cudaStream_t)stream));
     return GK_OK;
 }
 
-int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t precision,
-                           int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream)
+int gk_update_from_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2, void *ws,
+                          size_t ws_bytes, void *stream)
+{
+    return update_from_groups_impl(X, false, n, d, ld, offsets, members, k, C, counts, sum_d2, ws, ws_bytes, stream);
+}
+
+int gk_update_from_groups_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                               const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2, void *ws,
+                               size_t ws_bytes, void *stream)
+{
+    return update_from_groups_impl(X, true, n, d, ld, offsets, members, k, C, counts, sum_d2, ws, ws_bytes, stream);
+}
+
+
+static int graph_refine_groups_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld,
+                                    const int32_t *offsets, const int32_t *members, int32_t k, int32_t kappa,
+                                    int32_t max_cluster, int32_t precision, int32_t *g_idx, float *g_dist, void *ws,
+                                    size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -337,17 +421,36 @@ int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, con
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_REFINE, n, d, k);
-    GK_CUDA(launch_refine(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch, L.st,
+    GK_CUDA(launch_refine(X, bf16, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch, L.st,
                           (cudaStream_t)stream, precision));
     return GK_OK;
 }
 
-int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
-                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t precision, int32_t *labels_out,
-                  float *C_out, int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+int gk_graph_refine_groups(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t precision,
+                           int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream)
+{
+    return graph_refine_groups_impl(X, false, n, d, ld, offsets, members, k, kappa, max_cluster, precision, g_idx,
+                                    g_dist, ws, ws_bytes, stream);
+}
+
+int gk_graph_refine_groups_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                                const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster,
+                                int32_t precision, int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes,
+                                void *stream)
+{
+    return graph_refine_groups_impl(X, true, n, d, ld, offsets, members, k, kappa, max_cluster, precision, g_idx,
+                                    g_dist, ws, ws_bytes, stream);
+}
+
+
+static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k,
+                           const int32_t *g_idx, int32_t kappa, int32_t iters, const int32_t *init_labels,
+                           uint64_t seed, int32_t precision, int32_t *labels_out, float *C_out, int32_t *counts_out,
+                           double *e_log, void *ws, size_t ws_bytes, void *stream)
 {
     int rc;
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
         return rc;
     if (k < 1)
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
@@ -357,6 +460,9 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
         return fail(GK_ERR_INVALID,
                     "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
+    if (bf16 && precision >= 2)
+        return fail(GK_ERR_INVALID,
+                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
@@ -375,12 +481,12 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
         GK_CUDA(launch_init_labels(n, k, seed, cur, s));
     GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)k * (size_t)d, s));
     GK_CUDA(launch_group(cur, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
+    GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
     for (int t = 0; t < iters; t++) {
-        GK_CUDA(launch_assign(X, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
+        GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
                               L.asg_scratch, L.st, s, precision, L.grp.members));
         GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
-        GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
+        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
                               L.upd_scratch, s));
         int32_t *tmp = cur;
         cur = nxt;
@@ -395,18 +501,40 @@ int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, c
     return GK_OK;
 }
 
-int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p, int32_t *g_idx,
-                       float *g_dist, int32_t *labels_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx, int32_t kappa,
+                  int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t precision, int32_t *labels_out,
+                  float *C_out, int32_t *counts_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+{
+    return kmeans_fit_impl(X, false, n, d, ld, k, g_idx, kappa, iters, init_labels, seed, precision, labels_out,
+                           C_out, counts_out, e_log, ws, ws_bytes, stream);
+}
+
+int gk_kmeans_fit_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t k, const int32_t *g_idx,
+                       int32_t kappa, int32_t iters, const int32_t *init_labels, uint64_t seed, int32_t precision,
+                       int32_t *labels_out, float *C_out, int32_t *counts_out, double *e_log, void *ws,
+                       size_t ws_bytes, void *stream)
+{
+    return kmeans_fit_impl(X, true, n, d, ld, k, g_idx, kappa, iters, init_labels, seed, precision, labels_out,
+                           C_out, counts_out, e_log, ws, ws_bytes, stream);
+}
+
+
+static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p,
+                                int32_t *g_idx, float *g_dist, int32_t *labels_out, double *e_log, void *ws,
+                                size_t ws_bytes, void *stream)
 {
     int rc;
     if (!p)
         return fail(GK_ERR_INVALID, "params is NULL");
-    if ((rc = check_x(X, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
         return rc;
     if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 ||
         p->precision < 0 || p->precision > 3 || p->reserved != 0)
         return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
                     p->max_cluster, p->precision);
+    if (bf16 && p->precision >= 2)
+        return fail(GK_ERR_INVALID,
+                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
     if (!g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "graph arrays are NULL");
     const int32_t k0 = build_k0(n, p->xi);
@@ -417,21 +545,21 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
     cudaStream_t s = (cudaStream_t)stream;
     const int tau = p->tau;
     int32_t *cur = L.labels_a, *nxt = L.labels_b;
-    GK_CUDA(launch_init_graph(X, n, d, ld, p->kappa, p->seed, g_idx, g_dist, L.st, s));
+    GK_CUDA(launch_init_graph(X, bf16, n, d, ld, p->kappa, p->seed, g_idx, g_dist, L.st, s));
     GK_CUDA(launch_init_labels(n, k0, p->seed, cur, s));
     GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)k0 * (size_t)d, s));
     GK_CUDA(launch_group(cur, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
+    GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
                           L.upd_scratch, s));
     for (int t = 0; t < tau; t++) {
         // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
-        GK_CUDA(launch_assign(X, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
+        GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
                               nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
         GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-        GK_CUDA(launch_update(X, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
+        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
                               L.elog + 2 + 2 * t, L.upd_scratch, s));
         // exhaustive pairs inside the clusters of the new partition
-        GK_CUDA(launch_refine(X, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
+        GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
                               g_dist, L.ref_scratch, L.st, s, p->precision));
         int32_t *tmp = cur;
         cur = nxt;
@@ -447,6 +575,20 @@ int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const g
     }
     return GK_OK;
 }
+
+int gk_build_knn_graph(const float *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p, int32_t *g_idx,
+                       float *g_dist, int32_t *labels_out, double *e_log, void *ws, size_t ws_bytes, void *stream)
+{
+    return build_knn_graph_impl(X, false, n, d, ld, p, g_idx, g_dist, labels_out, e_log, ws, ws_bytes, stream);
+}
+
+int gk_build_knn_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const gk_graph_params *p,
+                            int32_t *g_idx, float *g_dist, int32_t *labels_out, double *e_log, void *ws,
+                            size_t ws_bytes, void *stream)
+{
+    return build_knn_graph_impl(X, true, n, d, ld, p, g_idx, g_dist, labels_out, e_log, ws, ws_bytes, stream);
+}
+
 
 int gk_read_status(void *ws, void *stream)
 {

@@ -16,6 +16,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 namespace gkm {
 
 bool assign_tc_supported(int64_t d, int64_t ld, const float *X, const float *C, int32_t kappa);
@@ -69,8 +71,8 @@ __device__ __forceinline__ float cand_d2<1>(const float *__restrict__ xs, const 
     return a0 + a1;
 }
 
-template <int VEC>
-__global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+template <int VEC, typename XT>
+__global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
                                                           const int32_t *__restrict__ G, int kappa,
                                                           const float *__restrict__ C, int k,
                                                           const int32_t *__restrict__ Lin,
@@ -92,14 +94,13 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const float *__restric
     const int ncand = kappa + 1;
     for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
         // stage x_i
-        const float *xi = X + i * ld;
+        const XT *xi = X + i * ld;
         if (VEC == 4) {
-            const float4 *x4 = reinterpret_cast<const float4 *>(xi);
             for (int t = lane; t < (d >> 2); t += 32)
-                reinterpret_cast<float4 *>(xs)[t] = x4[t];
+                reinterpret_cast<float4 *>(xs)[t] = ldx4<XT>(xi + 4 * t);
         } else {
             for (int t = lane; t < d; t += 32)
-                xs[t] = xi[t];
+                xs[t] = ldx(xi + t);
         }
         // candidate labels: slot 0 is the own label, slot 1 + j the label of neighbour j
         const int own = Lin[i];
@@ -198,8 +199,8 @@ constexpr int AS_HASH = 256;                                  // slots of the pe
 constexpr int AS_QROW = (AS_QCAP + AS_G + 3) / 4 * 4;         // candidate list row, padding included
 static_assert(AS_HASH > AS_QCAP, "the label set must never fill up");
 
-template <int NV>
-__global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *__restrict__ X, int64_t n, int d,
+template <int NV, typename XT>
+__global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const XT *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
                                                                const int32_t *__restrict__ Lin,
@@ -217,12 +218,12 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const float *_
     const int ncand = kappa + 1;
 
     for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
-        const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
+        const XT *xrow = X + i * ld;
         float4 xv[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             int col = lane + 32 * v;
-            xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xv[v] = col < d4 ? ldx4<XT, true>(xrow + 4 * col) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int q = lane * 4; q < AS_HASH; q += 128)
@@ -758,10 +759,11 @@ size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d)
     return part + shadow + best + tiles + sel;
 }
 
-cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
-                          const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,
-                          int precision, const int32_t *members)
+template <typename XT>
+static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                            const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
+                            double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,
+                            int precision, const int32_t *members)
 {
     char *sp = static_cast<char *>(scratch);
     double *blk_sum = reinterpret_cast<double *>(sp);
@@ -781,51 +783,59 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
     sp += al256((size_t)n * 8 * 4);
     int32_t *sel_n = reinterpret_cast<int32_t *>(sp);
 
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
-                      ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+    const bool vec4 = x_vec4(X, d, ld) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int d4 = (int)(d / 4);
     cudaError_t e;
-    if (precision == 2 && vec4 && d4 <= 32 * 8) {
-        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
+    bool done = false;
+    if constexpr (std::is_same_v<XT, float>) {  // BF16 screening: FP32 samples only
+        if (precision == 2 && vec4 && d4 <= 32 * 8) {
+            k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
+                                                                                      cnorm);
 #define GK_ASB8(NV)                                                                                              \
     k_assign_rows_bf8<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,      \
                                                              labels_in, labels_out, best, st)
-        if (d4 <= 32)
-            GK_ASB8(1);
-        else if (d4 <= 64)
-            GK_ASB8(2);
-        else if (d4 <= 128)
-            GK_ASB8(4);
-        else
-            GK_ASB8(8);
+            if (d4 <= 32)
+                GK_ASB8(1);
+            else if (d4 <= 64)
+                GK_ASB8(2);
+            else if (d4 <= 128)
+                GK_ASB8(4);
+            else
+                GK_ASB8(8);
 #undef GK_ASB8
-    } else if (precision == 3 && vec4 && d4 <= 32 * 8) {
-        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
-        const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
-        if (tiles) {
-            if ((e = launch_assign_tc(X, n, d, ld, g_idx, kappa, C, Cb, delta, cnorm, k, labels_in, members,
-                                      sel_lab, sel_n, tile_flag, st, s)) != cudaSuccess)
-                return e;
-        }
+            done = true;
+        } else if (precision == 3 && vec4 && d4 <= 32 * 8) {
+            k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
+                                                                                      cnorm);
+            const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);
+            if (tiles) {
+                if ((e = launch_assign_tc(X, n, d, ld, g_idx, kappa, C, Cb, delta, cnorm, k, labels_in, members,
+                                          sel_lab, sel_n, tile_flag, st, s)) != cudaSuccess)
+                    return e;
+            }
 #define GK_ASGB(NV, T)                                                                                           \
     k_assign_rows_bf<NV, T><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,   \
                                                                 labels_in, labels_out, best, blk_sum, blk_chg,      \
                                                                 members, tile_flag, sel_lab, sel_n, st)
-        if (tiles) {
-            GK_ASGB(1, true);  // d <= 128 on the tensor-core path
-        } else if (d4 <= 32) {
-            GK_ASGB(1, false);
-        } else if (d4 <= 64) {
-            GK_ASGB(2, false);
-        } else if (d4 <= 128) {
-            GK_ASGB(4, false);
-        } else {
-            GK_ASGB(8, false);
-        }
+            if (tiles) {
+                GK_ASGB(1, true);  // d <= 128 on the tensor-core path
+            } else if (d4 <= 32) {
+                GK_ASGB(1, false);
+            } else if (d4 <= 64) {
+                GK_ASGB(2, false);
+            } else if (d4 <= 128) {
+                GK_ASGB(4, false);
+            } else {
+                GK_ASGB(8, false);
+            }
 #undef GK_ASGB
+            done = true;
+        }
+    }
+    if (done) {
     } else if (vec4 && d4 <= 32 * 8) {
 #define GK_ASG(NV)                                                                                               \
-    k_assign_rows<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,         \
+    k_assign_rows<NV, XT><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,         \
                                                           labels_out, best, st)
         if (d4 <= 32)
             GK_ASG(1);
@@ -841,16 +851,16 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
         size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;
         const int shm_max = (int)(sizeof(float) * (size_t)AS_WARPS * MAX_D + sizeof(int) * AS_WARPS * AS_QCAP);
         if (vec4) {
-            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<4>), shm_max)) !=
+            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<4, XT>), shm_max)) !=
                 cudaSuccess)
                 return e;
-            k_assign<4><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+            k_assign<4, XT><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
                                                                 labels_out, best, blk_sum, blk_chg, st);
         } else {
-            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<1>), shm_max)) !=
+            if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<1, XT>), shm_max)) !=
                 cudaSuccess)
                 return e;
-            k_assign<1><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
+            k_assign<1, XT><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
                                                                 labels_out, best, blk_sum, blk_chg, st);
         }
     }
@@ -859,6 +869,18 @@ cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, cons
         k_assign_finish<<<1, 1024, 0, s>>>(blk_sum, blk_chg, AS_BLOCKS, sum_d2, n_changed);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_assign(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                          int32_t kappa, const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out,
+                          float *best_d2, double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st,
+                          cudaStream_t s, int precision, const int32_t *members)
+{
+    if (bf16)
+        return assign_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, g_idx, kappa, C, k, labels_in, labels_out,
+                        best_d2, sum_d2, n_changed, scratch, st, s, precision, members);
+    return assign_t(static_cast<const float *>(X), n, d, ld, g_idx, kappa, C, k, labels_in, labels_out, best_d2,
+                    sum_d2, n_changed, scratch, st, s, precision, members);
 }
 
 }  // namespace gkm

@@ -39,14 +39,6 @@ __device__ __forceinline__ float transpose_reduce(float (&v)[G])
 
 __device__ __forceinline__ float transpose_reduce32(float (&v)[32]) { return transpose_reduce<32>(v); }
 
-__device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
-{
-    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&v.x);
-    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v.y);
-    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-    return make_float4(fa.x, fa.y, fb.x, fb.y);
-}
-
 // Partial (per lane) squared distance of x (registers) to a row of 16-byte
 // vectors, in the accumulation order of the assignment kernels: two
 // accumulators, (a0, a1) += (e0^2, e1^2), then += (e2^2, e3^2) per vector,

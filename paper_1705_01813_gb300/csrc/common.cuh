@@ -1,6 +1,7 @@
 // Shared device helpers of libgkm (CUDA, sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,36 +53,61 @@ __device__ __forceinline__ uint64_t sm64_draw(uint64_t key, uint64_t counter)
     return sm64_mix(key + (counter + 1ull) * SM64_GAMMA);
 }
 
+// Samples are stored as FP32 or BF16; a BF16 element is widened exactly to
+// FP32 on load, and all arithmetic is FP32, so BF16 samples give the results
+// of their FP32 widening bit for bit.
+__device__ __forceinline__ float4 bf16x4_to_float4(uint2 v)
+{
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&v.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&v.y);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <typename XT>
+__device__ __forceinline__ float ldx(const XT *p);
+template <>
+__device__ __forceinline__ float ldx<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+
+// Four consecutive elements (16-byte aligned for FP32, 8-byte aligned for BF16); STREAM: read once (no L1 reuse).
+template <typename XT, bool STREAM = false>
+__device__ __forceinline__ float4 ldx4(const XT *p);
+template <>
+__device__ __forceinline__ float4 ldx4<float, false>(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+template <>
+__device__ __forceinline__ float4 ldx4<float, true>(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+template <>
+__device__ __forceinline__ float4 ldx4<__nv_bfloat16, false>(const __nv_bfloat16 *p)
+{
+    return bf16x4_to_float4(__ldg(reinterpret_cast<const uint2 *>(p)));
+}
+template <>
+__device__ __forceinline__ float4 ldx4<__nv_bfloat16, true>(const __nv_bfloat16 *p)
+{
+    return bf16x4_to_float4(__ldcs(reinterpret_cast<const uint2 *>(p)));
+}
+
+// Rows of X can be read four elements at a time.
+template <typename XT>
+inline bool x_vec4(const XT *X, int64_t d, int64_t ld)
+{
+    return d % 4 == 0 && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(XT))) == 0;
+}
+
 // Squared Euclidean distance between two samples in FP32, one accumulator,
 // coordinates in ascending order: acc = fma(x_t - y_t, x_t - y_t, acc).
 // Every exact pair distance of the graph (initial graph, refinement, rerank)
 // uses this order, so that the distance of a pair is the same bits wherever it
 // is computed and d(i, j) == d(j, i).
-__device__ __forceinline__ float pair_d2_seq(const float *__restrict__ a, const float *__restrict__ b, int d)
+template <typename XT>
+__device__ __forceinline__ float pair_d2_seq(const XT *__restrict__ a, const XT *__restrict__ b, int d)
 {
     float acc = 0.f;
     for (int t = 0; t < d; t++) {
-        float diff = a[t] - b[t];
+        float diff = ldx(a + t) - ldx(b + t);
         acc = fmaf(diff, diff, acc);
-    }
-    return acc;
-}
-
-// The same sum with 16-byte loads (a, b 16-byte aligned, d a multiple of 4):
-// the accumulation order, and therefore the result, is that of pair_d2_seq.
-__device__ __forceinline__ float pair_d2_seq4(const float *__restrict__ a, const float *__restrict__ b, int d)
-{
-    const float4 *a4 = reinterpret_cast<const float4 *>(a);
-    const float4 *b4 = reinterpret_cast<const float4 *>(b);
-    float acc = 0.f;
-#pragma unroll 4
-    for (int t = 0; t < (d >> 2); t++) {
-        float4 x = a4[t], y = __ldg(b4 + t);
-        float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
-        acc = fmaf(e0, e0, acc);
-        acc = fmaf(e1, e1, acc);
-        acc = fmaf(e2, e2, acc);
-        acc = fmaf(e3, e3, acc);
     }
     return acc;
 }
@@ -146,10 +172,11 @@ struct Carver {
 // device, the first time only (thread-safe); `bytes` must be the same on every call.
 cudaError_t set_max_smem(const void *kernel, int bytes);
 
-// Internal launchers (each returns cudaError_t of the launch).
+// Internal launchers (each returns cudaError_t of the launch).  Those that read the samples take them as
+// X (FP32, or BF16 when bf16 is set) with leading dimension ld in elements.
 cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s);
-cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
-                              int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s);
+cudaError_t launch_init_graph(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t kappa,
+                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s);
 
 // Grouping of samples by label (CSR).  Scratch sizes via group_scratch_bytes().
 size_t group_scratch_bytes(int64_t n, int32_t k);
@@ -161,27 +188,28 @@ size_t scan_scratch_bytes(int64_t count);
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int64_t count, void *scratch, cudaStream_t s);
 
 size_t update_scratch_bytes(int64_t n, int32_t k);
-cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
                           void *scratch, cudaStream_t s);
 
 size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d);
-// precision 0 and 1: FP32 candidate rows; 2: BF16 screening (tensor cores over 128-sample tiles when
-// members, the grouping of labels_in, is given and d <= 128) with the exact FP32 recompute (same results)
-cudaError_t launch_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
-                          const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out, float *best_d2,
-                          double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st, cudaStream_t s,
-                          int precision, const int32_t *members);
+// precision 0 and 1: FP32 candidate rows; 2: BF16 screening on the SIMT cores; 3: on the tensor cores over
+// 128-sample tiles when members, the grouping of labels_in, is given and d <= 128; both with the exact FP32
+// recompute (same results).  2 and 3 take FP32 samples only.
+cudaError_t launch_assign(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                          int32_t kappa, const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out,
+                          float *best_d2, double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st,
+                          cudaStream_t s, int precision, const int32_t *members);
 
 void set_last_error(const char *msg);
 
 size_t refine_scratch_bytes(int64_t n, int32_t k);
 // precision 0: FP32 pair distances on the SIMT cores; 1: tensor-core Gram with exact FP32 rerank
-cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+cudaError_t launch_refine(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                           float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision);
 size_t refine_tc_scratch_bytes(int64_t n, int32_t k);
-cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+cudaError_t launch_refine_tc(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
                              int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
                              void *scratch, DevStatus *st, cudaStream_t s);

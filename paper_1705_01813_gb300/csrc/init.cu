@@ -41,13 +41,18 @@ __host__ __device__ inline int ig_batch(int kappa)
     return (kappa + nb - 1) / nb;
 }
 
-// Dynamic shared memory per warp: on the vector path a batch of rows, each
-// padded by 16 bytes so that the 32 lanes reading one row each hit distinct
-// banks; on both paths at least the kappa 8-byte keys of the rank sort (they
-// reuse the area).  Kernel and launcher both size the warp areas with this.
-__host__ __device__ inline size_t ig_warp_bytes(int kappa, bool vec4)
+// Staged row stride in elements: IG_DC plus 16 bytes, so that the 32 lanes
+// reading their own rows 16 bytes at a time hit distinct banks.
+template <typename XT>
+__host__ __device__ constexpr int ig_stride() { return IG_DC + 16 / (int)sizeof(XT); }
+
+// Dynamic shared memory per warp: on the vector path a batch of rows; on both
+// paths at least the kappa 8-byte keys of the rank sort (they reuse the area).
+// Kernel and launcher both size the warp areas with this.
+template <typename XT>
+__host__ __device__ inline size_t ig_warp_bytes(int kappa, bool vec)
 {
-    size_t b = vec4 ? sizeof(float) * (size_t)ig_batch(kappa) * (IG_DC + 4) : 0;
+    size_t b = vec ? sizeof(XT) * (size_t)ig_batch(kappa) * ig_stride<XT>() : 0;
     if (b < sizeof(uint64_t) * (size_t)kappa)
         b = sizeof(uint64_t) * (size_t)kappa;
     return (b + 15) & ~size_t(15);
@@ -67,12 +72,29 @@ __device__ __forceinline__ uint64_t mod_n(uint64_t a, uint64_t n, uint64_t minv)
     return r;
 }
 
-__global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__restrict__ X, int64_t n, int d,
+// 16 bytes of elements as floats: from shared memory (SHARED) or through L1.
+template <typename XT, bool SHARED>
+__device__ __forceinline__ void ld16(const XT *p, float (&v)[16 / sizeof(XT)])
+{
+    const uint4 q = SHARED ? *reinterpret_cast<const uint4 *>(p) : __ldg(reinterpret_cast<const uint4 *>(p));
+    if constexpr (sizeof(XT) == 4) {
+        v[0] = __uint_as_float(q.x);
+        v[1] = __uint_as_float(q.y);
+        v[2] = __uint_as_float(q.z);
+        v[3] = __uint_as_float(q.w);
+    } else {
+        const float4 a = bf16x4_to_float4(make_uint2(q.x, q.y)), b = bf16x4_to_float4(make_uint2(q.z, q.w));
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    }
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__restrict__ X, int64_t n, int d,
                                                               int64_t ld, int kappa, uint64_t key, uint64_t minv,
                                                               int32_t *__restrict__ g_idx,
-                                                              float *__restrict__ g_dist, DevStatus *st,
-                                                              bool vec4)
+                                                              float *__restrict__ g_dist, DevStatus *st, bool vec)
 {
+    constexpr int RS = ig_stride<XT>(), E = 16 / (int)sizeof(XT);
     __shared__ int s_idx[IG_WARPS][MAX_KAPPA];
     __shared__ uint64_t s_bar[IG_WARPS];
     // dynamic: per warp one batch of staged rows; after the distances, the row's keys
@@ -80,7 +102,8 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *ridx = s_idx[w];
     const int B = ig_batch(kappa);
-    float *rows = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(s_dyn) + (size_t)w * ig_warp_bytes(kappa, vec4));
+    XT *rows =
+        reinterpret_cast<XT *>(reinterpret_cast<unsigned char *>(s_dyn) + (size_t)w * ig_warp_bytes<XT>(kappa, vec));
     uint64_t *rkey = reinterpret_cast<uint64_t *>(rows);
     uint64_t *bar = s_bar + w;
     if (lane == 0) {
@@ -119,27 +142,26 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__
             got = min(kappa, got + __popc(oks));
             __syncwarp();
         }
-        const float *xi = X + i * ld;
+        const XT *xi = X + i * ld;
         float dist[(MAX_KAPPA + 31) / 32];  // distance of neighbour b0 + lane of batch b (lane < batch size)
-        if (vec4) {
+        if (vec) {
             // A batch's neighbour rows are copied to shared memory by the TMA engine
             // (one bulk copy per row, issued by the row's lane, counted on the warp's
             // mbarrier); lane q then sums its row's squared differences in ascending
             // coordinate order (the order of pair_d2_seq), x_i coming through L1.
-            const float2 m1 = make_float2(-1.f, -1.f);
             for (int b0 = 0, bi = 0; b0 < kappa; b0 += B, bi++) {
                 const int nb = min(B, kappa - b0);
                 float acc = 0.f;
                 for (int t0 = 0; t0 < d; t0 += IG_DC) {
                     const int dc = min(IG_DC, d - t0);
+                    const uint32_t bytes = (uint32_t)(dc * (int)sizeof(XT));
                     __syncwarp();                 // the previous rows are no longer read
                     tc::fence_proxy_async_smem();  // ... before the async proxy rewrites them
                     if (lane == 0)
-                        tc::mbar_arrive_expect_tx(bar, (uint32_t)(nb * dc * 4));
+                        tc::mbar_arrive_expect_tx(bar, (uint32_t)nb * bytes);
                     __syncwarp();
                     if (lane < nb)
-                        tc::bulk_g2s(rows + lane * (IG_DC + 4), X + (int64_t)ridx[b0 + lane] * ld + t0,
-                                     (uint32_t)(dc * 4), bar);
+                        tc::bulk_g2s(rows + lane * RS, X + (int64_t)ridx[b0 + lane] * ld + t0, bytes, bar);
                     const bool ok = __all_sync(FULL_MASK, tc::mbar_wait_bounded(bar, phase, IG_WAIT_ITERS));
                     phase ^= 1u;
                     if (!ok) {  // the copies did not complete: report, give them one more bounded wait, stop
@@ -149,16 +171,16 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__
                         return;
                     }
                     if (lane < nb) {
-                        const float4 *xa = reinterpret_cast<const float4 *>(xi + t0);
-                        const float4 *xb = reinterpret_cast<const float4 *>(rows + lane * (IG_DC + 4));
-                        for (int t = 0; t < dc / 4; t++) {
-                            const float4 va = __ldg(xa + t), vb = xb[t];
-                            const float2 e01 = __ffma2_rn(make_float2(vb.x, vb.y), m1, make_float2(va.x, va.y));
-                            const float2 e23 = __ffma2_rn(make_float2(vb.z, vb.w), m1, make_float2(va.z, va.w));
-                            acc = fmaf(e01.x, e01.x, acc);
-                            acc = fmaf(e01.y, e01.y, acc);
-                            acc = fmaf(e23.x, e23.x, acc);
-                            acc = fmaf(e23.y, e23.y, acc);
+                        const XT *xa = xi + t0, *xb = rows + lane * RS;
+                        for (int t = 0; t < dc; t += E) {
+                            float va[E], vb[E];
+                            ld16<XT, false>(xa + t, va);
+                            ld16<XT, true>(xb + t, vb);
+#pragma unroll
+                            for (int e = 0; e < E; e++) {
+                                const float df = va[e] - vb[e];
+                                acc = fmaf(df, df, acc);
+                            }
                         }
                     }
                 }
@@ -198,22 +220,33 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const float *__
     }
 }
 
-cudaError_t launch_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
-                              int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
+template <typename XT>
+static cudaError_t init_graph_t(const XT *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                                int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
 {
     int64_t blocks = (n + IG_WARPS - 1) / IG_WARPS;
     if (blocks > 152 * 64)
         blocks = 152 * 64;
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    const size_t shm = IG_WARPS * ig_warp_bytes(kappa, vec4);
-    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_init_graph),
-                                 (int)(IG_WARPS * ig_warp_bytes(MAX_KAPPA, true)));
+    // bulk copies of row chunks need 16-byte aligned rows and chunk sizes
+    const bool vec = (d * (int64_t)sizeof(XT)) % 16 == 0 && (ld * (int64_t)sizeof(XT)) % 16 == 0 &&
+                     (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const size_t shm = IG_WARPS * ig_warp_bytes<XT>(kappa, vec);
+    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_init_graph<XT>),
+                                 (int)(IG_WARPS * ig_warp_bytes<XT>(MAX_KAPPA, true)));
     if (e != cudaSuccess)
         return e;
     const uint64_t minv = ~0ull / (uint64_t)n;
-    k_init_graph<<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, minv, g_idx,
-                                                           g_dist, st, vec4);
+    k_init_graph<XT><<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, minv,
+                                                               g_idx, g_dist, st, vec);
     return cudaGetLastError();
+}
+
+cudaError_t launch_init_graph(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t kappa,
+                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
+{
+    if (bf16)
+        return init_graph_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s);
+    return init_graph_t(static_cast<const float *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s);
 }
 
 }  // namespace gkm

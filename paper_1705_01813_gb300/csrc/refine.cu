@@ -25,6 +25,8 @@
 #include "common.cuh"
 #include "merge.cuh"
 
+#include <type_traits>
+
 namespace gkm {
 
 constexpr int RF_THREADS = 256;
@@ -67,8 +69,8 @@ __global__ void k_count_runs(const int32_t *__restrict__ off, int k, int cap, in
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const float *__restrict__ X, int64_t n, int d, int64_t ld,
+template <int T, typename XT>
+__global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
                                                        const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ mem,
                                                        const int32_t *__restrict__ run_off,
@@ -141,10 +143,10 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const fl
                         int row = e / RF_DK, tt = e % RF_DK;
                         int t = t0 + tt;
                         int a = rid[row];
-                        xr[tt * XS + row] = (a >= 0 && t < d) ? __ldg(X + (int64_t)a * ld + t) : 0.f;
+                        xr[tt * XS + row] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
                         if (!same) {
                             int b = cid[row];
-                            xc[tt * XS + row] = (b >= 0 && t < d) ? __ldg(X + (int64_t)b * ld + t) : 0.f;
+                            xc[tt * XS + row] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
                         }
                     }
                     __syncthreads();
@@ -204,9 +206,10 @@ size_t refine_scratch_bytes(int64_t n, int32_t k)
     return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n, k);
 }
 
-cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                          const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
-                          float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision)
+template <typename XT>
+static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                            const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
+                            float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision)
 {
     int32_t *nruns = static_cast<int32_t *>(scratch);
     int32_t *run_off = nruns + (k + 1);
@@ -215,10 +218,10 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
     cudaError_t e =
-        set_max_smem(reinterpret_cast<const void *>(k_refine<64>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
+        set_max_smem(reinterpret_cast<const void *>(k_refine<64, XT>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
     if (e != cudaSuccess)
         return e;
-    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128>),
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128, XT>),
                           (int)RefineTile<128>::smem_bytes(MAX_KAPPA))) != cudaSuccess)
         return e;
     k_count_runs<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(offsets, k, max_cluster, nruns);
@@ -233,21 +236,33 @@ cudaError_t launch_refine(const float *X, int64_t n, int64_t d, int64_t ld, cons
     // the fixed per-run cost of the Gram path (20k x 32: 0.18 ms against 0.12 ms per call).
     if (precision >= 1 && d >= 64 && d <= 128) {
         // tensor-core Gram for runs of <= 128 members, the FP32 kernel for longer runs
-        if ((e = launch_refine_tc(X, n, d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, grid, g_idx,
-                                  g_dist, tc_scratch, st, s)) != cudaSuccess)
+        constexpr bool bf16 = std::is_same_v<XT, __nv_bfloat16>;
+        if ((e = launch_refine_tc(X, bf16, n, d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, grid,
+                                  g_idx, g_dist, tc_scratch, st, s)) != cudaSuccess)
             return e;
         if (max_cluster > 128)
-            k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
+            k_refine<128, XT><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
                                                                      run_cl, k, kappa, max_cluster, 128, g_idx,
                                                                      g_dist, st);
         return cudaGetLastError();
     }
     // runs of <= 64 members, then the longer runs (up to 128 per tile, longer runs in tiles)
-    k_refine<64><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+    k_refine<64, XT><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                            kappa, max_cluster, 0, g_idx, g_dist, st);
-    k_refine<128><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+    k_refine<128, XT><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                              kappa, max_cluster, 64, g_idx, g_dist, st);
     return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
+                          float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision)
+{
+    if (bf16)
+        return refine_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, offsets, members, k, kappa, max_cluster,
+                        g_idx, g_dist, scratch, st, s, precision);
+    return refine_t(static_cast<const float *>(X), n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist,
+                    scratch, st, s, precision);
 }
 
 }  // namespace gkm

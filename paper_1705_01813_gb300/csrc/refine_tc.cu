@@ -58,7 +58,8 @@ constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) *
 // their m-th entries, and a warp reading one row, touch 32 distinct banks.
 __device__ __forceinline__ int buf_slot(int r, int m) { return r * 32 + (m ^ (r & 31)); }
 
-__global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restrict__ X, int64_t n, int d,
+template <typename XT>
+__global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict__ X, int64_t n, int d,
                                                             int64_t ld, const int32_t *__restrict__ off,
                                                             const int32_t *__restrict__ mem,
                                                             const int32_t *__restrict__ run_off,
@@ -124,8 +125,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
     const int ref = rid[0] >= 0 ? rid[0] : 0;
-    const float *xref = X + (int64_t)ref * ld;
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const XT *xref = X + (int64_t)ref * ld;
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(XT))) == 0;
 
     // ---- Gram matrix of the centred run, K-chunk by K-chunk ----
     bool inexact = false;
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
         float xr[4];
 #pragma unroll
         for (int e = 0; e < 4; e++)
-            xr[e] = t + e < d ? __ldg(xref + t + e) : 0.f;
+            xr[e] = t + e < d ? ldx(xref + t + e) : 0.f;
         // warp w stages rows w, w + 4, ..., TC_RB of them per batch with their loads in flight together
         for (int row0 = w; row0 < srows; row0 += TC_WARPS * TC_RB) {
             float v[TC_RB][4];
@@ -151,9 +152,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
                 for (int e = 0; e < 4; e++)
                     v[b][e] = 0.f;
                 if (a >= 0) {
-                    const float *xa = X + (int64_t)a * ld + t;
+                    const XT *xa = X + (int64_t)a * ld + t;
                     if (vec4 && t + 3 < d) {
-                        const float4 q = __ldg(reinterpret_cast<const float4 *>(xa));
+                        const float4 q = ldx4<XT>(xa);
                         v[b][0] = q.x;
                         v[b][1] = q.y;
                         v[b][2] = q.z;
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
 #pragma unroll
                         for (int e = 0; e < 4; e++)
                             if (t + e < d)
-                                v[b][e] = __ldg(xa + e);
+                                v[b][e] = ldx(xa + e);
                     }
 #pragma unroll
                     for (int e = 0; e < 4; e++)
@@ -307,7 +308,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const float *__restr
 // exact return at once.
 constexpr int EX_THREADS = TC_M;
 
-__global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const float *__restrict__ X, int64_t n, int d,
+template <typename XT>
+__global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const XT *__restrict__ X, int64_t n, int d,
                                                              int64_t ld, const int32_t *__restrict__ off,
                                                              const int32_t *__restrict__ mem,
                                                              const int32_t *__restrict__ run_off,
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const float *__rest
     for (int row = w; row < sz; row += EX_THREADS / 32) {
         const int a = rid[row];
         for (int t = lane; t < d; t += 32)
-            xs[row * ds + t] = a >= 0 ? __ldg(X + (int64_t)a * ld + t) : 0.f;
+            xs[row * ds + t] = a >= 0 ? ldx(X + (int64_t)a * ld + t) : 0.f;
     }
     __syncthreads();
     const int total = pre[EX_THREADS];
@@ -443,10 +445,11 @@ size_t refine_tc_scratch_bytes(int64_t n, int32_t k)
     return 2 * a + c + t;
 }
 
-cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                             const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
-                             int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
-                             void *scratch, DevStatus *st, cudaStream_t s)
+template <typename XT>
+static cudaError_t refine_tc_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                               const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
+                               int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
+                               void *scratch, DevStatus *st, cudaStream_t s)
 {
     const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
     int32_t *cand_id = static_cast<int32_t *>(scratch);
@@ -454,11 +457,11 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
     int32_t *cand_n = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a);
     int32_t *run_tag = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a +
                                                    (((size_t)n * sizeof(int32_t) + 255) & ~size_t(255)));
-    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_refine_gram), (int)TC_SMEM);
+    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_refine_gram<XT>), (int)TC_SMEM);
     if (e != cudaSuccess)
         return e;
     const size_t shm_exact = sizeof(float) * (size_t)TC_M * (size_t)(d + 1);  // d <= 128 on this path
-    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact), (int)(sizeof(float) * TC_M * (128 + 1)))) !=
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact<XT>), (int)(sizeof(float) * TC_M * (128 + 1)))) !=
         cudaSuccess)
         return e;
     const size_t shm_merge = MG_WARPS * merge_warp_bytes(kappa);
@@ -469,10 +472,10 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
         return e;
     if ((e = cudaMemsetAsync(run_tag, 0, sizeof(int32_t) * (size_t)grid, s)) != cudaSuccess)
         return e;
-    k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+    k_refine_gram<XT><<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                               kappa, max_cluster, g_idx, g_dist, cand_id, cand_d,
                                                               cand_n, run_tag, st);
-    k_refine_exact<<<(unsigned)grid, EX_THREADS, shm_exact, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl,
+    k_refine_exact<XT><<<(unsigned)grid, EX_THREADS, shm_exact, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl,
                                                                  k, max_cluster, run_tag, cand_id, cand_d, cand_n,
                                                                  st);
     int64_t mblocks = (n + MG_WARPS - 1) / MG_WARPS;
@@ -481,6 +484,18 @@ cudaError_t launch_refine_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
     k_refine_merge<<<(unsigned)mblocks, MG_WARPS * 32, shm_merge, s>>>(n, kappa, cand_id, cand_d, cand_n, g_idx,
                                                                         g_dist);
     return cudaGetLastError();
+}
+
+cudaError_t launch_refine_tc(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                             const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
+                             int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
+                             void *scratch, DevStatus *st, cudaStream_t s)
+{
+    if (bf16)
+        return refine_tc_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, offsets, members, run_off, run_cl, k,
+                           kappa, max_cluster, grid, g_idx, g_dist, scratch, st, s);
+    return refine_tc_t(static_cast<const float *>(X), n, d, ld, offsets, members, run_off, run_cl, k, kappa,
+                       max_cluster, grid, g_idx, g_dist, scratch, st, s);
 }
 
 }  // namespace gkm

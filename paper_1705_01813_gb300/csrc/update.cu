@@ -12,6 +12,8 @@
 // once per cluster, in the distortion term.
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace gkm {
 
 constexpr int UP_WARPS = 4;
@@ -121,14 +123,25 @@ __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL]
 // next stage's loads are in flight while the current one is summed; the
 // summation order is the same.  The ring shares its memory with the partial
 // sums of the epilogue, which run after it.
-template <int VEC, int CPL, bool PIPE>
-__global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restrict__ X, int d, int64_t ld,
+// One VEC-wide vector of a sample row as floats (BF16 samples are widened).
+template <int VEC, typename XT>
+__device__ __forceinline__ typename VecT<VEC>::T load_vec(const XT *p)
+{
+    if constexpr (VEC == 4)
+        return ldx4<XT, true>(p);
+    else
+        return ldx(p);
+}
+
+template <int VEC, int CPL, bool PIPE, typename XT>
+__global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__ X, int d, int64_t ld,
                                                           const int32_t *__restrict__ off,
                                                           const int32_t *__restrict__ mem, int k,
                                                           float *__restrict__ C, int32_t *__restrict__ counts,
                                                           double *__restrict__ contrib)
 {
     using V = typename VecT<VEC>::T;
+    static_assert(!PIPE || std::is_same_v<XT, float>, "the cp.async ring moves FP32 rows");
     constexpr int UNR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : (CPL >= 2 ? 4 : 4));  // member rows in flight per group
     constexpr int R = PIPE ? UP_RV / CPL : 1;  // rows per group and stage
     constexpr size_t PART_BYTES = sizeof(float2) * UP_WARPS * 32 * CPL * VEC;
@@ -229,12 +242,12 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const float *__restric
                     for (int z = 0; z < UNR; z++) {
                         const int p = p0 + z * gstride;
                         if (p < mc) {
-                            const V *row = Xv + (int64_t)s_mem[p] * ldv;
+                            const XT *rowx = X + (int64_t)s_mem[p] * ld;
 #pragma unroll
                             for (int u = 0; u < CPL; u++) {
                                 const int col = cb + sub + u * L;
                                 if (col < nv)
-                                    v[z][u] = __ldcs(row + col);
+                                    v[z][u] = load_vec<VEC>(rowx + (int64_t)col * VEC);
                             }
                         }
                     }
@@ -316,44 +329,54 @@ __global__ void __launch_bounds__(1024) k_sum_f64(const double *__restrict__ v, 
 
 size_t update_scratch_bytes(int64_t, int32_t k) { return ((size_t)k * sizeof(double) + 255) & ~size_t(255); }
 
-cudaError_t launch_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
-                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
-                          void *scratch, cudaStream_t s)
+template <typename XT>
+static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *offsets, const int32_t *members,
+                            int32_t k, float *C, int32_t *counts, double *sum_d2, void *scratch, cudaStream_t s)
 {
-    (void)n;
     double *contrib = static_cast<double *>(scratch);
-    const int64_t blocks = k;
-    bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const bool vec4 = x_vec4(X, d, ld);
     const int nv = vec4 ? (int)(d / 4) : (int)d;
     const int L = nv >= 32 ? 32 : (nv >= 16 ? 16 : nv >= 8 ? 8 : nv >= 4 ? 4 : nv >= 2 ? 2 : 1);
     const int need = (nv + L - 1) / L;  // vectors per lane to cover a row in one column block
-    const unsigned grid = (unsigned)blocks;
+    const unsigned grid = (unsigned)k;
     const int dd = (int)d;
-#define GK_UPD(VEC, CPL) \
-    k_update<VEC, CPL, false><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib)
+    constexpr bool PIPE = std::is_same_v<XT, float>;  // FP32 rows stream through the cp.async ring
+#define GK_UPD(VEC, CPL, P) \
+    k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib)
     if (vec4) {
         if (need <= 1)
-            k_update<4, 1, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
+            GK_UPD(4, 1, PIPE);
         else if (need <= 2)
-            k_update<4, 2, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
+            GK_UPD(4, 2, PIPE);
         else if (need <= 4)
-            k_update<4, 4, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
+            GK_UPD(4, 4, PIPE);
         else
-            k_update<4, 8, true><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib);
+            GK_UPD(4, 8, PIPE);
     } else {
         if (need <= 1)
-            GK_UPD(1, 1);
+            GK_UPD(1, 1, false);
         else if (need <= 2)
-            GK_UPD(1, 2);
+            GK_UPD(1, 2, false);
         else if (need <= 4)
-            GK_UPD(1, 4);
+            GK_UPD(1, 4, false);
         else
-            GK_UPD(1, 8);
+            GK_UPD(1, 8, false);
     }
 #undef GK_UPD
     if (sum_d2)
         k_sum_f64<<<1, 1024, 0, s>>>(contrib, k, sum_d2);
     return cudaGetLastError();
+}
+
+cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                          const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                          void *scratch, cudaStream_t s)
+{
+    (void)n;
+    if (bf16)
+        return update_t(static_cast<const __nv_bfloat16 *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch,
+                        s);
+    return update_t(static_cast<const float *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch, s);
 }
 
 }  // namespace gkm

@@ -27,6 +27,10 @@ EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_siz
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
            "gk_graph_refine_groups", "gk_update_step_noalloc"]
+#: entry points that read the samples and have a BF16-sample twin named <name>_bf16
+X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
+             "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit"]
+EXPORTS += [name + "_bf16" for name in X_ENTRIES]
 
 
 class GraphParams(ctypes.Structure):
@@ -76,6 +80,8 @@ def load(build_if_missing: bool = True):
             L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
             L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_update_step_noalloc.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
+            for name in X_ENTRIES:
+                getattr(L, name + "_bf16").argtypes = getattr(L, name).argtypes
             for name in EXPORTS:
                 if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
                     getattr(L, name).restype = ctypes.c_int
@@ -98,9 +104,16 @@ def _stream(stream=None):
 
 
 def _x(X: torch.Tensor):
-    if X.device.type != "cuda" or X.dtype != torch.float32 or X.dim() != 2 or X.stride(1) != 1:
-        raise ValueError("X must be a CUDA float32 matrix with unit column stride")
+    if (X.device.type != "cuda" or X.dtype not in (torch.float32, torch.bfloat16) or X.dim() != 2
+            or X.stride(1) != 1):
+        raise ValueError("X must be a CUDA float32 or bfloat16 matrix with unit column stride")
     return X.shape[0], X.shape[1], X.stride(0)
+
+
+def _entry(name: str, X: torch.Tensor):
+    """The library entry point for samples of X's type: BF16 samples go to the <name>_bf16 twin, which
+    widens every element exactly to FP32 as it reads it."""
+    return getattr(load(), name + "_bf16" if X.dtype == torch.bfloat16 else name)
 
 
 def _dev(t: torch.Tensor, dtype, name: str):
@@ -177,7 +190,7 @@ def init_graph(X: torch.Tensor, kappa: int, seed: int, g_idx=None, g_dist=None, 
     gi = torch.empty((n, kappa), dtype=torch.int32, device=X.device) if g_idx is None else g_idx
     gd = torch.empty((n, kappa), dtype=torch.float32, device=X.device) if g_dist is None else g_dist
     ws = ws or workspace(256, X.device)
-    _check(load().gk_init_graph(_ptr(X), n, d, ld, kappa, seed, _ptr(gi), _ptr(gd), ws.ptr, ws.nbytes,
+    _check(_entry("gk_init_graph", X)(_ptr(X), n, d, ld, kappa, seed, _ptr(gi), _ptr(gd), ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return gi, gd
 
@@ -202,7 +215,7 @@ def assign_step(X, g_idx, C, labels_in, labels_out=None, best_d2=ALLOC, sum_d2=A
     sum_d2 = torch.empty(1, dtype=torch.float64, device=dev) if sum_d2 is ALLOC else sum_d2
     n_changed = torch.empty(1, dtype=torch.int64, device=dev) if n_changed is ALLOC else n_changed
     ws = ws or workspace(workspace_size(GK_OP_ASSIGN, n, d, k, kappa), dev)
-    _check(load().gk_assign_step(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
+    _check(_entry("gk_assign_step", X)(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(C), k, _ptr(labels_in),
                                  _ptr(labels_out), _ptr(best_d2), _ptr(sum_d2), _ptr(n_changed), precision,
                                  _ptr(members), ws.ptr, ws.nbytes, _stream(stream)))
     return labels_out, best_d2, sum_d2, n_changed
@@ -220,7 +233,7 @@ def update_step(X, labels, k: int, C, counts=None, sum_d2=None, offsets=None, me
     offsets = torch.empty(k + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
     members = torch.empty(n, dtype=torch.int32, device=dev) if members is None else members
     ws = ws or workspace(workspace_size(GK_OP_UPDATE, n, d, k), dev)
-    _check(load().gk_update_step(_ptr(X), n, d, ld, _ptr(labels), k, _ptr(C), _ptr(counts), _ptr(sum_d2),
+    _check(_entry("gk_update_step", X)(_ptr(X), n, d, ld, _ptr(labels), k, _ptr(C), _ptr(counts), _ptr(sum_d2),
                                  _ptr(offsets), _ptr(members), ws.ptr, ws.nbytes, _stream(stream)))
     return C, counts, sum_d2, offsets, members
 
@@ -234,7 +247,7 @@ def graph_refine(X, labels, k: int, g_idx, g_dist, max_cluster: int = 128, preci
     _dev(g_dist, torch.float32, "g_dist")
     kappa = g_idx.shape[1]
     ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, kappa), X.device)
-    _check(load().gk_graph_refine(_ptr(X), n, d, ld, _ptr(labels), k, kappa, max_cluster, precision, _ptr(g_idx),
+    _check(_entry("gk_graph_refine", X)(_ptr(X), n, d, ld, _ptr(labels), k, kappa, max_cluster, precision, _ptr(g_idx),
                                   _ptr(g_dist), ws.ptr, ws.nbytes, _stream(stream)))
     return g_idx, g_dist
 
@@ -251,7 +264,7 @@ def build_knn_graph(X, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int
     labels_out = torch.empty(n, dtype=torch.int32, device=dev) if labels_out is None else labels_out
     log = (ctypes.c_double * (2 * tau + 1))() if want_log else None
     ws = ws or workspace(int(load().gk_workspace_size_build(n, d, ctypes.byref(p))), dev)
-    _check(load().gk_build_knn_graph(_ptr(X), n, d, ld, ctypes.byref(p), _ptr(g_idx), _ptr(g_dist),
+    _check(_entry("gk_build_knn_graph", X)(_ptr(X), n, d, ld, ctypes.byref(p), _ptr(g_idx), _ptr(g_dist),
                                      _ptr(labels_out), log, ws.ptr, ws.nbytes, _stream(stream)))
     return g_idx, g_dist, labels_out, (list(log) if want_log else None)
 
@@ -269,7 +282,7 @@ def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, la
     counts_out = torch.empty(k, dtype=torch.int32, device=dev) if counts_out is None else counts_out
     log = (ctypes.c_double * (2 * iters + 1))() if want_log else None
     ws = ws or workspace(workspace_size(GK_OP_FIT, n, d, k, kappa), dev)
-    _check(load().gk_kmeans_fit(_ptr(X), n, d, ld, k, _ptr(g_idx), kappa, iters, _ptr(init_labels), seed,
+    _check(_entry("gk_kmeans_fit", X)(_ptr(X), n, d, ld, k, _ptr(g_idx), kappa, iters, _ptr(init_labels), seed,
                                 precision, _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return labels_out, C_out, counts_out, (list(log) if want_log else None)
@@ -295,7 +308,7 @@ def update_from_groups(X, offsets, members, k: int, C, counts=None, sum_d2=None,
     """Segmented mean over a CSR grouping, in place on C."""
     n, d, ld = _x(X)
     ws = ws or workspace(workspace_size(GK_OP_UPDATE, n, d, k), X.device)
-    _check(load().gk_update_from_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, _ptr(C),
+    _check(_entry("gk_update_from_groups", X)(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, _ptr(C),
                                         _ptr(counts), _ptr(sum_d2), ws.ptr, ws.nbytes, _stream(stream)))
     return C
 
@@ -305,7 +318,7 @@ def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster:
     """Graph refinement over a CSR grouping, in place on (g_idx, g_dist)."""
     n, d, ld = _x(X)
     ws = ws or workspace(workspace_size(GK_OP_REFINE, n, d, k, g_idx.shape[1]), X.device)
-    _check(load().gk_graph_refine_groups(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, g_idx.shape[1],
+    _check(_entry("gk_graph_refine_groups", X)(_ptr(X), n, d, ld, _ptr(offsets), _ptr(members), k, g_idx.shape[1],
                                          max_cluster, precision, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
                                          _stream(stream)))
     return g_idx, g_dist
