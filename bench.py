@@ -44,6 +44,9 @@ CPU_SAMPLE = 100_000        # cpu_baseline: oracle on the first 100k samples at 
 REF_SAMPLE = 40_000         # --impl reference: oracle per step on the first 40k samples at d = 128
 
 
+L2_BYTES = 129 << 20  # GB300 L2
+
+
 def oracle_sample(w, base):
     """Samples the oracle runs on: `base` at d = 128, fewer for wider rows (its time grows with d)."""
     return min(w.n, max(2000, base * 128 // max(w.d, 1)))
@@ -58,10 +61,11 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=1,
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=None,
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
                          "BF16 screening in the assignment (SIMT); 3 the screening on the tensor cores (all give "
-                         "the same results)")
+                         "the same results).  Default: the fastest for the workload (2 for the deep-feature "
+                         "workload, whose centroid table exceeds L2; 1 otherwise)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step launched op by op only (default: also captured into a CUDA graph, whose "
@@ -72,7 +76,10 @@ def parse():
                     help="no GPU run: read an ncu --csv log with dram__bytes_read.sum, dram__bytes_write.sum and "
                          "gpu__time_duration.sum of this workload's kernels and record the per-launch means in "
                          "profiles/traffic.json, tagged with the current kernel sources")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.precision is None:
+        args.precision = 2 if datagen.WORKLOADS[args.workload].storage == "bf16" else 1
+    return args
 
 
 def dist_env():
@@ -247,9 +254,9 @@ def launches_per_step(w, precision):
     # assign (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core
     # tiles, SIMT leftovers (3)
     asg = 3 if precision < 2 else (4 if precision == 2 or w.d > 128 else 5)
-    # refine: run count, scan, run clusters, then Gram + exact recompute + merge (tensor cores, d <= 128) or the
-    # two FP32 tile widths
-    ref = 1 + 3 + 1 + (3 if precision >= 1 and 64 <= w.d <= 128 else 2)
+    # refine: run count, scan, run clusters, then Gram + exact recompute + merge (tensor cores) or the two FP32
+    # tile widths
+    ref = 1 + 3 + 1 + (3 if tc_refine(precision, w.d, w.storage) else 2)
     graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
     fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
     return graph + fit
@@ -259,7 +266,7 @@ def algorithmic_bytes(tag, w, k):
     """HBM bytes one launch of a step's kernel must move (per-unit figures x units; L2-resident
     label gathers not counted)."""
     n, d, kappa = w.n, w.d, w.kappa
-    s = 4
+    s = 2 if w.storage == "bf16" else 4  # bytes per stored sample element
     if tag == "assign":
         return n * (s * d + 4 * kappa + 4 + 4) + k * d * 4
     if tag == "update":
@@ -271,8 +278,13 @@ def algorithmic_bytes(tag, w, k):
     return 0
 
 
-def kernel_of(tag, precision=1, d=128):
-    if tag == "refine" and precision >= 1 and 64 <= d <= 128:  # the library's dispatch: tensor-core Gram
+def tc_refine(precision, d, storage="f32"):
+    """The library's dispatch of the refinement to the tensor-core Gram (the same for both storage types)."""
+    return precision >= 1 and 64 <= d <= 128
+
+
+def kernel_of(tag, precision=1, d=128, storage="f32"):
+    if tag == "refine" and tc_refine(precision, d, storage):
         return "k_refine_gram"
     if tag == "assign" and precision == 2:
         return "k_assign_rows_bf8"
@@ -293,8 +305,8 @@ def file_sha(f):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def source_sha(tag, precision=1, d=128):
-    return file_sha(KERNEL_SOURCE[kernel_of(tag, precision, d)])
+def source_sha(tag, precision=1, d=128, storage="f32"):
+    return file_sha(KERNEL_SOURCE[kernel_of(tag, precision, d, storage)])
 
 
 def write_traffic(csv_path, workload):
@@ -339,15 +351,15 @@ def write_traffic(csv_path, workload):
     print(json.dumps({k: v["dram_bytes_per_launch"] for k, v in j.items() if not k.startswith("_")}, indent=1))
 
 
-def ncu_traffic(tag, workload, precision=1, d=128):
+def ncu_traffic(tag, workload, precision=1, d=128, storage="f32"):
     """DRAM bytes per launch from the committed ncu summary, if it is for the current source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
-    e = j.get(f"{kernel_of(tag, precision, d)}:{workload}")
-    if not e or e.get("source_sha") != source_sha(tag, precision, d):
+    e = j.get(f"{kernel_of(tag, precision, d, storage)}:{workload}")
+    if not e or e.get("source_sha") != source_sha(tag, precision, d, storage):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -363,8 +375,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = datagen.WORKLOADS[args.workload]
-    Xh = w.data()
-    X = torch.from_numpy(Xh).cuda()
+    X, Xh = workload_samples(w, torch)
     gkm.load()
 
     path = Path(gkm, torch, w, X, args.precision)
@@ -444,7 +455,7 @@ def run_gpu(args):
     # e2e through the one-call API with host buffers
     e2e = None
     if not args.no_e2e:
-        Xpin = torch.from_numpy(Xh).pin_memory()
+        Xpin = Xh.pin_memory()
         Xdev = torch.empty_like(X)
         lab_h = torch.empty(w.n, dtype=torch.int32).pin_memory()
         C_h = torch.empty((w.k, w.d), dtype=torch.float32).pin_memory()
@@ -481,7 +492,7 @@ def run_gpu(args):
         if world > 1:
             t_e2e = reduce_max(t_e2e, dist, "cuda")
         e2e = {"value": whole_job_rate(w.n, args.steps, world, t_e2e), "unit": "samples/s",
-               "h2d_bytes_per_step": int(Xh.nbytes),
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
                "d2h_bytes_per_step": int(lab_h.numel() * 4 + C_h.numel() * 4),
                "ms_per_step": 1e3 * t_e2e / args.steps}
 
@@ -522,21 +533,23 @@ def run_gpu(args):
         "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "kappa": w.kappa, "k0": w.k0, "xi": w.xi,
                    "tau": w.tau, "iters": w.iters, "max_cluster": w.max_cluster,
                    "step": "graph construction (tau rounds at k0) + fit (iters at k), whole path",
-                   "l2": "inputs larger than L2 (X is %d MB)" % (Xh.nbytes >> 20),
+                   "storage": w.storage,
+                   "l2": "inputs larger than L2 (X is %d MB)" % ((Xh.numel() * Xh.element_size()) >> 20),
                    "parallelism": f"replicas x{world}"},
         "fit_s": step_s,
         "precision": {0: "fp32 throughout",
                       1: "bf16 tcgen05 gram in the refinement with exact fp32 recompute inside its error bound",
-                      2: "1 plus bf16 tcgen05 screening of assignment candidates with exact fp32 recompute"}
+                      2: "1 plus bf16 screening of assignment candidates (simt) with exact fp32 recompute",
+                      3: "1 plus bf16 tcgen05 screening of assignment candidates with exact fp32 recompute"}
                      [args.precision],
         "plain_fp32_ms_per_step": fp32_ms,
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},
         "per_step_share": {t: round(v / sum(totals.values()), 4) for t, v in totals.items()},
-        "roofline": {"kernel": kernel_of(dom, args.precision, w.d), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": kernel_of(dom, args.precision, w.d, w.storage), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": int(alg),
-                     "traffic": ncu_traffic(dom, w.name, args.precision, w.d)},
+                     "traffic": ncu_traffic(dom, w.name, args.precision, w.d, w.storage)},
         "gpu_launches": launches_per_step(w, args.precision) * args.steps,
         "candidates_u": u or None,
         "clocks": ck,
@@ -547,6 +560,19 @@ def run_gpu(args):
         "e2e": e2e,
     }
     # roofline of every call type, for context
+    # Centroid tables larger than L2 (129 MB) make every candidate's centroid row an HBM read: the
+    # assignment's bytes then include n u d (BF16 rows at precision >= 2, FP32 rows otherwise) per call,
+    # u the measured mean candidate count of the phase (graph rounds at k0, fit iterations at k).
+    if dom == "assign" and u:
+        row_b = 2 if args.precision >= 2 else 4
+        per = [(w.k0, u.get("build"), w.tau), (w.k, u.get("fit"), w.iters)]
+        big = [(uu, cnt) for kk, uu, cnt in per if uu and kk * w.d * 4 > L2_BYTES]
+        if big:
+            gath = sum(w.n * uu * w.d * row_b * cnt for uu, cnt in big) / (w.tau + w.iters)
+            res["roofline"]["centroid_gathers"] = {
+                "bytes_per_launch": int(gath), "achieved_with_gathers": (alg + gath) / avg / 1e9,
+                "frac_with_gathers": (alg + gath) / avg / 1e9 / hbm,
+                "note": "centroid table above L2: candidate rows gathered from HBM (pass-2 exact rows not counted)"}
     res["roofline_all"] = {}
     for t, v in per_tag.items():
         if t == "init_graph":
@@ -556,7 +582,7 @@ def run_gpu(args):
     if world == 1 and args.serve_jobs > 0:
         res["serving"] = serving(args)
     if world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(w, Xh)
+        res["cpu_baseline"] = cpu_baseline(w, Xh[:oracle_sample(w, CPU_SAMPLE)].float().numpy())
     print(json.dumps(res), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -597,6 +623,18 @@ def serving(args):
                         "d in {64, 128, 256}, k = n/100, kappa = 20, Gaussian mixtures generated on the device"}
 
 
+def workload_samples(w, torch):
+    """(X on the device, the same samples in host memory) for a workload: FP32 recipes are drawn on the
+    host; the BF16-stored deep-feature recipe is drawn on the device (its host generator would take hours
+    at 10^7 rows) and copied back for the end-to-end leg and the oracle's sample."""
+    if w.storage == "bf16":
+        X = datagen.deep_like_device(w.n, w.d, w.extra["n_dirs"], 50.0, w.seed, device="cuda")
+        torch.cuda.empty_cache()
+        return X, X.cpu()
+    Xh = torch.from_numpy(w.data())
+    return Xh.cuda(), Xh
+
+
 def _oracle_step(O, w, X, k_scale):
     ns = X.shape[0]
     k = max(1, int(round(w.k * ns / w.n)))
@@ -607,9 +645,10 @@ def _oracle_step(O, w, X, k_scale):
 
 
 def cpu_baseline(w, Xh):
+    """The oracle on the leading rows Xh (FP32; BF16 samples widened) of the workload's samples."""
     from oracle import oracle as O
-    ns = oracle_sample(w, CPU_SAMPLE)
-    X = np.ascontiguousarray(Xh[:ns])
+    ns = Xh.shape[0]
+    X = np.ascontiguousarray(Xh, dtype=np.float32)
     t0 = time.perf_counter()
     k = _oracle_step(O, w, X, True)
     dt = time.perf_counter() - t0
@@ -625,9 +664,11 @@ def run_reference(args):
         return
     from oracle import oracle as O
     w = datagen.WORKLOADS[args.workload]
-    Xh = w.data()
     ns = oracle_sample(w, REF_SAMPLE)
-    X = np.ascontiguousarray(Xh[:ns])
+    if w.storage == "bf16":  # the recipe drawn on the host for the sample only (BF16 values widened)
+        X = datagen.bf16_bits_to_f32(datagen.deep_like(ns, w.d, w.extra["n_dirs"], 50.0, w.seed))
+    else:
+        X = np.ascontiguousarray(w.data()[:ns])
     for _ in range(args.warmup):
         _oracle_step(O, w, X, True)
     t0 = time.perf_counter()
@@ -635,7 +676,9 @@ def run_reference(args):
         k = _oracle_step(O, w, X, True)
     dt = time.perf_counter() - t0
     v = ns * args.steps / dt
-    sample = (f"first {ns} samples of {w.name} per step, k = {k}, k0 = {ns // w.xi}: graph construction + fit, "
+    drawn = (f"{ns} samples of the {w.name} recipe drawn on the host" if w.storage == "bf16" else
+             f"first {ns} samples of {w.name}")
+    sample = (f"{drawn} per step, k = {k}, k0 = {ns // w.xi}: graph construction + fit, "
               f"single-threaded FP64 C oracle")
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,

@@ -174,8 +174,10 @@ GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  *              the run's centred coordinates are integers of magnitude <= 255
  *              (and 2 d 255^2 < 2^24), otherwise every pair within a rigorous
  *              error bound of entering a row is recomputed in FP32 as with 0;
- *              the tensor-core path serves 64 <= d <= 128; other widths use
- *              the SIMT kernels of 0; all settings give the same graph.
+ *              the tensor-core path serves 64 <= d <= 128 (BF16 samples are
+ *              staged uncentred, so their Gram carries no BF16 rounding);
+ *              other widths use the SIMT kernels of 0; all settings give the
+ *              same graph.
  *   g_idx / g_dist  device, n x kappa, in: current graph, out: refined graph
  */
 GK_API int gk_graph_refine(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
@@ -265,11 +267,13 @@ GK_API int gk_update_step_noalloc(const float *X, int64_t n, int64_t d, int64_t 
  * element is widened exactly to FP32 when read and all arithmetic is the FP32
  * path's, so the results are those of the FP32 call on the widened samples,
  * bit for bit; the samples take half the device memory and half the read
- * traffic.  (The deep-feature workload of the paper's largest experiment,
- * Sec. 5, stores its 10^7 x 512 vectors this way.)  The assignment's BF16
- * screening (precision 2 and 3) reads FP32 samples only: with BF16 samples the
- * assignment takes precision 0 or 1 (gk_assign_step_bf16, gk_kmeans_fit_bf16,
- * and p->precision of gk_build_knn_graph_bf16), else GK_ERR_INVALID.
+ * traffic.  (Deep-feature vectors at the paper's largest scale, 10^7 x 512,
+ * Sec. 5, take 10 GB this way.)  At precision 2 the assignment screens its
+ * candidates against BF16 centroids with the samples unrounded, as for FP32
+ * samples.  The tensor-core screening (precision 3) reads FP32 samples only:
+ * with BF16 samples the assignment takes precision 0, 1 or 2
+ * (gk_assign_step_bf16, gk_kmeans_fit_bf16, and p->precision of
+ * gk_build_knn_graph_bf16), else GK_ERR_INVALID.
  */
 GK_API int gk_init_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
                               int32_t *g_idx, float *g_dist, void *ws, size_t ws_bytes, void *stream);

@@ -229,9 +229,9 @@ static int assign_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int6
         return fail(GK_ERR_INVALID,
                     "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
-    if (bf16 && precision >= 2)
+    if (bf16 && precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
+                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
@@ -460,9 +460,9 @@ static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64
         return fail(GK_ERR_INVALID,
                     "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
                     precision);
-    if (bf16 && precision >= 2)
+    if (bf16 && precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
+                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
@@ -532,9 +532,9 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
         p->precision < 0 || p->precision > 3 || p->reserved != 0)
         return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
                     p->max_cluster, p->precision);
-    if (bf16 && p->precision >= 2)
+    if (bf16 && p->precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0 or 1 (its BF16 screening reads FP32 samples)");
+                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
     if (!g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "graph arrays are NULL");
     const int32_t k0 = build_k0(n, p->xi);

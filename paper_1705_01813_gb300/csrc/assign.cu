@@ -328,10 +328,12 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const XT *__re
 // Pass 2 recomputes, one at a time and against C, every candidate whose lower
 // value D~ - E_r does not exceed the smallest upper value D~ + E_r (usually the
 // winner alone), with the lane partials and summation tree of k_assign_rows,
-// so the winner and its distance are that kernel's bit for bit.
-template <int NV>
+// so the winner and its distance are that kernel's bit for bit.  The samples
+// (FP32 or BF16, widened exactly) enter both passes unrounded: the bound covers
+// the centroids' rounding alone.
+template <int NV, typename XT>
 __global__ void __launch_bounds__(AS_WARPS * 32, NV >= 4 ? 3 : 4) k_assign_rows_bf8(
-    const float *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
+    const XT *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
     const float *__restrict__ C, const __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ delta, int k,
     const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout, float *__restrict__ best_out, DevStatus *st)
 {
@@ -350,12 +352,12 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV >= 4 ? 3 : 4) k_assign_rows_
     const int ncand = kappa + 1;
 
     for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
-        const float4 *x4 = reinterpret_cast<const float4 *>(X + i * ld);
+        const XT *xrow = X + i * ld;
         float4 xv[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
             int col = lane + 32 * v;
-            xv[v] = col < d4 ? __ldcs(x4 + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xv[v] = col < d4 ? ldx4<XT, true>(xrow + 4 * col) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int q = lane * 4; q < AS_HASH; q += 128)
@@ -787,24 +789,25 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     const int d4 = (int)(d / 4);
     cudaError_t e;
     bool done = false;
-    if constexpr (std::is_same_v<XT, float>) {  // BF16 screening: FP32 samples only
-        if (precision == 2 && vec4 && d4 <= 32 * 8) {
-            k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
-                                                                                      cnorm);
+    if (precision == 2 && vec4 && d4 <= 32 * 8) {
+        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
+                                                                                  cnorm);
 #define GK_ASB8(NV)                                                                                              \
-    k_assign_rows_bf8<NV><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,      \
-                                                             labels_in, labels_out, best, st)
-            if (d4 <= 32)
-                GK_ASB8(1);
-            else if (d4 <= 64)
-                GK_ASB8(2);
-            else if (d4 <= 128)
-                GK_ASB8(4);
-            else
-                GK_ASB8(8);
+    k_assign_rows_bf8<NV, XT><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,  \
+                                                                 labels_in, labels_out, best, st)
+        if (d4 <= 32)
+            GK_ASB8(1);
+        else if (d4 <= 64)
+            GK_ASB8(2);
+        else if (d4 <= 128)
+            GK_ASB8(4);
+        else
+            GK_ASB8(8);
 #undef GK_ASB8
-            done = true;
-        } else if (precision == 3 && vec4 && d4 <= 32 * 8) {
+        done = true;
+    }
+    if constexpr (std::is_same_v<XT, float>) {  // tensor-core screening: FP32 samples only
+        if (precision == 3 && vec4 && d4 <= 32 * 8) {
             k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
                                                                                       cnorm);
             const bool tiles = members && assign_tc_supported(d, ld, X, C, kappa);

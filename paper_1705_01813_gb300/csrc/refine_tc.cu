@@ -5,21 +5,24 @@
 // Three kernels per refinement:
 //
 // k_refine_gram, one CTA (4 warps) per run of <= 128 members.  The run's rows,
-// centred on the run's first member, are converted to BF16 and staged in
-// shared memory in the 128-byte swizzle layout (two 64-column K-blocks at a
-// time); one thread issues the 128 x N x 16 MMAs of G = X' X'^T into tensor
-// memory and commits them to an mbarrier.  Thread t then owns TMEM lane t,
-// i.e. row t of G, forms d2(t, j) = n_t + n_j - 2 G_tj (n = squared norms of
-// the centred rows) and appends to its graph row's candidate list every j
-// that may enter the row: key (d2, id_j) below the row's kappa-th key.
-// Exactness: when every centred coordinate of the run is an integer of
+// FP32 samples centred on the run's first member (BF16 samples as they are),
+// are converted to BF16 and staged in shared memory in the 128-byte swizzle
+// layout (two 64-column K-blocks at a time); one thread issues the
+// 128 x N x 16 MMAs of G = X' X'^T into tensor memory and commits them to an
+// mbarrier.  Thread t then owns TMEM lane t, i.e. row t of G, forms
+// d2(t, j) = n_t + n_j - 2 G_tj (n = squared norms of the staged rows) and
+// appends to its graph row's candidate list every j that may enter the row:
+// key (d2, id_j) below the row's kappa-th key.
+// Exactness: when every staged coordinate of the run is an integer of
 // magnitude <= 255 and 2 d 255^2 < 2^24, every BF16 value, product and partial
 // sum is an exact integer below 2^24, so d2 equals the FP32 sum of squared
 // differences bit for bit.  Otherwise a pair is kept when d2 - E_tj is not
 // above the kappa-th distance, E_tj being a rigorous bound on the error of the
 // Gram distance (BF16 rounding of both operands, (4u + 2u^2) |x_t'| |x_j'|
-// with u = 2^-8, plus FP32 accumulation and combination), marked (recorded by
-// its column in the run instead of its id), and the run is flagged.
+// with u = 2^-8, a term that vanishes when every staged coordinate is a BF16
+// value already, as for BF16 samples; plus FP32 accumulation and combination),
+// marked (recorded by its column in the run instead of its id), and the run is
+// flagged.
 //
 // k_refine_exact, one CTA per flagged run: the run's FP32 rows are staged in
 // shared memory once and every marked pair is recomputed exactly in the order
@@ -34,6 +37,7 @@
 #include "tc.cuh"
 
 #include <cuda_bf16.h>
+#include <type_traits>
 
 namespace gkm {
 
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     int *btot = bcnt + TC_M;  // candidates of each row written so far
     uint64_t *bar = reinterpret_cast<uint64_t *>(btot + TC_M);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
-    int *flags = reinterpret_cast<int *>(tslot + 1);  // [0] not exact, [1] timeout
+    int *flags = reinterpret_cast<int *>(tslot + 1);  // [0] not exact, [1] timeout, [2] a value not BF16
     const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
 
     // this block's run: cluster r with run_off[r] <= run < run_off[r + 1]
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
         tc::fence_mbar_init();
         flags[0] = 0;
         flags[1] = 0;
+        flags[2] = 0;
     }
     // this thread's graph row and its kappa-th key (read now so the loads overlap the staging)
     int gi_row = tid < sz ? S[tid] : -1;
@@ -128,8 +133,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     const XT *xref = X + (int64_t)ref * ld;
     const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(XT))) == 0;
 
-    // ---- Gram matrix of the centred run, K-chunk by K-chunk ----
-    bool inexact = false;
+    // ---- Gram matrix of the (centred) run, K-chunk by K-chunk ----
+    // BF16 samples are staged as they are: their values, products and the Gram's
+    // accumulation carry no BF16 rounding (centring would round the differences)
+    constexpr bool CENTRE = !std::is_same_v<XT, __nv_bfloat16>;
+    bool inexact = false, lossy = false;
     uint32_t phase = 0;
     const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
     const int kchunk = TC_KCH * TC_KB;  // 128 coordinates: 4 per lane
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
         float xr[4];
 #pragma unroll
         for (int e = 0; e < 4; e++)
-            xr[e] = t + e < d ? ldx(xref + t + e) : 0.f;
+            xr[e] = CENTRE && t + e < d ? ldx(xref + t + e) : 0.f;
         // warp w stages rows w, w + 4, ..., TC_RB of them per batch with their loads in flight together
         for (int row0 = w; row0 < srows; row0 += TC_WARPS * TC_RB) {
             float v[TC_RB][4];
@@ -183,6 +191,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
                 if (row < srows) {
                     __nv_bfloat162 p0 = __floats2bfloat162_rn(v[b][0], v[b][1]);
                     __nv_bfloat162 p1 = __floats2bfloat162_rn(v[b][2], v[b][3]);
+                    if (CENTRE) {
+                        const float2 b0 = __bfloat1622float2(p0), b1 = __bfloat1622float2(p1);
+                        lossy |= b0.x != v[b][0] || b0.y != v[b][1] || b1.x != v[b][2] || b1.y != v[b][3];
+                    }
                     uint2 pk;
                     pk.x = *reinterpret_cast<uint32_t *>(&p0);
                     pk.y = *reinterpret_cast<uint32_t *>(&p1);
@@ -221,6 +233,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     }
     if (inexact)
         atomicOr(&flags[0], 1);
+    if (lossy)
+        atomicOr(&flags[2], 1);
     __syncthreads();
     const bool timed_out = flags[1] != 0;
     if (timed_out && tid == 0)
@@ -240,7 +254,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     const int row = tid;
     const float n_i = nrm[row];
     const float u = 1.0f / 256.0f;
-    const float c1 = 1.02f * (4.f * u + 2.f * u * u + 4.f * (d + 2) * 5.9604645e-8f);
+    const float rnd = flags[2] != 0 ? 4.f * u + 2.f * u * u : 0.f;  // BF16 rounding of the operands
+    // accumulation of G: exact products, each 16-deep step aligned to its largest term and truncated (an
+    // error below 16 units of 2^-23 of the step's terms), over d / 16 steps, doubled by the factor 2 of
+    // 2 G and once more as a margin
+    const float c1 = 1.02f * (rnd + 8.f * (d + 2) * 5.9604645e-8f);
     const float c2 = 1.02f * (d + 8) * 1.1920929e-7f;
     btot[tid] = 0;
     for (int c0 = 0; c0 < N; c0 += 32) {
@@ -301,11 +319,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
 }
 
 // Exact distances of the marked candidates of an inexact run: one CTA per run
-// stages the run's FP32 rows in shared memory (row stride d + 1 words) and the
-// threads share out all (row, candidate) pairs of the run; each marked pair
-// (t, column c) is recomputed by one thread in the order of pair_d2_seq and
-// written back in place with the id of column c.  Runs the Gram kernel found
-// exact return at once.
+// stages the run's rows in FP32 in shared memory (row stride d + 1 words) and
+// the threads share out all (row, candidate) pairs of the run; each marked
+// pair (t, column c) is recomputed by one thread in the order of pair_d2_seq
+// and written back in place with the id of column c.  Runs the Gram kernel
+// found exact return at once.
 constexpr int EX_THREADS = TC_M;
 
 template <typename XT>
@@ -319,7 +337,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const XT *__restric
                                                              float *__restrict__ cand_d,
                                                              const int32_t *__restrict__ cand_n, DevStatus *st)
 {
-    extern __shared__ float xs[];  // [sz][d + 1]
+    extern __shared__ float xs[];  // [sz][d + 1], d <= 128
     __shared__ int rid[TC_M], pre[TC_M + 1], wsum[EX_THREADS / 32];
     const int run = blockIdx.x;
     if (run >= run_off[k] || run_tag[run] == 0)
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(EX_THREADS) k_refine_exact(const XT *__restric
         for (int t = lane; t < d; t += 32)
             xs[row * ds + t] = a >= 0 ? ldx(X + (int64_t)a * ld + t) : 0.f;
     }
-    __syncthreads();
+    __syncthreads();  // the staged rows and the prefix pre[] (pre[EX_THREADS]: the run's pair count)
     const int total = pre[EX_THREADS];
     for (int p = tid; p < total; p += EX_THREADS) {
         int lo = 0, hi = sz;  // the row of pair p: last row with pre[row] <= p
@@ -461,8 +479,8 @@ static cudaError_t refine_tc_t(const XT *X, int64_t n, int64_t d, int64_t ld, co
     if (e != cudaSuccess)
         return e;
     const size_t shm_exact = sizeof(float) * (size_t)TC_M * (size_t)(d + 1);  // d <= 128 on this path
-    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact<XT>), (int)(sizeof(float) * TC_M * (128 + 1)))) !=
-        cudaSuccess)
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact<XT>),
+                          (int)(sizeof(float) * TC_M * (128 + 1)))) != cudaSuccess)
         return e;
     const size_t shm_merge = MG_WARPS * merge_warp_bytes(kappa);
     if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_merge),

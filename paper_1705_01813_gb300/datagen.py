@@ -201,6 +201,52 @@ def gauss_mixture_device(n: int, d: int, n_centers: int, seed: int, device, box:
     return X
 
 
+def deep_like_device(n: int, d: int = 512, n_dirs: int = 2_000_000, kappa_vmf: float = 50.0,
+                     seed: int = BASE_SEED + 3, device="cuda", chunk: int = 1 << 18):
+    """The vMF mixture of deep_like drawn on the GPU with a seeded torch generator (same recipe, different
+    stream of random numbers); returns an n x d bfloat16 tensor on the device.  The n_dirs x d table of
+    mean directions is held on the device (4 GB at 2,000,000 x 512).  The cosine w to the mean direction
+    follows Wood (1994), with its Beta((d-1)/2, (d-1)/2) draw taken as a ratio of two chi-square
+    variables of d - 1 degrees of freedom (sums of squared normals)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    mu = torch.empty((n_dirs, d), dtype=torch.float32, device=device)
+    for s in range(0, n_dirs, chunk):
+        blk = torch.randn((min(n_dirs, s + chunk) - s, d), generator=g, device=device)
+        mu[s:s + blk.shape[0]] = blk / blk.norm(dim=1, keepdim=True)
+    kap = float(kappa_vmf)
+    b = (-2.0 * kap + math.sqrt(4.0 * kap * kap + (d - 1.0) ** 2)) / (d - 1.0)
+    x0 = (1.0 - b) / (1.0 + b)
+    c = kap * x0 + (d - 1.0) * math.log(1.0 - x0 * x0)
+
+    def chi2(m):
+        return torch.randn((m, d - 1), generator=g, device=device).double().square().sum(1)
+
+    X = torch.empty((n, d), dtype=torch.bfloat16, device=device)
+    for s in range(0, n, chunk):
+        m = min(n, s + chunk) - s
+        z = torch.randint(0, n_dirs, (m,), generator=g, device=device)
+        w = torch.empty(m, dtype=torch.float64, device=device)
+        todo = torch.arange(m, device=device)
+        while todo.numel():
+            r = todo.numel()
+            a1, a2 = chi2(r), chi2(r)
+            zb = a1 / (a1 + a2)
+            ww = (1.0 - (1.0 + b) * zb) / (1.0 - (1.0 - b) * zb)
+            u = torch.rand(r, generator=g, device=device, dtype=torch.float64)
+            ok = kap * ww + (d - 1.0) * torch.log(1.0 - x0 * ww) - c >= torch.log(u)
+            w[todo[ok]] = ww[ok]
+            todo = todo[~ok]
+        mz = mu[z]
+        v = torch.randn((m, d), generator=g, device=device)
+        v -= (v * mz).sum(1, keepdim=True) * mz
+        v /= v.norm(dim=1, keepdim=True)
+        x = w[:, None].float() * mz + torch.sqrt(torch.clamp(1.0 - w * w, min=0.0))[:, None].float() * v
+        X[s:s + m] = x.to(torch.bfloat16)
+    return X
+
+
 def serving_jobs(count: int = 512, rate: float = 20.0, seed: int = BASE_SEED + 4):
     """Poisson job stream: arrival times, n log-uniform in [1e4, 1e6], d in {64,128,256}, k = n/100."""
     g = _rng(seed)

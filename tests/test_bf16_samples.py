@@ -3,7 +3,8 @@ the FP32 call returns on the same samples widened to FP32, bit for bit (the kern
 element exactly as they read it and keep the FP32 arithmetic).  The FP32 path is checked against
 the oracle elsewhere; one update is checked against the oracle here directly, on the widened
 samples.  Widths cover the 16-byte vector paths (d a multiple of 8), the scalar paths (odd d), the
-tensor-core refinement (64 <= d <= 128) and a GIST-like width; one case has a padded row stride."""
+tensor-core refinement (64 <= d <= 128; BF16 samples staged uncentred, FP32 samples centred) and wide
+rows; one case has a padded row stride."""
 import numpy as np
 import pytest
 
@@ -51,7 +52,7 @@ def test_init_graph(G, n, d, kappa):
     _same(G.init_graph(xb, kappa, 11), G.init_graph(xf, kappa, 11))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("n,d,k,kappa,ld", [(20000, 32, 200, 20, None), (5003, 33, 97, 16, None),
                                             (4001, 128, 300, 12, None), (3001, 960, 40, 10, None),
                                             (6007, 64, 120, 20, 72)])
@@ -65,8 +66,8 @@ def test_assign_step(G, n, d, k, kappa, ld, precision):
     _same(a, b)
 
 
-@pytest.mark.parametrize("precision", [2, 3])
-def test_assign_bf16_screening_rejects_bf16_samples(G, precision):
+@pytest.mark.parametrize("precision", [3])
+def test_assign_tensor_core_screening_rejects_bf16_samples(G, precision):
     xb, _ = _pair(1000, 32, 1)
     gi, _ = G.init_graph(xb, 8, 3)
     L = G.init_labels(1000, 10, 5)
@@ -102,7 +103,8 @@ def test_update_step_matches_oracle_on_widened_samples(G):
 @pytest.mark.parametrize("n,d,k,kappa,cap", [(20000, 32, 400, 20, 128), (5003, 68, 60, 33, 128),
                                              (6007, 80, 20, 10, 128), (1501, 65, 9, 12, 128),
                                              (4001, 128, 90, 12, 128), (3001, 960, 50, 50, 128),
-                                             (2000, 8, 3, 16, 500)])
+                                             (2000, 8, 3, 16, 500), (2003, 200, 40, 20, 128),
+                                             (4001, 512, 80, 40, 128), (3000, 256, 2, 24, 300)])
 def test_graph_refine(G, n, d, k, kappa, cap, precision):
     xb, xf = _pair(n, d, n + d)
     L = G.init_labels(n, k, 23)
@@ -128,7 +130,7 @@ def test_group_entry_points(G):
     _same(gb, gf)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("n,d,k", [(20000, 32, 200), (8009, 100, 80)])
 def test_fit_and_build(G, n, d, k, precision):
     xb, xf = _pair(n, d, n - d)
@@ -138,3 +140,38 @@ def test_fit_and_build(G, n, d, k, precision):
     L0 = G.init_labels(n, k, 47)
     _same(G.kmeans_fit(xb, k, a[0], 5, init_labels=L0, precision=precision),
           G.kmeans_fit(xf, k, a[0], 5, init_labels=L0, precision=precision))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("d", [512, 128, 96])
+def test_graph_refine_unit_vectors(G, d, precision):
+    """Deep-feature-shaped rows (weakly concentrated von Mises-Fisher unit vectors, stored BF16): all pair
+    distances lie close together, the case that tests the Gram's error bound hardest (d <= 128)."""
+    from paper_1705_01813_gb300 import datagen
+    n, k, kappa = 6000, 120, 40
+    xb = datagen.deep_like_device(n, d, 1200, 50.0, seed=53, device="cuda")
+    xf = xb.float()
+    L = G.init_labels(n, k, 59)
+    gb = G.init_graph(xf, kappa, 61)
+    gf = tuple(t.clone() for t in gb)
+    for _ in range(2):
+        G.graph_refine(xb, L, k, *gb, precision=precision)
+        G.graph_refine(xf, L, k, *gf, precision=precision)
+    _same(gb, gf)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_assign_unit_vectors_many_candidates(G, precision):
+    """Deep-feature-shaped rows at the ratio n / k = 10 of the 10^7 x 512 workload: every sample has
+    about kappa + 1 distinct candidate clusters at nearly equal distances, the hardest case for the
+    BF16 screening's bound."""
+    from paper_1705_01813_gb300 import datagen
+    n, d, k, kappa = 20000, 512, 2000, 40
+    xb = datagen.deep_like_device(n, d, 4000, 50.0, seed=67, device="cuda")
+    xf = xb.float()
+    gi, _ = G.init_graph(xf, kappa, 71)
+    L = G.init_labels(n, k, 73)
+    C, _, _, _, _ = G.update_step(xf, L, k, torch.zeros((k, d), device="cuda"))
+    a = G.assign_step(xb, gi, C, L, precision=precision)
+    b = G.assign_step(xf, gi, C, L, precision=0)
+    _same(a, b)
