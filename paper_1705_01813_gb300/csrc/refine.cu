@@ -11,10 +11,13 @@
 // shared memory, several blocks per SM) and a 128-wide tile for the others.
 // A run is covered by T x T tiles (rows x columns of the run); for each tile
 // the block stages 32 coordinates of the row and column samples at a time in
-// shared memory and every thread accumulates a (T/16) x (T/16) set of pair
-// distances (rows ty + 16 a, columns tx + 16 b) with one accumulator in
-// ascending coordinate order (the order of pair_d2_seq), so a pair's distance
-// has the same bits here, in the initial graph and in any later round.  Each
+// shared memory (the row samples twice over, as broadcast pairs) and every
+// thread accumulates the pair distances of Q = T/16 consecutive rows and Q
+// consecutive columns, two columns at a time in packed FP32x2 FMAs (the
+// difference as fma(y, -1, x), then fma(e, e, acc): per pair the operations of
+// pair_d2_seq), with one accumulator in ascending coordinate order, so a
+// pair's distance has the same bits here, in the initial graph and in any
+// later round.  Each
 // warp then merges the tile's candidates into the graph rows of its rows:
 // candidates that beat the row's kappa-th key and are not already in the row
 // are compacted, ranked among themselves, located in the row by binary
@@ -35,11 +38,12 @@ constexpr int RF_DK = 32;  // coordinates staged per step
 
 template <int T>
 struct RefineTile {
-    static constexpr int XS = T + 1;  // padded stride of the staged coordinates
-    static constexpr int DS = T + 1;  // padded stride of the distance tile
-    static constexpr int Q = T / 16;  // pairs per thread along each axis
+    static constexpr int XR = 2 * T + 4;  // stride of a staged coordinate of the row samples (each value twice)
+    static constexpr int XC = T + 4;      // stride of a staged coordinate of the column samples
+    static constexpr int DS = T + 1;      // padded stride of the distance tile
+    static constexpr int Q = T / 16;      // consecutive rows, and columns, per thread
     // the distance tile reuses the staging buffers (written after the last stage)
-    static constexpr size_t stage_floats = 2 * RF_DK * XS;
+    static constexpr size_t stage_floats = (size_t)RF_DK * (XR + XC);
     static constexpr size_t tile_floats = (size_t)T * DS;
     static constexpr size_t fixed_bytes =
         sizeof(float) * (stage_floats > tile_floats ? stage_floats : tile_floats) + sizeof(int) * 2 * T;
@@ -69,8 +73,98 @@ __global__ void k_count_runs(const int32_t *__restrict__ off, int k, int cap, in
     }
 }
 
+// Pair distances of one T x T tile of a run into dt[row * DS + col]: rows are the samples rid[0 .. nr),
+// columns the samples cid[] (SAME: the rows again).  Called by all threads of the block; the caller
+// synchronises before reading dt.
+template <int T, bool SAME, typename XT>
+__device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, int64_t ld, const int *rid,
+                                               const int *cid, int nr, float *xr, float *xc, float *dt)
+{
+    using TL = RefineTile<T>;
+    constexpr int XR = TL::XR, XC = TL::XC, DS = TL::DS, Q = TL::Q;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    // this thread: rows Q ty .. Q ty + Q - 1, columns Q tx .. Q tx + Q - 1 of the tile; a warp
+    // holds two values of ty, so warps whose rows all lie beyond the run skip the arithmetic
+    const bool rows_live = Q * ty < nr;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 acc[Q][Q / 2];
+#pragma unroll
+    for (int a = 0; a < Q; a++)
+#pragma unroll
+        for (int b = 0; b < Q / 2; b++)
+            acc[a][b] = make_float2(0.f, 0.f);
+    // coordinates t0 .. t0+31 of the row and column samples, zero padded, are loaded into
+    // registers one stage ahead (their loads in flight during the previous stage's arithmetic)
+    constexpr int PER = T * RF_DK / RF_THREADS;
+    float pr_v[PER], pc_v[SAME ? 1 : PER];
+    auto fetch = [&](int t0) {
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const int e = tid + p * RF_THREADS, row = e / RF_DK, t = t0 + e % RF_DK;
+            const int a = rid[row];
+            pr_v[p] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
+            if constexpr (!SAME) {
+                const int b = cid[row];
+                pc_v[p] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
+            }
+        }
+    };
+    fetch(0);
+    for (int t0 = 0; t0 < d; t0 += RF_DK) {
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const int e = tid + p * RF_THREADS, row = e / RF_DK, tt = e % RF_DK;
+            *reinterpret_cast<float2 *>(xr + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
+            if constexpr (SAME)
+                xc[tt * XC + row] = pr_v[p];
+            else
+                xc[tt * XC + row] = pc_v[p];
+        }
+        __syncthreads();
+        if (t0 + RF_DK < d)
+            fetch(t0 + RF_DK);
+        const int tmax = min(RF_DK, d - t0);
+        if (rows_live) {
+            for (int tt = 0; tt < tmax; tt++) {
+                float2 vr[Q], vc[Q / 2];
+                const float4 *pr = reinterpret_cast<const float4 *>(xr + tt * XR + 2 * Q * ty);
+                const float4 *pc = reinterpret_cast<const float4 *>(xc + tt * XC + Q * tx);
+#pragma unroll
+                for (int q = 0; q < Q / 2; q++) {
+                    const float4 r4 = pr[q];
+                    vr[2 * q] = make_float2(r4.x, r4.y);
+                    vr[2 * q + 1] = make_float2(r4.z, r4.w);
+                }
+#pragma unroll
+                for (int q = 0; q < Q / 4; q++) {
+                    const float4 c4 = pc[q];
+                    vc[2 * q] = make_float2(c4.x, c4.y);
+                    vc[2 * q + 1] = make_float2(c4.z, c4.w);
+                }
+#pragma unroll
+                for (int a = 0; a < Q; a++)
+#pragma unroll
+                    for (int b = 0; b < Q / 2; b++) {
+                        const float2 e = __ffma2_rn(vc[b], m1, vr[a]);
+                        acc[a][b] = __ffma2_rn(e, e, acc[a][b]);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    if (rows_live) {
+#pragma unroll
+        for (int a = 0; a < Q; a++)
+#pragma unroll
+            for (int b = 0; b < Q / 2; b++) {
+                dt[(Q * ty + a) * DS + Q * tx + 2 * b] = acc[a][b].x;
+                dt[(Q * ty + a) * DS + Q * tx + 2 * b + 1] = acc[a][b].y;
+            }
+    }
+}
+
 template <int T, typename XT>
-__global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+__global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
                                                        const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ mem,
                                                        const int32_t *__restrict__ run_off,
@@ -79,10 +173,10 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const XT
                                                        float *__restrict__ g_dist, DevStatus *st)
 {
     using TL = RefineTile<T>;
-    constexpr int XS = TL::XS, DS = TL::DS, Q = TL::Q;
+    constexpr int DS = TL::DS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *xr = reinterpret_cast<float *>(smem_raw);
-    float *xc = xr + RF_DK * XS;
+    float *xr = reinterpret_cast<float *>(smem_raw);  // [RF_DK][XR]: row sample values as (v, v) pairs
+    float *xc = xr + RF_DK * TL::XR;                  // [RF_DK][XC]: column sample values
     float *dt = xr;  // aliases the staging buffers
     constexpr size_t span = TL::stage_floats > TL::tile_floats ? TL::stage_floats : TL::tile_floats;
     int *rid = reinterpret_cast<int *>(xr + span);
@@ -93,7 +187,6 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const XT
     uint64_t *nk = rk + kappa;
     uint64_t *bk = nk + kappa;
     unsigned *dup = reinterpret_cast<unsigned *>(bk + T);
-    const int ty = tid >> 4, tx = tid & 15;
 
     // block `run` handles that run: find its cluster r, run_off[r] <= run < run_off[r + 1]
     const int run = blockIdx.x;
@@ -129,55 +222,10 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 1) k_refine(const XT
                     cid[q] = b;
                 }
                 __syncthreads();
-                const int nqr = (nr + 15) >> 4, nqc = (ncl + 15) >> 4;
-                const float *xcs = same ? xr : xc;
-                float acc[Q][Q];
-#pragma unroll
-                for (int a = 0; a < Q; a++)
-#pragma unroll
-                    for (int b = 0; b < Q; b++)
-                        acc[a][b] = 0.f;
-                for (int t0 = 0; t0 < d; t0 += RF_DK) {
-                    // stage coordinates t0 .. t0+31 of the row (and column) samples, zero padded
-                    for (int e = tid; e < T * RF_DK; e += RF_THREADS) {
-                        int row = e / RF_DK, tt = e % RF_DK;
-                        int t = t0 + tt;
-                        int a = rid[row];
-                        xr[tt * XS + row] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
-                        if (!same) {
-                            int b = cid[row];
-                            xc[tt * XS + row] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
-                        }
-                    }
-                    __syncthreads();
-                    const int tmax = min(RF_DK, d - t0);
-                    for (int tt = 0; tt < tmax; tt++) {
-                        float vr[Q], vc[Q];
-#pragma unroll
-                        for (int q = 0; q < Q; q++) {
-                            vr[q] = xr[tt * XS + ty + 16 * q];
-                            vc[q] = xcs[tt * XS + tx + 16 * q];
-                        }
-#pragma unroll
-                        for (int a = 0; a < Q; a++) {
-                            if (a < nqr) {
-#pragma unroll
-                                for (int b = 0; b < Q; b++) {
-                                    if (b < nqc) {
-                                        float diff = vr[a] - vc[b];
-                                        acc[a][b] = fmaf(diff, diff, acc[a][b]);
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-#pragma unroll
-                for (int a = 0; a < Q; a++)
-#pragma unroll
-                    for (int b = 0; b < Q; b++)
-                        dt[(ty + 16 * a) * DS + tx + 16 * b] = acc[a][b];
+                if (same)
+                    tile_distances<T, true>(X, d, ld, rid, cid, nr, xr, xc, dt);
+                else
+                    tile_distances<T, false>(X, d, ld, rid, cid, nr, xr, xc, dt);
                 __syncthreads();
                 RowRegs cur, nxt;
                 if (w < nr && rid[w] >= 0)
