@@ -606,6 +606,10 @@ def serving(args):
     sat = serve.summarize(sat_res)
     pb = serve.ServeParams(budget_bytes=p.budget_bytes, slots=p.slots, precision=args.precision, batching=True)
     bsrv = serve.Server(pb)
+    # warm-up of the batched form on jobs that make multi-job batches (first-use costs of its launches, about
+    # 5 s on a fresh box, would otherwise land on the stream's first jobs)
+    bsrv.run(specs[:16], realtime=False)
+    torch.cuda.synchronize()
     blive = serve.summarize(bsrv.run(specs, realtime=True))
     bsat_res = bsrv.run(specs, realtime=False)
     bsat = serve.summarize(bsat_res)
