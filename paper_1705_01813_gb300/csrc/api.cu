@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -147,6 +148,30 @@ cudaError_t set_max_smem(const void *kernel, int bytes)
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) == cudaSuccess)
         done.insert({dev, kernel});
     return e;
+}
+
+cudaError_t resident_grid(const void *kernel, int threads, size_t smem, int *grid)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> known;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = known.find({dev, kernel});
+    if (it != known.end()) {
+        *grid = it->second;
+        return cudaSuccess;
+    }
+    int sms = 0, per = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem)) != cudaSuccess)
+        return e;
+    *grid = sms * (per > 0 ? per : 1);
+    known[{dev, kernel}] = *grid;
+    return cudaSuccess;
 }
 }  // namespace gkm
 

@@ -28,6 +28,11 @@ cudaError_t launch_assign_tc(const float *X, int64_t n, int64_t d, int64_t ld, c
 
 constexpr int AS_WARPS = 8;
 constexpr int AS_BLOCKS = 152 * 8;  // fixed grid: the FP64 partial sums have a fixed order
+// The row kernels for d <= 256 fit six blocks per SM (at most 40 registers a thread: more warps in flight
+// for the latency-bound centroid gathers).  Every row kernel runs on a grid of the blocks resident at once
+// (resident_grid), one wave; the distortion sums do not depend on it: k_assign_reduce forms them on its
+// own fixed grid.
+constexpr int AS_ROWS_PER_SM = 6;
 constexpr int AS_QCAP = MAX_KAPPA + 1;
 constexpr int AS_TILE = 128;  // samples per tile of the tensor-core assignment
 
@@ -200,7 +205,7 @@ constexpr int AS_QROW = (AS_QCAP + AS_G + 3) / 4 * 4;         // candidate list 
 static_assert(AS_HASH > AS_QCAP, "the label set must never fill up");
 
 template <int NV, typename XT>
-__global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const XT *__restrict__ X, int64_t n, int d,
+__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k_assign_rows(const XT *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
                                                                const int32_t *__restrict__ Lin,
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32, 4) k_assign_rows(const XT *__re
 // (FP32 or BF16, widened exactly) enter both passes unrounded: the bound covers
 // the centroids' rounding alone.
 template <int NV, typename XT>
-__global__ void __launch_bounds__(AS_WARPS * 32, NV >= 4 ? 3 : 4) k_assign_rows_bf8(
+__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 3) k_assign_rows_bf8(
     const XT *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
     const float *__restrict__ C, const __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ delta, int k,
     const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout, float *__restrict__ best_out, DevStatus *st)
@@ -788,13 +793,19 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     const bool vec4 = x_vec4(X, d, ld) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int d4 = (int)(d / 4);
     cudaError_t e;
+    int grid = 0;
     bool done = false;
     if (precision == 2 && vec4 && d4 <= 32 * 8) {
         k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
                                                                                   cnorm);
 #define GK_ASB8(NV)                                                                                              \
-    k_assign_rows_bf8<NV, XT><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,  \
-                                                                 labels_in, labels_out, best, st)
+    do {                                                                                                         \
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows_bf8<NV, XT>), AS_WARPS * 32, 0,      \
+                               &grid)) != cudaSuccess)                                                           \
+            return e;                                                                                            \
+        k_assign_rows_bf8<NV, XT><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k, \
+                                                                 labels_in, labels_out, best, st);               \
+    } while (0)
         if (d4 <= 32)
             GK_ASB8(1);
         else if (d4 <= 64)
@@ -838,8 +849,13 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     if (done) {
     } else if (vec4 && d4 <= 32 * 8) {
 #define GK_ASG(NV)                                                                                               \
-    k_assign_rows<NV, XT><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,         \
-                                                          labels_out, best, st)
+    do {                                                                                                         \
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows<NV, XT>), AS_WARPS * 32, 0, &grid)) != \
+            cudaSuccess)                                                                                         \
+            return e;                                                                                            \
+        k_assign_rows<NV, XT><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,      \
+                                                             labels_out, best, st);                              \
+    } while (0)
         if (d4 <= 32)
             GK_ASG(1);
         else if (d4 <= 64)

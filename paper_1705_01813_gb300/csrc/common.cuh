@@ -171,6 +171,9 @@ struct Carver {
 // cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize, bytes) on the current
 // device, the first time only (thread-safe); `bytes` must be the same on every call.
 cudaError_t set_max_smem(const void *kernel, int bytes);
+// SMs x blocks of `kernel` resident on one SM (threads per block, dynamic shared memory smem): a grid that
+// runs in one wave.  Computed once per device and kernel.
+cudaError_t resident_grid(const void *kernel, int threads, size_t smem, int *grid);
 
 // Internal launchers (each returns cudaError_t of the launch).  Those that read the samples take them as
 // X (FP32, or BF16 when bf16 is set) with leading dimension ld in elements.
