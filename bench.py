@@ -67,6 +67,8 @@ def parse():
                          "the same results).  Default: the fastest for the workload (2 for the deep-feature "
                          "workload, whose centroid table exceeds L2; 1 otherwise)")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-ceilings", action="store_true",
+                    help="skip the probe kernels that measure the L2 / HBM gather and FP32 FMA ceilings")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step launched op by op only (default: also captured into a CUDA graph, whose "
                          "replay time is the value)")
@@ -502,6 +504,10 @@ def run_gpu(args):
         return
 
     hbm, bf16, peak_src = load_peaks()
+    ceilings = None
+    if not args.no_ceilings:
+        from paper_1705_01813_gb300 import peaks
+        ceilings = peaks.measure()
     # dominant kernel: the call with the largest share of the step
     totals = {t: sum(v) for t, v in per_tag.items()}
     dom = max(totals, key=totals.get)
@@ -551,6 +557,7 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": int(alg),
                      "traffic": ncu_traffic(dom, w.name, args.precision, w.d, w.storage)},
         "gpu_launches": launches_per_step(w, args.precision) * args.steps,
+        "measured_ceilings": ceilings,
         "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
@@ -560,19 +567,27 @@ def run_gpu(args):
         "e2e": e2e,
     }
     # roofline of every call type, for context
-    # Centroid tables larger than L2 (129 MB) make every candidate's centroid row an HBM read: the
-    # assignment's bytes then include n u d (BF16 rows at precision >= 2, FP32 rows otherwise) per call,
-    # u the measured mean candidate count of the phase (graph rounds at k0, fit iterations at k).
+    # The assignment gathers one centroid row per candidate: n u d (BF16 rows at precision >= 2, FP32 rows
+    # otherwise) bytes per call beyond the algorithmic ones, u the measured mean candidate count of the phase
+    # (graph rounds at k0, fit iterations at k).  They come from L2 while the centroid table fits it and from
+    # HBM otherwise; the probe kernels measure both gather ceilings on this GPU.
     if dom == "assign" and u:
         row_b = 2 if args.precision >= 2 else 4
         per = [(w.k0, u.get("build"), w.tau), (w.k, u.get("fit"), w.iters)]
-        big = [(uu, cnt) for kk, uu, cnt in per if uu and kk * w.d * 4 > L2_BYTES]
-        if big:
-            gath = sum(w.n * uu * w.d * row_b * cnt for uu, cnt in big) / (w.tau + w.iters)
-            res["roofline"]["centroid_gathers"] = {
-                "bytes_per_launch": int(gath), "achieved_with_gathers": (alg + gath) / avg / 1e9,
-                "frac_with_gathers": (alg + gath) / avg / 1e9 / hbm,
-                "note": "centroid table above L2: candidate rows gathered from HBM (pass-2 exact rows not counted)"}
+        g_l2 = sum(w.n * uu * w.d * row_b * c for kk, uu, c in per if uu and kk * w.d * 4 <= L2_BYTES)
+        g_hbm = sum(w.n * uu * w.d * row_b * c for kk, uu, c in per if uu and kk * w.d * 4 > L2_BYTES)
+        g_l2, g_hbm = g_l2 / (w.tau + w.iters), g_hbm / (w.tau + w.iters)
+        gath = {"bytes_per_launch": int(g_l2 + g_hbm), "from_l2": int(g_l2), "from_hbm": int(g_hbm),
+                "achieved_gbs": (g_l2 + g_hbm) / avg / 1e9,
+                "note": "candidate centroid rows, one per candidate (exact second-pass rows at precision 2 not "
+                        "counted)"}
+        if ceilings:
+            # time the gathers would take at the measured ceilings, against the call's time
+            t_min = g_l2 / (ceilings["l2_gather_gbs"] * 1e9) + g_hbm / (ceilings["hbm_gather_gbs"] * 1e9)
+            gath["ceiling"] = "measured warp-per-row gather (" + ("L2" if g_hbm == 0 else "HBM" if g_l2 == 0
+                                                                   else "L2 and HBM") + ")"
+            gath["frac_of_gather_ceiling"] = t_min / avg
+        res["roofline"]["centroid_gathers"] = gath
     res["roofline_all"] = {}
     for t, v in per_tag.items():
         if t == "init_graph":

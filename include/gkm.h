@@ -303,6 +303,27 @@ GK_API int gk_kmeans_fit_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t l
                               double *e_log, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Measurement probes: the ceilings against which the assignment is read where
+ * HBM bandwidth does not bound it (its centroid rows come from L2).  Both run
+ * 152 x 8 blocks of 8 warps and write one float per warp to sink (device,
+ * GK_PROBE_SINK floats, contents meaningless), on `stream`; the caller times
+ * them.
+ *
+ * gk_probe_gather: for j < count, one warp reads row idx[j] of table (device,
+ *   rows x row_floats FP32, row-major, 16-byte aligned; row_floats a multiple
+ *   of 4 up to 512) in 16-byte loads, eight rows of a warp in flight, as the
+ *   assignment reads its candidate centroid rows.  Bytes read:
+ *   count x row_floats x 4.  Entries of idx outside [0, rows) read nothing.
+ * gk_probe_fma: every thread runs eight independent chains of `iters` packed
+ *   FP32x2 FMAs (the distance loops' instruction): 32 x iters FLOP per
+ *   thread, 152 x 8 x 256 threads.
+ */
+#define GK_PROBE_SINK 9728
+GK_API int gk_probe_gather(const float *table, int64_t rows, int32_t row_floats, const int32_t *idx, int64_t count,
+                           float *sink, void *stream);
+GK_API int gk_probe_fma(float *sink, int64_t iters, void *stream);
+
+/*
  * Synchronise `stream`, return the status word the kernels of calls that used
  * `ws` recorded (GK_OK if none), and clear it.  Also returns GK_ERR_CUDA if the
  * stream itself reports an error.
