@@ -597,7 +597,7 @@ def run_gpu(args):
     if world == 1 and args.serve_jobs > 0:
         res["serving"] = serving(args)
     if world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(w, Xh[:oracle_sample(w, CPU_SAMPLE)].float().numpy())
+        res["cpu_baseline"] = cpu_baseline(w, Xh[:oracle_sample(w, CPU_SAMPLE)].float().numpy(), args.precision)
     print(json.dumps(res), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -654,27 +654,53 @@ def workload_samples(w, torch):
     return Xh.cuda(), Xh
 
 
-def _oracle_step(O, w, X, k_scale):
+def _oracle_step(O, w, X):
+    """Graph construction and fit of the oracle on the samples X; returns (k, graph ids, final labels, final
+    distortion)."""
     ns = X.shape[0]
     k = max(1, int(round(w.k * ns / w.n)))
     gi, _, _, _ = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
     L0 = O.init_labels(ns, k, w.seed + 1)
-    O.fit(X, k, gi, w.iters, L0)
-    return k
+    Lf, _, _, E = O.fit(X, k, gi, w.iters, L0)
+    return k, gi, Lf, float(np.asarray(E)[-1])
 
 
-def cpu_baseline(w, Xh):
-    """The oracle on the leading rows Xh (FP32; BF16 samples widened) of the workload's samples."""
+def gpu_vs_oracle(w, X, k, ora, precision):
+    """The library's graph construction and fit on the oracle's sample (same seeds, the workload's storage
+    type), against the oracle's results: relative difference of the final distortion, and the fractions of
+    equal final labels and of equal graph rows (differences come from near ties, decided in FP32 here and
+    in FP64 there, and what follows from them in a free-running fit)."""
+    import torch
+
+    from paper_1705_01813_gb300 import gkm
+    gi_o, L_o, E_o = ora
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    if w.storage == "bf16":
+        Xd = Xd.to(torch.bfloat16)  # the sample holds widened BF16 values: exact
+    gi, _, _, _ = gkm.build_knn_graph(Xd, w.kappa, w.xi, w.tau, w.max_cluster, w.seed, want_log=False,
+                                      precision=precision)
+    lab, _, _, log = gkm.kmeans_fit(Xd, k, gi, w.iters, seed=w.seed + 1, precision=precision)
+    gi_h, lab_h = gi.cpu().numpy(), lab.cpu().numpy()
+    return {"final_distortion_rel_diff": abs(log[-1] - E_o) / E_o,
+            "labels_equal": float((lab_h == L_o).mean()),
+            "graph_rows_equal": float((gi_h == gi_o).all(1).mean()),
+            "precision": precision}
+
+
+def cpu_baseline(w, Xh, precision=1):
+    """The oracle on the leading rows Xh (FP32; BF16 samples widened) of the workload's samples, timed; then
+    the library on the same rows against the oracle's results."""
     from oracle import oracle as O
     ns = Xh.shape[0]
     X = np.ascontiguousarray(Xh, dtype=np.float32)
     t0 = time.perf_counter()
-    k = _oracle_step(O, w, X, True)
+    k, gi_o, L_o, E_o = _oracle_step(O, w, X)
     dt = time.perf_counter() - t0
     return {"value": ns / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
             "sample": f"first {ns} samples of {w.name}, k = {k}, k0 = {ns // w.xi}, kappa = {w.kappa}, "
                       f"tau = {w.tau}, iters = {w.iters}: graph construction + fit, single-threaded FP64 C",
-            "seconds": dt}
+            "seconds": dt,
+            "gpu_vs_oracle": gpu_vs_oracle(w, X, k, (gi_o, L_o, E_o), precision)}
 
 
 def run_reference(args):
@@ -689,10 +715,10 @@ def run_reference(args):
     else:
         X = np.ascontiguousarray(w.data()[:ns])
     for _ in range(args.warmup):
-        _oracle_step(O, w, X, True)
+        _oracle_step(O, w, X)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        k = _oracle_step(O, w, X, True)
+        k = _oracle_step(O, w, X)[0]
     dt = time.perf_counter() - t0
     v = ns * args.steps / dt
     drawn = (f"{ns} samples of the {w.name} recipe drawn on the host" if w.storage == "bf16" else

@@ -61,7 +61,8 @@ enum {
     GK_OP_UPDATE = 1,
     GK_OP_REFINE = 2,
     GK_OP_FIT = 3,
-    GK_OP_BUILD = 4
+    GK_OP_BUILD = 4,
+    GK_OP_RECALL = 5
 };
 
 /* Parameters of the graph construction (Alg. 3 and Sec. 4.4 of the paper). */
@@ -88,9 +89,10 @@ GK_API const char *gk_version(void);
 GK_API const char *gk_last_error(void);
 
 /*
- * Bytes of workspace the operation `op` (GK_OP_ASSIGN, _UPDATE, _REFINE, _FIT)
- * needs for these sizes; 0 for an unknown op.  k is the number of clusters.
- * The graph construction has its own query, gk_workspace_size_build().
+ * Bytes of workspace the operation `op` (GK_OP_ASSIGN, _UPDATE, _REFINE, _FIT,
+ * _RECALL) needs for these sizes; 0 for an unknown op.  k is the number of
+ * clusters (for GK_OP_RECALL: the number of queries m).  The graph
+ * construction has its own query, gk_workspace_size_build().
  */
 GK_API size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa);
 
@@ -301,6 +303,33 @@ GK_API int gk_kmeans_fit_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t l
                               int32_t kappa, int32_t iters, const int32_t *init_labels, uint64_t seed,
                               int32_t precision, int32_t *labels_out, float *C_out, int32_t *counts_out,
                               double *e_log, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Top-1 recall of a KNN graph on sampled queries (Sec. 5: the recall of the
+ * top-1 neighbour, estimated on randomly chosen samples where the full ground
+ * truth is too costly).  For each query q = queries[t] the exact nearest
+ * neighbour among the other n - 1 samples is found by brute force (squared
+ * Euclidean distance in FP32 in the canonical order of the graph's distances,
+ * ties to the smaller id: the graph's key order); q is a hit when it is
+ * g_idx[q][0].  Graph rows hold exact distances sorted by key, so a row holds
+ * its sample's nearest neighbour exactly when that is its first entry.
+ *   X, n, d, ld    samples as in gk_assign_step (n >= 2)
+ *   g_idx, kappa   device int32[n x kappa]: the graph
+ *   queries        device int32[m]: sample ids (drawn by the caller); an id
+ *                  outside [0, n) is reported in the status word, never a hit
+ *   nn_idx, nn_dist  device int32[m] / float[m] or NULL: each query's exact
+ *                  nearest neighbour and its distance (-1 / +inf if none)
+ *   hits           device int64[1]: number of hits (overwritten)
+ *   ws             gk_workspace_size(GK_OP_RECALL, n, d, m, kappa) bytes
+ * Cost: m n d pair terms, on the SIMT cores (FP32 tiles of 64 queries x 64
+ * samples).
+ */
+GK_API int gk_graph_recall(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                           const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist, int64_t *hits,
+                           void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                                int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,
+                                int64_t *hits, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Measurement probes: the ceilings against which the assignment is read where

@@ -84,6 +84,7 @@ struct Layout {
     void *upd_scratch;
     void *asg_scratch;
     void *ref_scratch;
+    void *rec_scratch;
     int32_t *labels_a;
     int32_t *labels_b;
     float *cent;
@@ -120,6 +121,8 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
         L.labels_a = cv.take<int32_t>((size_t)n);
         L.cent = cv.take<float>((size_t)k * (size_t)d);
     }
+    if (op == GK_OP_RECALL)  // k: the number of queries
+        L.rec_scratch = cv.take<char>(recall_scratch_bytes(n, k));
     L.bytes = cv.off;
     return L;
 }
@@ -185,7 +188,7 @@ const char *gk_last_error(void) { return g_err; }
 size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa)
 {
     (void)kappa;
-    if (op < GK_OP_ASSIGN || op > GK_OP_FIT || n < 0 || d < 0 || k < 0)
+    if (op < GK_OP_ASSIGN || op > GK_OP_RECALL || op == GK_OP_BUILD || n < 0 || d < 0 || k < 0)
         return 0;
     return carve(nullptr, op, n, d, k).bytes;
 }
@@ -615,6 +618,42 @@ int gk_build_knn_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld,
     return build_knn_graph_impl(X, true, n, d, ld, p, g_idx, g_dist, labels_out, e_log, ws, ws_bytes, stream);
 }
 
+
+static int graph_recall_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                             int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,
+                             int64_t *hits, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(kappa, n)))
+        return rc;
+    if (m < 1)
+        return fail(GK_ERR_INVALID, "m = %d < 1", m);
+    if (!g_idx || !queries || !hits)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    Layout L = carve(nullptr, GK_OP_RECALL, n, d, m);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_RECALL, n, d, m);
+    GK_CUDA(launch_recall(X, bf16, n, d, ld, g_idx, kappa, queries, m, nn_idx, nn_dist, hits, L.rec_scratch, L.st,
+                          (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_graph_recall(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                    const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist, int64_t *hits, void *ws,
+                    size_t ws_bytes, void *stream)
+{
+    return graph_recall_impl(X, false, n, d, ld, g_idx, kappa, queries, m, nn_idx, nn_dist, hits, ws, ws_bytes,
+                             stream);
+}
+
+int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                         const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist, int64_t *hits, void *ws,
+                         size_t ws_bytes, void *stream)
+{
+    return graph_recall_impl(X, true, n, d, ld, g_idx, kappa, queries, m, nn_idx, nn_dist, hits, ws, ws_bytes,
+                             stream);
+}
 
 int gk_probe_gather(const float *table, int64_t rows, int32_t row_floats, const int32_t *idx, int64_t count,
                     float *sink, void *stream)

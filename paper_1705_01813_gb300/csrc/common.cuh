@@ -175,6 +175,12 @@ cudaError_t set_max_smem(const void *kernel, int bytes);
 // runs in one wave.  Computed once per device and kernel.
 cudaError_t resident_grid(const void *kernel, int threads, size_t smem, int *grid);
 
+// top-1 recall of a graph on sampled queries (recall.cu)
+size_t recall_scratch_bytes(int64_t n, int32_t m);
+cudaError_t launch_recall(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                          int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,
+                          int64_t *hits, void *scratch, DevStatus *st, cudaStream_t s);
+
 // measurement probes (probes.cu)
 constexpr int PROBE_SINK = 152 * 8 * 8;  // floats the probes' sink must hold
 cudaError_t launch_probe_gather(const float *table, int64_t rows, int row_floats, const int32_t *idx, int64_t count,

@@ -1,0 +1,126 @@
+// FP32 pair-distance tiles of the SIMT kernels (the refinement's run tiles and
+// the recall estimator's query x sample tiles): a block of RF_THREADS threads
+// computes a T x T tile of squared Euclidean distances in the canonical order
+// (one accumulator per pair, coordinates in ascending order, the difference
+// and its square as two FMAs), so every pair has the bits of pair_d2_seq.
+#pragma once
+
+#include "common.cuh"
+
+namespace gkm {
+
+constexpr int RF_THREADS = 256;
+constexpr int RF_WARPS = RF_THREADS / 32;
+constexpr int RF_DK = 32;  // coordinates staged per step
+
+template <int T>
+struct RefineTile {
+    static constexpr int XR = 2 * T + 4;  // stride of a staged coordinate of the row samples (each value twice)
+    static constexpr int XC = T + 4;      // stride of a staged coordinate of the column samples
+    static constexpr int DS = T + 1;      // padded stride of the distance tile
+    static constexpr int Q = T / 16;      // consecutive rows, and columns, per thread
+    // the distance tile reuses the staging buffers (written after the last stage)
+    static constexpr size_t stage_floats = (size_t)RF_DK * (XR + XC);
+    static constexpr size_t tile_floats = (size_t)T * DS;
+    static constexpr size_t fixed_bytes =
+        sizeof(float) * (stage_floats > tile_floats ? stage_floats : tile_floats) + sizeof(int) * 2 * T;
+    // per warp: row keys (kappa), merged-row keys (kappa), candidate keys (T), dup bits
+    __host__ __device__ static size_t warp_bytes(int kappa)
+    {
+        return sizeof(uint64_t) * (size_t)(2 * kappa + T) + 4 * sizeof(unsigned);
+    }
+    static_assert(fixed_bytes % 8 == 0, "the per-warp key buffers need 8-byte alignment");
+    __host__ __device__ static size_t smem_bytes(int kappa) { return fixed_bytes + RF_WARPS * warp_bytes(kappa); }
+};
+
+// Pair distances of one T x T tile into dt[row * DS + col]: rows are the samples rid[0 .. nr),
+// columns the samples cid[] (SAME: the rows again).  Called by all threads of the block; the caller
+// synchronises before reading dt.
+template <int T, bool SAME, typename XT>
+__device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, int64_t ld, const int *rid,
+                                               const int *cid, int nr, float *xr, float *xc, float *dt)
+{
+    using TL = RefineTile<T>;
+    constexpr int XR = TL::XR, XC = TL::XC, DS = TL::DS, Q = TL::Q;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    // this thread: rows Q ty .. Q ty + Q - 1, columns Q tx .. Q tx + Q - 1 of the tile; a warp
+    // holds two values of ty, so warps whose rows all lie beyond the run skip the arithmetic
+    const bool rows_live = Q * ty < nr;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 acc[Q][Q / 2];
+#pragma unroll
+    for (int a = 0; a < Q; a++)
+#pragma unroll
+        for (int b = 0; b < Q / 2; b++)
+            acc[a][b] = make_float2(0.f, 0.f);
+    // coordinates t0 .. t0+31 of the row and column samples, zero padded, are loaded into
+    // registers one stage ahead (their loads in flight during the previous stage's arithmetic)
+    constexpr int PER = T * RF_DK / RF_THREADS;
+    float pr_v[PER], pc_v[SAME ? 1 : PER];
+    auto fetch = [&](int t0) {
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const int e = tid + p * RF_THREADS, row = e / RF_DK, t = t0 + e % RF_DK;
+            const int a = rid[row];
+            pr_v[p] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
+            if constexpr (!SAME) {
+                const int b = cid[row];
+                pc_v[p] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
+            }
+        }
+    };
+    fetch(0);
+    for (int t0 = 0; t0 < d; t0 += RF_DK) {
+#pragma unroll
+        for (int p = 0; p < PER; p++) {
+            const int e = tid + p * RF_THREADS, row = e / RF_DK, tt = e % RF_DK;
+            *reinterpret_cast<float2 *>(xr + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
+            if constexpr (SAME)
+                xc[tt * XC + row] = pr_v[p];
+            else
+                xc[tt * XC + row] = pc_v[p];
+        }
+        __syncthreads();
+        if (t0 + RF_DK < d)
+            fetch(t0 + RF_DK);
+        const int tmax = min(RF_DK, d - t0);
+        if (rows_live) {
+            for (int tt = 0; tt < tmax; tt++) {
+                float2 vr[Q], vc[Q / 2];
+                const float4 *pr = reinterpret_cast<const float4 *>(xr + tt * XR + 2 * Q * ty);
+                const float4 *pc = reinterpret_cast<const float4 *>(xc + tt * XC + Q * tx);
+#pragma unroll
+                for (int q = 0; q < Q / 2; q++) {
+                    const float4 r4 = pr[q];
+                    vr[2 * q] = make_float2(r4.x, r4.y);
+                    vr[2 * q + 1] = make_float2(r4.z, r4.w);
+                }
+#pragma unroll
+                for (int q = 0; q < Q / 4; q++) {
+                    const float4 c4 = pc[q];
+                    vc[2 * q] = make_float2(c4.x, c4.y);
+                    vc[2 * q + 1] = make_float2(c4.z, c4.w);
+                }
+#pragma unroll
+                for (int a = 0; a < Q; a++)
+#pragma unroll
+                    for (int b = 0; b < Q / 2; b++) {
+                        const float2 e = __ffma2_rn(vc[b], m1, vr[a]);
+                        acc[a][b] = __ffma2_rn(e, e, acc[a][b]);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    if (rows_live) {
+#pragma unroll
+        for (int a = 0; a < Q; a++)
+#pragma unroll
+            for (int b = 0; b < Q / 2; b++) {
+                dt[(Q * ty + a) * DS + Q * tx + 2 * b] = acc[a][b].x;
+                dt[(Q * ty + a) * DS + Q * tx + 2 * b + 1] = acc[a][b].y;
+            }
+    }
+}
+
+}  // namespace gkm

@@ -20,16 +20,17 @@ _lib = None
 _lock = threading.Lock()
 
 GK_OK, GK_ERR_INVALID, GK_ERR_CUDA, GK_ERR_NOMEM, GK_ERR_TIMEOUT, GK_ERR_NUMERIC = range(6)
-GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD = range(5)
+GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL = range(6)
 
 #: every entry point the header declares (checked by the tests)
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
-           "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_probe_gather", "gk_probe_fma"]
+           "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall", "gk_probe_gather",
+           "gk_probe_fma"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
-             "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit"]
+             "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall"]
 EXPORTS += [name + "_bf16" for name in X_ENTRIES]
 
 
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True):
             L.gk_update_from_groups.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, SZ, P]
             L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_update_step_noalloc.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
+            L.gk_graph_recall.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, SZ, P]
             L.gk_probe_gather.argtypes = [P, I64, I32, P, I64, P, P]
             L.gk_probe_fma.argtypes = [P, I64, P]
             for name in X_ENTRIES:
@@ -324,6 +326,23 @@ def graph_refine_groups(X, offsets, members, k: int, g_idx, g_dist, max_cluster:
                                          max_cluster, precision, _ptr(g_idx), _ptr(g_dist), ws.ptr, ws.nbytes,
                                          _stream(stream)))
     return g_idx, g_dist
+
+
+def graph_recall(X, g_idx, queries, nn_idx=None, nn_dist=None, ws: Workspace | None = None, stream=None):
+    """Top-1 recall of the graph on the sampled queries (Sec. 5); returns (hits tensor [1] int64, nn_idx,
+    nn_dist): each query's exact nearest neighbour and its distance."""
+    n, d, ld = _x(X)
+    _dev(g_idx, torch.int32, "g_idx")
+    _dev(queries, torch.int32, "queries")
+    m, dev = queries.numel(), X.device
+    nn_idx = torch.empty(m, dtype=torch.int32, device=dev) if nn_idx is None else nn_idx
+    nn_dist = torch.empty(m, dtype=torch.float32, device=dev) if nn_dist is None else nn_dist
+    hits = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = ws or workspace(workspace_size(GK_OP_RECALL, n, d, m, g_idx.shape[1]), dev)
+    _check(_entry("gk_graph_recall", X)(_ptr(X), n, d, ld, _ptr(g_idx), g_idx.shape[1], _ptr(queries), m,
+                                        _ptr(nn_idx), _ptr(nn_dist), _ptr(hits), ws.ptr, ws.nbytes,
+                                        _stream(stream)))
+    return hits, nn_idx, nn_dist
 
 
 PROBE_SINK = 9728  # floats of the probes' sink (GK_PROBE_SINK)

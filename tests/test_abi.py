@@ -94,4 +94,9 @@ def test_argument_errors(lib):
     p = gkm.GraphParams(5, 50, 10, 128, 0, 7, 0)
     assert lib.gk_build_knn_graph(P, 100, 4, 4, ctypes.byref(p), P, P, None, None, ws, 1 << 30,
                                   None) == gkm.GK_ERR_INVALID
+    assert lib.gk_graph_recall(P, 10, 4, 4, P, 2, P, 0, None, None, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert b"m = 0" in lib.gk_last_error()
+    assert lib.gk_graph_recall(P, 10, 4, 4, P, 2, P, 5, None, None, None, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert gkm.workspace_size(gkm.GK_OP_RECALL, 1000, 4, 100) > gkm.workspace_size(gkm.GK_OP_RECALL, 1000, 4, 1)
+    assert gkm.workspace_size(gkm.GK_OP_BUILD, 1000, 4, 100) == 0  # the build has its own query
     assert lib.gk_read_status(None, None) == gkm.GK_ERR_INVALID
