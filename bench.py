@@ -503,6 +503,20 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
+    # graph quality: top-1 recall of the constructed graph on seeded sampled queries (Sec. 5), timed apart
+    gq = torch.Generator(device="cuda")
+    gq.manual_seed(w.seed + 7)
+    n_q = min(w.n, 1000)
+    queries = torch.randint(0, w.n, (n_q,), generator=gq, device="cuda", dtype=torch.int32)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record()
+    hits, _, _ = gkm.graph_recall(path.X, path.gi, queries)
+    r1.record()
+    torch.cuda.synchronize()
+    recall = {"value": int(hits.item()) / n_q, "queries": n_q, "ms": r0.elapsed_time(r1),
+              "note": "top-1 recall of the graph after the step's construction (tau rounds), exact neighbours by "
+                      "brute force on seeded random queries"}
+
     hbm, bf16, peak_src = load_peaks()
     ceilings = None
     if not args.no_ceilings:
@@ -558,6 +572,7 @@ def run_gpu(args):
                      "traffic": ncu_traffic(dom, w.name, args.precision, w.d, w.storage)},
         "gpu_launches": launches_per_step(w, args.precision) * args.steps,
         "measured_ceilings": ceilings,
+        "graph_recall_top1": recall,
         "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
