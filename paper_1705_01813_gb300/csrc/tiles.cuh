@@ -42,10 +42,23 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
 {
     using TL = RefineTile<T>;
     constexpr int XR = TL::XR, XC = TL::XC, DS = TL::DS, Q = TL::Q;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    // this thread: rows Q ty .. Q ty + Q - 1, columns Q tx .. Q tx + Q - 1 of the tile; a warp
-    // holds two values of ty, so warps whose rows all lie beyond the run skip the arithmetic
-    const bool rows_live = Q * ty < nr;
+    const int tid = threadIdx.x;
+    // this thread: rows Q by .. Q by + Q - 1, columns Q bx .. Q bx + Q - 1 of the tile.  Two tiles: block
+    // (by, bx) = (tid / 16, tid % 16), and warps whose rows all lie beyond the run skip the arithmetic.  A run's
+    // own tile (SAME) is symmetric, d(i, j) = d(j, i) bit for bit (the difference only changes sign): threads
+    // 0 .. 135 take the blocks with by <= bx, row by row, so that warps 5 to 7 skip the arithmetic, and each
+    // block is also written mirrored.
+    int by = tid >> 4, bx = tid & 15;
+    if constexpr (SAME) {
+        int t = tid, r = 0;
+        while (r < 16 && t >= 16 - r) {
+            t -= 16 - r;
+            r++;
+        }
+        by = r;
+        bx = r + t;
+    }
+    const bool rows_live = SAME ? (by < 16 && Q * bx < nr) : (Q * by < nr);
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 acc[Q][Q / 2];
 #pragma unroll
@@ -87,8 +100,8 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
         if (rows_live) {
             for (int tt = 0; tt < tmax; tt++) {
                 float2 vr[Q], vc[Q / 2];
-                const float4 *pr = reinterpret_cast<const float4 *>(xr + tt * XR + 2 * Q * ty);
-                const float4 *pc = reinterpret_cast<const float4 *>(xc + tt * XC + Q * tx);
+                const float4 *pr = reinterpret_cast<const float4 *>(xr + tt * XR + 2 * Q * by);
+                const float4 *pc = reinterpret_cast<const float4 *>(xc + tt * XC + Q * bx);
 #pragma unroll
                 for (int q = 0; q < Q / 2; q++) {
                     const float4 r4 = pr[q];
@@ -117,8 +130,12 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
         for (int a = 0; a < Q; a++)
 #pragma unroll
             for (int b = 0; b < Q / 2; b++) {
-                dt[(Q * ty + a) * DS + Q * tx + 2 * b] = acc[a][b].x;
-                dt[(Q * ty + a) * DS + Q * tx + 2 * b + 1] = acc[a][b].y;
+                dt[(Q * by + a) * DS + Q * bx + 2 * b] = acc[a][b].x;
+                dt[(Q * by + a) * DS + Q * bx + 2 * b + 1] = acc[a][b].y;
+                if (SAME && by != bx) {
+                    dt[(Q * bx + 2 * b) * DS + Q * by + a] = acc[a][b].x;
+                    dt[(Q * bx + 2 * b + 1) * DS + Q * by + a] = acc[a][b].y;
+                }
             }
     }
 }
