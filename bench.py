@@ -64,8 +64,8 @@ def parse():
     ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=None,
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
                          "BF16 screening in the assignment (SIMT); 3 the screening on the tensor cores (all give "
-                         "the same results).  Default: the fastest for the workload (2 for the deep-feature "
-                         "workload, whose centroid table exceeds L2; 1 otherwise)")
+                         "the same results).  Default: chosen by the autotuner (tune.py) on the workload's own "
+                         "graph and labels after the first warm-up step")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-ceilings", action="store_true",
                     help="skip the probe kernels that measure the L2 / HBM gather and FP32 FMA ceilings")
@@ -78,10 +78,7 @@ def parse():
                     help="no GPU run: read an ncu --csv log with dram__bytes_read.sum, dram__bytes_write.sum and "
                          "gpu__time_duration.sum of this workload's kernels and record the per-launch means in "
                          "profiles/traffic.json, tagged with the current kernel sources")
-    args = ap.parse_args()
-    if args.precision is None:
-        args.precision = 2 if datagen.WORKLOADS[args.workload].storage == "bf16" else 1
-    return args
+    return ap.parse_args()
 
 
 def dist_env():
@@ -380,11 +377,19 @@ def run_gpu(args):
     X, Xh = workload_samples(w, torch)
     gkm.load()
 
-    path = Path(gkm, torch, w, X, args.precision)
+    tuning = None
+    path = Path(gkm, torch, w, X, 1 if args.precision is None else args.precision)
     u = {}
     for q in range(args.warmup):  # the last warm-up step also measures u (outside the timed region)
         path.step(probe=(lambda ph, lab: u.__setitem__(ph, round(path.mean_candidates(lab), 2)))
                   if q == args.warmup - 1 else None)
+        if q == 0 and args.precision is None:
+            # the autotuner on this replica's graph and fit labels (all levels give the same results)
+            from paper_1705_01813_gb300 import tune
+            torch.cuda.synchronize()
+            tuning = tune.tune_precision(path.X, path.gi, path.gd, path.la if w.iters % 2 == 0 else path.lb, w.k,
+                                         tau=w.tau, iters=w.iters, max_cluster=w.max_cluster)
+            args.precision = path.precision = tuning["precision"]
     torch.cuda.synchronize()
     if gkm.read_status(path.ws) != gkm.GK_OK:
         raise RuntimeError("device status error during warm-up")
@@ -572,6 +577,7 @@ def run_gpu(args):
                      "traffic": ncu_traffic(dom, w.name, args.precision, w.d, w.storage)},
         "gpu_launches": launches_per_step(w, args.precision) * args.steps,
         "measured_ceilings": ceilings,
+        "precision_tuning": tuning,
         "graph_recall_top1": recall,
         "candidates_u": u or None,
         "clocks": ck,
