@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_nn_tiles(const XT *__restrict__ 
 {
     using TL = RefineTile<NN_T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *xr = reinterpret_cast<float *>(smem_raw);
-    float *xc = xr + RF_DK * TL::XR;
+    float *xr = reinterpret_cast<float *>(smem_raw);  // staging buffers of the pair tiles (tiles.cuh)
     float *dt = xr;  // aliases the staging buffers
     constexpr size_t span = TL::stage_floats > TL::tile_floats ? TL::stage_floats : TL::tile_floats;
     int *rid = reinterpret_cast<int *>(xr + span);
@@ -73,7 +72,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_nn_tiles(const XT *__restrict__ 
         if (tid < NN_T)
             cid[tid] = j0 + tid < n ? (int)(j0 + tid) : -1;
         __syncthreads();
-        tile_distances<NN_T, false>(X, d, ld, rid, cid, nr, xr, xc, dt);
+        tile_distances<NN_T, false>(X, d, ld, rid, cid, nr, xr, dt);
         __syncthreads();
         // warp w: queries w, w + 8, ..., the smallest key of the tile's samples other than the query
         for (int row = w; row < nr; row += RF_WARPS) {

@@ -62,8 +62,7 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT
     using TL = RefineTile<T>;
     constexpr int DS = TL::DS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *xr = reinterpret_cast<float *>(smem_raw);  // [RF_DK][XR]: row sample values as (v, v) pairs
-    float *xc = xr + RF_DK * TL::XR;                  // [RF_DK][XC]: column sample values
+    float *xr = reinterpret_cast<float *>(smem_raw);  // staging buffers of the pair tiles (tiles.cuh)
     float *dt = xr;  // aliases the staging buffers
     constexpr size_t span = TL::stage_floats > TL::tile_floats ? TL::stage_floats : TL::tile_floats;
     int *rid = reinterpret_cast<int *>(xr + span);
@@ -110,9 +109,9 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT
                 }
                 __syncthreads();
                 if (same)
-                    tile_distances<T, true>(X, d, ld, rid, cid, nr, xr, xc, dt);
+                    tile_distances<T, true>(X, d, ld, rid, cid, nr, xr, dt);
                 else
-                    tile_distances<T, false>(X, d, ld, rid, cid, nr, xr, xc, dt);
+                    tile_distances<T, false>(X, d, ld, rid, cid, nr, xr, dt);
                 __syncthreads();
                 RowRegs cur, nxt;
                 if (w < nr && rid[w] >= 0)

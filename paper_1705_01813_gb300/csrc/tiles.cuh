@@ -19,8 +19,12 @@ struct RefineTile {
     static constexpr int XC = T + 4;      // stride of a staged coordinate of the column samples
     static constexpr int DS = T + 1;      // padded stride of the distance tile
     static constexpr int Q = T / 16;      // consecutive rows, and columns, per thread
-    // the distance tile reuses the staging buffers (written after the last stage)
-    static constexpr size_t stage_floats = (size_t)RF_DK * (XR + XC);
+    // staging buffers: two for the 64-wide tile (one stage consumed while the next is stored), one for the
+    // 128-wide tile (two would halve its blocks per SM); the distance tile reuses them (written after the
+    // last stage)
+    static constexpr int NBUF = T == 64 ? 2 : 1;
+    static constexpr size_t buf_floats = (size_t)RF_DK * (XR + XC);
+    static constexpr size_t stage_floats = NBUF * buf_floats;
     static constexpr size_t tile_floats = (size_t)T * DS;
     static constexpr size_t fixed_bytes =
         sizeof(float) * (stage_floats > tile_floats ? stage_floats : tile_floats) + sizeof(int) * 2 * T;
@@ -34,11 +38,12 @@ struct RefineTile {
 };
 
 // Pair distances of one T x T tile into dt[row * DS + col]: rows are the samples rid[0 .. nr),
-// columns the samples cid[] (SAME: the rows again).  Called by all threads of the block; the caller
-// synchronises before reading dt.
+// columns the samples cid[] (SAME: the rows again).  stage points at the block's staging area
+// (RefineTile<T>::stage_floats floats), dt at the distance tile, which may alias it.  Called by all threads
+// of the block; the caller synchronises before reading dt.
 template <int T, bool SAME, typename XT>
 __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, int64_t ld, const int *rid,
-                                               const int *cid, int nr, float *xr, float *xc, float *dt)
+                                               const int *cid, int nr, float *stage, float *dt)
 {
     using TL = RefineTile<T>;
     constexpr int XR = TL::XR, XC = TL::XC, DS = TL::DS, Q = TL::Q;
@@ -82,26 +87,35 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
             }
         }
     };
-    fetch(0);
-    for (int t0 = 0; t0 < d; t0 += RF_DK) {
+    // stage s of the coordinates goes to buffer s % NBUF (rows [RF_DK][XR], then columns [RF_DK][XC]); with
+    // two buffers the next stage is stored while the current one is consumed, one barrier per stage
+    auto store = [&](float *buf) {
+        float *br = buf, *bc = buf + RF_DK * XR;
 #pragma unroll
         for (int p = 0; p < PER; p++) {
             const int e = tid + p * RF_THREADS, row = e / RF_DK, tt = e % RF_DK;
-            *reinterpret_cast<float2 *>(xr + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
+            *reinterpret_cast<float2 *>(br + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
             if constexpr (SAME)
-                xc[tt * XC + row] = pr_v[p];
+                bc[tt * XC + row] = pr_v[p];
             else
-                xc[tt * XC + row] = pc_v[p];
+                bc[tt * XC + row] = pc_v[p];
         }
-        __syncthreads();
-        if (t0 + RF_DK < d)
+    };
+    constexpr int NBUF = TL::NBUF;
+    fetch(0);
+    store(stage);
+    __syncthreads();
+    for (int t0 = 0, sidx = 0; t0 < d; t0 += RF_DK, sidx = (sidx + 1) % NBUF) {
+        const float *cur = stage + sidx * TL::buf_floats;
+        const bool more = t0 + RF_DK < d;
+        if (more)
             fetch(t0 + RF_DK);
         const int tmax = min(RF_DK, d - t0);
         if (rows_live) {
             for (int tt = 0; tt < tmax; tt++) {
                 float2 vr[Q], vc[Q / 2];
-                const float4 *pr = reinterpret_cast<const float4 *>(xr + tt * XR + 2 * Q * by);
-                const float4 *pc = reinterpret_cast<const float4 *>(xc + tt * XC + Q * bx);
+                const float4 *pr = reinterpret_cast<const float4 *>(cur + tt * XR + 2 * Q * by);
+                const float4 *pc = reinterpret_cast<const float4 *>(cur + RF_DK * XR + tt * XC + Q * bx);
 #pragma unroll
                 for (int q = 0; q < Q / 2; q++) {
                     const float4 r4 = pr[q];
@@ -123,7 +137,17 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
                     }
             }
         }
-        __syncthreads();
+        if constexpr (NBUF == 2) {
+            if (more)
+                store(stage + (sidx ^ 1) * TL::buf_floats);  // read last in the previous stage, before its barrier
+            __syncthreads();
+        } else {
+            __syncthreads();  // every thread is done with the buffer
+            if (more) {
+                store(stage);
+                __syncthreads();
+            }
+        }
     }
     if (rows_live) {
 #pragma unroll
