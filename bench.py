@@ -7,11 +7,17 @@ SIFT-shaped n = 1,000,000, d = 128, k = 10,000, kappa = 50 workload):
       tau = 10 rounds of {graph-guided assignment, grouping, update, pair refinement}
   graph-guided k-means (Alg. 2, closest-centroid rule): seeded labels at k,
       then 10 iterations of {assignment, grouping, update}
-The step is driven through the library's step entry points with CUDA events
-between the calls (the same kernels the one-call API runs), which gives the
-per-kernel durations used for the roofline.  `e2e` times the one-call API
+The step is driven through the library's step entry points (the same kernels
+the one-call API runs): once launched call by call with CUDA events between the
+calls (the per-kernel durations of the roofline), then captured into a CUDA
+graph whose replay time is `value`.  `e2e` times the one-call API
 (gk_build_knn_graph + gk_kmeans_fit) with the samples copied from pinned host
-memory and the labels and centroids copied back inside the timed region.
+memory and the labels and centroids copied back inside the timed region.  By
+default the precision level is chosen by the autotuner (tune.py) after the
+first warm-up step.  Outside the timed region the line also reports the
+constructed graph's top-1 recall (Sec. 5), the probe-measured gather and FMA
+ceilings, the serving passes and the oracle's timing on a bounded sample with
+the library's results on that sample compared to the oracle's.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gkm|reference]
 Under torchrun (N > 1) every rank runs an independent replica on its GPU
