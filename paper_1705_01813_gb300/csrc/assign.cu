@@ -82,8 +82,6 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const XT *__restrict__
                                                           const float *__restrict__ C, int k,
                                                           const int32_t *__restrict__ Lin,
                                                           int32_t *__restrict__ Lout, float *__restrict__ best_out,
-                                                          double *__restrict__ blk_sum,
-                                                          unsigned long long *__restrict__ blk_changed,
                                                           DevStatus *st)
 {
     extern __shared__ __align__(16) float smem[];
@@ -91,11 +89,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const XT *__restrict__
     const int dpad = (d + 3) & ~3;
     float *xs = smem + w * dpad;
     int *qlist = reinterpret_cast<int *>(smem + AS_WARPS * dpad) + w * AS_QCAP;
-    __shared__ double s_sum[AS_WARPS];
-    __shared__ unsigned long long s_chg[AS_WARPS];
 
-    double wsum = 0.0;
-    unsigned long long wchg = 0;
     const int ncand = kappa + 1;
     for (int64_t i = (int64_t)blockIdx.x * AS_WARPS + w; i < n; i += (int64_t)gridDim.x * AS_WARPS) {
         // stage x_i
@@ -167,25 +161,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign(const XT *__restrict__
             Lout[i] = br;
             if (best_out)
                 best_out[i] = bd;
-            wsum += (double)bd;
-            wchg += (br != own) ? 1ull : 0ull;
         }
         __syncwarp();
-    }
-    if (lane == 0) {
-        s_sum[w] = wsum;
-        s_chg[w] = wchg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        unsigned long long c = 0;
-        for (int q = 0; q < AS_WARPS; q++) {
-            t += s_sum[q];
-            c += s_chg[q];
-        }
-        blk_sum[blockIdx.x] = t;
-        blk_changed[blockIdx.x] = c;
     }
 }
 
@@ -516,16 +493,12 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
                                                                   const int32_t *__restrict__ Lin,
                                                                   int32_t *__restrict__ Lout,
                                                                   float *__restrict__ best_out,
-                                                                  double *__restrict__ blk_sum,
-                                                                  unsigned long long *__restrict__ blk_changed,
                                                                   const int32_t *__restrict__ tmem_members, const int32_t *__restrict__ tile_flag,
                                                                const int32_t *__restrict__ sel_lab,
                                                                const int32_t *__restrict__ sel_n, DevStatus *st)
 {
     __shared__ int s_q[AS_WARPS][AS_QCAP];
     __shared__ float s_lo[AS_WARPS][AS_QCAP + 31];
-    __shared__ double s_sum[AS_WARPS];
-    __shared__ unsigned long long s_chg[AS_WARPS];
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *qlist = s_q[w];
     const int d4 = d >> 2;
@@ -533,8 +506,6 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
     const uint2 *Cb4 = reinterpret_cast<const uint2 *>(Cb);  // 4 BF16 per 8 bytes
     const float gam = (float)(d + 8) * 5.9604645e-8f;         // FP32 rounding of a d-term sum, relative
 
-    double wsum = 0.0;
-    unsigned long long wchg = 0;
     const int ncand = kappa + 1;
     for (int64_t p = (int64_t)blockIdx.x * AS_WARPS + w; p < n; p += (int64_t)gridDim.x * AS_WARPS) {
         int64_t i = p;
@@ -667,25 +638,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_assign_rows_bf(const float *_
             Lout[i] = br;
             if (best_out)
                 best_out[i] = bd;
-            wsum += (double)bd;
-            wchg += (br != own) ? 1ull : 0ull;
         }
         __syncwarp();
-    }
-    if (lane == 0) {
-        s_sum[w] = wsum;
-        s_chg[w] = wchg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        unsigned long long c = 0;
-        for (int q = 0; q < AS_WARPS; q++) {
-            t += s_sum[q];
-            c += s_chg[q];
-        }
-        blk_sum[blockIdx.x] = t;
-        blk_changed[blockIdx.x] = c;
     }
 }
 
@@ -829,7 +783,7 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
             }
 #define GK_ASGB(NV, T)                                                                                           \
     k_assign_rows_bf<NV, T><<<AS_BLOCKS, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k,   \
-                                                                labels_in, labels_out, best, blk_sum, blk_chg,      \
+                                                                labels_in, labels_out, best,                        \
                                                                 members, tile_flag, sel_lab, sel_n, st)
             if (tiles) {
                 GK_ASGB(1, true);  // d <= 128 on the tensor-core path
@@ -874,13 +828,13 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
                 cudaSuccess)
                 return e;
             k_assign<4, XT><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
-                                                                labels_out, best, blk_sum, blk_chg, st);
+                                                                labels_out, best, st);
         } else {
             if ((e = set_max_smem(reinterpret_cast<const void *>(k_assign<1, XT>), shm_max)) !=
                 cudaSuccess)
                 return e;
             k_assign<1, XT><<<AS_BLOCKS, AS_WARPS * 32, shm, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,
-                                                                labels_out, best, blk_sum, blk_chg, st);
+                                                                labels_out, best, st);
         }
     }
     if (sum_d2 || n_changed) {
