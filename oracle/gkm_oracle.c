@@ -158,6 +158,40 @@ void or_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kap
     }
 }
 
+/*
+ * The same initial rows for a few listed samples only (for spot checks at
+ * sizes where the full construction is too slow): row q of g_idx / g_dist
+ * receives sample rows[q]'s list, drawn and sorted exactly as above.
+ */
+void or_init_graph_rows(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
+                        const int64_t *rows, int64_t nrows, int32_t *g_idx, double *g_dist)
+{
+    uint64_t key = seed ^ OR_TAG_GRAPH;
+    for (int64_t q = 0; q < nrows; q++) {
+        const int64_t i = rows[q];
+        int32_t *row = g_idx + q * kappa;
+        double *rd = g_dist + q * kappa;
+        int32_t got = 0;
+        for (uint64_t a = 0; got < kappa; a++) {
+            int64_t j = (int64_t)(or_draw(key, ((uint64_t)i << 32) | a) % (uint64_t)n);
+            if (j == i)
+                continue;
+            int dup = 0;
+            for (int32_t t = 0; t < got; t++)
+                if (row[t] == j) {
+                    dup = 1;
+                    break;
+                }
+            if (dup)
+                continue;
+            row[got] = (int32_t)j;
+            rd[got] = or_d2_ff(X + i * ld, X + j * ld, d);
+            got++;
+        }
+        or_sort_row(row, rd, kappa);
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Assignment: Alg. 2 with the closest-centroid rule (GK-means^-)            */
 /* ------------------------------------------------------------------------- */

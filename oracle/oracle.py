@@ -55,6 +55,7 @@ def _bind(lib):
     lib.or_draw.restype = U64
     lib.or_init_labels.argtypes = [I64, I32, U64, P]
     lib.or_init_graph.argtypes = [P, I64, I64, I64, I32, U64, P, P]
+    lib.or_init_graph_rows.argtypes = [P, I64, I64, I64, I32, U64, P, I64, P, P]
     lib.or_assign.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, I64]
     lib.or_assign_exhaustive.argtypes = [P, I64, I64, I64, P, I32, P, P]
     lib.or_update.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
@@ -133,6 +134,15 @@ class Oracle:
         idx = np.empty((n, kappa), np.int32)
         dist = np.empty((n, kappa), np.float64)
         self._lib.or_init_graph(_p(X), n, d, d, kappa, seed, _p(idx), _p(dist))
+        return idx, dist
+
+    def init_graph_rows(self, X, kappa: int, seed: int, rows):
+        """The initial graph's rows for the listed samples only (the same draws and distances)."""
+        X, n, d = _x(X)
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        idx = np.empty((r.shape[0], kappa), np.int32)
+        dist = np.empty((r.shape[0], kappa), np.float64)
+        self._lib.or_init_graph_rows(_p(X), n, d, d, kappa, seed, _p(r), r.shape[0], _p(idx), _p(dist))
         return idx, dist
 
     def assign(self, X, G, C, labels, rows=None):

@@ -300,6 +300,15 @@ def check_refine_rows_and_chunks(orc):
             assert run_of[j] == run_of[i]
 
 
+def check_init_graph_rows(orc):
+    # the row-restricted form (for spot checks at full size) gives the full construction's rows
+    X = _blobs(500, 6, 5, 13)
+    gi, gd = orc.init_graph(X, 9, 21)
+    rows = [0, 499, 7, 250, 7]
+    ri, rd = orc.init_graph_rows(X, 9, 21, rows)
+    assert np.array_equal(ri, gi[rows]) and np.array_equal(rd, gd[rows])
+
+
 def check_group_csr(orc):
     g = np.random.default_rng(8)
     L = g.integers(0, 50, 3000).astype(np.int32)
@@ -311,7 +320,7 @@ def check_group_csr(orc):
 CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_assign_complete_graph,
           check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
           check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
-          check_group_csr]
+          check_init_graph_rows, check_group_csr]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
