@@ -677,6 +677,10 @@ def workload_samples(w, torch):
         X = datagen.deep_like_device(w.n, w.d, w.extra["n_dirs"], 50.0, w.seed, device="cuda")
         torch.cuda.empty_cache()
         return X, X.cpu()
+    if w.name.startswith("gist"):  # 10^9 Beta draws: a minute on the host, a second on the device
+        X = datagen.gist_like_device(w.n, w.d, w.extra.get("n_latent", 1000), w.seed, device="cuda")
+        torch.cuda.empty_cache()
+        return X, X.cpu()
     Xh = torch.from_numpy(w.data())
     return Xh.cuda(), Xh
 
@@ -739,6 +743,8 @@ def run_reference(args):
     ns = oracle_sample(w, REF_SAMPLE)
     if w.storage == "bf16":  # the recipe drawn on the host for the sample only (BF16 values widened)
         X = datagen.bf16_bits_to_f32(datagen.deep_like(ns, w.d, w.extra["n_dirs"], 50.0, w.seed))
+    elif w.name.startswith("gist"):
+        X = datagen.gist_like(ns, w.d, w.extra.get("n_latent", 1000), w.seed)
     else:
         X = np.ascontiguousarray(w.data()[:ns])
     for _ in range(args.warmup):
@@ -748,8 +754,8 @@ def run_reference(args):
         k = _oracle_step(O, w, X)[0]
     dt = time.perf_counter() - t0
     v = ns * args.steps / dt
-    drawn = (f"{ns} samples of the {w.name} recipe drawn on the host" if w.storage == "bf16" else
-             f"first {ns} samples of {w.name}")
+    drawn = (f"{ns} samples of the {w.name} recipe drawn on the host" if w.storage == "bf16" or
+             w.name.startswith("gist") else f"first {ns} samples of {w.name}")
     sample = (f"{drawn} per step, k = {k}, k0 = {ns // w.xi}: graph construction + fit, "
               f"single-threaded FP64 C oracle")
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world,

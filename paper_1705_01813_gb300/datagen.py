@@ -79,6 +79,59 @@ def gist_like(n: int, d: int = 960, n_latent: int = 1000, seed: int = BASE_SEED 
     return X
 
 
+def gamma_device(alpha, g, max_rounds: int = 64):
+    """Gamma(alpha, 1) draws, one per element of the tensor alpha (> 0), with the seeded torch generator g:
+    Marsaglia and Tsang (2000) rejection for shape >= 1 (d = a - 1/3, c = 1/sqrt(9d), v = (1 + c z)^3,
+    accept when log u < z^2/2 + d - d v + d log v), and for shape < 1 the draw at shape + 1 times
+    u^(1/shape)."""
+    import torch
+    a = alpha.to(torch.float64)
+    small = a < 1.0
+    sh = torch.where(small, a + 1.0, a)
+    dd = sh - 1.0 / 3.0
+    c = 1.0 / torch.sqrt(9.0 * dd)
+    out = torch.empty_like(a)
+    todo = torch.arange(a.numel(), device=a.device)
+    flat_d, flat_c = dd.reshape(-1), c.reshape(-1)
+    for _ in range(max_rounds):
+        if todo.numel() == 0:
+            break
+        z = torch.randn(todo.shape, generator=g, device=a.device, dtype=torch.float64)
+        u = torch.rand(todo.shape, generator=g, device=a.device, dtype=torch.float64)
+        dq, cq = flat_d[todo], flat_c[todo]
+        v = (1.0 + cq * z) ** 3
+        ok = (v > 0) & (torch.log(u) < 0.5 * z * z + dq - dq * v + dq * torch.log(torch.clamp(v, min=1e-300)))
+        out.view(-1)[todo[ok]] = (dq * v)[ok]
+        todo = todo[~ok]
+    if todo.numel():
+        raise RuntimeError("gamma sampler did not converge")
+    u = torch.rand(a.shape, generator=g, device=a.device, dtype=torch.float64)
+    return torch.where(small, out * u ** (1.0 / a), out)
+
+
+def gist_like_device(n: int, d: int = 960, n_latent: int = 1000, seed: int = BASE_SEED + 2, conc: float = 50.0,
+                     device="cuda", chunk: int = 1 << 16):
+    """The recipe of gist_like drawn on the GPU with a seeded torch generator (same recipe, different stream of
+    random numbers): latent mu ~ Beta(2, 8) clipped to [1e-3, 1 - 1e-3], x_t ~ Beta(conc mu, conc (1 - mu)),
+    every Beta draw as G_a / (G_a + G_b) of two Gamma draws.  Returns an n x d FP32 tensor on the device."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+
+    def beta(a, b):
+        ga, gb = gamma_device(a, g), gamma_device(b, g)
+        return ga / (ga + gb)
+
+    mu = torch.clamp(beta(torch.full((n_latent, d), 2.0, device=device, dtype=torch.float64),
+                          torch.full((n_latent, d), 8.0, device=device, dtype=torch.float64)), 1e-3, 1 - 1e-3)
+    z = torch.randint(0, n_latent, (n,), generator=g, device=device)
+    X = torch.empty((n, d), dtype=torch.float32, device=device)
+    for s in range(0, n, chunk):
+        m = mu[z[s:s + chunk]]
+        X[s:s + m.shape[0]] = beta(conc * m, conc * (1.0 - m)).to(torch.float32)
+    return X
+
+
 def _vmf_w(g: np.random.Generator, kappa: float, d: int, size: int) -> np.ndarray:
     """Wood (1994) rejection sampler for the cosine w of a vMF draw in d dimensions."""
     b = (-2.0 * kappa + math.sqrt(4.0 * kappa * kappa + (d - 1.0) ** 2)) / (d - 1.0)

@@ -50,3 +50,25 @@ def test_vmf_mixture_host_and_device_agree():
         return float(S.max(1).values.mean())
 
     assert abs(nn_cos(A) - nn_cos(B)) < 0.03 * nn_cos(B)
+
+
+@pytest.mark.parametrize("shape", [0.3, 1.0, 10.0, 40.0])
+def test_gamma_device_moments(shape):
+    """Gamma(a, 1) has mean a and variance a (the device Beta draws are ratios of these)."""
+    torch = pytest.importorskip("torch")
+    g = torch.Generator()
+    g.manual_seed(int(shape * 100))
+    x = datagen.gamma_device(torch.full((200_000,), shape), g).double()
+    se = (shape / 200_000) ** 0.5
+    assert abs(x.mean().item() - shape) < 5 * se
+    assert abs(x.var().item() - shape) < 0.03 * shape + 5 * se
+
+
+def test_gist_device_generator_matches_host_recipe():
+    torch = pytest.importorskip("torch")
+    A = datagen.gist_like_device(20000, 96, 50, seed=5, device="cpu", chunk=4096).numpy().astype(np.float64)
+    B = datagen.gist_like(20000, 96, 50, seed=5).astype(np.float64)
+    assert A.shape == B.shape and 0.0 <= A.min() and A.max() <= 1.0  # FP32 may round an extreme draw to 0 or 1
+    # Beta(2, 8) latent means (mean 0.2); the spread mixes the latent and the per-sample Beta draws
+    assert abs(A.mean() - B.mean()) < 0.01 and abs(A.std() - B.std()) < 0.01
+    assert abs(A.mean() - 0.2) < 0.01
