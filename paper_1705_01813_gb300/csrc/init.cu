@@ -31,7 +31,11 @@ cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *lab
 // rejection rule.  Each lane then computes the FP32 distance of one neighbour
 // (pair_d2_seq), and the row is sorted by (distance, id) by ranking.
 constexpr int IG_WARPS = 4;
-constexpr int IG_DC = 128;  // coordinates staged per step (vector path)
+constexpr int IG_DC_BYTES = 512;  // bytes of a row staged per step (vector path)
+
+// Coordinates staged per step: 128 FP32 or 256 BF16 values (one 512-byte bulk copy per row).
+template <typename XT>
+__host__ __device__ constexpr int ig_dc() { return IG_DC_BYTES / (int)sizeof(XT); }
 constexpr uint32_t IG_WAIT_ITERS = 1u << 22;
 
 // Rows staged per batch: kappa cut into equal batches of at most 32.
@@ -41,10 +45,10 @@ __host__ __device__ inline int ig_batch(int kappa)
     return (kappa + nb - 1) / nb;
 }
 
-// Staged row stride in elements: IG_DC plus 16 bytes, so that the 32 lanes
+// Staged row stride in elements: ig_dc() plus 16 bytes, so that the 32 lanes
 // reading their own rows 16 bytes at a time hit distinct banks.
 template <typename XT>
-__host__ __device__ constexpr int ig_stride() { return IG_DC + 16 / (int)sizeof(XT); }
+__host__ __device__ constexpr int ig_stride() { return ig_dc<XT>() + 16 / (int)sizeof(XT); }
 
 // Dynamic shared memory per warp: on the vector path a batch of rows; on both
 // paths at least the kappa 8-byte keys of the rank sort (they reuse the area).
@@ -152,8 +156,8 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__res
             for (int b0 = 0, bi = 0; b0 < kappa; b0 += B, bi++) {
                 const int nb = min(B, kappa - b0);
                 float acc = 0.f;
-                for (int t0 = 0; t0 < d; t0 += IG_DC) {
-                    const int dc = min(IG_DC, d - t0);
+                for (int t0 = 0; t0 < d; t0 += ig_dc<XT>()) {
+                    const int dc = min(ig_dc<XT>(), d - t0);
                     const uint32_t bytes = (uint32_t)(dc * (int)sizeof(XT));
                     __syncwarp();                 // the previous rows are no longer read
                     tc::fence_proxy_async_smem();  // ... before the async proxy rewrites them

@@ -46,7 +46,8 @@ def _same(a, b):
             assert x == y
 
 
-@pytest.mark.parametrize("n,d,kappa", [(3000, 32, 20), (1037, 33, 50), (2000, 128, 16), (501, 5, 8)])
+@pytest.mark.parametrize("n,d,kappa", [(3000, 32, 20), (1037, 33, 50), (2000, 128, 16), (501, 5, 8),
+                                       (1500, 512, 40), (999, 264, 24)])  # 256-element chunks, ragged last one
 def test_init_graph(G, n, d, kappa):
     xb, xf = _pair(n, d, d)
     _same(G.init_graph(xb, kappa, 11), G.init_graph(xf, kappa, 11))
