@@ -1,0 +1,47 @@
+"""The bench's accounting of this library's kernels: `gpu_launches` (launches_per_step) against the kernels a step
+actually launches, counted by the torch profiler, and the kernel -> source map its DRAM-traffic records use."""
+import os
+import re
+
+import pytest
+
+import bench
+from paper_1705_01813_gb300 import datagen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_kernel_source_map_names_real_kernels():
+    for name, src in bench.KERNEL_SOURCE.items():
+        text = open(os.path.join(ROOT, "paper_1705_01813_gb300", "csrc", src)).read()
+        assert re.search(r"__global__[^;{]*\b" + name + r"\s*\(", text), (name, src)
+
+
+def test_kernel_of_follows_the_dispatch_rules():
+    assert bench.kernel_of("refine", 1, 128) == "k_refine_gram" and bench.kernel_of("refine", 0, 128) == "k_refine"
+    assert bench.kernel_of("refine", 1, 960) == "k_refine" and bench.kernel_of("refine", 1, 32) == "k_refine"
+    assert bench.kernel_of("assign", 2) == "k_assign_rows_bf8" and bench.kernel_of("assign", 1) == "k_assign_rows"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_launches_per_step_matches_the_profiler(precision):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from torch.profiler import ProfilerActivity, profile
+
+    from paper_1705_01813_gb300 import gkm
+    w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
+    X = torch.from_numpy(w.data()).cuda()
+    path = bench.Path(gkm, torch, w, X, precision)
+    path.step()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        path.step()
+        torch.cuda.synchronize()
+    names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+    ours = [nm for nm in names if nm.startswith("gkm::") or "gkm::" in nm.split("(")[0]]
+    if not ours:
+        pytest.skip("the profiler recorded no kernel names here")
+    assert len(ours) == bench.launches_per_step(w, precision)
