@@ -37,11 +37,15 @@ def test_launches_per_step_matches_the_profiler(precision):
     path = bench.Path(gkm, torch, w, X, precision)
     path.step()
     torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        path.step()
-        torch.cuda.synchronize()
-    names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
-    ours = [nm for nm in names if nm.startswith("gkm::") or "gkm::" in nm.split("(")[0]]
+    ours = []
+    for _ in range(2):  # a first profiling session may come back empty while the profiler initialises
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            path.step()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        ours = [nm for nm in names if nm.startswith("gkm::") or "gkm::" in nm.split("(")[0]]
+        if ours:
+            break
     if not ours:
         pytest.skip("the profiler recorded no kernel names here")
     assert len(ours) == bench.launches_per_step(w, precision)
