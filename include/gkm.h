@@ -332,6 +332,23 @@ GK_API int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t
                                 int64_t *hits, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Replay of repeated requests (off by default).  With replay on, a call of
+ * gk_build_knn_graph(_bf16) or gk_kmeans_fit(_bf16) whose arguments (every
+ * pointer, size and parameter; the device) equal an earlier call's is
+ * launched as one CUDA graph, captured on that earlier call, instead of its
+ * few hundred kernel launches one by one.  The graph reads and writes the
+ * same addresses as a direct call, so the results are the same; the host
+ * distortion log (e_log) is filled after it as before.  The first call with
+ * new arguments pays the capture.  A call on a stream that is being captured
+ * already, or on the legacy default stream (NULL), runs directly.  At most 32
+ * graphs are kept (the oldest dropped, after a device synchronisation).
+ * gk_set_replay(0) drops them all, after synchronising their devices.
+ * Meant for a loop that repeats one request on the same buffers; a stream of
+ * differently shaped requests would pay a capture per request.
+ */
+GK_API int gk_set_replay(int enable);
+
+/*
  * Measurement probes: the ceilings against which the assignment is read where
  * HBM bandwidth does not bound it (its centroid rows come from L2).  Both run
  * 152 x 8 blocks of 8 warps and write one float per warp to sink (device,

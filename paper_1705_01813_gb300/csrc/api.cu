@@ -9,6 +9,7 @@
 #include <mutex>
 #include <set>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -128,6 +129,114 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
 }
 
 int32_t build_k0(int64_t n, int32_t xi) { return (int32_t)(n / xi > 0 ? n / xi : 1); }
+
+// ---------------------------------------------------------------------------
+// Replay of repeated one-call requests (opt-in, gk_set_replay).  A graph
+// construction or fit whose arguments (pointers, sizes, parameters, device)
+// equal an earlier call's is launched as the CUDA graph captured on that
+// call, instead of its few hundred kernel launches one by one; the graph
+// reads and writes the same addresses, so the results are those of a direct
+// call.  A call on a stream that is already being captured, or on the legacy
+// default stream, enqueues its launches directly.
+// ---------------------------------------------------------------------------
+constexpr size_t REPLAY_MAX = 32;  // cached graphs; the oldest is dropped beyond
+
+struct Replay {
+    std::mutex mu;
+    bool on = false;
+    std::map<std::vector<uint64_t>, cudaGraphExec_t> execs;
+    std::vector<std::vector<uint64_t>> order;  // insertion order, for dropping the oldest
+
+    // Drops every cached graph after the work of the devices they belong to has finished (a graph may still be
+    // running from a replay).
+    void clear()
+    {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        std::set<int> devs;
+        for (auto &kv : execs)
+            devs.insert((int)kv.first.back());
+        for (int dv : devs) {
+            cudaSetDevice(dv);
+            cudaDeviceSynchronize();
+        }
+        cudaSetDevice(cur);
+        for (auto &kv : execs)
+            cudaGraphExecDestroy(kv.second);
+        execs.clear();
+        order.clear();
+    }
+};
+
+Replay &replay()
+{
+    static Replay r;
+    return r;
+}
+
+// Runs enqueue() (which returns a GK_ code) directly, or through the replay cache under `key`.
+template <typename F>
+int enqueue_or_replay(std::vector<uint64_t> key, cudaStream_t s, F enqueue)
+{
+    Replay &R = replay();
+    {
+        std::lock_guard<std::mutex> lock(R.mu);
+        if (!R.on)
+            return enqueue();
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s == nullptr || cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return enqueue();
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    key.push_back((uint64_t)dev);
+    {
+        std::lock_guard<std::mutex> lock(R.mu);
+        auto it = R.execs.find(key);
+        if (it != R.execs.end()) {
+            GK_CUDA(cudaGraphLaunch(it->second, s));
+            return GK_OK;
+        }
+    }
+    GK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != GK_OK || e != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        return rc != GK_OK ? rc : fail(GK_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess)
+        return fail(GK_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    {
+        std::lock_guard<std::mutex> lock(R.mu);
+        auto it = R.execs.find(key);
+        if (it == R.execs.end()) {
+            if (R.order.size() >= REPLAY_MAX) {
+                auto old = R.execs.find(R.order.front());
+                if (old != R.execs.end()) {
+                    cudaDeviceSynchronize();  // the oldest graph may still be running from a replay
+                    cudaGraphExecDestroy(old->second);
+                    R.execs.erase(old);
+                }
+                R.order.erase(R.order.begin());
+            }
+            R.execs[key] = exec;
+            R.order.push_back(key);
+        } else {  // another thread captured the same call meanwhile
+            cudaGraphExecDestroy(exec);
+            exec = it->second;
+        }
+        GK_CUDA(cudaGraphLaunch(exec, s));
+    }
+    return GK_OK;
+}
+
+uint64_t u64(const void *p) { return (uint64_t)reinterpret_cast<uintptr_t>(p); }
 
 }  // namespace
 
@@ -260,7 +369,7 @@ static int assign_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int6
                     precision);
     if (bf16 && precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
+                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
@@ -450,8 +559,8 @@ static int graph_refine_groups_impl(const void *X, bool bf16, int64_t n, int64_t
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_REFINE, n, d, k);
-    GK_CUDA(launch_refine(X, bf16, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch, L.st,
-                          (cudaStream_t)stream, precision));
+    GK_CUDA(launch_refine(X, bf16, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, L.ref_scratch,
+                          L.st, (cudaStream_t)stream, precision));
     return GK_OK;
 }
 
@@ -491,7 +600,7 @@ static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64
                     precision);
     if (bf16 && precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
+                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
@@ -501,26 +610,36 @@ static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64
     cudaStream_t s = (cudaStream_t)stream;
     int32_t *cnt = counts_out ? counts_out : L.grp.counts;
 
-    // ping-pong the labels so that the final ones land in labels_out
-    int32_t *cur = (iters % 2 == 0) ? labels_out : L.labels_b;
-    int32_t *nxt = (iters % 2 == 0) ? L.labels_b : labels_out;
-    if (init_labels)
-        GK_CUDA(cudaMemcpyAsync(cur, init_labels, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    else
-        GK_CUDA(launch_init_labels(n, k, seed, cur, s));
-    GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)k * (size_t)d, s));
-    GK_CUDA(launch_group(cur, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0, L.upd_scratch, s));
-    for (int t = 0; t < iters; t++) {
-        GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t, nullptr,
-                              L.asg_scratch, L.st, s, precision, L.grp.members));
-        GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
-        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
+    auto enqueue = [&]() -> int {
+        // ping-pong the labels so that the final ones land in labels_out
+        int32_t *cur = (iters % 2 == 0) ? labels_out : L.labels_b;
+        int32_t *nxt = (iters % 2 == 0) ? L.labels_b : labels_out;
+        if (init_labels)
+            GK_CUDA(cudaMemcpyAsync(cur, init_labels, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        else
+            GK_CUDA(launch_init_labels(n, k, seed, cur, s));
+        GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)k * (size_t)d, s));
+        GK_CUDA(launch_group(cur, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0,
                               L.upd_scratch, s));
-        int32_t *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
+        for (int t = 0; t < iters; t++) {
+            GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t,
+                                  nullptr, L.asg_scratch, L.st, s, precision, L.grp.members));
+            GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
+            GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
+                                  L.upd_scratch, s));
+            int32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        return GK_OK;
+    };
+    const std::vector<uint64_t> key = {1, u64(X), (uint64_t)bf16, (uint64_t)n, (uint64_t)d, (uint64_t)ld, (uint64_t)k,
+                                       u64(g_idx), (uint64_t)kappa, (uint64_t)iters, u64(init_labels), seed,
+                                       (uint64_t)precision, u64(labels_out), u64(C_out), u64(counts_out), u64(ws),
+                                       (uint64_t)ws_bytes};
+    if ((rc = enqueue_or_replay(key, s, enqueue)) != GK_OK)
+        return rc;
     if (e_log) {
         GK_CUDA(cudaMemcpyAsync(e_log, L.elog, sizeof(double) * (size_t)(2 * iters + 1), cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
@@ -563,7 +682,7 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
                     p->max_cluster, p->precision);
     if (bf16 && p->precision == 3)
         return fail(GK_ERR_INVALID,
-                    "BF16 samples: the assignment's precision must be 0, 1 or 2 (its tensor-core screening reads FP32 samples)");
+                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
     if (!g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "graph arrays are NULL");
     const int32_t k0 = build_k0(n, p->xi);
@@ -573,29 +692,38 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
     L = carve(ws, GK_OP_BUILD, n, d, k0);
     cudaStream_t s = (cudaStream_t)stream;
     const int tau = p->tau;
-    int32_t *cur = L.labels_a, *nxt = L.labels_b;
-    GK_CUDA(launch_init_graph(X, bf16, n, d, ld, p->kappa, p->seed, g_idx, g_dist, L.st, s));
-    GK_CUDA(launch_init_labels(n, k0, p->seed, cur, s));
-    GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)k0 * (size_t)d, s));
-    GK_CUDA(launch_group(cur, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
-                          L.upd_scratch, s));
-    for (int t = 0; t < tau; t++) {
-        // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
-        GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
-                              nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
-        GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
-        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
-                              L.elog + 2 + 2 * t, L.upd_scratch, s));
-        // exhaustive pairs inside the clusters of the new partition
-        GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
-                              g_dist, L.ref_scratch, L.st, s, p->precision));
-        int32_t *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-    if (labels_out)
-        GK_CUDA(cudaMemcpyAsync(labels_out, cur, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    auto enqueue = [&]() -> int {
+        int32_t *cur = L.labels_a, *nxt = L.labels_b;
+        GK_CUDA(launch_init_graph(X, bf16, n, d, ld, p->kappa, p->seed, g_idx, g_dist, L.st, s));
+        GK_CUDA(launch_init_labels(n, k0, p->seed, cur, s));
+        GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)k0 * (size_t)d, s));
+        GK_CUDA(launch_group(cur, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
+                              L.upd_scratch, s));
+        for (int t = 0; t < tau; t++) {
+            // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
+            GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
+                                  nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
+            GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+            GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
+                                  L.elog + 2 + 2 * t, L.upd_scratch, s));
+            // exhaustive pairs inside the clusters of the new partition
+            GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
+                                  g_dist, L.ref_scratch, L.st, s, p->precision));
+            int32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        if (labels_out)
+            GK_CUDA(cudaMemcpyAsync(labels_out, cur, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        return GK_OK;
+    };
+    const std::vector<uint64_t> key = {2, u64(X), (uint64_t)bf16, (uint64_t)n, (uint64_t)d, (uint64_t)ld,
+                                       (uint64_t)p->kappa, (uint64_t)p->xi, (uint64_t)p->tau,
+                                       (uint64_t)p->max_cluster, p->seed, (uint64_t)p->precision, u64(g_idx),
+                                       u64(g_dist), u64(labels_out), u64(ws), (uint64_t)ws_bytes};
+    if ((rc = enqueue_or_replay(key, s, enqueue)) != GK_OK)
+        return rc;
     if (e_log) {
         GK_CUDA(cudaMemcpyAsync(e_log, L.elog, sizeof(double) * (size_t)(2 * tau + 1), cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
@@ -653,6 +781,16 @@ int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, co
 {
     return graph_recall_impl(X, true, n, d, ld, g_idx, kappa, queries, m, nn_idx, nn_dist, hits, ws, ws_bytes,
                              stream);
+}
+
+int gk_set_replay(int enable)
+{
+    Replay &R = replay();
+    std::lock_guard<std::mutex> lock(R.mu);
+    R.on = enable != 0;
+    if (!R.on)
+        R.clear();
+    return GK_OK;
 }
 
 int gk_probe_gather(const float *table, int64_t rows, int32_t row_floats, const int32_t *idx, int64_t count,

@@ -27,7 +27,7 @@ EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_siz
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
            "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall", "gk_probe_gather",
-           "gk_probe_fma"]
+           "gk_probe_fma", "gk_set_replay"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
              "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall"]
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
             L.gk_graph_recall.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, SZ, P]
             L.gk_probe_gather.argtypes = [P, I64, I32, P, I64, P, P]
             L.gk_probe_fma.argtypes = [P, I64, P]
+            L.gk_set_replay.argtypes = [I32]
             for name in X_ENTRIES:
                 getattr(L, name + "_bf16").argtypes = getattr(L, name).argtypes
             for name in EXPORTS:
@@ -343,6 +344,12 @@ def graph_recall(X, g_idx, queries, nn_idx=None, nn_dist=None, ws: Workspace | N
                                         _ptr(nn_idx), _ptr(nn_dist), _ptr(hits), ws.ptr, ws.nbytes,
                                         _stream(stream)))
     return hits, nn_idx, nn_dist
+
+
+def set_replay(enable: bool):
+    """Replay repeated build_knn_graph / kmeans_fit calls with equal arguments as one captured CUDA graph (see
+    gk_set_replay); off by default."""
+    _check(load().gk_set_replay(1 if enable else 0))
 
 
 PROBE_SINK = 9728  # floats of the probes' sink (GK_PROBE_SINK)
