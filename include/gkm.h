@@ -21,8 +21,10 @@
  *    stream) and is asynchronous unless the entry point says it synchronises.
  *  - Arguments are checked on the host before anything is enqueued; a bad
  *    argument returns GK_ERR_INVALID and gk_last_error() says why.  Errors the
- *    kernels find (a label or neighbour id out of range) are recorded in a
- *    status word inside `ws` and read back by gk_read_status().
+ *    kernels find (a label or neighbour id out of range: GK_ERR_INVALID; a
+ *    non-finite sample, seen by the update: GK_ERR_NUMERIC; a bounded wait
+ *    that ran out: GK_ERR_TIMEOUT) are recorded in a status word inside `ws`
+ *    and read back by gk_read_status().
  *  - ws/ws_bytes: caller-provided device scratch of at least
  *    gk_workspace_size(op, ...) bytes, 256-byte aligned.  A call that needs
  *    more returns GK_ERR_INVALID with the required size in the message.
@@ -158,6 +160,9 @@ GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  *            (Eq. 4), from the Eq. 2 identity sum ||x||^2 - sum_r D_r'D_r / n_r
  *   offsets, members  device int32[k + 1] / int32[n] or NULL: the CSR grouping
  *            (cluster r owns members[offsets[r] .. offsets[r+1]) )
+ * A NaN or infinite sample makes its cluster's distortion term non-finite:
+ * the update records GK_ERR_NUMERIC (detail: the cluster) in the status word.
+ * The same holds for every update inside gk_kmeans_fit and gk_build_knn_graph.
  */
 GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
                    int32_t *counts, double *sum_d2, int32_t *offsets, int32_t *members, void *ws, size_t ws_bytes,

@@ -423,7 +423,7 @@ static int update_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int6
     int32_t *mem = members ? members : L.grp.members;
     int32_t *cnt = counts ? counts : L.grp.counts;
     GK_CUDA(launch_group(labels, n, k, off, mem, cnt, L.grp.scratch, L.st, s));
-    GK_CUDA(launch_update(X, bf16, n, d, ld, off, mem, k, C, cnt, sum_d2, L.upd_scratch, s));
+    GK_CUDA(launch_update(X, bf16, n, d, ld, off, mem, k, C, cnt, sum_d2, L.upd_scratch, L.st, s));
     return GK_OK;
 }
 
@@ -519,7 +519,7 @@ static int update_from_groups_impl(const void *X, bool bf16, int64_t n, int64_t 
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_UPDATE, n, d, k);
-    GK_CUDA(launch_update(X, bf16, n, d, ld, offsets, members, k, C, counts, sum_d2, L.upd_scratch,
+    GK_CUDA(launch_update(X, bf16, n, d, ld, offsets, members, k, C, counts, sum_d2, L.upd_scratch, L.st,
                           (cudaStream_t)stream));
     return GK_OK;
 }
@@ -621,13 +621,13 @@ static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64
         GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)k * (size_t)d, s));
         GK_CUDA(launch_group(cur, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 0,
-                              L.upd_scratch, s));
+                              L.upd_scratch, L.st, s));
         for (int t = 0; t < iters; t++) {
             GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, kappa, C_out, k, cur, nxt, nullptr, L.elog + 1 + 2 * t,
                                   nullptr, L.asg_scratch, L.st, s, precision, L.grp.members));
             GK_CUDA(launch_group(nxt, n, k, L.grp.offsets, L.grp.members, cnt, L.grp.scratch, L.st, s));
             GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k, C_out, cnt, L.elog + 2 + 2 * t,
-                                  L.upd_scratch, s));
+                                  L.upd_scratch, L.st, s));
             int32_t *tmp = cur;
             cur = nxt;
             nxt = tmp;
@@ -699,14 +699,14 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
         GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)k0 * (size_t)d, s));
         GK_CUDA(launch_group(cur, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
         GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts, L.elog + 0,
-                              L.upd_scratch, s));
+                              L.upd_scratch, L.st, s));
         for (int t = 0; t < tau; t++) {
             // one k-means iteration at k0 on the current graph (Sec. 4.5: t = 1 per round)
             GK_CUDA(launch_assign(X, bf16, n, d, ld, g_idx, p->kappa, L.cent, k0, cur, nxt, nullptr, L.elog + 1 + 2 * t,
                                   nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
             GK_CUDA(launch_group(nxt, n, k0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
             GK_CUDA(launch_update(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, L.cent, L.grp.counts,
-                                  L.elog + 2 + 2 * t, L.upd_scratch, s));
+                                  L.elog + 2 + 2 * t, L.upd_scratch, L.st, s));
             // exhaustive pairs inside the clusters of the new partition
             GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
                                   g_dist, L.ref_scratch, L.st, s, p->precision));

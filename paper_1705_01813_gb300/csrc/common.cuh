@@ -205,7 +205,7 @@ cudaError_t launch_scan(const int32_t *in, int32_t *out, int64_t count, void *sc
 size_t update_scratch_bytes(int64_t n, int32_t k);
 cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
-                          void *scratch, cudaStream_t s);
+                          void *scratch, DevStatus *st, cudaStream_t s);
 
 size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d);
 // precision 0 and 1: FP32 candidate rows; 2: BF16 screening on the SIMT cores; 3: on the tensor cores over

@@ -121,7 +121,7 @@ extern "C" GK_API int gk_update_step_noalloc(const float *X, int64_t n, int64_t 
     // zeroes its own counters; everything else is overwritten before it is read)
     if ((e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s)) == cudaSuccess &&
         (e = launch_group(labels, n, k, off, mem, cnt, gscratch, st, s)) == cudaSuccess)
-        e = launch_update(X, false, n, d, ld, off, mem, k, C, cnt, sum_d2, uscratch, s);
+        e = launch_update(X, false, n, d, ld, off, mem, k, C, cnt, sum_d2, uscratch, st, s);
     if (e != cudaSuccess) {
         return report(GK_ERR_CUDA, "launch failed: %s", cudaGetErrorString(e));
     }

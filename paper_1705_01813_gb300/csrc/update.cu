@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
                                                           const int32_t *__restrict__ off,
                                                           const int32_t *__restrict__ mem, int k,
                                                           float *__restrict__ C, int32_t *__restrict__ counts,
-                                                          double *__restrict__ contrib)
+                                                          double *__restrict__ contrib, DevStatus *st)
 {
     using V = typename VecT<VEC>::T;
     static_assert(!PIPE || std::is_same_v<XT, float>, "the cp.async ring moves FP32 rows");
@@ -304,7 +304,10 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
             sq = df_add(sq, DF{s_sq[ww].x, s_sq[ww].y});
             dd = df_add(dd, DF{s_dd[ww].x, s_dd[ww].y});
         }
-        contrib[r] = df_to_double(sq) - df_to_double(dd) / (double)m;
+        const double cr = df_to_double(sq) - df_to_double(dd) / (double)m;
+        contrib[r] = cr;
+        if (!isfinite(cr))  // a non-finite sample in the cluster (Inf or NaN spreads into its sums)
+            flag_error(st, GK_ERR_NUMERIC, (unsigned)r);
     }
 }
 
@@ -331,7 +334,8 @@ size_t update_scratch_bytes(int64_t, int32_t k) { return ((size_t)k * sizeof(dou
 
 template <typename XT>
 static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *offsets, const int32_t *members,
-                            int32_t k, float *C, int32_t *counts, double *sum_d2, void *scratch, cudaStream_t s)
+                            int32_t k, float *C, int32_t *counts, double *sum_d2, void *scratch, DevStatus *st,
+                            cudaStream_t s)
 {
     double *contrib = static_cast<double *>(scratch);
     const bool vec4 = x_vec4(X, d, ld);
@@ -342,7 +346,7 @@ static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *o
     const int dd = (int)d;
     constexpr bool PIPE = std::is_same_v<XT, float>;  // FP32 rows stream through the cp.async ring
 #define GK_UPD(VEC, CPL, P) \
-    k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib)
+    k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib, st)
     if (vec4) {
         if (need <= 1)
             GK_UPD(4, 1, PIPE);
@@ -370,13 +374,13 @@ static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *o
 
 cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
-                          void *scratch, cudaStream_t s)
+                          void *scratch, DevStatus *st, cudaStream_t s)
 {
     (void)n;
     if (bf16)
         return update_t(static_cast<const __nv_bfloat16 *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch,
-                        s);
-    return update_t(static_cast<const float *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch, s);
+                        st, s);
+    return update_t(static_cast<const float *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch, st, s);
 }
 
 }  // namespace gkm

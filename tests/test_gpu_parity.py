@@ -394,3 +394,23 @@ def test_deterministic_and_resumable(G):
     lc, Cc, _, Ec = G.kmeans_fit(X, w.k, gi, 3, init_labels=lb.clone())
     assert torch.equal(la, lc) and torch.equal(Ca, Cc)
     assert Ea[-1] == Ec[-1]
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_non_finite_sample_is_reported(G, bad):
+    """A NaN or infinite sample is reported as GK_ERR_NUMERIC through the status word (update step and fit);
+    finite data reports nothing."""
+    X = _blobs(3000, 16, 10, 11)
+    Xd = _cuda(X)
+    k = 20
+    L = G.init_labels(3000, k, 4)
+    ws = G.workspace(G.workspace_size(G.GK_OP_FIT, 3000, 16, k, 8))
+    G.update_step(Xd, L, k, torch.zeros((k, 16), device="cuda"), ws=ws)
+    assert G.read_status(ws) == G.GK_OK
+    Xd[1234, 5] = bad
+    G.update_step(Xd, L, k, torch.zeros((k, 16), device="cuda"), ws=ws)
+    assert G.read_status(ws) == G.GK_ERR_NUMERIC
+    assert G.read_status(ws) == G.GK_OK  # reading clears it
+    gi, _ = G.init_graph(_cuda(X), 8, 2)
+    G.kmeans_fit(Xd, k, gi, 2, seed=3, want_log=False, ws=ws)
+    assert G.read_status(ws) == G.GK_ERR_NUMERIC

@@ -110,3 +110,24 @@ def test_arena_run_equals_allocating_run():
     stream.synchronize()
     assert torch.equal(la, lb) and torch.equal(Ca, Cb) and Ea == Eb
     assert arena.buf.numel() >= serve.job_bytes(first, p)
+
+
+@pytest.mark.gpu
+def test_injected_job_failure_is_raised_and_the_server_recovers(monkeypatch):
+    """A failure injected on the host into one job (an allocation failure) ends the run with that error; the
+    slots and the budget are released, so the same server serves the next run."""
+    specs = _specs([(10000, 64)] * 6)
+    real = serve.run_job
+
+    def flaky(s, p, device, stream, arena=None):
+        if s.jid == 3:
+            raise MemoryError("injected allocation failure")
+        return real(s, p, device, stream, arena)
+
+    monkeypatch.setattr(serve, "run_job", flaky)
+    srv = serve.Server(serve.ServeParams(slots=2))
+    with pytest.raises(MemoryError, match="injected"):
+        srv.run(specs, realtime=False)
+    monkeypatch.setattr(serve, "run_job", real)
+    res = srv.run(specs[:3], realtime=False)
+    assert [r.jid for r in res] == [0, 1, 2] and all(np.isfinite(r.distortion) for r in res)
