@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k
 // (FP32 or BF16, widened exactly) enter both passes unrounded: the bound covers
 // the centroids' rounding alone.
 template <int NV, typename XT>
-__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 3) k_assign_rows_bf8(
+__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV == 4 ? 4 : 3)) k_assign_rows_bf8(
     const XT *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
     const float *__restrict__ C, const __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ delta, int k,
     const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout, float *__restrict__ best_out, DevStatus *st)
