@@ -114,14 +114,14 @@ def test_full_size_sampled_parity(G, name, precision):
     kmax = max(k0, k)
     ws = G.workspace(max(G.workspace_size(G.GK_OP_FIT, n, d, kmax, kappa),
                          G.workspace_size(G.GK_OP_REFINE, n, d, kmax, kappa)))
-    # initial graph (c1)
+    # the random initial graph
     gi, gd = G.init_graph(X, kappa, w.seed, ws=ws)
     gi_h = gi[torch.from_numpy(rows).cuda().long()].cpu().numpy()
     R.need(np.concatenate([rows, gi_h.ravel()]))
     oi, od = O.init_graph_rows(R.h, kappa, w.seed, rows)
     P.check_graph(R.h, gi_h, gd[torch.from_numpy(rows).cuda().long()].cpu().numpy(), oi, od, rows=rows,
                   exact=exact)
-    # round 1 of the construction at k0: update (b), assignment (a), update, refinement (c2-c6)
+    # the construction's first round at k0: update, assignment, update, refinement
     la = G.init_labels(n, k0, w.seed)
     off, mem, cnt = G.group_by_label(la, k0, ws=ws)
     C0 = torch.zeros((k0, d), device="cuda")
