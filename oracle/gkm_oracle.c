@@ -17,6 +17,8 @@
  *   - cluster count k0 = floor(n / xi): Alg. 3 and Sec. 4.3
  *   - one k-means iteration per graph round: Sec. 4.5
  *   - average distortion: Eq. 4 (Sec. 5.1)
+ *   - two-means tree, the initial partition of Alg. 2: Alg. 1 (Sec. 3.2),
+ *     with its own readings T1-T6 stated where it is defined
  *
  * Readings where the paper is silent (all stated again where they are used):
  *   R1 the sample's own cluster is a candidate as well as its neighbours';
@@ -601,4 +603,179 @@ void or_brute_knn(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kapp
         if (got < kappa)
             or_sort_row(row, rd, got);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Alg. 1: two-means tree (Sec. 3.2)                                          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Starting from one cluster holding every sample, the largest cluster is
+ * taken out, bisected, the two halves are made equal in size, and both go
+ * back, until there are k clusters.  Readings where the paper is silent:
+ *   T1 a bisection is Lloyd's 2-means (the closest-centroid form used by the
+ *      rest of this path; the paper bisects with its boost form) for `iters`
+ *      iterations from two seed samples;
+ *   T2 the seeds are the two members with the smallest keys
+ *      (draw(seed ^ TREE, depth * 2^32 + id), id), depth = the cluster's
+ *      depth in the tree (the root has depth 0);
+ *   T3 each decision is taken in FP32, the precision of the CUDA path: the
+ *      squared distance sums fma(x_t - c_t, x_t - c_t, acc) over ascending t
+ *      in one FP32 accumulator; a member joins half u when d(x, c_u) <= d(x, c_v);
+ *      a centre is the FP32 rounding of the FP64 mean of its half (members in
+ *      ascending id); an empty half keeps its centre;
+ *   T4 equal sizes: the members are ordered by (d(x, c_u) - d(x, c_v) in FP32,
+ *      id) with the final centres; the first ceil(m / 2) form u, the rest v;
+ *   T5 among clusters of the largest size the shallowest is taken first, then
+ *      the one that comes first in the order of T6;
+ *   T6 the clusters are numbered left to right in the tree, u before v.
+ */
+static const uint64_t OR_TAG_TREE = 0x5452454500000000ULL; /* "TREE" */
+
+/* T3: FP32 squared distance, ascending coordinates, one fused multiply-add per step */
+static float or_d2_f32(const float *x, const float *c, int64_t d)
+{
+    float acc = 0.0f;
+    for (int64_t t = 0; t < d; t++) {
+        float e = x[t] - c[t];
+        acc = fmaf(e, e, acc);
+    }
+    return acc;
+}
+
+typedef struct {
+    float key;
+    int32_t id;
+} or_tree_key;
+
+static int or_tree_key_cmp(const void *a, const void *b)
+{
+    const or_tree_key *p = (const or_tree_key *)a, *q = (const or_tree_key *)b;
+    if (p->key != q->key)
+        return p->key < q->key ? -1 : 1;
+    return (p->id > q->id) - (p->id < q->id);
+}
+
+static int or_id_cmp(const void *a, const void *b)
+{
+    int32_t p = *(const int32_t *)a, q = *(const int32_t *)b;
+    return (p > q) - (p < q);
+}
+
+/* One bisection (T1-T4) of the members mem[0..m), m >= 2, in ascending id.
+ * On return mem[0..ceil(m/2)) is half u and the rest half v, each in ascending id. */
+static void or_bisect(const float *X, int64_t d, int64_t ld, int32_t *mem, int64_t m, int32_t depth,
+                      int32_t iters, uint64_t seed, float *cu, float *cv, double *su, double *sv, or_tree_key *keys)
+{
+    uint64_t key = seed ^ OR_TAG_TREE;
+    int64_t a = -1, b = -1;
+    uint64_t ha = 0, hb = 0;
+    for (int64_t p = 0; p < m; p++) { /* T2: ascending id, so an equal draw keeps the smaller id first */
+        uint64_t h = or_draw(key, ((uint64_t)(uint32_t)depth << 32) | (uint64_t)(uint32_t)mem[p]);
+        if (a < 0 || h < ha) {
+            b = a;
+            hb = ha;
+            a = p;
+            ha = h;
+        } else if (b < 0 || h < hb) {
+            b = p;
+            hb = h;
+        }
+    }
+    memcpy(cu, X + (int64_t)mem[a] * ld, sizeof(float) * (size_t)d);
+    memcpy(cv, X + (int64_t)mem[b] * ld, sizeof(float) * (size_t)d);
+    for (int32_t it = 0; it < iters; it++) { /* T1, T3 */
+        int64_t nu = 0, nv = 0;
+        memset(su, 0, sizeof(double) * (size_t)d);
+        memset(sv, 0, sizeof(double) * (size_t)d);
+        for (int64_t p = 0; p < m; p++) {
+            const float *x = X + (int64_t)mem[p] * ld;
+            double *s = or_d2_f32(x, cu, d) <= or_d2_f32(x, cv, d) ? su : sv;
+            for (int64_t t = 0; t < d; t++)
+                s[t] += (double)x[t];
+            if (s == su)
+                nu++;
+            else
+                nv++;
+        }
+        for (int64_t t = 0; t < d; t++) {
+            if (nu)
+                cu[t] = (float)(su[t] / (double)nu);
+            if (nv)
+                cv[t] = (float)(sv[t] / (double)nv);
+        }
+    }
+    for (int64_t p = 0; p < m; p++) { /* T4 */
+        const float *x = X + (int64_t)mem[p] * ld;
+        keys[p].key = or_d2_f32(x, cu, d) - or_d2_f32(x, cv, d);
+        keys[p].id = mem[p];
+    }
+    qsort(keys, (size_t)m, sizeof(or_tree_key), or_tree_key_cmp);
+    int64_t h = (m + 1) / 2;
+    for (int64_t p = 0; p < m; p++)
+        mem[p] = keys[p].id;
+    qsort(mem, (size_t)h, sizeof(int32_t), or_id_cmp);
+    qsort(mem + h, (size_t)(m - h), sizeof(int32_t), or_id_cmp);
+}
+
+/*
+ * Alg. 1: labels[i] in [0, k) for every sample, 1 <= k <= n.  A cluster is a
+ * range [off, off + m) of one permutation of the samples, so that "left to
+ * right" (T6) is the order of off.  Returns 0, or 1 for bad arguments or no memory.
+ */
+int or_two_means_tree(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters, uint64_t seed,
+                      int32_t *labels)
+{
+    if (k < 1 || (int64_t)k > n || iters < 0)
+        return 1;
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int64_t *size = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    int32_t *depth = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    float *cu = (float *)malloc(sizeof(float) * (size_t)d);
+    float *cv = (float *)malloc(sizeof(float) * (size_t)d);
+    double *su = (double *)malloc(sizeof(double) * (size_t)d);
+    double *sv = (double *)malloc(sizeof(double) * (size_t)d);
+    or_tree_key *keys = (or_tree_key *)malloc(sizeof(or_tree_key) * (size_t)n);
+    int rc = 1;
+    if (!perm || !off || !size || !depth || !cu || !cv || !su || !sv || !keys)
+        goto done;
+    for (int64_t i = 0; i < n; i++)
+        perm[i] = (int32_t)i;
+    off[0] = 0;
+    size[0] = n;
+    depth[0] = 0;
+    for (int32_t t = 1; t < k; t++) {
+        int32_t s = 0; /* pop: largest size, then smallest depth, then leftmost (T5) */
+        for (int32_t r = 1; r < t; r++)
+            if (size[r] > size[s] || (size[r] == size[s] && (depth[r] < depth[s] ||
+                                                            (depth[r] == depth[s] && off[r] < off[s]))))
+                s = r;
+        int64_t m = size[s], h = (m + 1) / 2;
+        or_bisect(X, d, ld, perm + off[s], m, depth[s], iters, seed, cu, cv, su, sv, keys);
+        off[t] = off[s] + h; /* v */
+        size[t] = m - h;
+        depth[t] = depth[s] + 1;
+        size[s] = h; /* u keeps the left range */
+        depth[s] += 1;
+    }
+    for (int32_t s = 0; s < k; s++) { /* T6: rank of off */
+        int32_t rank = 0;
+        for (int32_t r = 0; r < k; r++)
+            rank += off[r] < off[s];
+        for (int64_t p = off[s]; p < off[s] + size[s]; p++)
+            labels[perm[p]] = rank;
+    }
+    rc = 0;
+done:
+    free(perm);
+    free(off);
+    free(size);
+    free(depth);
+    free(cu);
+    free(cv);
+    free(su);
+    free(sv);
+    free(keys);
+    return rc;
 }

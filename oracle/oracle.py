@@ -15,6 +15,7 @@ Every function restates the paper (Deng & Zhao, arXiv 1705.01813):
   graph_refine(_rows)        Alg. 3 exhaustive pairs inside each cluster
   build_graph                Alg. 3 with one GK-means iteration per round (Sec. 4.5)
   brute_knn                  exact KNN graph by all pairs
+  two_means_tree             Alg. 1: k clusters by bisecting the largest cluster into equal halves
 
 Parity status: every function above is pinned by tests/test_oracle_pins.py
 (brute force, closed forms, invariants, published SplitMix64 outputs); the
@@ -66,6 +67,8 @@ def _bind(lib):
     lib.or_build_graph.argtypes = [P, I64, I64, I64, I32, I32, I32, I32, U64, ctypes.c_int, P, P, P, P]
     lib.or_build_graph.restype = ctypes.c_int
     lib.or_brute_knn.argtypes = [P, I64, I64, I64, I32, P, P]
+    lib.or_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P]
+    lib.or_two_means_tree.restype = ctypes.c_int
     return lib
 
 
@@ -240,6 +243,14 @@ class Oracle:
         gd = np.empty((n, kappa), np.float64)
         self._lib.or_brute_knn(_p(X), n, d, d, kappa, _p(gi), _p(gd))
         return gi, gd
+
+    def two_means_tree(self, X, k: int, iters: int = 2, seed: int = 0) -> np.ndarray:
+        """Alg. 1 (readings T1-T6 in gkm_oracle.c); labels in [0, k), numbered left to right in the tree."""
+        X, n, d = _x(X)
+        out = np.empty(n, np.int32)
+        if self._lib.or_two_means_tree(_p(X), n, d, d, k, iters, seed, _p(out)):
+            raise ValueError("two_means_tree: need 1 <= k <= n and iters >= 0")
+        return out
 
 
 _default = None

@@ -7,6 +7,10 @@ textbook routines (a complete graph makes the graph-guided assignment
 exhaustive Lloyd; k0 = 1 makes Alg. 3 an exact KNN search), closed forms (the
 Eq. 2 identity n E = sum ||x||^2 - I), and invariants (non-increasing
 distortion, sorted duplicate-free graph rows, result-neutral visited set).
+The two-means tree (Alg. 1) is pinned by the cluster sizes that n and k alone
+fix, by one-dimensional data (every cluster a run of consecutive values), by
+its root split against textbook 2-means followed by a median split, and by
+separated blobs.
 
 The second half plants plausible mistakes in a copy of the oracle's C source
 and shows that at least one pin fails for each.
@@ -22,6 +26,7 @@ from oracle import oracle as O
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 TAG_LABELS = 0x4C41424C00000000
 TAG_GRAPH = 0x4752415000000000
+TAG_TREE = 0x5452454500000000
 
 
 def _golden(name):
@@ -317,10 +322,85 @@ def check_group_csr(orc):
     assert np.array_equal(off, np.concatenate([[0], np.cumsum(np.bincount(L, minlength=53))]))
 
 
+# Alg. 1 (two-means tree).  Cluster sizes depend on n and k only: every split halves a cluster (u the larger
+# half), whole levels of the tree are split before the next one starts, and a partial last level splits its
+# largest clusters first, leftmost first among equal sizes.
+def _tree_sizes(n, k):
+    sizes = [n]
+    while 2 * len(sizes) <= k:
+        sizes = [h for m in sizes for h in ((m + 1) // 2, m // 2)]
+    picked = set(sorted(range(len(sizes)), key=lambda j: (-sizes[j], j))[:k - len(sizes)])
+    out = []
+    for j, m in enumerate(sizes):
+        out += [(m + 1) // 2, m // 2] if j in picked else [m]
+    return out
+
+
+def check_tree_sizes(orc):
+    g = np.random.default_rng(11)
+    for n, k in [(1000, 7), (10, 6), (10, 7), (37, 37), (64, 1), (100, 3), (1001, 12), (5, 4), (7, 5), (6, 5)]:
+        X = g.standard_normal((n, 3)).astype(np.float32)
+        L = orc.two_means_tree(X, k, iters=2, seed=n + k)
+        assert L.min() == 0 and L.max() == k - 1
+        assert np.bincount(L, minlength=k).tolist() == _tree_sizes(n, k), (n, k)
+
+
+def check_tree_1d(orc):
+    # d = 1: d(x, c_u) - d(x, c_v) is linear in x, so every bisection splits the sorted values at their middle and
+    # every cluster is a run of consecutive values (distinct integers: no rounding ties)
+    g = np.random.default_rng(12)
+    x = g.permutation(997).astype(np.float32)
+    for k, iters in [(2, 0), (5, 1), (16, 3), (50, 2)]:
+        L = orc.two_means_tree(_col(x), k, iters=iters, seed=k)
+        runs = L[np.argsort(x)]
+        assert (np.diff(runs) != 0).sum() == k - 1, (k, iters)
+
+
+def _tree_seeds(orc, ids, depth, seed):
+    h = [(orc.draw(seed ^ TAG_TREE, (depth << 32) | int(i)), int(i)) for i in ids]
+    (_, a), (_, b) = sorted(h)[:2]
+    return a, b
+
+
+def check_tree_root_split(orc):
+    # k = 2 is one bisection: Lloyd's 2-means (textbook numpy, FP64) from the seed pair, then the ceil(n/2) members
+    # with the smallest d(x, c_u) - d(x, c_v) (ties by id) form cluster 0
+    g = np.random.default_rng(13)
+    for n, d, iters, seed in [(301, 5, 0, 1), (301, 5, 1, 2), (400, 2, 3, 3), (257, 7, 4, 4)]:
+        X = (g.standard_normal((n, d)) + 3 * (g.random((n, 1)) < 0.3)).astype(np.float32)
+        a, b = _tree_seeds(orc, range(n), 0, seed)
+        C = X[[a, b]].astype(np.float64)
+        for _ in range(iters):
+            D = _np_d2(X, C)
+            C, _ = _np_means(X, (D[:, 1] < D[:, 0]).astype(np.int64), 2, C)
+        D = _np_d2(X, C)
+        order = np.lexsort((np.arange(n), D[:, 0] - D[:, 1]))
+        want = np.ones(n, np.int32)
+        want[order[:(n + 1) // 2]] = 0
+        assert np.array_equal(orc.two_means_tree(X, 2, iters=iters, seed=seed), want), (n, iters)
+        # k = 3 splits the larger (left) half of that same root split further
+        L3 = orc.two_means_tree(X, 3, iters=iters, seed=seed)
+        assert np.array_equal(L3 == 2, want == 1)
+
+
+def check_tree_blobs(orc):
+    # 8 tight, well separated blobs of 64 samples: the equal-size splits fall between blobs, one blob per cluster
+    g = np.random.default_rng(14)
+    c = g.uniform(-10, 10, (8, 4))
+    z = np.repeat(np.arange(8), 64)
+    X = (c[z] + 0.01 * g.standard_normal((512, 4))).astype(np.float32)
+    L = orc.two_means_tree(X, 8, iters=5, seed=5)
+    for b in range(8):
+        assert len(set(L[z == b].tolist())) == 1
+    assert len(set(L.tolist())) == 8
+
+
+
 CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_assign_complete_graph,
           check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
           check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
-          check_init_graph_rows, check_group_csr]
+          check_init_graph_rows, check_group_csr, check_tree_sizes, check_tree_1d, check_tree_root_split,
+          check_tree_blobs]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
@@ -371,6 +451,15 @@ MUTANTS = [
      "            int dup = 0;", check_init_graph),
     ("graph_seed_reused", "uint64_t key = seed ^ OR_TAG_GRAPH;", "uint64_t key = seed ^ OR_TAG_LABELS;",
      check_init_graph),
+    ("tree_half_floor", "int64_t h = (m + 1) / 2;\n    for (int64_t p = 0; p < m; p++)",
+     "int64_t h = m / 2;\n    for (int64_t p = 0; p < m; p++)", check_tree_root_split),
+    ("tree_key_sign", "keys[p].key = or_d2_f32(x, cu, d) - or_d2_f32(x, cv, d);",
+     "keys[p].key = or_d2_f32(x, cv, d) - or_d2_f32(x, cu, d);", check_tree_root_split),
+    ("tree_no_iterations", "it < iters; it++", "it < 0; it++", check_tree_root_split),
+    ("tree_depth_tiebreak_dropped", "(depth[r] < depth[s] ||", "(0 ||", check_tree_sizes),
+    ("tree_labels_by_creation", "labels[perm[p]] = rank;", "labels[perm[p]] = s;", check_tree_sizes),
+    ("tree_v_keeps_left_range", "off[t] = off[s] + h; /* v */", "off[t] = off[s]; off[s] += m - h; /* v */",
+     check_tree_1d),
 ]
 
 
