@@ -64,7 +64,8 @@ enum {
     GK_OP_REFINE = 2,
     GK_OP_FIT = 3,
     GK_OP_BUILD = 4,
-    GK_OP_RECALL = 5
+    GK_OP_RECALL = 5,
+    GK_OP_TREE = 6
 };
 
 /* Parameters of the graph construction (Alg. 3 and Sec. 4.4 of the paper). */
@@ -92,7 +93,7 @@ GK_API const char *gk_last_error(void);
 
 /*
  * Bytes of workspace the operation `op` (GK_OP_ASSIGN, _UPDATE, _REFINE, _FIT,
- * _RECALL) needs for these sizes; 0 for an unknown op.  k is the number of
+ * _RECALL, _TREE) needs for these sizes; 0 for an unknown op.  k is the number of
  * clusters (for GK_OP_RECALL: the number of queries m).  The graph
  * construction has its own query, gk_workspace_size_build().
  */
@@ -335,6 +336,38 @@ GK_API int gk_graph_recall(const float *X, int64_t n, int64_t d, int64_t ld, con
 GK_API int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
                                 int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,
                                 int64_t *hits, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Two-means tree (Alg. 1, Sec. 3.2): the initial partition of the paper's
+ * GK-means.  Starting from one cluster of all samples, the largest cluster is
+ * bisected and the halves are made equal in size until there are k clusters.
+ * One bisection of a cluster of m members: the two members with the smallest
+ * (SplitMix64 draw of (seed, depth, id), id) are the starting centres; `iters`
+ * Lloyd 2-means iterations follow (a member joins half u when its squared
+ * distance to c_u is at most that to c_v; a centre becomes the FP32 rounding of
+ * the FP64 mean of its half; an empty half keeps its centre); then the members
+ * are ordered by (d(x, c_u) - d(x, c_v), id) and the first ceil(m/2) form u,
+ * the rest v.  Distances and their difference are FP32, summed over ascending
+ * coordinates with one fused multiply-add per step.  Among clusters of the
+ * largest size the shallowest splits first, then the leftmost.  The sizes
+ * depend on n and k only: at depth L a cluster has floor(n / 2^L) or one more
+ * members.
+ *   X, n, d, ld    samples as in gk_assign_step (n >= 1)
+ *   k              clusters, 1 <= k <= n
+ *   iters          Lloyd iterations per bisection, 0 <= iters <= 64
+ *   seed           seed of the starting centres
+ *   labels         device int32[n] (out): each sample's cluster; clusters are
+ *                  numbered left to right in the tree (u before v)
+ *   ws             gk_workspace_size(GK_OP_TREE, n, d, k, 0) bytes
+ * Bad arguments return GK_ERR_INVALID; a non-finite distance sets
+ * GK_ERR_NUMERIC in the status word (the partition is still complete).
+ * Cost per depth: (iters + 1) reads of X plus 8 reads of one 64-bit key per
+ * sample; depths = floor(log2 k) + (1 if k is not a power of two).
+ */
+GK_API int gk_two_means_tree(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
+                             uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
+                                  uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Replay of repeated requests (off by default).  With replay on, a call of

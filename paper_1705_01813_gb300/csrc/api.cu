@@ -86,6 +86,7 @@ struct Layout {
     void *asg_scratch;
     void *ref_scratch;
     void *rec_scratch;
+    void *tree_scratch;
     int32_t *labels_a;
     int32_t *labels_b;
     float *cent;
@@ -124,6 +125,8 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     }
     if (op == GK_OP_RECALL)  // k: the number of queries
         L.rec_scratch = cv.take<char>(recall_scratch_bytes(n, k));
+    if (op == GK_OP_TREE)
+        L.tree_scratch = cv.take<char>(tree_scratch_bytes(n, d, k));
     L.bytes = cv.off;
     return L;
 }
@@ -297,7 +300,7 @@ const char *gk_last_error(void) { return g_err; }
 size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa)
 {
     (void)kappa;
-    if (op < GK_OP_ASSIGN || op > GK_OP_RECALL || op == GK_OP_BUILD || n < 0 || d < 0 || k < 0)
+    if (op < GK_OP_ASSIGN || op > GK_OP_TREE || op == GK_OP_BUILD || n < 0 || d < 0 || k < 0)
         return 0;
     return carve(nullptr, op, n, d, k).bytes;
 }
@@ -781,6 +784,38 @@ int gk_graph_recall_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, co
 {
     return graph_recall_impl(X, true, n, d, ld, g_idx, kappa, queries, m, nn_idx, nn_dist, hits, ws, ws_bytes,
                              stream);
+}
+
+static int two_means_tree_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k,
+                               int32_t iters, uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_x(X, bf16, n, d, ld, 1)))
+        return rc;
+    if (k < 1 || (int64_t)k > n)
+        return fail(GK_ERR_INVALID, "k = %d out of range [1, n = %lld]", k, (long long)n);
+    if (iters < 0 || iters > 64)
+        return fail(GK_ERR_INVALID, "iters = %d out of range [0, 64]", iters);
+    if (!labels)
+        return fail(GK_ERR_INVALID, "labels is NULL");
+    Layout L = carve(nullptr, GK_OP_TREE, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_TREE, n, d, k);
+    GK_CUDA(launch_tree(X, bf16, n, d, ld, k, iters, seed, labels, L.tree_scratch, L.st, (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_two_means_tree(const float *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters, uint64_t seed,
+                      int32_t *labels, void *ws, size_t ws_bytes, void *stream)
+{
+    return two_means_tree_impl(X, false, n, d, ld, k, iters, seed, labels, ws, ws_bytes, stream);
+}
+
+int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
+                           uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream)
+{
+    return two_means_tree_impl(X, true, n, d, ld, k, iters, seed, labels, ws, ws_bytes, stream);
 }
 
 int gk_set_replay(int enable)

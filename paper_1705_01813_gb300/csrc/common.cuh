@@ -181,6 +181,11 @@ cudaError_t launch_recall(const void *X, bool bf16, int64_t n, int64_t d, int64_
                           int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,
                           int64_t *hits, void *scratch, DevStatus *st, cudaStream_t s);
 
+// two-means tree, Alg. 1 (tree.cu): labels[n] in [0, k)
+size_t tree_scratch_bytes(int64_t n, int64_t d, int32_t k);
+cudaError_t launch_tree(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
+                        uint64_t seed, int32_t *labels, void *scratch, DevStatus *st, cudaStream_t s);
+
 // measurement probes (probes.cu)
 constexpr int PROBE_SINK = 152 * 8 * 8;  // floats the probes' sink must hold
 cudaError_t launch_probe_gather(const float *table, int64_t rows, int row_floats, const int32_t *idx, int64_t count,

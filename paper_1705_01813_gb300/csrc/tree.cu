@@ -1,0 +1,582 @@
+// Two-means tree (Alg. 1, Sec. 3.2): k clusters by repeated bisection of the
+// largest cluster into two halves of equal size.
+//
+// Every bisection halves a cluster (half u takes ceil(m/2) members), so the
+// sizes in the tree depend on n and k only: the clusters of depth L have
+// floor(n / 2^L) or that plus one members, whole depths are split before the
+// next depth starts (a child is never larger than a cluster left at its
+// parent's depth, and the shallower cluster goes first among equal sizes), and
+// when k is not a power of two the last depth splits its larger clusters
+// first, leftmost first.  The kernels therefore run one depth at a time over
+// all of its clusters at once.  A cluster is a range [off, off + m) of a
+// permutation of the samples; the permutation keeps each cluster's members in
+// ascending id, and cluster j of depth L has the range that the bits of j
+// (most significant first, 0 = u) pick out from the root.
+//
+// One bisection (each step over every cluster of the depth):
+//   seeds    the two members with the smallest (draw(seed ^ TREE, L * 2^32 + id), id)
+//   iters x  Lloyd 2-means: a member joins u when d(x, c_u) <= d(x, c_v), then
+//            each centre becomes the FP32 rounding of the FP64 mean of its half
+//            (an empty half keeps its centre)
+//   keys     (d(x, c_u) - d(x, c_v) in FP32, id) as one ordered 64-bit word
+//   select   the ceil(m/2)-th smallest key of the cluster (radix select)
+//   split    members with a key up to it form u, the rest v, each in the
+//            order they had (a stable partition: ascending id again)
+// Distances are FP32 with one accumulator over ascending coordinates and one
+// fused multiply-add per step, the decisions' precision.  Clusters are
+// numbered left to right at the end.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gkm {
+namespace {
+
+constexpr uint64_t TAG_TREE = 0x5452454500000000ull;  // "TREE"
+constexpr int TR_THREADS = 128;                       // pass kernel: one member per thread at a time
+constexpr int TR_STAGE = 32;                          // coordinates staged per round
+constexpr int TR_PITCH = TR_STAGE + 1;                // padded row of the stage (conflict-free column reads)
+constexpr int64_t TR_CHUNK = 2048;                    // members per pass block; larger clusters take several
+constexpr int SEL_THREADS = 256;
+
+// Range of cluster j of depth L: the bits of j from the most significant, 0 = u (the left ceil(m/2)).
+__device__ __forceinline__ void seg_geom(int64_t n, int L, int64_t j, int64_t &off, int64_t &m)
+{
+    off = 0;
+    m = n;
+    for (int b = L - 1; b >= 0; b--) {
+        const int64_t h = (m + 1) >> 1;
+        if ((j >> b) & 1) {
+            off += h;
+            m -= h;
+        } else {
+            m = h;
+        }
+    }
+}
+
+// Order-preserving map of an FP32 value to an unsigned word.
+__device__ __forceinline__ uint32_t f32_order(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ bool hk_less(uint64_t ha, int ia, uint64_t hb, int ib)
+{
+    return ha < hb || (ha == hb && ia < ib);
+}
+
+// (h1, i1) <= (h2, i2) are the two smallest keys seen; merge another such pair (g1, j1) <= (g2, j2).
+__device__ __forceinline__ void top2_merge(uint64_t &h1, int &i1, uint64_t &h2, int &i2, uint64_t g1, int j1,
+                                           uint64_t g2, int j2)
+{
+    if (hk_less(g1, j1, h1, i1)) {  // the other pair's first wins; the second is the smaller of h1 and g2
+        if (hk_less(h1, i1, g2, j2)) {
+            h2 = h1;
+            i2 = i1;
+        } else {
+            h2 = g2;
+            i2 = j2;
+        }
+        h1 = g1;
+        i1 = j1;
+    } else if (hk_less(g1, j1, h2, i2)) {
+        h2 = g1;
+        i2 = j1;
+    }
+}
+
+__global__ void k_tree_iota(int32_t *perm, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        perm[i] = (int32_t)i;
+}
+
+// Last, partial depth L: which of its S = 2^L clusters split (r of them, the larger first, then the leftmost) and
+// how many split before each.  One block.
+__global__ void __launch_bounds__(1024) k_tree_plan(int64_t n, int L, int64_t r, int32_t *spl, int32_t *pre)
+{
+    __shared__ int wsum[32];
+    const int64_t S = (int64_t)1 << L;
+    const int64_t a = n >> L;
+    const int64_t r1 = min(r, n - a * S);  // larger clusters (a + 1 members) split
+    const int64_t r0 = r - r1;             // clusters of a members split
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < S; t0 += blockDim.x) {
+        const int64_t j = t0 + threadIdx.x;
+        bool big = false;
+        if (j < S) {
+            int64_t off, m;
+            seg_geom(n, L, j, off, m);
+            big = m == a + 1;
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, big);
+        if (lane == 0)
+            wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+            before += w < warp ? wsum[w] : 0;
+            total += wsum[w];
+        }
+        const int64_t rank1 = carry + before + __popc(bal & lanemask_lt());
+        if (j < S) {
+            const int64_t rank0 = j - rank1;
+            spl[j] = big ? (rank1 < r1) : (rank0 < r0);
+            pre[j] = (int32_t)(min(rank1, r1) + min(rank0, r0));
+        }
+        carry += total;
+        __syncthreads();
+    }
+}
+
+// Seeds of every cluster of depth L that splits: the two members of smallest (draw, id); their rows become the
+// starting centres c_u, c_v (cen: 2 x d floats per cluster).
+template <typename XT>
+__global__ void __launch_bounds__(SEL_THREADS) k_tree_seed(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+                                                            int L, const int32_t *__restrict__ perm,
+                                                            const int32_t *__restrict__ spl, uint64_t seed,
+                                                            float *__restrict__ cen, DevStatus *st)
+{
+    __shared__ uint64_t sh[2][SEL_THREADS / 32];
+    __shared__ int si[2][SEL_THREADS / 32];
+    const int64_t j = blockIdx.x;
+    if (spl && !spl[j])
+        return;
+    int64_t off, m;
+    seg_geom(n, L, j, off, m);
+    const uint64_t key = seed ^ TAG_TREE;
+    uint64_t h1 = ~0ull, h2 = ~0ull;
+    int i1 = INT32_MAX, i2 = INT32_MAX;
+    for (int64_t p = off + threadIdx.x; p < off + m; p += blockDim.x) {
+        const int id = perm[p];
+        const uint64_t h = sm64_draw(key, ((uint64_t)(uint32_t)L << 32) | (uint32_t)id);
+        if (hk_less(h, id, h1, i1)) {
+            h2 = h1;
+            i2 = i1;
+            h1 = h;
+            i1 = id;
+        } else if (hk_less(h, id, h2, i2)) {
+            h2 = h;
+            i2 = id;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        top2_merge(h1, i1, h2, i2, __shfl_xor_sync(FULL_MASK, h1, o), __shfl_xor_sync(FULL_MASK, i1, o),
+                   __shfl_xor_sync(FULL_MASK, h2, o), __shfl_xor_sync(FULL_MASK, i2, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][warp] = h1;
+        sh[1][warp] = h2;
+        si[0][warp] = i1;
+        si[1][warp] = i2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        h1 = sh[0][0];
+        h2 = sh[1][0];
+        i1 = si[0][0];
+        i2 = si[1][0];
+        for (int w = 1; w < SEL_THREADS / 32; w++)
+            top2_merge(h1, i1, h2, i2, sh[0][w], si[0][w], sh[1][w], si[1][w]);
+        if ((unsigned)i1 >= (unsigned)n || (unsigned)i2 >= (unsigned)n) {
+            flag_error(st, GK_ERR_INVALID, (unsigned)j);
+            i1 = i2 = 0;
+        }
+        si[0][0] = i1;
+        si[1][0] = i2;
+    }
+    __syncthreads();
+    const XT *xa = X + (int64_t)si[0][0] * ld, *xb = X + (int64_t)si[1][0] * ld;
+    float *c = cen + j * 2 * (int64_t)d;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        c[t] = ldx(xa + t);
+        c[d + t] = ldx(xb + t);
+    }
+}
+
+
+// Chunk c of cluster j: C chunks of nearly equal length over the cluster's range.
+__device__ __forceinline__ void chunk_range(int64_t off, int64_t m, int64_t C, int64_t c, int64_t &b, int64_t &e)
+{
+    b = off + c * m / C;
+    e = off + (c + 1) * m / C;
+}
+
+// Dynamic shared memory of the pass kernel: FP64 sums of both halves, both centres, the staged rows, the block's
+// member ids and halves.
+__host__ __device__ constexpr size_t pass_smem(int d)
+{
+    return (size_t)16 * d + (size_t)8 * d + sizeof(float) * TR_THREADS * TR_PITCH + 2 * sizeof(int) * TR_THREADS;
+}
+
+// One pass over the members of every splitting cluster of depth L, C chunks per cluster (grid S x C).  Each thread
+// takes one member at a time: the rows of the block's 128 members are staged 32 coordinates at a time and each
+// thread sums its member's two distances in the canonical FP32 order.
+//   KEYS = false (a Lloyd iteration): the member joins u when d_u <= d_v and its row is added, in FP64 and in
+//     member order, to its half's sums; with one chunk the block writes the new centres, otherwise its sums and
+//     counts go to part (2d + 2 doubles per chunk) for k_tree_reduce.
+//   KEYS = true: keys[p] = (order(d_u - d_v) << 32) | id.
+template <typename XT, bool KEYS>
+__global__ void __launch_bounds__(TR_THREADS) k_tree_pass(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+                                                          int L, int64_t C, const int32_t *__restrict__ perm,
+                                                          const int32_t *__restrict__ spl, float *__restrict__ cen,
+                                                          double *__restrict__ part, uint64_t *__restrict__ keys,
+                                                          DevStatus *st)
+{
+    extern __shared__ __align__(16) unsigned char tr_smem[];
+    double *acc = reinterpret_cast<double *>(tr_smem);              // [2][d]
+    float *cuv = reinterpret_cast<float *>(acc + 2 * (size_t)d);    // [2][d]
+    float *stage = cuv + 2 * (size_t)d;                             // [TR_THREADS][TR_PITCH]
+    int *sid = reinterpret_cast<int *>(stage + TR_THREADS * TR_PITCH);
+    int *shalf = sid + TR_THREADS;
+    const int64_t j = blockIdx.x / C, c = blockIdx.x % C;
+    if (spl && !spl[j])
+        return;
+    int64_t off, m, b, e;
+    seg_geom(n, L, j, off, m);
+    chunk_range(off, m, C, c, b, e);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *cj = cen + j * 2 * (int64_t)d;
+    for (int t = tid; t < 2 * d; t += TR_THREADS) {
+        cuv[t] = cj[t];
+        if (!KEYS)
+            acc[t] = 0.0;
+    }
+    __syncthreads();
+    int64_t cnt_u = 0, cnt_v = 0;
+    for (int64_t g = b; g < e; g += TR_THREADS) {
+        const int64_t p = g + tid;
+        const bool valid = p < e;
+        int id = perm[valid ? p : b];
+        if ((unsigned)id >= (unsigned)n) {
+            flag_error(st, GK_ERR_INVALID, (unsigned)j);
+            id = 0;
+        }
+        sid[tid] = id;
+        float du = 0.f, dv = 0.f;
+        for (int t0 = 0; t0 < d; t0 += TR_STAGE) {
+            const int tw = min(TR_STAGE, d - t0);
+            __syncthreads();  // sid written; the previous round's stage consumed
+            for (int r = warp; r < TR_THREADS; r += TR_THREADS / 32)
+                if (lane < tw)
+                    stage[r * TR_PITCH + lane] = ldx(X + (int64_t)sid[r] * ld + t0 + lane);
+            __syncthreads();
+            const float *xs = stage + tid * TR_PITCH;
+            for (int tt = 0; tt < tw; tt++) {
+                const float x = xs[tt];
+                const float eu = __fsub_rn(x, cuv[t0 + tt]);
+                const float ev = __fsub_rn(x, cuv[d + t0 + tt]);
+                du = __fmaf_rn(eu, eu, du);
+                dv = __fmaf_rn(ev, ev, dv);
+            }
+        }
+        if (KEYS) {
+            if (valid) {
+                const float dk = __fsub_rn(du, dv);
+                if (!isfinite(dk))
+                    flag_error(st, GK_ERR_NUMERIC, (unsigned)id);
+                keys[p] = ((uint64_t)f32_order(dk) << 32) | (uint32_t)id;
+            }
+        } else {
+            shalf[tid] = valid ? (du <= dv ? 0 : 1) : 2;
+            __syncthreads();
+            const int gn = (int)min((int64_t)TR_THREADS, e - g);
+            for (int r = 0; r < gn; r++) {  // member order: ascending id within the cluster
+                const int h = shalf[r];
+                const XT *row = X + (int64_t)sid[r] * ld;
+                double *ah = acc + (size_t)h * d;
+                for (int t = tid; t < d; t += TR_THREADS)
+                    ah[t] += (double)ldx(row + t);
+                cnt_u += h == 0;
+                cnt_v += h == 1;
+            }
+        }
+        __syncthreads();  // sid and shalf are rewritten by the next group
+    }
+    if (KEYS)
+        return;
+    if (C == 1) {
+        for (int t = tid; t < d; t += TR_THREADS) {
+            if (cnt_u)
+                cj[t] = (float)(acc[t] / (double)cnt_u);
+            if (cnt_v)
+                cj[d + t] = (float)(acc[d + t] / (double)cnt_v);
+        }
+    } else {
+        double *pc = part + blockIdx.x * (2 * (int64_t)d + 2);
+        for (int t = tid; t < 2 * d; t += TR_THREADS)
+            pc[t] = acc[t];
+        if (tid == 0) {
+            pc[2 * d] = (double)cnt_u;
+            pc[2 * d + 1] = (double)cnt_v;
+        }
+    }
+}
+
+// Centres of the clusters split over several chunks: the chunks' FP64 sums added in chunk order.
+__global__ void __launch_bounds__(TR_THREADS) k_tree_reduce(int d, int64_t C, const int32_t *__restrict__ spl,
+                                                            float *__restrict__ cen, const double *__restrict__ part)
+{
+    const int64_t j = blockIdx.x;
+    if (spl && !spl[j])
+        return;
+    const double *p0 = part + j * C * (2 * (int64_t)d + 2);
+    double nu = 0.0, nv = 0.0;
+    for (int64_t c = 0; c < C; c++) {
+        nu += p0[c * (2 * (int64_t)d + 2) + 2 * d];
+        nv += p0[c * (2 * (int64_t)d + 2) + 2 * d + 1];
+    }
+    float *cj = cen + j * 2 * (int64_t)d;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        double su = 0.0, sv = 0.0;
+        for (int64_t c = 0; c < C; c++) {
+            su += p0[c * (2 * (int64_t)d + 2) + t];
+            sv += p0[c * (2 * (int64_t)d + 2) + d + t];
+        }
+        if (nu > 0.0)
+            cj[t] = (float)(su / nu);
+        if (nv > 0.0)
+            cj[d + t] = (float)(sv / nv);
+    }
+}
+
+
+// The ceil(m/2)-th smallest key of every splitting cluster (keys are distinct: they end in the member's id), by
+// radix selection over 8-bit digits from the most significant.
+__global__ void __launch_bounds__(SEL_THREADS) k_tree_select(int64_t n, int L, const int32_t *__restrict__ spl,
+                                                             const uint64_t *__restrict__ keys,
+                                                             uint64_t *__restrict__ thr)
+{
+    __shared__ unsigned hist[256];
+    __shared__ uint64_t s_prefix;
+    __shared__ int64_t s_rank;
+    const int64_t j = blockIdx.x;
+    if (spl && !spl[j])
+        return;
+    int64_t off, m;
+    seg_geom(n, L, j, off, m);
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint64_t prefix = 0, mask = 0;
+    int64_t rank = (m + 1) / 2 - 1;  // among the keys that match the prefix so far
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        hist[tid] = 0;  // SEL_THREADS == 256 bins
+        __syncthreads();
+        for (int64_t p = off + tid; p < off + m; p += SEL_THREADS) {
+            const uint64_t k = keys[p];
+            if ((k & mask) == prefix)
+                atomicAdd(&hist[(k >> shift) & 255], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {  // lane q holds bins 8q .. 8q + 7
+            unsigned own = 0;
+            for (int q = 0; q < 8; q++)
+                own += hist[8 * lane + q];
+            unsigned incl = own;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= o)
+                    incl += v;
+            }
+            const unsigned hit = __ballot_sync(FULL_MASK, (int64_t)incl > rank);
+            const int first = __ffs(hit) - 1;  // exists: the matching keys number more than rank
+            if (lane == first) {
+                int64_t base = incl - own;
+                int dg = 8 * lane;
+                for (int q = 0; q < 8; q++) {
+                    const unsigned h = hist[8 * lane + q];
+                    if (base + (int64_t)h > rank) {
+                        dg = 8 * lane + q;
+                        break;
+                    }
+                    base += h;
+                }
+                s_prefix = prefix | ((uint64_t)dg << shift);
+                s_rank = rank - base;
+            }
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        rank = s_rank;
+        mask |= (uint64_t)255 << shift;
+    }
+    if (tid == 0)
+        thr[j] = prefix;
+}
+
+// Stable partition of every cluster of depth L: the members with key <= thr[j] to the left ceil(m/2) positions,
+// the others after them, each in their previous order; clusters that do not split are copied.
+__global__ void __launch_bounds__(SEL_THREADS) k_tree_split(int64_t n, int L, const int32_t *__restrict__ spl,
+                                                            const uint64_t *__restrict__ keys,
+                                                            const uint64_t *__restrict__ thr,
+                                                            const int32_t *__restrict__ perm_in,
+                                                            int32_t *__restrict__ perm_out, DevStatus *st)
+{
+    __shared__ int wsum[SEL_THREADS / 32];
+    const int64_t j = blockIdx.x;
+    int64_t off, m;
+    seg_geom(n, L, j, off, m);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (spl && !spl[j]) {
+        for (int64_t p = off + tid; p < off + m; p += SEL_THREADS)
+            perm_out[p] = perm_in[p];
+        return;
+    }
+    const uint64_t T = thr[j];
+    const int64_t h = (m + 1) / 2;
+    int64_t bu = 0, bv = 0;
+    for (int64_t t0 = off; t0 < off + m; t0 += SEL_THREADS) {
+        const int64_t p = t0 + tid;
+        const bool valid = p < off + m;
+        const uint64_t k = valid ? keys[p] : 0;
+        const bool f = valid && k <= T;
+        const unsigned bal = __ballot_sync(FULL_MASK, f);
+        if (lane == 0)
+            wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < SEL_THREADS / 32; w++) {
+            before += w < warp ? wsum[w] : 0;
+            total += wsum[w];
+        }
+        const int64_t ru = before + __popc(bal & lanemask_lt());  // u members before this one in the tile
+        if (valid) {
+            const int64_t dst = f ? off + bu + ru : off + h + bv + (tid - ru);
+            if (dst >= off && dst < off + m)
+                perm_out[dst] = (int32_t)(uint32_t)k;
+            else
+                flag_error(st, GK_ERR_INVALID, (unsigned)j);
+        }
+        const int64_t nvalid = min((int64_t)SEL_THREADS, off + m - t0);
+        bu += total;
+        bv += nvalid - total;
+        __syncthreads();
+    }
+}
+
+// Labels: clusters numbered left to right.  Cluster j of the last depth L keeps number j + pre[j], or, when it
+// splits (spl[j]), its halves take j + pre[j] and j + pre[j] + 1.  With spl == NULL the depth is complete.
+__global__ void __launch_bounds__(TR_THREADS) k_tree_label(int64_t n, int L, const int32_t *__restrict__ spl,
+                                                           const int32_t *__restrict__ pre,
+                                                           const int32_t *__restrict__ perm,
+                                                           int32_t *__restrict__ labels)
+{
+    const int64_t j = blockIdx.x;
+    int64_t off, m;
+    seg_geom(n, L, j, off, m);
+    const bool split = spl && spl[j];
+    const int32_t base = (int32_t)j + (spl ? pre[j] : 0);
+    const int64_t h = (m + 1) / 2;
+    for (int64_t p = off + threadIdx.x; p < off + m; p += blockDim.x) {
+        const int id = perm[p];
+        if ((unsigned)id < (unsigned)n)
+            labels[id] = base + (split && p - off >= h ? 1 : 0);
+    }
+}
+
+
+// Depth L such that 2^L <= k < 2^(L + 1): depths 0 .. L - 1 split completely, depth L splits k - 2^L clusters.
+int tree_depth(int32_t k)
+{
+    int L = 0;
+    while (((int64_t)2 << L) <= (int64_t)k)
+        L++;
+    return L;
+}
+
+// Pass blocks per cluster at depth L: clusters of up to TR_CHUNK members take one.
+int64_t tree_chunks(int64_t n, int L)
+{
+    const int64_t a1 = (n >> L) + 1;
+    return std::max<int64_t>(1, (a1 + TR_CHUNK - 1) / TR_CHUNK);
+}
+
+struct TreeBufs {
+    int32_t *perm_a, *perm_b, *spl, *pre;
+    uint64_t *keys, *thr;
+    float *cen;
+    double *part;
+    size_t bytes;
+};
+
+TreeBufs tree_carve(void *scratch, int64_t n, int64_t d, int32_t k)
+{
+    Carver cv{static_cast<char *>(scratch), 0, 0};
+    const int Lf = tree_depth(k);
+    const int64_t S = (int64_t)1 << Lf;
+    int64_t part = 0;  // doubles
+    for (int L = 0; L <= Lf; L++) {
+        const int64_t C = tree_chunks(n, L);
+        if (C > 1)
+            part = std::max(part, ((int64_t)1 << L) * C * (2 * d + 2));
+    }
+    TreeBufs B{};
+    B.perm_a = cv.take<int32_t>((size_t)n);
+    B.perm_b = cv.take<int32_t>((size_t)n);
+    B.keys = cv.take<uint64_t>((size_t)n);
+    B.cen = cv.take<float>((size_t)S * 2 * (size_t)d);
+    B.thr = cv.take<uint64_t>((size_t)S);
+    B.spl = cv.take<int32_t>((size_t)S);
+    B.pre = cv.take<int32_t>((size_t)S);
+    B.part = cv.take<double>((size_t)std::max<int64_t>(part, 1));
+    B.bytes = cv.off;
+    return B;
+}
+
+template <typename XT>
+cudaError_t tree_run(const XT *X, int64_t n, int d, int64_t ld, int32_t k, int32_t iters, uint64_t seed,
+                     int32_t *labels, const TreeBufs &B, DevStatus *st, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = set_max_smem((const void *)k_tree_pass<XT, false>, (int)pass_smem(MAX_D))) != cudaSuccess ||
+        (e = set_max_smem((const void *)k_tree_pass<XT, true>, (int)pass_smem(MAX_D))) != cudaSuccess)
+        return e;
+    const size_t smem = pass_smem(d);
+    k_tree_iota<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(B.perm_a, n);
+    const int Lf = tree_depth(k);
+    const int64_t r = (int64_t)k - ((int64_t)1 << Lf);
+    int32_t *cur = B.perm_a, *nxt = B.perm_b;
+    for (int L = 0; L <= Lf; L++) {
+        const int32_t *spl = nullptr;
+        const int64_t S = (int64_t)1 << L;
+        if (L == Lf) {
+            if (r == 0)
+                break;
+            k_tree_plan<<<1, 1024, 0, s>>>(n, L, r, B.spl, B.pre);
+            spl = B.spl;
+        }
+        const int64_t C = tree_chunks(n, L);
+        k_tree_seed<XT><<<(unsigned)S, SEL_THREADS, 0, s>>>(X, n, d, ld, L, cur, spl, seed, B.cen, st);
+        for (int it = 0; it < iters; it++) {
+            k_tree_pass<XT, false><<<(unsigned)(S * C), TR_THREADS, smem, s>>>(X, n, d, ld, L, C, cur, spl, B.cen,
+                                                                                B.part, B.keys, st);
+            if (C > 1)
+                k_tree_reduce<<<(unsigned)S, TR_THREADS, 0, s>>>(d, C, spl, B.cen, B.part);
+        }
+        k_tree_pass<XT, true><<<(unsigned)(S * C), TR_THREADS, smem, s>>>(X, n, d, ld, L, C, cur, spl, B.cen, B.part,
+                                                                           B.keys, st);
+        k_tree_select<<<(unsigned)S, SEL_THREADS, 0, s>>>(n, L, spl, B.keys, B.thr);
+        k_tree_split<<<(unsigned)S, SEL_THREADS, 0, s>>>(n, L, spl, B.keys, B.thr, cur, nxt, st);
+        std::swap(cur, nxt);
+    }
+    k_tree_label<<<(unsigned)((int64_t)1 << Lf), TR_THREADS, 0, s>>>(n, Lf, r > 0 ? B.spl : nullptr, B.pre, cur,
+                                                                      labels);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tree_scratch_bytes(int64_t n, int64_t d, int32_t k) { return tree_carve(nullptr, n, d, k).bytes; }
+
+cudaError_t launch_tree(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
+                        uint64_t seed, int32_t *labels, void *scratch, DevStatus *st, cudaStream_t s)
+{
+    const TreeBufs B = tree_carve(scratch, n, d, k);
+    if (bf16)
+        return tree_run(static_cast<const __nv_bfloat16 *>(X), n, (int)d, ld, k, iters, seed, labels, B, st, s);
+    return tree_run(static_cast<const float *>(X), n, (int)d, ld, k, iters, seed, labels, B, st, s);
+}
+
+}  // namespace gkm

@@ -20,17 +20,18 @@ _lib = None
 _lock = threading.Lock()
 
 GK_OK, GK_ERR_INVALID, GK_ERR_CUDA, GK_ERR_NOMEM, GK_ERR_TIMEOUT, GK_ERR_NUMERIC = range(6)
-GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL = range(6)
+GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL, GK_OP_TREE = range(7)
 
 #: every entry point the header declares (checked by the tests)
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
            "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall", "gk_probe_gather",
-           "gk_probe_fma", "gk_set_replay"]
+           "gk_probe_fma", "gk_set_replay", "gk_two_means_tree"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
-             "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall"]
+             "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall",
+             "gk_two_means_tree"]
 EXPORTS += [name + "_bf16" for name in X_ENTRIES]
 
 
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
             L.gk_probe_gather.argtypes = [P, I64, I32, P, I64, P, P]
             L.gk_probe_fma.argtypes = [P, I64, P]
             L.gk_set_replay.argtypes = [I32]
+            L.gk_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P, P, SZ, P]
             for name in X_ENTRIES:
                 getattr(L, name + "_bf16").argtypes = getattr(L, name).argtypes
             for name in EXPORTS:
@@ -344,6 +346,19 @@ def graph_recall(X, g_idx, queries, nn_idx=None, nn_dist=None, ws: Workspace | N
                                         _ptr(nn_idx), _ptr(nn_dist), _ptr(hits), ws.ptr, ws.nbytes,
                                         _stream(stream)))
     return hits, nn_idx, nn_dist
+
+
+def two_means_tree(X, k: int, iters: int = 2, seed: int = 0, out: torch.Tensor | None = None,
+                   ws: Workspace | None = None, stream=None) -> torch.Tensor:
+    """Alg. 1: labels int32[n] of k clusters made by bisecting the largest cluster into equal halves (see
+    gk_two_means_tree); clusters are numbered left to right in the tree."""
+    n, d, ld = _x(X)
+    out = torch.empty(n, dtype=torch.int32, device=X.device) if out is None else out
+    _dev(out, torch.int32, "out")
+    ws = ws or workspace(workspace_size(GK_OP_TREE, n, d, k), X.device)
+    _check(_entry("gk_two_means_tree", X)(_ptr(X), n, d, ld, k, iters, seed, _ptr(out), ws.ptr, ws.nbytes,
+                                          _stream(stream)))
+    return out
 
 
 def set_replay(enable: bool):

@@ -99,4 +99,16 @@ def test_argument_errors(lib):
     assert lib.gk_graph_recall(P, 10, 4, 4, P, 2, P, 5, None, None, None, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
     assert gkm.workspace_size(gkm.GK_OP_RECALL, 1000, 4, 100) > gkm.workspace_size(gkm.GK_OP_RECALL, 1000, 4, 1)
     assert gkm.workspace_size(gkm.GK_OP_BUILD, 1000, 4, 100) == 0  # the build has its own query
+    assert lib.gk_two_means_tree(P, 10, 4, 4, 0, 2, 0, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert b"k = 0" in lib.gk_last_error()
+    assert lib.gk_two_means_tree(P, 10, 4, 4, 11, 2, 0, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_two_means_tree(P, 10, 4, 4, 3, -1, 0, P, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert b"iters" in lib.gk_last_error()
+    assert lib.gk_two_means_tree(P, 10, 4, 4, 3, 2, 0, None, ws, 1 << 20, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_two_means_tree(P, 10, 4, 4, 3, 2, 0, P, ws, 16, None) == gkm.GK_ERR_INVALID
+    assert b"too small" in lib.gk_last_error()
+    # the tree's scratch: two permutations and the keys (16 bytes per sample) plus 2 d floats per cluster of the
+    # deepest complete depth
+    big, small = (gkm.workspace_size(gkm.GK_OP_TREE, 100000, 64, k) for k in (4096, 2))
+    assert big - small >= (4096 - 2) * 2 * 64 * 4 and small >= 100000 * 16
     assert lib.gk_read_status(None, None) == gkm.GK_ERR_INVALID
