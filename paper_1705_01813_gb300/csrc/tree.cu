@@ -34,10 +34,11 @@ namespace {
 
 constexpr uint64_t TAG_TREE = 0x5452454500000000ull;  // "TREE"
 constexpr int TR_THREADS = 128;                       // pass kernel: one member per thread at a time
-constexpr int TR_STAGE = 32;                          // coordinates staged per round
+constexpr int TR_STAGE = 64;                          // coordinates staged per round
 constexpr int TR_PITCH = TR_STAGE + 1;                // padded row of the stage (conflict-free column reads)
 constexpr int64_t TR_CHUNK = 512;                     // members per chunk block; larger clusters take several
 constexpr int SEL_THREADS = 256;
+static_assert(TR_THREADS == 2 * TR_STAGE, "the sums give each thread one coordinate of one half");
 
 // Range of cluster j of depth L: the bits of j from the most significant, 0 = u (the left ceil(m/2)).
 __device__ __forceinline__ void seg_geom(int64_t n, int L, int64_t j, int64_t &off, int64_t &m)
@@ -60,6 +61,27 @@ __device__ __forceinline__ uint32_t f32_order(float f)
 {
     const uint32_t u = __float_as_uint(f);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// FP32 -> FP64 widening on the integer pipe (every binary32 value is a binary64 value: the fields are moved, a
+// subnormal is normalised).  GB300's FP64 pipe is narrow, and the Lloyd sums keep it busy with their additions.
+__device__ __forceinline__ double widen(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    uint64_t bits;
+    if (e == 0xFFu) {
+        bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
+    } else if (e != 0) {
+        bits = sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29);
+    } else if (m == 0) {
+        bits = sign;
+    } else {
+        const int p = 31 - __clz(m);  // leading one of the subnormal's m * 2^-149
+        bits = sign | ((uint64_t)(p + 874) << 52) | ((uint64_t)(m ^ (1u << p)) << (52 - p));
+    }
+    return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ bool hk_less(uint64_t ha, int ia, uint64_t hb, int ib)
@@ -254,6 +276,19 @@ __global__ void __launch_bounds__(TR_THREADS) k_tree_seed_final(const XT *__rest
     }
 }
 
+// The coordinates t0 .. t0 + tw - 1 of the block's TR_THREADS member rows into the stage: warp w loads rows
+// w, w + 4, ..., one coalesced load per 32 coordinates.
+template <typename XT>
+__device__ __forceinline__ void stage_rows(const XT *__restrict__ X, int64_t ld, const int *sid, int t0, int tw,
+                                           float *stage, int warp, int lane)
+{
+    for (int r = warp; r < TR_THREADS; r += TR_THREADS / 32) {
+        const XT *row = X + (int64_t)sid[r] * ld + t0;
+        for (int q = lane; q < tw; q += 32)
+            stage[r * TR_PITCH + q] = ldx(row + q);
+    }
+}
+
 // Dynamic shared memory of the pass kernel: FP64 sums of both halves, both centres, the staged rows, the block's
 // member ids and halves.
 __host__ __device__ constexpr size_t pass_smem(int d)
@@ -262,7 +297,7 @@ __host__ __device__ constexpr size_t pass_smem(int d)
 }
 
 // One pass over the members of every splitting cluster of depth L, C chunks per cluster (grid S x C).  Each thread
-// takes one member at a time: the rows of the block's 128 members are staged 32 coordinates at a time and each
+// takes one member at a time: the rows of the block's 128 members are staged 64 coordinates at a time and each
 // thread sums its member's two distances in the canonical FP32 order.
 //   KEYS = false (a Lloyd iteration): the member joins u when d_u <= d_v and its row is added, in FP64 and in
 //     member order, to its half's sums (a second staging of the group's rows; one thread per coordinate and
@@ -310,9 +345,7 @@ __global__ void __launch_bounds__(TR_THREADS) k_tree_pass(const XT *__restrict__
         for (int t0 = 0; t0 < d; t0 += TR_STAGE) {
             const int tw = min(TR_STAGE, d - t0);
             __syncthreads();  // sid written; the previous round's stage consumed
-            for (int r = warp; r < TR_THREADS; r += TR_THREADS / 32)
-                if (lane < tw)
-                    stage[r * TR_PITCH + lane] = ldx(X + (int64_t)sid[r] * ld + t0 + lane);
+            stage_rows(X, ld, sid, t0, tw, stage, warp, lane);
             __syncthreads();
             const float *xs = stage + tid * TR_PITCH;
             for (int tt = 0; tt < tw; tt++) {
@@ -331,24 +364,22 @@ __global__ void __launch_bounds__(TR_THREADS) k_tree_pass(const XT *__restrict__
                 keys[p] = ((uint64_t)f32_order(dk) << 32) | (uint32_t)id;
             }
         } else {
-            // the group's rows are staged again, 32 coordinates at a time; thread (c, h) of the first 64 adds
-            // coordinate c of the members of half h in member order (ascending id within the cluster)
+            // the group's rows are staged again, 64 coordinates at a time; thread (c, h) adds coordinate c of the
+            // members of half h in member order (ascending id within the cluster)
             shalf[tid] = valid ? (du <= dv ? 0 : 1) : 2;
             const int gn = (int)min((int64_t)TR_THREADS, e - g);
             for (int t0 = 0; t0 < d; t0 += TR_STAGE) {
                 const int tw = min(TR_STAGE, d - t0);
                 __syncthreads();  // shalf written; the previous round's stage consumed
-                for (int r = warp; r < TR_THREADS; r += TR_THREADS / 32)
-                    if (lane < tw)
-                        stage[r * TR_PITCH + lane] = ldx(X + (int64_t)sid[r] * ld + t0 + lane);
+                stage_rows(X, ld, sid, t0, tw, stage, warp, lane);
                 __syncthreads();
-                if (tid < 2 * TR_STAGE && lane < tw) {
-                    const int hh = tid >> 5;
-                    double sum = acc[(size_t)hh * d + t0 + lane];
+                const int hh = tid / TR_STAGE, cc = tid % TR_STAGE;  // warps 0-1: half u, 2-3: half v
+                if (cc < tw) {
+                    double sum = acc[(size_t)hh * d + t0 + cc];
                     for (int r = 0; r < gn; r++)
                         if (shalf[r] == hh)
-                            sum += (double)stage[r * TR_PITCH + lane];
-                    acc[(size_t)hh * d + t0 + lane] = sum;
+                            sum += widen(stage[r * TR_PITCH + cc]);
+                    acc[(size_t)hh * d + t0 + cc] = sum;
                 }
             }
             for (int r = 0; r < gn; r++) {
