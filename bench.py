@@ -73,6 +73,8 @@ def parse():
                          "the same results).  Default: chosen by the autotuner (tune.py) on the workload's own "
                          "graph and labels after the first warm-up step")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-tree", action="store_true",
+                    help="skip the timing of the two-means tree (Alg. 1) at the workload's n, d and k")
     ap.add_argument("--no-ceilings", action="store_true",
                     help="skip the probe kernels that measure the L2 / HBM gather and FP32 FMA ceilings")
     ap.add_argument("--no-replay", action="store_true",
@@ -538,6 +540,8 @@ def run_gpu(args):
               "note": "top-1 recall of the graph after the step's construction (tau rounds), exact neighbours by "
                       "brute force on seeded random queries"}
 
+    tree = None if args.no_tree else time_tree(gkm, torch, path.X, w)
+
     hbm, bf16, peak_src = load_peaks()
     ceilings = None
     if not args.no_ceilings:
@@ -595,6 +599,7 @@ def run_gpu(args):
         "measured_ceilings": ceilings,
         "precision_tuning": tuning,
         "graph_recall_top1": recall,
+        "two_means_tree": tree,
         "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
@@ -775,6 +780,34 @@ def run_reference(args):
            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
+
+
+def time_tree(gkm, torch, X, w, iters=2, reps=3):
+    """The two-means tree (Alg. 1) at the workload's n, d and k: mean time of `reps` calls after one warm-up,
+    and the rate of its reads of X ((iters + 1) passes per complete depth).  It is the paper's initial
+    partition; the timed step starts from seeded random labels, as the workloads state."""
+    n, d = X.shape
+    ws = gkm.workspace(gkm.workspace_size(gkm.GK_OP_TREE, n, d, w.k), X.device)
+    lab = torch.empty(n, dtype=torch.int32, device=X.device)
+    gkm.two_means_tree(X, w.k, iters=iters, seed=w.seed, out=lab, ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.current_stream()
+    e0.record(s)
+    for _ in range(reps):
+        gkm.two_means_tree(X, w.k, iters=iters, seed=w.seed, out=lab, ws=ws)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    depths = max(w.k, 1).bit_length() - 1  # complete depths; a partial one follows when k is not a power of two
+    x_bytes = depths * (iters + 1) * n * d * X.element_size()
+    status = gkm.read_status(ws)
+    del ws
+    return {"ms": round(ms, 3), "k": w.k, "iters": iters, "complete_depths": depths,
+            "x_read_GB": round(x_bytes / 1e9, 3), "x_read_GBs": round(x_bytes / ms / 1e6, 1),
+            "device_status": status,
+            "note": "Alg. 1 initial partition (equal halves, Lloyd 2-means per bisection, FP64 sums); "
+                    "not part of the timed step"}
 
 
 def main():
