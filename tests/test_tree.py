@@ -2,7 +2,7 @@
 
 Both sides take every decision in FP32 with the same definition of the squared distance (one accumulator over
 ascending coordinates, one fused multiply-add per step) and round each centre from an FP64 mean, so the labels
-agree exactly.  (A cluster of more than 2048 members has its FP64 sums added in chunks on the GPU; a centre could
+agree exactly.  (A cluster of more than 512 members has its FP64 sums added in chunks on the GPU; a centre could
 then differ in its last FP32 bit only if its FP64 mean lay within 1e-16 of a rounding boundary.)"""
 import numpy as np
 import pytest
@@ -43,7 +43,7 @@ def _run(G, X, k, iters, seed):
 
 
 @pytest.mark.parametrize("n,d,k,iters,kind", [
-    (20000, 32, 200, 2, "gauss"),    # several pass blocks per cluster at depths 0-3; a partial last depth
+    (20000, 32, 200, 2, "gauss"),    # several chunk blocks per cluster at depths 0-5; a partial last depth
     (12000, 48, 128, 3, "int"),      # k a power of two; integer data (exact sums)
     (5003, 7, 1000, 1, "gauss"),     # narrow rows, small clusters
     (3000, 130, 37, 0, "gauss"),     # seeds only; a ragged stage of coordinates
@@ -92,7 +92,7 @@ def test_tree_row_stride(G):
 
 
 def test_tree_full_size(G):
-    # SIFT-shaped size (10^6 x 128, k = 10^4, pass blocks of 2048 members over the large clusters): the sizes that
+    # SIFT-shaped size (10^6 x 128, k = 10^4, chunk blocks of 512 members over the large clusters): the sizes that
     # n and k fix, a repeat bit for bit, and the two depths below the root against the oracle run at k = 4 (each
     # of the 10^4 clusters lies inside one of its 4)
     n, d, k = 1_000_000, 128, 10_000
