@@ -338,7 +338,8 @@ def _tree_sizes(n, k):
 
 def check_tree_sizes(orc):
     g = np.random.default_rng(11)
-    for n, k in [(1000, 7), (10, 6), (10, 7), (37, 37), (64, 1), (100, 3), (1001, 12), (5, 4), (7, 5), (6, 5)]:
+    sweep = [(int(n), int(g.integers(1, n + 1))) for n in g.integers(2, 300, 60)]
+    for n, k in [(1000, 7), (10, 6), (10, 7), (37, 37), (64, 1), (100, 3), (1001, 12), (5, 4), (7, 5), (6, 5)] + sweep:
         X = g.standard_normal((n, 3)).astype(np.float32)
         L = orc.two_means_tree(X, k, iters=2, seed=n + k)
         assert L.min() == 0 and L.max() == k - 1
