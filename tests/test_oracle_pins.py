@@ -429,6 +429,11 @@ def test_paper_trends():
     Ln, Cn = _np_lloyd(X, L0, k, 5)
     En = ((X.astype(np.float64) - Cn[Ln]) ** 2).sum(1).mean()
     assert Ef[-1] <= En * 1.05
+    # the two-means tree as the initial partition (Alg. 2 starts from it, Sec. 4.2): the fit on the graph ends
+    # lower than from random labels
+    Lt = orc.two_means_tree(X, k, iters=2, seed=3)
+    _, _, _, Et = orc.fit(X, k, gi, 5, Lt)
+    assert Et[-1] < Ef[-1]
 
 
 # ------------------------------------------------------- planted mistakes ----
