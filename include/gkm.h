@@ -22,15 +22,17 @@
  *  - Arguments are checked on the host before anything is enqueued; a bad
  *    argument returns GK_ERR_INVALID and gk_last_error() says why.  Errors the
  *    kernels find (a label or neighbour id out of range: GK_ERR_INVALID; a
- *    non-finite sample, seen by the update: GK_ERR_NUMERIC; a bounded wait
- *    that ran out: GK_ERR_TIMEOUT) are recorded in a status word inside `ws`
- *    and read back by gk_read_status().
+ *    non-finite sample, seen by the update or the two-means tree:
+ *    GK_ERR_NUMERIC; a bounded wait that ran out: GK_ERR_TIMEOUT) are recorded
+ *    in a status word inside `ws` and read back by gk_read_status().
  *  - ws/ws_bytes: caller-provided device scratch of at least
  *    gk_workspace_size(op, ...) bytes, 256-byte aligned.  A call that needs
  *    more returns GK_ERR_INVALID with the required size in the message.
  *    Concurrent calls must use distinct workspaces.
- *  - The library is reentrant across streams; its only global state is the
- *    thread-local message returned by gk_last_error().
+ *  - The library is reentrant across streams.  Its global state: the
+ *    thread-local message returned by gk_last_error(), each kernel's shared
+ *    memory limit (set once per device), and, with gk_set_replay on, the
+ *    cache of captured request graphs.
  */
 #ifndef GKM_H
 #define GKM_H
