@@ -35,7 +35,16 @@
  *      OOPSLA 2014) used as a counter-based function, see or_draw().
  *
  * Inputs X are read as stored (FP32) and widened to FP64 element by element.
+ *
+ * Threads: with OpenMP the loops over samples, runs and clusters are shared
+ * out over the host cores; every result is written by one thread and every sum
+ * keeps its order (a cluster's members in ascending id, the distortion over
+ * samples in index order), so the results do not depend on the thread count
+ * (or_set_threads; tests check it).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -68,6 +77,19 @@ uint64_t or_splitmix64_next(uint64_t *state)
 uint64_t or_draw(uint64_t key, uint64_t counter)
 {
     return or_mix(key + (counter + 1) * OR_GAMMA);
+}
+
+/* Threads of the parallel loops (1: single-threaded); returns the count in effect. */
+int or_set_threads(int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0)
+        omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
 }
 
 /* squared Euclidean distance in FP64, inputs widened exactly */
@@ -136,6 +158,7 @@ void or_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32_t kap
                    int32_t *g_idx, double *g_dist)
 {
     uint64_t key = seed ^ OR_TAG_GRAPH;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; i++) {
         int32_t *row = g_idx + i * kappa;
         double *rd = g_dist + i * kappa;
@@ -210,8 +233,11 @@ static void or_assign_impl(const float *X, int64_t n, int64_t d, int64_t ld, con
                            const double *C, int32_t k, const int32_t *L_in, int32_t *L_out, double *best,
                            int32_t *uniq, const int64_t *rows, int64_t nrows, int all_clusters)
 {
-    int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kappa + 1));
     int64_t cnt = rows ? nrows : n;
+#pragma omp parallel
+    {
+    int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kappa + 1));
+#pragma omp for schedule(dynamic, 256)
     for (int64_t r = 0; r < cnt; r++) {
         int64_t i = rows ? rows[r] : r;
         const float *x = X + i * ld;
@@ -256,6 +282,7 @@ static void or_assign_impl(const float *X, int64_t n, int64_t d, int64_t ld, con
             uniq[rows ? r : i] = u;
     }
     free(Q);
+    }
 }
 
 void or_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *G, int32_t kappa,
@@ -265,12 +292,62 @@ void or_assign(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *
     or_assign_impl(X, n, d, ld, G, kappa, C, k, L_in, L_out, best, uniq, rows, nrows, 0);
 }
 
+/*
+ * Near-tie report of the assignment (for the checks of this oracle against
+ * arithmetic of another precision; not a step of the paper).  For each sample
+ * i: Q as the assignment forms it (own label, then the kappa neighbours'
+ * labels, each cluster once), the two smallest squared distances
+ * d1 <= d2 to distinct clusters of Q, and margin[i] = (d2 - d1) / d1:
+ * 0 for an exact tie, +inf when Q holds one cluster or d1 = 0 < d2.  A
+ * sample whose margin is below a tolerance may go to either of its two best
+ * clusters under arithmetic that rounds differently.
+ */
+void or_assign_margin(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *G, int32_t kappa,
+                      const double *C, const int32_t *L_in, double *margin)
+{
+    int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kappa + 1));
+    for (int64_t i = 0; i < n; i++) {
+        int32_t u = 0;
+        Q[u++] = L_in[i];
+        for (int32_t j = 0; j < kappa; j++) {
+            int32_t lab = L_in[G[i * kappa + j]];
+            int seen = 0;
+            for (int32_t q = 0; q < u; q++)
+                if (Q[q] == lab) {
+                    seen = 1;
+                    break;
+                }
+            if (!seen)
+                Q[u++] = lab;
+        }
+        double d1 = INFINITY, d2 = INFINITY;
+        for (int32_t q = 0; q < u; q++) {
+            double dd = or_d2_fd(X + i * ld, C + (int64_t)Q[q] * d, d);
+            if (dd < d1) {
+                d2 = d1;
+                d1 = dd;
+            } else if (dd < d2) {
+                d2 = dd;
+            }
+        }
+        if (u < 2)
+            margin[i] = INFINITY;
+        else if (d1 > 0.0)
+            margin[i] = (d2 - d1) / d1;
+        else
+            margin[i] = d2 > 0.0 ? INFINITY : 0.0;
+    }
+    free(Q);
+}
+
 /* Exhaustive Lloyd assignment: every one of the k centroids is a candidate. */
 void or_assign_exhaustive(const float *X, int64_t n, int64_t d, int64_t ld, const double *C, int32_t k,
                           int32_t *L_out, double *best)
 {
     or_assign_impl(X, n, d, ld, NULL, 0, C, k, NULL, L_out, best, NULL, NULL, 0, 1);
 }
+
+static void or_group(const int32_t *L, int64_t n, int32_t k, int64_t *offsets, int32_t *members);
 
 /* ------------------------------------------------------------------------- */
 /* Update: centroid = mean of members (Sec. 1), D_r of Eq. 2, E of Eq. 4     */
@@ -286,13 +363,17 @@ void or_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *
                int64_t *counts, double *E, double *I_out)
 {
     double *D = (double *)calloc((size_t)k * (size_t)d, sizeof(double));
-    for (int32_t r = 0; r < k; r++)
-        counts[r] = 0;
-    for (int64_t i = 0; i < n; i++) {
-        int32_t r = L[i];
-        counts[r]++;
-        for (int64_t t = 0; t < d; t++)
-            D[(int64_t)r * d + t] += (double)X[i * ld + t];
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)k + 1));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    or_group(L, n, k, off, mem); /* S_r: the members of cluster r in ascending sample order */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int32_t r = 0; r < k; r++) {
+        counts[r] = off[r + 1] - off[r];
+        for (int64_t p = off[r]; p < off[r + 1]; p++) {
+            const int64_t i = mem[p];
+            for (int64_t t = 0; t < d; t++)
+                D[(int64_t)r * d + t] += (double)X[i * ld + t];
+        }
     }
     double I = 0.0;
     for (int32_t r = 0; r < k; r++) {
@@ -306,14 +387,22 @@ void or_update(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *
         I += dd / (double)counts[r];
     }
     if (E) {
+        /* the terms in parallel, their sum in index order */
+        double *term = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; i++)
+            term[i] = or_d2_fd(X + i * ld, C + (int64_t)L[i] * d, d);
         double s = 0.0;
         for (int64_t i = 0; i < n; i++)
-            s += or_d2_fd(X + i * ld, C + (int64_t)L[i] * d, d);
+            s += term[i];
         *E = s / (double)n;
+        free(term);
     }
     if (I_out)
         *I_out = I;
     free(D);
+    free(off);
+    free(mem);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -432,6 +521,8 @@ static void or_refine_impl(const float *X, int64_t n, int64_t d, int64_t ld, con
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)k + 1));
     int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     or_group(L, n, k, off, mem);
+    /* a row belongs to one run of one cluster, so clusters may run in parallel (the shared visited set may not) */
+#pragma omp parallel for schedule(dynamic, 4) if (visited == NULL)
     for (int32_t r = 0; r < k; r++) {
         int64_t m = off[r + 1] - off[r];
         if (m < 2)

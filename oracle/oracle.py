@@ -10,6 +10,7 @@ Every function restates the paper (Deng & Zhao, arXiv 1705.01813):
   init_labels / init_graph   seeded start (Alg. 3 starts from random neighbour lists; SplitMix64 by its published definition)
   assign                     Alg. 2 with the closest-centroid rule of Sec. 4.2 (GK-means^-)
   assign_exhaustive          Lloyd's assignment after Eq. 1 (every centroid a candidate)
+  assign_margin              near-tie report: relative gap of each sample's two best candidate clusters
   update                     centroid = mean (Sec. 1), Eq. 2 objective I, Eq. 4 distortion
   fit                        C0 = update(L0), then T x {assign, update}
   graph_refine(_rows)        Alg. 3 exhaustive pairs inside each cluster
@@ -50,6 +51,8 @@ def _bind(lib):
     I64 = ctypes.c_int64
     I32 = ctypes.c_int32
     U64 = ctypes.c_uint64
+    lib.or_set_threads.argtypes = [ctypes.c_int]
+    lib.or_set_threads.restype = ctypes.c_int
     lib.or_splitmix64_next.argtypes = [P]
     lib.or_splitmix64_next.restype = U64
     lib.or_draw.argtypes = [U64, U64]
@@ -59,6 +62,7 @@ def _bind(lib):
     lib.or_init_graph_rows.argtypes = [P, I64, I64, I64, I32, U64, P, I64, P, P]
     lib.or_assign.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, P, I64]
     lib.or_assign_exhaustive.argtypes = [P, I64, I64, I64, P, I32, P, P]
+    lib.or_assign_margin.argtypes = [P, I64, I64, I64, P, I32, P, P, P]
     lib.or_update.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
     lib.or_fit.argtypes = [P, I64, I64, I64, I32, P, I32, I32, P, P, P, P, P]
     lib.or_graph_refine.argtypes = [P, I64, I64, I64, P, I32, I32, I32, P, P]
@@ -78,7 +82,7 @@ def compile_source(src: str, lib_path: str) -> str:
     os.makedirs(os.path.dirname(lib_path), exist_ok=True)
     tmp = lib_path + f".{os.getpid()}.tmp"
     subprocess.check_call(
-        ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", "-std=c11",
+        ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC", "-std=c11",
          "-o", tmp, src, "-lm"])
     os.replace(tmp, lib_path)
     return lib_path
@@ -117,6 +121,11 @@ class Oracle:
 
     def __init__(self, lib_path: str | None = None):
         self._lib = _load() if lib_path is None else _bind(ctypes.CDLL(lib_path))
+
+    def set_threads(self, threads: int) -> int:
+        """Host threads of the oracle's parallel loops (1: single-threaded; 0: leave as is); returns the count in
+        effect.  Results do not depend on it."""
+        return int(self._lib.or_set_threads(int(threads)))
 
     def splitmix64_stream(self, seed: int, count: int) -> list[int]:
         """The published SplitMix64 sequence: ``count`` outputs from state ``seed``."""
@@ -167,6 +176,17 @@ class Oracle:
         self._lib.or_assign(_p(X), n, d, d, _p(G), kappa, _p(C), k, _p(L), _p(Lo), _p(best), _p(uniq),
                           _p(r), 0 if r is None else m)
         return Lo, best, uniq
+
+    def assign_margin(self, X, G, C, labels):
+        """Near-tie report of the assignment: per sample (d2 - d1) / d1 over its two best distinct candidate
+        clusters (0: exact tie, inf: one candidate cluster or d1 = 0 < d2)."""
+        X, n, d = _x(X)
+        G = _i32(G)
+        C = _f64(C)
+        L = _i32(labels)
+        out = np.empty(n, np.float64)
+        self._lib.or_assign_margin(_p(X), n, d, d, _p(G), G.shape[1], _p(C), _p(L), _p(out))
+        return out
 
     def assign_exhaustive(self, X, C):
         X, n, d = _x(X)

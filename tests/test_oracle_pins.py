@@ -5,7 +5,8 @@ mathematics: hand-worked examples (tests/golden/worked_1d.json), the published
 SplitMix64 outputs (tests/golden/splitmix64.json), special cases that reduce to
 textbook routines (a complete graph makes the graph-guided assignment
 exhaustive Lloyd; k0 = 1 makes Alg. 3 an exact KNN search), closed forms (the
-Eq. 2 identity n E = sum ||x||^2 - I), and invariants (non-increasing
+Eq. 2 identity n E = sum ||x||^2 - I; the assignment's near-tie margin as the
+gap of the two smallest entries of the full distance table), and invariants (non-increasing
 distortion, sorted duplicate-free graph rows, result-neutral visited set).
 The two-means tree (Alg. 1) is pinned by the cluster sizes that n and k alone
 fix, by one-dimensional data (every cluster a run of consecutive values), by
@@ -124,6 +125,32 @@ def check_worked_assign(orc):
         c = g[case]
         Lo, _, _ = orc.assign(_col(c["x"]), c["graph"], c["centroids"], c["labels"])
         assert Lo.tolist() == c["labels_after_assign"], case
+
+
+def check_worked_margin(orc):
+    g = _golden("worked_1d.json")["margin"]
+    m = orc.assign_margin(_col(g["x"]), np.asarray(g["graph"]), np.asarray(g["centroids"]), np.asarray(g["labels"]))
+    assert np.array_equal(m, np.asarray([float(v) for v in g["margin"]]))
+
+
+def check_margin_complete_graph(orc):
+    """With every cluster a candidate, the margin is the relative gap of the two smallest entries of each row of
+    the full distance table (numpy sort): the textbook second-nearest-centroid gap."""
+    g = np.random.default_rng(21)
+    n, d, k = 300, 5, 7
+    X = g.standard_normal((n, d)).astype(np.float32)
+    L = g.permutation(np.arange(n) % k).astype(np.int32)
+    members = [np.nonzero(L == r)[0][0] for r in range(k)]
+    G = np.tile(np.asarray(members, np.int32), (n, 1))
+    C = g.standard_normal((k, d))
+    D = np.sort(_np_d2(X, C), axis=1)
+    want = (D[:, 1] - D[:, 0]) / D[:, 0]
+    got = orc.assign_margin(X, G, C, L)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    # and a sample's assigned cluster is its nearest one whenever its margin is positive
+    Lo, _, _ = orc.assign(X, G, C, L)
+    pos = got > 0
+    assert np.array_equal(Lo[pos], np.argmin(_np_d2(X, C), 1)[pos])
 
 
 def check_assign_complete_graph(orc):
@@ -397,7 +424,8 @@ def check_tree_blobs(orc):
 
 
 
-CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_assign_complete_graph,
+CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_worked_margin,
+          check_margin_complete_graph, check_assign_complete_graph,
           check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
           check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
           check_init_graph_rows, check_group_csr, check_tree_sizes, check_tree_1d, check_tree_root_split,
@@ -461,6 +489,8 @@ MUTANTS = [
      "int64_t h = m / 2;\n    for (int64_t p = 0; p < m; p++)", check_tree_root_split),
     ("tree_key_sign", "keys[p].key = or_d2_f32(x, cu, d) - or_d2_f32(x, cv, d);",
      "keys[p].key = or_d2_f32(x, cv, d) - or_d2_f32(x, cu, d);", check_tree_root_split),
+    ("margin_runner_up_not_shifted", "                d2 = d1;\n                d1 = dd;", "                d1 = dd;",
+     check_worked_margin),
     ("tree_no_iterations", "it < iters; it++", "it < 0; it++", check_tree_root_split),
     ("tree_depth_tiebreak_dropped", "(depth[r] < depth[s] ||", "(0 ||", check_tree_sizes),
     ("tree_labels_by_creation", "labels[perm[p]] = rank;", "labels[perm[p]] = s;", check_tree_sizes),
@@ -478,3 +508,22 @@ def test_planted_mistake_is_caught(tmp_path, name, find, repl, check):
     lib = O.compile_source(str(mut), str(tmp_path / f"lib{name}.so"))
     with pytest.raises(AssertionError):
         check(O.Oracle(lib))
+
+
+def test_oracle_results_do_not_depend_on_threads():
+    """The oracle's parallel loops write each result from one thread and keep every sum's order, so one thread and
+    several give the same bits (graph, labels, centroids, distortion logs)."""
+    from paper_1705_01813_gb300 import datagen
+    X = datagen.sift_like(4000, 64, 40, seed=2)
+    orc = O.default()
+    before = orc.set_threads(0)
+    out = {}
+    try:
+        for th in (1, 4):
+            orc.set_threads(th)
+            gi, gd, L, E = orc.build_graph(X, 20, xi=50, tau=4, seed=3)
+            Lf, C, cnt, Ef = orc.fit(X, 40, gi, 5, orc.init_labels(4000, 40, 4))
+            out[th] = (gi, gd, L, E, Lf, C, cnt, Ef)
+    finally:
+        orc.set_threads(before)
+    assert all(np.array_equal(a, b) for a, b in zip(out[1], out[4]))
