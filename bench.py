@@ -2,7 +2,8 @@
 """Benchmark of the graph-guided k-means hot path on GB300.
 
 One step is one pass of the whole path over the workload (default: the
-SIFT-shaped n = 1,000,000, d = 128, k = 10,000, kappa = 50 workload):
+deep-feature-shaped n = 10,000,000, d = 512 (BF16 samples), k = 1,000,000,
+kappa = 40 workload, the paper's largest scale; --workload picks another):
   graph construction (Alg. 3): random graph and labels at k0 = n / xi, then
       tau = 10 rounds of {graph-guided assignment, grouping, update, pair refinement}
   graph-guided k-means (Alg. 2, closest-centroid rule): seeded labels at k,
@@ -44,10 +45,13 @@ if ROOT not in sys.path:
 
 from paper_1705_01813_gb300 import datagen  # noqa: E402
 
-METRIC = "assign-step samples/s and fit time vs plain FP32; serve jobs/s, p50/p99"
-DEFAULT_WORKLOAD = "sift_n1000000_d128_k10000"
+# `value` is samples per second of the whole path (one graph construction + one fit per step); the assign-step
+# rate, the fit time against the plain FP32 path and the serving figures of the headline metric ride beside it
+METRIC = ("whole-path samples/s (graph construction + fit per step); beside it: assign-step samples/s, fit time vs "
+          "plain FP32, serve jobs/s and p50/p99")
+DEFAULT_WORKLOAD = "deep_n10000000_d512_k1000000"
 CPU_SAMPLE = 100_000        # cpu_baseline: oracle on the first 100k samples at d = 128 (about 10-30 s)
-REF_SAMPLE = 40_000         # --impl reference: oracle per step on the first 40k samples at d = 128
+REF_SAMPLE = 100_000        # --impl reference: oracle per step on the first 100k samples at d = 128 (fewer for wider rows)
 
 
 L2_BYTES = 129 << 20  # GB300 L2
@@ -83,8 +87,12 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step launched op by op only (default: also captured into a CUDA graph, whose "
                          "replay time is the value)")
-    ap.add_argument("--serve-jobs", type=int, default=96,
-                    help="jobs of the serving stream to run after the step measurement (0: none)")
+    ap.add_argument("--serve-jobs", type=int, default=512,
+                    help="jobs of the serving stream to run after the step measurement (0: none; 512: all)")
+    ap.add_argument("--compare-steps", type=int, default=2,
+                    help="steps of the plain FP32 path timed for the comparison (after one untimed step)")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="requests timed through the one-call API with host buffers (at most --steps)")
     ap.add_argument("--traffic-from", metavar="CSV",
                     help="no GPU run: read an ncu --csv log with dram__bytes_read.sum, dram__bytes_write.sum and "
                          "gpu__time_duration.sum of this workload's kernels and record the per-launch means in "
@@ -253,13 +261,13 @@ class Path:
 
 
 def _radix_passes(k):
-    bits = max(0, int(k - 1).bit_length())
-    return (bits + 7) // 8
+    # 8-bit passes over the sort keys 0..k (k: the key of an out-of-range label)
+    return (int(k).bit_length() + 7) // 8
 
 
 def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
-    grp = lambda k: 1 + 3 + (5 * _radix_passes(k) if _radix_passes(k) else 1)  # noqa: E731
+    grp = lambda k: 1 + 3 + 5 * _radix_passes(k)  # noqa: E731
     upd = 2
     # assign (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core
     # tiles, SIMT leftovers (3)
@@ -463,11 +471,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, args.compare_steps)):
             path.step()
         b.record()
         torch.cuda.synchronize()
-        fp32_ms = a.elapsed_time(b) / max(1, args.steps)
+        fp32_ms = a.elapsed_time(b) / max(1, args.compare_steps)
         path.precision = args.precision
 
     # e2e through the one-call API with host buffers
@@ -504,10 +512,11 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
         with torch.cuda.stream(e2e_stream):
             a.record()
-            for _ in range(args.steps):
+            for _ in range(e2e_steps):
                 e2e_step()
             b.record()
         torch.cuda.synchronize()
@@ -516,10 +525,10 @@ def run_gpu(args):
         t_e2e = max(a.elapsed_time(b) / 1e3, wall)
         if world > 1:
             t_e2e = reduce_max(t_e2e, dist, "cuda")
-        e2e = {"value": whole_job_rate(w.n, args.steps, world, t_e2e), "unit": "samples/s",
+        e2e = {"value": whole_job_rate(w.n, e2e_steps, world, t_e2e), "unit": "samples/s",
                "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
                "d2h_bytes_per_step": int(lab_h.numel() * 4 + C_h.numel() * 4),
-               "ms_per_step": 1e3 * t_e2e / args.steps, "replay": not args.no_replay}
+               "ms_per_step": 1e3 * t_e2e / e2e_steps, "steps": e2e_steps, "replay": not args.no_replay}
 
     if rank != 0:
         if world > 1:
@@ -545,8 +554,8 @@ def run_gpu(args):
     hbm, bf16, peak_src = load_peaks()
     ceilings = None
     if not args.no_ceilings:
-        from paper_1705_01813_gb300 import peaks
-        ceilings = peaks.measure()
+        from benchlib import probes
+        ceilings = probes.measure()
     # dominant kernel: the call with the largest share of the step
     totals = {t: sum(v) for t, v in per_tag.items()}
     dom = max(totals, key=totals.get)
@@ -733,23 +742,52 @@ def gpu_vs_oracle(w, X, k, ora, precision):
             "precision": precision}
 
 
+def host_cpu():
+    """(model name, logical CPUs) of the host from lscpu, with os.cpu_count() as the fallback."""
+    model, cpus = None, os.cpu_count()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and model is None:
+                model = v.strip()
+            elif k.strip() == "CPU(s)":
+                cpus = int(v.strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return model, cpus
+
+
+def time_oracle(O, w, X, threads):
+    """The oracle's graph construction + fit on X with `threads` host threads: (seconds, k, results)."""
+    used = O.set_threads(threads)
+    t0 = time.perf_counter()
+    out = _oracle_step(O, w, X)
+    return time.perf_counter() - t0, used, out
+
+
 def cpu_baseline(w, Xh, precision=1):
-    """The oracle on the leading rows Xh (FP32; BF16 samples widened) of the workload's samples, timed; then
-    the library on the same rows against the oracle's results."""
+    """The oracle on the leading rows Xh (FP32; BF16 samples widened) of the workload's samples, timed on all host
+    cores and on one (the paper's own setting); then the library on the same rows against the oracle's
+    results."""
     from oracle import oracle as O
     ns = Xh.shape[0]
     X = np.ascontiguousarray(Xh, dtype=np.float32)
-    t0 = time.perf_counter()
-    k, gi_o, L_o, E_o = _oracle_step(O, w, X)
-    dt = time.perf_counter() - t0
-    return {"value": ns / dt, "unit": "samples/s", "cores": 1, "kind": "oracle",
+    model, cpus = host_cpu()
+    dt_all, used_all, (k, gi_o, L_o, E_o) = time_oracle(O, w, X, cpus or 1)
+    dt_one, _, out_one = time_oracle(O, w, X, 1)
+    O.set_threads(cpus or 1)
+    assert np.array_equal(out_one[2], L_o)  # the thread count does not change the oracle's results
+    return {"value": ns / dt_all, "unit": "samples/s", "cores": used_all, "kind": "oracle",
             "sample": f"first {ns} samples of {w.name}, k = {k}, k0 = {ns // w.xi}, kappa = {w.kappa}, "
-                      f"tau = {w.tau}, iters = {w.iters}: graph construction + fit, single-threaded FP64 C",
-            "seconds": dt,
+                      f"tau = {w.tau}, iters = {w.iters}: graph construction + fit, FP64 C with OpenMP",
+            "seconds": dt_all, "cpu_model": model, "host_cpus": cpus,
+            "single_thread": {"value": ns / dt_one, "unit": "samples/s", "cores": 1, "seconds": dt_one},
             "gpu_vs_oracle": gpu_vs_oracle(w, X, k, (gi_o, L_o, E_o), precision)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (all host cores, OpenMP) on a bounded sample of the workload per step."""
     rank, _, world = dist_env()
     if rank != 0:
         return
@@ -762,6 +800,8 @@ def run_reference(args):
         X = datagen.gist_like(ns, w.d, w.extra.get("n_latent", 1000), w.seed)
     else:
         X = np.ascontiguousarray(w.data()[:ns])
+    model, cpus = host_cpu()
+    used = O.set_threads(cpus or 1)
     for _ in range(args.warmup):
         _oracle_step(O, w, X)
     t0 = time.perf_counter()
@@ -772,12 +812,13 @@ def run_reference(args):
     drawn = (f"{ns} samples of the {w.name} recipe drawn on the host" if w.storage == "bf16" or
              w.name.startswith("gist") else f"first {ns} samples of {w.name}")
     sample = (f"{drawn} per step, k = {k}, k0 = {ns // w.xi}: graph construction + fit, "
-              f"single-threaded FP64 C oracle")
+              f"FP64 C oracle with OpenMP on {used} threads ({model})")
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "kappa": w.kappa, "sample_n": ns},
-           "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": "samples/s", "cores": used, "kind": "oracle", "sample": sample,
+                            "cpu_model": model},
            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
 

@@ -1,0 +1,99 @@
+"""Workloads behind the kernel-counter summaries in profiles/: each case makes the library calls that its
+summary's ncu command captured, on seeded synthetic samples generated here.
+
+    python -m benchlib.cases deep_assign_bf16
+    python -m benchlib.cases gist_refine
+    python -m benchlib.cases tree --n 1000000 --d 128 --k 10000 --iters 2 --calls 2
+
+deep_assign_bf16  10^6 x 512 BF16 deep-feature-shaped samples (200,000 vMF directions, kappa_vMF = 50, seed 11);
+                  graph construction with kappa = 40, tau = 1 at precision 2, then two fit iterations at
+                  k = 100,000 (a centroid table far larger than L2, like the 10^7 x 512 workload's).
+gist_refine       3 x 10^5 x 960 GIST-shaped samples (1,000 latent centres, seed 5); graph construction with
+                  kappa = 50, xi = 50, tau = 3 at precision 1 (the FP32 tile refinement at this width).
+tree              the two-means tree (Alg. 1) on N(0, 1) samples drawn by a CUDA torch generator seeded with
+                  --data-seed (BF16 with --bf16); --calls tree calls on one workspace, the first a warm-up;
+                  prints one JSON line with the mean time of the other calls and the device status word.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def deep_assign_bf16(argv):
+    import torch
+
+    from paper_1705_01813_gb300 import datagen, gkm
+    X = datagen.deep_like_device(1_000_000, 512, 200_000, 50.0, seed=11, device="cuda")
+    torch.cuda.empty_cache()
+    gi, _, _, _ = gkm.build_knn_graph(X, 40, xi=50, tau=1, seed=1, precision=2)
+    _, _, _, log = gkm.kmeans_fit(X, 100_000, gi, 2, seed=2, precision=2)
+    torch.cuda.synchronize()
+    print("deep_assign_bf16 final distortion", log[-1])
+
+
+def gist_refine(argv):
+    import torch
+
+    from paper_1705_01813_gb300 import datagen, gkm
+    X = torch.from_numpy(datagen.gist_like(300_000, 960, 1000, seed=5)).cuda()
+    _, _, _, log = gkm.build_knn_graph(X, 50, xi=50, tau=3, seed=1, precision=1)
+    torch.cuda.synchronize()
+    print("gist_refine final distortion", log[-1])
+
+
+def tree(argv):
+    import torch
+
+    from paper_1705_01813_gb300 import gkm
+    ap = argparse.ArgumentParser(prog="benchlib.cases tree")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--d", type=int, default=128)
+    ap.add_argument("--k", type=int, default=10_000)
+    ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--data-seed", type=int, default=1)
+    ap.add_argument("--calls", type=int, default=2)
+    ap.add_argument("--bf16", action="store_true")
+    a = ap.parse_args(argv)
+    X = torch.randn((a.n, a.d), device="cuda", generator=torch.Generator(device="cuda").manual_seed(a.data_seed))
+    if a.bf16:
+        X = X.to(torch.bfloat16)
+    ws = gkm.workspace(gkm.workspace_size(gkm.GK_OP_TREE, a.n, a.d, a.k), X.device)
+    lab = torch.empty(a.n, dtype=torch.int32, device="cuda")
+    gkm.two_means_tree(X, a.k, iters=a.iters, seed=a.seed, out=lab, ws=ws)
+    torch.cuda.synchronize()
+    ms = None
+    if a.calls > 1:
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(a.calls - 1):
+            gkm.two_means_tree(X, a.k, iters=a.iters, seed=a.seed, out=lab, ws=ws)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (a.calls - 1)
+    print(json.dumps({"n": a.n, "d": a.d, "k": a.k, "iters": a.iters, "bf16": a.bf16, "ms_per_call": ms,
+                      "status": gkm.read_status(ws)}))
+
+
+CASES = {"deep_assign_bf16": deep_assign_bf16, "gist_refine": gist_refine, "tree": tree}
+
+
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
+    if not argv or argv[0] not in CASES:
+        raise SystemExit("usage: python -m benchlib.cases {" + ",".join(CASES) + "} [options]")
+    from paper_1705_01813_gb300 import gkm
+    gkm.load()
+    CASES[argv[0]](argv[1:])
+
+
+if __name__ == "__main__":
+    main()

@@ -1,5 +1,5 @@
-// Measurement probes: the ceilings the assignment's roofline is read against
-// where HBM is not the bound.
+// Measurement probes of the benchmark (not part of libgkm): the ceilings the
+// assignment's roofline is read against where HBM is not the bound.
 //
 // k_probe_gather reads whole table rows chosen by an index list the way the
 // assignment reads candidate centroid rows: one warp per row, 16 bytes per
@@ -8,19 +8,26 @@
 // deep-feature one).  k_probe_fma runs independent packed FP32x2 FMA chains
 // (the instruction of the distance loops).  Both write one value per warp so
 // that the work cannot be dropped.
-#include "common.cuh"
+//
+// Built into libgkm_probes.so by benchlib/probes.py; the entry points below
+// return 0 on success, 1 on a bad argument, 2 on a CUDA launch error.
+#include <cuda_runtime.h>
+#include <stdint.h>
 
-namespace gkm {
+namespace {
 
+constexpr unsigned FULL = 0xffffffffu;
 constexpr int PG_WARPS = 8;
-constexpr int PG_ROWS = 8;  // rows in flight per warp
+constexpr int PG_ROWS = 8;        // rows in flight per warp
+constexpr int GRID = 152 * 8;     // both probes: 152 x 8 blocks
+constexpr int SINK = GRID * PG_WARPS;  // one sink value per warp
 
 template <int NV>
 __global__ void __launch_bounds__(PG_WARPS * 32) k_probe_gather(const float4 *__restrict__ table, int64_t rows,
                                                                 int row4, const int32_t *__restrict__ idx,
                                                                 int64_t count, float *__restrict__ sink)
 {
-    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * PG_WARPS + w, nwarps = (int64_t)gridDim.x * PG_WARPS;
     float acc = 0.f;
     for (int64_t j0 = warp * PG_ROWS; j0 < count; j0 += nwarps * PG_ROWS) {
@@ -29,7 +36,7 @@ __global__ void __launch_bounds__(PG_WARPS * 32) k_probe_gather(const float4 *__
         for (int r = 0; r < PG_ROWS; r++) {
             const int64_t j = j0 + r;
             int row = j < count ? __ldg(idx + j) : -1;
-            row = row < rows ? row : -1;  // indices outside the table read nothing
+            row = (row >= 0 && row < rows) ? row : -1;  // indices outside the table read nothing
 #pragma unroll
             for (int q = 0; q < NV; q++) {
                 const int col = lane + 32 * q;
@@ -45,7 +52,7 @@ __global__ void __launch_bounds__(PG_WARPS * 32) k_probe_gather(const float4 *__
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        acc += __shfl_xor_sync(FULL, acc, o);
     if (lane == 0)
         sink[warp] = acc;
 }
@@ -71,28 +78,43 @@ __global__ void __launch_bounds__(256) k_probe_fma(float *__restrict__ sink, int
         sink[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = t;
 }
 
-// both probes: 152 x 8 blocks of 8 warps, one sink value per warp (PROBE_SINK floats)
-static_assert(PROBE_SINK == 152 * 8 * PG_WARPS, "sink size");
+}  // namespace
 
-cudaError_t launch_probe_gather(const float *table, int64_t rows, int row_floats, const int32_t *idx, int64_t count,
-                                float *sink, cudaStream_t s)
+extern "C" {
+
+__attribute__((visibility("default"))) int gkb_probe_sink_floats(void) { return SINK; }
+
+// For j < count, one warp reads row idx[j] of table (rows x row_floats FP32,
+// row-major, 16-byte aligned; row_floats a multiple of 4 up to 512) in
+// 16-byte loads.  Bytes read: count x row_floats x 4.  sink: SINK floats.
+__attribute__((visibility("default"))) int gkb_probe_gather(const float *table, int64_t rows, int32_t row_floats,
+                                                            const int32_t *idx, int64_t count, float *sink,
+                                                            void *stream)
 {
+    if (!table || !idx || !sink || rows < 1 || rows > INT32_MAX || count < 0)
+        return 1;
+    if (row_floats < 4 || row_floats > 512 || row_floats % 4 != 0 || (reinterpret_cast<uintptr_t>(table) & 15))
+        return 1;
     const int row4 = row_floats / 4;
     const float4 *t4 = reinterpret_cast<const float4 *>(table);
-    const int grid = 152 * 8;
+    cudaStream_t s = (cudaStream_t)stream;
     if (row4 <= 32)
-        k_probe_gather<1><<<grid, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
+        k_probe_gather<1><<<GRID, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
     else if (row4 <= 64)
-        k_probe_gather<2><<<grid, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
+        k_probe_gather<2><<<GRID, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
     else
-        k_probe_gather<4><<<grid, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
-    return cudaGetLastError();
+        k_probe_gather<4><<<GRID, PG_WARPS * 32, 0, s>>>(t4, rows, row4, idx, count, sink);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
-cudaError_t launch_probe_fma(float *sink, int64_t iters, cudaStream_t s)
+// Every thread runs eight independent chains of `iters` packed FP32x2 FMAs:
+// 32 x iters FLOP per thread, GRID x 256 threads.
+__attribute__((visibility("default"))) int gkb_probe_fma(float *sink, int64_t iters, void *stream)
 {
-    k_probe_fma<<<152 * 8, 256, 0, s>>>(sink, iters);
-    return cudaGetLastError();
+    if (!sink || iters < 0)
+        return 1;
+    k_probe_fma<<<GRID, 256, 0, (cudaStream_t)stream>>>(sink, iters);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
-}  // namespace gkm
+}  // extern "C"

@@ -165,6 +165,9 @@ GK_API int gk_assign_step(const float *X, int64_t n, int64_t d, int64_t ld, cons
  *            (cluster r owns members[offsets[r] .. offsets[r+1]) )
  * A NaN or infinite sample makes its cluster's distortion term non-finite:
  * the update records GK_ERR_NUMERIC (detail: the cluster) in the status word.
+ * A label outside [0, k) is recorded as GK_ERR_INVALID; its sample belongs to
+ * no cluster (it is listed after every cluster's members, beyond
+ * offsets[k]), so the other clusters' results are those of their members.
  * The same holds for every update inside gk_kmeans_fit and gk_build_knn_graph.
  */
 GK_API int gk_update_step(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, float *C,
@@ -264,8 +267,11 @@ GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32
  *    each other's results.  Serialise them, e.g. on one stream.
  *  - The array keeps the previous call's contents; the call clears what must
  *    start at zero.  Labels out of range are not reported through a status
- *    word here (there is no workspace to read it from): they are left out of
- *    `counts`, so sum(counts) < n reveals them.
+ *    word here (there is no workspace to read it from).  A sample whose label
+ *    is outside [0, k) belongs to no cluster: the centroids, counts and
+ *    distortion terms of the clusters are those of the other samples alone
+ *    (as for gk_update_step, which also records the bad label in its status
+ *    word), so sum(counts) < n reveals such samples.
  */
 GK_API int gk_update_step_noalloc(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
                                   float *C, int32_t *counts, double *sum_d2, void *stream);
@@ -387,27 +393,6 @@ GK_API int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64
  * differently shaped requests would pay a capture per request.
  */
 GK_API int gk_set_replay(int enable);
-
-/*
- * Measurement probes: the ceilings against which the assignment is read where
- * HBM bandwidth does not bound it (its centroid rows come from L2).  Both run
- * 152 x 8 blocks of 8 warps and write one float per warp to sink (device,
- * GK_PROBE_SINK floats, contents meaningless), on `stream`; the caller times
- * them.
- *
- * gk_probe_gather: for j < count, one warp reads row idx[j] of table (device,
- *   rows x row_floats FP32, row-major, 16-byte aligned; row_floats a multiple
- *   of 4 up to 512) in 16-byte loads, eight rows of a warp in flight, as the
- *   assignment reads its candidate centroid rows.  Bytes read:
- *   count x row_floats x 4.  Entries of idx outside [0, rows) read nothing.
- * gk_probe_fma: every thread runs eight independent chains of `iters` packed
- *   FP32x2 FMAs (the distance loops' instruction): 32 x iters FLOP per
- *   thread, 152 x 8 x 256 threads.
- */
-#define GK_PROBE_SINK 9728
-GK_API int gk_probe_gather(const float *table, int64_t rows, int32_t row_floats, const int32_t *idx, int64_t count,
-                           float *sink, void *stream);
-GK_API int gk_probe_fma(float *sink, int64_t iters, void *stream);
 
 /*
  * Synchronise `stream`, return the status word the kernels of calls that used

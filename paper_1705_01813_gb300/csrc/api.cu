@@ -828,29 +828,6 @@ int gk_set_replay(int enable)
     return GK_OK;
 }
 
-int gk_probe_gather(const float *table, int64_t rows, int32_t row_floats, const int32_t *idx, int64_t count,
-                    float *sink, void *stream)
-{
-    if (!table || !idx || !sink)
-        return fail(GK_ERR_INVALID, "a required array is NULL");
-    if (rows < 1 || rows > INT32_MAX || count < 0)
-        return fail(GK_ERR_INVALID, "rows = %lld, count = %lld", (long long)rows, (long long)count);
-    if (row_floats < 4 || row_floats > 512 || row_floats % 4 != 0)
-        return fail(GK_ERR_INVALID, "row_floats = %d (a multiple of 4 in [4, 512])", row_floats);
-    if ((reinterpret_cast<uintptr_t>(table) & 15) != 0)
-        return fail(GK_ERR_INVALID, "table is not 16-byte aligned");
-    GK_CUDA(launch_probe_gather(table, rows, row_floats, idx, count, sink, (cudaStream_t)stream));
-    return GK_OK;
-}
-
-int gk_probe_fma(float *sink, int64_t iters, void *stream)
-{
-    if (!sink || iters < 0)
-        return fail(GK_ERR_INVALID, "sink is NULL or iters < 0");
-    GK_CUDA(launch_probe_fma(sink, iters, (cudaStream_t)stream));
-    return GK_OK;
-}
-
 int gk_read_status(void *ws, void *stream)
 {
     if (!ws)

@@ -300,9 +300,11 @@ __global__ void __launch_bounds__(AT_THREADS) k_assign_tc(const float *__restric
             phase ^= 1u;
             tc::fence_after_sync();
             // every thread saw the MMAs complete (opB may now hold values); a timeout is block-wide
-            timed_out = __syncthreads_or(late ? 1 : 0) != 0 || timed_out;
+            timed_out = __syncthreads_or(late ? 1 : 0) != 0;
+            if (timed_out)
+                break;  // stage and issue nothing more: the abandoned MMAs may still read opB
             // ---- 6. screening of this thread's own candidate columns ----
-            if (!timed_out) {
+            {
                 float *vrow = vals + tid * AT_VS;
                 for (int s0 = 0; s0 < N; s0 += 32) {
                     float g[32];
@@ -355,8 +357,12 @@ __global__ void __launch_bounds__(AT_THREADS) k_assign_tc(const float *__restric
             }
             __syncthreads();  // values read, opB free for the next chunk
         }
-        if (timed_out && tid == 0)
-            flag_error(st, GK_ERR_TIMEOUT, blockIdx.x);
+        if (timed_out) {
+            if (tid == 0)
+                flag_error(st, GK_ERR_TIMEOUT, blockIdx.x);
+            // one more bounded wait for the abandoned MMAs before their tensor memory is freed below
+            tc::mbar_wait_bounded(bar, phase ^ 1u, AT_WAIT_ITERS);
+        }
     }
 
     // ---- 7. the screened candidates of each sample, for the exact pass ----

@@ -186,12 +186,6 @@ size_t tree_scratch_bytes(int64_t n, int64_t d, int32_t k);
 cudaError_t launch_tree(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
                         uint64_t seed, int32_t *labels, void *scratch, DevStatus *st, cudaStream_t s);
 
-// measurement probes (probes.cu)
-constexpr int PROBE_SINK = 152 * 8 * 8;  // floats the probes' sink must hold
-cudaError_t launch_probe_gather(const float *table, int64_t rows, int row_floats, const int32_t *idx, int64_t count,
-                                float *sink, cudaStream_t s);
-cudaError_t launch_probe_fma(float *sink, int64_t iters, cudaStream_t s);
-
 // Internal launchers (each returns cudaError_t of the launch).  Those that read the samples take them as
 // X (FP32, or BF16 when bf16 is set) with leading dimension ld in elements.
 cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s);

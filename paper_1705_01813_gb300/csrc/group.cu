@@ -170,8 +170,17 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 __device__ __forceinline__ int digit_of(int32_t key, int shift) { return (int)(((uint32_t)key >> shift) & (RADIX - 1)); }
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const int32_t *__restrict__ keys, int64_t n, int shift,
-                                                           int32_t *__restrict__ tile_hist, int ntiles)
+// The sort key of a label: a label outside [0, k) sorts as k, after every
+// cluster, so that it cannot shift the member ranges of the valid clusters
+// (the label count leaves it out of every cluster and records it in the status
+// word).  The passes cover the bits of k itself for this reason.
+__device__ __forceinline__ int32_t sort_key(int32_t label, int32_t k)
+{
+    return (uint32_t)label < (uint32_t)k ? label : k;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const int32_t *__restrict__ keys, int64_t n, int32_t k,
+                                                           int shift, int32_t *__restrict__ tile_hist, int ntiles)
 {
     __shared__ int h[RADIX];
     for (int b = threadIdx.x; b < RADIX; b += RS_THREADS)
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const int32_t *__rest
     for (int q = threadIdx.x; q < RS_TILE; q += RS_THREADS) {
         int64_t e = base + q;
         if (e < n)
-            atomicAdd(&h[digit_of(keys[e], shift)], 1);
+            atomicAdd(&h[digit_of(sort_key(keys[e], k), shift)], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < RADIX; b += RS_THREADS)
@@ -190,7 +199,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const int32_t *__rest
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const int32_t *__restrict__ keys_in,
                                                               const int32_t *__restrict__ vals_in, int64_t n,
-                                                              int shift, const int32_t *__restrict__ tile_off,
+                                                              int32_t k, int shift,
+                                                              const int32_t *__restrict__ tile_off,
                                                               int ntiles, int32_t *__restrict__ keys_out,
                                                               int32_t *__restrict__ vals_out)
 {
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const int32_t *__r
     for (int r = 0; r < RS_ITEMS; r++) {
         int64_t e = wbase + r * 32 + lane;
         bool valid = e < n;
-        key[r] = valid ? keys_in[e] : 0;
+        key[r] = valid ? sort_key(keys_in[e], k) : 0;
         val[r] = valid ? (vals_in ? vals_in[e] : (int)e) : 0;
         int dg = valid ? digit_of(key[r], shift) : RADIX;
         dig[r] = dg;
@@ -239,15 +249,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const int32_t *__r
     }
 }
 
-__global__ void k_iota(int32_t *__restrict__ out, int64_t n)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (int32_t)i;
-}
-
+// 8-bit passes that cover every sort key 0..k (k: the key of an out-of-range label)
 static int radix_passes(int32_t k)
 {
-    uint32_t top = (uint32_t)(k - 1);
+    uint32_t top = (uint32_t)k;
     int bits = 0;
     while (top) {
         bits++;
@@ -299,11 +304,7 @@ cudaError_t launch_group(const int32_t *labels, int64_t n, int32_t k, int32_t *o
         return e;
 
     // members: stable sort of ids by label
-    int passes = radix_passes(k);
-    if (passes == 0) {
-        k_iota<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, s>>>(members, n);
-        return cudaGetLastError();
-    }
+    const int passes = radix_passes(k);  // at least one (k >= 1)
     const int32_t *kin = labels;
     const int32_t *vin = nullptr;
     for (int p = 0; p < passes; p++) {
@@ -311,10 +312,11 @@ cudaError_t launch_group(const int32_t *labels, int64_t n, int32_t k, int32_t *o
         int32_t *kout = last ? nullptr : (p & 1 ? kbuf1 : kbuf0);
         int32_t *vout = last ? members : (p & 1 ? vbuf1 : vbuf0);
         int shift = p * RADIX_BITS;
-        k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(kin, n, shift, thist, (int)ntiles);
+        k_radix_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(kin, n, k, shift, thist, (int)ntiles);
         if ((e = launch_scan(thist, thist, hist, sc, s)) != cudaSuccess)
             return e;
-        k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(kin, vin, n, shift, thist, (int)ntiles, kout, vout);
+        k_radix_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(kin, vin, n, k, shift, thist, (int)ntiles, kout,
+                                                                vout);
         kin = kout;
         vin = vout;
     }

@@ -230,18 +230,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
         phase ^= 1u;
         tc::fence_after_sync();
         __syncthreads();  // the staging area may be rewritten only after every warp saw the MMAs complete
+        // flags[1] is read by every thread between this barrier and the next staging barrier, which no thread
+        // can pass before all have read it, so the exit below is block-uniform
+        if (flags[1] != 0)
+            break;
+    }
+    if (flags[1] != 0) {
+        // a wait gave up: issue and stage nothing more, skip the epilogue, and give the abandoned MMAs one
+        // more bounded wait before their tensor memory is freed
+        if (tid == 0)
+            flag_error(st, GK_ERR_TIMEOUT, (unsigned)run);
+        tc::mbar_wait_bounded(bar, phase ^ 1u, TC_WAIT_ITERS);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (w == 0)
+            tc::tmem_dealloc(taddr, ncols);
+        return;
     }
     if (inexact)
         atomicOr(&flags[0], 1);
     if (lossy)
         atomicOr(&flags[2], 1);
     __syncthreads();
-    const bool timed_out = flags[1] != 0;
-    if (timed_out && tid == 0)
-        flag_error(st, GK_ERR_TIMEOUT, (unsigned)run);
     // integer run with |x| <= 255: exact only while 2 d 255^2 < 2^24
     const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
-    if (tid == 0 && !timed_out)
+    if (tid == 0)
         run_tag[run] = exact ? 0 : 1;  // k_refine_exact recomputes the marked pairs of this run
 
     // ---- candidates of row tid (TMEM lane tid), 32 columns at a time ----
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     // whole row segments to the global lists, so that the stores coalesce.
     int *bid = reinterpret_cast<int *>(stage);
     float *bdv = reinterpret_cast<float *>(bid + TC_M * 32);
-    const bool rows_here = !timed_out && 32 * w < sz;  // warp-uniform
+    const bool rows_here = 32 * w < sz;  // warp-uniform
     const int row = tid;
     const float n_i = nrm[row];
     const float u = 1.0f / 256.0f;

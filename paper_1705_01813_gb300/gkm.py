@@ -26,8 +26,8 @@ GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL, 
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
-           "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall", "gk_probe_gather",
-           "gk_probe_fma", "gk_set_replay", "gk_two_means_tree"]
+           "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall",
+           "gk_set_replay", "gk_two_means_tree"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
              "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall",
@@ -83,8 +83,6 @@ def load(build_if_missing: bool = True):
             L.gk_graph_refine_groups.argtypes = [P, I64, I64, I64, P, P, I32, I32, I32, I32, P, P, P, SZ, P]
             L.gk_update_step_noalloc.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P]
             L.gk_graph_recall.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, SZ, P]
-            L.gk_probe_gather.argtypes = [P, I64, I32, P, I64, P, P]
-            L.gk_probe_fma.argtypes = [P, I64, P]
             L.gk_set_replay.argtypes = [I32]
             L.gk_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P, P, SZ, P]
             for name in X_ENTRIES:
@@ -365,24 +363,6 @@ def set_replay(enable: bool):
     """Replay repeated build_knn_graph / kmeans_fit calls with equal arguments as one captured CUDA graph (see
     gk_set_replay); off by default."""
     _check(load().gk_set_replay(1 if enable else 0))
-
-
-PROBE_SINK = 9728  # floats of the probes' sink (GK_PROBE_SINK)
-
-
-def probe_gather(table, idx, sink, stream=None):
-    """Warp-per-row gather of table rows idx[j] (see gk_probe_gather); returns the bytes it reads."""
-    _dev(table, torch.float32, "table")
-    _dev(idx, torch.int32, "idx")
-    _check(load().gk_probe_gather(_ptr(table), table.shape[0], table.shape[1], _ptr(idx), idx.numel(), _ptr(sink),
-                                  _stream(stream)))
-    return idx.numel() * table.shape[1] * 4
-
-
-def probe_fma(sink, iters: int, stream=None):
-    """Packed FP32x2 FMA chains (see gk_probe_fma); returns the FLOP count."""
-    _check(load().gk_probe_fma(_ptr(sink), iters, _stream(stream)))
-    return 32 * iters * 152 * 8 * 256
 
 
 def read_status(ws: Workspace, stream=None) -> int:

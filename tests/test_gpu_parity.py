@@ -310,6 +310,10 @@ def test_build_graph_precisions_identical(G):
 # --------------------------------------------------------------- fit / build
 
 def test_fit_lockstep_and_free_running(G):
+    """The fit free-running on the Gaussian-mixture workload from the oracle's graph and labels.  The oracle meets
+    near ties on this input (assignment margins down to about 1e-6), so labels are compared as a divergence
+    measure; the final distortion must agree within the stated 1e-5.  Element-wise equality of a whole path on
+    inputs without near ties is tests/test_free_running.py."""
     w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
     X = w.data()
     gi, _, _, _ = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
@@ -319,12 +323,14 @@ def test_fit_lockstep_and_free_running(G):
     Eg = np.array(Eg)
     assert (np.diff(Eg) <= 1e-6 * Eg[:-1]).all()  # non-increasing
     # free running: the final distortion agrees with the oracle's
-    P.check_rel(Eg[-1], Eo[-1], rel=1e-4, what="final distortion")
+    P.check_rel(Eg[-1], Eo[-1], rel=1e-5, what="final distortion")
     frac = (_np(lg) != Lo).mean()
     assert frac < 1e-3
 
 
 def test_build_graph_free_running(G):
+    """The graph construction free-running on the Gaussian-mixture workload (an input with near ties, see
+    above): row invariants, quality against the oracle's graph, and the final distortion within 1e-5."""
     w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
     X = w.data()
     oi, od, oL, oE = O.build_graph(X, w.kappa, xi=w.xi, tau=w.tau, max_cluster=w.max_cluster, seed=w.seed)
@@ -337,7 +343,7 @@ def test_build_graph_free_running(G):
     agree = (gi[:, 0] == oi[:, 0]).mean()
     assert agree > 0.97
     assert abs(np.mean(gd[:, -1]) / np.mean(od[:, -1]) - 1) < 1e-3
-    assert abs(gE[-1] / oE[-1] - 1) < 1e-3
+    P.check_rel(gE[-1], oE[-1], rel=1e-5, what="final distortion")
 
 
 # --------------------------------------------------------------- edge cases
@@ -378,6 +384,27 @@ def test_out_of_range_labels_are_reported(G):
     ws2 = G.Workspace(G.workspace_size(G.GK_OP_ASSIGN, 500, 4, 5, 3))
     G.assign_step(_cuda(X), _cuda(gi), torch.zeros((5, 4), device="cuda"), _cuda(np.zeros(500, np.int32)), ws=ws2)
     assert G.read_status(ws2) == G.GK_ERR_INVALID
+
+
+def test_out_of_range_labels_belong_to_no_cluster(G):
+    """A sample with a label outside [0, k) is listed after every cluster's members: offsets and the valid
+    clusters' members equal the grouping of the valid samples alone, and the bad samples fill the tail."""
+    n, k = 9000, 256  # k = 256: the sort key k of a bad label needs a second 8-bit pass
+    g = np.random.default_rng(3)
+    L = g.integers(0, k, n).astype(np.int32)
+    bad = np.sort(g.choice(n, 11, replace=False))
+    L[bad[:6]] = [k, k + 1, 300, 511, 1 << 20, 2**31 - 1]
+    L[bad[6:]] = [-1, -2, -256, -(1 << 20), -(2**31)]
+    ws = G.Workspace(G.workspace_size(G.GK_OP_UPDATE, n, 1, k))
+    off, mem, cnt = G.group_by_label(_cuda(L), k, ws=ws)
+    assert G.read_status(ws) == G.GK_ERR_INVALID
+    ok = (L >= 0) & (L < k)
+    want_off = np.concatenate([[0], np.cumsum(np.bincount(L[ok], minlength=k))])
+    want_mem = np.argsort(np.where(ok, L, k), kind="stable").astype(np.int32)
+    assert np.array_equal(off.cpu().numpy(), want_off)
+    assert np.array_equal(mem.cpu().numpy(), want_mem)
+    assert np.array_equal(np.sort(mem.cpu().numpy()[want_off[-1]:]), bad)
+    assert np.array_equal(cnt.cpu().numpy(), np.bincount(L[ok], minlength=k))
 
 
 def test_deterministic_and_resumable(G):
