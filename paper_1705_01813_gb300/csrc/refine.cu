@@ -135,9 +135,9 @@ static size_t run_bytes(int32_t k) { return ((size_t)(2 * (k + 1)) * sizeof(int3
 // runs per refinement are at most k + n / max_cluster (max_cluster >= 2)
 static size_t run_cl_bytes(int64_t n, int32_t k) { return ((size_t)(k + n / 2 + 1) * sizeof(int32_t) + 255) / 256 * 256; }
 
-size_t refine_scratch_bytes(int64_t n, int32_t k)
+size_t refine_scratch_bytes(int64_t n, int32_t k, int64_t d)
 {
-    return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n, k);
+    return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n, k, d);
 }
 
 template <typename XT>

@@ -2,17 +2,24 @@
 // taken from a Gram matrix on the tensor cores (tcgen05, BF16 inputs, FP32
 // accumulation in tensor memory), and the same graph as the FP32 path.
 //
-// Three kernels per refinement:
+// Four kernels per refinement:
 //
-// k_refine_gram, one CTA (4 warps) per run of <= 128 members.  The run's rows,
-// FP32 samples centred on the run's first member (BF16 samples as they are),
-// are converted to BF16 and staged in shared memory in the 128-byte swizzle
-// layout (two 64-column K-blocks at a time); one thread issues the
-// 128 x N x 16 MMAs of G = X' X'^T into tensor memory and commits them to an
-// mbarrier.  Thread t then owns TMEM lane t, i.e. row t of G, forms
-// d2(t, j) = n_t + n_j - 2 G_tj (n = squared norms of the staged rows) and
-// appends to its graph row's candidate list every j that may enter the row:
-// key (d2, id_j) below the row's kappa-th key.
+// k_refine_perm, one CTA per run of <= 128 members: the cluster-sorted copy.
+// Row p of Xp is the sample at position p of the grouping (members[p]) in
+// BF16: FP32 samples centred on their run's first member, BF16 samples as
+// they are; rows padded with zeros to a multiple of 8 columns.  It also writes
+// each row's FP32 squared norm (of the unrounded centred values) and per run
+// two flags: a centred value that is not an integer of magnitude <= 255, and
+// a value that BF16 rounded.
+//
+// k_refine_gram, one CTA (4 warps) per run: one thread loads the run's 128-row
+// tile of Xp with the TMA engine (cp.async.bulk.tensor, 64-column boxes in the
+// 128-byte swizzle layout the MMA descriptors expect; rows of the next runs
+// and past the end come along and are ignored) and issues the 128 x N x 16
+// MMAs of G = X' X'^T into tensor memory.  Thread t then owns TMEM lane t,
+// i.e. row t of G, forms d2(t, j) = n_t + n_j - 2 G_tj (n = the squared
+// norms) and appends to its graph row's candidate list every j that may enter
+// the row: key (d2, id_j) below the row's kappa-th key.
 // Exactness: when every staged coordinate of the run is an integer of
 // magnitude <= 255 and 2 d 255^2 < 2^24, every BF16 value, product and partial
 // sum is an exact integer below 2^24, so d2 equals the FP32 sum of squared
@@ -36,18 +43,20 @@
 #include "merge.cuh"
 #include "tc.cuh"
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from cudaGetDriverEntryPointByVersion)
 #include <cuda_bf16.h>
+
+#include <mutex>
 #include <type_traits>
 
 namespace gkm {
 
 constexpr int TC_M = 128;                // rows of the MMA tile (TMEM lanes) and widest run
-constexpr int TC_KB = 64;                // BF16 elements per K-block (one 128-byte swizzle row)
-constexpr int TC_KCH = 2;                // K-blocks staged per chunk
+constexpr int TC_KB = 64;                // BF16 elements per K-block (one 128-byte swizzle row, one TMA box)
+constexpr int TC_KCH = 2;                // K-blocks of the widest row (d <= 128)
 constexpr int TC_KB_BYTES = TC_M * 128;  // 16 KB per K-block
 constexpr int TC_THREADS = 128;          // one thread per TMEM lane
 constexpr int TC_WARPS = TC_THREADS / 32;
-constexpr int TC_RB = 8;                 // rows a warp stages per batch
 constexpr int TC_CAP = 128;              // candidate slots per graph row
 constexpr uint32_t TC_WAIT_ITERS = 1u << 22;
 constexpr unsigned TC_RERANK = 0x80000000u;  // candidate id flag: distance needs the exact recompute
@@ -57,19 +66,110 @@ constexpr size_t TC_BUF = (size_t)2 * TC_M * 32 * sizeof(int);  // ids and dista
 static_assert(TC_BUF <= TC_STAGE, "the epilogue's candidate buffers reuse the staging area");
 constexpr size_t TC_SMEM = 1024 /*alignment slack*/ + TC_STAGE + sizeof(float) * TC_M + sizeof(int) * TC_M * 3 + 64;
 
+// Columns of a row of the cluster-sorted copy: d rounded up to 8 (16-byte rows for the tensor map).
+static int64_t perm_cols(int64_t d) { return (d + 7) & ~int64_t(7); }
+
 // Slot of entry m (< 32) of row r in the candidate buffers: rows of 32 words
 // with the entry index xor-ed by r % 32, so the 32 rows of a warp writing
 // their m-th entries, and a warp reading one row, touch 32 distinct banks.
 __device__ __forceinline__ int buf_slot(int r, int m) { return r * 32 + (m ^ (r & 31)); }
 
+// The run of block `run`: its cluster r, first member position p0 (in members / Xp) and size sz.
+__device__ __forceinline__ void run_range(int run, const int32_t *__restrict__ off, const int32_t *__restrict__ run_off,
+                                          const int32_t *__restrict__ run_cl, int cap, int *p0, int *sz, int *r)
+{
+    *r = run_cl[run];
+    const int beg = off[*r], m = off[*r + 1] - beg;
+    const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
+    const int c = run - run_off[*r];
+    *p0 = beg + c * rbase + min(c, rem);
+    *sz = rbase + (c < rem ? 1 : 0);
+}
+
 template <typename XT>
-__global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict__ X, int64_t n, int d,
-                                                            int64_t ld, const int32_t *__restrict__ off,
+__global__ void __launch_bounds__(TC_THREADS) k_refine_perm(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+                                                            const int32_t *__restrict__ off,
+                                                            const int32_t *__restrict__ mem,
+                                                            const int32_t *__restrict__ run_off,
+                                                            const int32_t *__restrict__ run_cl, int k, int cap,
+                                                            int dp, __nv_bfloat16 *__restrict__ Xp,
+                                                            float *__restrict__ pnrm, int32_t *__restrict__ run_flags,
+                                                            DevStatus *st)
+{
+    const int run = blockIdx.x;
+    if (run >= run_off[k])
+        return;
+    int p0, sz, r;
+    run_range(run, off, run_off, run_cl, cap, &p0, &sz, &r);
+    if (sz < 2 || sz > TC_M)  // no pairs, or a run of the FP32 kernel
+        return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
+    // BF16 samples are copied as they are: their values, products and the Gram's accumulation carry no BF16
+    // rounding (centring would round the differences)
+    constexpr bool CENTRE = !std::is_same_v<XT, __nv_bfloat16>;
+    int ref = mem[p0];
+    ref = (unsigned)ref < (unsigned)n ? ref : -1;
+    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(XT))) == 0;
+    bool inexact = false, lossy = false;
+    for (int q = w; q < sz; q += TC_WARPS) {
+        const int p = p0 + q;
+        int a = mem[p];
+        if ((unsigned)a >= (unsigned)n) {
+            if (lane == 0)
+                flag_error(st, GK_ERR_INVALID, (unsigned)r);
+            a = -1;
+        }
+        float part = 0.f;
+        for (int t = lane * 4; t < dp; t += 128) {
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (a >= 0 && t < d) {
+                const XT *xa = X + (int64_t)a * ld + t;
+                const XT *xr = X + (int64_t)(ref >= 0 ? ref : a) * ld + t;
+                if (vec4) {
+                    const float4 xv = ldx4<XT>(xa);
+                    v[0] = xv.x, v[1] = xv.y, v[2] = xv.z, v[3] = xv.w;
+                    if (CENTRE && ref >= 0) {
+                        const float4 rv = ldx4<XT>(xr);
+                        v[0] -= rv.x, v[1] -= rv.y, v[2] -= rv.z, v[3] -= rv.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; e++)
+                        if (t + e < d)
+                            v[e] = ldx(xa + e) - (CENTRE && ref >= 0 ? ldx(xr + e) : 0.f);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                part = fmaf(v[e], v[e], part);
+                inexact |= !(v[e] == rintf(v[e]) && fabsf(v[e]) <= 255.f);
+            }
+            const __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]), b1 = __floats2bfloat162_rn(v[2], v[3]);
+            const float2 f0 = __bfloat1622float2(b0), f1 = __bfloat1622float2(b1);
+            lossy |= f0.x != v[0] || f0.y != v[1] || f1.x != v[2] || f1.y != v[3];
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t *>(&b0);
+            pk.y = *reinterpret_cast<const uint32_t *>(&b1);
+            *reinterpret_cast<uint2 *>(Xp + (int64_t)p * dp + t) = pk;
+        }
+        part = warp_total(part);
+        if (lane == 0)
+            pnrm[p] = part;
+    }
+    const int any_inexact = __syncthreads_or(inexact ? 1 : 0), any_lossy = __syncthreads_or(lossy ? 1 : 0);
+    if (tid == 0)
+        run_flags[run] = (any_inexact ? 1 : 0) | (any_lossy ? 2 : 0);
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const __grid_constant__ CUtensorMap tmap, int64_t n,
+                                                            int d, const int32_t *__restrict__ off,
                                                             const int32_t *__restrict__ mem,
                                                             const int32_t *__restrict__ run_off,
                                                             const int32_t *__restrict__ run_cl, int k, int kappa,
                                                             int cap, const int32_t *__restrict__ g_idx,
                                                             const float *__restrict__ g_dist,
+                                                            const float *__restrict__ pnrm,
+                                                            const int32_t *__restrict__ run_flags,
                                                             int32_t *__restrict__ cand_id,
                                                             float *__restrict__ cand_d, int32_t *__restrict__ cand_n,
                                                             int32_t *__restrict__ run_tag, DevStatus *st)
@@ -81,179 +181,96 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     int *rid = reinterpret_cast<int *>(nrm + TC_M);
     int *bcnt = rid + TC_M;   // candidates of each row in the current chunk
     int *btot = bcnt + TC_M;  // candidates of each row written so far
-    uint64_t *bar = reinterpret_cast<uint64_t *>(btot + TC_M);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
-    int *flags = reinterpret_cast<int *>(tslot + 1);  // [0] not exact, [1] timeout, [2] a value not BF16
+    uint64_t *bar = reinterpret_cast<uint64_t *>(btot + TC_M);  // [0] the tile's copies, [1] the MMAs
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
     const int tid = threadIdx.x, w = tid >> 5, lane = lane_id();
 
-    // this block's run: cluster r with run_off[r] <= run < run_off[r + 1]
     const int run = blockIdx.x;
     if (run >= run_off[k])
         return;
-    const int r = run_cl[run];
-    const int beg = off[r], m = off[r + 1] - beg;
-    const int nc = (m + cap - 1) / cap, rbase = m / nc, rem = m % nc;
-    const int c = run - run_off[r];
-    const int s0 = c * rbase + min(c, rem), sz = rbase + (c < rem ? 1 : 0);
+    int p0, sz, r;
+    run_range(run, off, run_off, run_cl, cap, &p0, &sz, &r);
     if (sz < 2 || sz > TC_M)  // longer runs (max_cluster > 128) go to the FP32 kernel
         return;
-    const int32_t *S = mem + beg + s0;
     const int N = (sz + 15) & ~15;
     const uint32_t ncols = sz <= 32 ? 32u : sz <= 64 ? 64u : 128u;
+    const int nkb = (d + TC_KB - 1) / TC_KB;
 
     if (w == 0) {
         tc::tmem_alloc(tslot, ncols);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
         tc::fence_mbar_init();
-        flags[0] = 0;
-        flags[1] = 0;
-        flags[2] = 0;
+        // the run's rows p0 .. p0 + 127 of the cluster-sorted copy, one 64-column box per K-block
+        tc::mbar_arrive_expect_tx(&bar[0], (uint32_t)(nkb * TC_KB_BYTES));
+        for (int kb = 0; kb < nkb; kb++)
+            tc::tma_load_2d(stage + kb * TC_KB_BYTES, &tmap, kb * TC_KB, p0, &bar[0]);
     }
-    // this thread's graph row and its kappa-th key (read now so the loads overlap the staging)
-    int gi_row = tid < sz ? S[tid] : -1;
+    // this thread's graph row, its kappa-th key and its norm, while the tile is in flight
+    int gi_row = tid < sz ? mem[p0 + tid] : -1;
     if (gi_row >= n) {
         flag_error(st, GK_ERR_INVALID, (unsigned)r);
         gi_row = -1;
     }
     rid[tid] = gi_row;
+    nrm[tid] = tid < sz ? pnrm[p0 + tid] : 0.f;
     float thd = 0.f;
     int thi = 0;
     if (gi_row >= 0) {
         thd = __ldcg(g_dist + (int64_t)gi_row * kappa + kappa - 1);
         thi = __ldcg(g_idx + (int64_t)gi_row * kappa + kappa - 1);
     }
+    const int rf = run_flags[run];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *tslot;
-    const int ref = rid[0] >= 0 ? rid[0] : 0;
-    const XT *xref = X + (int64_t)ref * ld;
-    const bool vec4 = (d % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(XT))) == 0;
 
-    // ---- Gram matrix of the (centred) run, K-chunk by K-chunk ----
-    // BF16 samples are staged as they are: their values, products and the Gram's
-    // accumulation carry no BF16 rounding (centring would round the differences)
-    constexpr bool CENTRE = !std::is_same_v<XT, __nv_bfloat16>;
-    bool inexact = false, lossy = false;
-    uint32_t phase = 0;
-    const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
-    const int kchunk = TC_KCH * TC_KB;  // 128 coordinates: 4 per lane
-    const int srows = (sz + 7) & ~7;    // rows staged (the rest of the tile is never read back)
-    for (int k0 = 0; k0 < d; k0 += kchunk) {
-        const int kk = lane * 4, t = k0 + kk;
-        const int kb = kk / TC_KB, kin = kk % TC_KB;
-        float xr[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++)
-            xr[e] = CENTRE && t + e < d ? ldx(xref + t + e) : 0.f;
-        // warp w stages rows w, w + 4, ..., TC_RB of them per batch with their loads in flight together
-        for (int row0 = w; row0 < srows; row0 += TC_WARPS * TC_RB) {
-            float v[TC_RB][4];
-#pragma unroll
-            for (int b = 0; b < TC_RB; b++) {
-                const int row = row0 + b * TC_WARPS;
-                const int a = row < srows ? rid[row] : -1;
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    v[b][e] = 0.f;
-                if (a >= 0) {
-                    const XT *xa = X + (int64_t)a * ld + t;
-                    if (vec4 && t + 3 < d) {
-                        const float4 q = ldx4<XT>(xa);
-                        v[b][0] = q.x;
-                        v[b][1] = q.y;
-                        v[b][2] = q.z;
-                        v[b][3] = q.w;
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; e++)
-                            if (t + e < d)
-                                v[b][e] = ldx(xa + e);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; e++)
-                        v[b][e] = t + e < d ? v[b][e] - xr[e] : 0.f;
-                }
-            }
-            float part[TC_RB];
-#pragma unroll
-            for (int b = 0; b < TC_RB; b++) {
-                const int row = row0 + b * TC_WARPS;
-                part[b] = 0.f;
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    part[b] = fmaf(v[b][e], v[b][e], part[b]);
-                    inexact |= !(v[b][e] == rintf(v[b][e]) && fabsf(v[b][e]) <= 255.f);
-                }
-                if (row < srows) {
-                    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[b][0], v[b][1]);
-                    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[b][2], v[b][3]);
-                    if (CENTRE) {
-                        const float2 b0 = __bfloat1622float2(p0), b1 = __bfloat1622float2(p1);
-                        lossy |= b0.x != v[b][0] || b0.y != v[b][1] || b1.x != v[b][2] || b1.y != v[b][3];
-                    }
-                    uint2 pk;
-                    pk.x = *reinterpret_cast<uint32_t *>(&p0);
-                    pk.y = *reinterpret_cast<uint32_t *>(&p1);
-                    *reinterpret_cast<uint2 *>(stage + kb * TC_KB_BYTES + tc::swz128_offset(row, kin)) = pk;
-                }
-            }
-            // lane l ends with the total of row row0 + (l / (32 / TC_RB)) TC_WARPS
-            const float tot = transpose_reduce<TC_RB>(part);
-            const int row = row0 + (lane / (32 / TC_RB)) * TC_WARPS;
-            if (lane % (32 / TC_RB) == 0 && row < srows)
-                nrm[row] = (k0 == 0 ? 0.f : nrm[row]) + tot;
-        }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const int nkb = min(TC_KCH, (d - k0 + TC_KB - 1) / TC_KB);
-            for (int kb = 0; kb < nkb; kb++) {
-                const uint32_t a_addr = tc::smem_addr(stage + kb * TC_KB_BYTES);
-#pragma unroll
-                for (int s = 0; s < TC_KB / 16; s++) {
-                    const uint64_t desc = tc::desc_k128(a_addr + 32 * s);
-                    tc::mma_bf16(taddr, desc, desc, idesc, (k0 > 0) || (kb > 0) || (s > 0));
-                }
-            }
-            tc::mma_commit(bar);
-        }
-        __syncwarp();
-        if (!tc::mbar_wait_bounded(bar, phase, TC_WAIT_ITERS)) {
-            if (lane == 0)
-                atomicOr(&flags[1], 1);
-        }
-        phase ^= 1u;
-        tc::fence_after_sync();
-        __syncthreads();  // the staging area may be rewritten only after every warp saw the MMAs complete
-        // flags[1] is read by every thread between this barrier and the next staging barrier, which no thread
-        // can pass before all have read it, so the exit below is block-uniform
-        if (flags[1] != 0)
-            break;
-    }
-    if (flags[1] != 0) {
-        // a wait gave up: issue and stage nothing more, skip the epilogue, and give the abandoned MMAs one
-        // more bounded wait before their tensor memory is freed
+    // ---- the tile, then the Gram matrix of the (centred) run ----
+    bool late = !tc::mbar_wait_bounded(&bar[0], 0, TC_WAIT_ITERS);
+    if (__syncthreads_or(late ? 1 : 0)) {
+        // the copies gave up: issue nothing, give them one more bounded wait, free the tensor memory
         if (tid == 0)
             flag_error(st, GK_ERR_TIMEOUT, (unsigned)run);
-        tc::mbar_wait_bounded(bar, phase ^ 1u, TC_WAIT_ITERS);
+        tc::mbar_wait_bounded(&bar[0], 0, TC_WAIT_ITERS);
         tc::fence_before_sync();
         __syncthreads();
         if (w == 0)
             tc::tmem_dealloc(taddr, ncols);
         return;
     }
-    if (inexact)
-        atomicOr(&flags[0], 1);
-    if (lossy)
-        atomicOr(&flags[2], 1);
-    __syncthreads();
+    if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::idesc_bf16_f32(TC_M, N);
+        for (int kb = 0; kb < nkb; kb++) {
+            const uint32_t a_addr = tc::smem_addr(stage + kb * TC_KB_BYTES);
+#pragma unroll
+            for (int s = 0; s < TC_KB / 16; s++) {
+                const uint64_t desc = tc::desc_k128(a_addr + 32 * s);
+                tc::mma_bf16(taddr, desc, desc, idesc, (kb > 0) || (s > 0));
+            }
+        }
+        tc::mma_commit(&bar[1]);
+    }
+    __syncwarp();
+    late = !tc::mbar_wait_bounded(&bar[1], 0, TC_WAIT_ITERS);
+    tc::fence_after_sync();
+    if (__syncthreads_or(late ? 1 : 0)) {
+        // the MMAs gave up: skip the epilogue, one more bounded wait before their tensor memory is freed
+        if (tid == 0)
+            flag_error(st, GK_ERR_TIMEOUT, (unsigned)run);
+        tc::mbar_wait_bounded(&bar[1], 0, TC_WAIT_ITERS);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (w == 0)
+            tc::tmem_dealloc(taddr, ncols);
+        return;
+    }
     // integer run with |x| <= 255: exact only while 2 d 255^2 < 2^24
-    const bool exact = flags[0] == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
+    const bool exact = (rf & 1) == 0 && 2.0 * d * 255.0 * 255.0 < 16777216.0;
     if (tid == 0)
         run_tag[run] = exact ? 0 : 1;  // k_refine_exact recomputes the marked pairs of this run
 
@@ -267,7 +284,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_refine_gram(const XT *__restrict
     const int row = tid;
     const float n_i = nrm[row];
     const float u = 1.0f / 256.0f;
-    const float rnd = flags[2] != 0 ? 4.f * u + 2.f * u * u : 0.f;  // BF16 rounding of the operands
+    const float rnd = (rf & 2) != 0 ? 4.f * u + 2.f * u * u : 0.f;  // BF16 rounding of the operands
     // accumulation of G: exact products, each 16-deep step aligned to its largest term and truncated (an
     // error below 16 units of 2^-23 of the step's terms), over d / 16 steps, doubled by the factor 2 of
     // 2 G and once more as a margin
@@ -468,12 +485,55 @@ __global__ void __launch_bounds__(MG_WARPS * 32) k_refine_merge(int64_t n, int k
 }
 
 // candidate ids and distances (n x TC_CAP each), counts (n), run flags (at most k + n / 2 + 1 runs)
-size_t refine_tc_scratch_bytes(int64_t n, int32_t k)
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// candidate ids and distances (n x TC_CAP each), counts (n), run tags and run flags (at most k + n / 2 + 1 runs
+// each), and for 64 <= d <= 128 the cluster-sorted BF16 copy (n x perm_cols(d)) with its row norms (n)
+size_t refine_tc_scratch_bytes(int64_t n, int32_t k, int64_t d)
 {
-    const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
-    const size_t c = ((size_t)n * sizeof(int32_t) + 255) & ~size_t(255);
-    const size_t t = ((size_t)(k + n / 2 + 1) * sizeof(int32_t) + 255) & ~size_t(255);
-    return 2 * a + c + t;
+    const size_t a = al256((size_t)n * TC_CAP * sizeof(int32_t));
+    const size_t c = al256((size_t)n * sizeof(int32_t));
+    const size_t t = al256((size_t)(k + n / 2 + 1) * sizeof(int32_t));
+    const size_t perm = (d >= 64 && d <= 128) ? al256((size_t)n * (size_t)perm_cols(d) * 2) + al256((size_t)n * 4) : 0;
+    return 2 * a + c + 2 * t + perm;
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static cudaError_t encode_tiled(EncodeTiledFn *fn)
+{
+    static std::once_flag once;
+    static void *ptr = nullptr;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q);
+        if (err == cudaSuccess && (q != cudaDriverEntryPointSuccess || !ptr))
+            err = cudaErrorNotSupported;
+    });
+    *fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    return err;
+}
+
+// Tensor map of the cluster-sorted copy: n rows of dp BF16 (row stride dp * 2 bytes, a multiple of 16), boxes of
+// 64 columns x 128 rows in the 128-byte swizzle layout, rows past n read as zeros.
+static cudaError_t perm_tensor_map(CUtensorMap *tm, const __nv_bfloat16 *Xp, int64_t n, int64_t dp)
+{
+    EncodeTiledFn fn = nullptr;
+    cudaError_t e = encode_tiled(&fn);
+    if (e != cudaSuccess)
+        return e;
+    const cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_KB, (cuuint32_t)TC_M};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(Xp), dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <typename XT>
@@ -482,14 +542,22 @@ static cudaError_t refine_tc_t(const XT *X, int64_t n, int64_t d, int64_t ld, co
                                int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,
                                void *scratch, DevStatus *st, cudaStream_t s)
 {
-    const size_t a = ((size_t)n * TC_CAP * sizeof(int32_t) + 255) & ~size_t(255);
-    int32_t *cand_id = static_cast<int32_t *>(scratch);
-    float *cand_d = reinterpret_cast<float *>(static_cast<char *>(scratch) + a);
-    int32_t *cand_n = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a);
-    int32_t *run_tag = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + 2 * a +
-                                                   (((size_t)n * sizeof(int32_t) + 255) & ~size_t(255)));
-    cudaError_t e = set_max_smem(reinterpret_cast<const void *>(k_refine_gram<XT>), (int)TC_SMEM);
+    const size_t a = al256((size_t)n * TC_CAP * sizeof(int32_t));
+    const size_t t = al256((size_t)(k + n / 2 + 1) * sizeof(int32_t));
+    char *sp = static_cast<char *>(scratch);
+    int32_t *cand_id = reinterpret_cast<int32_t *>(sp);
+    float *cand_d = reinterpret_cast<float *>(sp + a);
+    int32_t *cand_n = reinterpret_cast<int32_t *>(sp + 2 * a);
+    int32_t *run_tag = reinterpret_cast<int32_t *>(sp + 2 * a + al256((size_t)n * 4));
+    int32_t *run_flags = reinterpret_cast<int32_t *>(sp + 2 * a + al256((size_t)n * 4) + t);
+    __nv_bfloat16 *Xp = reinterpret_cast<__nv_bfloat16 *>(sp + 2 * a + al256((size_t)n * 4) + 2 * t);
+    const int64_t dp = perm_cols(d);
+    float *pnrm = reinterpret_cast<float *>(reinterpret_cast<char *>(Xp) + al256((size_t)n * (size_t)dp * 2));
+    CUtensorMap tmap;
+    cudaError_t e = perm_tensor_map(&tmap, Xp, n, dp);
     if (e != cudaSuccess)
+        return e;
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_gram), (int)TC_SMEM)) != cudaSuccess)
         return e;
     const size_t shm_exact = sizeof(float) * (size_t)TC_M * (size_t)(d + 1);  // d <= 128 on this path
     if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine_exact<XT>),
@@ -503,9 +571,11 @@ static cudaError_t refine_tc_t(const XT *X, int64_t n, int64_t d, int64_t ld, co
         return e;
     if ((e = cudaMemsetAsync(run_tag, 0, sizeof(int32_t) * (size_t)grid, s)) != cudaSuccess)
         return e;
-    k_refine_gram<XT><<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
-                                                              kappa, max_cluster, g_idx, g_dist, cand_id, cand_d,
-                                                              cand_n, run_tag, st);
+    k_refine_perm<XT><<<(unsigned)grid, TC_THREADS, 0, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+                                                            max_cluster, (int)dp, Xp, pnrm, run_flags, st);
+    k_refine_gram<<<(unsigned)grid, TC_THREADS, TC_SMEM, s>>>(tmap, n, (int)d, offsets, members, run_off, run_cl, k,
+                                                              kappa, max_cluster, g_idx, g_dist, pnrm, run_flags,
+                                                              cand_id, cand_d, cand_n, run_tag, st);
     k_refine_exact<XT><<<(unsigned)grid, EX_THREADS, shm_exact, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl,
                                                                  k, max_cluster, run_tag, cand_id, cand_d, cand_n,
                                                                  st);

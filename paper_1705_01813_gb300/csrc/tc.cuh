@@ -95,6 +95,20 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, u
                  : "memory");
 }
 
+// Tiled TMA load of a 2-D box (tensor map in kernel-parameter or global
+// memory) into this CTA's shared memory at `smem_dst`; c0 is the innermost
+// coordinate (its byte offset must be a multiple of 16), c1 the row.  The
+// box's bytes complete on `bar` as transaction bytes; rows outside the tensor
+// read as zeros.
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const void *tmap, int32_t c0, int32_t c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(smem_dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // ---- MMA ------------------------------------------------------------------
 
 // Shared-memory matrix descriptor for a K-major operand stored in the 128-byte

@@ -211,6 +211,7 @@ REFINE_CASES = [
     (5003, 68, 60, 33, 128),     # clusters of ~83
     (6007, 80, 20, 10, 128),     # clusters of ~300 cut into runs
     (2000, 72, 3, 16, 500),      # runs longer than one 128-row tile go to the FP32 kernel
+    (3001, 65, 25, 12, 128),     # odd d (scalar rows in the cluster-sorted copy), tiles past the last row
     (1501, 65, 9, 12, 128),      # odd width: scalar staging
 ]
 
