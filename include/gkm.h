@@ -248,6 +248,52 @@ GK_API int gk_kmeans_fit(const float *X, int64_t n, int64_t d, int64_t ld, int32
                          size_t ws_bytes, void *stream);
 
 /*
+ * Batches of independent clustering jobs (batching; the paper clusters one
+ * data set): several jobs with the same row width d and kappa run as one
+ * problem, so every kernel launch of the path serves all of them.  Job j owns
+ * the samples first_j .. first_j + n_j - 1 of X (the jobs' samples
+ * concatenated in job order; first_0 = 0, first_{j+1} = first_j + n_j) and
+ * runs what gk_build_knn_graph and gk_kmeans_fit run for it alone: the graph
+ * construction (Alg. 3) at k0_j = max(1, floor(n_j / xi)) from graph_seed,
+ * then `iters` iterations of Alg. 2 at k_j clusters from the labels
+ * gk_init_labels(n_j, k_j, fit_seed) draws.  Each job's graph rows, labels,
+ * centroids and final distortion equal its solo results bit for bit: its rows,
+ * labels and clusters are numbered after the jobs before it, so no cluster and
+ * no graph row spans two jobs and every tie order is the solo one.
+ *   jobs        HOST gk_job[njobs], 1 <= njobs <= GK_MAX_BATCH_JOBS; for every
+ *               job n_j >= 2, kappa < n_j, k_j >= 1, reserved 0
+ *   p           kappa, xi, tau, max_cluster, precision as for
+ *               gk_build_knn_graph (p->seed is not used: seeds are per job)
+ *   g_idx, g_dist  device [N x kappa], N = sum n_j: the constructed graph, ids
+ *               in batch numbering (job j's ids are first_j + its solo ids)
+ *   labels_out  device int32[N]: job j's final labels in [0, k_j)
+ *   C_out       device float[(sum k_j) x d]: job j's centroids in rows
+ *               sum_{i<j} k_i .. + k_j - 1
+ *   distortion  device double[njobs]: each job's final distortion (Eq. 4)
+ *   ws          gk_workspace_size_batch(d, njobs, jobs, p) bytes
+ * With gk_set_replay on, a call whose arguments and job table equal an
+ * earlier call's replays its captured CUDA graph.
+ */
+#define GK_MAX_BATCH_JOBS 64
+
+typedef struct {
+    int64_t n;           /* samples of the job                                           */
+    int32_t k;           /* clusters of its fit                                          */
+    int32_t reserved;    /* must be 0                                                    */
+    uint64_t graph_seed; /* seed of its random initial graph and labels at k0            */
+    uint64_t fit_seed;   /* seed of its initial labels at k                              */
+} gk_job;
+
+GK_API size_t gk_workspace_size_batch(int64_t d, int32_t njobs, const gk_job *jobs, const gk_graph_params *p);
+GK_API int gk_batch_fit(const float *X, int64_t d, int64_t ld, int32_t njobs, const gk_job *jobs,
+                        const gk_graph_params *p, int32_t iters, int32_t *g_idx, float *g_dist, int32_t *labels_out,
+                        float *C_out, double *distortion, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_batch_fit_bf16(const uint16_t *X, int64_t d, int64_t ld, int32_t njobs, const gk_job *jobs,
+                             const gk_graph_params *p, int32_t iters, int32_t *g_idx, float *g_dist,
+                             int32_t *labels_out, float *C_out, double *distortion, void *ws, size_t ws_bytes,
+                             void *stream);
+
+/*
  * gk_update_step without a workspace, for callers that cannot allocate device
  * memory: for instance an application whose framework owns all device memory
  * through its own pool and forbids raw cudaMalloc, or a latency-bound serving

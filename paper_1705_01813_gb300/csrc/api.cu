@@ -11,6 +11,7 @@
 #include <utility>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 
 using namespace gkm;
@@ -114,7 +115,7 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     if (need_assign)
         L.asg_scratch = cv.take<char>(assign_scratch_bytes(n, k, d));
     if (op == GK_OP_REFINE || op == GK_OP_BUILD)
-        L.ref_scratch = cv.take<char>(refine_scratch_bytes(n, k));
+        L.ref_scratch = cv.take<char>(refine_scratch_bytes(n, k, d));
     if (op == GK_OP_FIT || op == GK_OP_BUILD) {
         L.labels_b = cv.take<int32_t>((size_t)n);
         L.elog = cv.take<double>(MAX_LOG);
@@ -749,6 +750,167 @@ int gk_build_knn_graph_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld,
     return build_knn_graph_impl(X, true, n, d, ld, p, g_idx, g_dist, labels_out, e_log, ws, ws_bytes, stream);
 }
 
+
+// ---------------------------------------------------------------------------
+// Batches (gk_batch_fit): the jobs' samples are concatenated; job j's graph
+// rows, labels and clusters are shifted by its first sample, first cluster at
+// k0 and first cluster at k, so no cluster and no graph row spans two jobs and
+// every tie order ((distance, id), (distance, label)) is that of the job alone.
+// ---------------------------------------------------------------------------
+struct BatchDims {
+    BatchTable t{};      // samples and clusters at k (the fit)
+    int32_t k0first[MAX_BATCH_JOBS + 1];
+    int64_t N = 0;
+    int32_t K0 = 0, K = 0;
+};
+
+static int batch_dims(int32_t njobs, const gk_job *jobs, const gk_graph_params *p, BatchDims *bd)
+{
+    if (njobs < 1 || njobs > MAX_BATCH_JOBS)
+        return fail(GK_ERR_INVALID, "njobs = %d out of range [1, %d]", njobs, MAX_BATCH_JOBS);
+    if (!jobs || !p)
+        return fail(GK_ERR_INVALID, "jobs or params is NULL");
+    if (p->xi < 1)
+        return fail(GK_ERR_INVALID, "xi = %d < 1", p->xi);
+    int64_t N = 0, K0 = 0, K = 0;
+    bd->t.njobs = njobs;
+    for (int j = 0; j < njobs; j++) {
+        const gk_job &J = jobs[j];
+        if (J.n < 2 || J.k < 1 || J.reserved != 0 || (int64_t)p->kappa >= J.n)
+            return fail(GK_ERR_INVALID, "job %d: n = %lld, k = %d (need n >= 2, kappa < n, k >= 1, reserved 0)", j,
+                        (long long)J.n, J.k);
+        bd->t.first[j] = N;
+        bd->t.kfirst[j] = (int32_t)K;
+        bd->k0first[j] = (int32_t)K0;
+        N += J.n;
+        K0 += build_k0(J.n, p->xi);
+        K += J.k;
+        if (N >= MAX_ROWS || K0 >= INT32_MAX || K >= INT32_MAX)
+            return fail(GK_ERR_INVALID, "batch too large: %lld samples, %lld clusters", (long long)N, (long long)K);
+    }
+    bd->t.first[njobs] = N;
+    bd->t.kfirst[njobs] = (int32_t)K;
+    bd->k0first[njobs] = (int32_t)K0;
+    bd->N = N;
+    bd->K0 = (int32_t)K0;
+    bd->K = (int32_t)K;
+    return GK_OK;
+}
+
+static int batch_fit_impl(const void *X, bool bf16, int64_t d, int64_t ld, int32_t njobs, const gk_job *jobs,
+                          const gk_graph_params *p, int32_t iters, int32_t *g_idx, float *g_dist, int32_t *labels_out,
+                          float *C_out, double *distortion, void *ws, size_t ws_bytes, void *stream)
+{
+    BatchDims bd;
+    int rc;
+    if ((rc = batch_dims(njobs, jobs, p, &bd)))
+        return rc;
+    const int64_t N = bd.N;
+    if ((rc = check_x(X, bf16, N, d, ld, 2)) || (rc = check_kappa(p->kappa, N)))
+        return rc;
+    if (p->tau < 0 || p->max_cluster < 2 || p->precision < 0 || p->precision > 3 || p->reserved != 0)
+        return fail(GK_ERR_INVALID, "bad params (tau=%d max_cluster=%d precision=%d)", p->tau, p->max_cluster,
+                    p->precision);
+    if (bf16 && p->precision == 3)
+        return fail(GK_ERR_INVALID, "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    if (iters < 0)
+        return fail(GK_ERR_INVALID, "iters = %d < 0", iters);
+    if (!g_idx || !g_dist || !labels_out || !C_out || !distortion)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    const int32_t Km = bd.K0 > bd.K ? bd.K0 : bd.K;
+    Layout L = carve(nullptr, GK_OP_BUILD, N, d, Km);
+    if ((rc = check_ws(ws, ws_bytes, L.bytes)))
+        return rc;
+    L = carve(ws, GK_OP_BUILD, N, d, Km);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int es = bf16 ? 2 : 4;
+    const char *Xc = static_cast<const char *>(X);
+    auto enqueue = [&]() -> int {
+        int32_t *cur = L.labels_a, *nxt = L.labels_b;
+        // each job's random graph and labels at its k0, drawn on its own rows as alone, then shifted
+        for (int j = 0; j < njobs; j++) {
+            const int64_t f = bd.t.first[j], nj = jobs[j].n;
+            GK_CUDA(launch_init_graph(Xc + (size_t)f * (size_t)ld * es, bf16, nj, d, ld, p->kappa, jobs[j].graph_seed,
+                                      g_idx + f * p->kappa, g_dist + f * p->kappa, L.st, s, (int32_t)f));
+            GK_CUDA(launch_init_labels(nj, build_k0(nj, p->xi), jobs[j].graph_seed, cur + f, s, bd.k0first[j]));
+        }
+        // Alg. 3 over the whole batch at k0 = sum of the jobs' k0
+        GK_CUDA(cudaMemsetAsync(L.cent, 0, sizeof(float) * (size_t)bd.K0 * (size_t)d, s));
+        GK_CUDA(launch_group(cur, N, bd.K0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K0, L.cent, L.grp.counts, nullptr,
+                              L.upd_scratch, L.st, s));
+        for (int t = 0; t < p->tau; t++) {
+            GK_CUDA(launch_assign(X, bf16, N, d, ld, g_idx, p->kappa, L.cent, bd.K0, cur, nxt, nullptr, nullptr,
+                                  nullptr, L.asg_scratch, L.st, s, p->precision, L.grp.members));
+            GK_CUDA(launch_group(nxt, N, bd.K0, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+            GK_CUDA(launch_update(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K0, L.cent, L.grp.counts,
+                                  nullptr, L.upd_scratch, L.st, s));
+            GK_CUDA(launch_refine(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K0, p->kappa, p->max_cluster,
+                                  g_idx, g_dist, L.ref_scratch, L.st, s, p->precision));
+            int32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        // Alg. 2 at each job's k from its own seeded labels
+        for (int j = 0; j < njobs; j++) {
+            const int64_t f = bd.t.first[j];
+            GK_CUDA(launch_init_labels(jobs[j].n, jobs[j].k, jobs[j].fit_seed, cur + f, s, bd.t.kfirst[j]));
+        }
+        GK_CUDA(cudaMemsetAsync(C_out, 0, sizeof(float) * (size_t)bd.K * (size_t)d, s));
+        GK_CUDA(launch_group(cur, N, bd.K, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+        GK_CUDA(launch_update(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K, C_out, L.grp.counts, nullptr,
+                              L.upd_scratch, L.st, s));
+        for (int t = 0; t < iters; t++) {
+            GK_CUDA(launch_assign(X, bf16, N, d, ld, g_idx, p->kappa, C_out, bd.K, cur, nxt, nullptr, nullptr, nullptr,
+                                  L.asg_scratch, L.st, s, p->precision, L.grp.members));
+            GK_CUDA(launch_group(nxt, N, bd.K, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st, s));
+            GK_CUDA(launch_update(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K, C_out, L.grp.counts,
+                                  nullptr, L.upd_scratch, L.st, s));
+            int32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        // each job's distortion from the last update's per-cluster terms, and labels in each job's numbering
+        GK_CUDA(launch_batch_distortion(update_contrib(L.upd_scratch), bd.t, distortion, s));
+        GK_CUDA(launch_batch_labels(cur, N, bd.t, labels_out, s));
+        return GK_OK;
+    };
+    std::vector<uint64_t> key = {3, u64(X), (uint64_t)bf16, (uint64_t)d, (uint64_t)ld, (uint64_t)njobs,
+                                 (uint64_t)p->kappa, (uint64_t)p->xi, (uint64_t)p->tau, (uint64_t)p->max_cluster,
+                                 (uint64_t)p->precision, (uint64_t)iters, u64(g_idx), u64(g_dist), u64(labels_out),
+                                 u64(C_out), u64(distortion), u64(ws), (uint64_t)ws_bytes};
+    for (int j = 0; j < njobs; j++) {
+        key.push_back((uint64_t)jobs[j].n);
+        key.push_back((uint64_t)jobs[j].k);
+        key.push_back(jobs[j].graph_seed);
+        key.push_back(jobs[j].fit_seed);
+    }
+    return enqueue_or_replay(key, s, enqueue);
+}
+
+size_t gk_workspace_size_batch(int64_t d, int32_t njobs, const gk_job *jobs, const gk_graph_params *p)
+{
+    BatchDims bd;
+    if (d < 1 || batch_dims(njobs, jobs, p, &bd) != GK_OK)
+        return 0;
+    return carve(nullptr, GK_OP_BUILD, bd.N, d, bd.K0 > bd.K ? bd.K0 : bd.K).bytes;
+}
+
+int gk_batch_fit(const float *X, int64_t d, int64_t ld, int32_t njobs, const gk_job *jobs,
+                 const gk_graph_params *p, int32_t iters, int32_t *g_idx, float *g_dist, int32_t *labels_out,
+                 float *C_out, double *distortion, void *ws, size_t ws_bytes, void *stream)
+{
+    return batch_fit_impl(X, false, d, ld, njobs, jobs, p, iters, g_idx, g_dist, labels_out, C_out, distortion, ws,
+                          ws_bytes, stream);
+}
+
+int gk_batch_fit_bf16(const uint16_t *X, int64_t d, int64_t ld, int32_t njobs, const gk_job *jobs,
+                      const gk_graph_params *p, int32_t iters, int32_t *g_idx, float *g_dist, int32_t *labels_out,
+                      float *C_out, double *distortion, void *ws, size_t ws_bytes, void *stream)
+{
+    return batch_fit_impl(X, true, d, ld, njobs, jobs, p, iters, g_idx, g_dist, labels_out, C_out, distortion, ws,
+                          ws_bytes, stream);
+}
 
 static int graph_recall_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
                              int32_t kappa, const int32_t *queries, int32_t m, int32_t *nn_idx, float *nn_dist,

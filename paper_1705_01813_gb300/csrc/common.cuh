@@ -188,9 +188,12 @@ cudaError_t launch_tree(const void *X, bool bf16, int64_t n, int64_t d, int64_t 
 
 // Internal launchers (each returns cudaError_t of the launch).  Those that read the samples take them as
 // X (FP32, or BF16 when bf16 is set) with leading dimension ld in elements.
-cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s);
+// (label_offset / id_offset are added to every label / neighbour id written: a job's numbering inside a batch)
+cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s,
+                               int32_t label_offset = 0);
 cudaError_t launch_init_graph(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t kappa,
-                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s);
+                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s,
+                              int32_t id_offset = 0);
 
 // Grouping of samples by label (CSR).  Scratch sizes via group_scratch_bytes().
 size_t group_scratch_bytes(int64_t n, int32_t k);
@@ -202,6 +205,15 @@ size_t scan_scratch_bytes(int64_t count);
 cudaError_t launch_scan(const int32_t *in, int32_t *out, int64_t count, void *scratch, cudaStream_t s);
 
 size_t update_scratch_bytes(int64_t n, int32_t k);
+// the per-cluster distortion terms the last launch_update left in its scratch (k doubles)
+const double *update_contrib(const void *scratch);
+// distortion of each job of a batch from those terms: the FP64 sum of its clusters' terms in the order of the
+// update's own sum (one block per job, the same tree), divided by the job's samples (batch.cu)
+struct BatchTable;
+cudaError_t launch_batch_distortion(const double *contrib, const BatchTable &t, double *out, cudaStream_t s);
+// labels of a batch back to each job's numbering: labels_out[i] = labels[i] - (first cluster of i's job)
+cudaError_t launch_batch_labels(const int32_t *labels, int64_t N, const BatchTable &t, int32_t *labels_out,
+                                cudaStream_t s);
 cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
                           void *scratch, DevStatus *st, cudaStream_t s);
@@ -217,12 +229,12 @@ cudaError_t launch_assign(const void *X, bool bf16, int64_t n, int64_t d, int64_
 
 void set_last_error(const char *msg);
 
-size_t refine_scratch_bytes(int64_t n, int32_t k);
+size_t refine_scratch_bytes(int64_t n, int32_t k, int64_t d);
 // precision 0: FP32 pair distances on the SIMT cores; 1: tensor-core Gram with exact FP32 rerank
 cudaError_t launch_refine(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                           const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                           float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision);
-size_t refine_tc_scratch_bytes(int64_t n, int32_t k);
+size_t refine_tc_scratch_bytes(int64_t n, int32_t k, int64_t d);
 cudaError_t launch_refine_tc(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                              const int32_t *members, const int32_t *run_off, const int32_t *run_cl, int32_t k,
                              int32_t kappa, int32_t max_cluster, int64_t grid, int32_t *g_idx, float *g_dist,

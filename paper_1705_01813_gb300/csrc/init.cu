@@ -7,20 +7,21 @@
 
 namespace gkm {
 
-__global__ void k_init_labels(int64_t n, int32_t k, uint64_t key, int32_t *__restrict__ labels)
+__global__ void k_init_labels(int64_t n, int32_t k, uint64_t key, int32_t off, int32_t *__restrict__ labels)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        labels[i] = (int32_t)(sm64_draw(key, (uint64_t)i) % (uint64_t)k);
+        labels[i] = (int32_t)(sm64_draw(key, (uint64_t)i) % (uint64_t)k) + off;
 }
 
-cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s)
+cudaError_t launch_init_labels(int64_t n, int32_t k, uint64_t seed, int32_t *labels, cudaStream_t s,
+                               int32_t label_offset)
 {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 64)
         blocks = 152 * 64;
     if (blocks < 1)
         blocks = 1;
-    k_init_labels<<<(unsigned)blocks, 256, 0, s>>>(n, k, seed ^ TAG_LABELS, labels);
+    k_init_labels<<<(unsigned)blocks, 256, 0, s>>>(n, k, seed ^ TAG_LABELS, label_offset, labels);
     return cudaGetLastError();
 }
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ void ld16(const XT *p, float (&v)[16 / sizeof(XT)])
 template <typename XT>
 __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__restrict__ X, int64_t n, int d,
                                                               int64_t ld, int kappa, uint64_t key, uint64_t minv,
-                                                              int32_t *__restrict__ g_idx,
+                                                              int32_t id_off, int32_t *__restrict__ g_idx,
                                                               float *__restrict__ g_dist, DevStatus *st, bool vec)
 {
     constexpr int RS = ig_stride<XT>(), E = 16 / (int)sizeof(XT);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__res
             int r = 0;
             for (int p = 0; p < kappa; p++)
                 r += rkey[p] < kq ? 1 : 0;
-            g_idx[out + r] = key_id(kq);
+            g_idx[out + r] = key_id(kq) + id_off;
             g_dist[out + r] = key_dist(kq);
         }
         __syncwarp();
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__res
 
 template <typename XT>
 static cudaError_t init_graph_t(const XT *X, int64_t n, int64_t d, int64_t ld, int32_t kappa, uint64_t seed,
-                                int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
+                                int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s, int32_t id_offset)
 {
     int64_t blocks = (n + IG_WARPS - 1) / IG_WARPS;
     if (blocks > 152 * 64)
@@ -241,16 +242,18 @@ static cudaError_t init_graph_t(const XT *X, int64_t n, int64_t d, int64_t ld, i
         return e;
     const uint64_t minv = ~0ull / (uint64_t)n;
     k_init_graph<XT><<<(unsigned)blocks, IG_WARPS * 32, shm, s>>>(X, n, (int)d, ld, kappa, seed ^ TAG_GRAPH, minv,
-                                                               g_idx, g_dist, st, vec);
+                                                               id_offset, g_idx, g_dist, st, vec);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_graph(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t kappa,
-                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s)
+                              uint64_t seed, int32_t *g_idx, float *g_dist, DevStatus *st, cudaStream_t s,
+                              int32_t id_offset)
 {
     if (bf16)
-        return init_graph_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s);
-    return init_graph_t(static_cast<const float *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s);
+        return init_graph_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s,
+                            id_offset);
+    return init_graph_t(static_cast<const float *>(X), n, d, ld, kappa, seed, g_idx, g_dist, st, s, id_offset);
 }
 
 }  // namespace gkm

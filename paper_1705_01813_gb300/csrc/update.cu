@@ -332,6 +332,8 @@ __global__ void __launch_bounds__(1024) k_sum_f64(const double *__restrict__ v, 
 
 size_t update_scratch_bytes(int64_t, int32_t k) { return ((size_t)k * sizeof(double) + 255) & ~size_t(255); }
 
+const double *update_contrib(const void *scratch) { return static_cast<const double *>(scratch); }
+
 template <typename XT>
 static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *offsets, const int32_t *members,
                             int32_t k, float *C, int32_t *counts, double *sum_d2, void *scratch, DevStatus *st,

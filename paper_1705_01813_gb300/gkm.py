@@ -27,11 +27,11 @@ EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_siz
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
            "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall",
-           "gk_set_replay", "gk_two_means_tree"]
+           "gk_set_replay", "gk_two_means_tree", "gk_workspace_size_batch", "gk_batch_fit"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
              "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall",
-             "gk_two_means_tree"]
+             "gk_two_means_tree", "gk_batch_fit"]
 EXPORTS += [name + "_bf16" for name in X_ENTRIES]
 
 
@@ -39,6 +39,15 @@ class GraphParams(ctypes.Structure):
     _fields_ = [("kappa", ctypes.c_int32), ("xi", ctypes.c_int32), ("tau", ctypes.c_int32),
                 ("max_cluster", ctypes.c_int32), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Job(ctypes.Structure):
+    """One job of a batch (gk_job): n samples, k clusters, the seeds of its graph construction and its fit."""
+    _fields_ = [("n", ctypes.c_int64), ("k", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("graph_seed", ctypes.c_uint64), ("fit_seed", ctypes.c_uint64)]
+
+
+MAX_BATCH_JOBS = 64  # GK_MAX_BATCH_JOBS
 
 
 class GkError(RuntimeError):
@@ -85,10 +94,15 @@ def load(build_if_missing: bool = True):
             L.gk_graph_recall.argtypes = [P, I64, I64, I64, P, I32, P, I32, P, P, P, P, SZ, P]
             L.gk_set_replay.argtypes = [I32]
             L.gk_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P, P, SZ, P]
+            L.gk_workspace_size_batch.restype = SZ
+            L.gk_workspace_size_batch.argtypes = [I64, I32, P, ctypes.POINTER(GraphParams)]
+            L.gk_batch_fit.argtypes = [P, I64, I64, I32, P, ctypes.POINTER(GraphParams), I32, P, P, P, P, P, P, SZ,
+                                       P]
             for name in X_ENTRIES:
                 getattr(L, name + "_bf16").argtypes = getattr(L, name).argtypes
             for name in EXPORTS:
-                if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build"):
+                if name not in ("gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build",
+                                "gk_workspace_size_batch"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -291,6 +305,46 @@ def kmeans_fit(X, k: int, g_idx, iters: int, init_labels=None, seed: int = 0, la
                                 precision, _ptr(labels_out), _ptr(C_out), _ptr(counts_out), log, ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return labels_out, C_out, counts_out, (list(log) if want_log else None)
+
+
+def _jobs(jobs) -> "ctypes.Array":
+    """A gk_job array from (n, k, graph_seed, fit_seed) tuples."""
+    arr = (Job * len(jobs))()
+    for a, (n, k, gs, fs) in zip(arr, jobs):
+        a.n, a.k, a.reserved, a.graph_seed, a.fit_seed = int(n), int(k), 0, int(gs), int(fs)
+    return arr
+
+
+def workspace_size_batch(d: int, jobs, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int = 128,
+                         precision: int = 0) -> int:
+    p = GraphParams(kappa, xi, tau, max_cluster, 0, precision, 0)
+    return int(load().gk_workspace_size_batch(d, len(jobs), ctypes.cast(_jobs(jobs), ctypes.c_void_p),
+                                              ctypes.byref(p)))
+
+
+def batch_fit(X, jobs, kappa: int, xi: int = 50, tau: int = 10, max_cluster: int = 128, iters: int = 10,
+              precision: int = 0, g_idx=None, g_dist=None, labels_out=None, C_out=None, distortion=None,
+              ws: Workspace | None = None, stream=None):
+    """Independent jobs as one batch (gk_batch_fit): X holds the jobs' samples concatenated, jobs is a list of
+    (n, k, graph_seed, fit_seed).  Returns (g_idx, g_dist, labels (each job's own numbering), centroids (jobs'
+    rows stacked), distortion [njobs] FP64 on the device)."""
+    N, d, ld = _x(X)
+    if sum(int(j[0]) for j in jobs) != N:
+        raise ValueError("the jobs' sample counts must add up to X's rows")
+    dev = X.device
+    K = sum(int(j[1]) for j in jobs)
+    p = GraphParams(kappa, xi, tau, max_cluster, 0, precision, 0)
+    arr = _jobs(jobs)
+    g_idx = torch.empty((N, kappa), dtype=torch.int32, device=dev) if g_idx is None else g_idx
+    g_dist = torch.empty((N, kappa), dtype=torch.float32, device=dev) if g_dist is None else g_dist
+    labels_out = torch.empty(N, dtype=torch.int32, device=dev) if labels_out is None else labels_out
+    C_out = torch.empty((K, d), dtype=torch.float32, device=dev) if C_out is None else C_out
+    distortion = torch.empty(len(jobs), dtype=torch.float64, device=dev) if distortion is None else distortion
+    ws = ws or workspace(workspace_size_batch(d, jobs, kappa, xi, tau, max_cluster, precision), dev)
+    _check(_entry("gk_batch_fit", X)(_ptr(X), d, ld, len(jobs), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(p),
+                                     iters, _ptr(g_idx), _ptr(g_dist), _ptr(labels_out), _ptr(C_out),
+                                     _ptr(distortion), ws.ptr, ws.nbytes, _stream(stream)))
+    return g_idx, g_dist, labels_out, C_out, distortion
 
 
 def group_by_label(labels, k: int, offsets=None, members=None, counts=None, ws: Workspace | None = None,

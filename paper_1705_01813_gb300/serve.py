@@ -111,9 +111,22 @@ class Arena:
         self.buf = None
         self.off = 0
 
+    @property
+    def capacity(self) -> int:
+        """Bytes this arena holds on the device."""
+        return 0 if self.buf is None else int(self.buf.numel())
+
+    def release(self):
+        """Give the buffer up (the caller returns it to the device with torch.cuda.empty_cache())."""
+        self.buf = None
+        self.off = 0
+
     def reset(self, nbytes: int):
         if self.buf is None or self.buf.numel() < nbytes:
+            replaced = self.buf is not None
             self.buf = None
+            if replaced:  # the smaller buffer goes back to the device, not to the allocator's cache
+                torch.cuda.empty_cache()
             self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
         self.off = 0
 
@@ -177,47 +190,37 @@ def build_k0(n: int, xi: int) -> int:
     return max(1, n // xi)
 
 
-def _batch_dims(specs: list[JobSpec], p: ServeParams):
-    ns = [s.n for s in specs]
-    k0s = [build_k0(n, p.xi) for n in ns]
-    ks = [s.k for s in specs]
-    noff, k0off, koff = [0], [0], [0]
-    for n, a, b in zip(ns, k0s, ks):
-        noff.append(noff[-1] + n)
-        k0off.append(k0off[-1] + a)
-        koff.append(koff[-1] + b)
-    return k0s, noff, k0off, koff
+def _batch_jobs(specs: list[JobSpec]) -> list[tuple]:
+    """gk_batch_fit's job table: (n, k, graph seed, fit seed); a job's fit starts from init_labels(seed + 1) as in
+    run_job."""
+    return [(s.n, s.k, s.seed, s.seed + 1) for s in specs]
 
 
-def _batch_ws_bytes(N: int, d: int, K: int, kappa: int) -> int:
-    return max(gkm.workspace_size(gkm.GK_OP_FIT, N, d, K, kappa), gkm.workspace_size(gkm.GK_OP_REFINE, N, d, K, kappa))
+def _batch_ws_bytes(specs: list[JobSpec], p: ServeParams) -> int:
+    return gkm.workspace_size_batch(specs[0].d, _batch_jobs(specs), specs[0].kappa, p.xi, p.tau, p.max_cluster,
+                                    p.precision)
 
 
 def batch_bytes(specs: list[JobSpec], p: ServeParams) -> int:
     """Device bytes of a batch (what run_batch takes from its slot's arena)."""
-    _, noff, k0off, koff = _batch_dims(specs, p)
-    N, K0, K = noff[-1], k0off[-1], koff[-1]
+    N, K = sum(s.n for s in specs), sum(s.k for s in specs)
     d, kappa = specs[0].d, specs[0].kappa
-    Km = max(K0, K)
-    return (N * d * 4 + 8 * max(s.n for s in specs) + N * kappa * 8 + 3 * N * 4 + (Km + 1) * 4 + Km * 4 + 16
-            + (K0 + K) * d * 4 + _batch_ws_bytes(N, d, Km, kappa) + 16 * 256)
+    return (N * d * 4 + 8 * max(s.n for s in specs) + N * kappa * 8 + N * 4 + K * d * 4 + 8 * len(specs)
+            + _batch_ws_bytes(specs, p) + 16 * 256)
 
 
 def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.Stream, arena: Arena | None = None):
-    """Jobs of one row width d and one kappa as one problem.  Their samples are concatenated; each
-    job's random graph and labels are drawn on its own slice (as alone) and shifted by the job's
-    first sample and first cluster.  No cluster and no graph row then spans two jobs, and the
-    shifts keep every tie order ((distance, id) in rows, (distance, label) in assignments), so each
-    launch of the assignment, grouping, update and refinement serves all jobs at once and every
-    job gets the labels and centroids it gets alone.  All tensors come from `arena` (a private one
-    when none is given).  Returns [(distortion, labels, centroids)], the last two views into the
-    arena."""
+    """Jobs of one row width d and one kappa as one problem, through the library's batched call (gk_batch_fit):
+    their samples are concatenated, each kernel launch serves all of them, and each job gets the graph, labels,
+    centroids and distortion it gets alone, bit for bit (the library numbers each job's rows and clusters after
+    the jobs before it and draws its random start on its own rows).  All tensors come from `arena` (a private
+    one when none is given).  Returns [(distortion, labels, centroids)], the last two views into the arena."""
     d, kappa = specs[0].d, specs[0].kappa
     if any(s.d != d or s.kappa != kappa for s in specs):
         raise ValueError("a batch holds jobs of one row width and one kappa")
-    k0s, noff, k0off, koff = _batch_dims(specs, p)
-    N, K0, K = noff[-1], k0off[-1], koff[-1]
-    Km = max(K0, K)
+    if len(specs) > gkm.MAX_BATCH_JOBS:
+        raise ValueError(f"a batch holds at most {gkm.MAX_BATCH_JOBS} jobs")
+    N, K = sum(s.n for s in specs), sum(s.k for s in specs)
     i32, f32 = torch.int32, torch.float32
     arena = arena or Arena(device)
     with torch.cuda.stream(stream):
@@ -225,67 +228,40 @@ def run_batch(specs: list[JobSpec], p: ServeParams, device, stream: torch.cuda.S
         X = arena.take((N, d), f32)
         z = arena.take((max(s.n for s in specs),), torch.int64)
         gi, gd = arena.take((N, kappa), i32), arena.take((N, kappa), f32)
-        la, lb, mem = arena.take((N,), i32), arena.take((N,), i32), arena.take((N,), i32)
-        off, cnt = arena.take((Km + 1,), i32), arena.take((Km,), i32)
-        sd = arena.take((2,), torch.float64)
-        C0, C = arena.take((K0, d), f32), arena.take((K, d), f32)
-        ws = arena.workspace(_batch_ws_bytes(N, d, Km, kappa), stream)
-        for j, s in enumerate(specs):  # per job: samples, random graph, initial labels at k0
-            sl = slice(noff[j], noff[j + 1])
-            job_data(s, device, out=X[sl], z_out=z[:s.n])
-            gkm.init_graph(X[sl], kappa, s.seed, gi[sl], gd[sl], ws=ws, stream=stream)
-            gi[sl] += noff[j]
-            gkm.init_labels(s.n, k0s[j], s.seed, out=la[sl], stream=stream)
-            la[sl] += k0off[j]
-        # Alg. 3 on the whole batch
-        C0.zero_()
-        gkm.group_by_label(la, K0, off, mem, cnt, ws=ws, stream=stream)
-        gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
-        cur, nxt = la, lb
-        for _ in range(p.tau):
-            gkm.assign_step(X, gi, C0, cur, nxt, None, sd[1:2], None, p.precision, mem, ws=ws, stream=stream)
-            gkm.group_by_label(nxt, K0, off, mem, cnt, ws=ws, stream=stream)
-            gkm.update_from_groups(X, off, mem, K0, C0, cnt, sd[0:1], ws=ws, stream=stream)
-            gkm.graph_refine_groups(X, off, mem, K0, gi, gd, p.max_cluster, p.precision, ws=ws, stream=stream)
-            cur, nxt = nxt, cur
-        # the fit at each job's k, from each job's seeded labels
-        cur, nxt = la, lb
-        for j, s in enumerate(specs):
-            sl = slice(noff[j], noff[j + 1])
-            gkm.init_labels(s.n, s.k, s.seed + 1, out=cur[sl], stream=stream)
-            cur[sl] += koff[j]
-        C.zero_()
-        gkm.group_by_label(cur, K, off, mem, cnt, ws=ws, stream=stream)
-        gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
-        for _ in range(p.iters):
-            gkm.assign_step(X, gi, C, cur, nxt, None, sd[1:2], None, p.precision, mem, ws=ws, stream=stream)
-            gkm.group_by_label(nxt, K, off, mem, cnt, ws=ws, stream=stream)
-            gkm.update_from_groups(X, off, mem, K, C, cnt, sd[0:1], ws=ws, stream=stream)
-            cur, nxt = nxt, cur
-        # per job: labels back to the job's numbering, distortion (mean squared distance to the own
-        # centroid, FP64 sums over chunks of rows)
-        out = []
-        step = 1 << 16
-        for j, s in enumerate(specs):
-            sl = slice(noff[j], noff[j + 1])
-            cur[sl] -= koff[j]
-            Cj = C[koff[j]:koff[j + 1]]
-            E = torch.zeros((), dtype=torch.float64, device=device)
-            for c0 in range(noff[j], noff[j + 1], step):
-                c1 = min(noff[j + 1], c0 + step)
-                E += ((X[c0:c1].double() - Cj[cur[c0:c1].long()].double()) ** 2).sum()
-            out.append((E / s.n, cur[sl], Cj))
-        stream.synchronize()
-        return [(float(E), lab, Cj) for E, lab, Cj in out]
+        lab = arena.take((N,), i32)
+        C = arena.take((K, d), f32)
+        dist = arena.take((len(specs),), torch.float64)
+        ws = arena.workspace(_batch_ws_bytes(specs, p), stream)
+        first = 0
+        for s in specs:  # each job's samples, generated on its own rows
+            job_data(s, device, out=X[first:first + s.n], z_out=z[:s.n])
+            first += s.n
+        gkm.batch_fit(X, _batch_jobs(specs), kappa, xi=p.xi, tau=p.tau, max_cluster=p.max_cluster, iters=p.iters,
+                      precision=p.precision, g_idx=gi, g_dist=gd, labels_out=lab, C_out=C, distortion=dist, ws=ws,
+                      stream=stream)
+    stream.synchronize()
+    E = dist.cpu().tolist()
+    out, first, kfirst = [], 0, 0
+    for j, s in enumerate(specs):
+        out.append((E[j], lab[first:first + s.n], C[kfirst:kfirst + s.k]))
+        first += s.n
+        kfirst += s.k
+    return out
 
 
 class Server:
-    """Admits jobs by HBM budget and slots, runs each on its own stream, records latencies."""
+    """Admits jobs by HBM budget and slots, runs each on its own stream, records latencies.
+
+    The budget bounds the device memory the slots' arenas hold, idle or not: a job (or batch) is admitted to a
+    free slot only when the arenas, with that slot's grown to the job's size, fit in the budget; idle slots'
+    arenas are released (largest first) to make room, and a replaced or released buffer goes back to the
+    device.  `max_held` is the most the arenas held at once over the server's runs."""
 
     def __init__(self, params: ServeParams | None = None, device=None):
         self.p = params or ServeParams()
         self.device = _device(device)
         self.arenas: list[Arena] = []  # one per slot, kept across runs
+        self.max_held = 0
         gkm.load()
 
     def run(self, specs: list[JobSpec], realtime: bool = True) -> list[JobResult]:
@@ -297,15 +273,16 @@ class Server:
             if need > p.budget_bytes:
                 raise ValueError(f"job {s.jid} needs {need} bytes, more than the budget")
         lock = threading.Condition()
-        state = {"used": 0, "inflight": 0, "error": None}
+        state = {"inflight": 0, "error": None}
         results: dict[int, JobResult] = {}
         streams = [torch.cuda.Stream(device=self.device) for _ in range(p.slots)]
         while len(self.arenas) < p.slots:
             self.arenas.append(Arena(self.device))
+        held = [a.capacity for a in self.arenas]  # bytes each slot's arena holds or is about to hold
         free_streams = list(range(p.slots))
         t0 = time.perf_counter()
 
-        def worker(batch: list[JobSpec], si: int, start: float, nbytes: int):
+        def worker(batch: list[JobSpec], si: int, start: float):
             try:
                 torch.cuda.set_device(self.device)
                 if p.batching:
@@ -328,7 +305,6 @@ class Server:
             with lock:
                 for r in res or []:
                     results[r.jid] = r
-                state["used"] -= nbytes
                 state["inflight"] -= 1
                 free_streams.append(si)
                 lock.notify_all()
@@ -363,15 +339,34 @@ class Server:
                     continue
                 batch = next_batch(now)
                 nbytes = batch_bytes(batch, p) if p.batching else job_bytes(s, p)
-                if state["inflight"] >= p.slots or state["used"] + nbytes > p.budget_bytes:
+                if state["inflight"] >= p.slots:
                     lock.wait(timeout=0.05)
                     continue
+                # the free slot whose arena already holds the job (the smallest such), else the largest one
+                fits = [j for j in free_streams if held[j] >= nbytes]
+                si = min(fits, key=lambda j: held[j]) if fits else max(free_streams, key=lambda j: held[j])
+                need = sum(held) - held[si] + max(held[si], nbytes)
+                if need > p.budget_bytes:
+                    released = False
+                    for sj in sorted((j for j in free_streams if j != si and held[j] > 0), key=lambda j: -held[j]):
+                        if need <= p.budget_bytes:
+                            break
+                        self.arenas[sj].release()
+                        need -= held[sj]
+                        held[sj] = 0
+                        released = True
+                    if released:
+                        torch.cuda.empty_cache()
+                    if need > p.budget_bytes:
+                        lock.wait(timeout=0.05)
+                        continue
+                held[si] = max(held[si], nbytes)
+                self.max_held = max(self.max_held, sum(held))
                 for b in batch:
                     queue.remove(b)
-                state["used"] += nbytes
                 state["inflight"] += 1
-                si = free_streams.pop()
-                th = threading.Thread(target=worker, args=(batch, si, now, nbytes), daemon=True)
+                free_streams.remove(si)
+                th = threading.Thread(target=worker, args=(batch, si, now), daemon=True)
                 th.start()
                 threads.append(th)
         for th in threads:

@@ -64,6 +64,31 @@ def test_admission_keeps_budget_and_slots():
 
 
 @pytest.mark.gpu
+def test_admission_counts_the_arenas_the_slots_hold():
+    """The budget bounds what the slots' arenas hold, idle or not: after two big jobs grew two arenas, small jobs
+    reuse those or wait, and never make the arenas hold more than the budget."""
+    big = _specs([(40000, 128)] * 2)
+    small = [serve.JobSpec(10 + i, 0.0, 20000, 64, 200, 20, 2000 + i) for i in range(6)]
+    p = serve.ServeParams(slots=4)
+    p.budget_bytes = 2 * serve.job_bytes(big[0], p) + serve.job_bytes(small[0], p) // 2
+    srv = serve.Server(p)
+    srv.run(big, realtime=False)
+    assert sum(a.capacity for a in srv.arenas) == 2 * serve.job_bytes(big[0], p)
+    res = srv.run(small, realtime=False)
+    assert len(res) == 6 and _peak_in_flight(res) <= 2
+    assert srv.max_held <= p.budget_bytes
+    assert sum(a.capacity for a in srv.arenas) <= p.budget_bytes
+    # a job that needs a larger arena makes the server release an idle one first
+    p2 = serve.ServeParams(slots=2, budget_bytes=serve.job_bytes(big[0], p) + serve.job_bytes(small[0], p) // 2)
+    srv2 = serve.Server(p2)
+    srv2.run(small[:2], realtime=False)
+    assert sorted(a.capacity for a in srv2.arenas) == [serve.job_bytes(small[0], p)] * 2
+    srv2.run(big[:1], realtime=False)
+    assert srv2.max_held <= p2.budget_bytes
+    assert sorted(a.capacity for a in srv2.arenas) == [0, serve.job_bytes(big[0], p)]
+
+
+@pytest.mark.gpu
 def test_stream_latency_counts_from_arrival():
     specs = _specs([(10000, 64)] * 4, arrival_gap=0.05)
     res = serve.Server(serve.ServeParams(slots=2)).run(specs, realtime=True)
