@@ -269,14 +269,16 @@ def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + 5 * _radix_passes(k)  # noqa: E731
     upd = 2
-    # assign (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core
-    # tiles, SIMT leftovers (3)
-    asg = 3 if precision < 2 else (4 if precision == 2 or w.d > 128 else 5)
-    # refine: run count, scan, run clusters, then Gram + exact recompute + merge (tensor cores) or the two FP32
-    # tile widths
-    ref = 1 + 3 + 1 + (3 if tc_refine(precision, w.d, w.storage) else 2)
-    graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg + grp(w.k0) + upd + ref)
-    fit = 1 + grp(w.k) + upd + w.iters * (asg + grp(w.k) + upd)
+
+    def asg(k):
+        # (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core tiles,
+        # SIMT leftovers (3)
+        return 3 if precision < 2 else (4 if precision == 2 or w.d > 128 else 5)
+    # refine: run count, scan, run clusters, then cluster-sorted copy + Gram + exact recompute + merge (tensor
+    # cores) or the two FP32 tile widths
+    ref = 1 + 3 + 1 + (4 if tc_refine(precision, w.d, w.storage) else 2)
+    graph = 1 + 1 + grp(w.k0) + upd + w.tau * (asg(w.k0) + grp(w.k0) + upd + ref)
+    fit = 1 + grp(w.k) + upd + w.iters * (asg(w.k) + grp(w.k) + upd)
     return graph + fit
 
 
@@ -313,7 +315,8 @@ def kernel_of(tag, precision=1, d=128, storage="f32"):
 
 
 # source file of each kernel whose DRAM traffic is recorded
-KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_rows_bf8": "assign.cu", "k_assign_tc": "assign_tc.cu", "k_update": "update.cu",
+KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_rows_bf8": "assign.cu", "k_assign_tc": "assign_tc.cu",
+                 "k_update": "update.cu",
                  "k_radix_scatter": "group.cu", "k_refine": "refine.cu", "k_refine_gram": "refine_tc.cu",
                  "k_refine_merge": "refine_tc.cu", "k_refine_exact": "refine_tc.cu", "k_init_graph": "init.cu"}
 
