@@ -71,10 +71,11 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=None,
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3, 4], default=None,
                     help="0 FP32 SIMT throughout; 1 tensor-core Gram + FP32 rerank in the refinement; 2 also "
-                         "BF16 screening in the assignment (SIMT); 3 the screening on the tensor cores (all give "
-                         "the same results).  Default: chosen by the autotuner (tune.py) on the workload's own "
+                         "BF16 screening in the assignment (SIMT); 3 the screening on the tensor cores; 4 int8 "
+                         "screening (SIMT) (all give the same results).  Default: chosen by the autotuner (tune.py) on "
+                         "the workload's own "
                          "graph and labels after the first warm-up step")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-tree", action="store_true",
@@ -268,12 +269,14 @@ def _radix_passes(k):
 def launches_per_step(w, precision):
     """Kernels of this library launched by one step (mirrors the library's launch sequence)."""
     grp = lambda k: 1 + 3 + 5 * _radix_passes(k)  # noqa: E731
-    upd = 2
+    # update: the warp-per-cluster kernel for clusters of at most 32 members (16-byte rows of at most 512 values),
+    # the block kernel for the others, the FP64 sum
+    upd = 3 if (w.d % 4 == 0 and w.d <= 512) else 2
 
     def asg(k):
-        # (then reduce and finish): kernel (0, 1); BF16 copy + screening kernel (2); BF16 copy, tensor-core tiles,
-        # SIMT leftovers (3)
-        return 3 if precision < 2 else (4 if precision == 2 or w.d > 128 else 5)
+        # (then reduce and finish): kernel (0, 1); shadow copy + screening kernel (2, 4); BF16 copy, tensor-core
+        # tiles, SIMT leftovers (3)
+        return 3 if precision < 2 else (4 if precision in (2, 4) or w.d > 128 else 5)
     # refine: run count, scan, run clusters, then cluster-sorted copy + Gram + exact recompute + merge (tensor
     # cores) or the two FP32 tile widths
     ref = 1 + 3 + 1 + (4 if tc_refine(precision, w.d, w.storage) else 2)
@@ -306,8 +309,8 @@ def tc_refine(precision, d, storage="f32"):
 def kernel_of(tag, precision=1, d=128, storage="f32"):
     if tag == "refine" and tc_refine(precision, d, storage):
         return "k_refine_gram"
-    if tag == "assign" and precision == 2:
-        return "k_assign_rows_bf8"
+    if tag == "assign" and precision in (2, 4):
+        return "k_assign_rows_scr"
     if tag == "assign" and precision == 3:
         return "k_assign_tc"
     return {"assign": "k_assign_rows", "update": "k_update", "group": "k_radix_scatter", "refine": "k_refine",
@@ -315,7 +318,7 @@ def kernel_of(tag, precision=1, d=128, storage="f32"):
 
 
 # source file of each kernel whose DRAM traffic is recorded
-KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_rows_bf8": "assign.cu", "k_assign_tc": "assign_tc.cu",
+KERNEL_SOURCE = {"k_assign_rows": "assign.cu", "k_assign_rows_scr": "assign.cu", "k_assign_tc": "assign_tc.cu",
                  "k_update": "update.cu",
                  "k_radix_scatter": "group.cu", "k_refine": "refine.cu", "k_refine_gram": "refine_tc.cu",
                  "k_refine_merge": "refine_tc.cu", "k_refine_exact": "refine_tc.cu", "k_init_graph": "init.cu"}
@@ -468,7 +471,8 @@ def run_gpu(args):
 
     # the plain FP32 path (SIMT pair distances) on the same workload, for comparison
     fp32_ms = None
-    if args.precision != 0 and not args.no_fp32_compare:
+    lvl = args.precision & 0xff  # the level; bits 8-15 carry the assignment's candidates per group
+    if lvl != 0 and not args.no_fp32_compare:
         path.precision = 0
         path.step()
         torch.cuda.synchronize()
@@ -597,17 +601,20 @@ def run_gpu(args):
         "precision": {0: "fp32 throughout",
                       1: "bf16 tcgen05 gram in the refinement with exact fp32 recompute inside its error bound",
                       2: "1 plus bf16 screening of assignment candidates (simt) with exact fp32 recompute",
-                      3: "1 plus bf16 tcgen05 screening of assignment candidates with exact fp32 recompute"}
-                     [args.precision],
+                      3: "1 plus bf16 tcgen05 screening of assignment candidates with exact fp32 recompute",
+                      4: "1 plus int8 (per-row scale) screening of assignment candidates (simt) with exact fp32 "
+                         "recompute"}
+                     [lvl],
+        "assign_group_width": (args.precision >> 8) & 0xff or None,
         "plain_fp32_ms_per_step": fp32_ms,
         "assign_samples_per_s": w.n / statistics.mean(assign_times) if assign_times else None,
         "per_call_ms": {t: round(1e3 * statistics.mean(v), 4) for t, v in per_tag.items()},
         "per_step_share": {t: round(v / sum(totals.values()), 4) for t, v in totals.items()},
-        "roofline": {"kernel": kernel_of(dom, args.precision, w.d, w.storage), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": kernel_of(dom, lvl, w.d, w.storage), "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": int(alg),
-                     "traffic": ncu_traffic(dom, w.name, args.precision, w.d, w.storage)},
-        "gpu_launches": launches_per_step(w, args.precision) * args.steps,
+                     "traffic": ncu_traffic(dom, w.name, lvl, w.d, w.storage)},
+        "gpu_launches": launches_per_step(w, lvl) * args.steps,
         "measured_ceilings": ceilings,
         "precision_tuning": tuning,
         "graph_recall_top1": recall,
@@ -626,7 +633,7 @@ def run_gpu(args):
     # (graph rounds at k0, fit iterations at k).  They come from L2 while the centroid table fits it and from
     # HBM otherwise; the probe kernels measure both gather ceilings on this GPU.
     if dom == "assign" and u:
-        row_b = 2 if args.precision >= 2 else 4
+        row_b = {2: 2, 3: 2, 4: 1}.get(lvl, 4)
         per = [(w.k0, u.get("build"), w.tau), (w.k, u.get("fit"), w.iters)]
         g_l2 = sum(w.n * uu * w.d * row_b * c for kk, uu, c in per if uu and kk * w.d * 4 <= L2_BYTES)
         g_hbm = sum(w.n * uu * w.d * row_b * c for kk, uu, c in per if uu and kk * w.d * 4 > L2_BYTES)

@@ -78,12 +78,13 @@ typedef struct {
     int32_t max_cluster; /* a cluster larger than this is cut into runs of consecutive
                             members (ascending id) whose sizes differ by at most one    */
     uint64_t seed;       /* seed of the random initial graph and labels (SplitMix64)    */
-    int32_t precision;   /* 0: FP32 throughout; 1: refinement pair distances from a BF16
-                            Gram on the tensor cores with an exact FP32 recompute of the
-                            pairs inside its error bound (64 <= d <= 128; other widths
-                            use the FP32 kernels); 2 and 3: 1 and the assignment's
-                            BF16 screening as in gk_assign_step.  All give the same
-                            graph.                                                      */
+    int32_t precision;   /* bits 0-7: 0: FP32 throughout; 1: refinement pair distances from
+                            a BF16 Gram on the tensor cores with an exact FP32 recompute
+                            of the pairs inside its error bound (64 <= d <= 128; other
+                            widths use the FP32 kernels); 2, 3 and 4: 1 and the
+                            assignment's screening as in gk_assign_step.  Bits 8-15:
+                            the assignment's candidates per group, as there.  All give
+                            the same graph.                                             */
     int32_t reserved;    /* must be 0                                                   */
 } gk_graph_params;
 
@@ -136,13 +137,19 @@ GK_API int gk_init_graph(const float *X, int64_t n, int64_t d, int64_t ld, int32
  *   sum_d2    device double[1] or NULL: sum of best_d2 (n times the distortion
  *             after the assignment, Eq. 4), computed in FP64
  *   n_changed device int64[1] or NULL: samples whose label changed
- *   precision 0 or 1: candidate distances read the FP32 centroid rows; 2 and 3:
- *             they are first screened against a BF16 copy of the centroids (2:
- *             on the SIMT cores, one sample per warp; 3: for d <= 128 on the
- *             tensor cores, 128 samples of adjacent clusters at a time) and
- *             every candidate within a rigorous error bound of the minimum is
+ *   precision bits 0-7, the level: 0 or 1: candidate distances read the FP32
+ *             centroid rows; 2, 3 and 4: they are first screened against a
+ *             copy of the centroids (2: BF16, on the SIMT cores, one sample per
+ *             warp; 3: BF16, for d <= 128 on the tensor cores, 128 samples of
+ *             adjacent clusters at a time; 4: int8 with a per-row scale, on the
+ *             SIMT cores, a quarter of the FP32 row's bytes) and every
+ *             candidate within a rigorous error bound of the minimum is
  *             recomputed against the FP32 rows in the same order as with 0, so
  *             labels_out, best_d2, sum_d2 and n_changed are identical.
+ *             Bits 8-15: candidates per group of the row kernels, 0 (default:
+ *             8, or 4 for rows of more than 512 values), 4 or 8 (rows of more
+ *             than 512 values always take 4); a tile shape, the results are the
+ *             same.  Other bits must be 0.
  *   members   device int32[n] or NULL: the samples grouped by labels_in, as
  *             gk_group_by_label returns them; used by precision 3 to form the
  *             tiles (NULL: the call groups them itself)

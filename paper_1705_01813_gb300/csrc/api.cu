@@ -62,6 +62,21 @@ int check_kappa(int32_t kappa, int64_t n)
     return GK_OK;
 }
 
+// The precision argument: bits 0-7 the level (0-4), bits 8-15 the assignment's candidates per group (0: the
+// kernels' default, else 4 or 8; a tile shape with the same results), no other bits.
+int check_precision(int32_t precision, bool bf16)
+{
+    const int level = precision & 0xff, gw = (precision >> 8) & 0xff;
+    if (precision < 0 || (precision >> 16) != 0 || level > 4 || (gw != 0 && gw != 4 && gw != 8))
+        return fail(GK_ERR_INVALID,
+                    "precision = %d (bits 0-7: level 0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores), "
+                    "4: int8 screening, each + exact recompute; bits 8-15: 0, 4 or 8 candidates per group)",
+                    precision);
+    if (bf16 && level == 3)
+        return fail(GK_ERR_INVALID, "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    return GK_OK;
+}
+
 int check_ws(void *ws, size_t ws_bytes, size_t need)
 {
     if (!ws)
@@ -367,18 +382,13 @@ static int assign_step_impl(const void *X, bool bf16, int64_t n, int64_t d, int6
         return fail(GK_ERR_INVALID, "a required array is NULL");
     if (labels_in == labels_out)
         return fail(GK_ERR_INVALID, "labels_out must not alias labels_in");
-    if (precision < 0 || precision > 3)
-        return fail(GK_ERR_INVALID,
-                    "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
-                    precision);
-    if (bf16 && precision == 3)
-        return fail(GK_ERR_INVALID,
-                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    if ((rc = check_precision(precision, bf16)))
+        return rc;
     Layout L = carve(nullptr, GK_OP_ASSIGN, n, d, k);
     if ((rc = check_ws(ws, ws_bytes, L.bytes)))
         return rc;
     L = carve(ws, GK_OP_ASSIGN, n, d, k);
-    if (precision == 3 && !members) {  // group the samples by their input label for the tile screening
+    if ((precision & 0xff) == 3 && !members) {  // group the samples by their input label for the tile screening
         GK_CUDA(launch_group(labels_in, n, k, L.grp.offsets, L.grp.members, L.grp.counts, L.grp.scratch, L.st,
                              (cudaStream_t)stream));
         members = L.grp.members;
@@ -457,8 +467,9 @@ static int graph_refine_impl(const void *X, bool bf16, int64_t n, int64_t d, int
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
-    if (precision < 0 || precision > 3)
-        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 to 3: tensor-core Gram + FP32 rerank)", precision);
+    if ((rc = check_precision(precision, false)))
+        return rc;
+    precision &= 0xff;  // the refinement's path: 0 FP32 tiles, >= 1 the tensor-core Gram where d allows
     if (!labels || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -555,8 +566,9 @@ static int graph_refine_groups_impl(const void *X, bool bf16, int64_t n, int64_t
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (max_cluster < 2)
         return fail(GK_ERR_INVALID, "max_cluster = %d < 2", max_cluster);
-    if (precision < 0 || precision > 3)
-        return fail(GK_ERR_INVALID, "precision = %d (0: FP32, 1 to 3: tensor-core Gram + FP32 rerank)", precision);
+    if ((rc = check_precision(precision, false)))
+        return rc;
+    precision &= 0xff;
     if (!offsets || !members || !g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_REFINE, n, d, k);
@@ -598,13 +610,8 @@ static int kmeans_fit_impl(const void *X, bool bf16, int64_t n, int64_t d, int64
         return fail(GK_ERR_INVALID, "k = %d < 1", k);
     if (iters < 0 || 2 * iters + 1 > MAX_LOG)
         return fail(GK_ERR_INVALID, "iters = %d out of range [0, %d]", iters, (MAX_LOG - 1) / 2);
-    if (precision < 0 || precision > 3)
-        return fail(GK_ERR_INVALID,
-                    "precision = %d (0, 1: FP32 rows; 2, 3: BF16 screening (3: on the tensor cores) + exact recompute)",
-                    precision);
-    if (bf16 && precision == 3)
-        return fail(GK_ERR_INVALID,
-                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    if ((rc = check_precision(precision, bf16)))
+        return rc;
     if (!g_idx || !labels_out || !C_out)
         return fail(GK_ERR_INVALID, "a required array is NULL");
     Layout L = carve(nullptr, GK_OP_FIT, n, d, k);
@@ -680,13 +687,10 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
         return fail(GK_ERR_INVALID, "params is NULL");
     if ((rc = check_x(X, bf16, n, d, ld, 2)) || (rc = check_kappa(p->kappa, n)))
         return rc;
-    if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 ||
-        p->precision < 0 || p->precision > 3 || p->reserved != 0)
-        return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d precision=%d)", p->xi, p->tau,
-                    p->max_cluster, p->precision);
-    if (bf16 && p->precision == 3)
-        return fail(GK_ERR_INVALID,
-                    "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    if (p->xi < 1 || p->tau < 0 || 2 * p->tau + 1 > MAX_LOG || p->max_cluster < 2 || p->reserved != 0)
+        return fail(GK_ERR_INVALID, "bad params (xi=%d tau=%d max_cluster=%d)", p->xi, p->tau, p->max_cluster);
+    if ((rc = check_precision(p->precision, bf16)))
+        return rc;
     if (!g_idx || !g_dist)
         return fail(GK_ERR_INVALID, "graph arrays are NULL");
     const int32_t k0 = build_k0(n, p->xi);
@@ -713,7 +717,7 @@ static int build_knn_graph_impl(const void *X, bool bf16, int64_t n, int64_t d, 
                                   L.elog + 2 + 2 * t, L.upd_scratch, L.st, s));
             // exhaustive pairs inside the clusters of the new partition
             GK_CUDA(launch_refine(X, bf16, n, d, ld, L.grp.offsets, L.grp.members, k0, p->kappa, p->max_cluster, g_idx,
-                                  g_dist, L.ref_scratch, L.st, s, p->precision));
+                                  g_dist, L.ref_scratch, L.st, s, p->precision & 0xff));
             int32_t *tmp = cur;
             cur = nxt;
             nxt = tmp;
@@ -808,11 +812,10 @@ static int batch_fit_impl(const void *X, bool bf16, int64_t d, int64_t ld, int32
     const int64_t N = bd.N;
     if ((rc = check_x(X, bf16, N, d, ld, 2)) || (rc = check_kappa(p->kappa, N)))
         return rc;
-    if (p->tau < 0 || p->max_cluster < 2 || p->precision < 0 || p->precision > 3 || p->reserved != 0)
-        return fail(GK_ERR_INVALID, "bad params (tau=%d max_cluster=%d precision=%d)", p->tau, p->max_cluster,
-                    p->precision);
-    if (bf16 && p->precision == 3)
-        return fail(GK_ERR_INVALID, "BF16 samples: precision must be 0, 1 or 2 (3 screens on FP32 samples)");
+    if (p->tau < 0 || p->max_cluster < 2 || p->reserved != 0)
+        return fail(GK_ERR_INVALID, "bad params (tau=%d max_cluster=%d)", p->tau, p->max_cluster);
+    if ((rc = check_precision(p->precision, bf16)))
+        return rc;
     if (iters < 0)
         return fail(GK_ERR_INVALID, "iters = %d < 0", iters);
     if (!g_idx || !g_dist || !labels_out || !C_out || !distortion)
@@ -846,7 +849,7 @@ static int batch_fit_impl(const void *X, bool bf16, int64_t d, int64_t ld, int32
             GK_CUDA(launch_update(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K0, L.cent, L.grp.counts,
                                   nullptr, L.upd_scratch, L.st, s));
             GK_CUDA(launch_refine(X, bf16, N, d, ld, L.grp.offsets, L.grp.members, bd.K0, p->kappa, p->max_cluster,
-                                  g_idx, g_dist, L.ref_scratch, L.st, s, p->precision));
+                                  g_idx, g_dist, L.ref_scratch, L.st, s, p->precision & 0xff));
             int32_t *tmp = cur;
             cur = nxt;
             nxt = tmp;

@@ -181,7 +181,7 @@ constexpr int AS_HASH = 256;                                  // slots of the pe
 constexpr int AS_QROW = (AS_QCAP + AS_G + 3) / 4 * 4;         // candidate list row, padding included
 static_assert(AS_HASH > AS_QCAP, "the label set must never fill up");
 
-template <int NV, typename XT>
+template <int NV, typename XT, int GS>
 __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k_assign_rows(const XT *__restrict__ X, int64_t n, int d,
                                                                int64_t ld, const int32_t *__restrict__ G, int kappa,
                                                                const float *__restrict__ C, int k,
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k
     const int w = threadIdx.x >> 5, lane = lane_id();
     int *qlist = s_q[w];
     int *tab = s_h[w];
-    constexpr int GS = NV >= 8 ? AS_G / 2 : AS_G;  // wide rows: smaller groups keep the loads in registers
+    static_assert(GS == 4 || GS == 8, "candidates per group: 4 or 8");
     const int d4 = d >> 2;
     const float4 *C4 = reinterpret_cast<const float4 *>(C);
     const int ncand = kappa + 1;
@@ -301,10 +301,11 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k
     }
 }
 
-// k_assign_rows with the candidate distances screened against the BF16 copy Cb
-// of the centroids (half the bytes per candidate row).  Pass 1 takes every
-// candidate's distance D~ to Cb_r as k_assign_rows does (same lane layout,
-// same 8-candidate groups, BF16 rows widened exactly); with delta_r >=
+// k_assign_rows with the candidate distances screened against a shadow copy of
+// the centroids: BF16 rows (FMT 0, half the bytes per candidate row) or int8
+// rows with a per-row scale (FMT 1, a quarter).  Pass 1 takes every
+// candidate's distance D~ to the shadow row as k_assign_rows does (same lane
+// layout, same candidate groups, shadow values widened exactly); with delta_r >=
 // ||C_r - Cb_r||, |D - D~| <= delta_r (2 sqrt(D~) + delta_r) for the exact
 // distances D, D~, and adding the FP32 rounding of both sums gives a bound E_r.
 // Pass 2 recomputes, one at a time and against C, every candidate whose lower
@@ -313,11 +314,14 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k
 // so the winner and its distance are that kernel's bit for bit.  The samples
 // (FP32 or BF16, widened exactly) enter both passes unrounded: the bound covers
 // the centroids' rounding alone.
-template <int NV, typename XT>
-__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV == 4 ? 4 : 3)) k_assign_rows_bf8(
+// Shadow formats of the screening: FMT 0 BF16 rows (4 values per 8 bytes), FMT 1 int8 rows with a per-row
+// scale s_r (4 values per 4 bytes; see lane_partial_q8), half the bytes again.
+template <int NV, typename XT, int GS, int FMT>
+__global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV == 4 ? 4 : 3)) k_assign_rows_scr(
     const XT *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
-    const float *__restrict__ C, const __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ delta, int k,
-    const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout, float *__restrict__ best_out, DevStatus *st)
+    const float *__restrict__ C, const void *__restrict__ Cs, const float *__restrict__ delta,
+    const float *__restrict__ scale, int k, const int32_t *__restrict__ Lin, int32_t *__restrict__ Lout,
+    float *__restrict__ best_out, DevStatus *st)
 {
     __shared__ __align__(16) int s_q[AS_WARPS][AS_QROW];
     __shared__ __align__(16) int s_h[AS_WARPS][AS_HASH];
@@ -326,10 +330,11 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV 
     int *qlist = s_q[w];
     int *tab = s_h[w];
     float *lov = s_lo[w];
-    constexpr int GS = NV >= 8 ? AS_G / 2 : AS_G;
+    static_assert(GS == 4 || GS == 8, "candidates per group: 4 or 8");
     const int d4 = d >> 2;
     const float4 *C4 = reinterpret_cast<const float4 *>(C);
-    const uint2 *Cb4 = reinterpret_cast<const uint2 *>(Cb);  // 4 BF16 per 8 bytes
+    const uint2 *Cb4 = static_cast<const uint2 *>(Cs);       // FMT 0: 4 BF16 per 8 bytes
+    const uint32_t *Cq4 = static_cast<const uint32_t *>(Cs);  // FMT 1: 4 int8 per 4 bytes
     const float gam = (float)(d + 8) * 5.9604645e-8f;         // FP32 rounding of a d-term sum, relative
     const int ncand = kappa + 1;
 
@@ -403,8 +408,14 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV 
             float part[GS];
 #pragma unroll
             for (int c = 0; c < GS; c++) {
-                const uint2 *row = Cb4 + (int64_t)lab[c] * d4;
-                part[c] = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
+                if constexpr (FMT == 0) {
+                    const uint2 *row = Cb4 + (int64_t)lab[c] * d4;
+                    part[c] = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
+                } else {
+                    const uint32_t *row = Cq4 + (int64_t)lab[c] * d4;
+                    part[c] = lane_partial_q8<NV>(xv, d4, -__ldg(scale + lab[c]),
+                                                  [&](int col) { return __ldg(row + col); });
+                }
             }
             const float dt = transpose_reduce<GS>(part);
             const int cl = lane / (32 / GS);
@@ -472,6 +483,47 @@ __global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bf
         if (lane == 0) {
             delta[r] = (float)(sqrt(e) * (1.0 + 1e-6)) + 1e-30f;  // rounded up
             cnorm[r] = (float)c2;                                 // ||C_r||^2 (a bound input only)
+        }
+    }
+}
+
+// Int8 shadow of the centroids: per row r the scale s_r = max_t |C_rt| / 127 (1 for a zero row), codes
+// q_rt = rint(C_rt / s_r) clamped to [-127, 127] and stored as q + 128, four per 32-bit word in the order of the
+// row's values; delta_r >= ||C_r - q_r s_r|| from the exact products q s in FP64.
+__global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, uint32_t *__restrict__ Cq,
+                            float *__restrict__ delta, float *__restrict__ scale)
+{
+    const int lane = lane_id();
+    const int d4 = d >> 2;
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < k; r += gridDim.x * (blockDim.x >> 5)) {
+        const float4 *row = reinterpret_cast<const float4 *>(C + (int64_t)r * d);
+        float mx = 0.f;
+        for (int col = lane; col < d4; col += 32) {
+            const float4 v = row[col];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+        const float sc = mx > 0.f ? mx / 127.f : 1.f;
+        double e = 0.0;
+        for (int col = lane; col < d4; col += 32) {
+            const float4 v = row[col];
+            const float vals[4] = {v.x, v.y, v.z, v.w};
+            uint32_t word = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float qf = fminf(127.f, fmaxf(-127.f, rintf(vals[q] / sc)));
+                word |= (uint32_t)((int)qf + 128) << (8 * q);
+                const double diff = (double)vals[q] - (double)qf * (double)sc;  // q s exact in FP64
+                e += diff * diff;
+            }
+            Cq[(int64_t)r * d4 + col] = word;
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            e += __shfl_xor_sync(FULL_MASK, e, o);
+        if (lane == 0) {
+            delta[r] = (float)(sqrt(e) * (1.0 + 1e-6)) + 1e-30f;  // rounded up
+            scale[r] = sc;
         }
     }
 }
@@ -746,19 +798,43 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
 
     const bool vec4 = x_vec4(X, d, ld) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int d4 = (int)(d / 4);
+    // candidates per group of the row kernels (a tile shape: every width gives the same bits, transpose_reduce
+    // forms each total with warp_total's tree): 8 by default, 4 for rows of more than 512 values, where 8 would
+    // not keep the loads in registers; a caller (the autotuner) may ask for 4 or 8
+    const int gw = (precision >> 8) & 0xff;
+    precision &= 0xff;
     cudaError_t e;
     int grid = 0;
     bool done = false;
-    if (precision == 2 && vec4 && d4 <= 32 * 8) {
-        k_shadow_bf16<<<(k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16, 256, 0, s>>>(C, k, (int)d, Cb, delta,
-                                                                                  cnorm);
+    if ((precision == 2 || precision == 4) && vec4 && d4 <= 32 * 8) {
+        // the shadow: BF16 (2) or int8 with a per-row scale (4); the int8 codes take the BF16 shadow's space
+        const int sgrid = (k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16;
+        if (precision == 2)
+            k_shadow_bf16<<<sgrid, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
+        else
+            k_shadow_i8<<<sgrid, 256, 0, s>>>(C, k, (int)d, reinterpret_cast<uint32_t *>(Cb), delta, cnorm);
+#define GK_ASB8F(NV, GS, F)                                                                                      \
+    do {                                                                                                         \
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows_scr<NV, XT, GS, F>), AS_WARPS * 32,  \
+                               0, &grid)) != cudaSuccess)                                                        \
+            return e;                                                                                            \
+        k_assign_rows_scr<NV, XT, GS, F><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb,   \
+                                                                        delta, cnorm, k, labels_in, labels_out,  \
+                                                                        best, st);                               \
+    } while (0)
+#define GK_ASB8G(NV, GS)                                                                                         \
+    do {                                                                                                         \
+        if (precision == 2)                                                                                      \
+            GK_ASB8F(NV, GS, 0);                                                                                 \
+        else                                                                                                     \
+            GK_ASB8F(NV, GS, 1);                                                                                 \
+    } while (0)
 #define GK_ASB8(NV)                                                                                              \
     do {                                                                                                         \
-        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows_bf8<NV, XT>), AS_WARPS * 32, 0,      \
-                               &grid)) != cudaSuccess)                                                           \
-            return e;                                                                                            \
-        k_assign_rows_bf8<NV, XT><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, Cb, delta, k, \
-                                                                 labels_in, labels_out, best, st);               \
+        if (NV >= 8 || gw == 4)                                                                                  \
+            GK_ASB8G(NV, 4);                                                                                     \
+        else                                                                                                     \
+            GK_ASB8G(NV, 8);                                                                                     \
     } while (0)
         if (d4 <= 32)
             GK_ASB8(1);
@@ -769,6 +845,8 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
         else
             GK_ASB8(8);
 #undef GK_ASB8
+#undef GK_ASB8G
+#undef GK_ASB8F
         done = true;
     }
     if constexpr (std::is_same_v<XT, float>) {  // tensor-core screening: FP32 samples only
@@ -802,13 +880,20 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     }
     if (done) {
     } else if (vec4 && d4 <= 32 * 8) {
+#define GK_ASGG(NV, GS)                                                                                          \
+    do {                                                                                                         \
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows<NV, XT, GS>), AS_WARPS * 32, 0,      \
+                               &grid)) != cudaSuccess)                                                           \
+            return e;                                                                                            \
+        k_assign_rows<NV, XT, GS><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,  \
+                                                                 labels_out, best, st);                          \
+    } while (0)
 #define GK_ASG(NV)                                                                                               \
     do {                                                                                                         \
-        if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows<NV, XT>), AS_WARPS * 32, 0, &grid)) != \
-            cudaSuccess)                                                                                         \
-            return e;                                                                                            \
-        k_assign_rows<NV, XT><<<grid, AS_WARPS * 32, 0, s>>>(X, n, (int)d, ld, g_idx, kappa, C, k, labels_in,      \
-                                                             labels_out, best, st);                              \
+        if (NV >= 8 || gw == 4)                                                                                  \
+            GK_ASGG(NV, 4);                                                                                      \
+        else                                                                                                     \
+            GK_ASGG(NV, 8);                                                                                      \
     } while (0)
         if (d4 <= 32)
             GK_ASG(1);
@@ -819,6 +904,7 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
         else
             GK_ASG(8);
 #undef GK_ASG
+#undef GK_ASGG
     } else {
         int dpad = (int)((d + 3) & ~3);
         size_t shm = sizeof(float) * (size_t)AS_WARPS * dpad + sizeof(int) * AS_WARPS * AS_QCAP;

@@ -65,6 +65,36 @@ __device__ __forceinline__ float lane_partial(const float4 (&xv)[NV], int d4, Ro
     return a.x + a.y;
 }
 
+// Partial squared distance of x to a row of an int8 shadow (4 values per 32-bit word, each stored as q + 128,
+// the row's values being q s with |q| <= 127): word col holds the values of vector col.  Each byte is widened
+// exactly (the float 2^23 + u, minus 2^23 + 128) and e = x - q s is one fma (the product q s is exact inside it),
+// so the partial is the FP32 sum of (x - c~)^2 for the shadow values c~ = q s.
+template <int NV, typename RowLoad>
+__device__ __forceinline__ float lane_partial_q8(const float4 (&xv)[NV], int d4, float neg_s, RowLoad load)
+{
+    const int lane = lane_id();
+    const float2 ns2 = make_float2(neg_s, neg_s);
+    const float2 off2 = make_float2(-8388736.f, -8388736.f);  // -(2^23 + 128)
+    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        const int col = lane + 32 * v;
+        if (col < d4) {
+            const uint32_t w = load(col);
+            const float2 u01 = make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540)),
+                                           __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541)));
+            const float2 u23 = make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7542)),
+                                           __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7543)));
+            const float2 q01 = __fadd2_rn(u01, off2), q23 = __fadd2_rn(u23, off2);
+            const float2 e01 = __ffma2_rn(q01, ns2, make_float2(xv[v].x, xv[v].y));
+            const float2 e23 = __ffma2_rn(q23, ns2, make_float2(xv[v].z, xv[v].w));
+            a = __ffma2_rn(e01, e01, a);
+            a = __ffma2_rn(e23, e23, a);
+        }
+    }
+    return a.x + a.y;
+}
+
 // Complete one candidate's distance from the lane partials: the xor butterfly
 // pairs lanes by bit 4, then 3, 2, 1, 0, which is the grouping of
 // transpose_reduce32, so the total has the same bits as there.

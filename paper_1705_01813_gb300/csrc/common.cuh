@@ -220,8 +220,9 @@ cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_
 
 size_t assign_scratch_bytes(int64_t n, int32_t k, int64_t d);
 // precision 0 and 1: FP32 candidate rows; 2: BF16 screening on the SIMT cores; 3: on the tensor cores over
-// 128-sample tiles when members, the grouping of labels_in, is given and d <= 128; both with the exact FP32
-// recompute (same results).  2 and 3 take FP32 samples only.
+// 128-sample tiles when members, the grouping of labels_in, is given and d <= 128; 4: int8 screening (per-row
+// scale) on the SIMT cores; all with the exact FP32 recompute (same results).  3 takes FP32 samples only.
+// Bits 8-15 of precision: candidates per group of the row kernels (0: default, 4 or 8).
 cudaError_t launch_assign(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
                           int32_t kappa, const float *C, int32_t k, const int32_t *labels_in, int32_t *labels_out,
                           float *best_d2, double *sum_d2, int64_t *n_changed, void *scratch, DevStatus *st,

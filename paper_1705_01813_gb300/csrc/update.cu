@@ -12,6 +12,8 @@
 // once per cluster, in the distortion term.
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 namespace gkm {
@@ -136,7 +138,7 @@ __device__ __forceinline__ typename VecT<VEC>::T load_vec(const XT *p)
 template <int VEC, int CPL, bool PIPE, typename XT>
 __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__ X, int d, int64_t ld,
                                                           const int32_t *__restrict__ off,
-                                                          const int32_t *__restrict__ mem, int k,
+                                                          const int32_t *__restrict__ mem, int k, int small_max,
                                                           float *__restrict__ C, int32_t *__restrict__ counts,
                                                           double *__restrict__ contrib, DevStatus *st)
 {
@@ -162,16 +164,17 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
     const int64_t ldv = ld / VEC;
     const V *Xv = reinterpret_cast<const V *>(X);
 
-    const int r = blockIdx.x;
-    if (r >= k)
-        return;
+    // clusters r = blockIdx.x, + gridDim.x, ...; those of at most small_max members are k_update_small's
+    for (int r = blockIdx.x; r < k; r += gridDim.x) {
     const int beg = off[r], m = off[r + 1] - beg;
+    if (m <= small_max)
+        continue;
     if (counts && threadIdx.x == 0)
         counts[r] = m;
     if (m == 0) {
         if (threadIdx.x == 0)
             contrib[r] = 0.0;
-        return;
+        continue;
     }
     const float mf = (float)m, inv_m = 1.0f / mf;
     DF sq_lane = {0.f, 0.f}, dd_lane = {0.f, 0.f};
@@ -309,6 +312,116 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
         if (!isfinite(cr))  // a non-finite sample in the cluster (Inf or NaN spreads into its sums)
             flag_error(st, GK_ERR_NUMERIC, (unsigned)r);
     }
+    __syncthreads();  // s_sq / s_dd are read above before the next cluster writes them
+    }
+}
+
+// Clusters of at most US_MAXM members, one warp each (the deep-feature workload's clusters hold about ten):
+// lane l owns row vectors l, l + 32, ... (NVL of them); the members' rows stream through the warp RIF at a
+// time, and every coordinate is summed over the members in member order with compensated FP32 arithmetic,
+// then combined and divided as in k_update.  No shared memory and no block barrier, so a cluster costs a
+// few dependent loads instead of a block's set-up.
+constexpr int US_WARPS = 8;
+constexpr int US_MAXM = 32;
+
+// A row vector of 4 elements as loaded (16 bytes of FP32, 8 bytes of BF16), widened when it is summed.
+template <typename XT>
+struct RawVec;
+template <>
+struct RawVec<float> {
+    using T = float4;
+    __device__ static T load(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+    __device__ static float4 widen(T v) { return v; }
+    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct RawVec<__nv_bfloat16> {
+    using T = uint2;
+    __device__ static T load(const __nv_bfloat16 *p) { return __ldcs(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float4 widen(T v) { return bf16x4_to_float4(v); }
+    __device__ static T zero() { return make_uint2(0u, 0u); }
+};
+
+template <int NVL, typename XT>
+__global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__restrict__ X, int d, int64_t ld,
+                                                                const int32_t *__restrict__ off,
+                                                                const int32_t *__restrict__ mem, int k,
+                                                                float *__restrict__ C, int32_t *__restrict__ counts,
+                                                                double *__restrict__ contrib, DevStatus *st)
+{
+    constexpr int RIF = NVL == 1 ? 8 : NVL == 2 ? 4 : 2;  // member rows in flight (registers allowing)
+    using RV = RawVec<XT>;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int nv = d / 4;
+    for (int r = blockIdx.x * US_WARPS + w; r < k; r += gridDim.x * US_WARPS) {
+        const int beg = off[r], m = off[r + 1] - beg;
+        if (m > US_MAXM)
+            continue;  // a cluster of k_update
+        if (counts && lane == 0)
+            counts[r] = m;
+        if (m == 0) {
+            if (lane == 0)
+                contrib[r] = 0.0;
+            continue;
+        }
+        const int myid = lane < m ? __ldg(mem + beg + lane) : 0;
+        float s[NVL][4], c[NVL][4];
+#pragma unroll
+        for (int u = 0; u < NVL; u++)
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                s[u][q] = c[u][q] = 0.f;
+        float qs = 0.f, qc = 0.f;
+        for (int p0 = 0; p0 < m; p0 += RIF) {
+            typename RV::T raw[RIF][NVL];
+#pragma unroll
+            for (int z = 0; z < RIF; z++) {
+                const int a = __shfl_sync(FULL_MASK, myid, (p0 + z) & 31);
+                const XT *row = X + (int64_t)a * ld;
+#pragma unroll
+                for (int u = 0; u < NVL; u++) {
+                    const int col = lane + 32 * u;
+                    raw[z][u] = (p0 + z < m && col < nv) ? RV::load(row + 4 * col) : RV::zero();
+                }
+            }
+#pragma unroll
+            for (int z = 0; z < RIF; z++) {
+                if (p0 + z < m) {
+                    float4 v[NVL];
+#pragma unroll
+                    for (int u = 0; u < NVL; u++)
+                        v[u] = RV::widen(raw[z][u]);
+                    accumulate<4, NVL>(v, s, c, qs, qc, 0, lane, 32, nv);
+                }
+            }
+        }
+        const float mf = (float)m, inv_m = 1.0f / mf;
+        DF sq = fast_two_sum(qs, -qc), dd = {0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < NVL; u++) {
+            const int col = lane + 32 * u;
+            if (col < nv) {
+                float out[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const DF S = fast_two_sum(s[u][q], -c[u][q]);  // the Kahan sum s - c, exactly
+                    out[q] = df_div(S, mf, inv_m);
+                    dd = df_add(dd, df_sqr(S));
+                }
+                *reinterpret_cast<float4 *>(C + (int64_t)r * d + 4 * col) = make_float4(out[0], out[1], out[2], out[3]);
+            }
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+            sq = df_add(sq, df_shfl_xor(sq, o));
+            dd = df_add(dd, df_shfl_xor(dd, o));
+        }
+        if (lane == 0) {
+            const double cr = df_to_double(sq) - df_to_double(dd) / (double)m;
+            contrib[r] = cr;
+            if (!isfinite(cr))
+                flag_error(st, GK_ERR_NUMERIC, (unsigned)r);
+        }
+    }
 }
 
 // Deterministic FP64 sum of `count` values (one block, fixed order).
@@ -335,20 +448,61 @@ size_t update_scratch_bytes(int64_t, int32_t k) { return ((size_t)k * sizeof(dou
 const double *update_contrib(const void *scratch) { return static_cast<const double *>(scratch); }
 
 template <typename XT>
-static cudaError_t update_t(const XT *X, int64_t d, int64_t ld, const int32_t *offsets, const int32_t *members,
-                            int32_t k, float *C, int32_t *counts, double *sum_d2, void *scratch, DevStatus *st,
-                            cudaStream_t s)
+static cudaError_t update_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                            const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
+                            void *scratch, DevStatus *st, cudaStream_t s)
 {
     double *contrib = static_cast<double *>(scratch);
     const bool vec4 = x_vec4(X, d, ld);
     const int nv = vec4 ? (int)(d / 4) : (int)d;
     const int L = nv >= 32 ? 32 : (nv >= 16 ? 16 : nv >= 8 ? 8 : nv >= 4 ? 4 : nv >= 2 ? 2 : 1);
     const int need = (nv + L - 1) / L;  // vectors per lane to cover a row in one column block
-    const unsigned grid = (unsigned)k;
     const int dd = (int)d;
     constexpr bool PIPE = std::is_same_v<XT, float>;  // FP32 rows stream through the cp.async ring
+    // clusters of at most US_MAXM members go to the warp-per-cluster kernel where rows are 16-byte vectors of at
+    // most 4 per lane and the centroid rows 16-byte aligned; the block kernel takes the others
+    const bool small = vec4 && nv <= 32 * 4 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+    const int small_max = small ? US_MAXM : -1;
+    cudaError_t e;
+    if (small) {
+        int g = 0;
+#define GK_UPS(NVL)                                                                                                \
+    do {                                                                                                         \
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_update_small<NVL, XT>), US_WARPS * 32, 0, &g)) !=   \
+            cudaSuccess)                                                                                         \
+            return e;                                                                                            \
+        k_update_small<NVL, XT><<<(unsigned)g, US_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts,  \
+                                                                      contrib, st);                              \
+    } while (0)
+        if (nv <= 32)
+            GK_UPS(1);
+        else if (nv <= 64)
+            GK_UPS(2);
+        else
+            GK_UPS(4);
+#undef GK_UPS
+    }
+    // the block kernel walks the clusters grid-stride on a one-wave grid (at most k blocks)
+    int bg = 0;
+    if ((e = resident_grid(reinterpret_cast<const void *>(vec4 ? (need <= 1 ? (const void *)k_update<4, 1, PIPE, XT>
+                                                                             : need <= 2 ? (const void *)k_update<4, 2, PIPE, XT>
+                                                                             : need <= 4 ? (const void *)k_update<4, 4, PIPE, XT>
+                                                                                         : (const void *)k_update<4, 8, PIPE, XT>)
+                                                                 : (need <= 1 ? (const void *)k_update<1, 1, false, XT>
+                                                                             : need <= 2 ? (const void *)k_update<1, 2, false, XT>
+                                                                             : need <= 4 ? (const void *)k_update<1, 4, false, XT>
+                                                                                         : (const void *)k_update<1, 8, false, XT>)),
+                           UP_WARPS * 32, 0, &bg)) != cudaSuccess)
+        return e;
+    // one block per cluster while the clusters are mostly the block kernel's (the hardware then hands clusters
+    // of uneven sizes to SMs as blocks finish); where most clusters are small, a one-wave grid walks the few
+    // large ones instead of launching a block per cluster that would return at once.  Which block sums a
+    // cluster changes none of its bits.
+    const bool mostly_small = small && n <= (int64_t)k * US_MAXM;
+    const unsigned grid = (unsigned)(mostly_small ? (k < bg ? k : bg) : k);
 #define GK_UPD(VEC, CPL, P) \
-    k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts, contrib, st)
+    k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, small_max, C, counts, \
+                                                             contrib, st)
     if (vec4) {
         if (need <= 1)
             GK_UPD(4, 1, PIPE);
@@ -378,11 +532,10 @@ cudaError_t launch_update(const void *X, bool bf16, int64_t n, int64_t d, int64_
                           const int32_t *members, int32_t k, float *C, int32_t *counts, double *sum_d2,
                           void *scratch, DevStatus *st, cudaStream_t s)
 {
-    (void)n;
     if (bf16)
-        return update_t(static_cast<const __nv_bfloat16 *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch,
-                        st, s);
-    return update_t(static_cast<const float *>(X), d, ld, offsets, members, k, C, counts, sum_d2, scratch, st, s);
+        return update_t(static_cast<const __nv_bfloat16 *>(X), n, d, ld, offsets, members, k, C, counts, sum_d2,
+                        scratch, st, s);
+    return update_t(static_cast<const float *>(X), n, d, ld, offsets, members, k, C, counts, sum_d2, scratch, st, s);
 }
 
 }  // namespace gkm

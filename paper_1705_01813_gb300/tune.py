@@ -1,11 +1,14 @@
-"""Autotuner over the library's precision levels.
+"""Autotuner over the library's precision levels and the assignment's tile shape.
 
 Every level gives the same labels, centroids, distortions and graph bit for bit (the GPU tests assert it), so
-the fastest one for a workload can be chosen by measurement alone: one assignment per level (0 to 3; 0 to 2
-for BF16 samples) and one refinement per refinement path (level 0: the FP32 tiles; levels 1 to 3: the
+the fastest one for a workload can be chosen by measurement alone: one assignment per level (0 to 4; 3 only
+for FP32 samples) and one refinement per refinement path (level 0: the FP32 tiles; levels 1 to 4: the
 tensor-core Gram where d allows it) are timed with CUDA events on the caller's samples and graph, and each
 level is scored by the time the whole path would spend in those calls (the assignment runs tau + iters times
-per graph construction and fit, the refinement tau times).  Choices are cached per shape key.
+per graph construction and fit, the refinement tau times).  At the levels whose assignment runs the row kernels
+(all but 3) the assignment is also timed with 4 and with 8 candidates per group (bits 8-15 of the precision
+argument; the kernels' summation tree is the same for both, so the results are too), and the faster width goes
+with the level.  Choices are cached per shape key.
 """
 from __future__ import annotations
 
@@ -52,16 +55,23 @@ def tune_precision(X: torch.Tensor, g_idx: torch.Tensor, g_dist: torch.Tensor, l
         return _CACHE[key]
     n, d = X.shape
     dev = X.device
-    levels = [0, 1, 2] if X.dtype == torch.bfloat16 else [0, 1, 2, 3]
+    levels = [0, 1, 2, 4] if X.dtype == torch.bfloat16 else [0, 1, 2, 3, 4]
     off, mem, cnt = gkm.group_by_label(labels, k)
     C = torch.zeros((k, d), dtype=torch.float32, device=dev)
     gkm.update_from_groups(X, off, mem, k, C, cnt)
     ws = gkm.workspace(max(gkm.workspace_size(gkm.GK_OP_ASSIGN, n, d, k, kappa),
                            gkm.workspace_size(gkm.GK_OP_REFINE, n, d, k, kappa)), dev)
     out = torch.empty_like(labels)
-    assign_ms = {}
+    assign_ms, group_width = {}, {}
+    widths = [8, 4] if d <= 512 else [4]  # rows of more than 512 values take groups of 4
     for p in levels:
-        assign_ms[p] = _time(lambda: gkm.assign_step(X, g_idx, C, labels, out, None, None, None, p, mem, ws=ws), reps)
+        best_w, best_t = 0, float("inf")
+        for gw in (widths if p != 3 else [0]):
+            code = p | (gw << 8)
+            t = _time(lambda: gkm.assign_step(X, g_idx, C, labels, out, None, None, None, code, mem, ws=ws), reps)
+            if t < best_t:
+                best_w, best_t = gw, t
+        assign_ms[p], group_width[p] = best_t, best_w
     gi, gd = g_idx.clone(), g_dist.clone()
 
     def refine(p):
@@ -75,6 +85,8 @@ def tune_precision(X: torch.Tensor, g_idx: torch.Tensor, g_dist: torch.Tensor, l
              (refine_ms["fp32_tiles"] if p == 0 else refine_ms["precision_ge_1"]) * tau - copy_ms * tau
              for p in levels}
     best = min(levels, key=lambda p: (score[p], p))
-    res = {"precision": best, "assign_ms": assign_ms, "refine_ms": refine_ms, "score_ms": score, "key": list(key)}
+    res = {"precision": best | (group_width[best] << 8), "level": best, "group_width": group_width[best],
+           "assign_ms": assign_ms, "group_width_by_level": group_width, "refine_ms": refine_ms, "score_ms": score,
+           "key": list(key)}
     _CACHE[key] = res
     return res

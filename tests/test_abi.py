@@ -73,9 +73,12 @@ def test_argument_errors(lib):
     assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 0, None, ws, 16,
                               None) == gkm.GK_ERR_INVALID
     assert b"too small" in lib.gk_last_error()
-    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 4, None, ws, 1 << 20,
+    assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, 5, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert b"precision" in lib.gk_last_error()
+    for bad in (2 | (3 << 8), 1 | (16 << 8), 1 << 16, -1):  # group width not 0, 4 or 8; bits above 15; negative
+        assert lib.gk_assign_step(P, 10, 4, 4, P, 2, P, 2, P, _fake(0x30000000), None, None, None, bad, None, ws,
+                                  1 << 20, None) == gkm.GK_ERR_INVALID
     assert lib.gk_update_step(None, 10, 4, 4, P, 2, P, None, None, None, None, ws, 1 << 20,
                               None) == gkm.GK_ERR_INVALID
     assert lib.gk_update_step(P, 10, 4, 4, P, 0, P, None, None, None, None, ws, 1 << 20,

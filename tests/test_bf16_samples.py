@@ -53,7 +53,7 @@ def test_init_graph(G, n, d, kappa):
     _same(G.init_graph(xb, kappa, 11), G.init_graph(xf, kappa, 11))
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 4])
 @pytest.mark.parametrize("n,d,k,kappa,ld", [(20000, 32, 200, 20, None), (5003, 33, 97, 16, None),
                                             (4001, 128, 300, 12, None), (3001, 960, 40, 10, None),
                                             (6007, 64, 120, 20, 72)])
@@ -131,7 +131,7 @@ def test_group_entry_points(G):
     _same(gb, gf)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 4])
 @pytest.mark.parametrize("n,d,k", [(20000, 32, 200), (8009, 100, 80)])
 def test_fit_and_build(G, n, d, k, precision):
     xb, xf = _pair(n, d, n - d)
@@ -161,11 +161,11 @@ def test_graph_refine_unit_vectors(G, d, precision):
     _same(gb, gf)
 
 
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 2, 4])
 def test_assign_unit_vectors_many_candidates(G, precision):
     """Deep-feature-shaped rows at the ratio n / k = 10 of the 10^7 x 512 workload: every sample has
     about kappa + 1 distinct candidate clusters at nearly equal distances, the hardest case for the
-    BF16 screening's bound."""
+    BF16 and int8 screenings' bounds."""
     from paper_1705_01813_gb300 import datagen
     n, d, k, kappa = 20000, 512, 2000, 40
     xb = datagen.deep_like_device(n, d, 4000, 50.0, seed=67, device="cuda")

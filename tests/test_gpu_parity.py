@@ -102,7 +102,7 @@ def _assign_case(G, X, kappa, k, seed, graph="knn", precision=0):
     (1500, 1, 5, 3),          # d = 1
     (700, 16, 3, 128),        # kappa at its maximum, many repeated labels
 ])
-@pytest.mark.parametrize("precision", [0, 2, 3])
+@pytest.mark.parametrize("precision", [0, 2, 3, 4])
 def test_assign_lockstep(G, n, d, k, kappa, precision):
     X = _blobs(n, d, max(2, k // 2), n + d)
     ex = _assign_case(G, X, kappa, k, seed=n, precision=precision)
@@ -127,7 +127,7 @@ def test_assign_bf16_shadow_equals_fp32(G, data):
     C64, _, _, _ = O.update(X, L, k)
     Xd, gd, Cd, Ld = _cuda(X), _cuda(gi), _cuda(C64.astype(np.float32)), _cuda(L)
     a = G.assign_step(Xd, gd, Cd, Ld, precision=0)
-    for prec in (2, 3):
+    for prec in (2, 3, 4):
         b = G.assign_step(Xd, gd, Cd, Ld, precision=prec)
         for x, y in zip(a, b):
             assert torch.equal(x, y)
@@ -293,16 +293,33 @@ def test_fit_precisions_identical(G):
     gi, _, _, _ = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=4, seed=w.seed)
     L0 = G.init_labels(w.n, w.k, 9)
     a = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=0)
-    for prec in (1, 2, 3):
+    for prec in (1, 2, 3, 4):
         b = G.kmeans_fit(X, w.k, gi, 6, init_labels=L0, precision=prec)
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]) and a[3] == b[3]
+
+
+@pytest.mark.parametrize("d", [32, 128, 960])
+def test_assign_group_width_is_result_neutral(G, d):
+    """The assignment's candidates per group (bits 8-15 of precision: 4 or 8, a tile shape the autotuner picks)
+    change no bit of the labels, the winning distances or their sum, at levels 0, 2 and 4."""
+    X = _blobs(6007, d, 40, d)
+    gi = np.random.default_rng(d).integers(0, 6007, (6007, 24)).astype(np.int32)
+    L = np.random.default_rng(d + 1).integers(0, 90, 6007).astype(np.int32)
+    C64, _, _, _ = O.update(X, L, 90)
+    C = _cuda(C64.astype(np.float32))
+    for level in (0, 2, 4):
+        ref = G.assign_step(_cuda(X), _cuda(gi), C, _cuda(L), precision=level)
+        for gw in (4, 8):
+            out = G.assign_step(_cuda(X), _cuda(gi), C, _cuda(L), precision=level | (gw << 8))
+            assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1])
+            assert out[2].item() == ref[2].item() and out[3].item() == ref[3].item()
 
 
 def test_build_graph_precisions_identical(G):
     w = datagen.WORKLOADS["gauss_n20000_d32_k200"]
     X = _cuda(w.data())
     a = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=0)
-    for prec in (1, 2, 3):
+    for prec in (1, 2, 3, 4):
         b = G.build_knn_graph(X, w.kappa, xi=w.xi, tau=w.tau, seed=w.seed, precision=prec)
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
         assert a[3] == b[3]

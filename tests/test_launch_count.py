@@ -20,11 +20,12 @@ def test_kernel_source_map_names_real_kernels():
 def test_kernel_of_follows_the_dispatch_rules():
     assert bench.kernel_of("refine", 1, 128) == "k_refine_gram" and bench.kernel_of("refine", 0, 128) == "k_refine"
     assert bench.kernel_of("refine", 1, 960) == "k_refine" and bench.kernel_of("refine", 1, 32) == "k_refine"
-    assert bench.kernel_of("assign", 2) == "k_assign_rows_bf8" and bench.kernel_of("assign", 1) == "k_assign_rows"
+    assert bench.kernel_of("assign", 2) == "k_assign_rows_scr" and bench.kernel_of("assign", 1) == "k_assign_rows"
+    assert bench.kernel_of("assign", 4) == "k_assign_rows_scr"
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 4])
 def test_launches_per_step_matches_the_profiler(precision):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():

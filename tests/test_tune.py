@@ -19,10 +19,11 @@ def test_tuner_picks_a_level_and_leaves_inputs_alone():
     gi0, gd0, lab0 = gi.clone(), gd.clone(), lab.clone()
     r = tune.tune_precision(X, gi, gd, lab, 600, tau=2, iters=3, use_cache=False)
     assert torch.equal(gi, gi0) and torch.equal(gd, gd0) and torch.equal(lab, lab0)
-    assert r["precision"] in (0, 1, 2, 3)
-    assert r["score_ms"][r["precision"]] == min(r["score_ms"].values())
-    assert set(r["assign_ms"]) == {0, 1, 2, 3}
+    assert r["level"] in (0, 1, 2, 3, 4) and r["group_width"] in (0, 4, 8)
+    assert r["precision"] == r["level"] | (r["group_width"] << 8)
+    assert r["score_ms"][r["level"]] == min(r["score_ms"].values())
+    assert set(r["assign_ms"]) == {0, 1, 2, 3, 4}
     r2 = tune.tune_precision(X, gi, gd, lab, 600, tau=2, iters=3)
     assert tune.tune_precision(X, gi, gd, lab, 700, tau=2, iters=3) is r2  # same shape bucket: cached
     rb = tune.tune_precision(X.to(torch.bfloat16), gi, gd, lab, 600, tau=2, iters=3, use_cache=False)
-    assert set(rb["assign_ms"]) == {0, 1, 2}  # no tensor-core screening for BF16 samples
+    assert set(rb["assign_ms"]) == {0, 1, 2, 4}  # no tensor-core screening for BF16 samples
