@@ -77,6 +77,8 @@ def parse():
                          "screening (SIMT) (all give the same results).  Default: chosen by the autotuner (tune.py) on "
                          "the workload's own "
                          "graph and labels after the first warm-up step")
+    ap.add_argument("--group-width", type=int, choices=[0, 4, 8], default=0,
+                    help="with --precision: the assignment's candidates per group (0: the kernels' default)")
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-tree", action="store_true",
                     help="skip the timing of the two-means tree (Alg. 1) at the workload's n, d and k")
@@ -403,6 +405,8 @@ def run_gpu(args):
     gkm.load()
 
     tuning = None
+    if args.precision is not None:
+        args.precision |= args.group_width << 8
     path = Path(gkm, torch, w, X, 1 if args.precision is None else args.precision)
     u = {}
     for q in range(args.warmup):  # the last warm-up step also measures u (outside the timed region)

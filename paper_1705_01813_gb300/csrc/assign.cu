@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : 4) k
 // (FP32 or BF16, widened exactly) enter both passes unrounded: the bound covers
 // the centroids' rounding alone.
 // Shadow formats of the screening: FMT 0 BF16 rows (4 values per 8 bytes), FMT 1 int8 rows with a per-row
-// scale s_r (4 values per 4 bytes; see lane_partial_q8), half the bytes again.
+// scale s_r (4 values per 4 bytes; see lane_partial_q8), half the bytes again; FMT 2 the same int8 rows stored
+// lane-major (d a multiple of 128), so that a lane's share of a row is one vector load.
 template <int NV, typename XT, int GS, int FMT>
 __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV == 4 ? 4 : 3)) k_assign_rows_scr(
     const XT *__restrict__ X, int64_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
@@ -411,10 +412,14 @@ __global__ void __launch_bounds__(AS_WARPS * 32, NV <= 2 ? AS_ROWS_PER_SM : (NV 
                 if constexpr (FMT == 0) {
                     const uint2 *row = Cb4 + (int64_t)lab[c] * d4;
                     part[c] = lane_partial<NV>(xv, d4, [&](int col) { return bf16x4_to_float4(__ldg(row + col)); });
-                } else {
+                } else if constexpr (FMT == 1) {
                     const uint32_t *row = Cq4 + (int64_t)lab[c] * d4;
                     part[c] = lane_partial_q8<NV>(xv, d4, -__ldg(scale + lab[c]),
                                                   [&](int col) { return __ldg(row + col); });
+                } else {  // FMT 2: lane-major int8 rows, d = 128 NV
+                    uint32_t wq[NV];
+                    load_q8w<NV>(Cq4 + (int64_t)lab[c] * d4, wq);
+                    part[c] = lane_partial_q8w<NV>(xv, -__ldg(scale + lab[c]), wq);
                 }
             }
             const float dt = transpose_reduce<GS>(part);
@@ -490,7 +495,7 @@ __global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bf
 // Int8 shadow of the centroids: per row r the scale s_r = max_t |C_rt| / 127 (1 for a zero row), codes
 // q_rt = rint(C_rt / s_r) clamped to [-127, 127] and stored as q + 128, four per 32-bit word in the order of the
 // row's values; delta_r >= ||C_r - q_r s_r|| from the exact products q s in FP64.
-__global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, uint32_t *__restrict__ Cq,
+__global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, bool lane_major, uint32_t *__restrict__ Cq,
                             float *__restrict__ delta, float *__restrict__ scale)
 {
     const int lane = lane_id();
@@ -517,7 +522,9 @@ __global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, uint32_t 
                 const double diff = (double)vals[q] - (double)qf * (double)sc;  // q s exact in FP64
                 e += diff * diff;
             }
-            Cq[(int64_t)r * d4 + col] = word;
+            // row-major: word col; lane-major (d4 = 32 nv): the word of vector col = l + 32 v goes to l nv + v
+            const int nv = d4 >> 5;
+            Cq[(int64_t)r * d4 + (lane_major ? (col & 31) * nv + (col >> 5) : col)] = word;
         }
         for (int o = 16; o > 0; o >>= 1)
             e += __shfl_xor_sync(FULL_MASK, e, o);
@@ -809,10 +816,13 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     if ((precision == 2 || precision == 4) && vec4 && d4 <= 32 * 8) {
         // the shadow: BF16 (2) or int8 with a per-row scale (4); the int8 codes take the BF16 shadow's space
         const int sgrid = (k + 7) / 8 < 152 * 16 ? (k + 7) / 8 : 152 * 16;
+        // int8 rows lane-major where every lane owns whole vectors (d a multiple of 128): one load per lane and row
+        const bool lane_major = precision == 4 && d % 128 == 0;
         if (precision == 2)
             k_shadow_bf16<<<sgrid, 256, 0, s>>>(C, k, (int)d, Cb, delta, cnorm);
         else
-            k_shadow_i8<<<sgrid, 256, 0, s>>>(C, k, (int)d, reinterpret_cast<uint32_t *>(Cb), delta, cnorm);
+            k_shadow_i8<<<sgrid, 256, 0, s>>>(C, k, (int)d, lane_major, reinterpret_cast<uint32_t *>(Cb), delta,
+                                              cnorm);
 #define GK_ASB8F(NV, GS, F)                                                                                      \
     do {                                                                                                         \
         if ((e = resident_grid(reinterpret_cast<const void *>(k_assign_rows_scr<NV, XT, GS, F>), AS_WARPS * 32,  \
@@ -826,6 +836,8 @@ static cudaError_t assign_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     do {                                                                                                         \
         if (precision == 2)                                                                                      \
             GK_ASB8F(NV, GS, 0);                                                                                 \
+        else if (lane_major && d4 == 32 * NV)                                                                    \
+            GK_ASB8F(NV, GS, 2);                                                                                 \
         else                                                                                                     \
             GK_ASB8F(NV, GS, 1);                                                                                 \
     } while (0)

@@ -95,6 +95,49 @@ __device__ __forceinline__ float lane_partial_q8(const float4 (&xv)[NV], int d4,
     return a.x + a.y;
 }
 
+// The same partial for a row of the lane-major int8 shadow (d a multiple of 128): the NV words lane l needs,
+// those of vectors l, l + 32, ..., are contiguous, so they arrive in one load (NV = 4: 16 bytes); the values,
+// their order and the result are those of lane_partial_q8 on the row-major shadow.
+template <int NV>
+__device__ __forceinline__ float lane_partial_q8w(const float4 (&xv)[NV], float neg_s, const uint32_t (&w)[NV])
+{
+    const float2 ns2 = make_float2(neg_s, neg_s);
+    const float2 off2 = make_float2(-8388736.f, -8388736.f);  // -(2^23 + 128)
+    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        const float2 u01 = make_float2(__uint_as_float(__byte_perm(w[v], 0x4B000000u, 0x7540)),
+                                       __uint_as_float(__byte_perm(w[v], 0x4B000000u, 0x7541)));
+        const float2 u23 = make_float2(__uint_as_float(__byte_perm(w[v], 0x4B000000u, 0x7542)),
+                                       __uint_as_float(__byte_perm(w[v], 0x4B000000u, 0x7543)));
+        const float2 q01 = __fadd2_rn(u01, off2), q23 = __fadd2_rn(u23, off2);
+        const float2 e01 = __ffma2_rn(q01, ns2, make_float2(xv[v].x, xv[v].y));
+        const float2 e23 = __ffma2_rn(q23, ns2, make_float2(xv[v].z, xv[v].w));
+        a = __ffma2_rn(e01, e01, a);
+        a = __ffma2_rn(e23, e23, a);
+    }
+    return a.x + a.y;
+}
+
+// The NV words of this lane from a lane-major int8 shadow row (row points at the row's first word).
+template <int NV>
+__device__ __forceinline__ void load_q8w(const uint32_t *__restrict__ row, uint32_t (&w)[NV])
+{
+    const int lane = lane_id();
+    if constexpr (NV % 4 == 0) {
+#pragma unroll
+        for (int h = 0; h < NV / 4; h++) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row) + lane * (NV / 4) + h);
+            w[4 * h] = q.x, w[4 * h + 1] = q.y, w[4 * h + 2] = q.z, w[4 * h + 3] = q.w;
+        }
+    } else if constexpr (NV == 2) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row) + lane);
+        w[0] = q.x, w[1] = q.y;
+    } else {
+        w[0] = __ldg(row + lane);
+    }
+}
+
 // Complete one candidate's distance from the lane partials: the xor butterfly
 // pairs lanes by bit 4, then 3, 2, 1, 0, which is the grouping of
 // transpose_reduce32, so the total has the same bits as there.

@@ -91,8 +91,10 @@ struct VecT<1> {
 __device__ __forceinline__ float comp(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ float comp(const float &v, int) { return v; }
 
-// Accumulate one loaded row slice into the compensated sums.
-template <int VEC, int CPL>
+// Accumulate one loaded row slice into the compensated sums.  EXACT_SQ: every x * x is exact in FP32 (BF16
+// samples: 8 significant bits), so the fma that splits off the square's rounding error would give 0 and is
+// skipped (same bits).
+template <int VEC, int CPL, bool EXACT_SQ = false>
 __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL], float (&s)[CPL][VEC],
                                            float (&c)[CPL][VEC], float &qs, float &qc, int cb, int sub, int L, int nv)
 {
@@ -106,9 +108,9 @@ __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL]
                 // x^2 = p + e exactly (e from one fma); p is summed, e folded
                 // into the compensation term (true sum ~ qs - qc)
                 float p2 = x * x;
-                float e2 = fmaf(x, x, -p2);
                 kahan_add(qs, qc, p2);
-                qc -= e2;
+                if constexpr (!EXACT_SQ)
+                    qc -= fmaf(x, x, -p2);
             }
         }
     }
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
 #pragma unroll
                             for (int u = 0; u < CPL; u++)
                                 vz[u] = buf[(z * CPL + u) * 32 + lane];
-                            accumulate<VEC, CPL>(vz, s, c, qs, qc, cb, sub, L, nv);
+                            accumulate<VEC, CPL, std::is_same_v<XT, __nv_bfloat16>>(vz, s, c, qs, qc, cb, sub, L, nv);
                         }
                     }
                     __syncwarp();  // stage t & 1 is refilled by issue(t + 2)
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
 #pragma unroll
                     for (int z = 0; z < UNR; z++)
                         if (p0 + z * gstride < mc)
-                            accumulate<VEC, CPL>(v[z], s, c, qs, qc, cb, sub, L, nv);
+                            accumulate<VEC, CPL, std::is_same_v<XT, __nv_bfloat16>>(v[z], s, c, qs, qc, cb, sub, L, nv);
                 }
             }
         }
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__r
 #pragma unroll
                     for (int u = 0; u < NVL; u++)
                         v[u] = RV::widen(raw[z][u]);
-                    accumulate<4, NVL>(v, s, c, qs, qc, 0, lane, 32, nv);
+                    accumulate<4, NVL, std::is_same_v<XT, __nv_bfloat16>>(v, s, c, qs, qc, 0, lane, 32, nv);
                 }
             }
         }

@@ -298,7 +298,7 @@ def test_fit_precisions_identical(G):
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]) and a[3] == b[3]
 
 
-@pytest.mark.parametrize("d", [32, 128, 960])
+@pytest.mark.parametrize("d", [32, 128, 256, 512, 960])
 def test_assign_group_width_is_result_neutral(G, d):
     """The assignment's candidates per group (bits 8-15 of precision: 4 or 8, a tile shape the autotuner picks)
     change no bit of the labels, the winning distances or their sum, at levels 0, 2 and 4."""
