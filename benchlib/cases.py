@@ -3,6 +3,7 @@ summary's ncu command captured, on seeded synthetic samples generated here.
 
     python -m benchlib.cases deep_assign_bf16
     python -m benchlib.cases gist_refine
+    python -m benchlib.cases assign_large_table [--precision P]
     python -m benchlib.cases tree --n 1000000 --d 128 --k 10000 --iters 2 --calls 2
 
 deep_assign_bf16  10^6 x 512 BF16 deep-feature-shaped samples (200,000 vMF directions, kappa_vMF = 50, seed 11);
@@ -10,6 +11,8 @@ deep_assign_bf16  10^6 x 512 BF16 deep-feature-shaped samples (200,000 vMF direc
                   k = 100,000 (a centroid table far larger than L2, like the 10^7 x 512 workload's).
 gist_refine       3 x 10^5 x 960 GIST-shaped samples (1,000 latent centres, seed 5); graph construction with
                   kappa = 50, xi = 50, tau = 3 at precision 1 (the FP32 tile refinement at this width).
+assign_large_table  one assignment over a 10^6-row centroid table (10^6 x 512 BF16 unit vectors, k = 10^6,
+                  a random kappa = 40 graph, random labels); --precision selects the screening level.
 tree              the two-means tree (Alg. 1) on N(0, 1) samples drawn by a CUDA torch generator seeded with
                   --data-seed (BF16 with --bf16); --calls tree calls on one workspace, the first a warm-up;
                   prints one JSON line with the mean time of the other calls and the device status word.
@@ -48,6 +51,31 @@ def gist_refine(argv):
     print("gist_refine final distortion", log[-1])
 
 
+def assign_large_table(argv):
+    """One assignment at the deep-feature fit's ratios with a centroid table far larger than L2: 10^6 x 512 BF16
+    unit vectors (normalised N(0, 1), seed 5), k = 10^6 centroids on sampled rows, a random kappa = 40 graph and
+    random labels (about 41 distinct candidates per sample, as at 10^7 x 512, k = 10^6); --precision (default
+    4 with 4 candidates per group, the tuned setting there); two calls, the second the one to capture."""
+    import torch
+
+    from paper_1705_01813_gb300 import gkm
+    ap = argparse.ArgumentParser(prog="benchlib.cases assign_large_table")
+    ap.add_argument("--precision", type=int, default=4 | (4 << 8))
+    a = ap.parse_args(argv)
+    n, d, k, kappa = 1_000_000, 512, 1_000_000, 40
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.nn.functional.normalize(torch.randn((n, d), generator=g, device="cuda"), dim=1).to(torch.bfloat16)
+    gi = torch.randint(0, n, (n, kappa), generator=g, device="cuda", dtype=torch.int32)
+    L = torch.randint(0, k, (n,), generator=g, device="cuda", dtype=torch.int32)
+    C = X[torch.randint(0, n, (k,), generator=g, device="cuda")].float()
+    ws = gkm.workspace(gkm.workspace_size(gkm.GK_OP_ASSIGN, n, d, k, kappa), X.device)
+    out = torch.empty_like(L)
+    for _ in range(2):
+        gkm.assign_step(X, gi, C, L, out, None, None, None, a.precision, None, ws=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"changed": int((out != L).sum()), "status": gkm.read_status(ws)}))
+
+
 def tree(argv):
     import torch
 
@@ -83,7 +111,8 @@ def tree(argv):
                       "status": gkm.read_status(ws)}))
 
 
-CASES = {"deep_assign_bf16": deep_assign_bf16, "gist_refine": gist_refine, "tree": tree}
+CASES = {"deep_assign_bf16": deep_assign_bf16, "gist_refine": gist_refine, "assign_large_table": assign_large_table,
+         "tree": tree}
 
 
 def main(argv=None):
