@@ -411,6 +411,71 @@ def check_tree_root_split(orc):
         assert np.array_equal(L3 == 2, want == 1)
 
 
+def _np_tree(orc, X, k, iters, seed):
+    """Alg. 1 restated with every decision in FP64 (numpy): pop the largest cluster (shallowest, then leftmost),
+    seeds by the tree's draw, `iters` Lloyd 2-means passes with FP64 means (an empty half keeps its centre), then
+    the ceil(m/2) members of smallest (d(x, c_u) - d(x, c_v), id) form u.  Returns the labels (leaves numbered left
+    to right) and the smallest relative margin of any of its decisions (Lloyd side choices and the split
+    boundaries): above the FP32 oracle's rounding, the two must take every decision alike."""
+    X64 = X.astype(np.float64)
+    leaves = [(np.arange(X.shape[0]), 0)]
+    margin = np.inf
+    while len(leaves) < k:
+        j = max(range(len(leaves)), key=lambda q: (len(leaves[q][0]), -leaves[q][1], -q))
+        ids, depth = leaves[j]
+        a, b = _tree_seeds(orc, ids, depth, seed)
+        C = X64[[a, b]]
+        Y = X64[ids]
+        for _ in range(iters):
+            D = _np_d2(Y, C)
+            margin = min(margin, float(np.min(np.abs(D[:, 0] - D[:, 1]) / (D[:, 0] + D[:, 1] + 1e-300))))
+            C, _ = _np_means(Y, (D[:, 1] < D[:, 0]).astype(np.int64), 2, C)
+        D = _np_d2(Y, C)
+        key = D[:, 0] - D[:, 1]
+        order = np.lexsort((ids, key))
+        h = (len(ids) + 1) // 2
+        if 0 < h < len(ids):
+            ks = key[order]
+            margin = min(margin, float((ks[h] - ks[h - 1]) / (np.abs(D).max() + 1e-300)))
+        u, v = np.sort(ids[order[:h]]), np.sort(ids[order[h:]])
+        leaves[j:j + 1] = [(u, depth + 1), (v, depth + 1)]
+    L = np.empty(X.shape[0], np.int32)
+    for c, (ids, _) in enumerate(leaves):
+        L[ids] = c
+    return L, margin
+
+
+def _partition_sse(X, L, k):
+    C, _ = _np_means(X, L, k, np.zeros((k, X.shape[1])))
+    return float(((X.astype(np.float64) - C[L]) ** 2).sum())
+
+
+def check_tree_fp64_decisions(orc):
+    # the FP32-decision oracle (reading T3) against the same algorithm deciding in FP64: where no FP64 decision
+    # lies within 1e-4 (relative) of its threshold the labels are equal; otherwise the partition's quality is
+    # close to it (uniform samples, many clusters: margins down to about 1e-6) in its labels and distortion
+    g = np.random.default_rng(15)
+    exact = 0
+    cases = [(200, 3, 5, 0, 1), (200, 3, 5, 2, 2), (333, 6, 9, 1, 3), (150, 2, 16, 3, 4), (400, 8, 7, 2, 5),
+             (120, 4, 30, 1, 6), (600, 5, 12, 2, 7), (2000, 2, 40, 2, 8), (3000, 1, 50, 1, 9), (1500, 3, 60, 3, 10)]
+    for q, (n, d, k, iters, seed) in enumerate(cases):
+        if q < 7:
+            X = (g.uniform(-5, 5, (6, d))[g.integers(0, 6, n)] + g.standard_normal((n, d))).astype(np.float32)
+        else:
+            X = g.uniform(-1, 1, (n, d)).astype(np.float32)
+        want, margin = _np_tree(orc, X, k, iters, seed)
+        got = orc.two_means_tree(X, k, iters=iters, seed=seed)
+        assert np.bincount(got, minlength=k).tolist() == np.bincount(want, minlength=k).tolist()
+        if margin > 1e-4:
+            assert np.array_equal(got, want), (n, d, k, iters, margin)
+            exact += 1
+        else:
+            assert (got == want).mean() >= 0.95, (n, d, k, iters, margin)
+            e64, e32 = _partition_sse(X, want, k), _partition_sse(X, got, k)
+            assert abs(e32 - e64) <= 1e-3 * e64, (e32, e64)
+    assert exact >= 3  # most cases decide with a margin: the equality above is exercised
+
+
 def check_tree_blobs(orc):
     # 8 tight, well separated blobs of 64 samples: the equal-size splits fall between blobs, one blob per cluster
     g = np.random.default_rng(14)
@@ -429,7 +494,7 @@ CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assi
           check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
           check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
           check_init_graph_rows, check_group_csr, check_tree_sizes, check_tree_1d, check_tree_root_split,
-          check_tree_blobs]
+          check_tree_fp64_decisions, check_tree_blobs]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
@@ -494,6 +559,8 @@ MUTANTS = [
     ("tree_no_iterations", "it < iters; it++", "it < 0; it++", check_tree_root_split),
     ("tree_depth_tiebreak_dropped", "(depth[r] < depth[s] ||", "(0 ||", check_tree_sizes),
     ("tree_labels_by_creation", "labels[perm[p]] = rank;", "labels[perm[p]] = s;", check_tree_sizes),
+    ("tree_seed_depth_ignored", "((uint64_t)(uint32_t)depth << 32)", "((uint64_t)0 << 32)",
+     check_tree_fp64_decisions),
     ("tree_v_keeps_left_range", "off[t] = off[s] + h; /* v */", "off[t] = off[s]; off[s] += m - h; /* v */",
      check_tree_1d),
 ]
