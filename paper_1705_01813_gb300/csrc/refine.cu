@@ -167,7 +167,8 @@ static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     // The tensor-core path for 64 <= d <= 128.  Its Gram is exact only for integer data with 2 d 255^2 < 2^24
     // (d <= 128), and wider rows made the recompute of every kept pair dearer than the FP32 tile kernels
     // (1M x 960 FP32: 91 ms against 25 ms per call; 10M x 512 BF16 unit vectors, whose Gram carries no BF16
-    // rounding but whose pairs mostly may enter a row: 106 ms against 86 ms); for d < 64 the tile kernels'
+    // rounding but of whose pairs about 45% may enter a row in every round: 106 ms against 86 ms); for d < 64 the
+    // tile kernels'
     // cost, proportional to d, is below the fixed per-run cost of the Gram path (20k x 32: 0.18 ms against
     // 0.12 ms per call).
     if (precision >= 1 && d >= 64 && d <= 128) {

@@ -42,8 +42,8 @@
 #include "common.cuh"
 #include "merge.cuh"
 #include "tc.cuh"
+#include "tmap.cuh"
 
-#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from cudaGetDriverEntryPointByVersion)
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -518,22 +518,28 @@ static cudaError_t encode_tiled(EncodeTiledFn *fn)
     return err;
 }
 
-// Tensor map of the cluster-sorted copy: n rows of dp BF16 (row stride dp * 2 bytes, a multiple of 16), boxes of
-// 64 columns x 128 rows in the 128-byte swizzle layout, rows past n read as zeros.
-static cudaError_t perm_tensor_map(CUtensorMap *tm, const __nv_bfloat16 *Xp, int64_t n, int64_t dp)
+cudaError_t bf16_tensor_map(CUtensorMap *tm, const void *base, int64_t cols, int64_t rows, int64_t row_elems,
+                            uint32_t box_cols, uint32_t box_rows)
 {
     EncodeTiledFn fn = nullptr;
     cudaError_t e = encode_tiled(&fn);
     if (e != cudaSuccess)
         return e;
-    const cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)TC_KB, (cuuint32_t)TC_M};
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)row_elems * 2};
+    const cuuint32_t box[2] = {box_cols, box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(Xp), dims, strides,
-                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tensor map of the cluster-sorted copy: n rows of dp BF16 (row stride dp * 2 bytes, a multiple of 16), boxes of
+// 64 columns x 128 rows in the 128-byte swizzle layout, rows past n read as zeros.
+static cudaError_t perm_tensor_map(CUtensorMap *tm, const __nv_bfloat16 *Xp, int64_t n, int64_t dp)
+{
+    return bf16_tensor_map(tm, Xp, dp, n, dp, TC_KB, TC_M);
 }
 
 template <typename XT>

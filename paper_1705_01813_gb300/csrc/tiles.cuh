@@ -50,20 +50,25 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     const int tid = threadIdx.x;
     // this thread: rows Q by .. Q by + Q - 1, columns Q bx .. Q bx + Q - 1 of the tile.  Two tiles: block
     // (by, bx) = (tid / 16, tid % 16), and warps whose rows all lie beyond the run skip the arithmetic.  A run's
-    // own tile (SAME) is symmetric, d(i, j) = d(j, i) bit for bit (the difference only changes sign): threads
-    // 0 .. 135 take the blocks with by <= bx, row by row, so that warps 5 to 7 skip the arithmetic, and each
-    // block is also written mirrored.
+    // own tile (SAME) is symmetric, d(i, j) = d(j, i) bit for bit (the difference only changes sign): only the
+    // nb (nb + 1) / 2 blocks with by <= bx < nb = ceil(nr / Q) hold pairs of the run, and they go to threads
+    // 0, 1, ... row by row (a run of 50 fills 91 threads, three warps; the other warps skip the arithmetic);
+    // each block is also written mirrored.
     int by = tid >> 4, bx = tid & 15;
+    bool rows_live;
     if constexpr (SAME) {
+        const int nb = (nr + Q - 1) / Q;
         int t = tid, r = 0;
-        while (r < 16 && t >= 16 - r) {
-            t -= 16 - r;
+        while (r < nb && t >= nb - r) {
+            t -= nb - r;
             r++;
         }
         by = r;
         bx = r + t;
+        rows_live = r < nb;
+    } else {
+        rows_live = Q * by < nr;
     }
-    const bool rows_live = SAME ? (by < 16 && Q * bx < nr) : (Q * by < nr);
     const float2 m1 = make_float2(-1.f, -1.f);
     float2 acc[Q][Q / 2];
 #pragma unroll

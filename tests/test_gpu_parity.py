@@ -270,6 +270,9 @@ def test_exact_knn_special_case(G, precision):
     (20011, 64, 9000, 60, "random"),  # random labels and graph: unions overflow, SIMT leftovers
     (20000, 128, 300, 50, "knn"),     # SIFT-like width, mid-size unions
     (517, 16, 3, 20, "knn"),          # partial last tile, three clusters
+    (5001, 96, 2500, 24, "random"),   # second K-block half past d (zero-filled), unions of 20-odd chunks
+    (4099, 64, 800, 20, "random"),    # one K-block, unions of about a dozen chunks
+    (6007, 128, 5000, 12, "random"),  # unions of 1,300-1,600 columns, some tiles near the 2,048 cap
 ])
 def test_assign_tensor_core_tiles_equal_fp32(G, n, d, k, kappa, graph):
     """Tensor-core screening over 128-sample tiles (with the SIMT kernel for tiles whose
