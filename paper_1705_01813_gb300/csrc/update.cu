@@ -91,29 +91,64 @@ struct VecT<1> {
 __device__ __forceinline__ float comp(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ float comp(const float &v, int) { return v; }
 
-// Accumulate one loaded row slice into the compensated sums.  EXACT_SQ: every x * x is exact in FP32 (BF16
-// samples: 8 significant bits), so the fma that splits off the square's rounding error would give 0 and is
-// skipped (same bits).
+// The Kahan step of kahan_add on two sums at once, in packed FP32x2 instructions with the same roundings (a - b
+// as fma(b, -1, a), a + b as fma(a, 1, b): each rounded once, as the scalar operations are).
+__device__ __forceinline__ void kahan_add2(float &s0, float &s1, float &c0, float &c1, float2 x)
+{
+    const float2 m1 = make_float2(-1.f, -1.f), p1 = make_float2(1.f, 1.f);
+    const float2 S = make_float2(s0, s1), Cc = make_float2(c0, c1);
+    const float2 y = __ffma2_rn(Cc, m1, x);                     // x - c
+    const float2 t = __ffma2_rn(S, p1, y);                      // s + y
+    const float2 cn = __ffma2_rn(y, m1, __ffma2_rn(S, m1, t));  // (t - s) - y
+    s0 = t.x, s1 = t.y, c0 = cn.x, c1 = cn.y;
+}
+
+// Accumulate one loaded row slice into the compensated sums: per coordinate the Kahan sum of x, and the sum of
+// squares as two compensated chains (qs.x takes the even coordinates of a vector, qs.y the odd ones), each
+// square x^2 = p + e split exactly (e from one fma), p summed and e folded into the compensation term (the true
+// sum being about qs - qc).  16-byte vectors run in packed FP32x2 instructions.  EXACT_SQ: every x * x is exact
+// in FP32 (BF16 samples: 8 significant bits), so the fma that splits off the square's rounding error would give 0
+// and is skipped (same bits).
 template <int VEC, int CPL, bool EXACT_SQ = false>
 __device__ __forceinline__ void accumulate(const typename VecT<VEC>::T (&v)[CPL], float (&s)[CPL][VEC],
-                                           float (&c)[CPL][VEC], float &qs, float &qc, int cb, int sub, int L, int nv)
+                                           float (&c)[CPL][VEC], float2 &qs, float2 &qc, int cb, int sub, int L,
+                                           int nv)
 {
 #pragma unroll
     for (int u = 0; u < CPL; u++) {
         if (cb + sub + u * L < nv) {
-#pragma unroll
-            for (int q = 0; q < VEC; q++) {
-                float x = comp(v[u], q);
-                kahan_add(s[u][q], c[u][q], x);
-                // x^2 = p + e exactly (e from one fma); p is summed, e folded
-                // into the compensation term (true sum ~ qs - qc)
-                float p2 = x * x;
-                kahan_add(qs, qc, p2);
+            if constexpr (VEC == 4) {
+                const float2 m1 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
+                const float2 xa = make_float2(comp(v[u], 0), comp(v[u], 1));
+                const float2 xb = make_float2(comp(v[u], 2), comp(v[u], 3));
+                kahan_add2(s[u][0], s[u][1], c[u][0], c[u][1], xa);
+                kahan_add2(s[u][2], s[u][3], c[u][2], c[u][3], xb);
+                const float2 pa = __ffma2_rn(xa, xa, z2), pb = __ffma2_rn(xb, xb, z2);
+                kahan_add2(qs.x, qs.y, qc.x, qc.y, pa);
                 if constexpr (!EXACT_SQ)
-                    qc -= fmaf(x, x, -p2);
+                    qc = __ffma2_rn(__ffma2_rn(xa, xa, make_float2(-pa.x, -pa.y)), m1, qc);
+                kahan_add2(qs.x, qs.y, qc.x, qc.y, pb);
+                if constexpr (!EXACT_SQ)
+                    qc = __ffma2_rn(__ffma2_rn(xb, xb, make_float2(-pb.x, -pb.y)), m1, qc);
+            } else {
+#pragma unroll
+                for (int q = 0; q < VEC; q++) {
+                    const float x = comp(v[u], q);
+                    kahan_add(s[u][q], c[u][q], x);
+                    const float p2 = x * x;
+                    kahan_add(qs.x, qc.x, p2);
+                    if constexpr (!EXACT_SQ)
+                        qc.x -= fmaf(x, x, -p2);
+                }
             }
         }
     }
+}
+
+// The sum of squares of a lane's compensated chains, as a double-float value.
+__device__ __forceinline__ DF chains_sum(float2 qs, float2 qc)
+{
+    return df_add(fast_two_sum(qs.x, -qc.x), fast_two_sum(qs.y, -qc.y));
 }
 
 // One block of UP_WARPS warps per cluster.  Each warp is split into G groups
@@ -182,7 +217,7 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
     DF sq_lane = {0.f, 0.f}, dd_lane = {0.f, 0.f};
     for (int cb = 0; cb < nv; cb += L * CPL) {
         float s[CPL][VEC], c[CPL][VEC];
-        float qs = 0.f, qc = 0.f;
+        float2 qs = make_float2(0.f, 0.f), qc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < CPL; u++)
 #pragma unroll
@@ -265,7 +300,7 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
         }
         if constexpr (PIPE)
             __syncthreads();  // every warp is done with the ring before the partial sums overwrite it
-        sq_lane = df_add(sq_lane, fast_two_sum(qs, -qc));
+        sq_lane = df_add(sq_lane, chains_sum(qs, qc));
         // combine the G groups of the warp, then the warps of the block, in a fixed order
 #pragma unroll
         for (int u = 0; u < CPL; u++) {
@@ -318,13 +353,18 @@ __global__ void __launch_bounds__(UP_WARPS * 32) k_update(const XT *__restrict__
     }
 }
 
-// Clusters of at most US_MAXM members, one warp each (the deep-feature workload's clusters hold about ten):
+// Clusters of at most maxm members, one warp each (the deep-feature workload's clusters hold about ten):
 // lane l owns row vectors l, l + 32, ... (NVL of them); the members' rows stream through the warp RIF at a
 // time, and every coordinate is summed over the members in member order with compensated FP32 arithmetic,
 // then combined and divided as in k_update.  No shared memory and no block barrier, so a cluster costs a
 // few dependent loads instead of a block's set-up.
 constexpr int US_WARPS = 8;
-constexpr int US_MAXM = 32;
+// Largest cluster of the warp kernel: 32 members for rows of at most 128 values (larger clusters of such rows are
+// faster in k_update's block: 1M x 128 FP32, clusters of about 100: 0.173 against 0.223 ms per call), 128 members
+// for wider rows (10M x 512 BF16, clusters of about 10 and 50: 3.8 against 5.1 ms).  The rule depends on the row
+// width only, so BF16 samples and their FP32 widening take the same kernel for every cluster.
+constexpr int US_MAXM_NARROW = 32;
+constexpr int US_MAXM_WIDE = 128;
 
 // A row vector of 4 elements as loaded (16 bytes of FP32, 8 bytes of BF16), widened when it is summed.
 template <typename XT>
@@ -347,7 +387,7 @@ struct RawVec<__nv_bfloat16> {
 template <int NVL, typename XT>
 __global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__restrict__ X, int d, int64_t ld,
                                                                 const int32_t *__restrict__ off,
-                                                                const int32_t *__restrict__ mem, int k,
+                                                                const int32_t *__restrict__ mem, int k, int maxm,
                                                                 float *__restrict__ C, int32_t *__restrict__ counts,
                                                                 double *__restrict__ contrib, DevStatus *st)
 {
@@ -357,7 +397,7 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__r
     const int nv = d / 4;
     for (int r = blockIdx.x * US_WARPS + w; r < k; r += gridDim.x * US_WARPS) {
         const int beg = off[r], m = off[r + 1] - beg;
-        if (m > US_MAXM)
+        if (m > maxm)
             continue;  // a cluster of k_update
         if (counts && lane == 0)
             counts[r] = m;
@@ -366,15 +406,21 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__r
                 contrib[r] = 0.0;
             continue;
         }
-        const int myid = lane < m ? __ldg(mem + beg + lane) : 0;
+        // member ids 32 at a time (lane l holds id p + l of the current 32), the next 32 loaded one chunk ahead
+        int myid = lane < m ? __ldg(mem + beg + lane) : 0;
+        int nxtid = 32 + lane < m ? __ldg(mem + beg + 32 + lane) : 0;
         float s[NVL][4], c[NVL][4];
 #pragma unroll
         for (int u = 0; u < NVL; u++)
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 s[u][q] = c[u][q] = 0.f;
-        float qs = 0.f, qc = 0.f;
+        float2 qs = make_float2(0.f, 0.f), qc = make_float2(0.f, 0.f);
         for (int p0 = 0; p0 < m; p0 += RIF) {
+            if (p0 > 0 && (p0 & 31) == 0) {  // RIF divides 32
+                myid = nxtid;
+                nxtid = p0 + 32 + lane < m ? __ldg(mem + beg + p0 + 32 + lane) : 0;
+            }
             typename RV::T raw[RIF][NVL];
 #pragma unroll
             for (int z = 0; z < RIF; z++) {
@@ -398,7 +444,7 @@ __global__ void __launch_bounds__(US_WARPS * 32, 3) k_update_small(const XT *__r
             }
         }
         const float mf = (float)m, inv_m = 1.0f / mf;
-        DF sq = fast_two_sum(qs, -qc), dd = {0.f, 0.f};
+        DF sq = chains_sum(qs, qc), dd = {0.f, 0.f};
 #pragma unroll
         for (int u = 0; u < NVL; u++) {
             const int col = lane + 32 * u;
@@ -461,10 +507,11 @@ static cudaError_t update_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     const int need = (nv + L - 1) / L;  // vectors per lane to cover a row in one column block
     const int dd = (int)d;
     constexpr bool PIPE = std::is_same_v<XT, float>;  // FP32 rows stream through the cp.async ring
-    // clusters of at most US_MAXM members go to the warp-per-cluster kernel where rows are 16-byte vectors of at
-    // most 4 per lane and the centroid rows 16-byte aligned; the block kernel takes the others
+    // clusters of at most small_max members go to the warp-per-cluster kernel where rows are 16-byte vectors of
+    // at most 4 per lane and the centroid rows 16-byte aligned; the block kernel takes the others (which kernel
+    // sums a cluster depends on its size and the row width only)
     const bool small = vec4 && nv <= 32 * 4 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
-    const int small_max = small ? US_MAXM : -1;
+    const int small_max = small ? (nv > 32 ? US_MAXM_WIDE : US_MAXM_NARROW) : -1;
     cudaError_t e;
     if (small) {
         int g = 0;
@@ -473,8 +520,8 @@ static cudaError_t update_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
         if ((e = resident_grid(reinterpret_cast<const void *>(k_update_small<NVL, XT>), US_WARPS * 32, 0, &g)) !=   \
             cudaSuccess)                                                                                         \
             return e;                                                                                            \
-        k_update_small<NVL, XT><<<(unsigned)g, US_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, C, counts,  \
-                                                                      contrib, st);                              \
+        k_update_small<NVL, XT><<<(unsigned)g, US_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, small_max, \
+                                                                      C, counts, contrib, st);                   \
     } while (0)
         if (nv <= 32)
             GK_UPS(1);
@@ -500,7 +547,7 @@ static cudaError_t update_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     // of uneven sizes to SMs as blocks finish); where most clusters are small, a one-wave grid walks the few
     // large ones instead of launching a block per cluster that would return at once.  Which block sums a
     // cluster changes none of its bits.
-    const bool mostly_small = small && n <= (int64_t)k * US_MAXM;
+    const bool mostly_small = small && n <= (int64_t)k * small_max;
     const unsigned grid = (unsigned)(mostly_small ? (k < bg ? k : bg) : k);
 #define GK_UPD(VEC, CPL, P) \
     k_update<VEC, CPL, P, XT><<<grid, UP_WARPS * 32, 0, s>>>(X, dd, ld, offsets, members, k, small_max, C, counts, \

@@ -81,7 +81,7 @@ def test_assign_tensor_core_screening_rejects_bf16_samples(G, precision):
 
 
 @pytest.mark.parametrize("n,d,k,ld", [(20000, 32, 200, None), (5003, 36, 97, None), (4099, 33, 600, None),
-                                      (3001, 960, 40, None), (7001, 24, 50, 40)])
+                                      (3001, 960, 40, None), (7001, 24, 50, 40), (12000, 256, 120, None)])
 def test_update_step(G, n, d, k, ld):
     xb, xf = _pair(n, d, n + 1, ld=ld)
     L = G.init_labels(n, k, 7)

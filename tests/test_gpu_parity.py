@@ -150,7 +150,8 @@ def test_assign_complete_graph_is_lloyd(G):
 
 @pytest.mark.parametrize("n,d,k", [(20000, 32, 200), (5003, 36, 97), (4099, 33, 6000), (3001, 960, 40),
                                    (1000, 1, 1), (257, 1030, 3), (70000, 8, 70000),
-                                   (2003, 200, 50), (1501, 512, 30), (777, 1028, 9)])  # 2, 4, 8 x 2 vectors per lane
+                                   (2003, 200, 50), (1501, 512, 30), (777, 1028, 9),  # 2, 4, 8 x 2 vectors per lane
+                                   (20011, 256, 150), (9001, 132, 80)])  # clusters around 128: both update kernels
 def test_update_lockstep(G, n, d, k):
     X = _blobs(n, d, 7, d)
     g = np.random.default_rng(n)
