@@ -493,8 +493,16 @@ __global__ void k_shadow_bf16(const float *__restrict__ C, int k, int d, __nv_bf
 }
 
 // Int8 shadow of the centroids: per row r the scale s_r = max_t |C_rt| / 127 (1 for a zero row), codes
-// q_rt = rint(C_rt / s_r) clamped to [-127, 127] and stored as q + 128, four per 32-bit word in the order of the
-// row's values; delta_r >= ||C_r - q_r s_r|| from the exact products q s in FP64.
+// q_rt = rint(C_rt / s_r) (the quotient taken as a product with 1 / s_r) clamped to [-127, 127] and stored as
+// q + 128, four per 32-bit word in the order of the row's values, and delta_r >= ||C_r - q_r s_r||, in FP32
+// only.  Each error v - q s is formed as (v - p) - e with p = fl(q s) and e = fma(q, s, -p) (q s = p + e
+// exactly); v - p is exact where p/2 <= v <= 2p (Sterbenz; |q| >= 1 puts v within half a step of q s), so the
+// computed error is within 2u |v - q s| + 1.01 u^2 max|C_r| of the true one (u = 2^-24).  The errors are squared
+// in units of w = max(s, FLT_MIN) (so that no square of a row of tiny values falls below the normal range) and
+// summed in FP32 (d fma steps and the warp's 5 additions: relative error below gamma_(d+5), one more u for the
+// division by w); delta_r inflates the square root by (d + 24) 1.2e-7 and 1e-5 (the 1 / (1 - 2u) above and this
+// evaluation's own roundings) and adds sqrt(d) 4e-15 max|C_r| (the absolute term, which also covers squares
+// below the normal range): a rigorous upper bound, no FP64.
 __global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, bool lane_major, uint32_t *__restrict__ Cq,
                             float *__restrict__ delta, float *__restrict__ scale)
 {
@@ -510,17 +518,21 @@ __global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, bool lane
         for (int o = 16; o > 0; o >>= 1)
             mx = fmaxf(mx, __shfl_xor_sync(FULL_MASK, mx, o));
         const float sc = mx > 0.f ? mx / 127.f : 1.f;
-        double e = 0.0;
+        const float inv = 1.f / sc;
+        const float wu = fmaxf(sc, 1.17549435e-38f), winv = 1.f / wu;  // error unit (FLT_MIN at least)
+        float e = 0.f;
         for (int col = lane; col < d4; col += 32) {
             const float4 v = row[col];
             const float vals[4] = {v.x, v.y, v.z, v.w};
             uint32_t word = 0;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const float qf = fminf(127.f, fmaxf(-127.f, rintf(vals[q] / sc)));
+                const float qf = fminf(127.f, fmaxf(-127.f, rintf(vals[q] * inv)));
                 word |= (uint32_t)((int)qf + 128) << (8 * q);
-                const double diff = (double)vals[q] - (double)qf * (double)sc;  // q s exact in FP64
-                e += diff * diff;
+                const float p = qf * sc;
+                const float pe = fmaf(qf, sc, -p);  // q s = p + pe exactly
+                const float z = ((vals[q] - p) - pe) * winv;
+                e = fmaf(z, z, e);
             }
             // row-major: word col; lane-major (d4 = 32 nv): the word of vector col = l + 32 v goes to l nv + v
             const int nv = d4 >> 5;
@@ -529,7 +541,8 @@ __global__ void k_shadow_i8(const float *__restrict__ C, int k, int d, bool lane
         for (int o = 16; o > 0; o >>= 1)
             e += __shfl_xor_sync(FULL_MASK, e, o);
         if (lane == 0) {
-            delta[r] = (float)(sqrt(e) * (1.0 + 1e-6)) + 1e-30f;  // rounded up
+            delta[r] = sqrtf(e * (1.f + (float)(d + 24) * 1.2e-7f)) * 1.00001f * wu + sqrtf((float)d) * 4e-15f * mx +
+                       1e-30f;
             scale[r] = sc;
         }
     }

@@ -109,7 +109,7 @@ def test_assign_lockstep(G, n, d, k, kappa, precision):
     assert ex <= max(2, n // 1000)
 
 
-@pytest.mark.parametrize("data", ["blobs", "far", "sift", "gist"])
+@pytest.mark.parametrize("data", ["blobs", "far", "tiny", "huge", "sift", "gist"])
 def test_assign_bf16_shadow_equals_fp32(G, data):
     """Candidates against the BF16 centroid copy, with the exact recompute inside the
     error bound, give the FP32 kernel's labels, distances, sum and count bit for bit."""
@@ -117,6 +117,10 @@ def test_assign_bf16_shadow_equals_fp32(G, data):
         X = _blobs(20000, 64, 100, 1)
     elif data == "far":
         X = (_blobs(20000, 64, 100, 2) + 500.0).astype(np.float32)
+    elif data == "tiny":  # per-row int8 scales near 1e-7, error bounds near 1e-9
+        X = (_blobs(20000, 64, 100, 3) * 1e-8).astype(np.float32)
+    elif data == "huge":
+        X = (_blobs(20000, 64, 100, 4) * 1e12).astype(np.float32)
     elif data == "sift":
         X = datagen.sift_like(20000, 128, 500, seed=3)
     else:
