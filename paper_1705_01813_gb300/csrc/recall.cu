@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_nn_tiles(const XT *__restrict__ 
         if (tid < NN_T)
             cid[tid] = j0 + tid < n ? (int)(j0 + tid) : -1;
         __syncthreads();
-        tile_distances<NN_T, false>(X, d, ld, rid, cid, nr, xr, dt);
+        tile_distances<NN_T, false, false>(X, d, ld, rid, cid, nr, xr, dt);
         __syncthreads();
         // warp w: queries w, w + 8, ..., the smallest key of the tile's samples other than the query
         for (int row = w; row < nr; row += RF_WARPS) {

@@ -50,7 +50,7 @@ __global__ void k_count_runs(const int32_t *__restrict__ off, int k, int cap, in
     }
 }
 
-template <int T, typename XT>
+template <int T, typename XT, bool VEC>
 __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
                                                        const int32_t *__restrict__ off,
                                                        const int32_t *__restrict__ mem,
@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT
                 }
                 __syncthreads();
                 if (same)
-                    tile_distances<T, true>(X, d, ld, rid, cid, nr, xr, dt);
+                    tile_distances<T, true, VEC>(X, d, ld, rid, cid, nr, xr, dt);
                 else
-                    tile_distances<T, false>(X, d, ld, rid, cid, nr, xr, dt);
+                    tile_distances<T, false, VEC>(X, d, ld, rid, cid, nr, xr, dt);
                 __syncthreads();
                 RowRegs cur, nxt;
                 if (w < nr && rid[w] >= 0)
@@ -140,8 +140,8 @@ size_t refine_scratch_bytes(int64_t n, int32_t k, int64_t d)
     return run_bytes(k) + run_cl_bytes(n, k) + scan_scratch_bytes(k) + refine_tc_scratch_bytes(n, k, d);
 }
 
-template <typename XT>
-static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+template <typename XT, bool VEC>
+static cudaError_t refine_tv(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
                             const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
                             float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision)
 {
@@ -152,10 +152,10 @@ static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
     size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
     cudaError_t e =
-        set_max_smem(reinterpret_cast<const void *>(k_refine<64, XT>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
+        set_max_smem(reinterpret_cast<const void *>(k_refine<64, XT, VEC>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
     if (e != cudaSuccess)
         return e;
-    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128, XT>),
+    if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128, XT, VEC>),
                           (int)RefineTile<128>::smem_bytes(MAX_KAPPA))) != cudaSuccess)
         return e;
     k_count_runs<<<(k + 255) / 256 < 1024 ? (k + 255) / 256 : 1024, 256, 0, s>>>(offsets, k, max_cluster, nruns);
@@ -178,17 +178,31 @@ static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const
                                   g_idx, g_dist, tc_scratch, st, s)) != cudaSuccess)
             return e;
         if (max_cluster > 128)
-            k_refine<128, XT><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
+            k_refine<128, XT, VEC><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off,
                                                                      run_cl, k, kappa, max_cluster, 128, g_idx,
                                                                      g_dist, st);
         return cudaGetLastError();
     }
     // runs of <= 64 members, then the longer runs (up to 128 per tile, longer runs in tiles)
-    k_refine<64, XT><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+    k_refine<64, XT, VEC><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                            kappa, max_cluster, 0, g_idx, g_dist, st);
-    k_refine<128, XT><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
+    k_refine<128, XT, VEC><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                              kappa, max_cluster, 64, g_idx, g_dist, st);
     return cudaGetLastError();
+}
+
+// the tile kernels with 16-byte stage loads where the rows allow them, for BF16 rows (eight elements per load
+// instead of one 2-byte load each; FP32 rows keep the element loads, whose kernel uses fewer registers)
+template <typename XT>
+static cudaError_t refine_t(const XT *X, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,
+                            const int32_t *members, int32_t k, int32_t kappa, int32_t max_cluster, int32_t *g_idx,
+                            float *g_dist, void *scratch, DevStatus *st, cudaStream_t s, int precision)
+{
+    if (std::is_same_v<XT, __nv_bfloat16> && tile_vec16(X, (int)d, ld))
+        return refine_tv<XT, true>(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, scratch, st, s,
+                                   precision);
+    return refine_tv<XT, false>(X, n, d, ld, offsets, members, k, kappa, max_cluster, g_idx, g_dist, scratch, st, s,
+                                precision);
 }
 
 cudaError_t launch_refine(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *offsets,

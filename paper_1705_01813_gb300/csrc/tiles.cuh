@@ -37,11 +37,38 @@ struct RefineTile {
     __host__ __device__ static size_t smem_bytes(int kappa) { return fixed_bytes + RF_WARPS * warp_bytes(kappa); }
 };
 
+// 16 bytes of sample elements (4 FP32 or 8 BF16) widened to floats.
+template <typename XT>
+__device__ __forceinline__ void widen16(const uint4 &q, float (&v)[16 / sizeof(XT)])
+{
+    if constexpr (sizeof(XT) == 4) {
+        v[0] = __uint_as_float(q.x), v[1] = __uint_as_float(q.y), v[2] = __uint_as_float(q.z),
+        v[3] = __uint_as_float(q.w);
+    } else {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            v[2 * i] = __uint_as_float(w[i] << 16);
+            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+}
+
+// Rows whose stage segments can be read as aligned 16-byte vectors: d and the row stride multiples of the
+// vector, the base 16-byte aligned (then every segment t0 .. t0 + RF_DK of a row is).
+template <typename XT>
+__host__ __device__ inline bool tile_vec16(const XT *X, int d, int64_t ld)
+{
+    constexpr int E = 16 / (int)sizeof(XT);
+    return d % E == 0 && ld % E == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
 // Pair distances of one T x T tile into dt[row * DS + col]: rows are the samples rid[0 .. nr),
 // columns the samples cid[] (SAME: the rows again).  stage points at the block's staging area
 // (RefineTile<T>::stage_floats floats), dt at the distance tile, which may alias it.  Called by all threads
-// of the block; the caller synchronises before reading dt.
-template <int T, bool SAME, typename XT>
+// of the block; the caller synchronises before reading dt.  VEC: the rows meet tile_vec16, and each stage is
+// fetched as 16-byte vectors (one load per 4 or 8 elements) instead of element by element.
+template <int T, bool SAME, bool VEC, typename XT>
 __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, int64_t ld, const int *rid,
                                                const int *cid, int nr, float *stage, float *dt)
 {
@@ -57,8 +84,12 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     int by = tid >> 4, bx = tid & 15;
     bool rows_live;
     if constexpr (SAME) {
+        // the arithmetic goes to the block's warps rot, rot + 1, ... (rot = blockIdx.x % 4): each warp of an SM
+        // issues on scheduler (its index % 4), so blocks that share an SM spread their few busy warps over all
+        // four schedulers instead of all starting at scheduler 0
+        const int rot = (int)(blockIdx.x & 3) * 32;
         const int nb = (nr + Q - 1) / Q;
-        int t = tid, r = 0;
+        int t = (tid - rot) & (RF_THREADS - 1), r = 0;
         while (r < nb && t >= nb - r) {
             t -= nb - r;
             r++;
@@ -79,16 +110,35 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     // coordinates t0 .. t0+31 of the row and column samples, zero padded, are loaded into
     // registers one stage ahead (their loads in flight during the previous stage's arithmetic)
     constexpr int PER = T * RF_DK / RF_THREADS;
-    float pr_v[PER], pc_v[SAME ? 1 : PER];
+    constexpr int E = 16 / (int)sizeof(XT), CPR = RF_DK / E;  // vector path: elements per vector, vectors per row
+    constexpr int PERV = T * CPR / RF_THREADS;
+    static_assert(PERV >= 1 && (T * CPR) % RF_THREADS == 0, "whole vectors per thread");
+    float pr_v[VEC ? 1 : PER], pc_v[(SAME || VEC) ? 1 : PER];
+    uint4 qr[VEC ? PERV : 1], qc[(SAME || !VEC) ? 1 : PERV];
     auto fetch = [&](int t0) {
+        if constexpr (VEC) {
 #pragma unroll
-        for (int p = 0; p < PER; p++) {
-            const int e = tid + p * RF_THREADS, row = e / RF_DK, t = t0 + e % RF_DK;
-            const int a = rid[row];
-            pr_v[p] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
-            if constexpr (!SAME) {
-                const int b = cid[row];
-                pc_v[p] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
+            for (int p = 0; p < PERV; p++) {
+                const int e = tid + p * RF_THREADS, row = e / CPR, t = t0 + (e % CPR) * E;
+                const int a = rid[row];
+                qr[p] = (a >= 0 && t < d) ? __ldg(reinterpret_cast<const uint4 *>(X + (int64_t)a * ld + t))
+                                          : make_uint4(0u, 0u, 0u, 0u);
+                if constexpr (!SAME) {
+                    const int b = cid[row];
+                    qc[p] = (b >= 0 && t < d) ? __ldg(reinterpret_cast<const uint4 *>(X + (int64_t)b * ld + t))
+                                              : make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < PER; p++) {
+                const int e = tid + p * RF_THREADS, row = e / RF_DK, t = t0 + e % RF_DK;
+                const int a = rid[row];
+                pr_v[p] = (a >= 0 && t < d) ? ldx(X + (int64_t)a * ld + t) : 0.f;
+                if constexpr (!SAME) {
+                    const int b = cid[row];
+                    pc_v[p] = (b >= 0 && t < d) ? ldx(X + (int64_t)b * ld + t) : 0.f;
+                }
             }
         }
     };
@@ -96,14 +146,30 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     // two buffers the next stage is stored while the current one is consumed, one barrier per stage
     auto store = [&](float *buf) {
         float *br = buf, *bc = buf + RF_DK * XR;
+        if constexpr (VEC) {
 #pragma unroll
-        for (int p = 0; p < PER; p++) {
-            const int e = tid + p * RF_THREADS, row = e / RF_DK, tt = e % RF_DK;
-            *reinterpret_cast<float2 *>(br + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
-            if constexpr (SAME)
-                bc[tt * XC + row] = pr_v[p];
-            else
-                bc[tt * XC + row] = pc_v[p];
+            for (int p = 0; p < PERV; p++) {
+                const int e = tid + p * RF_THREADS, row = e / CPR, tt0 = (e % CPR) * E;
+                float v[E], w[E];
+                widen16<XT>(qr[p], v);
+                if constexpr (!SAME)
+                    widen16<XT>(qc[p], w);
+#pragma unroll
+                for (int j = 0; j < E; j++) {
+                    *reinterpret_cast<float2 *>(br + (tt0 + j) * XR + 2 * row) = make_float2(v[j], v[j]);
+                    bc[(tt0 + j) * XC + row] = SAME ? v[j] : w[j];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < PER; p++) {
+                const int e = tid + p * RF_THREADS, row = e / RF_DK, tt = e % RF_DK;
+                *reinterpret_cast<float2 *>(br + tt * XR + 2 * row) = make_float2(pr_v[p], pr_v[p]);
+                if constexpr (SAME)
+                    bc[tt * XC + row] = pr_v[p];
+                else
+                    bc[tt * XC + row] = pc_v[p];
+            }
         }
     };
     constexpr int NBUF = TL::NBUF;
