@@ -498,7 +498,7 @@ size_t refine_tc_scratch_bytes(int64_t n, int32_t k, int64_t d)
     return 2 * a + c + 2 * t + perm;
 }
 
-// cuTensorMapEncodeTiled, from the driver through the runtime (no link against the driver library)
+// cuTensorMapEncodeTiled, from the CUDA driver through the runtime (no link against the driver library)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

@@ -1,7 +1,7 @@
 """Graph construction and fit driven step by step, with one JSONL record per round and per iteration.
 
 The steps are the library's step entry points in the order of gk_build_knn_graph and gk_kmeans_fit (so labels,
-centroids, graph and distortions equal the one-call API's bit for bit); between steps the driver reads, per graph
+centroids, graph and distortions equal the one-call API's bit for bit); between steps the loop reads, per graph
 round (Alg. 3) and per fit iteration (Alg. 2):
 
   E_assign   distortion after the assignment (mean best squared distance, Eq. 4)
@@ -11,7 +11,7 @@ round (Alg. 3) and per fit iteration (Alg. 2):
   u          mean number of distinct candidate clusters per sample (own label and the neighbours' labels)
   recall     (graph rounds) top-1 recall of the graph on sampled queries (Sec. 5), through gk_graph_recall
 
-Reading them synchronises the stream once per step, so this driver is for monitoring, not for timing.
+Reading them synchronises the stream once per step, so this loop is for monitoring, not for timing.
 """
 from __future__ import annotations
 
