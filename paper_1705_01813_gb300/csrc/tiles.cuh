@@ -183,7 +183,8 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
             fetch(t0 + RF_DK);
         const int tmax = min(RF_DK, d - t0);
         if (rows_live) {
-            for (int tt = 0; tt < tmax; tt++) {
+            // one staged coordinate: the thread's Q rows (each value twice) and Q columns, then the Q x Q pairs
+            auto step = [&](int tt) {
                 float2 vr[Q], vc[Q / 2];
                 const float4 *pr = reinterpret_cast<const float4 *>(cur + tt * XR + 2 * Q * by);
                 const float4 *pc = reinterpret_cast<const float4 *>(cur + RF_DK * XR + tt * XC + Q * bx);
@@ -206,6 +207,16 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
                         const float2 e = __ffma2_rn(vc[b], m1, vr[a]);
                         acc[a][b] = __ffma2_rn(e, e, acc[a][b]);
                     }
+            };
+            if (T == 64 && tmax == RF_DK) {  // a full stage of the 64-wide tile, unrolled (the next coordinates'
+                                              // loads overlap this one's FMAs; the 128-wide tile has no registers
+                                              // to spare)
+#pragma unroll 4
+                for (int tt = 0; tt < RF_DK; tt++)
+                    step(tt);
+            } else {
+                for (int tt = 0; tt < tmax; tt++)
+                    step(tt);
             }
         }
         if constexpr (NBUF == 2) {
