@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__res
                     }
                     if (lane < nb) {
                         const XT *xa = xi + t0, *xb = rows + lane * RS;
-                        for (int t = 0; t < dc; t += E) {
+                        auto part = [&](int t) {
                             float va[E], vb[E];
                             ld16<XT, false>(xa + t, va);
                             ld16<XT, true>(xb + t, vb);
@@ -186,6 +186,14 @@ __global__ void __launch_bounds__(IG_WARPS * 32, 4) k_init_graph(const XT *__res
                                 const float df = va[e] - vb[e];
                                 acc = fmaf(df, df, acc);
                             }
+                        };
+                        if (dc == ig_dc<XT>()) {  // a full chunk, unrolled: the next loads overlap this FMA chain
+#pragma unroll 4
+                            for (int t = 0; t < ig_dc<XT>(); t += E)
+                                part(t);
+                        } else {
+                            for (int t = 0; t < dc; t += E)
+                                part(t);
                         }
                     }
                 }
