@@ -131,6 +131,134 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT
     }
 }
 
+// Runs of at most 64 members, warp-specialised: a persistent block takes runs blockIdx.x, + gridDim.x, ...; five
+// of its warps (the compute group, WS_NC threads, rotated over the block's warps by blockIdx.x so that the blocks
+// of an SM spread them over its four schedulers) stage and compute a run's pair tile while the other three merge
+// the previous run's rows.  The two hand the distance tile over through named barriers: FULL (the compute group
+// arrives when the tile and the run's ids are written, the merge warps wait) and EMPTY (the merge warps arrive
+// when they no longer read it, the compute group waits before writing the next one).  Both sides walk the same
+// runs with the same skips, so the barriers pair up: per run one FULL and one EMPTY phase, plus the EMPTY phase
+// the merge warps open before the first run and the compute group closes after the last.  Pair arithmetic,
+// merge order and results are those of k_refine<64>.
+constexpr int WS_NC = 160;  // compute group: 5 warps, covers the 136 pair blocks of a 64-row triangle
+constexpr int WS_NM = 3;    // merge warps
+constexpr int WS_BAR_C = 1, WS_BAR_FULL = 2, WS_BAR_EMPTY = 3;
+
+// dynamic shared memory: two stage buffers, the distance tile, the run ids of two runs, the merge warps' buffers
+__host__ __device__ inline size_t refine_ws_smem_bytes(int kappa)
+{
+    using TL = RefineTile<64>;
+    return sizeof(float) * (TL::stage_floats + TL::tile_floats) + sizeof(int) * 2 * 64 + WS_NM * TL::warp_bytes(kappa);
+}
+
+template <typename XT, bool VEC>
+__global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+                                                             const int32_t *__restrict__ off,
+                                                             const int32_t *__restrict__ mem,
+                                                             const int32_t *__restrict__ run_off,
+                                                             const int32_t *__restrict__ run_cl, int k, int kappa,
+                                                             int cap, int32_t *__restrict__ g_idx,
+                                                             float *__restrict__ g_dist, DevStatus *st)
+{
+    constexpr int T = 64;
+    using TL = RefineTile<T>;
+    constexpr int DS = TL::DS, Q = TL::Q;
+    static_assert(WS_NC + 32 * WS_NM == RF_THREADS, "the block's warps are the two groups");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *stage = reinterpret_cast<float *>(smem_raw);
+    float *dt = stage + TL::stage_floats;
+    int *rids = reinterpret_cast<int *>(dt + TL::tile_floats);  // [2][T]: the ids of runs j and j + 1
+    unsigned char *mbase = reinterpret_cast<unsigned char *>(rids + 2 * T);
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int rr = (w - (int)(blockIdx.x & 3)) & 7;  // 0 .. 4: compute group, 5 .. 7: merge warps
+    const int nruns = run_off[k];
+    // run `run`: its cluster, first member (in mem) and size, as k_refine cuts clusters into runs
+    auto geometry = [&](int run, int &r, int &first, int &sz) {
+        r = run_cl[run];
+        const int beg = off[r], m = off[r + 1] - beg;
+        const int nc = (m + cap - 1) / cap, base = m / nc, rem = m % nc;
+        const int c = run - run_off[r];
+        first = beg + c * base + min(c, rem);
+        sz = base + (c < rem ? 1 : 0);
+    };
+    if (rr < 5) {
+        // ---- compute group ----
+        const int ct = rr * 32 + lane;
+        int j = 0;
+        for (int run = blockIdx.x; run < nruns; run += gridDim.x) {
+            int r, first, sz;
+            geometry(run, r, first, sz);
+            if (sz < 2 || sz > T)
+                continue;  // a run of the 128-wide kernel, or no pairs: skipped alike by the merge warps
+            int *rid = rids + (j & 1) * T;
+            if (ct < T) {
+                int a = ct < sz ? mem[first + ct] : -1;
+                if (a >= n) {  // corrupt grouping: record, skip the sample
+                    flag_error(st, GK_ERR_INVALID, (unsigned)r);
+                    a = -1;
+                }
+                rid[ct] = a;  // the merges of run j - 2, which read this slot, ended before EMPTY of run j - 1
+            }
+            bar_sync(WS_BAR_C, WS_NC);
+            float2 acc[Q][Q / 2];
+            int by, bx;
+            const bool live = tile_distances_group<WS_NC, VEC>(X, d, ld, rid, sz, stage, ct, WS_BAR_C, acc, by, bx);
+            bar_sync(WS_BAR_EMPTY, RF_THREADS);  // the merge warps no longer read the distance tile
+            if (live) {
+#pragma unroll
+                for (int a = 0; a < Q; a++)
+#pragma unroll
+                    for (int b = 0; b < Q / 2; b++) {
+                        dt[(Q * by + a) * DS + Q * bx + 2 * b] = acc[a][b].x;
+                        dt[(Q * by + a) * DS + Q * bx + 2 * b + 1] = acc[a][b].y;
+                        if (by != bx) {
+                            dt[(Q * bx + 2 * b) * DS + Q * by + a] = acc[a][b].x;
+                            dt[(Q * bx + 2 * b + 1) * DS + Q * by + a] = acc[a][b].y;
+                        }
+                    }
+            }
+            __threadfence_block();
+            bar_arrive(WS_BAR_FULL, RF_THREADS);  // this run's ids and distance tile are in place
+            j++;
+        }
+        bar_sync(WS_BAR_EMPTY, RF_THREADS);  // the merge warps' arrival after the last run
+    } else {
+        // ---- merge warps ----
+        const int mw = rr - 5;
+        unsigned char *wb = mbase + mw * TL::warp_bytes(kappa);
+        uint64_t *rk = reinterpret_cast<uint64_t *>(wb);
+        uint64_t *nk = rk + kappa;
+        uint64_t *bk = nk + kappa;
+        unsigned *dup = reinterpret_cast<unsigned *>(bk + T);
+        bar_arrive(WS_BAR_EMPTY, RF_THREADS);  // the distance tile starts free
+        int j = 0;
+        for (int run = blockIdx.x; run < nruns; run += gridDim.x) {
+            int r, first, sz;
+            geometry(run, r, first, sz);
+            if (sz < 2 || sz > T)
+                continue;
+            const int *rid = rids + (j & 1) * T;
+            bar_sync(WS_BAR_FULL, RF_THREADS);  // run j's ids and distances
+            RowRegs cur, nxt;
+            if (mw < sz && rid[mw] >= 0)
+                load_row(cur, g_idx + (int64_t)rid[mw] * kappa, g_dist + (int64_t)rid[mw] * kappa, kappa);
+            for (int row = mw; row < sz; row += WS_NM) {
+                const int i = rid[row];
+                const int rn = row + WS_NM;
+                if (rn < sz && rid[rn] >= 0)  // next row's list in flight during this merge
+                    load_row(nxt, g_idx + (int64_t)rid[rn] * kappa, g_dist + (int64_t)rid[rn] * kappa, kappa);
+                if (i >= 0)
+                    merge_row(i, rid, dt + row * DS, sz, kappa, cur, g_idx + (int64_t)i * kappa,
+                              g_dist + (int64_t)i * kappa, rk, bk, nk, dup);
+                cur = nxt;
+            }
+            __threadfence_block();
+            bar_arrive(WS_BAR_EMPTY, RF_THREADS);  // done with the distance tile and this slot of ids
+            j++;
+        }
+    }
+}
+
 static size_t run_bytes(int32_t k) { return ((size_t)(2 * (k + 1)) * sizeof(int32_t) + 255) / 256 * 256; }
 // runs per refinement are at most k + n / max_cluster (max_cluster >= 2)
 static size_t run_cl_bytes(int64_t n, int32_t k) { return ((size_t)(k + n / 2 + 1) * sizeof(int32_t) + 255) / 256 * 256; }
@@ -150,9 +278,14 @@ static cudaError_t refine_tv(const XT *X, int64_t n, int64_t d, int64_t ld, cons
     int32_t *run_cl = reinterpret_cast<int32_t *>(static_cast<char *>(scratch) + run_bytes(k));
     void *sc = static_cast<char *>(scratch) + run_bytes(k) + run_cl_bytes(n, k);
     void *tc_scratch = static_cast<char *>(sc) + scan_scratch_bytes(k);
-    size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa);
-    cudaError_t e =
-        set_max_smem(reinterpret_cast<const void *>(k_refine<64, XT, VEC>), (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
+    const size_t shm64 = RefineTile<64>::smem_bytes(kappa), shm128 = RefineTile<128>::smem_bytes(kappa),
+                 shm_ws = refine_ws_smem_bytes(kappa);
+    cudaError_t e;
+    if constexpr (VEC)
+        e = set_max_smem(reinterpret_cast<const void *>(k_refine_ws<XT, VEC>), (int)refine_ws_smem_bytes(MAX_KAPPA));
+    else
+        e = set_max_smem(reinterpret_cast<const void *>(k_refine<64, XT, VEC>),
+                         (int)RefineTile<64>::smem_bytes(MAX_KAPPA));
     if (e != cudaSuccess)
         return e;
     if ((e = set_max_smem(reinterpret_cast<const void *>(k_refine<128, XT, VEC>),
@@ -183,9 +316,24 @@ static cudaError_t refine_tv(const XT *X, int64_t n, int64_t d, int64_t ld, cons
                                                                      g_dist, st);
         return cudaGetLastError();
     }
-    // runs of <= 64 members, then the longer runs (up to 128 per tile, longer runs in tiles)
-    k_refine<64, XT, VEC><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
-                                                           kappa, max_cluster, 0, g_idx, g_dist, st);
+    // runs of <= 64 members, then the longer runs (up to 128 per tile, longer runs in tiles).  Rows staged by
+    // 16-byte loads take the persistent warp-specialised kernel (one wave of blocks; 10M x 512 BF16: 32.0 ->
+    // 31.3 ms per call, 98 -> 75 ms for runs of about ten); rows staged element by element keep the block per
+    // run, where five warps' share of the element loads made the specialised form slower (1M x 960 FP32: 7.6
+    // against 7.7 ms; 1M x 128 FP32: 3.7 against 3.9 ms)
+    if constexpr (VEC) {
+        int wgrid = 0;
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_refine_ws<XT, VEC>), RF_THREADS, shm_ws, &wgrid)) !=
+            cudaSuccess)
+            return e;
+        k_refine_ws<XT, VEC><<<(unsigned)(grid < wgrid ? grid : wgrid), RF_THREADS, shm_ws, s>>>(
+            X, n, (int)d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, g_idx, g_dist, st);
+    } else {
+        (void)shm_ws;
+        k_refine<64, XT, VEC><<<(unsigned)grid, RF_THREADS, shm64, s>>>(X, n, (int)d, ld, offsets, members, run_off,
+                                                                        run_cl, k, kappa, max_cluster, 0, g_idx,
+                                                                        g_dist, st);
+    }
     k_refine<128, XT, VEC><<<(unsigned)grid, RF_THREADS, shm128, s>>>(X, n, (int)d, ld, offsets, members, run_off, run_cl, k,
                                                              kappa, max_cluster, 64, g_idx, g_dist, st);
     return cudaGetLastError();

@@ -246,4 +246,148 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     }
 }
 
+// Named barriers (ids 1-15; 0 is __syncthreads): `count` threads, whole warps, complete a phase.  bar_sync
+// waits for the phase, bar_arrive counts this warp and goes on.
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// A run's own 64 x 64 tile (rows = columns = rid[0 .. nr)) computed by a group of NC threads of the block, with
+// index ct in [0, NC), that synchronise on named barrier bar (the rest of the block does other work meanwhile):
+// the arithmetic, the stages and the pair order of tile_distances<64, true, VEC>, so every distance has the same
+// bits.  Nothing is written to a distance tile: a thread that holds a block of pairs (returns true) gets the
+// block's position (by, bx) and its Q x Q distances in acc, for the caller to store when the tile is free.
+template <int NC, bool VEC, typename XT>
+__device__ __forceinline__ bool tile_distances_group(const XT *__restrict__ X, int d, int64_t ld, const int *rid,
+                                                     int nr, float *stage, int ct, int bar,
+                                                     float2 (&acc)[RefineTile<64>::Q][RefineTile<64>::Q / 2],
+                                                     int &by_out, int &bx_out)
+{
+    constexpr int T = 64;
+    using TL = RefineTile<T>;
+    constexpr int XR = TL::XR, XC = TL::XC, Q = TL::Q;
+    static_assert(NC % 32 == 0 && NC >= 136, "the group covers the 136 pair blocks of a 64-row triangle");
+    const int nb = (nr + Q - 1) / Q;
+    int t = ct, r = 0;
+    while (r < nb && t >= nb - r) {
+        t -= nb - r;
+        r++;
+    }
+    const int by = r, bx = r + t;
+    const bool rows_live = r < nb;
+    by_out = by, bx_out = bx;
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int a = 0; a < Q; a++)
+#pragma unroll
+        for (int b = 0; b < Q / 2; b++)
+            acc[a][b] = make_float2(0.f, 0.f);
+    // stage loads: 16-byte vectors (VEC) or elements, shared out over the NC threads
+    constexpr int E = 16 / (int)sizeof(XT), CPR = RF_DK / E;
+    constexpr int NV = T * CPR, NS = T * RF_DK;
+    constexpr int PV = (NV + NC - 1) / NC, PS = (NS + NC - 1) / NC;
+    uint4 qr[VEC ? PV : 1];
+    float pr[VEC ? 1 : PS];
+    auto fetch = [&](int t0) {
+        if constexpr (VEC) {
+#pragma unroll
+            for (int p = 0; p < PV; p++) {
+                const int e = ct + p * NC, row = e / CPR, tt = t0 + (e % CPR) * E;
+                const int a = e < NV ? rid[row] : -1;
+                qr[p] = (a >= 0 && tt < d) ? __ldg(reinterpret_cast<const uint4 *>(X + (int64_t)a * ld + tt))
+                                           : make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < PS; p++) {
+                const int e = ct + p * NC, row = e / RF_DK, tt = t0 + e % RF_DK;
+                const int a = e < NS ? rid[row] : -1;
+                pr[p] = (a >= 0 && tt < d) ? ldx(X + (int64_t)a * ld + tt) : 0.f;
+            }
+        }
+    };
+    auto store = [&](float *buf) {
+        float *br = buf, *bc = buf + RF_DK * XR;
+        if constexpr (VEC) {
+#pragma unroll
+            for (int p = 0; p < PV; p++) {
+                const int e = ct + p * NC;
+                if (e < NV) {
+                    const int row = e / CPR, tt0 = (e % CPR) * E;
+                    float v[E];
+                    widen16<XT>(qr[p], v);
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        *reinterpret_cast<float2 *>(br + (tt0 + j) * XR + 2 * row) = make_float2(v[j], v[j]);
+                        bc[(tt0 + j) * XC + row] = v[j];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < PS; p++) {
+                const int e = ct + p * NC;
+                if (e < NS) {
+                    const int row = e / RF_DK, tt = e % RF_DK;
+                    *reinterpret_cast<float2 *>(br + tt * XR + 2 * row) = make_float2(pr[p], pr[p]);
+                    bc[tt * XC + row] = pr[p];
+                }
+            }
+        }
+    };
+    fetch(0);
+    store(stage);
+    bar_sync(bar, NC);
+    for (int t0 = 0, sidx = 0; t0 < d; t0 += RF_DK, sidx ^= 1) {
+        const float *cur = stage + sidx * TL::buf_floats;
+        const bool more = t0 + RF_DK < d;
+        if (more)
+            fetch(t0 + RF_DK);
+        const int tmax = min(RF_DK, d - t0);
+        if (rows_live) {
+            auto step = [&](int tt) {
+                float2 vr[Q], vc[Q / 2];
+                const float4 *prr = reinterpret_cast<const float4 *>(cur + tt * XR + 2 * Q * by);
+                const float4 *pc = reinterpret_cast<const float4 *>(cur + RF_DK * XR + tt * XC + Q * bx);
+#pragma unroll
+                for (int q = 0; q < Q / 2; q++) {
+                    const float4 r4 = prr[q];
+                    vr[2 * q] = make_float2(r4.x, r4.y);
+                    vr[2 * q + 1] = make_float2(r4.z, r4.w);
+                }
+#pragma unroll
+                for (int q = 0; q < Q / 4; q++) {
+                    const float4 c4 = pc[q];
+                    vc[2 * q] = make_float2(c4.x, c4.y);
+                    vc[2 * q + 1] = make_float2(c4.z, c4.w);
+                }
+#pragma unroll
+                for (int a = 0; a < Q; a++)
+#pragma unroll
+                    for (int b = 0; b < Q / 2; b++) {
+                        const float2 e = __ffma2_rn(vc[b], m1, vr[a]);
+                        acc[a][b] = __ffma2_rn(e, e, acc[a][b]);
+                    }
+            };
+            if (tmax == RF_DK) {
+#pragma unroll 4
+                for (int tt = 0; tt < RF_DK; tt++)
+                    step(tt);
+            } else {
+                for (int tt = 0; tt < tmax; tt++)
+                    step(tt);
+            }
+        }
+        if (more)
+            store(stage + (sidx ^ 1) * TL::buf_floats);  // read last in the previous stage, before its barrier
+        bar_sync(bar, NC);
+    }
+    return rows_live;
+}
+
 }  // namespace gkm
