@@ -127,6 +127,17 @@ __device__ __forceinline__ unsigned lanemask_lt()
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Named barriers (ids 1-15; 0 is __syncthreads): `count` threads, whole warps, complete a phase.  bar_sync
+// waits for the phase, bar_arrive counts this warp and goes on.
+__device__ __forceinline__ void bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // 16-byte asynchronous copy global -> shared (both 16-byte aligned, L2 only),
 // grouping of the copies issued so far, and waits on the groups.
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)

@@ -246,17 +246,6 @@ __device__ __forceinline__ void tile_distances(const XT *__restrict__ X, int d, 
     }
 }
 
-// Named barriers (ids 1-15; 0 is __syncthreads): `count` threads, whole warps, complete a phase.  bar_sync
-// waits for the phase, bar_arrive counts this warp and goes on.
-__device__ __forceinline__ void bar_sync(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(int id, int count)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 // A run's own 64 x 64 tile (rows = columns = rid[0 .. nr)) computed by a group of NC threads of the block, with
 // index ct in [0, NC), that synchronise on named barrier bar (the rest of the block does other work meanwhile):
 // the arithmetic, the stages and the pair order of tile_distances<64, true, VEC>, so every distance has the same
