@@ -870,3 +870,167 @@ done:
     free(keys);
     return rc;
 }
+
+/* ======================================================================
+ * Boost form of GK-means (Sec. 3.1 Eq. 2 and Eq. 3; the move step of Alg. 2,
+ * Sec. 4.2).  State per cluster r: the composite vector D_r = sum of its
+ * members (Eq. 2), its size n_r and S_r = D_r'D_r.  Readings:
+ *   B1 a visit sequence `order` (sample ids, drawn by the caller) replaces
+ *      "one sample is randomly selected"; an epoch is one pass over it.
+ *   B2 the candidates of sample i are the distinct labels of its kappa
+ *      neighbours other than its own label u = L[i] (Alg. 2 collects Q).
+ *   B3 a sample alone in its cluster is not moved (Eq. 3 divides by n_u - 1).
+ *   B4 FP64 throughout; D_r starts as its members' rows summed in ascending
+ *      sample id; every squared norm is or_fold_sq below; Eq. 3 is evaluated
+ *      term by term, left to right, each operation rounded once.
+ *   B5 the candidate of largest gain wins, the smaller label on equal gains;
+ *      the sample moves iff that gain is > 0 (Alg. 2).
+ * ====================================================================== */
+
+/* Squared norm of v[0..d): the squares (each rounded once) of the vector
+ * zero-padded to the smallest power of two P >= d, then halving folds:
+ * while P > 1, P /= 2 and w[j] = w[j] + w[j + P] for j < P.  w: scratch of at
+ * least P doubles. */
+static double or_fold_sq_impl(const double *v, int64_t d, double *w)
+{
+    int64_t P = 1;
+    while (P < d)
+        P <<= 1;
+    for (int64_t j = 0; j < P; j++)
+        w[j] = j < d ? v[j] * v[j] : 0.0;
+    for (int64_t h = P / 2; h >= 1; h /= 2)
+        for (int64_t j = 0; j < h; j++)
+            w[j] = w[j] + w[j + h];
+    return w[0];
+}
+
+double or_fold_sq(const double *v, int64_t d)
+{
+    int64_t P = 1;
+    while (P < d)
+        P <<= 1;
+    double *w = (double *)malloc(sizeof(double) * (size_t)P);
+    if (!w)
+        return -1.0;
+    double r = or_fold_sq_impl(v, d, w);
+    free(w);
+    return r;
+}
+
+/* Eq. 2 state from labels: D (k x d, row-major), counts, S.  B4: each D_r is
+ * the running FP64 sum of its members' rows in ascending sample id. */
+int or_boost_init(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *L, int32_t k, double *D,
+                  int32_t *counts, double *S)
+{
+    double *w = (double *)malloc(sizeof(double) * (size_t)(2 * d + 2));
+    if (!w)
+        return 1;
+    for (int64_t e = 0; e < (int64_t)k * d; e++)
+        D[e] = 0.0;
+    for (int32_t r = 0; r < k; r++)
+        counts[r] = 0;
+    for (int64_t i = 0; i < n; i++) { /* ascending id: each D_r gets its members in that order */
+        int32_t r = L[i];
+        for (int64_t t = 0; t < d; t++)
+            D[(int64_t)r * d + t] = D[(int64_t)r * d + t] + (double)X[i * ld + t];
+        counts[r] += 1;
+    }
+    for (int32_t r = 0; r < k; r++)
+        S[r] = or_fold_sq_impl(D + (int64_t)r * d, d, w);
+    free(w);
+    return 0;
+}
+
+/* Eq. 3: gain of moving x from S_u (size nu, vector Du, S_u = Su) to S_v.
+ * Dv_plus_x_sq = (D_v + x)'(D_v + x), Du_minus_x_sq = (D_u - x)'(D_u - x). */
+static double or_boost_gain(double Dv_plus_x_sq, int32_t nv, double Sv, double Du_minus_x_sq, int32_t nu, double Su)
+{
+    return ((Dv_plus_x_sq / (double)(nv + 1) + Du_minus_x_sq / (double)(nu - 1)) - Sv / (double)nv) -
+           Su / (double)nu;
+}
+
+/* One epoch of Alg. 2's move step over the visits order[0..m): labels L, D,
+ * counts and S are updated in place, each move before the next visit is
+ * examined.  gains (m doubles, or NULL) receives the gain of the move made at
+ * each visit and 0 where the sample stayed.  Returns the number of moves, or
+ * -1 if out of memory. */
+int64_t or_boost_epoch(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *G, int32_t kappa,
+                       const int32_t *order, int64_t m, int32_t *L, int32_t k, double *D, int32_t *counts, double *S,
+                       double *gains)
+{
+    (void)n;
+    (void)k;
+    double *x = (double *)malloc(sizeof(double) * (size_t)d);
+    double *y = (double *)malloc(sizeof(double) * (size_t)d);
+    int64_t P = 1;
+    while (P < d)
+        P <<= 1;
+    double *w = (double *)malloc(sizeof(double) * (size_t)P);
+    int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)(kappa > 0 ? kappa : 1));
+    if (!x || !y || !w || !Q) {
+        free(x);
+        free(y);
+        free(w);
+        free(Q);
+        return -1;
+    }
+    int64_t moves = 0;
+    for (int64_t s = 0; s < m; s++) {
+        const int64_t i = order[s];
+        const int32_t u = L[i];
+        if (gains)
+            gains[s] = 0.0;
+        if (counts[u] < 2) /* B3 */
+            continue;
+        for (int64_t t = 0; t < d; t++)
+            x[t] = (double)X[i * ld + t];
+        /* Q: distinct labels of the neighbours, own label excluded (B2) */
+        int32_t nq = 0;
+        for (int32_t j = 0; j < kappa; j++) {
+            int32_t v = L[G[i * kappa + j]];
+            int seen = v == u;
+            for (int32_t q = 0; q < nq && !seen; q++)
+                seen = Q[q] == v;
+            if (!seen)
+                Q[nq++] = v;
+        }
+        if (nq == 0)
+            continue;
+        const double *Du = D + (int64_t)u * d;
+        for (int64_t t = 0; t < d; t++)
+            y[t] = Du[t] - x[t];
+        const double Bu = or_fold_sq_impl(y, d, w);
+        double best = 0.0;
+        int32_t bv = -1;
+        for (int32_t q = 0; q < nq; q++) {
+            const int32_t v = Q[q];
+            const double *Dv = D + (int64_t)v * d;
+            for (int64_t t = 0; t < d; t++)
+                y[t] = Dv[t] + x[t];
+            const double g = or_boost_gain(or_fold_sq_impl(y, d, w), counts[v], S[v], Bu, counts[u], S[u]);
+            if (bv < 0 || g > best || (g == best && v < bv)) /* B5 */
+                best = g, bv = v;
+        }
+        if (!(best > 0.0))
+            continue;
+        /* the move (Alg. 2): x leaves S_u and joins S_bv; sizes and S follow their definitions */
+        double *Dm = D + (int64_t)u * d, *Dp = D + (int64_t)bv * d;
+        for (int64_t t = 0; t < d; t++) {
+            Dm[t] = Dm[t] - x[t];
+            Dp[t] = Dp[t] + x[t];
+        }
+        counts[u] -= 1;
+        counts[bv] += 1;
+        S[u] = or_fold_sq_impl(Dm, d, w);
+        S[bv] = or_fold_sq_impl(Dp, d, w);
+        L[i] = bv;
+        if (gains)
+            gains[s] = best;
+        moves++;
+    }
+    free(x);
+    free(y);
+    free(w);
+    free(Q);
+    return moves;
+}

@@ -17,6 +17,8 @@ Every function restates the paper (Deng & Zhao, arXiv 1705.01813):
   build_graph                Alg. 3 with one GK-means iteration per round (Sec. 4.5)
   brute_knn                  exact KNN graph by all pairs
   two_means_tree             Alg. 1: k clusters by bisecting the largest cluster into equal halves
+  boost_init / boost_epoch   the boost form: Eq. 2 state (D_r, n_r, S_r) and Alg. 2's move step by Eq. 3 gains
+  fold_sq                    the fixed-order FP64 squared norm the boost form uses
 
 Parity status: every function above is pinned by tests/test_oracle_pins.py
 (brute force, closed forms, invariants, published SplitMix64 outputs); the
@@ -73,6 +75,12 @@ def _bind(lib):
     lib.or_brute_knn.argtypes = [P, I64, I64, I64, I32, P, P]
     lib.or_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P]
     lib.or_two_means_tree.restype = ctypes.c_int
+    lib.or_fold_sq.argtypes = [P, I64]
+    lib.or_fold_sq.restype = ctypes.c_double
+    lib.or_boost_init.argtypes = [P, I64, I64, I64, P, I32, P, P, P]
+    lib.or_boost_init.restype = ctypes.c_int
+    lib.or_boost_epoch.argtypes = [P, I64, I64, I64, P, I32, P, I64, P, I32, P, P, P, P]
+    lib.or_boost_epoch.restype = I64
     return lib
 
 
@@ -271,6 +279,41 @@ class Oracle:
         if self._lib.or_two_means_tree(_p(X), n, d, d, k, iters, seed, _p(out)):
             raise ValueError("two_means_tree: need 1 <= k <= n and iters >= 0")
         return out
+
+    def fold_sq(self, v) -> float:
+        """Squared norm of v in FP64 by halving folds over v zero-padded to a power of two (the boost form's
+        order of summation, reading B4 in gkm_oracle.c)."""
+        v = _f64(v).ravel()
+        return float(self._lib.or_fold_sq(_p(v), v.shape[0]))
+
+    def boost_init(self, X, labels, k: int):
+        """Eq. 2 state of a partition: (D k x d FP64 composite vectors, counts int32[k], S FP64[k] = D_r'D_r)."""
+        X, n, d = _x(X)
+        L = _i32(labels)
+        D = np.empty((k, d), np.float64)
+        cnt = np.empty(k, np.int32)
+        S = np.empty(k, np.float64)
+        if self._lib.or_boost_init(_p(X), n, d, d, _p(L), k, _p(D), _p(cnt), _p(S)):
+            raise MemoryError("boost_init")
+        return D, cnt, S
+
+    def boost_epoch(self, X, g_idx, order, labels, k: int, D, counts, S):
+        """Alg. 2's move step (Eq. 3 gains) over the visits `order`; returns new (labels, D, counts, S, moves,
+        gains) where gains[s] is the gain of the move made at visit s (0 if the sample stayed)."""
+        X, n, d = _x(X)
+        G = _i32(g_idx)
+        kappa = G.shape[1]
+        od = _i32(order)
+        L = _i32(labels).copy()
+        D = _f64(D).copy()
+        cnt = _i32(counts).copy()
+        S = _f64(S).copy()
+        gains = np.empty(od.shape[0], np.float64)
+        moves = self._lib.or_boost_epoch(_p(X), n, d, d, _p(G), kappa, _p(od), od.shape[0], _p(L), k, _p(D),
+                                         _p(cnt), _p(S), _p(gains))
+        if moves < 0:
+            raise MemoryError("boost_epoch")
+        return L, D, cnt, S, int(moves), gains
 
 
 _default = None

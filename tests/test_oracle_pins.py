@@ -11,7 +11,11 @@ distortion, sorted duplicate-free graph rows, result-neutral visited set).
 The two-means tree (Alg. 1) is pinned by the cluster sizes that n and k alone
 fix, by one-dimensional data (every cluster a run of consecutive values), by
 its root split against textbook 2-means followed by a median split, and by
-separated blobs.
+separated blobs.  The boost form (Eq. 3 gains, Alg. 2's move step) is pinned by
+hand-worked moves, ties and singletons (tests/golden/worked_boost.json), by
+each visit checked against the k-means objective recomputed from scratch, by
+its fixed FP64 summation order on vectors where the order decides the
+rounding, and by the Eq. 2 identity over a whole epoch.
 
 The second half plants plausible mistakes in a copy of the oracle's C source
 and shows that at least one pin fails for each.
@@ -489,12 +493,119 @@ def check_tree_blobs(orc):
 
 
 
+# ------------------------------------------------------------- boost form ----
+
+def check_boost_fold(orc):
+    """The boost form's FP64 squared norm: hand-worked halving folds that a running sum or adjacent pairs get
+    wrong, and exact integer sums at lengths that are not powers of two."""
+    f = _golden("worked_boost.json")["fold"]
+    for v, want in zip(f["vectors"], f["values"]):
+        assert orc.fold_sq(np.asarray(v, np.float64)) == want
+    rng = np.random.default_rng(3)
+    for d in (1, 2, 3, 17, 100, 129):
+        v = rng.integers(-1000, 1000, d)
+        assert orc.fold_sq(v.astype(np.float64)) == float(sum(int(a) * int(a) for a in v))
+
+
+def _boost_run(orc, case):
+    X = _col(case["x"])
+    D, cnt, S = orc.boost_init(X, case["labels"], case["k"])
+    return (D, cnt, S) + orc.boost_epoch(X, case["graph"], case["order"], case["labels"], case["k"], D, cnt, S)
+
+
+def check_boost_worked(orc):
+    g = _golden("worked_boost.json")
+    D0, c0, S0, L, D, cnt, S, moves, gains = _boost_run(orc, g["move"])
+    m = g["move"]
+    assert D0.tolist() == m["D_before"] and c0.tolist() == m["counts_before"] and S0.tolist() == m["S_before"]
+    assert L.tolist() == m["labels_after"] and D.tolist() == m["D_after"]
+    assert cnt.tolist() == m["counts_after"] and S.tolist() == m["S_after"]
+    assert gains.tolist() == m["gains"] and moves == m["moves"]
+    t = g["tie"]
+    _, _, _, L, D, cnt, S, moves, _ = _boost_run(orc, t)
+    assert L.tolist() == t["labels_after"] and D.tolist() == t["D_after"]
+    assert cnt.tolist() == t["counts_after"] and S.tolist() == t["S_after"] and moves == t["moves"]
+    s1 = g["singleton"]
+    _, _, _, L, _, _, _, moves, _ = _boost_run(orc, s1)
+    assert L.tolist() == s1["labels_after"] and moves == s1["moves"]
+
+
+def _sse(X, L, k):
+    """k-means objective by brute force: sum of squared distances to the member means (Eq. 1)."""
+    X = X.astype(np.float64)
+    cnt = np.bincount(L, minlength=k).astype(np.float64)
+    C = np.zeros((k, X.shape[1]))
+    np.add.at(C, L, X)
+    C[cnt > 0] /= cnt[cnt > 0, None]
+    return float(((X - C[L]) ** 2).sum())
+
+
+def check_boost_brute_force(orc):
+    """Each visit of the move step, checked against the k-means objective computed from scratch: a move lowers
+    the sum of squared errors by exactly its gain (Eq. 2: n E = sum ||x||^2 - I) and goes to the candidate cluster
+    of lowest objective; a sample that stays has no candidate that would lower it (or is alone)."""
+    rng = np.random.default_rng(7)
+    for n, d, k, kappa in ((40, 3, 5, 4), (60, 2, 8, 6), (30, 5, 3, 29)):
+        X = rng.integers(-20, 21, (n, d)).astype(np.float32)
+        L = rng.integers(0, k, n).astype(np.int32)
+        L[:k] = np.arange(k)
+        G = np.stack([rng.choice(np.delete(np.arange(n), i), kappa, replace=False) for i in range(n)])
+        D, cnt, S = orc.boost_init(X, L, k)
+        order = rng.integers(0, n, 3 * n)
+        moved = 0
+        for i in order:
+            before = _sse(X, L, k)
+            u = L[i]
+            Q = sorted(set(L[G[i]].tolist()) - {u})
+            L2, D, cnt, S, mv, gains = orc.boost_epoch(X, G, [i], L, k, D, cnt, S)
+            alt = {v: _sse(X, np.where(np.arange(n) == i, v, L), k) for v in Q}
+            if mv:
+                v = int(L2[i])
+                assert v in Q and np.bincount(L, minlength=k)[u] >= 2
+                assert gains[0] > 0
+                assert before - alt[v] == pytest.approx(gains[0], rel=1e-9, abs=1e-9)
+                assert alt[v] <= min(alt.values()) + 1e-9 * max(1.0, before)
+                moved += 1
+            else:
+                assert np.array_equal(L2, L)
+                if np.bincount(L, minlength=k)[u] >= 2 and Q:
+                    assert min(alt.values()) >= before - 1e-9 * max(1.0, before)
+            L = L2
+            D0, c0, S0 = orc.boost_init(X, L, k)  # integer data: every sum is exact in any order
+            assert np.array_equal(D, D0) and np.array_equal(cnt, c0) and np.array_equal(S, S0)
+        assert moved > 0
+
+
+def check_boost_epoch_invariants(orc):
+    """A whole epoch over a permutation on clustered data: the objective I (Eq. 2) rises by the sum of the
+    gains, the state matches the Eq. 2 state of the final labels, and the distortion falls."""
+    from paper_1705_01813_gb300 import datagen
+    X = datagen.sift_like(2000, 16, 40, seed=5)
+    k = 40
+    gi, _ = orc.brute_knn(X, 10)
+    L = orc.init_labels(2000, k, 9)
+    D, cnt, S = orc.boost_init(X, L, k)
+    I0 = float((S / cnt).sum())
+    order = np.random.default_rng(1).permutation(2000)
+    L2, D2, cnt2, S2, mv, gains = orc.boost_epoch(X, gi, order, L, k, D, cnt, S)
+    I1 = float((S2 / cnt2).sum())
+    assert mv > 100 and (gains >= 0).all() and (gains > 0).sum() == mv
+    assert I1 - I0 == pytest.approx(gains.sum(), rel=1e-9)
+    D3, cnt3, S3 = orc.boost_init(X, L2, k)
+    assert np.array_equal(cnt2, cnt3)
+    assert np.allclose(D2, D3, rtol=1e-12, atol=1e-9) and np.allclose(S2, S3, rtol=1e-12)
+    assert _sse(X, L2, k) < _sse(X, L, k)
+    sq = float((X.astype(np.float64) ** 2).sum())
+    assert (sq - I1) == pytest.approx(_sse(X, L2, k), rel=1e-9)
+
+
 CHECKS = [check_splitmix, check_init_labels, check_init_graph, check_worked_assign, check_worked_margin,
           check_margin_complete_graph, check_assign_complete_graph,
           check_assign_restricted, check_update, check_fit, check_worked_refine, check_exact_knn_special_case,
           check_graph_invariants_and_monotone, check_visited_neutral, check_refine_rows_and_chunks,
           check_init_graph_rows, check_group_csr, check_tree_sizes, check_tree_1d, check_tree_root_split,
-          check_tree_fp64_decisions, check_tree_blobs]
+          check_tree_fp64_decisions, check_tree_blobs, check_boost_fold, check_boost_worked,
+          check_boost_brute_force, check_boost_epoch_invariants]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[c.__name__ for c in CHECKS])
@@ -561,6 +672,15 @@ MUTANTS = [
     ("tree_labels_by_creation", "labels[perm[p]] = rank;", "labels[perm[p]] = s;", check_tree_sizes),
     ("tree_seed_depth_ignored", "((uint64_t)(uint32_t)depth << 32)", "((uint64_t)0 << 32)",
      check_tree_fp64_decisions),
+    ("boost_u_denominator", "Du_minus_x_sq / (double)(nu - 1)", "Du_minus_x_sq / (double)nu", check_boost_worked),
+    ("boost_tie_to_larger", "(g == best && v < bv)", "(g == best && v > bv)", check_boost_worked),
+    ("boost_u_sign", "            Dm[t] = Dm[t] - x[t];", "            Dm[t] = Dm[t] + x[t];", check_boost_worked),
+    ("boost_own_label_candidate", "int seen = v == u;", "int seen = 0;", check_boost_brute_force),
+    ("boost_first_neighbour_only", "for (int32_t j = 0; j < kappa; j++) {\n            int32_t v = L[G[i * kappa + j]];",
+     "for (int32_t j = 0; j < 1; j++) {\n            int32_t v = L[G[i * kappa + j]];", check_boost_brute_force),
+    ("boost_fold_adjacent", "w[j] = w[j] + w[j + h];", "w[j] = w[2 * j] + w[2 * j + 1];", check_boost_fold),
+    ("boost_init_skips_first", "for (int64_t i = 0; i < n; i++) { /* ascending id",
+     "for (int64_t i = 1; i < n; i++) { /* ascending id", check_boost_worked),
     ("tree_v_keeps_left_range", "off[t] = off[s] + h; /* v */", "off[t] = off[s]; off[s] += m - h; /* v */",
      check_tree_1d),
 ]
