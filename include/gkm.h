@@ -67,7 +67,8 @@ enum {
     GK_OP_FIT = 3,
     GK_OP_BUILD = 4,
     GK_OP_RECALL = 5,
-    GK_OP_TREE = 6
+    GK_OP_TREE = 6,
+    GK_OP_BOOST = 7
 };
 
 /* Parameters of the graph construction (Alg. 3 and Sec. 4.4 of the paper). */
@@ -96,7 +97,7 @@ GK_API const char *gk_last_error(void);
 
 /*
  * Bytes of workspace the operation `op` (GK_OP_ASSIGN, _UPDATE, _REFINE, _FIT,
- * _RECALL, _TREE) needs for these sizes; 0 for an unknown op.  k is the number of
+ * _RECALL, _TREE, _BOOST) needs for these sizes; 0 for an unknown op.  k is the number of
  * clusters (for GK_OP_RECALL: the number of queries m).  The graph
  * construction has its own query, gk_workspace_size_build().
  */
@@ -429,6 +430,66 @@ GK_API int gk_two_means_tree(const float *X, int64_t n, int64_t d, int64_t ld, i
                              uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream);
 GK_API int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
                                   uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Boost form of GK-means (Sec. 3.1 Eq. 2 and Eq. 3; the move step of Alg. 2,
+ * Sec. 4.2): the paper's standard configuration, in which one visited sample
+ * at a time moves to the neighbouring cluster of largest objective gain.
+ *
+ * State of a partition (Eq. 2), all device memory owned by the caller:
+ *   D       FP64 k x d, row-major (row r at D + r * d): D_r, the sum of the
+ *           members of cluster r
+ *   counts  int32[k]: n_r
+ *   S       FP64[k]: S_r = D_r'D_r
+ * The objective of Eq. 2 is I = sum over non-empty r of S_r / n_r, and the
+ * k-means distortion (Eq. 4) is (sum_i ||x_i||^2 - I) / n.
+ *
+ * Arithmetic (fixed, so that every move decision is reproducible): FP64.
+ * gk_boost_init sums each D_r over its members in ascending sample id.  A
+ * squared norm squares each element of the vector zero-padded to the smallest
+ * power of two P >= d (each product rounded once) and adds them by halving
+ * folds: while P > 1, P /= 2 and w[j] = w[j] + w[j + P] for j < P.  Samples
+ * are widened exactly to FP64 (BF16 through FP32).
+ *
+ * gk_boost_init: the state of the partition `labels` (int32[n] in [0, k)).
+ *   ws  gk_workspace_size(GK_OP_BOOST, n, d, k, 0) bytes
+ *
+ * gk_boost_epoch: one epoch of the move step.  For s = 0 .. m - 1 in order,
+ * sample i = order[s] with label u: if n_u >= 2, the candidates are the
+ * distinct labels of its kappa neighbours (g_idx row i) other than u, and the
+ * gain of moving to candidate v is
+ *   ((A_v / (n_v + 1) + B / (n_u - 1)) - S_v / n_v) - S_u / n_u,
+ *   A_v = (D_v + x)'(D_v + x),  B = (D_u - x)'(D_u - x)   (squared norms as above),
+ * each operation rounded once, left to right.  The candidate of largest gain
+ * (the smaller label on equal gains) is taken if its gain is > 0: then
+ * labels[i] = v, D_u -= x and D_v += x element by element, n_u -= 1,
+ * n_v += 1, S_u = B and S_v = A_v.  The next visit sees these changes.
+ *   X, n, d, ld    samples as in gk_assign_step, 1 <= d <= 1024
+ *   g_idx, kappa   KNN graph rows (only g_idx is read), 1 <= kappa <= 128
+ *   order          device int32[m]: the visited sample ids (the paper draws
+ *                  them at random; a permutation of [0, n) is one pass), m >= 0
+ *   labels, D, counts, S   the state, updated in place; it must be the state
+ *                  of `labels` (as gk_boost_init makes it) for the epoch to
+ *                  follow Eq. 3
+ *   n_moved        device int64[1] (out) or NULL: moves made
+ *   ws             gk_workspace_size(GK_OP_BOOST, n, d, k, kappa) bytes
+ * A visit id, label or neighbour id out of range sets GK_ERR_INVALID in the
+ * status word and that visit makes no move.
+ * One thread-block cluster runs the epoch (the visits are sequential by
+ * definition; a visit's FP64 work is spread over the cluster's SMs); a visit
+ * costs (candidates + 1) FP64 rows of d elements read, and 2 rows written
+ * when it moves.
+ */
+GK_API int gk_boost_init(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                         double *D, int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_boost_init_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                              double *D, int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_boost_epoch(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                          const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D, int32_t *counts,
+                          double *S, int64_t *n_moved, void *ws, size_t ws_bytes, void *stream);
+GK_API int gk_boost_epoch_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                               int32_t kappa, const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D,
+                               int32_t *counts, double *S, int64_t *n_moved, void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Replay of repeated requests (off by default).  With replay on, a call of

@@ -116,7 +116,7 @@ Layout carve(void *ws, int op, int64_t n, int64_t d, int32_t k)
     Layout L{};
     L.st = cv.take<DevStatus>(1);
     bool need_group = op == GK_OP_ASSIGN || op == GK_OP_UPDATE || op == GK_OP_REFINE || op == GK_OP_FIT ||
-                      op == GK_OP_BUILD;
+                      op == GK_OP_BUILD || op == GK_OP_BOOST;
     bool need_update = op == GK_OP_UPDATE || op == GK_OP_FIT || op == GK_OP_BUILD;
     bool need_assign = op == GK_OP_ASSIGN || op == GK_OP_FIT || op == GK_OP_BUILD;
     if (need_group) {
@@ -316,7 +316,7 @@ const char *gk_last_error(void) { return g_err; }
 size_t gk_workspace_size(int32_t op, int64_t n, int64_t d, int32_t k, int32_t kappa)
 {
     (void)kappa;
-    if (op < GK_OP_ASSIGN || op > GK_OP_TREE || op == GK_OP_BUILD || n < 0 || d < 0 || k < 0)
+    if (op < GK_OP_ASSIGN || op > GK_OP_BOOST || op == GK_OP_BUILD || n < 0 || d < 0 || k < 0)
         return 0;
     return carve(nullptr, op, n, d, k).bytes;
 }
@@ -981,6 +981,86 @@ int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, 
                            uint64_t seed, int32_t *labels, void *ws, size_t ws_bytes, void *stream)
 {
     return two_means_tree_impl(X, true, n, d, ld, k, iters, seed, labels, ws, ws_bytes, stream);
+}
+
+static int boost_check(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k, const void *D,
+                       const void *counts, const void *S, void *ws, size_t ws_bytes, Layout *L)
+{
+    int rc;
+    if ((rc = check_x(X, bf16, n, d, ld, 1)))
+        return rc;
+    if (d > boost_max_d())
+        return fail(GK_ERR_INVALID, "d = %lld > %lld (boost form)", (long long)d, (long long)boost_max_d());
+    if (k < 1 || (int64_t)k > n)
+        return fail(GK_ERR_INVALID, "k = %d out of range [1, n = %lld]", k, (long long)n);
+    if (!D || !counts || !S)
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    *L = carve(nullptr, GK_OP_BOOST, n, d, k);
+    if ((rc = check_ws(ws, ws_bytes, L->bytes)))
+        return rc;
+    *L = carve(ws, GK_OP_BOOST, n, d, k);
+    return GK_OK;
+}
+
+static int boost_init_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *labels,
+                           int32_t k, double *D, int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    Layout L;
+    if ((rc = boost_check(X, bf16, n, d, ld, k, D, counts, S, ws, ws_bytes, &L)))
+        return rc;
+    if (!labels)
+        return fail(GK_ERR_INVALID, "labels is NULL");
+    GK_CUDA(launch_boost_init(X, bf16, n, d, ld, labels, k, D, counts, S, L.grp.offsets, L.grp.members,
+                              L.grp.counts, L.grp.scratch, L.st, (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_boost_init(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k, double *D,
+                  int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream)
+{
+    return boost_init_impl(X, false, n, d, ld, labels, k, D, counts, S, ws, ws_bytes, stream);
+}
+
+int gk_boost_init_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
+                       double *D, int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream)
+{
+    return boost_init_impl(X, true, n, d, ld, labels, k, D, counts, S, ws, ws_bytes, stream);
+}
+
+static int boost_epoch_impl(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx,
+                            int32_t kappa, const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D,
+                            int32_t *counts, double *S, int64_t *n_moved, void *ws, size_t ws_bytes, void *stream)
+{
+    int rc;
+    Layout L;
+    if ((rc = boost_check(X, bf16, n, d, ld, k, D, counts, S, ws, ws_bytes, &L)))
+        return rc;
+    if ((rc = check_kappa(kappa, n)))
+        return rc;
+    if (m < 0)
+        return fail(GK_ERR_INVALID, "m = %lld < 0", (long long)m);
+    if (!g_idx || !labels || (m > 0 && !order))
+        return fail(GK_ERR_INVALID, "a required array is NULL");
+    GK_CUDA(launch_boost_epoch(X, bf16, n, d, ld, g_idx, kappa, order, m, labels, k, D, counts, S, n_moved, L.st,
+                               (cudaStream_t)stream));
+    return GK_OK;
+}
+
+int gk_boost_epoch(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                   const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D, int32_t *counts, double *S,
+                   int64_t *n_moved, void *ws, size_t ws_bytes, void *stream)
+{
+    return boost_epoch_impl(X, false, n, d, ld, g_idx, kappa, order, m, labels, k, D, counts, S, n_moved, ws,
+                            ws_bytes, stream);
+}
+
+int gk_boost_epoch_bf16(const uint16_t *X, int64_t n, int64_t d, int64_t ld, const int32_t *g_idx, int32_t kappa,
+                        const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D, int32_t *counts,
+                        double *S, int64_t *n_moved, void *ws, size_t ws_bytes, void *stream)
+{
+    return boost_epoch_impl(X, true, n, d, ld, g_idx, kappa, order, m, labels, k, D, counts, S, n_moved, ws, ws_bytes,
+                            stream);
 }
 
 int gk_set_replay(int enable)

@@ -197,6 +197,15 @@ size_t tree_scratch_bytes(int64_t n, int64_t d, int32_t k);
 cudaError_t launch_tree(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, int32_t k, int32_t iters,
                         uint64_t seed, int32_t *labels, void *scratch, DevStatus *st, cudaStream_t s);
 
+// boost form, Eq. 2 state and the move step of Alg. 2 with Eq. 3 gains (boost.cu); d <= boost_max_d()
+int64_t boost_max_d();
+cudaError_t launch_boost_init(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *labels,
+                              int32_t k, double *D, int32_t *counts, double *S, int32_t *offsets, int32_t *members,
+                              int32_t *grp_counts, void *grp_scratch, DevStatus *st, cudaStream_t s);
+cudaError_t launch_boost_epoch(const void *X, bool bf16, int64_t n, int64_t d, int64_t ld, const int32_t *G,
+                               int32_t kappa, const int32_t *order, int64_t m, int32_t *labels, int32_t k, double *D,
+                               int32_t *counts, double *S, int64_t *n_moved, DevStatus *st, cudaStream_t s);
+
 // Internal launchers (each returns cudaError_t of the launch).  Those that read the samples take them as
 // X (FP32, or BF16 when bf16 is set) with leading dimension ld in elements.
 // (label_offset / id_offset are added to every label / neighbour id written: a job's numbering inside a batch)

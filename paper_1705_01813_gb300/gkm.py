@@ -20,18 +20,19 @@ _lib = None
 _lock = threading.Lock()
 
 GK_OK, GK_ERR_INVALID, GK_ERR_CUDA, GK_ERR_NOMEM, GK_ERR_TIMEOUT, GK_ERR_NUMERIC = range(6)
-GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL, GK_OP_TREE = range(7)
+GK_OP_ASSIGN, GK_OP_UPDATE, GK_OP_REFINE, GK_OP_FIT, GK_OP_BUILD, GK_OP_RECALL, GK_OP_TREE, GK_OP_BOOST = range(8)
 
 #: every entry point the header declares (checked by the tests)
 EXPORTS = ["gk_version", "gk_last_error", "gk_workspace_size", "gk_workspace_size_build", "gk_init_labels",
            "gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_build_knn_graph",
            "gk_kmeans_fit", "gk_read_status", "gk_group_by_label", "gk_update_from_groups",
            "gk_graph_refine_groups", "gk_update_step_noalloc", "gk_graph_recall",
-           "gk_set_replay", "gk_two_means_tree", "gk_workspace_size_batch", "gk_batch_fit"]
+           "gk_set_replay", "gk_two_means_tree", "gk_workspace_size_batch", "gk_batch_fit", "gk_boost_init",
+           "gk_boost_epoch"]
 #: entry points that read the samples and have a BF16-sample twin named <name>_bf16
 X_ENTRIES = ["gk_init_graph", "gk_assign_step", "gk_update_step", "gk_graph_refine", "gk_update_from_groups",
              "gk_graph_refine_groups", "gk_build_knn_graph", "gk_kmeans_fit", "gk_graph_recall",
-             "gk_two_means_tree", "gk_batch_fit"]
+             "gk_two_means_tree", "gk_batch_fit", "gk_boost_init", "gk_boost_epoch"]
 EXPORTS += [name + "_bf16" for name in X_ENTRIES]
 
 
@@ -95,6 +96,8 @@ def load(build_if_missing: bool = True):
             L.gk_set_replay.argtypes = [I32]
             L.gk_two_means_tree.argtypes = [P, I64, I64, I64, I32, I32, U64, P, P, SZ, P]
             L.gk_workspace_size_batch.restype = SZ
+            L.gk_boost_init.argtypes = [P, I64, I64, I64, P, I32, P, P, P, P, SZ, P]
+            L.gk_boost_epoch.argtypes = [P, I64, I64, I64, P, I32, P, I64, P, I32, P, P, P, P, P, SZ, P]
             L.gk_workspace_size_batch.argtypes = [I64, I32, P, ctypes.POINTER(GraphParams)]
             L.gk_batch_fit.argtypes = [P, I64, I64, I32, P, ctypes.POINTER(GraphParams), I32, P, P, P, P, P, P, SZ,
                                        P]
@@ -411,6 +414,47 @@ def two_means_tree(X, k: int, iters: int = 2, seed: int = 0, out: torch.Tensor |
     _check(_entry("gk_two_means_tree", X)(_ptr(X), n, d, ld, k, iters, seed, _ptr(out), ws.ptr, ws.nbytes,
                                           _stream(stream)))
     return out
+
+
+def boost_init(X, labels, k: int, D=None, counts=None, S=None, ws: Workspace | None = None, stream=None):
+    """Eq. 2 state of the partition `labels` (see gk_boost_init): D (k x d FP64 composite vectors), counts
+    (int32[k]) and S (FP64[k], D_r'D_r)."""
+    n, d, ld = _x(X)
+    dev = X.device
+    D = torch.empty((k, d), dtype=torch.float64, device=dev) if D is None else D
+    counts = torch.empty(k, dtype=torch.int32, device=dev) if counts is None else counts
+    S = torch.empty(k, dtype=torch.float64, device=dev) if S is None else S
+    _dev(labels, torch.int32, "labels")
+    _dev(D, torch.float64, "D")
+    _dev(counts, torch.int32, "counts")
+    _dev(S, torch.float64, "S")
+    if tuple(D.shape) != (k, d):
+        raise ValueError("D must be k x d")
+    ws = ws or workspace(workspace_size(GK_OP_BOOST, n, d, k), dev)
+    _check(_entry("gk_boost_init", X)(_ptr(X), n, d, ld, _ptr(labels), k, _ptr(D), _ptr(counts), _ptr(S), ws.ptr,
+                                      ws.nbytes, _stream(stream)))
+    return D, counts, S
+
+
+def boost_epoch(X, g_idx, order, labels, k: int, D, counts, S, n_moved=None, ws: Workspace | None = None,
+                stream=None) -> torch.Tensor:
+    """One epoch of the boost form's move step (Eq. 3 gains, Alg. 2) over the visits `order` (int32 sample ids);
+    labels, D, counts and S are updated in place.  Returns n_moved (device int64[1])."""
+    n, d, ld = _x(X)
+    dev = X.device
+    for t, dt, name in ((g_idx, torch.int32, "g_idx"), (order, torch.int32, "order"), (labels, torch.int32, "labels"),
+                        (D, torch.float64, "D"), (counts, torch.int32, "counts"), (S, torch.float64, "S")):
+        _dev(t, dt, name)
+    if tuple(D.shape) != (k, d):
+        raise ValueError("D must be k x d")
+    n_moved = torch.empty(1, dtype=torch.int64, device=dev) if n_moved is None else n_moved
+    _dev(n_moved, torch.int64, "n_moved")
+    kappa = g_idx.shape[1]
+    ws = ws or workspace(workspace_size(GK_OP_BOOST, n, d, k, kappa), dev)
+    _check(_entry("gk_boost_epoch", X)(_ptr(X), n, d, ld, _ptr(g_idx), kappa, _ptr(order), order.numel(),
+                                       _ptr(labels), k, _ptr(D), _ptr(counts), _ptr(S), _ptr(n_moved), ws.ptr,
+                                       ws.nbytes, _stream(stream)))
+    return n_moved
 
 
 def set_replay(enable: bool):
