@@ -17,8 +17,10 @@ memory and the labels and centroids copied back inside the timed region.  By
 default the precision level is chosen by the autotuner (tune.py) after the
 first warm-up step.  Outside the timed region the line also reports the
 constructed graph's top-1 recall (Sec. 5), the probe-measured gather and FMA
-ceilings, the serving passes and the oracle's timing on a bounded sample with
-the library's results on that sample compared to the oracle's.
+ceilings, the serving passes, the boost form (Eq. 3 gains, Alg. 2 move step)
+from the fit's partition over a prefix of one epoch's visits, and the oracle's
+timing on a bounded sample with the library's results on that sample compared
+to the oracle's (graph and fit; the boost epoch bit for bit).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gkm|reference]
 Under torchrun (N > 1) every rank runs an independent replica on its GPU
@@ -80,6 +82,10 @@ def parse():
     ap.add_argument("--group-width", type=int, choices=[0, 4, 8], default=0,
                     help="with --precision: the assignment's candidates per group (0: the kernels' default)")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-boost", action="store_true",
+                    help="skip the timing of the boost form (Eq. 3 gains, Alg. 2 move step) on the fit's partition")
+    ap.add_argument("--boost-visits", type=int, default=100_000,
+                    help="visits of the timed boost epoch (a prefix of a seeded permutation of the samples)")
     ap.add_argument("--no-tree", action="store_true",
                     help="skip the timing of the two-means tree (Alg. 1) at the workload's n, d and k")
     ap.add_argument("--no-ceilings", action="store_true",
@@ -561,6 +567,8 @@ def run_gpu(args):
                       "brute force on seeded random queries"}
 
     tree = None if args.no_tree else time_tree(gkm, torch, path.X, w)
+    boost = None if args.no_boost else time_boost(gkm, torch, path.X, w, path.gi,
+                                                 path.la if w.iters % 2 == 0 else path.lb, args.boost_visits)
 
     hbm, bf16, peak_src = load_peaks()
     ceilings = None
@@ -623,6 +631,7 @@ def run_gpu(args):
         "precision_tuning": tuning,
         "graph_recall_top1": recall,
         "two_means_tree": tree,
+        "boost_form": boost,
         "candidates_u": u or None,
         "clocks": ck,
         "device_status": status,
@@ -792,12 +801,18 @@ def cpu_baseline(w, Xh, precision=1):
     dt_one, _, out_one = time_oracle(O, w, X, 1)
     O.set_threads(cpus or 1)
     assert np.array_equal(out_one[2], L_o)  # the thread count does not change the oracle's results
+    dt_b, order_b, state_b, out_b = oracle_boost(O, w, X, gi_o, L_o, k)
     return {"value": ns / dt_all, "unit": "samples/s", "cores": used_all, "kind": "oracle",
             "sample": f"first {ns} samples of {w.name}, k = {k}, k0 = {ns // w.xi}, kappa = {w.kappa}, "
                       f"tau = {w.tau}, iters = {w.iters}: graph construction + fit, FP64 C with OpenMP",
             "seconds": dt_all, "cpu_model": model, "host_cpus": cpus,
             "single_thread": {"value": ns / dt_one, "unit": "samples/s", "cores": 1, "seconds": dt_one},
-            "gpu_vs_oracle": gpu_vs_oracle(w, X, k, (gi_o, L_o, E_o), precision)}
+            "gpu_vs_oracle": gpu_vs_oracle(w, X, k, (gi_o, L_o, E_o), precision),
+            "boost_form": {"us_per_visit": round(1e6 * dt_b / ns, 3), "visits": ns, "seconds": dt_b, "cores": 1,
+                           "moves": out_b[4],
+                           "sample": "one epoch of the move step over a seeded permutation of the sample, from the "
+                                     "oracle fit's partition on the oracle's graph (FP64 C, sequential)",
+                           "gpu_vs_oracle": gpu_boost_vs_oracle(w, X, gi_o, L_o, k, order_b, state_b, out_b)}}
 
 
 def run_reference(args):
@@ -863,6 +878,79 @@ def time_tree(gkm, torch, X, w, iters=2, reps=3):
             "device_status": status,
             "note": "Alg. 1 initial partition (equal halves, Lloyd 2-means per bisection, FP64 sums); "
                     "not part of the timed step"}
+
+
+def time_boost(gkm, torch, X, w, gi, labels, visits=100_000):
+    """The boost form (Eq. 2 state, Alg. 2's move step with Eq. 3 gains) from the fit's final partition on the
+    step's graph: gk_boost_init, then one epoch over the first `visits` entries of a seeded permutation of the
+    samples (the visits are sequential by definition, so a prefix gives the per-visit rate of a whole epoch).
+    Not part of the timed step."""
+    n, d = X.shape
+    k, dev = w.k, X.device
+    visits = min(visits, n)
+    ws = gkm.workspace(gkm.workspace_size(gkm.GK_OP_BOOST, n, d, k, gi.shape[1]), dev)
+    L = labels.clone()
+    D = torch.empty((k, d), dtype=torch.float64, device=dev)
+    cnt = torch.empty(k, dtype=torch.int32, device=dev)
+    S = torch.empty(k, dtype=torch.float64, device=dev)
+    order = torch.randperm(n, generator=torch.Generator().manual_seed(w.seed + 11))[:visits].to(torch.int32).to(dev)
+    gkm.boost_init(X, L, k, D, cnt, S, ws=ws)
+    gkm.boost_epoch(X, gi, order[:0], L, k, D, cnt, S, ws=ws)  # first launch: the cluster shape is queried once
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    s = torch.cuda.current_stream()
+    e0.record(s)
+    gkm.boost_init(X, L, k, D, cnt, S, ws=ws)
+    e1.record(s)
+    ne = cnt > 0
+    I0 = float((S[ne] / cnt[ne]).sum())
+    e1b = torch.cuda.Event(enable_timing=True)
+    e1b.record(s)
+    mv = gkm.boost_epoch(X, gi, order, L, k, D, cnt, S, ws=ws)
+    e2.record(s)
+    torch.cuda.synchronize()
+    ms = e1b.elapsed_time(e2)
+    ne = cnt > 0
+    I1 = float((S[ne] / cnt[ne]).sum())
+    status = gkm.read_status(ws)
+    out = {"visits": visits, "epoch_prefix_ms": round(ms, 3), "us_per_visit": round(1e3 * ms / visits, 3),
+           "visits_per_s": round(visits / ms * 1e3, 1), "moves": int(mv.item()),
+           "init_ms": round(e0.elapsed_time(e1), 3), "projected_epoch_s": round(n * ms / visits / 1e3, 2),
+           "objective_I_gain_per_sample": (I1 - I0) / n, "device_status": status,
+           "note": "one thread-block cluster walks the visits in order (FP64, bit-equal to the oracle); the "
+                   "partition is the fit's final one and the graph the step's; not part of the timed step"}
+    del ws, D, S, cnt, L
+    return out
+
+
+def oracle_boost(O, w, X, gi, L, k):
+    """The oracle's boost form on a sample (its graph and its fit's labels), one epoch over a seeded permutation
+    of the sample: (seconds of the epoch, visits, the final state)."""
+    ns = X.shape[0]
+    order = np.random.default_rng(w.seed + 11).permutation(ns).astype(np.int32)
+    D, cnt, S = O.boost_init(X, L, k)
+    t0 = time.perf_counter()
+    out = O.boost_epoch(X, gi, order, L, k, D, cnt, S)
+    return time.perf_counter() - t0, order, (D, cnt, S), out
+
+
+def gpu_boost_vs_oracle(w, X, gi, L, k, order, state0, ora_out):
+    """The library's boost epoch on the oracle's sample from the same state and visits: equal bit for bit?"""
+    import torch
+
+    from paper_1705_01813_gb300 import gkm
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    if w.storage == "bf16":
+        Xd = Xd.to(torch.bfloat16)  # the sample holds widened BF16 values: exact
+    Ld = torch.from_numpy(np.ascontiguousarray(L, dtype=np.int32)).cuda()
+    D, cnt, S = gkm.boost_init(Xd, Ld, k)
+    init_equal = all(np.array_equal(a.cpu().numpy(), b) for a, b in zip((D, cnt, S), state0))
+    mv = gkm.boost_epoch(Xd, torch.from_numpy(np.ascontiguousarray(gi, dtype=np.int32)).cuda(),
+                         torch.from_numpy(order).cuda(), Ld, k, D, cnt, S)
+    Lo, Do, co, So, mo, _ = ora_out
+    equal = (np.array_equal(Ld.cpu().numpy(), Lo) and np.array_equal(D.cpu().numpy(), Do)
+             and np.array_equal(cnt.cpu().numpy(), co) and np.array_equal(S.cpu().numpy(), So))
+    return {"init_state_equal": init_equal, "epoch_state_equal": equal, "moves": int(mv.item()), "oracle_moves": mo}
 
 
 def main():

@@ -5,7 +5,9 @@
 // neighbours and moves to the one whose Eq. 3 gain
 //     ((D_v + x)'(D_v + x) / (n_v + 1) + (D_u - x)'(D_u - x) / (n_u - 1)) - S_v / n_v - S_u / n_u
 // is largest, if that gain is positive.  Each move changes two clusters and one
-// label before the next visit reads them, so the visits run in order.
+// label before the next visit reads them, so the result is that of visiting in
+// order; the kernel below evaluates windows of visits at once and commits them
+// in order only as far as that result allows.
 //
 // Arithmetic, fixed so that every decision is reproducible: FP64; D_r starts
 // as its members' rows summed in ascending sample id; a squared norm squares
@@ -16,11 +18,12 @@
 // divides by n_u - 1); equal gains go to the smaller label.
 //
 // Layout: D is k x d row-major FP64; S, counts and labels are k / k / n
-// arrays.  One thread-block cluster (up to 16 CTAs, one per SM) walks the
-// visits: one warp per candidate (and one for the own cluster) computes the
-// squared norm of D_v + x (D_u - x) with lane l holding elements l + 32 m,
-// and CTA 0 takes the arg-max and applies the move.  GB300 runs FP64 at a
-// small fraction of its FP32 rate, so a visit's FP64 work is spread over the
+// arrays.  One thread-block cluster (up to 16 CTAs, one per SM) runs the
+// epoch: one warp per (visit, cluster) task computes the squared norm of
+// D_v + x (D_u - x) with lane l holding elements l + 32 m, the owning CTA
+// divides its tasks' terms, and CTA 0 takes the arg-max of each visit, finds
+// how far the window may commit and applies the moves.  GB300 runs FP64 at a
+// small fraction of its FP32 rate, so the FP64 work is spread over the
 // cluster's SMs.  After a move, S_u and S_v are the two norms already computed
 // for the decision: the new rows are exactly the rounded sums that were
 // squared.
@@ -112,22 +115,31 @@ __global__ void __launch_bounds__(256) k_boost_norms(const double *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// One epoch of the move step over order[0..m), on one cluster of R CTAs.
+// One epoch of the move step over order[0..m), on one cluster of R CTAs, in
+// windows of up to W visits.
 //
-// Per visit: every CTA stages the sample and gathers the candidate set Q (the
-// same labels, so the same Q); the squared norms (task 0: D_u - x, task c:
-// D_v + x for the c-th candidate) are spread over the cluster's warps, and
-// each task's result (with S_v and n_v) is stored into CTA 0's shared memory;
-// a cluster barrier; CTA 0 evaluates the gains (its warps split the
-// divisions), takes the arg-max and applies the move; a second cluster barrier
-// publishes the move before the next visit reads labels or rows.  Both
-// barriers are unconditional, so the barrier sequence never depends on data.
-// The FP64 work of a visit thus runs on R SMs; mutable state (labels, D, S,
-// counts) is read through L2 (ld.global.cg), which the barriers order.
+// A window's visits are evaluated together against the state at its start:
+// every CTA stages the window's samples and gathers the candidate sets; the
+// squared norms of all the window's (visit, cluster) tasks are spread over the
+// cluster's warps, and each CTA divides its own tasks' terms (lanes over
+// tasks) and stores them into CTA 0.  CTA 0 takes each visit's arg-max, then
+// commits the visits in order up to the first one whose inputs an earlier
+// committed move of the window changed (its sample or one of its neighbours
+// moved; its own cluster or a candidate was the source or target of a move).
+// A committed visit therefore saw exactly the state the sequential walk gives
+// it, and the committed moves touch disjoint clusters, so CTA 0 applies them
+// together; the next window starts at the first visit not committed (the
+// first visit of a window always commits).  The window grows while windows
+// commit whole and shrinks to twice what the last one committed, so that few
+// evaluations are thrown away where moves collide often.  Both cluster
+// barriers of a window are unconditional.  Mutable state (labels, D, S, counts) is read through L2
+// (ld.global.cg), which the barriers order.
 // ---------------------------------------------------------------------------
 constexpr int BE_THREADS = 256;
 constexpr int BE_WARPS = BE_THREADS / 32;
 constexpr int BE_MAX_CLUSTER = 16;
+constexpr int BE_MAX_WINDOW = 32;
+constexpr size_t BE_SMEM_BUDGET = 200 * 1024;
 
 __device__ __forceinline__ void cluster_barrier()
 {
@@ -168,150 +180,208 @@ __device__ __forceinline__ void st_rank(const void *p, int rank, int v)
     asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(in_rank(p, rank)), "r"(v) : "memory");
 }
 
+// Dynamic shared memory of one CTA for windows of W visits (the same layout in every CTA of the cluster).
+struct WinLayout {
+    int W, kp, TM, TL;
+    size_t xs, ra, r1, r3, gk, la, ls, rn, ln, lo, tv, sq, sg, svis, su, snq, sbase, dq, ml, tl, mvj, bytes;
+    __host__ __device__ WinLayout(int W_, int P, int kappa, int R)
+    {
+        W = W_;
+        kp = (kappa + 31) / 32 * 32;
+        TM = W * (kappa + 1);
+        TL = (TM + R - 1) / R;
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = o;
+            o += (bytes + 15) / 16 * 16;
+            return at;
+        };
+        xs = take((size_t)W * P * 8);
+        ra = take((size_t)TM * 8);
+        r1 = take((size_t)TM * 8);
+        r3 = take((size_t)TM * 8);
+        gk = take((size_t)TM * 8);
+        la = take((size_t)TL * 8);
+        ls = take((size_t)TL * 8);
+        rn = take((size_t)TM * 4);
+        ln = take((size_t)TL * 4);
+        lo = take((size_t)TL * 4);
+        tv = take((size_t)TM * 4);
+        sq = take((size_t)W * kp * 4);
+        sg = take((size_t)W * kp * 4);
+        svis = take((size_t)W * 4);
+        su = take((size_t)W * 4);
+        snq = take((size_t)W * 4);
+        sbase = take((size_t)(W + 1) * 4);
+        dq = take((size_t)W * 4);
+        ml = take((size_t)W * 4);
+        tl = take((size_t)2 * W * 4);
+        mvj = take((size_t)W * 4);
+        bytes = o;
+    }
+};
+
 template <typename XT, int PL>
 __global__ void __launch_bounds__(BE_THREADS, 1)
     k_boost_epoch(const XT *__restrict__ X, int32_t n, int d, int64_t ld, const int32_t *__restrict__ G, int kappa,
                   const int32_t *__restrict__ order, int64_t m, int32_t *L, int32_t k, double *D, int32_t *cnt,
-                  double *S, int64_t *n_moved, DevStatus *st)
+                  double *S, int64_t *n_moved, DevStatus *st, int W)
 {
     constexpr int P = 32 * PL;
-    constexpr int XR = (P + BE_THREADS - 1) / BE_THREADS;  // sample elements staged per thread
-    constexpr int GR = MAX_KAPPA / 32;                      // graph ids per lane of warp 0
-    __shared__ double xs[2][P];          // the visited sample in FP64 (zero beyond d), by visit parity
-    __shared__ int32_t s_q[MAX_KAPPA];   // candidate clusters (every CTA)
-    __shared__ double s_a[MAX_KAPPA];    // CTA 0: (D_v + x)'(D_v + x), stored by the task owners
-    __shared__ double s_sv[MAX_KAPPA];   // CTA 0: S_v
-    __shared__ int32_t s_nv[MAX_KAPPA];  // CTA 0: n_v
-    __shared__ double s_t1[MAX_KAPPA];   // CTA 0: A_v / (n_v + 1)
-    __shared__ double s_t3[MAX_KAPPA];   // CTA 0: S_v / n_v
-    __shared__ double s_b, s_tu1, s_tu2; // CTA 0: B, B / (n_u - 1), S_u / n_u
-    __shared__ int s_nq, s_u, s_nu;
-    __shared__ double s_gb[MAX_KAPPA / 32];                      // CTA 0: each group's best gain,
-    __shared__ int s_gv[MAX_KAPPA / 32], s_gq[MAX_KAPPA / 32];  // its label and candidate index
-    __shared__ int s_mv[3];  // the last visit's move (sample, from, to; to = -1: none), stored by CTA 0
-
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_win, s_nm, s_T, s_first;
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const int rank = (int)cluster_rank(), R = (int)cluster_size();
-    int64_t moves = 0;
-    auto visit_id = [&](int64_t s) { return s < m ? __ldg(order + s) : -1; };
+    const WinLayout Y(W, P, kappa, R);
+    const int kp = Y.kp;
+    double *xs = reinterpret_cast<double *>(smem + Y.xs);
+    double *ra = reinterpret_cast<double *>(smem + Y.ra), *r1 = reinterpret_cast<double *>(smem + Y.r1);
+    double *r3 = reinterpret_cast<double *>(smem + Y.r3);
+    long long *gk = reinterpret_cast<long long *>(smem + Y.gk);
+    int *tv = reinterpret_cast<int *>(smem + Y.tv);
+    double *la = reinterpret_cast<double *>(smem + Y.la), *ls = reinterpret_cast<double *>(smem + Y.ls);
+    int *rn = reinterpret_cast<int *>(smem + Y.rn), *ln = reinterpret_cast<int *>(smem + Y.ln);
+    int *lo = reinterpret_cast<int *>(smem + Y.lo);
+    int *sq = reinterpret_cast<int *>(smem + Y.sq), *sg = reinterpret_cast<int *>(smem + Y.sg);
+    int *svis = reinterpret_cast<int *>(smem + Y.svis), *su = reinterpret_cast<int *>(smem + Y.su);
+    int *snq = reinterpret_cast<int *>(smem + Y.snq), *sbase = reinterpret_cast<int *>(smem + Y.sbase);
+    int *dq = reinterpret_cast<int *>(smem + Y.dq), *ml = reinterpret_cast<int *>(smem + Y.ml);
+    int *tl = reinterpret_cast<int *>(smem + Y.tl), *mvj = reinterpret_cast<int *>(smem + Y.mvj);
     auto valid = [&](int i) { return i >= 0 && i < n; };
-    // Pipeline: the sample row of the next visit (all threads), the labels of the next visit's neighbours and
-    // the graph row of the one after (warp 0).  Labels read one visit ahead miss only the move of the visit in
-    // between, which every CTA patches in from s_mv.
-    float xr[XR];
-    int gcur[GR], lcur[GR], gnx[GR], lnx[GR];
-    int ucur = -1, unx = -1;
-    auto load_x = [&](int i) {
-#pragma unroll
-        for (int c = 0; c < XR; c++) {
-            const int j = threadIdx.x + c * BE_THREADS;
-            xr[c] = valid(i) && j < d ? ldx(X + (int64_t)i * ld + j) : 0.f;
-        }
-    };
-    auto load_g = [&](int i, int (&g)[GR]) {
-#pragma unroll
-        for (int c = 0; c < GR; c++) {
-            const int j = lane + 32 * c;
-            g[c] = valid(i) && j < kappa ? __ldg(G + (int64_t)i * kappa + j) : -1;
-        }
-    };
-    auto load_l = [&](int i, const int (&g)[GR], int (&l)[GR], int &u) {
-        u = valid(i) ? __ldcg(L + i) : -1;
-#pragma unroll
-        for (int c = 0; c < GR; c++)
-            l[c] = valid(g[c]) ? __ldcg(L + g[c]) : -2;
-    };
-    int i_cur = visit_id(0), i_nx = visit_id(1), i_nx2 = visit_id(2);
-    load_x(i_cur);
-    if (w == 0) {
-        load_g(i_cur, gcur);
-        load_l(i_cur, gcur, lcur, ucur);
-        load_g(i_nx, gnx);
-    }
-    if (threadIdx.x == 0)
-        s_mv[0] = s_mv[1] = s_mv[2] = -1;
+    int64_t moves = 0;
+    int We = W;  // this window's size: doubled after a window that commits whole, else twice what committed
     cluster_barrier();  // every CTA of the cluster runs before any stores into another's shared memory
 
-    for (int64_t s = 0; s < m; s++) {
-        const int i = i_cur;
-        const int buf = (int)(s & 1);
-        const int pi = s_mv[0], pu = s_mv[1], pv = s_mv[2];  // the previous visit's move, pending in D
-        // ---- stage the sample; gather its candidates (warp 0 of every CTA, from the same labels)
-#pragma unroll
-        for (int c = 0; c < XR; c++) {
-            const int j = threadIdx.x + c * BE_THREADS;
-            if (j < P)
-                xs[buf][j] = (double)xr[c];
-        }
-        if (w == 0) {
-            int u = ucur;
-            if (pv >= 0 && i == pi)
-                u = pv;
+    for (int64_t s = 0; s < m;) {
+        const int Wn = (int)(m - s < (int64_t)We ? m - s : (int64_t)We);
+        // ---- the window's visits: ids, then samples, graph rows and own labels, then the neighbours' labels
+        if (threadIdx.x < Wn)
+            svis[threadIdx.x] = __ldg(order + s + threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x < Wn) {
+            const int i = svis[threadIdx.x];
+            int u = -1;
             if (!valid(i)) {
-                if (lane == 0 && rank == 0)
-                    flag_error(st, GK_ERR_INVALID, (unsigned)s);
-                u = -1;
-            } else if (u < 0 || u >= k) {
-                if (lane == 0 && rank == 0)
-                    flag_error(st, GK_ERR_INVALID, (unsigned)i);
-                u = -1;
+                if (rank == 0)
+                    flag_error(st, GK_ERR_INVALID, (unsigned)(s + threadIdx.x));
+            } else {
+                u = __ldcg(L + i);
+                if (u < 0 || u >= k) {
+                    if (rank == 0)
+                        flag_error(st, GK_ERR_INVALID, (unsigned)i);
+                    u = -1;
+                }
             }
+            su[threadIdx.x] = u;
+        }
+        // loads issued eight at a time per thread, then stored: one round trip per batch
+        for (int e0 = threadIdx.x; e0 < Wn * P; e0 += 8 * BE_THREADS) {
+            float v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int e = e0 + b * BE_THREADS, j = e / P, t = e - j * P;
+                v[b] = e < Wn * P && valid(svis[j]) && t < d ? ldx(X + (int64_t)svis[j] * ld + t) : 0.f;
+            }
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+                if (e0 + b * BE_THREADS < Wn * P)
+                    xs[e0 + b * BE_THREADS] = (double)v[b];
+        }
+        for (int e0 = threadIdx.x; e0 < Wn * kp; e0 += 8 * BE_THREADS) {
+            int v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int e = e0 + b * BE_THREADS, j = e / kp, t = e - j * kp;
+                v[b] = e < Wn * kp && valid(svis[j]) && t < kappa ? __ldg(G + (int64_t)svis[j] * kappa + t) : -1;
+            }
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+                if (e0 + b * BE_THREADS < Wn * kp)
+                    sg[e0 + b * BE_THREADS] = v[b];
+        }
+        __syncthreads();
+        for (int e0 = threadIdx.x; e0 < Wn * kp; e0 += 8 * BE_THREADS) {
+            int v[8];
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int e = e0 + b * BE_THREADS;
+                v[b] = -3;  // -3: no label wanted
+                if (e < Wn * kp && e % kp < kappa && su[e / kp] >= 0)
+                    v[b] = valid(sg[e]) ? __ldcg(L + sg[e]) : -2;
+            }
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const int e = e0 + b * BE_THREADS;
+                if (e >= Wn * kp)
+                    continue;
+                if (v[b] == -2 || (v[b] != -3 && (v[b] < 0 || v[b] >= k))) {
+                    if (rank == 0)
+                        flag_error(st, GK_ERR_INVALID, (unsigned)(v[b] == -2 ? svis[e / kp] : sg[e]));
+                    v[b] = -1;
+                }
+                sq[e] = v[b] == -3 ? -1 : v[b];
+            }
+        }
+        __syncthreads();
+        // candidate set of visit j (warp w takes j = w, w + 8, ...): distinct labels other than its own, in place
+        for (int j = w; j < Wn; j += BE_WARPS) {
+            const int u = su[j];
+            int lab[MAX_KAPPA / 32];
+#pragma unroll
+            for (int c = 0; c < MAX_KAPPA / 32; c++)
+                lab[c] = 32 * c < kp ? sq[j * kp + 32 * c + lane] : -1;
+            __syncwarp();
             int nq = 0;
 #pragma unroll
-            for (int c = 0; c < GR; c++) {
-                if (u < 0 || 32 * c >= kappa)
+            for (int c = 0; c < MAX_KAPPA / 32; c++) {
+                if (32 * c >= kp)
                     break;
-                int v = lcur[c];
-                if (pv >= 0 && gcur[c] == pi)
-                    v = pv;
-                const bool in_row = lane + 32 * c < kappa;
-                if (in_row && (v < 0 || v >= k) && rank == 0)
-                    flag_error(st, GK_ERR_INVALID, (unsigned)(v == -2 ? i : gcur[c]));
-                if (!in_row || v < 0 || v >= k || v == u)
-                    v = -1;
+                int v = lab[c] == u ? -1 : lab[c];
                 bool keep = v >= 0;
 #pragma unroll 8
-                for (int q = 0; q < nq; q++)  // broadcast reads, independent of one another
-                    keep &= s_q[q] != v;
+                for (int q = 0; q < nq; q++)
+                    keep &= sq[j * kp + q] != v;
                 const unsigned same = __match_any_sync(FULL_MASK, v);
                 keep = keep && (__ffs(same) - 1 == lane);
                 const unsigned km = __ballot_sync(FULL_MASK, keep);
                 if (keep)
-                    s_q[nq + __popc(km & lanemask_lt())] = v;
+                    sq[j * kp + nq + __popc(km & lanemask_lt())] = v;
                 nq += __popc(km);
                 __syncwarp();
             }
-            if (lane == 0) {
-                s_nq = nq;
-                s_u = u;
-            }
-            // one visit ahead: the next visit's labels (this visit's move is patched in later), the graph row
-            // of the visit after it
-            load_l(i_nx, gnx, lnx, unx);
-#pragma unroll
-            for (int c = 0; c < GR; c++)
-                gcur[c] = gnx[c];
-            load_g(i_nx2, gnx);
+            if (lane == 0)
+                snq[j] = u >= 0 ? nq : 0;
         }
-        load_x(i_nx);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // tasks of visit j: [sbase[j], sbase[j + 1]), the first its own cluster
+            int T = 0;
+            for (int j = 0; j < Wn; j++) {
+                sbase[j] = T;
+                T += snq[j] > 0 ? snq[j] + 1 : 0;
+            }
+            sbase[Wn] = T;
+            s_T = T;
+        }
+        __syncthreads();
+        for (int j = w; j < Wn; j += BE_WARPS)
+            for (int t = sbase[j] + lane; t < sbase[j + 1]; t += 32)
+                tv[t] = j;
         __syncthreads();
 
-        // ---- squared norms: task c = 0 the own cluster (D_u - x), c >= 1 candidate c - 1 (D_v + x); task c runs
-        //      on CTA c mod R, warp (c / R) mod BE_WARPS.  Rows pu and pv still lack the previous move.
-        const int nq = s_nq, u = s_u;
-        if (rank == 0 && w == BE_WARPS - 1 && nq > 0 && lane == 0) {  // S_u / n_u, beside task 0's fold
-            const int nu = __ldcg(cnt + u);
-            s_nu = nu;
-            s_tu2 = __ddiv_rn(__ldcg(S + u), (double)nu);
-        }
-        for (int c = rank + R * w; nq > 0 && c <= nq; c += R * BE_WARPS) {
-            const int r = c == 0 ? u : s_q[c - 1];
+        // ---- squared norms of the tasks: task t on CTA t mod R; c = 0 the own cluster (D_u - x), else a
+        //      candidate (D_v + x)
+        const int T = s_T;
+        for (int t = rank + R * w; t < T; t += R * BE_WARPS) {
+            const int j = tv[t];
+            const int c = t - sbase[j];
+            const int r = c == 0 ? su[j] : sq[j * kp + c - 1];
             const double *Dr = D + (int64_t)r * d;
+            const double *xj = xs + (size_t)j * P;
             double a[PL];
 #pragma unroll
             for (int q = 0; q < PL; q++) {
-                const int j = lane + 32 * q;
-                a[q] = j < d ? __ldcg(Dr + j) : 0.0;
+                const int e = lane + 32 * q;
+                a[q] = e < d ? __ldcg(Dr + e) : 0.0;
             }
             double sr = 0.0;
             int nr = 0;
@@ -319,143 +389,165 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
                 sr = __ldcg(S + r);
                 nr = __ldcg(cnt + r);
             }
-            const int pend = pv < 0 ? 0 : (r == pu ? -1 : (r == pv ? 1 : 0));
 #pragma unroll
             for (int q = 0; q < PL; q++) {
-                const int j = lane + 32 * q;
-                double y = 0.0;
-                if (j < d) {
-                    double dr = a[q];
-                    if (pend < 0)
-                        dr = __dsub_rn(dr, xs[buf ^ 1][j]);
-                    else if (pend > 0)
-                        dr = __dadd_rn(dr, xs[buf ^ 1][j]);
-                    y = c == 0 ? __dsub_rn(dr, xs[buf][j]) : __dadd_rn(dr, xs[buf][j]);
-                }
+                const int e = lane + 32 * q;
+                const double y = e < d ? (c == 0 ? __dsub_rn(a[q], xj[e]) : __dadd_rn(a[q], xj[e])) : 0.0;
                 a[q] = __dmul_rn(y, y);
             }
             const double tot = fold_lanes<PL>(a);
             if (lane == 0) {
-                if (c == 0) {  // on CTA 0: the own cluster's term B / (n_u - 1)
-                    s_b = tot;
-                    s_tu1 = __ddiv_rn(tot, (double)(nr - 1));
+                const int l = t / R;
+                la[l] = tot;
+                ls[l] = sr;
+                ln[l] = nr;
+                lo[l] = c == 0;
+            }
+        }
+        __syncthreads();
+        // this CTA's tasks' quotients, lanes over tasks; job even: A / (n_v + 1) (own: B / (n_u - 1)), odd: S / n
+        const int TLc = T > rank ? (T - rank + R - 1) / R : 0;
+        for (int jb = w; jb < 2 * ((TLc + 31) / 32); jb += BE_WARPS) {
+            const int l = (jb >> 1) * 32 + lane;
+            if (l < TLc) {
+                const int t = l * R + rank;
+                if (jb & 1) {
+                    st_rank(&r3[t], 0, __ddiv_rn(ls[l], (double)ln[l]));
                 } else {
-                    st_rank(&s_a[c - 1], 0, tot);
-                    st_rank(&s_sv[c - 1], 0, sr);
-                    st_rank(&s_nv[c - 1], 0, nr);
+                    st_rank(&r1[t], 0, __ddiv_rn(la[l], (double)(lo[l] ? ln[l] - 1 : ln[l] + 1)));
+                    st_rank(&ra[t], 0, la[l]);
+                    st_rank(&rn[t], 0, ln[l]);
                 }
             }
         }
         cluster_barrier();
 
-        // ---- CTA 0: the previous move's rows (warps 4-7, overlapping the rest); the Eq. 3 gains, the arg-max,
-        //      this move's sizes, norms and label
+        // ---- CTA 0: each visit's arg-max, the in-order commit and the committed moves
         if (rank == 0) {
-            const int nu = nq > 0 ? s_nu : 0;
-            if (w >= 4) {
-                if (pv >= 0) {
-                    double *Du = D + (int64_t)pu * d, *Dv = D + (int64_t)pv * d;
-                    for (int j = threadIdx.x - 128; j < d; j += BE_THREADS - 128) {
-                        Du[j] = __dsub_rn(__ldcg(Du + j), xs[buf ^ 1][j]);
-                        Dv[j] = __dadd_rn(__ldcg(Dv + j), xs[buf ^ 1][j]);
-                    }
-                }
-            } else if (nq > 0 && nu >= 2) {
-                // division job t: group t / 2 (32 candidates); t even: (D_v + x)'(D_v + x) / (n_v + 1), odd: S_v / n_v
-                for (int t = w; t < 2 * ((nq + 31) / 32); t += 4) {
-                    const int q = (t >> 1) * 32 + lane;
-                    if (q < nq) {
-                        if (t & 1)
-                            s_t3[q] = __ddiv_rn(s_sv[q], (double)s_nv[q]);
-                        else
-                            s_t1[q] = __ddiv_rn(s_a[q], (double)(s_nv[q] + 1));
-                    }
+            // the gain of every candidate task, as an integer key in the order of the FP64 values (the gains are
+            // sums and differences of non-negative terms, never -0, so the keys order them exactly)
+            for (int t = threadIdx.x; t < T; t += BE_THREADS) {
+                const int o = sbase[tv[t]];
+                if (t != o) {
+                    const double g = __dsub_rn(__dsub_rn(__dadd_rn(r1[t], r1[o]), r3[t]), r3[o]);
+                    const long long b = __double_as_longlong(g);
+                    gk[t] = b ^ ((b >> 63) & 0x7fffffffffffffffll);
                 }
             }
             __syncthreads();
-            // warp g: the gains of group g and their arg-max (the larger gain, then the smaller label)
-            if (w < (nq + 31) / 32 && nu >= 2) {
-                const int q = w * 32 + lane;
-                int bv = -1, bq = -1;
-                double best = 0.0;
-                if (q < nq) {
-                    bv = s_q[q];
-                    bq = q;
-                    best = __dsub_rn(__dsub_rn(__dadd_rn(s_t1[q], s_tu1), s_t3[q]), s_tu2);
-                }
+            for (int j = w; j < Wn; j += BE_WARPS) {
+                const int nq = snq[j], o = sbase[j];
+                int bt = -1, bv = -1;
+                long long best = 0;
+                if (nq > 0 && rn[o] >= 2) {
+                    for (int c = 1 + lane; c <= nq; c += 32) {
+                        const int t = o + c, v = sq[j * kp + c - 1];
+                        const long long g = gk[t];
+                        if (bv < 0 || g > best || (g == best && v < bv)) {
+                            best = g;
+                            bv = v;
+                            bt = t;
+                        }
+                    }
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) {
-                    const double ob = __shfl_xor_sync(FULL_MASK, best, o);
-                    const int ov = __shfl_xor_sync(FULL_MASK, bv, o), oq = __shfl_xor_sync(FULL_MASK, bq, o);
-                    if (ov >= 0 && (bv < 0 || ob > best || (ob == best && ov < bv))) {
-                        best = ob;
-                        bv = ov;
-                        bq = oq;
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        const long long ob = __shfl_xor_sync(FULL_MASK, best, off);
+                        const int ov = __shfl_xor_sync(FULL_MASK, bv, off), ot = __shfl_xor_sync(FULL_MASK, bt, off);
+                        if (ov >= 0 && (bv < 0 || ob > best || (ob == best && ov < bv))) {
+                            best = ob;
+                            bv = ov;
+                            bt = ot;
+                        }
                     }
                 }
-                if (lane == 0) {
-                    s_gb[w] = best;
-                    s_gv[w] = bv;
-                    s_gq[w] = bq;
+                if (lane == 0)
+                    dq[j] = bv >= 0 && best > 0 ? bt : -1;  // key > 0: gain > +0
+            }
+            __syncthreads();
+            // the visits that would move, in order: sample ml, clusters tl[2 q] (from) and tl[2 q + 1] (to)
+            if (threadIdx.x == 0) {
+                int nm = 0;
+                for (int j = 0; j < Wn; j++) {
+                    const int t = dq[j];
+                    if (t >= 0) {
+                        ml[nm] = svis[j];
+                        mvj[nm] = j;
+                        tl[2 * nm] = su[j];
+                        tl[2 * nm + 1] = sq[j * kp + t - sbase[j] - 1];
+                        nm++;
+                    }
+                }
+                s_nm = nm;
+                s_first = Wn;
+            }
+            __syncthreads();
+            // the window commits up to the first visit that depends on an earlier moving visit: its sample or a
+            // neighbour is that visit's sample, or its own cluster or a candidate is one that visit leaves or joins
+            {
+                const int nmv = s_nm, per = 1 + kp + 1 + kp;  // items of a visit: sample, neighbours, own, candidates
+                for (int e = threadIdx.x; nmv > 0 && e < Wn * per; e += BE_THREADS) {
+                    const int j = e / per, c = e - j * per;
+                    int x = -1;
+                    bool sample = true;
+                    if (c == 0) {
+                        x = svis[j];
+                    } else if (c <= kp) {
+                        x = c - 1 < kappa ? sg[j * kp + c - 1] : -1;
+                    } else if (su[j] >= 0) {
+                        sample = false;
+                        const int cc = c - kp - 1;  // 0: own cluster, else candidate cc - 1
+                        x = cc == 0 ? su[j] : (cc <= snq[j] ? sq[j * kp + cc - 1] : -1);
+                    }
+                    if (x < 0)
+                        continue;
+                    for (int q = 0; q < nmv && mvj[q] < j; q++)
+                        if (sample ? ml[q] == x : (tl[2 * q] == x || tl[2 * q + 1] == x)) {
+                            atomicMin(&s_first, j);
+                            break;
+                        }
                 }
             }
             __syncthreads();
+            const int done = s_first;
             if (w == 0) {
-                const int groups = nq > 0 && nu >= 2 ? (nq + 31) / 32 : 0;
-                int bv = -1, bq = -1;
-                double best = 0.0;
-                for (int g = 0; g < groups; g++) {
-                    const int ov = s_gv[g];
-                    const double ob = s_gb[g];
-                    if (ov >= 0 && (bv < 0 || ob > best || (ob == best && ov < bv))) {
-                        best = ob;
-                        bv = ov;
-                        bq = s_gq[g];
-                    }
-                }
-                const int v = best > 0.0 ? bv : -1;
-                if (lane < R) {  // every CTA learns the move (its rows stay pending in D until the next visit)
-                    st_rank(&s_mv[0], lane, i);
-                    st_rank(&s_mv[1], lane, u);
-                    st_rank(&s_mv[2], lane, v);
-                }
-                if (lane == 0 && v >= 0) {
-                    cnt[u] = nu - 1;
-                    cnt[v] = s_nv[bq] + 1;
-                    S[u] = s_b;
-                    S[v] = s_a[bq];
-                    L[i] = v;
-                    moves++;
-                }
+                if (lane < R)
+                    st_rank(&s_win, lane, done);
             }
+            int nm = 0;  // the committed moves: the moving visits before `done`
+            while (nm < s_nm && mvj[nm] < done)
+                nm++;
+            // the committed moves touch disjoint clusters: x leaves S_u for S_v in each
+            for (int e = threadIdx.x; e < nm * d; e += BE_THREADS) {
+                const int q = e / d, t = e - q * d, j = mvj[q];
+                const int u = su[j], v = tl[2 * q + 1];
+                const double x = xs[(size_t)j * P + t];
+                D[(int64_t)u * d + t] = __dsub_rn(__ldcg(D + (int64_t)u * d + t), x);
+                D[(int64_t)v * d + t] = __dadd_rn(__ldcg(D + (int64_t)v * d + t), x);
+            }
+            if (threadIdx.x < nm) {
+                const int j = mvj[threadIdx.x], o = sbase[j], t = dq[j];
+                const int u = su[j], v = tl[2 * threadIdx.x + 1];
+                cnt[u] = rn[o] - 1;
+                cnt[v] = rn[t] + 1;
+                S[u] = ra[o];
+                S[v] = ra[t];
+                L[svis[j]] = v;
+            }
+            moves += nm;
         }
-        cluster_barrier();  // the move's label, sizes and norms, and the previous move's rows, before the next visit
-        i_cur = i_nx;
-        i_nx = i_nx2;
-        i_nx2 = visit_id(s + 3);
-        if (w == 0) {
-            ucur = unx;
-#pragma unroll
-            for (int c = 0; c < GR; c++)
-                lcur[c] = lnx[c];
-        }
-    }
-    // the last move's rows
-    if (rank == 0 && m > 0 && s_mv[2] >= 0) {
-        const int pu = s_mv[1], pv = s_mv[2], pb = (int)((m - 1) & 1);
-        double *Du = D + (int64_t)pu * d, *Dv = D + (int64_t)pv * d;
-        for (int j = threadIdx.x; j < d; j += BE_THREADS) {
-            Du[j] = __dsub_rn(__ldcg(Du + j), xs[pb][j]);
-            Dv[j] = __dadd_rn(__ldcg(Dv + j), xs[pb][j]);
-        }
+        cluster_barrier();  // the window's moves before the next window reads labels and rows
+        const int got = s_win;  // the same in every CTA
+        We = got == Wn ? (2 * We < W ? 2 * We : W) : (2 * got < W ? (2 * got > 2 ? 2 * got : 2) : W);
+        s += got;
     }
     if (rank == 0 && threadIdx.x == 0 && n_moved)
         *n_moved = moves;
 }
 
-// Largest cluster (at most BE_MAX_CLUSTER CTAs) the device can run for this kernel, once per device and kernel.
+// Largest cluster (at most BE_MAX_CLUSTER CTAs) the device can run for this kernel with `smem` bytes of dynamic
+// shared memory per CTA, once per device and kernel.
 template <typename KernelT>
-int epoch_cluster_size(KernelT kern)
+int epoch_cluster_size(KernelT kern, size_t smem)
 {
     static std::mutex mu;
     static std::map<std::pair<int, const void *>, int> known;
@@ -467,21 +559,25 @@ int epoch_cluster_size(KernelT kern)
     auto it = known.find(key);
     if (it != known.end())
         return it->second;
-    int r = 8;  // portable size
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(BE_MAX_CLUSTER);
-        cfg.blockDim = dim3(BE_THREADS);
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = BE_MAX_CLUSTER;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int most = 0;
-        if (cudaOccupancyMaxPotentialClusterSize(&most, kern, &cfg) == cudaSuccess && most > 0)
-            r = most < BE_MAX_CLUSTER ? most : BE_MAX_CLUSTER;
+    int r = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess) {
+        r = 8;  // portable size
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(BE_MAX_CLUSTER);
+            cfg.blockDim = dim3(BE_THREADS);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = BE_MAX_CLUSTER;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int most = 0;
+            if (cudaOccupancyMaxPotentialClusterSize(&most, kern, &cfg) == cudaSuccess && most > 0)
+                r = most < BE_MAX_CLUSTER ? most : BE_MAX_CLUSTER;
+        }
     }
     cudaGetLastError();
     known[key] = r;
@@ -494,13 +590,19 @@ cudaError_t boost_epoch_t(const XT *X, int64_t n, int64_t d, int64_t ld, const i
                           int64_t *n_moved, DevStatus *st, cudaStream_t s)
 {
     auto kern = k_boost_epoch<XT, PL>;
-    const int R = epoch_cluster_size(kern);
+    const int R = epoch_cluster_size(kern, BE_SMEM_BUDGET);
     if (R < 1)
+        return cudaErrorInvalidConfiguration;
+    int W = BE_MAX_WINDOW;  // the largest window whose layout fits the budget
+    while (W > 1 && WinLayout(W, 32 * PL, kappa, R).bytes > BE_SMEM_BUDGET)
+        W--;
+    const size_t smem = WinLayout(W, 32 * PL, kappa, R).bytes;
+    if (smem > BE_SMEM_BUDGET)
         return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)R);
     cfg.blockDim = dim3(BE_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -510,7 +612,7 @@ cudaError_t boost_epoch_t(const XT *X, int64_t n, int64_t d, int64_t ld, const i
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, X, (int32_t)n, (int)d, ld, G, (int)kappa, order, m, L, k, D, cnt, S,
-                              n_moved, st);
+                              n_moved, st, W);
 }
 
 template <int PL>
