@@ -7,6 +7,7 @@ summary's ncu command captured, on seeded synthetic samples generated here.
     python -m benchlib.cases sift_assign_levels [--levels 1,3] [--reps R]
     python -m benchlib.cases assign_large_table [--precision P]
     python -m benchlib.cases tree --n 1000000 --d 128 --k 10000 --iters 2 --calls 2
+    python -m benchlib.cases boost [--visits V] [--calls C]
 
 deep_assign_bf16  10^6 x 512 BF16 deep-feature-shaped samples (200,000 vMF directions, kappa_vMF = 50, seed 11);
                   graph construction with kappa = 40, tau = 1 at precision 2, then two fit iterations at
@@ -18,6 +19,8 @@ gist_refine       3 x 10^5 x 960 GIST-shaped samples (1,000 latent centres, seed
 sift_assign_levels  the SIFT-shaped assignment after graph construction and fit, timed per precision level.
 assign_large_table  one assignment over a 10^6-row centroid table (10^6 x 512 BF16 unit vectors, k = 10^6,
                   a random kappa = 40 graph, random labels); --precision selects the screening level.
+boost             the boost form's epoch (Eq. 3 gains, Alg. 2 move step) on the SIFT-shaped sizes, from the
+                  library's graph and fit partition, over prefixes of seeded visit permutations.
 tree              the two-means tree (Alg. 1) on N(0, 1) samples drawn by a CUDA torch generator seeded with
                   --data-seed (BF16 with --bf16); --calls tree calls on one workspace, the first a warm-up;
                   prints one JSON line with the mean time of the other calls and the device status word.
@@ -182,8 +185,44 @@ def tree(argv):
                       "status": gkm.read_status(ws)}))
 
 
+def boost(argv):
+    """The boost form (Eq. 3 gains, Alg. 2 move step) on the SIFT-shaped workload's sizes: 10^6 x 128 FP32
+    samples (datagen.sift_like), the library's graph (kappa = 50, xi = 50, tau = 10) and its fit's partition
+    (k = 10^4, 10 iterations from seeded labels), then --calls epochs over the first --visits entries of seeded
+    permutations; prints one JSON line with the last call's time per visit."""
+    import torch
+
+    from paper_1705_01813_gb300 import datagen, gkm
+    ap = argparse.ArgumentParser(prog="benchlib.cases boost")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--d", type=int, default=128)
+    ap.add_argument("--k", type=int, default=10_000)
+    ap.add_argument("--kappa", type=int, default=50)
+    ap.add_argument("--visits", type=int, default=20_000)
+    ap.add_argument("--calls", type=int, default=2)
+    a = ap.parse_args(argv)
+    X = torch.from_numpy(datagen.sift_like(a.n, a.d)).cuda()
+    gi = gkm.build_knn_graph(X, a.kappa, xi=50, tau=10, seed=1, want_log=False)[0]
+    lab = gkm.kmeans_fit(X, a.k, gi, 10, seed=2, want_log=False)[0].clone()
+    ws = gkm.workspace(gkm.workspace_size(gkm.GK_OP_BOOST, a.n, a.d, a.k, a.kappa), X.device)
+    D, cnt, S = gkm.boost_init(X, lab, a.k, ws=ws)
+    g = torch.Generator().manual_seed(3)
+    ms = None
+    for _ in range(a.calls):
+        order = torch.randperm(a.n, generator=g)[:a.visits].to(torch.int32).cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mv = gkm.boost_epoch(X, gi, order, lab, a.k, D, cnt, S, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    print(json.dumps({"n": a.n, "d": a.d, "k": a.k, "kappa": a.kappa, "visits": a.visits,
+                      "us_per_visit": 1e3 * ms / a.visits, "moves": int(mv.item()), "status": gkm.read_status(ws)}))
+
+
 CASES = {"deep_assign_bf16": deep_assign_bf16, "gist_refine": gist_refine, "deep_refine_rounds": deep_refine_rounds,
-         "sift_assign_levels": sift_assign_levels, "assign_large_table": assign_large_table, "tree": tree}
+         "sift_assign_levels": sift_assign_levels, "assign_large_table": assign_large_table, "tree": tree,
+         "boost": boost}
 
 
 def main(argv=None):
