@@ -475,10 +475,14 @@ GK_API int gk_two_means_tree_bf16(const uint16_t *X, int64_t n, int64_t d, int64
  *   ws             gk_workspace_size(GK_OP_BOOST, n, d, k, kappa) bytes
  * A visit id, label or neighbour id out of range sets GK_ERR_INVALID in the
  * status word and that visit makes no move.
- * One thread-block cluster runs the epoch (the visits are sequential by
- * definition; a visit's FP64 work is spread over the cluster's SMs); a visit
- * costs (candidates + 1) FP64 rows of d elements read, and 2 rows written
- * when it moves.
+ * The result is that of the visits made one after another.  One thread-block
+ * cluster (up to 16 CTAs) runs the epoch: it evaluates windows of up to 32
+ * visits against the state at the window's start and commits them in order
+ * up to the first visit that depends on an earlier move of the window (its
+ * sample or a neighbour moved, or its own cluster or a candidate was left or
+ * joined); the rest is evaluated again in the next window.  A visit costs
+ * (candidates + 1) FP64 rows of d elements read, and 2 rows written when it
+ * moves.
  */
 GK_API int gk_boost_init(const float *X, int64_t n, int64_t d, int64_t ld, const int32_t *labels, int32_t k,
                          double *D, int32_t *counts, double *S, void *ws, size_t ws_bytes, void *stream);
