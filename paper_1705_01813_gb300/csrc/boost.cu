@@ -27,6 +27,7 @@
 // cluster's SMs.  After a move, S_u and S_v are the two norms already computed
 // for the decision: the new rows are exactly the rounded sums that were
 // squared.
+#include <climits>
 #include <map>
 #include <mutex>
 
@@ -59,7 +60,7 @@ __device__ __forceinline__ double fold_lanes(double (&w)[PL])
 template <typename XT>
 __device__ __forceinline__ double ldx64(const XT *p)
 {
-    return (double)ldx(p);
+    return widen(ldx(p));
 }
 
 // ---------------------------------------------------------------------------
@@ -139,6 +140,7 @@ constexpr int BE_THREADS = 256;
 constexpr int BE_WARPS = BE_THREADS / 32;
 constexpr int BE_MAX_CLUSTER = 16;
 constexpr int BE_MAX_WINDOW = 32;
+constexpr int BE_HASH = 128;  // entries of each commit hash table (at most 2 x 32 keys)
 constexpr size_t BE_SMEM_BUDGET = 200 * 1024;
 
 __device__ __forceinline__ void cluster_barrier()
@@ -183,7 +185,8 @@ __device__ __forceinline__ void st_rank(const void *p, int rank, int v)
 // Dynamic shared memory of one CTA for windows of W visits (the same layout in every CTA of the cluster).
 struct WinLayout {
     int W, kp, TM, TL;
-    size_t xs, ra, r1, r3, gk, la, ls, rn, ln, lo, tv, sq, sg, svis, su, snq, sbase, dq, ml, tl, mvj, bytes;
+    size_t xs, ra, r1, r3, gk, vbest, vwin, la, ls, rn, ln, lo, tv, sq, sg, svis, su, snq, sbase, dq, ml, tl, mvj,
+        hkey, hval, bytes;
     __host__ __device__ WinLayout(int W_, int P, int kappa, int R)
     {
         W = W_;
@@ -201,6 +204,8 @@ struct WinLayout {
         r1 = take((size_t)TM * 8);
         r3 = take((size_t)TM * 8);
         gk = take((size_t)TM * 8);
+        vbest = take((size_t)W * 8);
+        vwin = take((size_t)W * 8);
         la = take((size_t)TL * 8);
         ls = take((size_t)TL * 8);
         rn = take((size_t)TM * 4);
@@ -217,6 +222,8 @@ struct WinLayout {
         ml = take((size_t)W * 4);
         tl = take((size_t)2 * W * 4);
         mvj = take((size_t)W * 4);
+        hkey = take((size_t)2 * BE_HASH * 4);
+        hval = take((size_t)2 * BE_HASH * 4);
         bytes = o;
     }
 };
@@ -238,6 +245,9 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
     double *ra = reinterpret_cast<double *>(smem + Y.ra), *r1 = reinterpret_cast<double *>(smem + Y.r1);
     double *r3 = reinterpret_cast<double *>(smem + Y.r3);
     long long *gk = reinterpret_cast<long long *>(smem + Y.gk);
+    long long *vbest = reinterpret_cast<long long *>(smem + Y.vbest);
+    unsigned long long *vwin = reinterpret_cast<unsigned long long *>(smem + Y.vwin);
+    int *hkey = reinterpret_cast<int *>(smem + Y.hkey), *hval = reinterpret_cast<int *>(smem + Y.hval);
     int *tv = reinterpret_cast<int *>(smem + Y.tv);
     double *la = reinterpret_cast<double *>(smem + Y.la), *ls = reinterpret_cast<double *>(smem + Y.ls);
     int *rn = reinterpret_cast<int *>(smem + Y.rn), *ln = reinterpret_cast<int *>(smem + Y.ln);
@@ -255,8 +265,11 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
     for (int64_t s = 0; s < m;) {
         const int Wn = (int)(m - s < (int64_t)We ? m - s : (int64_t)We);
         // ---- the window's visits: ids, then samples, graph rows and own labels, then the neighbours' labels
-        if (threadIdx.x < Wn)
+        if (threadIdx.x < Wn) {
             svis[threadIdx.x] = __ldg(order + s + threadIdx.x);
+            vbest[threadIdx.x] = LLONG_MIN;
+            vwin[threadIdx.x] = ~0ull;
+        }
         __syncthreads();
         if (threadIdx.x < Wn) {
             const int i = svis[threadIdx.x];
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
 #pragma unroll
             for (int b = 0; b < 8; b++)
                 if (e0 + b * BE_THREADS < Wn * P)
-                    xs[e0 + b * BE_THREADS] = (double)v[b];
+                    xs[e0 + b * BE_THREADS] = widen(v[b]);  // on the integer pipe: the FP64 one is narrow
         }
         for (int e0 = threadIdx.x; e0 < Wn * kp; e0 += 8 * BE_THREADS) {
             int v[8];
@@ -424,87 +437,103 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
 
         // ---- CTA 0: each visit's arg-max, the in-order commit and the committed moves
         if (rank == 0) {
-            // the gain of every candidate task, as an integer key in the order of the FP64 values (the gains are
-            // sums and differences of non-negative terms, never -0, so the keys order them exactly)
+            // the gain of every candidate task as an integer key in the order of the FP64 values (the gains are sums
+            // and differences of non-negative terms, never -0, so the keys order them exactly); each visit's largest
+            // key, then the smallest (label, candidate) among the tasks that reach it
             for (int t = threadIdx.x; t < T; t += BE_THREADS) {
-                const int o = sbase[tv[t]];
+                const int j = tv[t], o = sbase[j];
                 if (t != o) {
                     const double g = __dsub_rn(__dsub_rn(__dadd_rn(r1[t], r1[o]), r3[t]), r3[o]);
                     const long long b = __double_as_longlong(g);
-                    gk[t] = b ^ ((b >> 63) & 0x7fffffffffffffffll);
+                    const long long key = b ^ ((b >> 63) & 0x7fffffffffffffffll);
+                    gk[t] = key;
+                    atomicMax(&vbest[j], key);
                 }
             }
             __syncthreads();
-            for (int j = w; j < Wn; j += BE_WARPS) {
-                const int nq = snq[j], o = sbase[j];
-                int bt = -1, bv = -1;
-                long long best = 0;
-                if (nq > 0 && rn[o] >= 2) {
-                    for (int c = 1 + lane; c <= nq; c += 32) {
-                        const int t = o + c, v = sq[j * kp + c - 1];
-                        const long long g = gk[t];
-                        if (bv < 0 || g > best || (g == best && v < bv)) {
-                            best = g;
-                            bv = v;
-                            bt = t;
-                        }
-                    }
-#pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        const long long ob = __shfl_xor_sync(FULL_MASK, best, off);
-                        const int ov = __shfl_xor_sync(FULL_MASK, bv, off), ot = __shfl_xor_sync(FULL_MASK, bt, off);
-                        if (ov >= 0 && (bv < 0 || ob > best || (ob == best && ov < bv))) {
-                            best = ob;
-                            bv = ov;
-                            bt = ot;
-                        }
-                    }
-                }
-                if (lane == 0)
-                    dq[j] = bv >= 0 && best > 0 ? bt : -1;  // key > 0: gain > +0
+            for (int t = threadIdx.x; t < T; t += BE_THREADS) {
+                const int j = tv[t], o = sbase[j];
+                if (t != o && gk[t] == vbest[j])
+                    atomicMin(&vwin[j], ((unsigned long long)(unsigned)sq[j * kp + t - o - 1] << 16) | (unsigned)(t - o));
+            }
+            for (int e = threadIdx.x; e < 2 * BE_HASH; e += BE_THREADS) {  // empty hash tables
+                hkey[e] = -1;
+                hval[e] = 0x7fffffff;
             }
             __syncthreads();
-            // the visits that would move, in order: sample ml, clusters tl[2 q] (from) and tl[2 q + 1] (to)
-            if (threadIdx.x == 0) {
-                int nm = 0;
-                for (int j = 0; j < Wn; j++) {
-                    const int t = dq[j];
-                    if (t >= 0) {
-                        ml[nm] = svis[j];
-                        mvj[nm] = j;
-                        tl[2 * nm] = su[j];
-                        tl[2 * nm + 1] = sq[j * kp + t - sbase[j] - 1];
-                        nm++;
+            // the visits that would move (key > 0: gain > +0; the own cluster keeps two members or more), in order:
+            // sample ml, clusters tl[2 q] (from) and tl[2 q + 1] (to)
+            if (w == 0) {
+                int t = -1;
+                if (lane < Wn && snq[lane] > 0 && rn[sbase[lane]] >= 2 && vbest[lane] > 0)
+                    t = sbase[lane] + (int)(vwin[lane] & 0xffff);
+                if (lane < Wn)
+                    dq[lane] = t;
+                const unsigned mm = __ballot_sync(FULL_MASK, t >= 0);
+                if (t >= 0) {
+                    const int q = __popc(mm & lanemask_lt());
+                    ml[q] = svis[lane];
+                    mvj[q] = lane;
+                    tl[2 * q] = su[lane];
+                    tl[2 * q + 1] = (int)(vwin[lane] >> 16);
+                }
+                if (lane == 0) {
+                    s_nm = __popc(mm);
+                    s_first = Wn;
+                }
+            }
+            __syncthreads();
+            // hash tables keyed by sample and by cluster: the earliest moving visit that moves that sample, or leaves
+            // or joins that cluster
+            const int nmv = s_nm;
+            if (threadIdx.x < 3 * nmv) {
+                const int q = threadIdx.x / 3, part = threadIdx.x - 3 * q;
+                const int x = part == 0 ? ml[q] : tl[2 * q + part - 1];
+                int *keys = hkey + (part == 0 ? 0 : BE_HASH), *vals = hval + (part == 0 ? 0 : BE_HASH);
+                for (int h = (int)(((unsigned)x * 2654435761u) >> 25), probe = 0; probe < BE_HASH;
+                     h = (h + 1) & (BE_HASH - 1), probe++) {
+                    const int prev = atomicCAS(&keys[h], -1, x);
+                    if (prev == -1 || prev == x) {
+                        atomicMin(&vals[h], mvj[q]);
+                        break;
                     }
                 }
-                s_nm = nm;
-                s_first = Wn;
             }
             __syncthreads();
             // the window commits up to the first visit that depends on an earlier moving visit: its sample or a
             // neighbour is that visit's sample, or its own cluster or a candidate is one that visit leaves or joins
-            {
-                const int nmv = s_nm, per = 1 + kp + 1 + kp;  // items of a visit: sample, neighbours, own, candidates
-                for (int e = threadIdx.x; nmv > 0 && e < Wn * per; e += BE_THREADS) {
-                    const int j = e / per, c = e - j * per;
-                    int x = -1;
-                    bool sample = true;
-                    if (c == 0) {
-                        x = svis[j];
-                    } else if (c <= kp) {
-                        x = c - 1 < kappa ? sg[j * kp + c - 1] : -1;
-                    } else if (su[j] >= 0) {
-                        sample = false;
-                        const int cc = c - kp - 1;  // 0: own cluster, else candidate cc - 1
-                        x = cc == 0 ? su[j] : (cc <= snq[j] ? sq[j * kp + cc - 1] : -1);
-                    }
-                    if (x < 0)
-                        continue;
-                    for (int q = 0; q < nmv && mvj[q] < j; q++)
-                        if (sample ? ml[q] == x : (tl[2 * q] == x || tl[2 * q + 1] == x)) {
-                            atomicMin(&s_first, j);
-                            break;
+            auto earliest = [&](int x, int table) {  // the earliest moving visit recorded for x, or Wn
+                const int *keys = hkey + table * BE_HASH, *vals = hval + table * BE_HASH;
+                for (int h = (int)(((unsigned)x * 2654435761u) >> 25), probe = 0; probe < BE_HASH;
+                     h = (h + 1) & (BE_HASH - 1), probe++) {
+                    const int kx = keys[h];
+                    if (kx == x)
+                        return vals[h];
+                    if (kx == -1)
+                        break;
+                }
+                return 0x7fffffff;
+            };
+            if (nmv > 0) {
+                const int per = 1 + kappa + 1 + kp;  // a visit's items: sample, neighbours, own cluster, candidates
+                for (int j = mvj[0] + 1 + w; j < Wn; j += BE_WARPS) {
+                    bool hit = false;
+                    for (int c = lane; c < per; c += 32) {
+                        int x = -1, table = 0;
+                        if (c == 0) {
+                            x = svis[j];
+                        } else if (c <= kappa) {
+                            x = sg[j * kp + c - 1];
+                        } else if (su[j] >= 0) {
+                            table = 1;
+                            const int cc = c - kappa - 1;  // 0: own cluster, else candidate cc - 1
+                            x = cc == 0 ? su[j] : (cc <= snq[j] ? sq[j * kp + cc - 1] : -1);
                         }
+                        if (x >= 0 && earliest(x, table) < j)
+                            hit = true;
+                    }
+                    if (__any_sync(FULL_MASK, hit) && lane == 0)
+                        atomicMin(&s_first, j);
                 }
             }
             __syncthreads();
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
                     st_rank(&s_win, lane, done);
             }
             int nm = 0;  // the committed moves: the moving visits before `done`
-            while (nm < s_nm && mvj[nm] < done)
+            while (nm < nmv && mvj[nm] < done)
                 nm++;
             // the committed moves touch disjoint clusters: x leaves S_u for S_v in each
             for (int e = threadIdx.x; e < nm * d; e += BE_THREADS) {

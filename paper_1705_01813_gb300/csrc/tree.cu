@@ -63,27 +63,6 @@ __device__ __forceinline__ uint32_t f32_order(float f)
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// FP32 -> FP64 widening on the integer pipe (every binary32 value is a binary64 value: the fields are moved, a
-// subnormal is normalised).  GB300's FP64 pipe is narrow, and the Lloyd sums keep it busy with their additions.
-__device__ __forceinline__ double widen(float x)
-{
-    const uint32_t u = __float_as_uint(x);
-    const uint64_t sign = (uint64_t)(u >> 31) << 63;
-    const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-    uint64_t bits;
-    if (e == 0xFFu) {
-        bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
-    } else if (e != 0) {
-        bits = sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29);
-    } else if (m == 0) {
-        bits = sign;
-    } else {
-        const int p = 31 - __clz(m);  // leading one of the subnormal's m * 2^-149
-        bits = sign | ((uint64_t)(p + 874) << 52) | ((uint64_t)(m ^ (1u << p)) << (52 - p));
-    }
-    return __longlong_as_double((long long)bits);
-}
-
 __device__ __forceinline__ bool hk_less(uint64_t ha, int ia, uint64_t hb, int ib)
 {
     return ha < hb || (ha == hb && ia < ib);
