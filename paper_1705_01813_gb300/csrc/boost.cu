@@ -515,23 +515,17 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
                 return 0x7fffffff;
             };
             if (nmv > 0) {
-                const int per = 1 + kappa + 1 + kp;  // a visit's items: sample, neighbours, own cluster, candidates
                 for (int j = mvj[0] + 1 + w; j < Wn; j += BE_WARPS) {
                     bool hit = false;
-                    for (int c = lane; c < per; c += 32) {
-                        int x = -1, table = 0;
-                        if (c == 0) {
-                            x = svis[j];
-                        } else if (c <= kappa) {
-                            x = sg[j * kp + c - 1];
-                        } else if (su[j] >= 0) {
-                            table = 1;
-                            const int cc = c - kappa - 1;  // 0: own cluster, else candidate cc - 1
-                            x = cc == 0 ? su[j] : (cc <= snq[j] ? sq[j * kp + cc - 1] : -1);
-                        }
-                        if (x >= 0 && earliest(x, table) < j)
-                            hit = true;
+                    for (int c = lane; c <= kappa; c += 32) {  // the sample (c = 0) and its neighbours
+                        const int x = c == 0 ? svis[j] : sg[j * kp + c - 1];
+                        hit |= x >= 0 && earliest(x, 0) < j;
                     }
+                    if (su[j] >= 0)
+                        for (int c = lane; c <= snq[j]; c += 32) {  // the own cluster (c = 0) and the candidates
+                            const int x = c == 0 ? su[j] : sq[j * kp + c - 1];
+                            hit |= earliest(x, 1) < j;
+                        }
                     if (__any_sync(FULL_MASK, hit) && lane == 0)
                         atomicMin(&s_first, j);
                 }
