@@ -132,16 +132,17 @@ __global__ void __launch_bounds__(RF_THREADS, T == 64 ? 3 : 2) k_refine(const XT
 }
 
 // Runs of at most 64 members, warp-specialised: a persistent block takes runs blockIdx.x, + gridDim.x, ...; five
-// of its warps (the compute group, WS_NC threads, rotated over the block's warps by blockIdx.x so that the blocks
-// of an SM spread them over its four schedulers) stage and compute a run's pair tile while the other three merge
-// the previous run's rows.  The two hand the distance tile over through named barriers: FULL (the compute group
+// of its nine warps (the compute group, WS_NC threads, rotated over the block's warps by blockIdx.x so that the
+// blocks of an SM spread them over its four schedulers) stage and compute a run's pair tile while the other four
+// merge the previous run's rows.  The two hand the distance tile over through named barriers: FULL (the compute group
 // arrives when the tile and the run's ids are written, the merge warps wait) and EMPTY (the merge warps arrive
 // when they no longer read it, the compute group waits before writing the next one).  Both sides walk the same
 // runs with the same skips, so the barriers pair up: per run one FULL and one EMPTY phase, plus the EMPTY phase
 // the merge warps open before the first run and the compute group closes after the last.  Pair arithmetic,
 // merge order and results are those of k_refine<64>.
 constexpr int WS_NC = 160;  // compute group: 5 warps, covers the 136 pair blocks of a 64-row triangle
-constexpr int WS_NM = 3;    // merge warps
+constexpr int WS_NM = 4;    // merge warps
+constexpr int WS_THREADS = WS_NC + 32 * WS_NM;
 constexpr int WS_BAR_C = 1, WS_BAR_FULL = 2, WS_BAR_EMPTY = 3;
 
 // dynamic shared memory: two stage buffers, the distance tile, the run ids of two runs, the merge warps' buffers
@@ -152,7 +153,7 @@ __host__ __device__ inline size_t refine_ws_smem_bytes(int kappa)
 }
 
 template <typename XT, bool VEC>
-__global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
+__global__ void __launch_bounds__(WS_THREADS, 3) k_refine_ws(const XT *__restrict__ X, int64_t n, int d, int64_t ld,
                                                              const int32_t *__restrict__ off,
                                                              const int32_t *__restrict__ mem,
                                                              const int32_t *__restrict__ run_off,
@@ -163,14 +164,14 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
     constexpr int T = 64;
     using TL = RefineTile<T>;
     constexpr int DS = TL::DS, Q = TL::Q;
-    static_assert(WS_NC + 32 * WS_NM == RF_THREADS, "the block's warps are the two groups");
+    constexpr int WARPS = WS_THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *stage = reinterpret_cast<float *>(smem_raw);
     float *dt = stage + TL::stage_floats;
     int *rids = reinterpret_cast<int *>(dt + TL::tile_floats);  // [2][T]: the ids of runs j and j + 1
     unsigned char *mbase = reinterpret_cast<unsigned char *>(rids + 2 * T);
     const int w = threadIdx.x >> 5, lane = lane_id();
-    const int rr = (w - (int)(blockIdx.x & 3)) & 7;  // 0 .. 4: compute group, 5 .. 7: merge warps
+    const int rr = (w + WARPS - (int)(blockIdx.x & 3)) % WARPS;  // 0 .. 4: compute group, 5 .. 8: merge warps
     const int nruns = run_off[k];
     // run `run`: its cluster, first member (in mem) and size, as k_refine cuts clusters into runs
     auto geometry = [&](int run, int &r, int &first, int &sz) {
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
             float2 acc[Q][Q / 2];
             int by, bx;
             const bool live = tile_distances_group<WS_NC, VEC>(X, d, ld, rid, sz, stage, ct, WS_BAR_C, acc, by, bx);
-            bar_sync(WS_BAR_EMPTY, RF_THREADS);  // the merge warps no longer read the distance tile
+            bar_sync(WS_BAR_EMPTY, WS_THREADS);  // the merge warps no longer read the distance tile
             if (live) {
 #pragma unroll
                 for (int a = 0; a < Q; a++)
@@ -218,10 +219,10 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
                     }
             }
             __threadfence_block();
-            bar_arrive(WS_BAR_FULL, RF_THREADS);  // this run's ids and distance tile are in place
+            bar_arrive(WS_BAR_FULL, WS_THREADS);  // this run's ids and distance tile are in place
             j++;
         }
-        bar_sync(WS_BAR_EMPTY, RF_THREADS);  // the merge warps' arrival after the last run
+        bar_sync(WS_BAR_EMPTY, WS_THREADS);  // the merge warps' arrival after the last run
     } else {
         // ---- merge warps ----
         const int mw = rr - 5;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
         uint64_t *nk = rk + kappa;
         uint64_t *bk = nk + kappa;
         unsigned *dup = reinterpret_cast<unsigned *>(bk + T);
-        bar_arrive(WS_BAR_EMPTY, RF_THREADS);  // the distance tile starts free
+        bar_arrive(WS_BAR_EMPTY, WS_THREADS);  // the distance tile starts free
         int j = 0;
         for (int run = blockIdx.x; run < nruns; run += gridDim.x) {
             int r, first, sz;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
             if (sz < 2 || sz > T)
                 continue;
             const int *rid = rids + (j & 1) * T;
-            bar_sync(WS_BAR_FULL, RF_THREADS);  // run j's ids and distances
+            bar_sync(WS_BAR_FULL, WS_THREADS);  // run j's ids and distances
             RowRegs cur, nxt;
             if (mw < sz && rid[mw] >= 0)
                 load_row(cur, g_idx + (int64_t)rid[mw] * kappa, g_dist + (int64_t)rid[mw] * kappa, kappa);
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(RF_THREADS, 3) k_refine_ws(const XT *__restric
                 cur = nxt;
             }
             __threadfence_block();
-            bar_arrive(WS_BAR_EMPTY, RF_THREADS);  // done with the distance tile and this slot of ids
+            bar_arrive(WS_BAR_EMPTY, WS_THREADS);  // done with the distance tile and this slot of ids
             j++;
         }
     }
@@ -323,10 +324,10 @@ static cudaError_t refine_tv(const XT *X, int64_t n, int64_t d, int64_t ld, cons
     // against 7.7 ms; 1M x 128 FP32: 3.7 against 3.9 ms)
     if constexpr (VEC) {
         int wgrid = 0;
-        if ((e = resident_grid(reinterpret_cast<const void *>(k_refine_ws<XT, VEC>), RF_THREADS, shm_ws, &wgrid)) !=
+        if ((e = resident_grid(reinterpret_cast<const void *>(k_refine_ws<XT, VEC>), WS_THREADS, shm_ws, &wgrid)) !=
             cudaSuccess)
             return e;
-        k_refine_ws<XT, VEC><<<(unsigned)(grid < wgrid ? grid : wgrid), RF_THREADS, shm_ws, s>>>(
+        k_refine_ws<XT, VEC><<<(unsigned)(grid < wgrid ? grid : wgrid), WS_THREADS, shm_ws, s>>>(
             X, n, (int)d, ld, offsets, members, run_off, run_cl, k, kappa, max_cluster, g_idx, g_dist, st);
     } else {
         (void)shm_ws;
