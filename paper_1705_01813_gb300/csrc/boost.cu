@@ -123,24 +123,27 @@ __global__ void __launch_bounds__(256) k_boost_norms(const double *__restrict__ 
 // every CTA stages the window's samples and gathers the candidate sets; the
 // squared norms of all the window's (visit, cluster) tasks are spread over the
 // cluster's warps, and each CTA divides its own tasks' terms (lanes over
-// tasks) and stores them into CTA 0.  CTA 0 takes each visit's arg-max, then
-// commits the visits in order up to the first one whose inputs an earlier
-// committed move of the window changed (its sample or one of its neighbours
-// moved; its own cluster or a candidate was the source or target of a move).
+// tasks) and stores them into CTA 0.  CTA 0 takes each visit's arg-max (a
+// shared atomicMax of the gain keys, then an atomicMin of (label, candidate)
+// among the tasks at the maximum), then commits the visits in order up to the
+// first one whose inputs an earlier committed move of the window changed (its
+// sample or one of its neighbours moved; its own cluster or a candidate was
+// the source or target of a move), found by looking every visit's items up in
+// two small hash tables of the moving visits' samples and clusters.
 // A committed visit therefore saw exactly the state the sequential walk gives
 // it, and the committed moves touch disjoint clusters, so CTA 0 applies them
 // together; the next window starts at the first visit not committed (the
 // first visit of a window always commits).  The window grows while windows
 // commit whole and shrinks to twice what the last one committed, so that few
 // evaluations are thrown away where moves collide often.  Both cluster
-// barriers of a window are unconditional.  Mutable state (labels, D, S, counts) is read through L2
-// (ld.global.cg), which the barriers order.
+// barriers of a window are unconditional.  Mutable state (labels, D, S,
+// counts) is read through L2 (ld.global.cg), which the barriers order.
 // ---------------------------------------------------------------------------
 constexpr int BE_THREADS = 256;
 constexpr int BE_WARPS = BE_THREADS / 32;
 constexpr int BE_MAX_CLUSTER = 16;
 constexpr int BE_MAX_WINDOW = 32;
-constexpr int BE_HASH = 128;  // entries of each commit hash table (at most 2 x 32 keys)
+constexpr int BE_HASH = 128;  // entries of each commit hash table (at most 32 samples, 64 clusters)
 constexpr size_t BE_SMEM_BUDGET = 200 * 1024;
 
 __device__ __forceinline__ void cluster_barrier()
@@ -453,8 +456,10 @@ __global__ void __launch_bounds__(BE_THREADS, 1)
             __syncthreads();
             for (int t = threadIdx.x; t < T; t += BE_THREADS) {
                 const int j = tv[t], o = sbase[j];
-                if (t != o && gk[t] == vbest[j])
-                    atomicMin(&vwin[j], ((unsigned long long)(unsigned)sq[j * kp + t - o - 1] << 16) | (unsigned)(t - o));
+                if (t != o && gk[t] == vbest[j]) {
+                    const unsigned long long label = (unsigned)sq[j * kp + t - o - 1];
+                    atomicMin(&vwin[j], (label << 16) | (unsigned)(t - o));
+                }
             }
             for (int e = threadIdx.x; e < 2 * BE_HASH; e += BE_THREADS) {  // empty hash tables
                 hkey[e] = -1;
