@@ -115,3 +115,24 @@ def test_argument_errors(lib):
     big, small = (gkm.workspace_size(gkm.GK_OP_TREE, 100000, 64, k) for k in (4096, 2))
     assert big - small >= (4096 - 2) * 2 * 64 * 4 and small >= 100000 * 16
     assert lib.gk_read_status(None, None) == gkm.GK_ERR_INVALID
+    # the boost form: d up to 1024, 1 <= k <= n, the state arrays, kappa, the visit count and sequence
+    big = 1 << 30
+    assert gkm.workspace_size(gkm.GK_OP_BOOST, 100000, 64, 100) > gkm.workspace_size(gkm.GK_OP_BOOST, 1000, 64, 100)
+    assert lib.gk_boost_init(P, 10, 1025, 1025, P, 2, P, P, P, ws, big, None) == gkm.GK_ERR_INVALID
+    assert b"1024" in lib.gk_last_error()
+    assert lib.gk_boost_init(P, 10, 4, 4, P, 0, P, P, P, ws, big, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_boost_init(P, 10, 4, 4, P, 11, P, P, P, ws, big, None) == gkm.GK_ERR_INVALID
+    assert b"k = 11" in lib.gk_last_error()
+    assert lib.gk_boost_init(P, 10, 4, 4, P, 2, None, P, P, ws, big, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_boost_init(P, 10, 4, 4, None, 2, P, P, P, ws, big, None) == gkm.GK_ERR_INVALID
+    assert b"labels" in lib.gk_last_error()
+    assert lib.gk_boost_init(P, 10, 4, 4, P, 2, P, P, P, ws, 16, None) == gkm.GK_ERR_INVALID
+    assert b"too small" in lib.gk_last_error()
+    assert lib.gk_boost_epoch(P, 10, 4, 4, P, 10, P, 5, P, 2, P, P, P, None, ws, big, None) == gkm.GK_ERR_INVALID
+    assert b"kappa" in lib.gk_last_error()
+    assert lib.gk_boost_epoch(P, 10, 4, 4, P, 3, P, -1, P, 2, P, P, P, None, ws, big, None) == gkm.GK_ERR_INVALID
+    assert b"m = -1" in lib.gk_last_error()
+    assert lib.gk_boost_epoch(P, 10, 4, 4, P, 3, None, 5, P, 2, P, P, P, None, ws, big, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_boost_epoch(P, 10, 4, 4, None, 3, P, 5, P, 2, P, P, P, None, ws, big, None) == gkm.GK_ERR_INVALID
+    assert lib.gk_boost_epoch_bf16(P, 10, 2000, 2000, P, 3, P, 5, P, 2, P, P, P, None, ws, big,
+                                   None) == gkm.GK_ERR_INVALID
