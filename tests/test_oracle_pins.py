@@ -640,6 +640,50 @@ def test_paper_trends():
     assert Et[-1] < Ef[-1]
 
 
+def _boost_windows(orc, X, G, order, L0, k, rng, rule=True):
+    """The speculative schedule of the GPU epoch, restated on the oracle: every visit of a window is decided
+    against the state at the window's start; the window commits, in order, up to the first visit that depends on
+    an earlier visit of the window that would move (its sample or a neighbour is that visit's sample, or its own
+    cluster or a candidate is one that visit leaves or joins; with rule=False whole windows commit). Returns the
+    number of committed visits whose speculative decision differs from the sequential walk's."""
+    D, cnt, S = orc.boost_init(X, L0, k)
+    L, s, wrong = L0.copy(), 0, 0
+    while s < len(order):
+        win = order[s:s + int(rng.integers(1, 33))]
+        moving, spec, first = [], [], len(win)
+        for p_, i in enumerate(win):
+            u = int(L[i])
+            items_s, items_c = {int(i)} | set(G[i].tolist()), {u} | (set(L[G[i]].tolist()) - {u})
+            if rule and any(mi in items_s or mu in items_c or mv in items_c for mi, mu, mv in moving):
+                first = p_
+                break
+            v = int(orc.boost_epoch(X, G, [i], L, k, D, cnt, S)[0][i])  # against the window's start state
+            spec.append(v)
+            if v != u:
+                moving.append((int(i), u, v))
+        for p_ in range(first):  # the sequential walk over the committed visits, one visit at a time
+            L, D, cnt, S = orc.boost_epoch(X, G, win[p_:p_ + 1], L, k, D, cnt, S)[:4]
+            wrong += int(L[win[p_]]) != spec[p_]
+        s += first
+    return wrong
+
+
+def test_boost_window_commit_rule_matches_sequential_decisions():
+    """Every visit the GPU epoch's window schedule commits was decided on exactly the state the sequential walk
+    gives it, whatever the window sizes; without the dependence rule, some speculative decisions are wrong."""
+    orc = O.default()
+    rng = np.random.default_rng(4)
+    wrong_without = 0
+    for n, d, k, kappa in ((300, 3, 12, 6), (200, 2, 40, 5)):
+        X = rng.integers(-30, 31, (n, d)).astype(np.float32)
+        L0 = rng.integers(0, k, n).astype(np.int32)
+        L0[:k] = np.arange(k)
+        G = np.stack([rng.choice(np.delete(np.arange(n), i), kappa, replace=False) for i in range(n)]).astype(np.int32)
+        order = rng.integers(0, n, 3 * n).astype(np.int32)
+        assert _boost_windows(orc, X, G, order, L0, k, np.random.default_rng(1)) == 0
+        wrong_without += _boost_windows(orc, X, G, order, L0, k, np.random.default_rng(1), rule=False)
+    assert wrong_without > 0
+
 # ------------------------------------------------------- planted mistakes ----
 
 MUTANTS = [
